@@ -1,0 +1,147 @@
+"""ctypes binding of the FP64 CPU oracle (``mhd_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by the smoke check and by
+the CPU-baseline leg of the benchmark.  The product path never imports it.
+
+Layout of the arrays passed in and out (float64, C order):
+  U: (5, nz, ny, nx)  rho, Mx, My, Mz, e   (cell averages, Eq. 11)
+  B: (3, nz, ny, nx)  Bx at x_{i-1/2}, By at y_{j-1/2}, Bz at z_{k-1/2} (Eq. 14)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mhd_oracle.c")
+_LIB = os.path.join(_HERE, "libmhd_oracle.so")
+
+VL, CTU = 0, 1
+PLM, PPM, PLM_PRIM = 0, 1, 2
+ROE, HLLD, HLLE = 0, 1, 2
+
+INTEGRATORS = {"vl": VL, "ctu": CTU}
+RECONS = {"plm": PLM, "ppm": PPM, "plm_prim": PLM_PRIM}
+SOLVERS = {"roe": ROE, "hlld": HLLD, "hlle": HLLE}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-ffp-contract=off: no fused multiply-add)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC",
+               "-o", _LIB, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.orc_step.restype = ctypes.c_long
+        L.orc_step.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [ctypes.c_int] * 3 + \
+                              [ctypes.c_double, dp, dp]
+        L.orc_cfl_dt.restype = ctypes.c_double
+        L.orc_cfl_dt.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double] * 3 + [dp, dp]
+        L.orc_divB.restype = None
+        L.orc_divB.argtypes = [ctypes.c_int] * 3 + [dp, dp, dp]
+        L.orc_sums.restype = None
+        L.orc_sums.argtypes = [ctypes.c_int] * 3 + [dp, dp, dp]
+        L.orc_prim.restype = None
+        L.orc_prim.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double, dp, dp, dp]
+        L.orc_eigen.restype = None
+        L.orc_eigen.argtypes = [dp, ctypes.c_double, ctypes.c_double, dp, dp, dp]
+        L.orc_riemann.restype = ctypes.c_int
+        L.orc_riemann.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double, dp]
+        L.orc_roe_waves.restype = ctypes.c_int
+        L.orc_roe_waves.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double, dp, dp, dp]
+        L.orc_flux_phys.restype = None
+        L.orc_flux_phys.argtypes = [dp, ctypes.c_double, ctypes.c_double, dp]
+        L.orc_recon_cell.restype = None
+        L.orc_recon_cell.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double, dp, dp]
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def step(U: np.ndarray, B: np.ndarray, dx: float, gamma: float, dt: float,
+         integrator="vl", recon="plm", riemann="roe") -> int:
+    """Advance (U, B) in place by dt; returns the count of Roe->HLLE fallbacks."""
+    nz, ny, nx = U.shape[1:]
+    assert U.shape == (5, nz, ny, nx) and B.shape == (3, nz, ny, nx)
+    return int(lib().orc_step(nx, ny, nz, dx, gamma, INTEGRATORS[integrator], RECONS[recon],
+                              SOLVERS[riemann], dt, _p(U), _p(B)))
+
+
+def cfl_dt(U, B, dx, gamma, cfl) -> float:
+    nz, ny, nx = U.shape[1:]
+    return float(lib().orc_cfl_dt(nx, ny, nz, dx, gamma, cfl, _p(U), _p(B)))
+
+
+def divB(B) -> tuple[float, float]:
+    """(max_c |sum_d dB_d| (= |div B| dx), B_rms)."""
+    nz, ny, nx = B.shape[1:]
+    m = np.zeros(1); r = np.zeros(1)
+    lib().orc_divB(nx, ny, nz, _p(B), _p(m), _p(r))
+    return float(m[0]), float(r[0])
+
+
+def sums(U, B) -> np.ndarray:
+    nz, ny, nx = U.shape[1:]
+    out = np.zeros(8)
+    lib().orc_sums(nx, ny, nz, _p(U), _p(B), _p(out))
+    return out
+
+
+def prim(U, B, gamma) -> np.ndarray:
+    nz, ny, nx = U.shape[1:]
+    W = np.zeros((8, nz, ny, nx))
+    lib().orc_prim(nx, ny, nz, gamma, _p(U), _p(B), _p(W))
+    return W
+
+
+def eigen(w, bn, gamma):
+    w = _f64(w); lam = np.zeros(7); R = np.zeros(49); L = np.zeros(49)
+    lib().orc_eigen(_p(w), bn, gamma, _p(lam), _p(R), _p(L))
+    return lam, R.reshape(7, 7), L.reshape(7, 7)
+
+
+def riemann(solver, wl, wr, bn, gamma):
+    wl = _f64(wl); wr = _f64(wr); f = np.zeros(7)
+    fb = lib().orc_riemann(SOLVERS[solver], _p(wl), _p(wr), bn, gamma, _p(f))
+    return f, int(fb)
+
+
+def roe_waves(wl, wr, bn, gamma):
+    wl = _f64(wl); wr = _f64(wr)
+    lam = np.zeros(7); eta = np.zeros(7); ru = np.zeros(49)
+    ok = lib().orc_roe_waves(_p(wl), _p(wr), bn, gamma, _p(lam), _p(eta), _p(ru))
+    return bool(ok), lam, eta, ru.reshape(7, 7)
+
+
+def flux_phys(w, bn, gamma):
+    w = _f64(w); f = np.zeros(7)
+    lib().orc_flux_phys(_p(w), bn, gamma, _p(f))
+    return f
+
+
+def recon_cell(recon, w5, bn5, gamma, trace=False, dtdx=0.0):
+    w5 = _f64(w5).reshape(5, 7); bn5 = _f64(bn5)
+    wm = np.zeros(7); wp = np.zeros(7)
+    lib().orc_recon_cell(RECONS[recon], int(trace), _p(w5), _p(bn5), gamma, dtdx, _p(wm), _p(wp))
+    return wm, wp
