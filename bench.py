@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Benchmark of the MHD patch advance: cell-updates/s on the 256^3 ABC box.
+
+One step = the whole hot path: primitives + CFL dt (on the device), the
+VL (or CTU) predictor sweeps, edge E, half update, corrector sweeps, edge E
+and the full CT + conservative update.  Inputs are synthetic (seeded ABC
+field, k = 4 pi, beta = 0.5, velocity noise 1e-3 c_s) and resident in HBM
+when the timed region starts; the state (8 x 256^3 values, 537 MB in FP32)
+is larger than the 126 MB L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank advances its own replica of the box
+(the path has no exchange step on one box per GPU: replicas only); the
+value is the aggregate over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s at 256³ ABC MHD (FP64 plain vs FP32/learned) + HBM roofline %"
+UNIT = "cell-updates/s"
+PAPER_P100 = {"fp32": 1.2e8, "fp64": 5.5e7}   # Sec. 5.2 (i), Tesla P100, VL + PLM + Roe
+GROUPS = ["prim_cfl", "predictor_sweeps", "emf1", "half_update", "corrector_sweeps", "emf2", "full_update"]
+SIZES = {"fp64": (8, 8, 8), "fp32": (4, 4, 4), "mixed": (4, 8, 4)}   # (rho/M, e/B, arithmetic) bytes
+# FP32/FP64 floating-point operations per face of one corrector sweep launch
+# (reconstruction + Riemann solve), counted by ncu on the 64^3 workload; see
+# profiles/.  None: not counted yet.
+FLOPS_PER_FACE = {}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return dict(hbm_gbs=d["hbm_gbs"], src="measured", sm_max_mhz=d.get("sm_max_mhz", 2032.0))
+    return dict(hbm_gbs=6400.0, src="fallback", sm_max_mhz=2032.0)
+
+
+def alu_peak_tflops(prec, sm_mhz):
+    """dense FP32 / FP64 ALU peak from the unit counts: 148 SMs x 128 FP32
+    lanes x 2 flops per FMA x clock; FP64 at the part's nominal 1.25 TFLOP/s
+    scaled by the clock."""
+    if prec == "fp64":
+        return 1.25 * sm_mhz / 2032.0
+    return 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class Clocks:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        rows = [l.split(",") for l in open(self.f.name).read().strip().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1])); mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload(n):
+    from paper_1804_03479_b300 import inputs as I
+    return I.abc(n, kmult=2, beta=0.5, seed=0)
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def time_variant(torch, mhd, st, prec, scheme, K, W, dist, stream, profile=True):
+    """Device-timed steps of one precision; returns ms/step, group ms and the solver."""
+    integ, recon, riemann = scheme
+    cast = torch.float32 if prec == "fp32" else torch.float64
+    U = torch.from_numpy(st.U).to(device="cuda", dtype=cast).contiguous()
+    B = torch.from_numpy(st.B).to(device="cuda", dtype=cast).contiguous()
+    s = mhd.Solver(st.U.shape[1:], st.dx, st.gamma, integ, recon, riemann, prec, 0.3, stream=stream.cuda_stream)
+    s.set_state(U, B)
+    del U, B
+    s.advance(W)
+    s.sync()
+    if profile:
+        s.profile_begin(K)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.advance(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    groups, rec = s.profile_end() if profile else ({}, 0)
+    s.sync()
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, groups, rec, s
+
+
+def roofline(prec, groups, steps, n, pk, sm_mhz):
+    """dominant kernel group and its achieved fraction of the roofline that bounds it"""
+    dom = max(groups, key=groups.get)
+    ms = groups[dom] / steps
+    szu, sze, szr = SIZES[prec]
+    # algorithmic bytes of one sweep launch per face: read the 8 primitives
+    # of the cell and its face B_n, write 7 flux components
+    sweep_bytes = 3 * n * (15 * szr + sze)
+    out = {"kernel": dom, "ms_per_step": ms, "share": groups[dom] / sum(groups.values())}
+    fpf = FLOPS_PER_FACE.get(prec)
+    if dom.endswith("sweeps") and fpf:
+        flops = 3 * n * fpf
+        ach = flops / (ms * 1e-3) / 1e12
+        peak = alu_peak_tflops(prec, sm_mhz)
+        out.update(bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
+                   peak_src=f"derived from unit counts at {sm_mhz:.0f} MHz", traffic=None,
+                   algorithmic=f"{fpf} flops per face x 3 axes x {n} faces")
+    else:
+        if dom.endswith("sweeps"):
+            b = sweep_bytes
+        elif dom == "full_update":
+            b = n * (2 * (4 * szu + 4 * sze) + 21 * szr + 3 * szr)
+        else:
+            b = n * 8 * (szu + szr)
+        ach = b / (ms * 1e-3) / 1e9
+        out.update(bound="hbm", achieved=ach, peak=pk["hbm_gbs"], unit="GB/s", frac=ach / pk["hbm_gbs"],
+                   peak_src=pk["src"], traffic=None, algorithmic_bytes_per_launch_group=b)
+    return out
+
+
+def cpu_baseline(scheme, target_s=12.0):
+    """the FP64 oracle as it stands, all host cores, on a 64^3 sample"""
+    from oracle import oracle as O
+    integ, recon, riemann = scheme
+    st = workload(64)
+    U, B = st.U.copy(), st.B.copy()
+    t0 = time.perf_counter()
+    dt = O.cfl_dt(U, B, st.dx, st.gamma, 0.3)
+    O.step(U, B, st.dx, st.gamma, dt, integ, recon, riemann)
+    t1 = time.perf_counter() - t0
+    m = max(1, min(40, int(target_s / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    for _ in range(m):
+        dt = O.cfl_dt(U, B, st.dx, st.gamma, 0.3)
+        O.step(U, B, st.dx, st.gamma, dt, integ, recon, riemann)
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": 64 ** 3 * m / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"64^3 ABC (k=4pi, beta=0.5, seed 0), {m} steps of {integ}+{recon}+{riemann} FP64 "
+                      f"incl. the CFL dt, OpenMP on all host threads"}
+
+
+def e2e(torch, mhd, st, prec, scheme, K, stream):
+    """same metric through the C ABI with host buffers: each step copies the
+    state in from pinned host memory, advances, copies it back out"""
+    integ, recon, riemann = scheme
+    cast = torch.float32 if prec == "fp32" else torch.float64
+    Uh = torch.from_numpy(st.U).to(dtype=cast).pin_memory()
+    Bh = torch.from_numpy(st.B).to(dtype=cast).pin_memory()
+    Uo = torch.empty_like(Uh).pin_memory()
+    Bo = torch.empty_like(Bh).pin_memory()
+    s = mhd.Solver(st.U.shape[1:], st.dx, st.gamma, integ, recon, riemann, prec, 0.3, stream=stream.cuda_stream)
+    s.set_state(Uh, Bh)
+    s.advance(1)
+    s.get_state(Uo, Bo)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        s.set_state(Uh, Bh)
+        s.advance(1)
+        s.get_state(Uo, Bo)
+    el = time.perf_counter() - t0
+    s.free()
+    nbytes = Uh.numel() * Uh.element_size() + Bh.numel() * Bh.element_size()
+    return {"value": st.U[0].size * K / el, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+            "steps": K, "path": "mhd_set_state(host) + mhd_advance(1) + mhd_get_state(host)"}
+
+
+def run_reference(args):
+    ws, rank, local = dist_info()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    scheme = (args.integrator, args.recon, args.riemann)
+    st = workload(64)
+    U, B = st.U.copy(), st.B.copy()
+    for _ in range(args.warmup):
+        dt = O.cfl_dt(U, B, st.dx, st.gamma, 0.3)
+        O.step(U, B, st.dx, st.gamma, dt, *scheme)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        dt = O.cfl_dt(U, B, st.dx, st.gamma, 0.3)
+        O.step(U, B, st.dx, st.gamma, dt, *scheme)
+    el = time.perf_counter() - t0
+    v = 64 ** 3 * args.steps / el
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = (f"each step one FP64 oracle step ({'+'.join(scheme)}, CFL dt included) on a 64^3 sample of the "
+              f"256^3 ABC workload family (k=4pi, beta=0.5, seed 0), OpenMP on all host threads")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "abc256_k4pi_beta0.5 (64^3 sample per step)", "scheme": "+".join(scheme)},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "mixed"])
+    ap.add_argument("--integrator", default="vl")
+    ap.add_argument("--recon", default="plm")
+    ap.add_argument("--riemann", default="roe")
+    ap.add_argument("--variants", default="fp64,mixed", help="other precisions measured beside the main line")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_1804_03479_b300 import build as Bld
+    Bld.build()
+    from paper_1804_03479_b300 import mhd
+
+    ws, rank, local = dist_info()
+    dist = None
+    if ws > 1:
+        import torch.distributed as td
+        torch.cuda.set_device(local)
+        td.init_process_group("nccl")
+        dist = td
+    else:
+        torch.cuda.set_device(0)
+    pk = peaks()
+    scheme = (args.integrator, args.recon, args.riemann)
+    st = workload(args.n)
+    n = args.n ** 3
+    stream = torch.cuda.Stream()
+    clk = Clocks(local)
+    clk.start()
+    ms, groups, rec, s = time_variant(torch, mhd, st, args.precision, scheme, args.steps, args.warmup, dist, stream)
+    clocks = clk.stop()
+    launches = s.launches_per_step() * args.steps
+    dev_bytes = s.device_bytes()
+    s.free()
+    sm_mhz = clocks["sm_mhz"] if clocks else pk["sm_max_mhz"]
+    value = ws * n * args.steps / (ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": value / PAPER_P100[args.precision] if args.precision in PAPER_P100 else None,
+        "dtype": {"fp32": "f32", "fp64": "f64", "mixed": "f32+f64"}[args.precision],
+        "data": "synthetic (seeded ABC field, k=4pi, beta=0.5, velocity noise 1e-3 c_s)",
+        "config": {"workload": f"abc{args.n}_k4pi_beta0.5", "grid": [args.n] * 3, "scheme": "+".join(scheme),
+                   "precision": args.precision, "cfl": 0.3, "dt": "CFL on device every step",
+                   "l2": "state larger than L2 (no flush)", "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
+                   "device_bytes": dev_bytes},
+        "roofline": roofline(args.precision, groups, rec, n, pk, sm_mhz) if rec else None,
+        "kernel_ms_per_step": {k: v / rec for k, v in groups.items()} if rec else None,
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0:
+        variants = {}
+        for prec in [p for p in args.variants.split(",") if p and p != args.precision]:
+            kv = max(3, min(args.steps, 10))
+            msv, gv, recv, sv = time_variant(torch, mhd, st, prec, scheme, kv, 2, None, stream)
+            sv.free()
+            vv = n * kv / (msv * 1e-3)
+            variants[prec] = {"value": vv, "unit": UNIT, "ms_per_step": msv / kv, "steps": kv,
+                              "vs_p100_paper": vv / PAPER_P100[prec] if prec in PAPER_P100 else None,
+                              "roofline": roofline(prec, gv, recv, n, pk, sm_mhz) if recv else None}
+        line["variants"] = variants
+        if not args.no_e2e:
+            line["e2e"] = e2e(torch, mhd, st, args.precision, scheme, max(3, min(args.steps, 8)), stream)
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(scheme)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

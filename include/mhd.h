@@ -1,0 +1,147 @@
+/*
+ * mhd.h -- C ABI of the B300 (sm_103a) ideal-MHD patch advance.
+ *
+ * The library advances the ideal-MHD equations (Eqs. 1-9 of "Magnetohydro-
+ * dynamics with GAMER", Zhang, Schive & Chiueh 2018) on a periodic uniform
+ * grid with dx = dy = dz (Sec. 3.1), using the unsplit VL or CTU scheme
+ * with constrained transport (Sec. 3.2, Eqs. 10-16).  Every step runs in
+ * hand-written CUDA kernels on the stream given at mhd_init.
+ *
+ * State layout (what mhd_set_state / mhd_get_state exchange), C order:
+ *   U: 5 arrays of n = nx*ny*nz cell averages (Eq. 11), in the order
+ *      rho, Mx, My, Mz, e; cell c = (k*ny + j)*nx + i, x fastest.
+ *   B: 3 arrays of n face averages (Eq. 14): B[0][c] is Bx on the face
+ *      x_{i-1/2} of cell c, B[1][c] is By on y_{j-1/2}, B[2][c] is Bz on
+ *      z_{k-1/2}.  Periodic: the face x_{nx-1/2} is B[0] of cell i = 0.
+ *   Element type: double for MHD_FP64 and MHD_MIXED, float for MHD_FP32.
+ *
+ * Errors: no call throws or aborts.  Every call returns an mhd_status;
+ * mhd_last_error() gives a one-line description.  Kernels run
+ * asynchronously; a device-side anomaly (rho <= 0 or P <= 0 at the start
+ * of a step) is recorded on the device and reported as MHD_ENEGATIVE by
+ * the next call that synchronises (mhd_cfl_dt, mhd_divB, mhd_sums,
+ * mhd_get_state, mhd_sync).  An error stays until mhd_clear_error.
+ *
+ * Ownership: the library allocates the state and all scratch on the
+ * device in mhd_init and frees them in mhd_free.  Pointers passed in are
+ * only read or written during the call (copies are stream-ordered and
+ * complete before the call returns when they touch host memory).
+ * Thread safety: one context must not be used from two threads at once.
+ */
+#ifndef MHD_H
+#define MHD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MHD_OK = 0,
+    MHD_EINVAL = 1,        /* bad argument (size, enum, null pointer, dt)      */
+    MHD_ENOMEM = 2,        /* device allocation failed                          */
+    MHD_ECUDA = 3,         /* a CUDA runtime call failed                        */
+    MHD_ENEGATIVE = 4,     /* rho <= 0 or P <= 0 (or not finite) in some cell   */
+    MHD_ETIMEOUT = 5,      /* a bounded device wait gave up                     */
+    MHD_EUNSUPPORTED = 6   /* combination not built                             */
+} mhd_status;
+
+enum { MHD_VL = 0, MHD_CTU = 1 };                     /* integrator, Sec. 3.2 */
+enum { MHD_PLM = 0, MHD_PPM = 1, MHD_PLM_PRIM = 2 };  /* reconstruction: PLM / PPM in
+                                                         characteristic variables;
+                                                         PLM_PRIM = primitive-variable
+                                                         PLM (VL only)            */
+enum { MHD_ROE = 0, MHD_HLLD = 1, MHD_HLLE = 2 };     /* Riemann solver, Sec. 3.2 */
+enum { MHD_FP64 = 0, MHD_FP32 = 1, MHD_MIXED = 2 };   /* MIXED: FP32 arithmetic and
+                                                         rho, M storage; FP64 e, face B,
+                                                         pressure recovery, CT and
+                                                         energy accumulation       */
+
+typedef struct {
+    int nx, ny, nz;   /* cells per axis, each >= 1                        */
+    double dx;        /* cell size, dx = dy = dz (Sec. 3.1)               */
+} mhd_grid;
+
+typedef struct {
+    int integrator;   /* MHD_VL or MHD_CTU                                */
+    int recon;        /* MHD_PLM, MHD_PPM, MHD_PLM_PRIM                   */
+    int riemann;      /* MHD_ROE, MHD_HLLD, MHD_HLLE                      */
+    int precision;    /* MHD_FP64, MHD_FP32, MHD_MIXED                    */
+    double cfl;       /* Courant number for mhd_cfl_dt / mhd_advance      */
+} mhd_scheme;
+
+typedef struct mhd_ctx mhd_ctx;
+
+/* Create a context for one periodic box: grid, adiabatic index gamma
+ * (Eq. 5) and scheme.  stream is a cudaStream_t (NULL = a stream the
+ * library creates).  Allocates the state and scratch on the current device.
+ * On failure *out is NULL and the status says why. */
+mhd_status mhd_init(const mhd_grid* grid, double gamma, const mhd_scheme* scheme, void* stream,
+                    mhd_ctx** out);
+
+/* Copy the state in (U: 5*n, B: 3*n elements of the layout above).
+ * on_device != 0: U, B are device pointers; else host pointers. */
+mhd_status mhd_set_state(mhd_ctx* ctx, const void* U, const void* B, int on_device);
+
+/* Copy the state out (same layout); synchronises the stream. */
+mhd_status mhd_get_state(mhd_ctx* ctx, void* U, void* B, int on_device);
+
+/* CFL time step (Sec. 3.2): cfl * dx / max over cells and axes of
+ * |v_d| + c_f,d, from the current state.  Synchronises. */
+mhd_status mhd_cfl_dt(mhd_ctx* ctx, double* dt);
+
+/* One step of the scheme (Sec. 3.2, CTU steps 1-8 or VL steps 1-7) with
+ * the given dt > 0.  Asynchronous. */
+mhd_status mhd_step(mhd_ctx* ctx, double dt);
+
+/* nsteps steps, each with its CFL dt computed and used on the device (no
+ * host round trip).  Asynchronous.  With use_graph != 0 one step is
+ * captured once into a CUDA graph and replayed. */
+mhd_status mhd_advance(mhd_ctx* ctx, int nsteps, int use_graph);
+
+/* dt used by the most recent step.  Synchronises. */
+mhd_status mhd_last_dt(mhd_ctx* ctx, double* dt);
+
+/* Discrete divergence (Eq. 16): *maxabs = max over cells of
+ * |sum_d B_d(c + e_d) - B_d(c)| (= max |div B| dx), *brms = rms of the
+ * cell-centre field.  Synchronises. */
+mhd_status mhd_divB(mhd_ctx* ctx, double* maxabs, double* brms);
+
+/* Sums over the box (FP64, fixed-order reduction): rho, Mx, My, Mz, e over
+ * cells, Bx, By, Bz over faces (8 values).  Synchronises. */
+mhd_status mhd_sums(mhd_ctx* ctx, double* sums8);
+
+/* Wait for all work queued on the context's stream; reports recorded
+ * device-side anomalies. */
+mhd_status mhd_sync(mhd_ctx* ctx);
+
+/* Kernel-group timing.  mhd_profile_begin arms CUDA events (on the
+ * context's stream) at the boundaries of the 7 kernel groups of each of the
+ * next max_steps directly launched steps (not graph replays): 0 primitives
+ * + CFL dt, 1 predictor sweeps (3 launches), 2 edge E, 3 half update,
+ * 4 corrector sweeps / CTU corrections (3 launches), 5 edge E, 6 full
+ * update.  mhd_profile_end synchronises, stops recording and writes the
+ * summed milliseconds of each group (ms[ngroups], ngroups <= 7) and the
+ * number of steps recorded. */
+mhd_status mhd_profile_begin(mhd_ctx* ctx, int max_steps);
+mhd_status mhd_profile_end(mhd_ctx* ctx, double* ms, int ngroups, int* steps);
+
+/* Cell index of the first anomaly found (or -1) and reset of the error. */
+long long mhd_bad_cell(mhd_ctx* ctx);
+void mhd_clear_error(mhd_ctx* ctx);
+
+/* One-line description of the last error (never NULL). */
+const char* mhd_last_error(mhd_ctx* ctx);
+
+/* Device memory the context holds, in bytes. */
+long long mhd_device_bytes(mhd_ctx* ctx);
+
+/* Number of kernel launches one step issues for this context's scheme. */
+int mhd_launches_per_step(mhd_ctx* ctx);
+
+/* Free the context and its device memory (NULL is allowed). */
+void mhd_free(mhd_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MHD_H */

@@ -1,0 +1,182 @@
+// mhd_engine.cuh -- context and the launch sequence of one step.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include "mhd.h"
+#include "mhd_kernels.cuh"
+
+struct mhd_ctx;
+typedef void (*mhd_step_fn)(mhd_ctx*, bool device_dt);
+
+struct mhd_ctx {
+    mhd_grid grid;
+    mhd_scheme sch;
+    double gamma;
+    cudaStream_t stream;
+    bool own_stream;
+    mhd::Grid g;
+    size_t szu, sze, szr;          // element sizes: rho/M storage, e/B storage, arithmetic
+    void* rho;
+    void* m[3];
+    void* e;
+    void* b[3];
+    void* W;                        // 8 primitives at t^n
+    void* Wh;                       // 8 primitives at t^{n+1/2}
+    void* F1;                       // 3 x 7 face fluxes
+    void* F2;                       // 3 x 7 face fluxes (CTU corrector)
+    void* E;                        // 3 edge fields
+    void* Bh[3];                    // half-step face field
+    void* WM;                       // 3 x 7 traced states (CTU)
+    void* WP;
+    void* stage;                    // staging for the mixed layout
+    double* dt;
+    unsigned long long* smax;
+    unsigned long long* bad;
+    double* part;
+    double* diag;
+    int nblk;                       // blocks of the per-cell kernels
+    long long bytes;
+    mhd_step_fn step;
+    int launches;
+    cudaGraphExec_t gexec;
+    bool have_graph;
+    // kernel-group timing (CUDA events on the context stream)
+    cudaEvent_t* prof_ev;           // [prof_cap][MHD_NGROUPS + 1]
+    int prof_cap, prof_steps;
+    bool prof_on;
+    mhd_status sticky;
+    char err[256];
+};
+
+#define MHD_NGROUPS 7   // prim+dt, predictor sweeps, emf, half, corrector sweeps, emf, full
+
+// record the boundary event `b` of the current step when timing is on
+inline void prof_mark(mhd_ctx* c, int b)
+{
+    if (c->prof_on && c->prof_steps < c->prof_cap)
+        cudaEventRecord(c->prof_ev[c->prof_steps * (MHD_NGROUPS + 1) + b], c->stream);
+}
+
+namespace mhd {
+
+template <class TU, class TE>
+inline StateP<TU, TE> state_of(mhd_ctx* c)
+{
+    StateP<TU, TE> s;
+    s.rho = (TU*)c->rho;
+    for (int d = 0; d < 3; d++) s.m[d] = (TU*)c->m[d];
+    s.e = (TE*)c->e;
+    for (int d = 0; d < 3; d++) s.b[d] = (TE*)c->b[d];
+    return s;
+}
+
+inline int sweep_blocks(const Grid& g, int d)
+{
+    int ex = TX, ey = d == 2 ? 1 : TL, ez = d == 2 ? TL : 1;
+    return ((g.nx + ex - 1) / ex) * ((g.ny + ey - 1) / ey) * ((g.nz + ez - 1) / ez);
+}
+
+template <class R, class TU, class TE, int INTEG, int RECON, int SOLVER>
+void run_step(mhd_ctx* c, bool device_dt)
+{
+    const Grid g = c->g;
+    const long long n = g.n;
+    cudaStream_t st = c->stream;
+    StateP<TU, TE> s = state_of<TU, TE>(c);
+    R* W = (R*)c->W;
+    R* Wh = (R*)c->Wh;
+    R* F1 = (R*)c->F1;
+    R* F2 = (R*)c->F2;
+    R* E = (R*)c->E;
+    TE* Bh[3] = {(TE*)c->Bh[0], (TE*)c->Bh[1], (TE*)c->Bh[2]};
+    const int nb = c->nblk;
+    const double gam = c->gamma;
+    const size_t smem = sweep_smem_bytes<R>(RECON);
+
+    prof_mark(c, 0);
+    if (device_dt) cudaMemsetAsync(c->smax, 0, sizeof(unsigned long long), st);
+    k_prim<R, TU, TE><<<nb, 256, 0, st>>>(g, s, W, gam, device_dt ? c->smax : nullptr, c->bad);
+    if (device_dt) k_finalize_dt<<<1, 1, 0, st>>>(c->smax, c->sch.cfl, g.dx, c->dt);
+    prof_mark(c, 1);
+
+    if (INTEG == VL) {
+        // VL steps 1-3: first-order fluxes with the face B_n, edge E, half update
+        for (int d = 0; d < 3; d++)
+            k_sweep<R, RECON, SOLVER, 0, TE><<<sweep_blocks(g, d), SWEEP_THREADS, 0, st>>>(
+                g, d, W, s.b[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dt, gam);
+        prof_mark(c, 2);
+        k_emf<R><<<nb, 256, 0, st>>>(g, F1, W, E);
+        prof_mark(c, 3);
+        k_half<R, TU, TE><<<nb, 256, 0, st>>>(g, s, F1, E, c->dt, gam, Bh[0], Bh[1], Bh[2], Wh);
+        prof_mark(c, 4);
+        // VL steps 4-7: reconstruct at the half step, Riemann, edge E, full update
+        for (int d = 0; d < 3; d++)
+            k_sweep<R, RECON, SOLVER, 1, TE><<<sweep_blocks(g, d), SWEEP_THREADS, smem, st>>>(
+                g, d, Wh, Bh[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dt, gam);
+        prof_mark(c, 5);
+        k_emf<R><<<nb, 256, 0, st>>>(g, F1, Wh, E);
+        prof_mark(c, 6);
+        k_full<R, TU, TE><<<nb, 256, 0, st>>>(g, s, F1, E, c->dt);
+        prof_mark(c, 7);
+    } else {
+        R* WM = (R*)c->WM;
+        R* WP = (R*)c->WP;
+        // CTU steps 1-2: traced states (+ source terms) and their fluxes
+        for (int d = 0; d < 3; d++)
+            k_sweep<R, RECON, SOLVER, 2, TE><<<sweep_blocks(g, d), SWEEP_THREADS, smem, st>>>(
+                g, d, W, s.b[d], F1 + (long long)d * 7 * n, WM + (long long)d * 7 * n, WP + (long long)d * 7 * n,
+                c->dt, gam);
+        prof_mark(c, 2);
+        // steps 3-4: edge E at t^n, dt/2 update of face B and cell state
+        k_emf<R><<<nb, 256, 0, st>>>(g, F1, W, E);
+        prof_mark(c, 3);
+        k_half<R, TU, TE><<<nb, 256, 0, st>>>(g, s, F1, E, c->dt, gam, Bh[0], Bh[1], Bh[2], Wh);
+        prof_mark(c, 4);
+        // steps 5-6: transverse correction and corrector fluxes
+        for (int d = 0; d < 3; d++)
+            k_ctu_correct<R, SOLVER, TE><<<nb, 256, 0, st>>>(g, d, WM + (long long)d * 7 * n,
+                                                              WP + (long long)d * 7 * n, W, F1, Bh[d],
+                                                              F2 + (long long)d * 7 * n, c->dt, gam);
+        prof_mark(c, 5);
+        // steps 7-8
+        k_emf<R><<<nb, 256, 0, st>>>(g, F2, Wh, E);
+        prof_mark(c, 6);
+        k_full<R, TU, TE><<<nb, 256, 0, st>>>(g, s, F2, E, c->dt);
+        prof_mark(c, 7);
+    }
+    if (c->prof_on && c->prof_steps < c->prof_cap) c->prof_steps++;
+}
+
+template <class R, class TE, int RECON, int SOLVER, int MODE>
+inline cudaError_t allow_smem()
+{
+    size_t b = sweep_smem_bytes<R>(RECON);
+    if (MODE == 0) return cudaSuccess;
+    return cudaFuncSetAttribute(k_sweep<R, RECON, SOLVER, MODE, TE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
+}
+
+// pick the step function of one precision; returns nullptr if not built
+template <class R, class TU, class TE>
+mhd_step_fn pick_step(int integ, int recon, int solver, cudaError_t* attr)
+{
+#define MHD_CASE(I, RC, S)                                                              \
+    if (integ == I && recon == RC && solver == S) {                                     \
+        *attr = allow_smem<R, TE, RC, S, (I == VL ? 1 : 2)>();                          \
+        return &run_step<R, TU, TE, I, RC, S>;                                          \
+    }
+    MHD_CASE(VL, PLM, ROE) MHD_CASE(VL, PLM, HLLD) MHD_CASE(VL, PLM, HLLE)
+    MHD_CASE(VL, PPM, ROE) MHD_CASE(VL, PPM, HLLD) MHD_CASE(VL, PPM, HLLE)
+    MHD_CASE(VL, PLM_PRIM, ROE) MHD_CASE(VL, PLM_PRIM, HLLD) MHD_CASE(VL, PLM_PRIM, HLLE)
+    MHD_CASE(CTU, PLM, ROE) MHD_CASE(CTU, PLM, HLLD) MHD_CASE(CTU, PLM, HLLE)
+    MHD_CASE(CTU, PPM, ROE) MHD_CASE(CTU, PPM, HLLD) MHD_CASE(CTU, PPM, HLLE)
+#undef MHD_CASE
+    *attr = cudaSuccess;
+    return nullptr;
+}
+
+}  // namespace mhd
+
+// per-precision entry points (one compilation unit each)
+mhd_step_fn mhd_pick_fp64(int integ, int recon, int solver, cudaError_t* attr);
+mhd_step_fn mhd_pick_fp32(int integ, int recon, int solver, cudaError_t* attr);
+mhd_step_fn mhd_pick_mixed(int integ, int recon, int solver, cudaError_t* attr);
