@@ -32,16 +32,23 @@ def rel_l1(a, b):
     return np.abs(a - b).sum() / (den if den > 0 else 1.0)
 
 
-def assert_state_close(Ug, Bg, U, B, tol, what=""):
+def assert_state_close(Ug, Bg, U, B, tol, what="", mfloor=0.0):
+    """relative L1 per field; mfloor > 0 puts a floor of mfloor * sum(rho)
+    under the momentum denominators (for fields that are themselves a tiny
+    perturbation of an O(1) background, e.g. a 1e-6 linear wave)"""
     for f in range(5):
-        r = rel_l1(Ug[f], U[f])
+        if f in (1, 2, 3) and mfloor > 0:
+            den = max(np.abs(U[f]).sum(), mfloor * np.abs(U[0]).sum())
+            r = np.abs(Ug[f] - U[f]).sum() / den
+        else:
+            r = rel_l1(Ug[f], U[f])
         assert r <= tol, f"{what} U[{f}] rel L1 {r:.3e}"
     for d in range(3):
         r = rel_l1(Bg[d], B[d])
         assert r <= tol, f"{what} B[{d}] rel L1 {r:.3e}"
 
 
-def run_parity(M, st, integ, recon, solver, nsteps, tol=TOL64):
+def run_parity(M, st, integ, recon, solver, nsteps, tol=TOL64, mfloor=0.0):
     U, B = st.U.copy(), st.B.copy()
     s = M.Solver(U.shape[1:], st.dx, st.gamma, integ, recon, solver, "fp64", 0.3)
     try:
@@ -53,7 +60,7 @@ def run_parity(M, st, integ, recon, solver, nsteps, tol=TOL64):
             s.step(dt)
             orc.step(U, B, st.dx, st.gamma, dt, integ, recon, solver)
             Ug, Bg = s.get_state()
-            assert_state_close(Ug, Bg, U, B, tol, f"{integ}/{recon}/{solver} step {it + 1}")
+            assert_state_close(Ug, Bg, U, B, tol, f"{integ}/{recon}/{solver} step {it + 1}", mfloor)
     finally:
         s.free()
 
@@ -75,7 +82,10 @@ def test_fp64_parity_ragged(M, integ, recon, solver):
 
 @pytest.mark.parametrize("shape", [(1, 16, 16), (16, 1, 8), (9, 7, 1), (33, 9, 9)])
 def test_fp64_parity_thin_boxes(M, shape):
-    st = I.abc(None, kmult=1, beta=0.5, seed=6, noise=5e-2, shape=shape)
+    # dx = 1/16 and k = 2 pi whatever the shape (abc() takes dx = L / ny and
+    # k = 2 pi kmult / L for a given shape)
+    L = shape[1] / 16.0
+    st = I.abc(None, kmult=L, beta=0.5, seed=6, noise=5e-2, shape=shape, L=L)
     run_parity(M, st, "vl", "ppm", "roe", 2)
     run_parity(M, st, "ctu", "plm", "hlld", 2)
 
@@ -89,10 +99,13 @@ def test_fp64_parity_abc64_config(M, integ, recon, solver):
 
 
 def test_fp64_parity_linear_wave(M):
+    """amplitude 1e-6 on rho = 1, P = 3/5, |B| ~ 1.6: the momentum is itself
+    a 1e-6 perturbation, so its denominator is floored at 1e-2 sum(rho)
+    (rounding of the O(1) flux terms is ~1e-16 per cell)"""
     st = I.linear_wave(32, "fast")
-    run_parity(M, st, "ctu", "plm", "roe", 3)
+    run_parity(M, st, "ctu", "plm", "roe", 3, mfloor=1e-2)
     st = I.linear_wave(32, "slow")
-    run_parity(M, st, "vl", "ppm", "hlld", 3)
+    run_parity(M, st, "vl", "ppm", "hlld", 3, mfloor=1e-2)
 
 
 def neighbourhood(U, B, k, j, i, r):
@@ -107,7 +120,7 @@ def neighbourhood(U, B, k, j, i, r):
 @pytest.mark.parametrize("integ,recon,solver,prec,tol", [
     ("vl", "plm", "roe", "fp64", TOL64),
     ("ctu", "ppm", "hlld", "fp64", TOL64),
-    ("vl", "plm", "roe", "fp32", 2e-5),
+    ("vl", "plm", "roe", "fp32", 1e-6),
 ])
 def test_full_size_sampled(M, integ, recon, solver, prec, tol):
     """256^3 (the benchmark workload, same launch configuration): one GPU step
@@ -130,8 +143,10 @@ def test_full_size_sampled(M, integ, recon, solver, prec, tol):
     assert abs(dt - dto) <= (1e-14 if prec == "fp64" else 1e-6) * dto
     rng = np.random.default_rng(11)
     r = 10
-    scaleU = [np.abs(U0d[f]).mean() + 1e-30 for f in range(5)]
-    scaleB = [np.abs(B0d[d]).mean() + 1e-30 for d in range(3)]
+    # error scale: every flux term is bounded by the energy density, so each
+    # cell quantity is compared against mean |e| (B against mean |B|)
+    scaleU = [np.abs(U0d[4]).mean()] * 5
+    scaleB = [np.abs(B0d).mean()] * 3
     for _ in range(24):
         k, j, i = rng.integers(0, 256, 3)
         u, b = neighbourhood(U0d, B0d, k, j, i, r)
@@ -187,10 +202,13 @@ def test_device_state_roundtrip_and_torch(M):
         s.free()
 
 
-@pytest.mark.parametrize("prec,tol", [("fp32", 3e-5), ("mixed", 3e-5)])
-def test_reduced_precision_error_statement(M, prec, tol):
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+def test_reduced_precision_error_statement(M, prec):
     """FP32 and mixed against the FP64 oracle after 10 steps of the 32^3 ABC
-    problem (same dt each step); relative L1 per field below `tol`."""
+    problem (same dt each step).  Stated bound on the relative L1 per field:
+    1e-6 for rho, e and the face B; 3e-4 for the momentum components, whose
+    values are the 1e-3 c_s velocity noise (a small denominator)."""
+    tol = np.array([1e-6, 3e-4, 3e-4, 3e-4, 1e-6, 1e-6, 1e-6, 1e-6])
     st = I.abc(32, kmult=1, beta=1.0, seed=0)
     U, B = st.U.copy(), st.B.copy()
     s = M.Solver(U.shape[1:], st.dx, st.gamma, "vl", "plm", "roe", prec, 0.3)
@@ -205,7 +223,7 @@ def test_reduced_precision_error_statement(M, prec, tol):
         errs = [rel_l1(Ug[f].astype(np.float64), U[f]) for f in range(5)] + \
                [rel_l1(Bg[d].astype(np.float64), B[d]) for d in range(3)]
         print(prec, ["%.2e" % e for e in errs])
-        assert max(errs) <= tol
+        assert np.all(np.array(errs) <= tol), errs
         m, brms = s.divB()
         assert m / brms <= (1e-5 if prec == "fp32" else 1e-13)
     finally:
