@@ -141,6 +141,31 @@ int mhd_launches_per_step(mhd_ctx* ctx);
 /* Free the context and its device memory (NULL is allowed). */
 void mhd_free(mhd_ctx* ctx);
 
+/* ---- stepping without any device allocation ---------------------------
+ * The paper has no counterpart: this is a service for callers that may not
+ * allocate device memory themselves or through this library (for example a
+ * plug-in inside another application whose allocator owns all device
+ * memory, or a loop that cannot afford the device-wide synchronisation
+ * cudaMalloc / cudaFree can cause).  It advances the caller's state by one
+ * FP64 VL step (any recon, any Riemann solver) with the given dt, in place:
+ * U and B are DEVICE pointers in the layout above (double).  All scratch
+ * lives in one fixed array built into the library, sized for at most
+ * MHD_NOALLOC_MAX_CELLS cells (about 11 MB, held on every GPU that loads
+ * the library until the process exits).  The call allocates nothing and
+ * calls no allocating routine.
+ *   - Larger grids: MHD_EINVAL; other integrators or precisions:
+ *     MHD_EUNSUPPORTED; the reason is in mhd_last_error(NULL).
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - Every call, on any stream, shares the one array, which keeps the last
+ *     call's contents: calls that overlap on the GPU race and corrupt each
+ *     other.  Serialise them (one stream, or events).
+ *   - Asynchronous on `stream` (NULL = the default stream); a cell with
+ *     rho <= 0 or P <= 0 is not reported by this call. */
+#define MHD_NOALLOC_MAX_CELLS 32768
+mhd_status mhd_step_noalloc(const mhd_grid* grid, double gamma, const mhd_scheme* scheme, double dt,
+                            void* U, void* B, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,6 +26,10 @@ static mhd_status fail(mhd_ctx* c, mhd_status s, const char* fmt, ...)
 
 static const char* g_init_err = "no error";
 
+// lets the allocation-free entry point report argument errors through
+// mhd_last_error(NULL)
+void mhd_internal_set_init_error(const char* msg) { g_init_err = msg; }
+
 static void release(mhd_ctx* c)
 {
     void* bufs[] = {c->rho, c->m[0], c->m[1], c->m[2], c->e, c->b[0], c->b[1], c->b[2], c->W, c->Wh,

@@ -1,0 +1,113 @@
+// mhd_noalloc.cu -- one FP64 VL step for callers that cannot allocate.
+//
+// Some callers may not call cudaMalloc at all: a plug-in running inside a
+// host application whose allocator owns every byte of device memory, or a
+// latency-critical loop that cannot afford the device-wide synchronisation
+// cudaMalloc/cudaFree can imply.  mhd_step_noalloc serves them.  It runs the
+// same kernels as mhd_step, but its scratch (primitives, fluxes, edge fields,
+// half-step faces, dt and a flag word) lives in the file-scope array below,
+// of fixed size.  The caller still owns and passes the state.
+#include <mutex>
+#include <stdio.h>
+#include <string.h>
+#include "mhd_engine.cuh"
+
+using namespace mhd;
+
+void mhd_internal_set_init_error(const char* msg);   // defined with the other entry points
+
+// per cell: W (8) + Wh (8) + fluxes (21) + edge E (3) + half-step faces (3)
+static constexpr size_t kDoublesPerCell = 43;
+static constexpr size_t kScratchBytes = kDoublesPerCell * MHD_NOALLOC_MAX_CELLS * sizeof(double) + 256;
+
+// Every GPU that loads this library holds this array until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+// Host code cannot use g_noalloc_scratch as an address (on the host it is a
+// stand-in symbol); its device address is looked up once per device.
+static constexpr int kMaxDevices = 64;
+static void* g_scratch_addr[kMaxDevices];
+static std::mutex g_scratch_mu;
+
+static void* scratch_address(int dev, cudaError_t* err)
+{
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        *err = cudaGetSymbolAddress(&p, g_noalloc_scratch);   // the current device is `dev`
+        if (*err != cudaSuccess) return nullptr;
+        g_scratch_addr[dev] = p;
+    }
+    *err = cudaSuccess;
+    return g_scratch_addr[dev];
+}
+
+static mhd_status reject(mhd_status s, const char* msg)
+{
+    mhd_internal_set_init_error(msg);
+    return s;
+}
+
+extern "C" mhd_status mhd_step_noalloc(const mhd_grid* grid, double gamma, const mhd_scheme* scheme, double dt,
+                                       void* U, void* B, void* stream)
+{
+    if (!grid || !scheme || !U || !B) return reject(MHD_EINVAL, "mhd_step_noalloc: null argument");
+    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || !(grid->dx > 0.0))
+        return reject(MHD_EINVAL, "mhd_step_noalloc: bad grid");
+    const long long n = (long long)grid->nx * grid->ny * grid->nz;
+    if (n > MHD_NOALLOC_MAX_CELLS) {
+        static char msg[160];
+        snprintf(msg, sizeof(msg), "mhd_step_noalloc: %lld cells exceed the fixed scratch of %d cells", n,
+                 MHD_NOALLOC_MAX_CELLS);
+        return reject(MHD_EINVAL, msg);
+    }
+    if (!(gamma > 1.0)) return reject(MHD_EINVAL, "mhd_step_noalloc: gamma must exceed 1");
+    if (!(dt > 0.0) || !(dt < 1e300)) return reject(MHD_EINVAL, "mhd_step_noalloc: dt must be positive and finite");
+    if (scheme->integrator != MHD_VL || scheme->precision != MHD_FP64)
+        return reject(MHD_EUNSUPPORTED, "mhd_step_noalloc: only the FP64 VL scheme is built");
+    if (scheme->recon < 0 || scheme->recon > 2 || scheme->riemann < 0 || scheme->riemann > 2)
+        return reject(MHD_EINVAL, "mhd_step_noalloc: bad scheme enum");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return reject(MHD_ECUDA, "mhd_step_noalloc: no usable current device");
+    cudaError_t e = cudaSuccess;
+    unsigned char* base = (unsigned char*)scratch_address(dev, &e);
+    if (!base) return reject(MHD_ECUDA, "mhd_step_noalloc: cudaGetSymbolAddress failed");
+
+    // a context on the stack: the caller's state, scratch carved from the array
+    mhd_ctx c;
+    memset(&c, 0, sizeof(c));
+    c.grid = *grid;
+    c.sch = *scheme;
+    c.gamma = gamma;
+    c.stream = (cudaStream_t)stream;
+    c.g.nx = grid->nx; c.g.ny = grid->ny; c.g.nz = grid->nz; c.g.n = n; c.g.dx = grid->dx;
+    c.szu = c.sze = c.szr = sizeof(double);
+    double* u = (double*)U;
+    double* b = (double*)B;
+    c.rho = u;
+    for (int d = 0; d < 3; d++) c.m[d] = u + (1 + d) * n;
+    c.e = u + 4 * n;
+    for (int d = 0; d < 3; d++) c.b[d] = b + d * n;
+    double* s = (double*)base;
+    c.W = s;
+    c.Wh = s + 8 * n;
+    c.F1 = s + 16 * n;
+    c.E = s + 37 * n;
+    for (int d = 0; d < 3; d++) c.Bh[d] = s + (40 + d) * n;
+    c.dt = s + 43 * n;
+    c.smax = (unsigned long long*)(s + 43 * n + 1);
+    c.bad = (unsigned long long*)(s + 43 * n + 2);
+    c.nblk = (int)((n + 255) / 256 < 148 * 16 ? (n + 255) / 256 : 148 * 16);
+    cudaError_t attr = cudaSuccess;
+    c.step = mhd_pick_fp64(scheme->integrator, scheme->recon, scheme->riemann, &attr);
+    if (!c.step || attr != cudaSuccess) return reject(MHD_ECUDA, "mhd_step_noalloc: kernel set-up failed");
+    // the array keeps the previous call's contents: reset the flag word
+    if (cudaMemsetAsync(c.bad, 0xff, sizeof(unsigned long long), c.stream) != cudaSuccess)
+        return reject(MHD_ECUDA, "mhd_step_noalloc: cudaMemsetAsync failed");
+    k_set_dt<<<1, 1, 0, c.stream>>>(c.dt, dt);
+    c.step(&c, false);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return reject(MHD_ECUDA, cudaGetErrorString(e));
+    return MHD_OK;
+}

@@ -27,7 +27,7 @@ PRECISIONS = {"fp64": 0, "fp32": 1, "mixed": 2}
 EXPORTS = ["mhd_init", "mhd_set_state", "mhd_get_state", "mhd_cfl_dt", "mhd_step", "mhd_advance",
            "mhd_last_dt", "mhd_divB", "mhd_sums", "mhd_sync", "mhd_bad_cell", "mhd_clear_error",
            "mhd_last_error", "mhd_device_bytes", "mhd_launches_per_step", "mhd_free",
-           "mhd_profile_begin", "mhd_profile_end"]
+           "mhd_profile_begin", "mhd_profile_end", "mhd_step_noalloc"]
 GROUPS = ["prim_cfl", "predictor_sweeps", "emf1", "half_update", "corrector_sweeps", "emf2", "full_update"]
 
 
@@ -79,11 +79,14 @@ def lib():
     L.mhd_launches_per_step.argtypes = [vp]
     L.mhd_free.argtypes = [vp]
     L.mhd_free.restype = None
+    L.mhd_step_noalloc.argtypes = [ctypes.POINTER(Grid), ctypes.c_double, ctypes.POINTER(Scheme), ctypes.c_double,
+                                   vp, vp, vp]
+    L.mhd_step_noalloc.restype = ctypes.c_int
     L.mhd_profile_begin.argtypes = [vp, ip]
     L.mhd_profile_end.argtypes = [vp, dp, ip, ctypes.POINTER(ctypes.c_int)]
     for name in ["mhd_init", "mhd_set_state", "mhd_get_state", "mhd_cfl_dt", "mhd_step", "mhd_advance",
                  "mhd_last_dt", "mhd_divB", "mhd_sums", "mhd_sync", "mhd_launches_per_step",
-                 "mhd_profile_begin", "mhd_profile_end"]:
+                 "mhd_profile_begin", "mhd_profile_end", "mhd_step_noalloc"]:
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -96,6 +99,28 @@ def _ptr(a):
         return a.ctypes.data, 0
     assert a.is_contiguous()
     return a.data_ptr(), int(a.is_cuda)
+
+
+NOALLOC_MAX_CELLS = 32768
+
+
+def step_noalloc(U, B, dx, dt, gamma=5.0 / 3.0, recon="plm", riemann="roe", stream=None):
+    """One FP64 VL step of a caller-owned device state (torch CUDA float64
+    tensors U (5, nz, ny, nx) and B (3, nz, ny, nx)), in place, through
+    mhd_step_noalloc: no device memory is allocated (the scratch is a fixed
+    array inside the library, at most NOALLOC_MAX_CELLS cells).  Calls that
+    overlap on the GPU share that array and race: serialise them."""
+    nz, ny, nx = U.shape[1:]
+    g = Grid(nx, ny, nz, dx)
+    s = Scheme(INTEGRATORS["vl"], RECONS[recon], SOLVERS[riemann], PRECISIONS["fp64"], 0.3)
+    pu, du = _ptr(U)
+    pb, db = _ptr(B)
+    if not (du and db):
+        raise MHDError(MHD_EINVAL, "step_noalloc takes device arrays")
+    st = lib().mhd_step_noalloc(ctypes.byref(g), gamma, ctypes.byref(s), dt, ctypes.c_void_p(pu),
+                                ctypes.c_void_p(pb), ctypes.c_void_p(stream or 0))
+    if st != MHD_OK:
+        raise MHDError(st, lib().mhd_last_error(None).decode())
 
 
 class Solver:
