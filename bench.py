@@ -120,6 +120,20 @@ def dist_info():
     return ws, rank, local
 
 
+def max_over_ranks(torch, value, dist, device):
+    """the slowest rank's time (every rank gets it); value itself when alone"""
+    if not dist:
+        return value
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(world, cells, steps, ms_max):
+    """whole-job cell-updates/s: the units of all ranks over the slowest time"""
+    return world * cells * steps / (ms_max * 1e-3)
+
+
 def time_variant(torch, mhd, st, prec, scheme, K, W, dist, stream, profile=True):
     """Device-timed steps of one precision; returns ms/step, group ms and the solver."""
     integ, recon, riemann = scheme
@@ -145,10 +159,7 @@ def time_variant(torch, mhd, st, prec, scheme, K, W, dist, stream, profile=True)
     ms = e0.elapsed_time(e1)
     groups, rec = s.profile_end() if profile else ({}, 0)
     s.sync()
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(torch, ms, dist, "cuda")
     return ms, groups, rec, s
 
 
@@ -204,6 +215,125 @@ def cpu_baseline(scheme, target_s=12.0):
                       f"incl. the CFL dt, OpenMP on all host threads"}
 
 
+def batch_variant(torch, mhd, K, stream):
+    """The batched uneven workload: 48 independent periodic boxes with sides
+    drawn from {32, 48, 64, 96, 128, 192} (seed 1), linear waves and ABC
+    fields in turn, FP32 VL + PPM + HLLD.  One graph-captured batched step
+    (every kernel stage one launch over all boxes, autotuned sweep tiling)
+    against a loop that steps each box on its own context."""
+    from paper_1804_03479_b300 import inputs as I
+    sides = I.box_sides(48, seed=1)
+    boxes = [I.batch_box(i, sd, seed=1) for i, sd in enumerate(sides)]
+    shapes = [b.U.shape[1:] for b in boxes]
+    dxs = [b.dx for b in boxes]
+    ncell = sum(int(np.prod(sh)) for sh in shapes)
+    s = mhd.Solver(None, None, 5 / 3, "vl", "ppm", "hlld", "fp32", 0.3, stream=stream.cuda_stream,
+                   shapes=shapes, dxs=dxs)
+    for k, b in enumerate(boxes):
+        s.set_state(torch.from_numpy(b.U).to("cuda", torch.float32), torch.from_numpy(b.B).to("cuda", torch.float32), box=k)
+    tl, bps, tune_ms = s.autotune(reps=2)
+    s.advance(2, use_graph=True)
+    s.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.advance(K, use_graph=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    s.sync()
+    s.free()
+    # the same boxes, one context each, stepped one after the other
+    ctxs = []
+    for b in boxes:
+        c = mhd.Solver(b.U.shape[1:], b.dx, 5 / 3, "vl", "ppm", "hlld", "fp32", 0.3, stream=stream.cuda_stream)
+        c.set_state(torch.from_numpy(b.U).to("cuda", torch.float32), torch.from_numpy(b.B).to("cuda", torch.float32))
+        ctxs.append(c)
+    for c in ctxs:
+        c.advance(1)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(K):
+        for c in ctxs:
+            c.advance(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_loop = e0.elapsed_time(e1) / K
+    for c in ctxs:
+        c.free()
+    return {"value": ncell / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": K, "boxes": 48,
+            "cells": ncell, "sides": sides, "scheme": "vl+ppm+hlld", "precision": "fp32",
+            "sweep_tiling": {"tile_len": tl, "blocks_per_sm": bps, "autotune_ms_per_step": tune_ms},
+            "launches_per_step": 12, "graph": True,
+            "per_box_loop": {"value": ncell / (ms_loop * 1e-3), "ms_per_step": ms_loop, "launches_per_step": 12 * 48},
+            "speedup_vs_per_box_loop": ms_loop / ms}
+
+
+def learned_variant(torch, mhd, K, stream):
+    """The learned path select on the 384^3 ABC box (k = 6 pi, beta = 0.1) with
+    ten seeded Sedov-type blasts (E = 1 in r < 0.05): the selector network is
+    trained here on pairs the method generates at 128^3 (ABC, blast and
+    Orszag-Tang states), then the selected FP32 VL run is timed against the
+    all-full (PPM + HLLD) run from the same state, with the L1 difference
+    after K steps per field."""
+    from paper_1804_03479_b300 import inputs as I
+    from paper_1804_03479_b300 import learned as LRN
+    t0 = time.perf_counter()
+    stats = {}
+    X, y, err = LRN.make_pairs(LRN.training_ics(128, seed=7), stats=stats)
+    net, hist = LRN.train(X, y, epochs=4, batch=8192, lr=2e-3)
+    conf_train = LRN.confusion(net, X, y)
+    t_train = time.perf_counter() - t0
+    npairs, safe = int(X.shape[0]), float(y.mean().item())
+    del X, y, err
+    st = I.abc_blasts(384, kmult=3, beta=0.1, nblast=10, E=1.0, radius=0.05, seed=2)
+    Xh, yh, _ = LRN.make_pairs([st], snapshots=(0,))
+    conf_held = LRN.confusion(net, Xh, yh)
+    del Xh, yh
+    out = {}
+    states = {}
+    for name in ("full", "selected"):
+        s = mhd.Solver(st.U.shape[1:], st.dx, st.gamma, *LRN.FULL, "fp32", 0.3, stream=stream.cuda_stream,
+                       pfloor=LRN.PFLOOR)
+        U = torch.from_numpy(st.U).to("cuda", torch.float32)
+        B = torch.from_numpy(st.B).to("cuda", torch.float32)
+        if name == "selected":
+            s.set_selector(net)
+        s.set_state(U, B)
+        s.advance(2)                      # warm-up, then back to the initial state
+        s.set_state(U, B)
+        s.sync()
+        s.profile_begin(K)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.advance(K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / K
+        groups, rec = s.profile_end()
+        if name == "selected":
+            out["cheap_fraction_blocks"], out["cheap_fraction_tiles"] = s.selector_stats()
+        s.get_state(U, B)
+        states[name] = (U, B)
+        out[name] = {"value": st.U[0].size / (ms * 1e-3), "ms_per_step": ms,
+                     "kernel_ms_per_step": {k: v / rec for k, v in groups.items()},
+                     "floored_cell_steps": s.floor_count()}
+        s.free()
+    net.free()
+    l1 = LRN.rel_l1_fields(states["selected"], states["full"])
+    return {"value": out["selected"]["value"], "unit": UNIT, "ms_per_step": out["selected"]["ms_per_step"],
+            "steps": K, "workload": "abc384_k6pi_beta0.1 + 10 blasts (E=1, r<0.05, seed 2)",
+            "precision": "fp32", "full_path": out["full"], "selected_path": out["selected"],
+            "speedup_vs_all_full": out["full"]["ms_per_step"] / out["selected"]["ms_per_step"],
+            "cheap_fraction_blocks": out["cheap_fraction_blocks"], "cheap_fraction_tiles": out["cheap_fraction_tiles"],
+            "rel_l1_vs_all_full_after_steps": dict(zip(["rho", "Mx", "My", "Mz", "e", "Bx", "By", "Bz"], l1)),
+            "tau": LRN.TAU, "pfloor": LRN.PFLOOR,
+            "training": {"pairs": npairs, "safe_fraction": safe, "wall_s": t_train, "train": conf_train,
+                         "held_out_384": conf_held, "loss_first_last": [hist[0], hist[-1]],
+                         "floored_cell_steps": stats.get("floored_cell_steps")}}
+
+
 def e2e(torch, mhd, st, prec, scheme, K, stream):
     """same metric through the C ABI with host buffers: each step copies the
     state in from pinned host memory, advances, copies it back out"""
@@ -228,6 +358,55 @@ def e2e(torch, mhd, st, prec, scheme, K, stream):
     nbytes = Uh.numel() * Uh.element_size() + Bh.numel() * Bh.element_size()
     return {"value": st.U[0].size * K / el, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
             "steps": K, "path": "mhd_set_state(host) + mhd_advance(1) + mhd_get_state(host)"}
+
+
+def run_stress(args):
+    """Mixed-precision stress: 512 x 256 x 256 (a 2 x 1 x 1 box, dx = 1/256)
+    low-beta ABC field (beta = 1e-3, rho = 1) plus a current loop
+    (A_z = 1e-3 (0.3 - r), r < 0.3) carried at v = (2, 2, 2).  The FP64,
+    MIXED and FP32 forms (VL + PLM + Roe) advance the same initial state with
+    one dt sequence (the FP64 run's CFL dt each step); reported: relative L1
+    per field of MIXED and FP32 against FP64 (the FP64 path matches the CPU
+    oracle to 1e-12 per step) and max |div B| dx / B_rms of each form."""
+    import torch
+    from paper_1804_03479_b300 import build as Bld
+    Bld.build()
+    from paper_1804_03479_b300 import inputs as I
+    from paper_1804_03479_b300 import mhd
+    torch.cuda.set_device(0)
+    nx, ny, nz = args.stress_shape
+    st = I.current_loop(nx, ny, nz)
+    forms = {}
+    for prec in ("fp64", "mixed", "fp32"):
+        cast = torch.float32 if prec == "fp32" else torch.float64
+        s = mhd.Solver(st.U.shape[1:], st.dx, st.gamma, args.integrator, args.recon, args.riemann, prec, 0.3)
+        s.set_state(torch.from_numpy(st.U).to("cuda", cast), torch.from_numpy(st.B).to("cuda", cast))
+        forms[prec] = s
+    t0 = time.perf_counter()
+    for _ in range(args.stress_steps):
+        dt = forms["fp64"].cfl_dt()
+        for s in forms.values():
+            s.step(dt)
+    for s in forms.values():
+        s.sync()
+    wall = time.perf_counter() - t0
+    ref = forms["fp64"].get_state()
+    names = ["rho", "Mx", "My", "Mz", "e", "Bx", "By", "Bz"]
+    out = {}
+    for prec, s in forms.items():
+        U, B = s.get_state()
+        m, r = s.divB()
+        entry = {"max_divB_dx_over_Brms": m / r}
+        if prec != "fp64":
+            l1 = [float(np.abs(U[f].astype(np.float64) - ref[0][f]).sum() / np.abs(ref[0][f]).sum()) for f in range(5)]
+            l1 += [float(np.abs(B[d].astype(np.float64) - ref[1][d]).sum() / np.abs(ref[1][d]).sum()) for d in range(3)]
+            entry["rel_l1_vs_fp64"] = dict(zip(names, l1))
+        out[prec] = entry
+        s.free()
+    line = {"mode": "precision_stress", "workload": f"current loop on low-beta ABC, {nx}x{ny}x{nz}, beta=1e-3, v=(2,2,2)",
+            "scheme": f"{args.integrator}+{args.recon}+{args.riemann}", "steps": args.stress_steps, "wall_s": wall,
+            "forms": out}
+    print(json.dumps(line), flush=True)
 
 
 def run_reference(args):
@@ -274,9 +453,16 @@ def main():
     ap.add_argument("--variants", default="fp64,mixed", help="other precisions measured beside the main line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--stress", action="store_true", help="mixed-precision stress run (not a bench line)")
+    ap.add_argument("--stress-steps", type=int, default=500)
+    ap.add_argument("--stress-shape", type=int, nargs=3, default=[512, 256, 256])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.stress:
+        return run_stress(args)
 
     import torch
     from paper_1804_03479_b300 import build as Bld
@@ -305,7 +491,7 @@ def main():
     dev_bytes = s.device_bytes()
     s.free()
     sm_mhz = clocks["sm_mhz"] if clocks else pk["sm_max_mhz"]
-    value = ws * n * args.steps / (ms * 1e-3)
+    value = aggregate_value(ws, n, args.steps, ms)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -331,6 +517,10 @@ def main():
             variants[prec] = {"value": vv, "unit": UNIT, "ms_per_step": msv / kv, "steps": kv,
                               "vs_p100_paper": vv / PAPER_P100[prec] if prec in PAPER_P100 else None,
                               "roofline": roofline(prec, gv, recv, n, pk, sm_mhz) if recv else None}
+        if not args.no_batch:
+            variants["batch48"] = batch_variant(torch, mhd, max(3, min(args.steps, 10)), stream)
+        if not args.no_learned:
+            variants["learned384"] = learned_variant(torch, mhd, max(3, min(args.steps, 10)), stream)
         line["variants"] = variants
         if not args.no_e2e:
             line["e2e"] = e2e(torch, mhd, st, args.precision, scheme, max(3, min(args.steps, 8)), stream)

@@ -67,6 +67,10 @@ typedef struct {
     int riemann;      /* MHD_ROE, MHD_HLLD, MHD_HLLE                      */
     int precision;    /* MHD_FP64, MHD_FP32, MHD_MIXED                    */
     double cfl;       /* Courant number for mhd_cfl_dt / mhd_advance      */
+    double pfloor;    /* pressure floor, 0 = none (the paper's scheme has
+                         none; > 0 raises e where P < pfloor at the start
+                         of a step and floors the half-step P: not
+                         conservative, counted by mhd_floor_count)        */
 } mhd_scheme;
 
 typedef struct mhd_ctx mhd_ctx;
@@ -78,37 +82,62 @@ typedef struct mhd_ctx mhd_ctx;
 mhd_status mhd_init(const mhd_grid* grid, double gamma, const mhd_scheme* scheme, void* stream,
                     mhd_ctx** out);
 
-/* Copy the state in (U: 5*n, B: 3*n elements of the layout above).
- * on_device != 0: U, B are device pointers; else host pointers. */
+/* Batch of independent periodic boxes (each its own grid and dt) advanced
+ * together: every kernel of a step is one launch over all boxes, the face
+ * sweeps run a persistent grid over the batch's tile list (tile shape set
+ * by mhd_set_sweep_config or mhd_autotune).  mhd_init is the batch of one.
+ * The paper advances many patch groups per GPU call (Sec. 4); here the
+ * groups are whole boxes. */
+mhd_status mhd_init_batch(int nbox, const mhd_grid* grids, double gamma, const mhd_scheme* scheme,
+                          void* stream, mhd_ctx** out);
+int mhd_nbox(mhd_ctx* ctx);
+
+/* Copy the state of box `box` in (U: 5*n, B: 3*n elements of the layout
+ * above, n the box's cell count).  on_device != 0: U, B are device
+ * pointers; else host pointers.  mhd_set_state is box 0. */
+mhd_status mhd_set_state_box(mhd_ctx* ctx, int box, const void* U, const void* B, int on_device);
 mhd_status mhd_set_state(mhd_ctx* ctx, const void* U, const void* B, int on_device);
 
-/* Copy the state out (same layout); synchronises the stream. */
+/* Copy the state of a box out (same layout); synchronises the stream. */
+mhd_status mhd_get_state_box(mhd_ctx* ctx, int box, void* U, void* B, int on_device);
 mhd_status mhd_get_state(mhd_ctx* ctx, void* U, void* B, int on_device);
 
-/* CFL time step (Sec. 3.2): cfl * dx / max over cells and axes of
- * |v_d| + c_f,d, from the current state.  Synchronises. */
+/* CFL time step of every box (Sec. 3.2): dt[b] = cfl * dx_b / max over the
+ * box's cells and axes of |v_d| + c_f,d, from the current state.
+ * dt has nbox entries.  Synchronises. */
 mhd_status mhd_cfl_dt(mhd_ctx* ctx, double* dt);
 
-/* One step of the scheme (Sec. 3.2, CTU steps 1-8 or VL steps 1-7) with
- * the given dt > 0.  Asynchronous. */
+/* One step of the scheme (Sec. 3.2, CTU steps 1-8 or VL steps 1-7) with the
+ * same dt > 0 for every box (mhd_step) or dt[b] per box (mhd_step_boxes).
+ * Asynchronous. */
 mhd_status mhd_step(mhd_ctx* ctx, double dt);
+mhd_status mhd_step_boxes(mhd_ctx* ctx, const double* dt);
 
-/* nsteps steps, each with its CFL dt computed and used on the device (no
- * host round trip).  Asynchronous.  With use_graph != 0 one step is
- * captured once into a CUDA graph and replayed. */
+/* nsteps steps, each with every box's CFL dt computed and used on the
+ * device (no host round trip).  Asynchronous.  With use_graph != 0 one step
+ * is captured once into a CUDA graph and replayed. */
 mhd_status mhd_advance(mhd_ctx* ctx, int nsteps, int use_graph);
 
-/* dt used by the most recent step.  Synchronises. */
+/* dt of every box used by the most recent step (nbox entries).  Synchronises. */
 mhd_status mhd_last_dt(mhd_ctx* ctx, double* dt);
 
-/* Discrete divergence (Eq. 16): *maxabs = max over cells of
- * |sum_d B_d(c + e_d) - B_d(c)| (= max |div B| dx), *brms = rms of the
- * cell-centre field.  Synchronises. */
+/* Discrete divergence (Eq. 16) per box: maxabs[b] = max over the box's
+ * cells of |sum_d B_d(c + e_d) - B_d(c)| (= max |div B| dx), brms[b] = rms
+ * of the box's cell-centre field (nbox entries each).  Synchronises. */
 mhd_status mhd_divB(mhd_ctx* ctx, double* maxabs, double* brms);
 
-/* Sums over the box (FP64, fixed-order reduction): rho, Mx, My, Mz, e over
- * cells, Bx, By, Bz over faces (8 values).  Synchronises. */
+/* Sums per box (FP64, fixed-order reduction): rho, Mx, My, Mz, e over cells,
+ * Bx, By, Bz over faces; sums8 has 8 * nbox entries.  Synchronises. */
 mhd_status mhd_sums(mhd_ctx* ctx, double* sums8);
+
+/* Face-sweep tiling: tiles of 32 x tile_len faces (tile_len 4, 8 or 16),
+ * blocks_per_sm x SMs persistent blocks.  mhd_autotune times every pair on
+ * the context's own batch (reps steps each, the state restored after each
+ * trial), keeps the fastest and reports it (ms per step in *ms_best).  The
+ * autotuner allocates a temporary copy of the state. */
+mhd_status mhd_set_sweep_config(mhd_ctx* ctx, int tile_len, int blocks_per_sm);
+mhd_status mhd_get_sweep_config(mhd_ctx* ctx, int* tile_len, int* blocks_per_sm);
+mhd_status mhd_autotune(mhd_ctx* ctx, int reps, int* tile_len, int* blocks_per_sm, double* ms_best);
 
 /* Wait for all work queued on the context's stream; reports recorded
  * device-side anomalies. */
@@ -125,6 +154,9 @@ mhd_status mhd_sync(mhd_ctx* ctx);
 mhd_status mhd_profile_begin(mhd_ctx* ctx, int max_steps);
 mhd_status mhd_profile_end(mhd_ctx* ctx, double* ms, int ngroups, int* steps);
 
+/* Cell-steps raised to the pressure floor since mhd_init.  Synchronises. */
+long long mhd_floor_count(mhd_ctx* ctx);
+
 /* Cell index of the first anomaly found (or -1) and reset of the error. */
 long long mhd_bad_cell(mhd_ctx* ctx);
 void mhd_clear_error(mhd_ctx* ctx);
@@ -140,6 +172,49 @@ int mhd_launches_per_step(mhd_ctx* ctx);
 
 /* Free the context and its device memory (NULL is allowed). */
 void mhd_free(mhd_ctx* ctx);
+
+/* ---- learned path selector ---------------------------------------------
+ * Per 4^3 block of cells a small MLP (48 features -> 64 -> 64 -> 1, ReLU,
+ * BF16 weights on the tensor cores, FP32 accumulation) predicts whether the
+ * cheap path (PLM in primitive variables + HLLE) stays within a stated error
+ * of the full path (characteristic PPM + HLLD) for one step.  Not in the
+ * paper: the paper's method is the full path everywhere; this is an
+ * acceleration judged against it.  All arrays are DEVICE pointers. */
+typedef struct mhd_mlp mhd_mlp;
+
+/* Network with seeded He-uniform weights, zero biases; Adam state zero. */
+mhd_status mhd_mlp_create(void* stream, unsigned long long seed, mhd_mlp** out);
+void mhd_mlp_free(mhd_mlp* mlp);
+/* Packed FP32 parameter count (7361): W1[48][64], b1[64], W2[64][64],
+ * b2[64], w3[64], b3. */
+int mhd_mlp_nparam(void);
+mhd_status mhd_mlp_set_weights(mhd_mlp* mlp, const float* w, int on_device);
+mhd_status mhd_mlp_get_weights(mhd_mlp* mlp, float* w, int on_device);
+/* Gradient of the weighted mean binary cross-entropy of the logits against
+ * y (0/1) over n samples X[n][48]; wgt[n] may be NULL (all 1); wsum is the
+ * sum of the weights.  grad_out: device [nparam]; *loss: host, may be NULL. */
+mhd_status mhd_mlp_grad(mhd_mlp* mlp, const float* X, const float* y, const float* wgt, long long n,
+                        double wsum, float* grad_out, float* loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on that gradient. */
+mhd_status mhd_mlp_train_step(mhd_mlp* mlp, const float* X, const float* y, const float* wgt, long long n,
+                              double wsum, double lr, float* loss);
+/* Logits of n feature rows (logit > 0: the cheap path is predicted safe). */
+mhd_status mhd_mlp_predict(mhd_mlp* mlp, const float* X, long long n, float* logits);
+/* 4^3 blocks of a one-box context whose sides are multiples of 4 (else -1). */
+long long mhd_nblocks(mhd_ctx* ctx);
+/* Features of every block of the current state, feats[nblocks][48]. */
+mhd_status mhd_block_features(mhd_ctx* ctx, float* feats);
+/* Per block, max over the 8 stored fields of mean |a - b| over the block
+ * divided by the field's scale in a (rho; rho c_ref for momentum; e; B_ref
+ * for the face B): the label metric of a training pair. */
+mhd_status mhd_block_error(mhd_ctx* a, mhd_ctx* b, float* err);
+/* Attach a trained network to a one-box FP32 VL context (NULL detaches):
+ * every following step computes the features, runs the network and steps
+ * each sweep tile on the full path when any block next to one of its faces
+ * is predicted unsafe, else on the cheap path. */
+mhd_status mhd_set_selector(mhd_ctx* ctx, mhd_mlp* mlp);
+/* Fractions of blocks and of sweep tiles the last selected step ran cheap. */
+mhd_status mhd_selector_stats(mhd_ctx* ctx, double* frac_blocks, double* frac_tiles);
 
 /* ---- stepping without any device allocation ---------------------------
  * The paper has no counterpart: this is a service for callers that may not

@@ -22,6 +22,13 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path
          "-I" + CSRC]
 
 
+# the FP32 and mixed pipelines use the fast (2-ulp) single-precision division
+# and square root and flush denormals; double-precision code is unaffected
+EXTRA = {"mhd_fp32.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
+         "mhd_mixed.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
+         "mhd_learned.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]}
+
+
 def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
@@ -40,9 +47,9 @@ def _stale(target, deps):
 
 def _compile(src, verbose):
     obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-    if not _stale(obj, [src] + headers()):
+    if not _stale(obj, [src, os.path.abspath(__file__)] + headers()):
         return obj, ""
-    cmd = [NVCC, *ARCH, *FLAGS, "-c", src, "-o", obj]
+    cmd = [NVCC, *ARCH, *FLAGS, *EXTRA.get(os.path.basename(src), []), "-c", src, "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)

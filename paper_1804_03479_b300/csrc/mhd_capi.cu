@@ -34,7 +34,9 @@ static void release(mhd_ctx* c)
 {
     void* bufs[] = {c->rho, c->m[0], c->m[1], c->m[2], c->e, c->b[0], c->b[1], c->b[2], c->W, c->Wh,
                     c->F1, c->F2, c->E, c->Bh[0], c->Bh[1], c->Bh[2], c->WM, c->WP, c->stage,
-                    c->dt, c->smax, c->bad, c->part, c->diag};
+                    c->dt, c->dtc, c->smax, c->smax_part, c->bad, c->nfloor, c->part, c->diag, c->dbox, c->sel_feats,
+                    c->sel_flags, c->sel_cnt, c->sel_list[0], c->sel_list[1], c->sel_list[2], c->sel_list[3],
+                    c->sel_list[4], c->sel_list[5]};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (c->have_graph) cudaGraphExecDestroy(c->gexec);
@@ -42,6 +44,7 @@ static void release(mhd_ctx* c)
         for (int q = 0; q < c->prof_cap * (MHD_NGROUPS + 1); q++) cudaEventDestroy(c->prof_ev[q]);
         free(c->prof_ev);
     }
+    free(c->hbox);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
@@ -52,19 +55,47 @@ static cudaError_t dalloc(mhd_ctx* c, void** p, size_t bytes)
     return e;
 }
 
-extern "C" mhd_status mhd_init(const mhd_grid* grid, double gamma, const mhd_scheme* scheme, void* stream,
-                               mhd_ctx** out)
+// tile prefix sums of the box table for tile length tl; uploads the table
+static cudaError_t layout_tiles(mhd_ctx* c, int tl)
+{
+    int t0[3] = {0, 0, 0};
+    for (int b = 0; b < c->nbox; b++) {
+        BoxDev& x = c->hbox[b];
+        for (int d = 0; d < 3; d++) {
+            x.tile0[d] = t0[d];
+            t0[d] += tiles_of_box(x.nx, x.ny, x.nz, d, tl);
+        }
+    }
+    c->B.tl = tl;
+    for (int d = 0; d < 3; d++) c->B.ntile[d] = t0[d];
+    if (c->have_graph) {   // a captured step holds the old tile layout
+        cudaGraphExecDestroy(c->gexec);
+        c->have_graph = false;
+    }
+    cudaError_t e = cudaMemcpyAsync(c->dbox, c->hbox, sizeof(BoxDev) * c->nbox, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return e;
+}
+
+static mhd_status init_common(int nbox, const mhd_grid* grids, double gamma, const mhd_scheme* scheme, void* stream,
+                              mhd_ctx** out)
 {
     if (!out) return MHD_EINVAL;
     *out = nullptr;
-    if (!grid || !scheme) { g_init_err = "null grid or scheme"; return MHD_EINVAL; }
-    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || !(grid->dx > 0.0)) { g_init_err = "bad grid"; return MHD_EINVAL; }
+    if (nbox < 1 || !grids || !scheme) { g_init_err = "null grid or scheme, or no box"; return MHD_EINVAL; }
+    for (int b = 0; b < nbox; b++)
+        if (grids[b].nx < 1 || grids[b].ny < 1 || grids[b].nz < 1 || !(grids[b].dx > 0.0) ||
+            (long long)grids[b].nx * grids[b].ny * grids[b].nz >= (1LL << 31)) {
+            g_init_err = "bad grid (sides >= 1, dx > 0, fewer than 2^31 cells per box)";
+            return MHD_EINVAL;
+        }
     if (!(gamma > 1.0)) { g_init_err = "gamma must exceed 1"; return MHD_EINVAL; }
     if (scheme->integrator < 0 || scheme->integrator > 1 || scheme->recon < 0 || scheme->recon > 2 ||
         scheme->riemann < 0 || scheme->riemann > 2 || scheme->precision < 0 || scheme->precision > 2) {
         g_init_err = "bad scheme enum";
         return MHD_EINVAL;
     }
+    if (!(scheme->pfloor >= 0.0)) { g_init_err = "pfloor must be >= 0"; return MHD_EINVAL; }
     if (scheme->integrator == MHD_CTU && scheme->recon == MHD_PLM_PRIM) {
         g_init_err = "PLM_PRIM is built for VL only";
         return MHD_EUNSUPPORTED;
@@ -72,28 +103,51 @@ extern "C" mhd_status mhd_init(const mhd_grid* grid, double gamma, const mhd_sch
     mhd_ctx* c = (mhd_ctx*)calloc(1, sizeof(mhd_ctx));
     if (!c) return MHD_ENOMEM;
     strcpy(c->err, "no error");
-    c->grid = *grid;
+    c->grid = grids[0];
     c->sch = *scheme;
     c->gamma = gamma;
-    c->g.nx = grid->nx; c->g.ny = grid->ny; c->g.nz = grid->nz;
-    c->g.n = (long long)grid->nx * grid->ny * grid->nz;
-    c->g.dx = grid->dx;
-    const long long n = c->g.n;
+    c->nbox = nbox;
+    c->hbox = (BoxDev*)calloc((size_t)nbox, sizeof(BoxDev));
+    if (!c->hbox) { free(c); return MHD_ENOMEM; }
+    long long off = 0, vb = 0;
+    for (int b = 0; b < nbox; b++) {
+        BoxDev& x = c->hbox[b];
+        x.nx = grids[b].nx; x.ny = grids[b].ny; x.nz = grids[b].nz;
+        x.n = (long long)x.nx * x.ny * x.nz;
+        x.off = off;
+        x.vblk0 = vb;
+        x.dx = grids[b].dx;
+        x.inv_dx = (float)(1.0 / grids[b].dx);
+        off += x.n;
+        vb += (x.n + CELL_THREADS - 1) / CELL_THREADS;
+    }
+    const long long n = off;
+    c->B.nbox = nbox;
+    c->B.N = n;
+    c->B.nvblk = vb;
     cudaError_t attr = cudaSuccess;
     switch (scheme->precision) {
         case MHD_FP64: c->szu = 8; c->sze = 8; c->szr = 8; c->step = mhd_pick_fp64(scheme->integrator, scheme->recon, scheme->riemann, &attr); break;
         case MHD_FP32: c->szu = 4; c->sze = 4; c->szr = 4; c->step = mhd_pick_fp32(scheme->integrator, scheme->recon, scheme->riemann, &attr); break;
         default:       c->szu = 4; c->sze = 8; c->szr = 4; c->step = mhd_pick_mixed(scheme->integrator, scheme->recon, scheme->riemann, &attr); break;
     }
-    if (!c->step) { free(c); g_init_err = "scheme combination not built"; return MHD_EUNSUPPORTED; }
-    if (attr != cudaSuccess) { free(c); g_init_err = "cudaFuncSetAttribute failed"; return MHD_ECUDA; }
+    if (!c->step) { free(c->hbox); free(c); g_init_err = "scheme combination not built"; return MHD_EUNSUPPORTED; }
+    c->plain_step = c->step;
+    if (attr != cudaSuccess) { free(c->hbox); free(c); g_init_err = "cudaFuncSetAttribute failed"; return MHD_ECUDA; }
     c->launches = 12;   // prim, dt, 3 sweeps, emf, half, 3 sweeps or corrections, emf, full
-    cudaError_t e = cudaSuccess;
-    if (stream) {
-        c->stream = (cudaStream_t)stream;
-    } else {
-        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
-        c->own_stream = true;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev);
+    c->sweep_bps = 4;
+    c->cell_grid = (int)(vb < 16LL * c->nsm ? vb : 16LL * c->nsm);
+    if (c->cell_grid < 1) c->cell_grid = 1;
+    if (e == cudaSuccess) {
+        if (stream) {
+            c->stream = (cudaStream_t)stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+            c->own_stream = true;
+        }
     }
     const bool ctu = scheme->integrator == MHD_CTU;
     if (e == cudaSuccess) e = dalloc(c, &c->rho, n * c->szu);
@@ -108,16 +162,21 @@ extern "C" mhd_status mhd_init(const mhd_grid* grid, double gamma, const mhd_sch
     for (int d = 0; d < 3 && e == cudaSuccess; d++) e = dalloc(c, &c->Bh[d], n * c->sze);
     if (e == cudaSuccess && ctu) e = dalloc(c, &c->WM, 21 * n * c->szr);
     if (e == cudaSuccess && ctu) e = dalloc(c, &c->WP, 21 * n * c->szr);
-    if (e == cudaSuccess && scheme->precision == MHD_MIXED) e = dalloc(c, &c->stage, 5 * n * sizeof(double));
-    if (e == cudaSuccess) e = dalloc(c, (void**)&c->dt, sizeof(double));
-    if (e == cudaSuccess) e = dalloc(c, (void**)&c->smax, sizeof(unsigned long long));
+    if (e == cudaSuccess && scheme->precision == MHD_MIXED) e = dalloc(c, &c->stage, 4 * n * sizeof(double));
+    if (e == cudaSuccess) e = dalloc(c, (void**)&c->dt, sizeof(double) * nbox);
+    if (e == cudaSuccess) e = dalloc(c, (void**)&c->dtc, sizeof(DtBox) * nbox);
+    if (e == cudaSuccess) e = dalloc(c, (void**)&c->smax, sizeof(double) * nbox);
+    if (e == cudaSuccess) e = dalloc(c, (void**)&c->smax_part, sizeof(double) * vb);
     if (e == cudaSuccess) e = dalloc(c, (void**)&c->bad, sizeof(unsigned long long));
-    c->nblk = (int)((n + 255) / 256 < 148 * 16 ? (n + 255) / 256 : 148 * 16);
-    if (e == cudaSuccess) e = dalloc(c, (void**)&c->part, (size_t)c->nblk * 10 * sizeof(double));
-    if (e == cudaSuccess) e = dalloc(c, (void**)&c->diag, 10 * sizeof(double));
+    if (e == cudaSuccess) e = dalloc(c, (void**)&c->nfloor, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->nfloor, 0, sizeof(unsigned long long), c->stream);
+    if (e == cudaSuccess) e = dalloc(c, (void**)&c->part, (size_t)vb * 10 * sizeof(double));
+    if (e == cudaSuccess) e = dalloc(c, (void**)&c->diag, (size_t)nbox * 10 * sizeof(double));
+    if (e == cudaSuccess) e = dalloc(c, (void**)&c->dbox, sizeof(BoxDev) * nbox);
+    c->B.b = c->dbox;
     if (e == cudaSuccess) e = cudaMemsetAsync(c->bad, 0xff, sizeof(unsigned long long), c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->dt, 0, sizeof(double), c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->dt, 0, sizeof(double) * nbox, c->stream);
+    if (e == cudaSuccess) e = layout_tiles(c, 8);
     if (e != cudaSuccess) {
         g_init_err = e == cudaErrorMemoryAllocation ? "device allocation failed" : cudaGetErrorString(e);
         mhd_status s = e == cudaErrorMemoryAllocation ? MHD_ENOMEM : MHD_ECUDA;
@@ -129,6 +188,20 @@ extern "C" mhd_status mhd_init(const mhd_grid* grid, double gamma, const mhd_sch
     return MHD_OK;
 }
 
+extern "C" mhd_status mhd_init(const mhd_grid* grid, double gamma, const mhd_scheme* scheme, void* stream,
+                               mhd_ctx** out)
+{
+    return init_common(1, grid, gamma, scheme, stream, out);
+}
+
+extern "C" mhd_status mhd_init_batch(int nbox, const mhd_grid* grids, double gamma, const mhd_scheme* scheme,
+                                     void* stream, mhd_ctx** out)
+{
+    return init_common(nbox, grids, gamma, scheme, stream, out);
+}
+
+extern "C" int mhd_nbox(mhd_ctx* c) { return c ? c->nbox : 0; }
+
 static mhd_status check_device_flags(mhd_ctx* c)
 {
     unsigned long long bad = ~0ull;
@@ -138,87 +211,116 @@ static mhd_status check_device_flags(mhd_ctx* c)
     return c->sticky;
 }
 
-extern "C" mhd_status mhd_set_state(mhd_ctx* c, const void* U, const void* B, int on_device)
+extern "C" mhd_status mhd_set_state_box(mhd_ctx* c, int box, const void* U, const void* B, int on_device)
 {
-    if (!c || !U || !B) return fail(c, MHD_EINVAL, "null pointer");
-    const long long n = c->g.n;
+    if (!c || !U || !B || box < 0 || box >= c->nbox) return fail(c, MHD_EINVAL, "bad arguments");
+    const long long n = c->hbox[box].n, off = c->hbox[box].off, N = c->B.N;
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (c->sch.precision != MHD_MIXED) {
         const size_t sz = c->szu;  // == sze for the uniform layouts
         const char* u = (const char*)U;
         const char* b = (const char*)B;
-        void* dst[5] = {c->rho, c->m[0], c->m[1], c->m[2], c->e};
-        for (int f = 0; f < 5; f++) CK(cudaMemcpyAsync(dst[f], u + f * n * sz, n * sz, k, c->stream));
-        for (int d = 0; d < 3; d++) CK(cudaMemcpyAsync(c->b[d], b + d * n * sz, n * sz, k, c->stream));
+        char* dst[5] = {(char*)c->rho, (char*)c->m[0], (char*)c->m[1], (char*)c->m[2], (char*)c->e};
+        for (int f = 0; f < 5; f++) CK(cudaMemcpyAsync(dst[f] + off * sz, u + f * n * sz, n * sz, k, c->stream));
+        for (int d = 0; d < 3; d++) CK(cudaMemcpyAsync((char*)c->b[d] + off * sz, b + d * n * sz, n * sz, k, c->stream));
     } else {
         const double* u = (const double*)U;
         const double* b = (const double*)B;
-        CK(cudaMemcpyAsync(c->stage, u, 4 * n * sizeof(double), k, c->stream));
-        CK(cudaMemcpyAsync(c->e, u + 4 * n, n * sizeof(double), k, c->stream));
-        for (int d = 0; d < 3; d++) CK(cudaMemcpyAsync(c->b[d], b + d * n, n * sizeof(double), k, c->stream));
-        void* dst[4] = {c->rho, c->m[0], c->m[1], c->m[2]};
+        double* stg = (double*)c->stage;
+        for (int f = 0; f < 4; f++) CK(cudaMemcpyAsync(stg + f * N + off, u + f * n, n * sizeof(double), k, c->stream));
+        CK(cudaMemcpyAsync((double*)c->e + off, u + 4 * n, n * sizeof(double), k, c->stream));
+        for (int d = 0; d < 3; d++) CK(cudaMemcpyAsync((double*)c->b[d] + off, b + d * n, n * sizeof(double), k, c->stream));
+        float* dst[4] = {(float*)c->rho, (float*)c->m[0], (float*)c->m[1], (float*)c->m[2]};
         for (int f = 0; f < 4; f++)
-            k_convert<float, double><<<c->nblk, 256, 0, c->stream>>>((float*)dst[f], (const double*)c->stage + f * n, n);
+            k_convert<float, double><<<1184, 256, 0, c->stream>>>(dst[f] + off, stg + f * N + off, n);
         CK(cudaGetLastError());
     }
     if (!on_device) CK(cudaStreamSynchronize(c->stream));
     return MHD_OK;
 }
 
-extern "C" mhd_status mhd_get_state(mhd_ctx* c, void* U, void* B, int on_device)
+extern "C" mhd_status mhd_get_state_box(mhd_ctx* c, int box, void* U, void* B, int on_device)
 {
-    if (!c || !U || !B) return fail(c, MHD_EINVAL, "null pointer");
-    const long long n = c->g.n;
+    if (!c || !U || !B || box < 0 || box >= c->nbox) return fail(c, MHD_EINVAL, "bad arguments");
+    const long long n = c->hbox[box].n, off = c->hbox[box].off, N = c->B.N;
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (c->sch.precision != MHD_MIXED) {
         const size_t sz = c->szu;
         char* u = (char*)U;
         char* b = (char*)B;
-        void* src[5] = {c->rho, c->m[0], c->m[1], c->m[2], c->e};
-        for (int f = 0; f < 5; f++) CK(cudaMemcpyAsync(u + f * n * sz, src[f], n * sz, k, c->stream));
-        for (int d = 0; d < 3; d++) CK(cudaMemcpyAsync(b + d * n * sz, c->b[d], n * sz, k, c->stream));
+        const char* src[5] = {(const char*)c->rho, (const char*)c->m[0], (const char*)c->m[1], (const char*)c->m[2],
+                              (const char*)c->e};
+        for (int f = 0; f < 5; f++) CK(cudaMemcpyAsync(u + f * n * sz, src[f] + off * sz, n * sz, k, c->stream));
+        for (int d = 0; d < 3; d++) CK(cudaMemcpyAsync(b + d * n * sz, (const char*)c->b[d] + off * sz, n * sz, k, c->stream));
     } else {
         double* u = (double*)U;
         double* b = (double*)B;
-        void* src[4] = {c->rho, c->m[0], c->m[1], c->m[2]};
+        double* stg = (double*)c->stage;
+        const float* src[4] = {(const float*)c->rho, (const float*)c->m[0], (const float*)c->m[1], (const float*)c->m[2]};
         for (int f = 0; f < 4; f++)
-            k_convert<double, float><<<c->nblk, 256, 0, c->stream>>>((double*)c->stage + f * n, (const float*)src[f], n);
+            k_convert<double, float><<<1184, 256, 0, c->stream>>>(stg + f * N + off, src[f] + off, n);
         CK(cudaGetLastError());
-        CK(cudaMemcpyAsync(u, c->stage, 4 * n * sizeof(double), k, c->stream));
-        CK(cudaMemcpyAsync(u + 4 * n, c->e, n * sizeof(double), k, c->stream));
-        for (int d = 0; d < 3; d++) CK(cudaMemcpyAsync(b + d * n, c->b[d], n * sizeof(double), k, c->stream));
+        for (int f = 0; f < 4; f++) CK(cudaMemcpyAsync(u + f * n, stg + f * N + off, n * sizeof(double), k, c->stream));
+        CK(cudaMemcpyAsync(u + 4 * n, (const double*)c->e + off, n * sizeof(double), k, c->stream));
+        for (int d = 0; d < 3; d++) CK(cudaMemcpyAsync(b + d * n, (const double*)c->b[d] + off, n * sizeof(double), k, c->stream));
     }
     CK(cudaStreamSynchronize(c->stream));
     return check_device_flags(c);
 }
 
+extern "C" mhd_status mhd_set_state(mhd_ctx* c, const void* U, const void* B, int on_device)
+{
+    return mhd_set_state_box(c, 0, U, B, on_device);
+}
+
+extern "C" mhd_status mhd_get_state(mhd_ctx* c, void* U, void* B, int on_device)
+{
+    return mhd_get_state_box(c, 0, U, B, on_device);
+}
+
 extern "C" mhd_status mhd_cfl_dt(mhd_ctx* c, double* dt)
 {
     if (!c || !dt) return fail(c, MHD_EINVAL, "null pointer");
-    CK(cudaMemsetAsync(c->smax, 0, sizeof(unsigned long long), c->stream));
+    const int nb = c->cell_grid;
     switch (c->sch.precision) {
-        case MHD_FP64: k_prim<double, double, double><<<c->nblk, 256, 0, c->stream>>>(c->g, state_of<double, double>(c), (double*)c->W, c->gamma, c->smax, c->bad); break;
-        case MHD_FP32: k_prim<float, float, float><<<c->nblk, 256, 0, c->stream>>>(c->g, state_of<float, float>(c), (float*)c->W, c->gamma, c->smax, c->bad); break;
-        default:       k_prim<float, float, double><<<c->nblk, 256, 0, c->stream>>>(c->g, state_of<float, double>(c), (float*)c->W, c->gamma, c->smax, c->bad); break;
+        case MHD_FP64: k_prim<double, double, double><<<nb, CELL_THREADS, 0, c->stream>>>(c->B, state_of<double, double>(c), (double*)c->W, c->gamma, c->smax_part, c->bad, c->sch.pfloor); break;
+        case MHD_FP32: k_prim<float, float, float><<<nb, CELL_THREADS, 0, c->stream>>>(c->B, state_of<float, float>(c), (float*)c->W, c->gamma, c->smax_part, c->bad, c->sch.pfloor); break;
+        default:       k_prim<float, float, double><<<nb, CELL_THREADS, 0, c->stream>>>(c->B, state_of<float, double>(c), (float*)c->W, c->gamma, c->smax_part, c->bad, c->sch.pfloor); break;
     }
+    k_finalize_dt<<<c->nbox, 256, 0, c->stream>>>(c->B, c->smax_part, c->sch.cfl, nullptr, c->smax, nullptr);
     CK(cudaGetLastError());
-    unsigned long long s = 0;
-    CK(cudaMemcpyAsync(&s, c->smax, sizeof(s), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    double smax;
-    memcpy(&smax, &s, sizeof(double));
+    double* s = (double*)malloc(sizeof(double) * c->nbox);
+    if (!s) return fail(c, MHD_ENOMEM, "host allocation failed");
+    cudaError_t e = cudaMemcpyAsync(s, c->smax, sizeof(double) * c->nbox, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) { free(s); return fail(c, MHD_ECUDA, "cfl readback: %s", cudaGetErrorString(e)); }
     mhd_status st = check_device_flags(c);
-    if (st != MHD_OK) return st;
-    if (!(smax > 0.0)) return fail(c, MHD_ENEGATIVE, "no positive signal speed");
-    *dt = c->sch.cfl * c->g.dx / smax;
-    return MHD_OK;
+    for (int b = 0; b < c->nbox && st == MHD_OK; b++) {
+        if (!(s[b] > 0.0)) st = fail(c, MHD_ENEGATIVE, "no positive signal speed in box %d", b);
+        else dt[b] = c->sch.cfl * c->hbox[b].dx / s[b];
+    }
+    free(s);
+    return st;
 }
 
 extern "C" mhd_status mhd_step(mhd_ctx* c, double dt)
 {
     if (!c) return MHD_EINVAL;
     if (!(dt > 0.0) || !(dt < 1e300)) return fail(c, MHD_EINVAL, "dt must be positive and finite");
-    k_set_dt<<<1, 1, 0, c->stream>>>(c->dt, dt);
+    k_set_dt<<<1, 256, 0, c->stream>>>(c->B, c->dt, dt, c->dtc);
+    c->step(c, false);
+    CK(cudaGetLastError());
+    return MHD_OK;
+}
+
+extern "C" mhd_status mhd_step_boxes(mhd_ctx* c, const double* dt)
+{
+    if (!c || !dt) return fail(c, MHD_EINVAL, "null pointer");
+    for (int b = 0; b < c->nbox; b++)
+        if (!(dt[b] > 0.0) || !(dt[b] < 1e300)) return fail(c, MHD_EINVAL, "dt of box %d must be positive and finite", b);
+    CK(cudaMemcpyAsync(c->dt, dt, sizeof(double) * c->nbox, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));   // dt is the caller's host array
+    k_set_dt<<<1, 256, 0, c->stream>>>(c->B, c->dt, 0.0, c->dtc);
     c->step(c, false);
     CK(cudaGetLastError());
     return MHD_OK;
@@ -250,21 +352,22 @@ extern "C" mhd_status mhd_advance(mhd_ctx* c, int nsteps, int use_graph)
 extern "C" mhd_status mhd_last_dt(mhd_ctx* c, double* dt)
 {
     if (!c || !dt) return fail(c, MHD_EINVAL, "null pointer");
-    CK(cudaMemcpyAsync(dt, c->dt, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(dt, c->dt, sizeof(double) * c->nbox, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return MHD_OK;
 }
 
-static mhd_status run_diag(mhd_ctx* c, double out[10])
+static mhd_status run_diag(mhd_ctx* c, double* out)
 {
+    const int nb = c->cell_grid;
     switch (c->sch.precision) {
-        case MHD_FP64: k_diag<double, double><<<c->nblk, 256, 0, c->stream>>>(c->g, state_of<double, double>(c), c->part); break;
-        case MHD_FP32: k_diag<float, float><<<c->nblk, 256, 0, c->stream>>>(c->g, state_of<float, float>(c), c->part); break;
-        default:       k_diag<float, double><<<c->nblk, 256, 0, c->stream>>>(c->g, state_of<float, double>(c), c->part); break;
+        case MHD_FP64: k_diag<double, double><<<nb, CELL_THREADS, 0, c->stream>>>(c->B, state_of<double, double>(c), c->part); break;
+        case MHD_FP32: k_diag<float, float><<<nb, CELL_THREADS, 0, c->stream>>>(c->B, state_of<float, float>(c), c->part); break;
+        default:       k_diag<float, double><<<nb, CELL_THREADS, 0, c->stream>>>(c->B, state_of<float, double>(c), c->part); break;
     }
-    k_finish_diag<<<1, 32, 0, c->stream>>>(c->part, c->nblk, c->diag);
+    k_finish_diag<<<c->nbox, 32, 0, c->stream>>>(c->B, c->part, c->diag);
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(out, c->diag, 10 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(out, c->diag, (size_t)c->nbox * 10 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return check_device_flags(c);
 }
@@ -272,19 +375,26 @@ static mhd_status run_diag(mhd_ctx* c, double out[10])
 extern "C" mhd_status mhd_divB(mhd_ctx* c, double* maxabs, double* brms)
 {
     if (!c || !maxabs || !brms) return fail(c, MHD_EINVAL, "null pointer");
-    double d[10];
+    double* d = (double*)malloc(sizeof(double) * 10 * c->nbox);
+    if (!d) return fail(c, MHD_ENOMEM, "host allocation failed");
     mhd_status s = run_diag(c, d);
-    *maxabs = d[0];
-    *brms = sqrt(d[1] / (double)c->g.n);
+    for (int b = 0; b < c->nbox; b++) {
+        maxabs[b] = d[b * 10];
+        brms[b] = sqrt(d[b * 10 + 1] / (double)c->hbox[b].n);
+    }
+    free(d);
     return s;
 }
 
 extern "C" mhd_status mhd_sums(mhd_ctx* c, double* sums8)
 {
     if (!c || !sums8) return fail(c, MHD_EINVAL, "null pointer");
-    double d[10];
+    double* d = (double*)malloc(sizeof(double) * 10 * c->nbox);
+    if (!d) return fail(c, MHD_ENOMEM, "host allocation failed");
     mhd_status s = run_diag(c, d);
-    for (int f = 0; f < 8; f++) sums8[f] = d[2 + f];
+    for (int b = 0; b < c->nbox; b++)
+        for (int f = 0; f < 8; f++) sums8[b * 8 + f] = d[b * 10 + 2 + f];
+    free(d);
     return s;
 }
 
@@ -294,6 +404,87 @@ extern "C" mhd_status mhd_sync(mhd_ctx* c)
     CK(cudaStreamSynchronize(c->stream));
     CK(cudaGetLastError());
     return check_device_flags(c);
+}
+
+extern "C" mhd_status mhd_set_sweep_config(mhd_ctx* c, int tile_len, int blocks_per_sm)
+{
+    if (!c) return MHD_EINVAL;
+    if (!(tile_len == 4 || tile_len == 8 || tile_len == 16) || blocks_per_sm < 1 || blocks_per_sm > 64)
+        return fail(c, MHD_EINVAL, "tile_len must be 4, 8 or 16 and blocks_per_sm in [1, 64]");
+    c->sweep_bps = blocks_per_sm;
+    CK(layout_tiles(c, tile_len));
+    return MHD_OK;
+}
+
+extern "C" mhd_status mhd_get_sweep_config(mhd_ctx* c, int* tile_len, int* blocks_per_sm)
+{
+    if (!c || !tile_len || !blocks_per_sm) return fail(c, MHD_EINVAL, "null pointer");
+    *tile_len = c->B.tl;
+    *blocks_per_sm = c->sweep_bps;
+    return MHD_OK;
+}
+
+// time `reps` directly launched steps of the current configuration
+static mhd_status time_steps(mhd_ctx* c, int reps, float* ms)
+{
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    CK(cudaEventRecord(a, c->stream));
+    for (int r = 0; r < reps; r++) c->step(c, true);
+    CK(cudaEventRecord(b, c->stream));
+    CK(cudaEventSynchronize(b));
+    CK(cudaEventElapsedTime(ms, a, b));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    CK(cudaGetLastError());
+    return MHD_OK;
+}
+
+// Try every (tile length, blocks per SM) pair on the context's own batch;
+// the state is copied aside first and restored after every trial.
+extern "C" mhd_status mhd_autotune(mhd_ctx* c, int reps, int* tile_len, int* blocks_per_sm, double* ms_best)
+{
+    if (!c || reps < 1) return fail(c, MHD_EINVAL, "bad arguments");
+    const long long N = c->B.N;
+    void* saved = nullptr;
+    const size_t ub = 4 * N * c->szu, eb = 4 * N * c->sze;
+    CK(cudaMalloc(&saved, ub + eb));
+    char* sv = (char*)saved;
+    void* fu[4] = {c->rho, c->m[0], c->m[1], c->m[2]};
+    void* fe[4] = {c->e, c->b[0], c->b[1], c->b[2]};
+    cudaError_t e = cudaSuccess;
+    for (int f = 0; f < 4 && e == cudaSuccess; f++)
+        e = cudaMemcpyAsync(sv + f * N * c->szu, fu[f], N * c->szu, cudaMemcpyDeviceToDevice, c->stream);
+    for (int f = 0; f < 4 && e == cudaSuccess; f++)
+        e = cudaMemcpyAsync(sv + ub + f * N * c->sze, fe[f], N * c->sze, cudaMemcpyDeviceToDevice, c->stream);
+    const int tls[3] = {4, 8, 16};
+    const int bpss[4] = {1, 2, 4, 8};
+    float best = 1e30f;
+    int btl = c->B.tl, bbps = c->sweep_bps;
+    mhd_status st = e == cudaSuccess ? MHD_OK : fail(c, MHD_ECUDA, "autotune copy: %s", cudaGetErrorString(e));
+    for (int i = 0; i < 3 && st == MHD_OK; i++)
+        for (int j = 0; j < 4 && st == MHD_OK; j++) {
+            c->sweep_bps = bpss[j];
+            if (layout_tiles(c, tls[i]) != cudaSuccess) { st = fail(c, MHD_ECUDA, "autotune layout"); break; }
+            float ms = 0.0f;
+            st = time_steps(c, 1, &ms);              // warm-up
+            if (st == MHD_OK) st = time_steps(c, reps, &ms);
+            for (int f = 0; f < 4; f++)
+                cudaMemcpyAsync(fu[f], sv + f * N * c->szu, N * c->szu, cudaMemcpyDeviceToDevice, c->stream);
+            for (int f = 0; f < 4; f++)
+                cudaMemcpyAsync(fe[f], sv + ub + f * N * c->sze, N * c->sze, cudaMemcpyDeviceToDevice, c->stream);
+            if (st == MHD_OK && ms < best) { best = ms; btl = tls[i]; bbps = bpss[j]; }
+        }
+    cudaStreamSynchronize(c->stream);
+    cudaFree(saved);
+    if (st != MHD_OK) return st;
+    c->sweep_bps = bbps;
+    CK(layout_tiles(c, btl));
+    if (tile_len) *tile_len = btl;
+    if (blocks_per_sm) *blocks_per_sm = bbps;
+    if (ms_best) *ms_best = best / reps;
+    return MHD_OK;
 }
 
 extern "C" mhd_status mhd_profile_begin(mhd_ctx* c, int max_steps)
@@ -330,6 +521,15 @@ extern "C" mhd_status mhd_profile_end(mhd_ctx* c, double* ms, int ngroups, int* 
     }
     if (steps) *steps = c->prof_steps;
     return MHD_OK;
+}
+
+extern "C" long long mhd_floor_count(mhd_ctx* c)
+{
+    if (!c) return -1;
+    unsigned long long v = 0;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return -1;
+    if (cudaMemcpy(&v, c->nfloor, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+    return (long long)v;
 }
 
 extern "C" long long mhd_bad_cell(mhd_ctx* c)

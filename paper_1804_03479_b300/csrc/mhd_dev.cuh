@@ -18,10 +18,12 @@ enum { ROE = 0, HLLD = 1, HLLE = 2 };
 template <class R> struct Num;
 template <> struct Num<double> {
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+    static __device__ __forceinline__ double abs_(double x) { return fabs(x); }
     static constexpr double hlld_degen = 1e-8;
 };
 template <> struct Num<float> {
     static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ float abs_(float x) { return fabsf(x); }
     static constexpr float hlld_degen = 1e-5f;
 };
 
@@ -281,7 +283,7 @@ __device__ __forceinline__ bool roe_flux(const R wl[7], const R wr[7], R bn, R g
         ru[4] = q[4] / gm1 + ke * q[0] + m.rho * (m.u * q[1] + m.v * q[2] + m.w * q[3]) + m.b1 * q[5] + m.b2 * q[6];
         ru[5] = q[5];
         ru[6] = q[6];
-        R c = eta[a], cd = fabs(lam[a]) * eta[a];
+        R c = eta[a], cd = Num<R>::abs_(lam[a]) * eta[a];
 #pragma unroll
         for (int k = 0; k < 7; k++) dis[k] += cd * ru[k];
         if (a < 6) {
@@ -315,7 +317,7 @@ __device__ __forceinline__ void hlld_star(const R w[7], R bn, R gm1, R S, R SM, 
     R den = scale - bn * bn;
     R rs = d / (S - SM);
     R vt1 = w[2], vt2 = w[3], bt1 = w[5], bt2 = w[6];
-    if (fabs(den) > Num<R>::hlld_degen * fabs(scale)) {
+    if (Num<R>::abs_(den) > Num<R>::hlld_degen * Num<R>::abs_(scale)) {
         R tmp = (SM - w[1]) / den;
         R fac = (d * (S - w[1]) - bn * bn) / den;
         vt1 = w[2] - bn * w[5] * tmp;
@@ -368,8 +370,8 @@ __device__ __forceinline__ void hlld_flux(const R wl[7], const R wr[7], R bn, R 
     hlld_star(wl, bn, gm1, SL, SM, pts, usl);
     hlld_star(wr, bn, gm1, SR, SM, pts, usr);
     R sql = Num<R>::sqrt_(usl[0]), sqr = Num<R>::sqrt_(usr[0]);
-    R SsL = SM - fabs(bn) / sql;
-    R SsR = SM + fabs(bn) / sqr;
+    R SsL = SM - Num<R>::abs_(bn) / sql;
+    R SsR = SM + Num<R>::abs_(bn) / sqr;
     const bool left = SM >= R(0);
     // the outer side whose fan we are in
     const R* wo = left ? wl : wr;
@@ -414,7 +416,7 @@ __device__ __forceinline__ void riemann(const R wl[7], const R wr[7], R bn, R gm
 template <class R>
 __device__ __forceinline__ R mc(R l, R r, R c)
 {
-    if (l * r > R(0)) return sgn1(c) * rmin(rmin(R(2) * fabs(l), R(2) * fabs(r)), fabs(c));
+    if (l * r > R(0)) return sgn1(c) * rmin(rmin(R(2) * Num<R>::abs_(l), R(2) * Num<R>::abs_(r)), Num<R>::abs_(c));
     return R(0);
 }
 

@@ -6,15 +6,21 @@
 #include "mhd_kernels.cuh"
 
 struct mhd_ctx;
+struct mhd_mlp;
 typedef void (*mhd_step_fn)(mhd_ctx*, bool device_dt);
 
 struct mhd_ctx {
-    mhd_grid grid;
+    mhd_grid grid;                  // box 0
     mhd_scheme sch;
     double gamma;
     cudaStream_t stream;
     bool own_stream;
-    mhd::Grid g;
+    int nbox;
+    mhd::BoxDev* hbox;              // host copy of the box table
+    mhd::BoxDev* dbox;              // device copy
+    mhd::Boxes B;                   // kernel view (points at dbox)
+    int nsm;                        // SMs of the device
+    int sweep_bps;                  // persistent sweep blocks per SM
     size_t szu, sze, szr;          // element sizes: rho/M storage, e/B storage, arithmetic
     void* rho;
     void* m[3];
@@ -29,15 +35,25 @@ struct mhd_ctx {
     void* WM;                       // 3 x 7 traced states (CTU)
     void* WP;
     void* stage;                    // staging for the mixed layout
-    double* dt;
-    unsigned long long* smax;
+    double* dt;                     // [nbox]
+    mhd::DtBox* dtc;                // [nbox] dt and its ratios to dx
+    double* smax;                   // [nbox] signal-speed maximum of each box
+    double* smax_part;              // [nvblk] maximum of each virtual block
+    int cell_grid;                  // persistent grid of the per-cell kernels
     unsigned long long* bad;
-    double* part;
-    double* diag;
-    int nblk;                       // blocks of the per-cell kernels
+    unsigned long long* nfloor;     // cells raised to the pressure floor
+    double* part;                   // [nvblk][10]
+    double* diag;                   // [nbox][10]
     long long bytes;
     mhd_step_fn step;
+    mhd_step_fn plain_step;         // the scheme's own step (without selector)
     int launches;
+    // learned path selector (FP32 VL, one box)
+    mhd_mlp* sel;
+    float* sel_feats;               // [nblocks][48]
+    unsigned char* sel_flags;       // [nblocks], 1 = full path
+    int* sel_cnt;                   // per axis: cheap, full tile counts
+    int* sel_list[6];               // per axis: cheap list, full list
     cudaGraphExec_t gexec;
     bool have_graph;
     // kernel-group timing (CUDA events on the context stream)
@@ -70,17 +86,18 @@ inline StateP<TU, TE> state_of(mhd_ctx* c)
     return s;
 }
 
-inline int sweep_blocks(const Grid& g, int d)
+inline int sweep_grid(const mhd_ctx* c, int d)
 {
-    int ex = TX, ey = d == 2 ? 1 : TL, ez = d == 2 ? TL : 1;
-    return ((g.nx + ex - 1) / ex) * ((g.ny + ey - 1) / ey) * ((g.nz + ez - 1) / ez);
+    int cap = c->sweep_bps * c->nsm;
+    return c->B.ntile[d] < cap ? c->B.ntile[d] : cap;
 }
 
 template <class R, class TU, class TE, int INTEG, int RECON, int SOLVER>
 void run_step(mhd_ctx* c, bool device_dt)
 {
-    const Grid g = c->g;
-    const long long n = g.n;
+    const Boxes g = c->B;
+    const long long n = g.N;
+    const int nb = c->cell_grid;
     cudaStream_t st = c->stream;
     StateP<TU, TE> s = state_of<TU, TE>(c);
     R* W = (R*)c->W;
@@ -89,59 +106,58 @@ void run_step(mhd_ctx* c, bool device_dt)
     R* F2 = (R*)c->F2;
     R* E = (R*)c->E;
     TE* Bh[3] = {(TE*)c->Bh[0], (TE*)c->Bh[1], (TE*)c->Bh[2]};
-    const int nb = c->nblk;
     const double gam = c->gamma;
-    const size_t smem = sweep_smem_bytes<R>(RECON);
+    const size_t smem = sweep_smem_bytes<R>(RECON, g.tl);
 
     prof_mark(c, 0);
-    if (device_dt) cudaMemsetAsync(c->smax, 0, sizeof(unsigned long long), st);
-    k_prim<R, TU, TE><<<nb, 256, 0, st>>>(g, s, W, gam, device_dt ? c->smax : nullptr, c->bad);
-    if (device_dt) k_finalize_dt<<<1, 1, 0, st>>>(c->smax, c->sch.cfl, g.dx, c->dt);
+    k_prim<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, W, gam, device_dt ? c->smax_part : nullptr, c->bad,
+                                                   c->sch.pfloor, c->nfloor);
+    if (device_dt) k_finalize_dt<<<c->nbox, 256, 0, st>>>(g, c->smax_part, c->sch.cfl, c->dt, c->smax, c->dtc);
     prof_mark(c, 1);
 
     if (INTEG == VL) {
         // VL steps 1-3: first-order fluxes with the face B_n, edge E, half update
         for (int d = 0; d < 3; d++)
-            k_sweep<R, RECON, SOLVER, 0, TE><<<sweep_blocks(g, d), SWEEP_THREADS, 0, st>>>(
-                g, d, W, s.b[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dt, gam);
+            k_sweep<R, RECON, SOLVER, 0, TE><<<sweep_grid(c, d), SWEEP_THREADS, 0, st>>>(
+                g, d, W, s.b[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam);
         prof_mark(c, 2);
-        k_emf<R><<<nb, 256, 0, st>>>(g, F1, W, E);
+        k_emf<R><<<nb, CELL_THREADS, 0, st>>>(g, F1, W, E);
         prof_mark(c, 3);
-        k_half<R, TU, TE><<<nb, 256, 0, st>>>(g, s, F1, E, c->dt, gam, Bh[0], Bh[1], Bh[2], Wh);
+        k_half<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2], Wh, c->sch.pfloor);
         prof_mark(c, 4);
         // VL steps 4-7: reconstruct at the half step, Riemann, edge E, full update
         for (int d = 0; d < 3; d++)
-            k_sweep<R, RECON, SOLVER, 1, TE><<<sweep_blocks(g, d), SWEEP_THREADS, smem, st>>>(
-                g, d, Wh, Bh[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dt, gam);
+            k_sweep<R, RECON, SOLVER, 1, TE><<<sweep_grid(c, d), SWEEP_THREADS, smem, st>>>(
+                g, d, Wh, Bh[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam);
         prof_mark(c, 5);
-        k_emf<R><<<nb, 256, 0, st>>>(g, F1, Wh, E);
+        k_emf<R><<<nb, CELL_THREADS, 0, st>>>(g, F1, Wh, E);
         prof_mark(c, 6);
-        k_full<R, TU, TE><<<nb, 256, 0, st>>>(g, s, F1, E, c->dt);
+        k_full<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc);
         prof_mark(c, 7);
     } else {
         R* WM = (R*)c->WM;
         R* WP = (R*)c->WP;
         // CTU steps 1-2: traced states (+ source terms) and their fluxes
         for (int d = 0; d < 3; d++)
-            k_sweep<R, RECON, SOLVER, 2, TE><<<sweep_blocks(g, d), SWEEP_THREADS, smem, st>>>(
+            k_sweep<R, RECON, SOLVER, 2, TE><<<sweep_grid(c, d), SWEEP_THREADS, smem, st>>>(
                 g, d, W, s.b[d], F1 + (long long)d * 7 * n, WM + (long long)d * 7 * n, WP + (long long)d * 7 * n,
-                c->dt, gam);
+                c->dtc, gam);
         prof_mark(c, 2);
         // steps 3-4: edge E at t^n, dt/2 update of face B and cell state
-        k_emf<R><<<nb, 256, 0, st>>>(g, F1, W, E);
+        k_emf<R><<<nb, CELL_THREADS, 0, st>>>(g, F1, W, E);
         prof_mark(c, 3);
-        k_half<R, TU, TE><<<nb, 256, 0, st>>>(g, s, F1, E, c->dt, gam, Bh[0], Bh[1], Bh[2], Wh);
+        k_half<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2], Wh, c->sch.pfloor);
         prof_mark(c, 4);
         // steps 5-6: transverse correction and corrector fluxes
         for (int d = 0; d < 3; d++)
-            k_ctu_correct<R, SOLVER, TE><<<nb, 256, 0, st>>>(g, d, WM + (long long)d * 7 * n,
+            k_ctu_correct<R, SOLVER, TE><<<nb, CELL_THREADS, 0, st>>>(g, d, WM + (long long)d * 7 * n,
                                                               WP + (long long)d * 7 * n, W, F1, Bh[d],
-                                                              F2 + (long long)d * 7 * n, c->dt, gam);
+                                                              F2 + (long long)d * 7 * n, c->dtc, gam);
         prof_mark(c, 5);
         // steps 7-8
-        k_emf<R><<<nb, 256, 0, st>>>(g, F2, Wh, E);
+        k_emf<R><<<nb, CELL_THREADS, 0, st>>>(g, F2, Wh, E);
         prof_mark(c, 6);
-        k_full<R, TU, TE><<<nb, 256, 0, st>>>(g, s, F2, E, c->dt);
+        k_full<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F2, E, c->dtc);
         prof_mark(c, 7);
     }
     if (c->prof_on && c->prof_steps < c->prof_cap) c->prof_steps++;
@@ -150,7 +166,7 @@ void run_step(mhd_ctx* c, bool device_dt)
 template <class R, class TE, int RECON, int SOLVER, int MODE>
 inline cudaError_t allow_smem()
 {
-    size_t b = sweep_smem_bytes<R>(RECON);
+    size_t b = sweep_smem_bytes<R>(RECON, TL_MAX);
     if (MODE == 0) return cudaSuccess;
     return cudaFuncSetAttribute(k_sweep<R, RECON, SOLVER, MODE, TE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
 }

@@ -1,0 +1,404 @@
+// mhd_learned.cu -- the learned path selector: MLP, training kernels'
+// driver, block features and errors, and the selected VL step (FP32).
+#include <stdlib.h>
+#include <string.h>
+#include "mhd_engine.cuh"
+#include "mhd_learned.cuh"
+
+using namespace mhd;
+
+void mhd_internal_set_init_error(const char* msg);
+
+struct mhd_mlp {
+    cudaStream_t stream;
+    float* p;            // FP32 master parameters
+    float* mom;          // Adam moments
+    float* vel;
+    float* grad;
+    float* loss;
+    unsigned short* w1t; // bf16 operand copies
+    unsigned short* w2t;
+    unsigned short* w2n;
+    // training scratch (grown on demand)
+    long long cap;
+    uint32_t* xq;
+    uint32_t* h1q;
+    uint32_t* dh2q;
+    uint32_t* dh1q;
+    long long step;
+};
+
+static MlpDev mlp_dev(const mhd_mlp* m)
+{
+    MlpDev d;
+    d.p = m->p;
+    d.w1t = (const uint32_t*)m->w1t;
+    d.w2t = (const uint32_t*)m->w2t;
+    d.w2n = (const uint32_t*)m->w2n;
+    return d;
+}
+
+static void mlp_release(mhd_mlp* m)
+{
+    void* bufs[] = {m->p, m->mom, m->vel, m->grad, m->loss, m->w1t, m->w2t, m->w2n, m->xq, m->h1q, m->dh2q, m->dh1q};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+}
+
+// splitmix64: the seeded stream of the initial weights
+static unsigned long long splitmix64(unsigned long long& s)
+{
+    unsigned long long z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+extern "C" mhd_status mhd_mlp_create(void* stream, unsigned long long seed, mhd_mlp** out)
+{
+    if (!out) return MHD_EINVAL;
+    *out = nullptr;
+    mhd_mlp* m = (mhd_mlp*)calloc(1, sizeof(mhd_mlp));
+    if (!m) return MHD_ENOMEM;
+    m->stream = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    float** fb[] = {&m->p, &m->mom, &m->vel, &m->grad};
+    for (float** b : fb)
+        if (e == cudaSuccess) e = cudaMalloc((void**)b, NPARAM * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&m->loss, sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&m->w1t, NF * NH * 2);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&m->w2t, NH * NH * 2);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&m->w2n, NH * NH * 2);
+    if (e != cudaSuccess) {
+        mlp_release(m);
+        free(m);
+        mhd_internal_set_init_error("mhd_mlp_create: device allocation failed");
+        return MHD_ENOMEM;
+    }
+    // He-uniform weights, zero biases (seeded)
+    float* h = (float*)calloc(NPARAM, sizeof(float));
+    unsigned long long s = seed;
+    for (int i = 0; i < NPARAM; i++) {
+        float bound = 0.f;
+        if (i < P_B1) bound = sqrtf(6.f / NF);
+        else if (i >= P_W2 && i < P_B2) bound = sqrtf(6.f / NH);
+        else if (i >= P_W3 && i < P_B3) bound = sqrtf(6.f / NH);
+        double u = (double)(splitmix64(s) >> 11) * (1.0 / 9007199254740992.0);
+        h[i] = bound * (float)(2.0 * u - 1.0);
+    }
+    e = cudaMemcpyAsync(m->p, h, NPARAM * sizeof(float), cudaMemcpyHostToDevice, m->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->mom, 0, NPARAM * sizeof(float), m->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->vel, 0, NPARAM * sizeof(float), m->stream);
+    if (e == cudaSuccess) {
+        k_mlp_refresh<<<32, 256, 0, m->stream>>>(m->p, m->w1t, m->w2t, m->w2n);
+        e = cudaStreamSynchronize(m->stream);
+    }
+    free(h);
+    if (e != cudaSuccess) {
+        mlp_release(m);
+        free(m);
+        return MHD_ECUDA;
+    }
+    *out = m;
+    return MHD_OK;
+}
+
+extern "C" void mhd_mlp_free(mhd_mlp* m)
+{
+    if (!m) return;
+    cudaStreamSynchronize(m->stream);
+    mlp_release(m);
+    free(m);
+}
+
+extern "C" int mhd_mlp_nparam(void) { return NPARAM; }
+
+extern "C" mhd_status mhd_mlp_set_weights(mhd_mlp* m, const float* w, int on_device)
+{
+    if (!m || !w) return MHD_EINVAL;
+    if (cudaMemcpyAsync(m->p, w, NPARAM * sizeof(float), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        m->stream) != cudaSuccess)
+        return MHD_ECUDA;
+    cudaMemsetAsync(m->mom, 0, NPARAM * sizeof(float), m->stream);
+    cudaMemsetAsync(m->vel, 0, NPARAM * sizeof(float), m->stream);
+    m->step = 0;
+    k_mlp_refresh<<<32, 256, 0, m->stream>>>(m->p, m->w1t, m->w2t, m->w2n);
+    return cudaStreamSynchronize(m->stream) == cudaSuccess ? MHD_OK : MHD_ECUDA;
+}
+
+extern "C" mhd_status mhd_mlp_get_weights(mhd_mlp* m, float* w, int on_device)
+{
+    if (!m || !w) return MHD_EINVAL;
+    if (cudaMemcpyAsync(w, m->p, NPARAM * sizeof(float), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        m->stream) != cudaSuccess)
+        return MHD_ECUDA;
+    return cudaStreamSynchronize(m->stream) == cudaSuccess ? MHD_OK : MHD_ECUDA;
+}
+
+static mhd_status ensure_train_cap(mhd_mlp* m, long long npad)
+{
+    if (npad <= m->cap) return MHD_OK;
+    uint32_t** bufs[] = {&m->xq, &m->h1q, &m->dh2q, &m->dh1q};
+    for (uint32_t** b : bufs)
+        if (*b) { cudaFree(*b); *b = nullptr; }
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc((void**)&m->xq, npad * NF * 2);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&m->h1q, npad * NH * 2);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&m->dh2q, npad * NH * 2);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&m->dh1q, npad * NH * 2);
+    if (e != cudaSuccess) { m->cap = 0; return MHD_ENOMEM; }
+    m->cap = npad;
+    return MHD_OK;
+}
+
+// gradient of the weighted mean BCE loss over n samples into m->grad
+static mhd_status mlp_gradient(mhd_mlp* m, const float* X, const float* y, const float* wgt, long long n, double wsum,
+                               float* loss_host)
+{
+    const long long npad = (n + 15) / 16 * 16;
+    mhd_status st = ensure_train_cap(m, npad);
+    if (st != MHD_OK) return st;
+    cudaMemsetAsync(m->grad, 0, NPARAM * sizeof(float), m->stream);
+    cudaMemsetAsync(m->loss, 0, sizeof(float), m->stream);
+    const int grid = (int)((npad / 16 + 7) / 8 < 1184 ? (npad / 16 + 7) / 8 : 1184);
+    k_mlp_train_act<<<grid, 256, 0, m->stream>>>(mlp_dev(m), X, y, wgt, n, npad, (float)(1.0 / wsum), m->xq, m->h1q,
+                                                 m->dh2q, m->dh1q, m->grad, m->loss);
+    const long long nw = 56 * ((npad + 255) / 256);
+    const int grid2 = (int)((nw + 7) / 8 < 1184 ? (nw + 7) / 8 : 1184);
+    k_mlp_wgrad<<<grid2, 256, 0, m->stream>>>((const unsigned short*)m->xq, (const unsigned short*)m->h1q,
+                                              (const unsigned short*)m->dh1q, (const unsigned short*)m->dh2q, npad,
+                                              m->grad);
+    if (cudaGetLastError() != cudaSuccess) return MHD_ECUDA;
+    if (loss_host) {
+        if (cudaMemcpyAsync(loss_host, m->loss, sizeof(float), cudaMemcpyDeviceToHost, m->stream) != cudaSuccess)
+            return MHD_ECUDA;
+        if (cudaStreamSynchronize(m->stream) != cudaSuccess) return MHD_ECUDA;
+    }
+    return MHD_OK;
+}
+
+extern "C" mhd_status mhd_mlp_grad(mhd_mlp* m, const float* X, const float* y, const float* wgt, long long n,
+                                   double wsum, float* grad_out, float* loss)
+{
+    if (!m || !X || !y || n < 1 || !(wsum > 0.0) || !grad_out) return MHD_EINVAL;
+    mhd_status st = mlp_gradient(m, X, y, wgt, n, wsum, loss);
+    if (st != MHD_OK) return st;
+    if (cudaMemcpyAsync(grad_out, m->grad, NPARAM * sizeof(float), cudaMemcpyDeviceToDevice, m->stream) != cudaSuccess)
+        return MHD_ECUDA;
+    return cudaStreamSynchronize(m->stream) == cudaSuccess ? MHD_OK : MHD_ECUDA;
+}
+
+extern "C" mhd_status mhd_mlp_train_step(mhd_mlp* m, const float* X, const float* y, const float* wgt, long long n,
+                                         double wsum, double lr, float* loss)
+{
+    if (!m || !X || !y || n < 1 || !(wsum > 0.0) || !(lr > 0.0)) return MHD_EINVAL;
+    mhd_status st = mlp_gradient(m, X, y, wgt, n, wsum, nullptr);
+    if (st != MHD_OK) return st;
+    m->step++;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)m->step), c2 = 1.f - powf(b2, (float)m->step);
+    k_adam<<<32, 256, 0, m->stream>>>(m->p, m->mom, m->vel, m->grad, (float)lr, b1, b2, 1e-8f, c1, c2);
+    k_mlp_refresh<<<32, 256, 0, m->stream>>>(m->p, m->w1t, m->w2t, m->w2n);
+    if (cudaGetLastError() != cudaSuccess) return MHD_ECUDA;
+    if (loss) {
+        if (cudaMemcpyAsync(loss, m->loss, sizeof(float), cudaMemcpyDeviceToHost, m->stream) != cudaSuccess)
+            return MHD_ECUDA;
+        if (cudaStreamSynchronize(m->stream) != cudaSuccess) return MHD_ECUDA;
+    }
+    return MHD_OK;
+}
+
+extern "C" mhd_status mhd_mlp_predict(mhd_mlp* m, const float* X, long long n, float* logits)
+{
+    if (!m || !X || !logits || n < 1) return MHD_EINVAL;
+    const int grid = (int)((n / 16 + 8) / 8 < 1184 ? (n / 16 + 8) / 8 : 1184);
+    k_mlp_infer<<<grid, 256, 0, m->stream>>>(mlp_dev(m), X, n, logits, nullptr);
+    if (cudaGetLastError() != cudaSuccess) return MHD_ECUDA;
+    return cudaStreamSynchronize(m->stream) == cudaSuccess ? MHD_OK : MHD_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// block features and block errors of single-box contexts
+// ---------------------------------------------------------------------------
+static bool blockable(const mhd_ctx* c)
+{
+    return c && c->nbox == 1 && c->hbox[0].nx % 4 == 0 && c->hbox[0].ny % 4 == 0 && c->hbox[0].nz % 4 == 0;
+}
+
+extern "C" long long mhd_nblocks(mhd_ctx* c)
+{
+    if (!blockable(c)) return -1;
+    return (long long)(c->hbox[0].nx / 4) * (c->hbox[0].ny / 4) * (c->hbox[0].nz / 4);
+}
+
+static void launch_features(mhd_ctx* c, float* feats)
+{
+    const long long nblk = mhd_nblocks(c);
+    const int grid = (int)((nblk + 7) / 8 < 148 * 8 ? (nblk + 7) / 8 : 148 * 8);
+    const int nb = c->cell_grid;
+    if (c->sch.precision == MHD_FP64) {
+        k_prim<double, double, double><<<nb, CELL_THREADS, 0, c->stream>>>(c->B, state_of<double, double>(c), (double*)c->W, c->gamma, nullptr, c->bad, c->sch.pfloor);
+        k_block_features<double><<<grid, 256, 0, c->stream>>>(c->hbox[0], (const double*)c->W, c->B.N, (float)c->gamma, feats);
+    } else if (c->sch.precision == MHD_FP32) {
+        k_prim<float, float, float><<<nb, CELL_THREADS, 0, c->stream>>>(c->B, state_of<float, float>(c), (float*)c->W, c->gamma, nullptr, c->bad, c->sch.pfloor);
+        k_block_features<float><<<grid, 256, 0, c->stream>>>(c->hbox[0], (const float*)c->W, c->B.N, (float)c->gamma, feats);
+    } else {
+        k_prim<float, float, double><<<nb, CELL_THREADS, 0, c->stream>>>(c->B, state_of<float, double>(c), (float*)c->W, c->gamma, nullptr, c->bad, c->sch.pfloor);
+        k_block_features<float><<<grid, 256, 0, c->stream>>>(c->hbox[0], (const float*)c->W, c->B.N, (float)c->gamma, feats);
+    }
+}
+
+extern "C" mhd_status mhd_block_features(mhd_ctx* c, float* feats)
+{
+    if (!blockable(c) || !feats) {
+        mhd_internal_set_init_error("mhd_block_features: one box with sides divisible by 4 and a device buffer");
+        return MHD_EINVAL;
+    }
+    launch_features(c, feats);
+    if (cudaGetLastError() != cudaSuccess) return MHD_ECUDA;
+    return cudaStreamSynchronize(c->stream) == cudaSuccess ? MHD_OK : MHD_ECUDA;
+}
+
+extern "C" mhd_status mhd_block_error(mhd_ctx* a, mhd_ctx* b, float* err)
+{
+    if (!blockable(a) || !blockable(b) || !err || a->sch.precision != b->sch.precision ||
+        a->hbox[0].nx != b->hbox[0].nx || a->hbox[0].ny != b->hbox[0].ny || a->hbox[0].nz != b->hbox[0].nz) {
+        mhd_internal_set_init_error("mhd_block_error: two single-box contexts of one shape and precision");
+        return MHD_EINVAL;
+    }
+    const long long nblk = mhd_nblocks(a);
+    const int grid = (int)((nblk + 7) / 8 < 148 * 8 ? (nblk + 7) / 8 : 148 * 8);
+    cudaStreamSynchronize(b->stream);
+    switch (a->sch.precision) {
+        case MHD_FP64: k_block_err<double, double><<<grid, 256, 0, a->stream>>>(a->hbox[0], state_of<double, double>(a), state_of<double, double>(b), (float)a->gamma, err); break;
+        case MHD_FP32: k_block_err<float, float><<<grid, 256, 0, a->stream>>>(a->hbox[0], state_of<float, float>(a), state_of<float, float>(b), (float)a->gamma, err); break;
+        default:       k_block_err<float, double><<<grid, 256, 0, a->stream>>>(a->hbox[0], state_of<float, double>(a), state_of<float, double>(b), (float)a->gamma, err); break;
+    }
+    if (cudaGetLastError() != cudaSuccess) return MHD_ECUDA;
+    return cudaStreamSynchronize(a->stream) == cudaSuccess ? MHD_OK : MHD_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// the selected step: features -> MLP -> flags -> tile lists -> cheap (PLM in
+// primitives + HLLE) and full (characteristic PPM + HLLD) sweeps
+// ---------------------------------------------------------------------------
+static void run_step_learned(mhd_ctx* c, bool device_dt)
+{
+    typedef float R;
+    const Boxes g = c->B;
+    const long long n = g.N;
+    const int nb = c->cell_grid;
+    cudaStream_t st = c->stream;
+    StateP<float, float> s = state_of<float, float>(c);
+    R* W = (R*)c->W;
+    R* Wh = (R*)c->Wh;
+    R* F1 = (R*)c->F1;
+    R* E = (R*)c->E;
+    float* Bh[3] = {(float*)c->Bh[0], (float*)c->Bh[1], (float*)c->Bh[2]};
+    const double gam = c->gamma;
+    const long long nblk = mhd_nblocks(c);
+    const size_t smem = sweep_smem_bytes<R>(PPM, g.tl);
+
+    prof_mark(c, 0);
+    k_prim<R, float, float><<<nb, CELL_THREADS, 0, st>>>(g, s, W, gam, device_dt ? c->smax_part : nullptr, c->bad,
+                                                         c->sch.pfloor, c->nfloor);
+    if (device_dt) k_finalize_dt<<<c->nbox, 256, 0, st>>>(g, c->smax_part, c->sch.cfl, c->dt, c->smax, c->dtc);
+    // selector: features of the current state, one inference, tile lists
+    const int fgrid = (int)((nblk + 7) / 8 < 148 * 8 ? (nblk + 7) / 8 : 148 * 8);
+    k_block_features<R><<<fgrid, 256, 0, st>>>(c->hbox[0], W, n, (float)gam, c->sel_feats);
+    const int igrid = (int)((nblk / 16 + 8) / 8 < 1184 ? (nblk / 16 + 8) / 8 : 1184);
+    k_mlp_infer<<<igrid, 256, 0, st>>>(mlp_dev(c->sel), c->sel_feats, nblk, nullptr, c->sel_flags);
+    cudaMemsetAsync(c->sel_cnt, 0, 6 * sizeof(int), st);
+    for (int d = 0; d < 3; d++)
+        k_tile_classify<<<(g.ntile[d] + 255) / 256, 256, 0, st>>>(c->hbox[0], d, g.tl, c->sel_flags,
+                                                                   c->sel_list[2 * d], c->sel_cnt + 2 * d,
+                                                                   c->sel_list[2 * d + 1], c->sel_cnt + 2 * d + 1,
+                                                                   g.ntile[d]);
+    prof_mark(c, 1);
+    // VL steps 1-3
+    for (int d = 0; d < 3; d++) {
+        k_sweep<R, PLM_PRIM, HLLE, 0, float><<<sweep_grid(c, d), SWEEP_THREADS, 0, st>>>(
+            g, d, W, s.b[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam, c->sel_list[2 * d], c->sel_cnt + 2 * d);
+        k_sweep<R, PPM, HLLD, 0, float><<<sweep_grid(c, d), SWEEP_THREADS, 0, st>>>(
+            g, d, W, s.b[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam, c->sel_list[2 * d + 1],
+            c->sel_cnt + 2 * d + 1);
+    }
+    prof_mark(c, 2);
+    k_emf<R><<<nb, CELL_THREADS, 0, st>>>(g, F1, W, E);
+    prof_mark(c, 3);
+    k_half<R, float, float><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2], Wh, c->sch.pfloor);
+    prof_mark(c, 4);
+    // VL steps 4-7
+    for (int d = 0; d < 3; d++) {
+        k_sweep<R, PLM_PRIM, HLLE, 1, float><<<sweep_grid(c, d), SWEEP_THREADS, sweep_smem_bytes<R>(PLM_PRIM, g.tl), st>>>(
+            g, d, Wh, Bh[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam, c->sel_list[2 * d], c->sel_cnt + 2 * d);
+        k_sweep<R, PPM, HLLD, 1, float><<<sweep_grid(c, d), SWEEP_THREADS, smem, st>>>(
+            g, d, Wh, Bh[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam, c->sel_list[2 * d + 1],
+            c->sel_cnt + 2 * d + 1);
+    }
+    prof_mark(c, 5);
+    k_emf<R><<<nb, CELL_THREADS, 0, st>>>(g, F1, Wh, E);
+    prof_mark(c, 6);
+    k_full<R, float, float><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc);
+    prof_mark(c, 7);
+    if (c->prof_on && c->prof_steps < c->prof_cap) c->prof_steps++;
+}
+
+extern "C" mhd_status mhd_set_selector(mhd_ctx* c, mhd_mlp* m)
+{
+    if (!c) return MHD_EINVAL;
+    if (!m) {   // back to the plain scheme
+        c->sel = nullptr;
+        c->step = c->plain_step;
+        c->launches = 12;
+        if (c->have_graph) { cudaGraphExecDestroy(c->gexec); c->have_graph = false; }
+        return MHD_OK;
+    }
+    if (!blockable(c) || c->sch.precision != MHD_FP32 || c->sch.integrator != MHD_VL) {
+        snprintf(c->err, sizeof(c->err), "the selector needs one FP32 VL box with sides divisible by 4");
+        return MHD_EUNSUPPORTED;
+    }
+    if (!c->sel_feats) {
+        const long long nblk = mhd_nblocks(c);
+        int ntmax = 0;
+        for (int d = 0; d < 3; d++) {
+            // the tile counts of the largest tile length bound every layout
+            int nt = tiles_of_box(c->hbox[0].nx, c->hbox[0].ny, c->hbox[0].nz, d, 4);
+            ntmax = nt > ntmax ? nt : ntmax;
+        }
+        cudaError_t e = cudaMalloc((void**)&c->sel_feats, nblk * NF * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&c->sel_flags, nblk);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&c->sel_cnt, 6 * sizeof(int));
+        for (int q = 0; q < 6 && e == cudaSuccess; q++) e = cudaMalloc((void**)&c->sel_list[q], (size_t)ntmax * sizeof(int));
+        if (e != cudaSuccess) return MHD_ENOMEM;
+        c->bytes += nblk * (NF * 4 + 1) + 24 + 6LL * ntmax * 4;
+        cudaFuncSetAttribute(k_sweep<float, PPM, HLLD, 1, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sweep_smem_bytes<float>(PPM, TL_MAX));
+    }
+    c->sel = m;
+    c->step = run_step_learned;
+    c->launches = 12 + 3 + 3 + 6;   // + features, MLP, 3 tile lists, 6 sweeps of the other path
+    if (c->have_graph) { cudaGraphExecDestroy(c->gexec); c->have_graph = false; }
+    return MHD_OK;
+}
+
+// fraction of 4^3 blocks and of sweep tiles the last selected step ran cheap
+extern "C" mhd_status mhd_selector_stats(mhd_ctx* c, double* frac_blocks, double* frac_tiles)
+{
+    if (!c || !c->sel || !frac_blocks || !frac_tiles) return MHD_EINVAL;
+    const long long nblk = mhd_nblocks(c);
+    unsigned char* f = (unsigned char*)malloc((size_t)nblk);
+    int cnt[6];
+    if (!f) return MHD_ENOMEM;
+    cudaError_t e = cudaMemcpyAsync(f, c->sel_flags, nblk, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, c->sel_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) { free(f); return MHD_ECUDA; }
+    long long cheap = 0;
+    for (long long i = 0; i < nblk; i++) cheap += f[i] == 0;
+    free(f);
+    *frac_blocks = (double)cheap / (double)nblk;
+    long long tc = cnt[0] + cnt[2] + cnt[4], tf = cnt[1] + cnt[3] + cnt[5];
+    *frac_tiles = tc + tf > 0 ? (double)tc / (double)(tc + tf) : 0.0;
+    return MHD_OK;
+}

@@ -16,9 +16,11 @@ using namespace mhd;
 
 void mhd_internal_set_init_error(const char* msg);   // defined with the other entry points
 
-// per cell: W (8) + Wh (8) + fluxes (21) + edge E (3) + half-step faces (3)
+// per cell: W (8) + Wh (8) + fluxes (21) + edge E (3) + half-step faces (3);
+// then dt, the CFL word, the flag word and the one-entry box table
 static constexpr size_t kDoublesPerCell = 43;
-static constexpr size_t kScratchBytes = kDoublesPerCell * MHD_NOALLOC_MAX_CELLS * sizeof(double) + 256;
+static constexpr size_t kScratchBytes = kDoublesPerCell * MHD_NOALLOC_MAX_CELLS * sizeof(double) + 1024;
+static_assert(sizeof(mhd::BoxDev) <= 256 && sizeof(mhd::DtBox) <= 256, "tables must fit the slack");
 
 // Every GPU that loads this library holds this array until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -81,7 +83,7 @@ extern "C" mhd_status mhd_step_noalloc(const mhd_grid* grid, double gamma, const
     c.sch = *scheme;
     c.gamma = gamma;
     c.stream = (cudaStream_t)stream;
-    c.g.nx = grid->nx; c.g.ny = grid->ny; c.g.nz = grid->nz; c.g.n = n; c.g.dx = grid->dx;
+    c.nbox = 1;
     c.szu = c.sze = c.szr = sizeof(double);
     double* u = (double*)U;
     double* b = (double*)B;
@@ -96,16 +98,44 @@ extern "C" mhd_status mhd_step_noalloc(const mhd_grid* grid, double gamma, const
     c.E = s + 37 * n;
     for (int d = 0; d < 3; d++) c.Bh[d] = s + (40 + d) * n;
     c.dt = s + 43 * n;
-    c.smax = (unsigned long long*)(s + 43 * n + 1);
+    c.smax = nullptr;          // steps with the caller's dt: no CFL reduction
+    c.smax_part = nullptr;
+    c.nfloor = nullptr;
     c.bad = (unsigned long long*)(s + 43 * n + 2);
-    c.nblk = (int)((n + 255) / 256 < 148 * 16 ? (n + 255) / 256 : 148 * 16);
+    // the one-entry box table lives in the array too, 64-byte aligned
+    size_t tab = ((43 * (size_t)n + 3) * sizeof(double) + 63) / 64 * 64;
+    BoxDev* dbox = (BoxDev*)(base + tab);
+    c.dtc = (DtBox*)(base + tab + 256);
+    BoxDev hb;
+    memset(&hb, 0, sizeof(hb));
+    hb.nx = grid->nx; hb.ny = grid->ny; hb.nz = grid->nz;
+    hb.n = n;
+    hb.dx = grid->dx;
+    hb.inv_dx = (float)(1.0 / grid->dx);
+    const int tl = 8;
+    hb.tile0[0] = hb.tile0[1] = hb.tile0[2] = 0;
+    c.B.b = dbox;
+    c.B.nbox = 1;
+    c.B.tl = tl;
+    c.B.N = n;
+    c.B.nvblk = (n + CELL_THREADS - 1) / CELL_THREADS;
+    for (int d = 0; d < 3; d++) c.B.ntile[d] = tiles_of_box(hb.nx, hb.ny, hb.nz, d, tl);
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return reject(MHD_ECUDA, "mhd_step_noalloc: device query failed");
+    c.nsm = nsm;
+    c.sweep_bps = 4;
+    c.cell_grid = (int)(c.B.nvblk < 16LL * nsm ? c.B.nvblk : 16LL * nsm);
+    // pageable source: the copy has read it by the time the call returns
+    if (cudaMemcpyAsync(dbox, &hb, sizeof(hb), cudaMemcpyHostToDevice, c.stream) != cudaSuccess)
+        return reject(MHD_ECUDA, "mhd_step_noalloc: box table copy failed");
     cudaError_t attr = cudaSuccess;
     c.step = mhd_pick_fp64(scheme->integrator, scheme->recon, scheme->riemann, &attr);
     if (!c.step || attr != cudaSuccess) return reject(MHD_ECUDA, "mhd_step_noalloc: kernel set-up failed");
     // the array keeps the previous call's contents: reset the flag word
     if (cudaMemsetAsync(c.bad, 0xff, sizeof(unsigned long long), c.stream) != cudaSuccess)
         return reject(MHD_ECUDA, "mhd_step_noalloc: cudaMemsetAsync failed");
-    k_set_dt<<<1, 1, 0, c.stream>>>(c.dt, dt);
+    k_set_dt<<<1, 32, 0, c.stream>>>(c.B, c.dt, dt, c.dtc);
     c.step(&c, false);
     e = cudaGetLastError();
     if (e != cudaSuccess) return reject(MHD_ECUDA, cudaGetErrorString(e));

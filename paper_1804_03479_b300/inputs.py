@@ -256,18 +256,18 @@ def abc_blasts(n=384, kmult=3, beta=0.1, nblast=10, E=1.0, radius=0.05, gamma=5.
     dx = st.dx
     rng = np.random.default_rng(seed + 1000)
     sites = rng.uniform(0.0, 1.0, size=(nblast, 3))
-    xc = (np.arange(n) + 0.5) * dx
-    Z, Y, X = np.meshgrid(xc, xc, xc, indexing="ij")
     W_P = np.zeros((n, n, n))
+    m = int(np.ceil(radius / dx)) + 1
     for s in sites:
-        d2 = 0.0
-        for coord, c0 in ((X, s[0]), (Y, s[1]), (Z, s[2])):
-            dd = (coord - c0 + 0.5) % 1.0 - 0.5
-            d2 = d2 + dd * dd
+        # cells of the periodic cube around the site; their centre offsets
+        idx = [np.arange(int(np.floor(c / dx)) - m, int(np.floor(c / dx)) + m + 1) for c in s]
+        off = [((ix + 0.5) * dx - c + 0.5) % 1.0 - 0.5 for ix, c in zip(idx, s)]
+        d2 = off[2][:, None, None] ** 2 + off[1][None, :, None] ** 2 + off[0][None, None, :] ** 2
         mask = d2 < radius * radius
         vol = mask.sum() * dx ** 3
         if vol > 0:
-            W_P[mask] += (gamma - 1.0) * E / vol
+            kk, jj, ii = np.nonzero(mask)
+            np.add.at(W_P, (idx[2][kk] % n, idx[1][jj] % n, idx[0][ii] % n), (gamma - 1.0) * E / vol)
     # add to the total energy: e += dP / (gamma - 1)
     st.U[4] += W_P / (gamma - 1.0)
     st.meta.update(kind="abc_blasts", sites=sites.tolist(), E=E, radius=radius)

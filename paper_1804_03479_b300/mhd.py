@@ -27,7 +27,12 @@ PRECISIONS = {"fp64": 0, "fp32": 1, "mixed": 2}
 EXPORTS = ["mhd_init", "mhd_set_state", "mhd_get_state", "mhd_cfl_dt", "mhd_step", "mhd_advance",
            "mhd_last_dt", "mhd_divB", "mhd_sums", "mhd_sync", "mhd_bad_cell", "mhd_clear_error",
            "mhd_last_error", "mhd_device_bytes", "mhd_launches_per_step", "mhd_free",
-           "mhd_profile_begin", "mhd_profile_end", "mhd_step_noalloc"]
+           "mhd_profile_begin", "mhd_profile_end", "mhd_step_noalloc", "mhd_init_batch", "mhd_nbox",
+           "mhd_set_state_box", "mhd_get_state_box", "mhd_step_boxes", "mhd_set_sweep_config",
+           "mhd_get_sweep_config", "mhd_autotune", "mhd_mlp_create", "mhd_mlp_free", "mhd_mlp_nparam",
+           "mhd_mlp_set_weights", "mhd_mlp_get_weights", "mhd_mlp_grad", "mhd_mlp_train_step",
+           "mhd_mlp_predict", "mhd_nblocks", "mhd_block_features", "mhd_block_error", "mhd_set_selector",
+           "mhd_selector_stats", "mhd_floor_count"]
 GROUPS = ["prim_cfl", "predictor_sweeps", "emf1", "half_update", "corrector_sweeps", "emf2", "full_update"]
 
 
@@ -43,7 +48,7 @@ class Grid(ctypes.Structure):
 
 class Scheme(ctypes.Structure):
     _fields_ = [("integrator", ctypes.c_int), ("recon", ctypes.c_int), ("riemann", ctypes.c_int),
-                ("precision", ctypes.c_int), ("cfl", ctypes.c_double)]
+                ("precision", ctypes.c_int), ("cfl", ctypes.c_double), ("pfloor", ctypes.c_double)]
 
 
 _lib = None
@@ -68,6 +73,8 @@ def lib():
     L.mhd_divB.argtypes = [vp, dp, dp]
     L.mhd_sums.argtypes = [vp, dp]
     L.mhd_sync.argtypes = [vp]
+    L.mhd_floor_count.argtypes = [vp]
+    L.mhd_floor_count.restype = ctypes.c_longlong
     L.mhd_bad_cell.argtypes = [vp]
     L.mhd_bad_cell.restype = ctypes.c_longlong
     L.mhd_clear_error.argtypes = [vp]
@@ -82,11 +89,51 @@ def lib():
     L.mhd_step_noalloc.argtypes = [ctypes.POINTER(Grid), ctypes.c_double, ctypes.POINTER(Scheme), ctypes.c_double,
                                    vp, vp, vp]
     L.mhd_step_noalloc.restype = ctypes.c_int
+    L.mhd_init_batch.argtypes = [ip, ctypes.POINTER(Grid), ctypes.c_double, ctypes.POINTER(Scheme), vp,
+                                 ctypes.POINTER(vp)]
+    L.mhd_nbox.argtypes = [vp]
+    L.mhd_nbox.restype = ip
+    L.mhd_set_state_box.argtypes = [vp, ip, vp, vp, ip]
+    L.mhd_get_state_box.argtypes = [vp, ip, vp, vp, ip]
+    L.mhd_step_boxes.argtypes = [vp, dp]
+    L.mhd_set_sweep_config.argtypes = [vp, ip, ip]
+    L.mhd_get_sweep_config.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip)]
+    L.mhd_autotune.argtypes = [vp, ip, ctypes.POINTER(ip), ctypes.POINTER(ip), dp]
+    for name in ["mhd_init_batch", "mhd_set_state_box", "mhd_get_state_box", "mhd_step_boxes",
+                 "mhd_set_sweep_config", "mhd_get_sweep_config", "mhd_autotune"]:
+        getattr(L, name).restype = ctypes.c_int
+    ll = ctypes.c_longlong
+    fp = ctypes.c_void_p
+    L.mhd_mlp_create.argtypes = [vp, ctypes.c_ulonglong, ctypes.POINTER(vp)]
+    L.mhd_mlp_free.argtypes = [vp]
+    L.mhd_mlp_free.restype = None
+    L.mhd_mlp_nparam.argtypes = []
+    L.mhd_mlp_nparam.restype = ip
+    L.mhd_mlp_set_weights.argtypes = [vp, fp, ip]
+    L.mhd_mlp_get_weights.argtypes = [vp, fp, ip]
+    L.mhd_mlp_grad.argtypes = [vp, fp, fp, fp, ll, ctypes.c_double, fp, ctypes.POINTER(ctypes.c_float)]
+    L.mhd_mlp_train_step.argtypes = [vp, fp, fp, fp, ll, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_float)]
+    L.mhd_mlp_predict.argtypes = [vp, fp, ll, fp]
+    L.mhd_nblocks.argtypes = [vp]
+    L.mhd_nblocks.restype = ll
+    L.mhd_block_features.argtypes = [vp, fp]
+    L.mhd_block_error.argtypes = [vp, vp, fp]
+    L.mhd_set_selector.argtypes = [vp, vp]
+    L.mhd_selector_stats.argtypes = [vp, dp, dp]
+    for name in ["mhd_mlp_create", "mhd_mlp_set_weights", "mhd_mlp_get_weights", "mhd_mlp_grad",
+                 "mhd_mlp_train_step", "mhd_mlp_predict", "mhd_block_features", "mhd_block_error",
+                 "mhd_set_selector", "mhd_selector_stats"]:
+        getattr(L, name).restype = ctypes.c_int
     L.mhd_profile_begin.argtypes = [vp, ip]
     L.mhd_profile_end.argtypes = [vp, dp, ip, ctypes.POINTER(ctypes.c_int)]
     for name in ["mhd_init", "mhd_set_state", "mhd_get_state", "mhd_cfl_dt", "mhd_step", "mhd_advance",
                  "mhd_last_dt", "mhd_divB", "mhd_sums", "mhd_sync", "mhd_launches_per_step",
-                 "mhd_profile_begin", "mhd_profile_end", "mhd_step_noalloc"]:
+                 "mhd_profile_begin", "mhd_profile_end", "mhd_step_noalloc", "mhd_init_batch", "mhd_nbox",
+           "mhd_set_state_box", "mhd_get_state_box", "mhd_step_boxes", "mhd_set_sweep_config",
+           "mhd_get_sweep_config", "mhd_autotune", "mhd_mlp_create", "mhd_mlp_free", "mhd_mlp_nparam",
+           "mhd_mlp_set_weights", "mhd_mlp_get_weights", "mhd_mlp_grad", "mhd_mlp_train_step",
+           "mhd_mlp_predict", "mhd_nblocks", "mhd_block_features", "mhd_block_error", "mhd_set_selector",
+           "mhd_selector_stats", "mhd_floor_count"]:
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -112,7 +159,7 @@ def step_noalloc(U, B, dx, dt, gamma=5.0 / 3.0, recon="plm", riemann="roe", stre
     overlap on the GPU share that array and race: serialise them."""
     nz, ny, nx = U.shape[1:]
     g = Grid(nx, ny, nz, dx)
-    s = Scheme(INTEGRATORS["vl"], RECONS[recon], SOLVERS[riemann], PRECISIONS["fp64"], 0.3)
+    s = Scheme(INTEGRATORS["vl"], RECONS[recon], SOLVERS[riemann], PRECISIONS["fp64"], 0.3, 0.0)
     pu, du = _ptr(U)
     pb, db = _ptr(B)
     if not (du and db):
@@ -124,17 +171,24 @@ def step_noalloc(U, B, dx, dt, gamma=5.0 / 3.0, recon="plm", riemann="roe", stre
 
 
 class Solver:
-    """One periodic box advanced by the library (one mhd_ctx)."""
+    """Periodic boxes advanced by the library (one mhd_ctx).  `shape` is one
+    box (nz, ny, nx); `shapes` a list of boxes for a batch (each (nz, ny, nx),
+    all with the same dx unless `dxs` is given)."""
 
     def __init__(self, shape, dx, gamma=5.0 / 3.0, integrator="vl", recon="plm", riemann="roe",
-                 precision="fp64", cfl=0.3, stream=None):
-        self.nz, self.ny, self.nx = shape if len(shape) == 3 else shape[-3:]
+                 precision="fp64", cfl=0.3, stream=None, shapes=None, dxs=None, pfloor=0.0):
+        shapes = [tuple(shape[-3:])] if shapes is None else [tuple(x) for x in shapes]
+        dxs = [dx] * len(shapes) if dxs is None else list(dxs)
+        self.shapes = shapes
+        self.nbox = len(shapes)
+        self.nz, self.ny, self.nx = shapes[0]
         self.precision = precision
         self.dtype = np.float32 if precision == "fp32" else np.float64
-        g = Grid(self.nx, self.ny, self.nz, dx)
-        s = Scheme(INTEGRATORS[integrator], RECONS[recon], SOLVERS[riemann], PRECISIONS[precision], cfl)
+        grids = (Grid * self.nbox)(*[Grid(sh[2], sh[1], sh[0], d) for sh, d in zip(shapes, dxs)])
+        s = Scheme(INTEGRATORS[integrator], RECONS[recon], SOLVERS[riemann], PRECISIONS[precision], cfl, pfloor)
         h = ctypes.c_void_p()
-        st = lib().mhd_init(ctypes.byref(g), gamma, ctypes.byref(s), ctypes.c_void_p(stream or 0), ctypes.byref(h))
+        st = lib().mhd_init_batch(self.nbox, grids, gamma, ctypes.byref(s), ctypes.c_void_p(stream or 0),
+                                  ctypes.byref(h))
         if st != MHD_OK:
             raise MHDError(st, lib().mhd_last_error(None).decode())
         self.h = h
@@ -144,49 +198,86 @@ class Solver:
         if st != MHD_OK:
             raise MHDError(st, lib().mhd_last_error(self.h).decode())
 
-    def set_state(self, U, B):
+    def set_state(self, U, B, box=0):
         pu, du = _ptr(U)
         pb, db = _ptr(B)
         assert du == db
-        self._check(lib().mhd_set_state(self.h, ctypes.c_void_p(pu), ctypes.c_void_p(pb), du))
+        self._check(lib().mhd_set_state_box(self.h, box, ctypes.c_void_p(pu), ctypes.c_void_p(pb), du))
 
-    def get_state(self, U=None, B=None):
+    def get_state(self, U=None, B=None, box=0):
         if U is None:
-            U = np.empty((5, self.nz, self.ny, self.nx), self.dtype)
-            B = np.empty((3, self.nz, self.ny, self.nx), self.dtype)
+            nz, ny, nx = self.shapes[box]
+            U = np.empty((5, nz, ny, nx), self.dtype)
+            B = np.empty((3, nz, ny, nx), self.dtype)
         pu, du = _ptr(U)
         pb, db = _ptr(B)
-        self._check(lib().mhd_get_state(self.h, ctypes.c_void_p(pu), ctypes.c_void_p(pb), du))
+        self._check(lib().mhd_get_state_box(self.h, box, ctypes.c_void_p(pu), ctypes.c_void_p(pb), du))
         return U, B
 
+    def cfl_dts(self):
+        dt = (ctypes.c_double * self.nbox)()
+        self._check(lib().mhd_cfl_dt(self.h, dt))
+        return np.array(dt[:])
+
     def cfl_dt(self):
-        dt = ctypes.c_double()
-        self._check(lib().mhd_cfl_dt(self.h, ctypes.byref(dt)))
-        return dt.value
+        return float(self.cfl_dts()[0])
 
     def step(self, dt):
-        self._check(lib().mhd_step(self.h, dt))
+        if np.ndim(dt) == 0:
+            self._check(lib().mhd_step(self.h, float(dt)))
+        else:
+            arr = (ctypes.c_double * self.nbox)(*[float(x) for x in dt])
+            self._check(lib().mhd_step_boxes(self.h, arr))
 
     def advance(self, nsteps, use_graph=False):
         self._check(lib().mhd_advance(self.h, nsteps, int(use_graph)))
 
+    def last_dts(self):
+        dt = (ctypes.c_double * self.nbox)()
+        self._check(lib().mhd_last_dt(self.h, dt))
+        return np.array(dt[:])
+
     def last_dt(self):
-        dt = ctypes.c_double()
-        self._check(lib().mhd_last_dt(self.h, ctypes.byref(dt)))
-        return dt.value
+        return float(self.last_dts()[0])
+
+    def divBs(self):
+        m = (ctypes.c_double * self.nbox)()
+        r = (ctypes.c_double * self.nbox)()
+        self._check(lib().mhd_divB(self.h, m, r))
+        return np.array(m[:]), np.array(r[:])
 
     def divB(self):
-        m, r = ctypes.c_double(), ctypes.c_double()
-        self._check(lib().mhd_divB(self.h, ctypes.byref(m), ctypes.byref(r)))
-        return m.value, r.value
+        m, r = self.divBs()
+        return float(m[0]), float(r[0])
+
+    def sums_boxes(self):
+        out = (ctypes.c_double * (8 * self.nbox))()
+        self._check(lib().mhd_sums(self.h, out))
+        return np.array(out[:]).reshape(self.nbox, 8)
 
     def sums(self):
-        out = (ctypes.c_double * 8)()
-        self._check(lib().mhd_sums(self.h, out))
-        return np.array(out[:])
+        return self.sums_boxes()[0]
+
+    def set_sweep_config(self, tile_len, blocks_per_sm):
+        self._check(lib().mhd_set_sweep_config(self.h, tile_len, blocks_per_sm))
+
+    def sweep_config(self):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        self._check(lib().mhd_get_sweep_config(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def autotune(self, reps=2):
+        """time every sweep tiling on this batch, keep the fastest;
+        returns (tile_len, blocks_per_sm, ms per step)"""
+        a, b, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        self._check(lib().mhd_autotune(self.h, reps, ctypes.byref(a), ctypes.byref(b), ctypes.byref(ms)))
+        return a.value, b.value, ms.value
 
     def sync(self):
         self._check(lib().mhd_sync(self.h))
+
+    def floor_count(self):
+        return int(lib().mhd_floor_count(self.h))
 
     def bad_cell(self):
         return lib().mhd_bad_cell(self.h)
@@ -210,9 +301,115 @@ class Solver:
         self._check(lib().mhd_profile_end(self.h, ms, 7, ctypes.byref(steps)))
         return dict(zip(GROUPS, ms[:])), steps.value
 
+    # --- learned path selector -------------------------------------------
+    def nblocks(self):
+        return int(lib().mhd_nblocks(self.h))
+
+    def block_features(self, out=None):
+        """features of every 4^3 block of the current state (torch CUDA [nblocks, 48])"""
+        import torch
+        if out is None:
+            out = torch.empty((self.nblocks(), 48), dtype=torch.float32, device="cuda")
+        st = lib().mhd_block_features(self.h, ctypes.c_void_p(out.data_ptr()))
+        if st != MHD_OK:
+            raise MHDError(st, lib().mhd_last_error(None).decode())
+        return out
+
+    def set_selector(self, mlp):
+        self._check(lib().mhd_set_selector(self.h, mlp.h if mlp is not None else None))
+        self._selector = mlp
+
+    def selector_stats(self):
+        """fractions of 4^3 blocks and of sweep tiles the last step ran cheap"""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        self._check(lib().mhd_selector_stats(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
     def free(self):
         if getattr(self, "h", None):
             lib().mhd_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def block_error(a, b, out=None):
+    """per 4^3 block, max over the stored fields of mean |a - b| / scale (torch CUDA)"""
+    import torch
+    if out is None:
+        out = torch.empty(a.nblocks(), dtype=torch.float32, device="cuda")
+    st = lib().mhd_block_error(a.h, b.h, ctypes.c_void_p(out.data_ptr()))
+    if st != MHD_OK:
+        raise MHDError(st, lib().mhd_last_error(None).decode())
+    return out
+
+
+class MLP:
+    """The selector network 48 -> 64 -> 64 -> 1 (BF16 tensor-core kernels).
+    Parameters are packed FP32: W1[48][64], b1[64], W2[64][64], b2[64], w3[64], b3."""
+
+    def __init__(self, seed=0, stream=None):
+        h = ctypes.c_void_p()
+        st = lib().mhd_mlp_create(ctypes.c_void_p(stream or 0), seed, ctypes.byref(h))
+        if st != MHD_OK:
+            raise MHDError(st, lib().mhd_last_error(None).decode())
+        self.h = h
+        self.nparam = int(lib().mhd_mlp_nparam())
+
+    def set_weights(self, w):
+        w = np.ascontiguousarray(np.asarray(w, dtype=np.float32))
+        assert w.size == self.nparam
+        st = lib().mhd_mlp_set_weights(self.h, ctypes.c_void_p(w.ctypes.data), 0)
+        if st != MHD_OK:
+            raise MHDError(st, "mhd_mlp_set_weights")
+
+    def weights(self):
+        w = np.empty(self.nparam, np.float32)
+        st = lib().mhd_mlp_get_weights(self.h, ctypes.c_void_p(w.ctypes.data), 0)
+        if st != MHD_OK:
+            raise MHDError(st, "mhd_mlp_get_weights")
+        return w
+
+    @staticmethod
+    def _ptr(t):
+        return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+    def grad(self, X, y, wgt=None):
+        """gradient of the weighted mean BCE loss (torch CUDA tensors in and out)"""
+        import torch
+        g = torch.empty(self.nparam, dtype=torch.float32, device="cuda")
+        loss = ctypes.c_float()
+        wsum = float(wgt.sum().item()) if wgt is not None else float(X.shape[0])
+        st = lib().mhd_mlp_grad(self.h, self._ptr(X), self._ptr(y), self._ptr(wgt), X.shape[0], wsum,
+                                self._ptr(g), ctypes.byref(loss))
+        if st != MHD_OK:
+            raise MHDError(st, "mhd_mlp_grad")
+        return g, loss.value
+
+    def train_step(self, X, y, wgt=None, lr=1e-3, want_loss=False):
+        loss = ctypes.c_float()
+        wsum = float(wgt.sum().item()) if wgt is not None else float(X.shape[0])
+        st = lib().mhd_mlp_train_step(self.h, self._ptr(X), self._ptr(y), self._ptr(wgt), X.shape[0], wsum, lr,
+                                      ctypes.byref(loss) if want_loss else None)
+        if st != MHD_OK:
+            raise MHDError(st, "mhd_mlp_train_step")
+        return loss.value if want_loss else None
+
+    def predict(self, X):
+        import torch
+        out = torch.empty(X.shape[0], dtype=torch.float32, device="cuda")
+        st = lib().mhd_mlp_predict(self.h, self._ptr(X), X.shape[0], self._ptr(out))
+        if st != MHD_OK:
+            raise MHDError(st, "mhd_mlp_predict")
+        return out
+
+    def free(self):
+        if getattr(self, "h", None):
+            lib().mhd_mlp_free(self.h)
             self.h = None
 
     def __del__(self):
