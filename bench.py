@@ -36,10 +36,19 @@ UNIT = "cell-updates/s"
 PAPER_P100 = {"fp32": 1.2e8, "fp64": 5.5e7}   # Sec. 5.2 (i), Tesla P100, VL + PLM + Roe
 GROUPS = ["prim_cfl", "predictor_sweeps", "emf1", "half_update", "corrector_sweeps", "emf2", "full_update"]
 SIZES = {"fp64": (8, 8, 8), "fp32": (4, 4, 4), "mixed": (4, 8, 4)}   # (rho/M, e/B, arithmetic) bytes
-# FP32/FP64 floating-point operations per face of one corrector sweep launch
-# (reconstruction + Riemann solve), counted by ncu on the 64^3 workload; see
-# profiles/.  None: not counted yet.
-FLOPS_PER_FACE = {}
+# Algorithmic floating-point operations per face of one corrector sweep launch
+# (one cell's reconstruction and one Riemann solve): the FADD + FMUL + 2 FFMA
+# count that ncu reports for the FP32 build at 160^3 (mean of the x and y
+# launches: 1251.1 and 1232.7), where every divide and square root is a single
+# MUFU op.  The same algorithm runs in the FP64 build, which expands divides
+# and square roots into FMA iterations (2394 executed FP64 flops per face at
+# 128^3), so the algorithmic figure is used for all precisions.
+FLOPS_PER_FACE = {"fp32": 1242.0, "fp64": 1242.0, "mixed": 1242.0}
+# DRAM bytes (read + write) per face of one corrector sweep launch, from
+# dram__bytes_read.sum + dram__bytes_write.sum of the same captures
+# (FP32: 238.2 MB per launch at 160^3; FP64: 237.8 MB per launch at 128^3),
+# scaled to other sizes by the number of faces.
+TRAFFIC_PER_FACE = {"fp32": 58.15, "fp64": 113.4}
 
 
 def peaks():
@@ -163,30 +172,50 @@ def time_variant(torch, mhd, st, prec, scheme, K, W, dist, stream, profile=True)
     return ms, groups, rec, s
 
 
+def group_bytes(prec, n):
+    """algorithmic HBM bytes of each kernel group of one VL step on n cells:
+    every array element a kernel needs is read once and every result written
+    once (neighbour re-reads assumed to hit in cache)"""
+    szu, sze, szr = SIZES[prec]
+    u = 4 * szu + 4 * sze          # rho, M (TU) and e, B faces (TE)
+    sweep = 8 * szr + sze + 7 * szr    # W and B_n in, 7 flux components out
+    emf = (9 + 6 + 3) * szr        # F_rho and the two E fluxes of 3 axes, v and B_cc, E out
+    return {"prim_cfl": n * (u + 8 * szr), "predictor_sweeps": 3 * n * sweep, "emf1": n * emf,
+            "half_update": n * (u + 18 * szr + 3 * sze + 8 * szr), "corrector_sweeps": 3 * n * sweep,
+            "emf2": n * emf, "full_update": n * (2 * u + 18 * szr)}
+
+
+def step_hbm(prec, n, ms_per_step, pk):
+    """the whole step against the HBM roofline: algorithmic bytes per cell
+    update (sum over the kernel groups) x cell updates / step time"""
+    bpc = sum(group_bytes(prec, n).values()) / n
+    gbs = bpc * n / (ms_per_step * 1e-3) / 1e9
+    return {"bytes_per_cell_update": bpc, "achieved_gbs": gbs, "peak_gbs": pk["hbm_gbs"],
+            "frac": gbs / pk["hbm_gbs"], "peak_src": pk["src"]}
+
+
 def roofline(prec, groups, steps, n, pk, sm_mhz):
     """dominant kernel group and its achieved fraction of the roofline that bounds it"""
     dom = max(groups, key=groups.get)
     ms = groups[dom] / steps
-    szu, sze, szr = SIZES[prec]
-    # algorithmic bytes of one sweep launch per face: read the 8 primitives
-    # of the cell and its face B_n, write 7 flux components
-    sweep_bytes = 3 * n * (15 * szr + sze)
+    gb = group_bytes(prec, n)
     out = {"kernel": dom, "ms_per_step": ms, "share": groups[dom] / sum(groups.values())}
     fpf = FLOPS_PER_FACE.get(prec)
     if dom.endswith("sweeps") and fpf:
         flops = 3 * n * fpf
         ach = flops / (ms * 1e-3) / 1e12
         peak = alu_peak_tflops(prec, sm_mhz)
+        tpf = TRAFFIC_PER_FACE.get(prec)
+        hbm = gb[dom] / (ms * 1e-3) / 1e9
         out.update(bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
-                   peak_src=f"derived from unit counts at {sm_mhz:.0f} MHz", traffic=None,
-                   algorithmic=f"{fpf} flops per face x 3 axes x {n} faces")
+                   peak_src=f"{'FP64' if prec == 'fp64' else 'FP32'} peak derived from unit counts at {sm_mhz:.0f} MHz",
+                   traffic=(tpf * n if tpf else None),
+                   algorithmic=f"{fpf:.0f} flops per face x {n} faces per launch, 3 launches",
+                   launches=3, ms_per_launch=ms / 3,
+                   hbm_view={"algorithmic_bytes_per_launch": gb[dom] // 3, "achieved_gbs": hbm,
+                             "frac_of_measured": hbm / pk["hbm_gbs"]})
     else:
-        if dom.endswith("sweeps"):
-            b = sweep_bytes
-        elif dom == "full_update":
-            b = n * (2 * (4 * szu + 4 * sze) + 21 * szr + 3 * szr)
-        else:
-            b = n * 8 * (szu + szr)
+        b = gb[dom]
         ach = b / (ms * 1e-3) / 1e9
         out.update(bound="hbm", achieved=ach, peak=pk["hbm_gbs"], unit="GB/s", frac=ach / pk["hbm_gbs"],
                    peak_src=pk["src"], traffic=None, algorithmic_bytes_per_launch_group=b)
@@ -442,7 +471,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=256)
@@ -503,6 +532,7 @@ def main():
                    "l2": "state larger than L2 (no flush)", "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
                    "device_bytes": dev_bytes},
         "roofline": roofline(args.precision, groups, rec, n, pk, sm_mhz) if rec else None,
+        "hbm_roofline_step": step_hbm(args.precision, n, ms / args.steps, pk),
         "kernel_ms_per_step": {k: v / rec for k, v in groups.items()} if rec else None,
         "gpu_launches": launches,
         "clocks": clocks,
@@ -516,7 +546,8 @@ def main():
             vv = n * kv / (msv * 1e-3)
             variants[prec] = {"value": vv, "unit": UNIT, "ms_per_step": msv / kv, "steps": kv,
                               "vs_p100_paper": vv / PAPER_P100[prec] if prec in PAPER_P100 else None,
-                              "roofline": roofline(prec, gv, recv, n, pk, sm_mhz) if recv else None}
+                              "roofline": roofline(prec, gv, recv, n, pk, sm_mhz) if recv else None,
+                              "hbm_roofline_step": step_hbm(prec, n, msv / kv, pk)}
         if not args.no_batch:
             variants["batch48"] = batch_variant(torch, mhd, max(3, min(args.steps, 10)), stream)
         if not args.no_learned:
