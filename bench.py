@@ -185,13 +185,42 @@ def group_bytes(prec, n):
             "emf2": n * emf, "full_update": n * (2 * u + 18 * szr)}
 
 
+# state bytes per cell update when the state is read once and written once
+# (rho, M in the arithmetic type of the form; e and the face B in FP64 for MIXED)
+STATE_BYTES = {"fp64": 128, "fp32": 64, "mixed": 96}
+
+
 def step_hbm(prec, n, ms_per_step, pk):
-    """the whole step against the HBM roofline: algorithmic bytes per cell
-    update (sum over the kernel groups) x cell updates / step time"""
+    """the whole step against the HBM roofline, two ways: (1) the state read
+    once and written once (the ceiling of a fully fused step), (2) the
+    algorithmic bytes of this multi-kernel step (sum over the kernel groups)"""
     bpc = sum(group_bytes(prec, n).values()) / n
     gbs = bpc * n / (ms_per_step * 1e-3) / 1e9
-    return {"bytes_per_cell_update": bpc, "achieved_gbs": gbs, "peak_gbs": pk["hbm_gbs"],
+    cups = n / (ms_per_step * 1e-3)
+    ceil = pk["hbm_gbs"] * 1e9 / STATE_BYTES[prec]
+    return {"state_bytes_per_cell_update": STATE_BYTES[prec], "state_roofline_cell_updates_per_s": ceil,
+            "frac_of_state_roofline": cups / ceil,
+            "step_bytes_per_cell_update": bpc, "step_achieved_gbs": gbs, "peak_gbs": pk["hbm_gbs"],
             "frac": gbs / pk["hbm_gbs"], "peak_src": pk["src"]}
+
+
+def scheme_matrix(torch, mhd, st, steps, stream, pk):
+    """{CTU, VL} x {PLM, PPM} x {HLLD, Roe} x {FP64, FP32} on the same box"""
+    n = int(np.prod(st.U.shape[1:]))
+    out = {}
+    for prec in ("fp32", "fp64"):
+        k = steps if prec == "fp32" else max(2, steps // 4)
+        for integ in ("ctu", "vl"):
+            for recon in ("plm", "ppm"):
+                for riem in ("hlld", "roe"):
+                    ms, _, _, s = time_variant(torch, mhd, st, prec, (integ, recon, riem), k, 2, None, stream,
+                                               profile=False)
+                    s.free()
+                    v = n * k / (ms * 1e-3)
+                    out[f"{integ}+{recon}+{riem}/{prec}"] = {
+                        "value": v, "ms_per_step": ms / k, "steps": k,
+                        "frac_of_state_roofline": v * STATE_BYTES[prec] / (pk["hbm_gbs"] * 1e9)}
+    return out
 
 
 def roofline(prec, groups, steps, n, pk, sm_mhz):
@@ -222,6 +251,16 @@ def roofline(prec, groups, steps, n, pk, sm_mhz):
     return out
 
 
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def cpu_baseline(scheme, target_s=12.0):
     """the FP64 oracle as it stands, all host cores, on a 64^3 sample"""
     from oracle import oracle as O
@@ -239,7 +278,7 @@ def cpu_baseline(scheme, target_s=12.0):
         O.step(U, B, st.dx, st.gamma, dt, integ, recon, riemann)
     el = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": 64 ** 3 * m / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+    return {"value": 64 ** 3 * m / el, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
             "sample": f"64^3 ABC (k=4pi, beta=0.5, seed 0), {m} steps of {integ}+{recon}+{riemann} FP64 "
                       f"incl. the CFL dt, OpenMP on all host threads"}
 
@@ -396,7 +435,10 @@ def run_stress(args):
     MIXED and FP32 forms (VL + PLM + Roe) advance the same initial state with
     one dt sequence (the FP64 run's CFL dt each step); reported: relative L1
     per field of MIXED and FP32 against FP64 (the FP64 path matches the CPU
-    oracle to 1e-12 per step) and max |div B| dx / B_rms of each form."""
+    oracle to 1e-12 per step) and max |div B| dx / B_rms of each form.  The
+    thermal pressure is below the loop's magnetic cross term, and the FP64
+    scheme itself reaches P < 0 within a step, so every form runs with the
+    same pressure floor (--stress-pfloor) and reports its floored cell-steps."""
     import torch
     from paper_1804_03479_b300 import build as Bld
     Bld.build()
@@ -405,10 +447,12 @@ def run_stress(args):
     torch.cuda.set_device(0)
     nx, ny, nz = args.stress_shape
     st = I.current_loop(nx, ny, nz)
+    pf = args.stress_pfloor
     forms = {}
     for prec in ("fp64", "mixed", "fp32"):
         cast = torch.float32 if prec == "fp32" else torch.float64
-        s = mhd.Solver(st.U.shape[1:], st.dx, st.gamma, args.integrator, args.recon, args.riemann, prec, 0.3)
+        s = mhd.Solver(st.U.shape[1:], st.dx, st.gamma, args.integrator, args.recon, args.riemann, prec, 0.3,
+                       pfloor=pf)
         s.set_state(torch.from_numpy(st.U).to("cuda", cast), torch.from_numpy(st.B).to("cuda", cast))
         forms[prec] = s
     t0 = time.perf_counter()
@@ -425,7 +469,8 @@ def run_stress(args):
     for prec, s in forms.items():
         U, B = s.get_state()
         m, r = s.divB()
-        entry = {"max_divB_dx_over_Brms": m / r}
+        entry = {"max_divB_dx_over_Brms": m / r, "floored_cell_steps": s.floor_count(),
+                 "finite": bool(np.all(np.isfinite(U)) and np.all(np.isfinite(B)))}
         if prec != "fp64":
             l1 = [float(np.abs(U[f].astype(np.float64) - ref[0][f]).sum() / np.abs(ref[0][f]).sum()) for f in range(5)]
             l1 += [float(np.abs(B[d].astype(np.float64) - ref[1][d]).sum() / np.abs(ref[1][d]).sum()) for d in range(3)]
@@ -434,7 +479,7 @@ def run_stress(args):
         s.free()
     line = {"mode": "precision_stress", "workload": f"current loop on low-beta ABC, {nx}x{ny}x{nz}, beta=1e-3, v=(2,2,2)",
             "scheme": f"{args.integrator}+{args.recon}+{args.riemann}", "steps": args.stress_steps, "wall_s": wall,
-            "forms": out}
+            "pfloor": pf, "cells": nx * ny * nz, "forms": out}
     print(json.dumps(line), flush=True)
 
 
@@ -463,7 +508,8 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "abc256_k4pi_beta0.5 (64^3 sample per step)", "scheme": "+".join(scheme)},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
+                             "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -483,10 +529,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-matrix", action="store_true", help="skip the 16 scheme x precision combinations")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--stress", action="store_true", help="mixed-precision stress run (not a bench line)")
     ap.add_argument("--stress-steps", type=int, default=500)
     ap.add_argument("--stress-shape", type=int, nargs=3, default=[512, 256, 256])
+    ap.add_argument("--stress-pfloor", type=float, default=1e-5)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -548,6 +596,8 @@ def main():
                               "vs_p100_paper": vv / PAPER_P100[prec] if prec in PAPER_P100 else None,
                               "roofline": roofline(prec, gv, recv, n, pk, sm_mhz) if recv else None,
                               "hbm_roofline_step": step_hbm(prec, n, msv / kv, pk)}
+        if not args.no_matrix:
+            variants["schemes256"] = scheme_matrix(torch, mhd, st, max(3, min(args.steps, 10)), stream, pk)
         if not args.no_batch:
             variants["batch48"] = batch_variant(torch, mhd, max(3, min(args.steps, 10)), stream)
         if not args.no_learned:

@@ -31,6 +31,7 @@ typedef struct {
     int nx, ny, nz;
     long n;
     double dx, gam;
+    double pfloor;   /* pressure floor, 0 = none (see prim_floor) */
 } grid_t;
 
 static long cidx(const grid_t *g, int i, int j, int k)
@@ -538,10 +539,16 @@ void orc_recon_cell(int recon, int trace, const double *w5flat, const double bn5
 
 /* cell-centred primitives (rho, vx, vy, vz, P, Bx, By, Bz) from U and the   */
 /* face B; B at the cell centre is the mean of its two faces (Fig. 1).       */
-static void prim_all(const grid_t *g, const double *U, const double *B, double *W)
+/* With a pressure floor (g->pfloor > 0, not part of the paper's scheme; the  */
+/* option used for blast and low-beta stress states) P below the floor is     */
+/* replaced by the floor; when e_raise is given (the energy array U + 4n, at  */
+/* the start of a step) the total energy of such a cell is raised by         */
+/* (pfloor - P)/(gamma - 1) so that the state carries P = pfloor.  Returns     */
+/* the number of floored cells.                                               */
+static long prim_floor(const grid_t *g, const double *U, const double *B, double *W, double *e_raise)
 {
-    long n = g->n;
-#pragma omp parallel for schedule(static)
+    long n = g->n, cnt = 0;
+#pragma omp parallel for schedule(static) reduction(+:cnt)
     for (long c = 0; c < n; c++) {
         double rho = U[c];
         double vx = U[n + c] / rho, vy = U[2 * n + c] / rho, vz = U[3 * n + c] / rho;
@@ -550,9 +557,22 @@ static void prim_all(const grid_t *g, const double *U, const double *B, double *
         double bz = 0.5 * (B[2 * n + c] + B[2 * n + shift(g, c, 2, 1)]);
         double p = (g->gam - 1.0) * (U[4 * n + c] - 0.5 * rho * (vx * vx + vy * vy + vz * vz)
                                      - 0.5 * (bx * bx + by * by + bz * bz));
+        if (g->pfloor > 0.0 && p < g->pfloor) {
+            if (e_raise) {
+                e_raise[c] = e_raise[c] + (g->pfloor - p) / (g->gam - 1.0);
+                cnt++;
+            }
+            p = g->pfloor;
+        }
         W[c] = rho; W[n + c] = vx; W[2 * n + c] = vy; W[3 * n + c] = vz;
         W[4 * n + c] = p; W[5 * n + c] = bx; W[6 * n + c] = by; W[7 * n + c] = bz;
     }
+    return cnt;
+}
+
+static void prim_all(const grid_t *g, const double *U, const double *B, double *W)
+{
+    prim_floor(g, U, B, W, NULL);
 }
 
 /* sweep-frame primitive vector of cell c for a sweep along d */
@@ -709,7 +729,7 @@ static long fluxes(const grid_t *g, int recon, int riemann, int first_order, int
 /* ------------------------------------------------------------------------ */
 /* One step of the VL scheme (Sec. 3.2, VL steps 1-7).                       */
 /* ------------------------------------------------------------------------ */
-static long step_vl(const grid_t *g, int recon, int riemann, double dt, double *U, double *B)
+static long step_vl(const grid_t *g, int recon, int riemann, double dt, double *U, double *B, long *nfloor)
 {
     long n = g->n;
     double *W = malloc(sizeof(double) * 8 * n);
@@ -719,7 +739,7 @@ static long step_vl(const grid_t *g, int recon, int riemann, double dt, double *
     double *Bh = malloc(sizeof(double) * 3 * n);
     long nfb = 0;
     /* steps 1-3: first-order fluxes with face B_n, edge E, half update */
-    prim_all(g, U, B, W);
+    *nfloor += prim_floor(g, U, B, W, U + 4 * n);
     nfb += fluxes(g, recon, riemann, 1, 0, dt, W, B, F, NULL, NULL);
     edge_emf(g, F, W, E);
     fv_update(g, 0.5 * dt, U, F, Uh);
@@ -737,7 +757,7 @@ static long step_vl(const grid_t *g, int recon, int riemann, double dt, double *
 /* ------------------------------------------------------------------------ */
 /* One step of the CTU scheme (Sec. 3.2, CTU steps 1-8).                     */
 /* ------------------------------------------------------------------------ */
-static long step_ctu(const grid_t *g, int recon, int riemann, double dt, double *U, double *B)
+static long step_ctu(const grid_t *g, int recon, int riemann, double dt, double *U, double *B, long *nfloor)
 {
     long n = g->n;
     double gam = g->gam;
@@ -752,7 +772,7 @@ static long step_ctu(const grid_t *g, int recon, int riemann, double dt, double 
     long nfb = 0;
     double hdt = 0.5 * dt;
     /* step 1: traced face states at t+dt/2 along every axis */
-    prim_all(g, U, B, W);
+    *nfloor += prim_floor(g, U, B, W, U + 4 * n);
     {
         /* fill WM/WP via the reconstruction pass, then add the source terms  */
         /* the 1-D system leaves out when dB_n/dn != 0: in primitive form     */
@@ -873,19 +893,31 @@ static long step_ctu(const grid_t *g, int recon, int riemann, double dt, double 
 /* Exported whole-grid entry points                                          */
 /* ------------------------------------------------------------------------ */
 
+/* advance U, B in place by dt with a pressure floor (0 = none); returns the */
+/* number of Roe->HLLE fallbacks, the floored cells in *nfloor               */
+long orc_step_floor(int nx, int ny, int nz, double dx, double gam, int integrator, int recon, int riemann,
+                    double dt, double pfloor, double *U, double *B, long *nfloor)
+{
+    grid_t g = {nx, ny, nz, (long)nx * ny * nz, dx, gam, pfloor};
+    *nfloor = 0;
+    if (integrator == CTU) return step_ctu(&g, recon, riemann, dt, U, B, nfloor);
+    return step_vl(&g, recon, riemann, dt, U, B, nfloor);
+}
+
 /* advance U, B in place by dt; returns the number of Roe->HLLE fallbacks */
 long orc_step(int nx, int ny, int nz, double dx, double gam, int integrator, int recon, int riemann,
               double dt, double *U, double *B)
 {
-    grid_t g = {nx, ny, nz, (long)nx * ny * nz, dx, gam};
-    if (integrator == CTU) return step_ctu(&g, recon, riemann, dt, U, B);
-    return step_vl(&g, recon, riemann, dt, U, B);
+    long nf = 0;
+    return orc_step_floor(nx, ny, nz, dx, gam, integrator, recon, riemann, dt, 0.0, U, B, &nf);
 }
 
-/* CFL time step (Sec. 3.2): cfl * dx / max over cells and axes of |v_d| + c_f,d */
-double orc_cfl_dt(int nx, int ny, int nz, double dx, double gam, double cfl, const double *U, const double *B)
+/* CFL time step (Sec. 3.2): cfl * dx / max over cells and axes of |v_d| + c_f,d, */
+/* with the pressure floor of the step applied to P (0 = none)                    */
+double orc_cfl_dt_floor(int nx, int ny, int nz, double dx, double gam, double cfl, double pfloor, const double *U,
+                        const double *B)
 {
-    grid_t g = {nx, ny, nz, (long)nx * ny * nz, dx, gam};
+    grid_t g = {nx, ny, nz, (long)nx * ny * nz, dx, gam, pfloor};
     long n = g.n;
     double *W = malloc(sizeof(double) * 8 * n);
     prim_all(&g, U, B, W);
@@ -902,6 +934,11 @@ double orc_cfl_dt(int nx, int ny, int nz, double dx, double gam, double cfl, con
     }
     free(W);
     return cfl * dx / smax;
+}
+
+double orc_cfl_dt(int nx, int ny, int nz, double dx, double gam, double cfl, const double *U, const double *B)
+{
+    return orc_cfl_dt_floor(nx, ny, nz, dx, gam, cfl, 0.0, U, B);
 }
 
 /* Eq. 16 times dx: max_c |sum_d (B_d(c+e_d) - B_d(c))|, and B_rms of the     */

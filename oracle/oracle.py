@@ -48,6 +48,11 @@ def lib():
         L.orc_step.restype = ctypes.c_long
         L.orc_step.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [ctypes.c_int] * 3 + \
                               [ctypes.c_double, dp, dp]
+        L.orc_step_floor.restype = ctypes.c_long
+        L.orc_step_floor.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [ctypes.c_int] * 3 + \
+                                    [ctypes.c_double, ctypes.c_double, dp, dp, ctypes.POINTER(ctypes.c_long)]
+        L.orc_cfl_dt_floor.restype = ctypes.c_double
+        L.orc_cfl_dt_floor.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double] * 4 + [dp, dp]
         L.orc_cfl_dt.restype = ctypes.c_double
         L.orc_cfl_dt.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double] * 3 + [dp, dp]
         L.orc_divB.restype = None
@@ -88,8 +93,24 @@ def step(U: np.ndarray, B: np.ndarray, dx: float, gamma: float, dt: float,
                               SOLVERS[riemann], dt, _p(U), _p(B)))
 
 
-def cfl_dt(U, B, dx, gamma, cfl) -> float:
+def step_floor(U: np.ndarray, B: np.ndarray, dx: float, gamma: float, dt: float,
+               integrator="vl", recon="plm", riemann="roe", pfloor=0.0) -> tuple[int, int]:
+    """step() with a pressure floor: cells whose P falls below pfloor at the
+    start of the step get their energy raised to P = pfloor, and every
+    primitive pass uses max(P, pfloor).  Returns (Roe->HLLE fallbacks,
+    floored cells)."""
     nz, ny, nx = U.shape[1:]
+    assert U.shape == (5, nz, ny, nx) and B.shape == (3, nz, ny, nx)
+    nf = ctypes.c_long(0)
+    fb = lib().orc_step_floor(nx, ny, nz, dx, gamma, INTEGRATORS[integrator], RECONS[recon], SOLVERS[riemann],
+                              dt, pfloor, _p(U), _p(B), ctypes.byref(nf))
+    return int(fb), int(nf.value)
+
+
+def cfl_dt(U, B, dx, gamma, cfl, pfloor=0.0) -> float:
+    nz, ny, nx = U.shape[1:]
+    if pfloor > 0.0:
+        return float(lib().orc_cfl_dt_floor(nx, ny, nz, dx, gamma, cfl, pfloor, _p(U), _p(B)))
     return float(lib().orc_cfl_dt(nx, ny, nz, dx, gamma, cfl, _p(U), _p(B)))
 
 

@@ -231,3 +231,42 @@ def test_cfl_closed_forms():
     ca = 1.5 / math.sqrt(2.0)
     smax = max(max(a, ca), math.sqrt(a * a + ca * ca))
     assert math.isclose(orc.cfl_dt(st.U, st.B, st.dx, g, 0.3), 0.3 * st.dx / smax, rel_tol=1e-14)
+
+
+def test_pressure_floor_raises_energy_only():
+    """The optional pressure floor (used for the blast and low-beta stress
+    states; not part of the paper's scheme): with pfloor = 0 the floored step
+    is the plain step bit for bit; with a floor, exactly the cells whose P is
+    below it at the start of the step are counted, and the step conserves
+    mass, momentum and face B as before while the energy sum grows by the
+    raise sum_c (pfloor - P_c)/(gamma - 1)."""
+    st = I.abc(16, kmult=1, beta=1.0, seed=3)
+    U, B = st.U.copy(), st.B.copy()
+    W0 = orc.prim(U, B, st.gamma)
+    # lower the energy of a few cells so that their pressure is below the floor
+    cells = [(1, 2, 3), (7, 7, 7), (15, 0, 9), (4, 11, 2)]
+    for (k, j, i) in cells:
+        U[4, k, j, i] -= (W0[4, k, j, i] + 0.05) / (st.gamma - 1.0)
+    pf = 0.02
+    W1 = orc.prim(U, B, st.gamma)
+    low = W1[4] < pf
+    assert int(low.sum()) == len(cells)
+    raise_sum = float(((pf - W1[4][low]) / (st.gamma - 1.0)).sum())
+    dt = orc.cfl_dt(U, B, st.dx, st.gamma, 0.3, pfloor=pf)
+    assert dt > 0 and math.isfinite(dt)
+    Ua, Ba = U.copy(), B.copy()
+    Ub, Bb = U.copy(), B.copy()
+    orc.step(Ua, Ba, st.dx, st.gamma, dt, "vl", "plm", "hlld")
+    fb, nf = orc.step_floor(Ub, Bb, st.dx, st.gamma, dt, "vl", "plm", "hlld", pfloor=0.0)
+    assert nf == 0 and np.array_equal(Ua, Ub) and np.array_equal(Ba, Bb)
+    s0 = orc.sums(U, B)
+    Uc, Bc = U.copy(), B.copy()
+    fb, nf = orc.step_floor(Uc, Bc, st.dx, st.gamma, dt, "vl", "plm", "hlld", pfloor=pf)
+    assert nf == len(cells)
+    s1 = orc.sums(Uc, Bc)
+    scale = np.abs(U).reshape(5, -1).sum(axis=1)
+    for f in (0, 1, 2, 3):
+        assert abs(s1[f] - s0[f]) <= 1e-13 * scale[f] + 1e-13
+    assert abs(s1[4] - (s0[4] + raise_sum)) <= 1e-12 * scale[4]
+    for d in range(3):
+        assert abs(s1[5 + d] - s0[5 + d]) <= 1e-13 * np.abs(B[d]).sum()
