@@ -981,3 +981,69 @@ void orc_prim(int nx, int ny, int nz, double gam, const double *U, const double 
     grid_t g = {nx, ny, nz, (long)nx * ny * nz, 1.0, gam};
     prim_all(&g, U, B, W);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Diagnostics of Sec. 4.3 / 4.5: current density J = curl B on the cell    */
+/* edges (Stokes' theorem on the four faces around an edge), and the         */
+/* energy integrals E_T, U_B, U_V of Sec. 4.5.                               */
+/* ------------------------------------------------------------------------ */
+
+/* dx times J on the edges: J_x at (i, j-1/2, k-1/2), J_y at (i-1/2, j,       */
+/* k-1/2), J_z at (i-1/2, j-1/2, k), the layout of the edge E fields:         */
+/*   dx J_a = (B_c(c) - B_c(c - e_b)) - (B_b(c) - B_b(c - e_c)),  b = a+1, c = a+2 */
+void orc_edge_current(int nx, int ny, int nz, const double *B, double *J)
+{
+    grid_t g = {nx, ny, nz, (long)nx * ny * nz, 1.0, 0.0};
+    long n = g.n;
+    for (long c = 0; c < n; c++) {
+        for (int a = 0; a < 3; a++) {
+            int b = (a + 1) % 3, cc = (a + 2) % 3;
+            J[a * n + c] = (B[cc * n + c] - B[cc * n + shift(&g, c, b, -1)])
+                         - (B[b * n + c] - B[b * n + shift(&g, c, cc, -1)]);
+        }
+    }
+}
+
+/* out[0] E_T   = sum e dx^3                                                  */
+/* out[1] U_B   = sum over faces B_f^2/2 dx^3 (the face-based magnetic energy) */
+/* out[2] U_V   = sum |M|^2/(2 rho) dx^3                                      */
+/* out[3] max over cells of dx |J_cc| / |B_cc|; J_cc the mean of the four     */
+/*        edges of the cell along each axis, B_cc the mean of its two faces    */
+/* out[4] number of cells with dx |J_cc| / |B_cc| > thr (the refinement test  */
+/*        |J|/|B| > thr/dx of Sec. 4.3 and 4.5)                                */
+/* out[5] max over cells of |J_cc|                                            */
+void orc_energies(int nx, int ny, int nz, double dx, const double *U, const double *B, double thr, double out[6])
+{
+    grid_t g = {nx, ny, nz, (long)nx * ny * nz, dx, 0.0};
+    long n = g.n;
+    double *J = malloc(sizeof(double) * 3 * n);
+    orc_edge_current(nx, ny, nz, B, J);
+    double et = 0.0, ub = 0.0, uv = 0.0, rmax = 0.0, jmax = 0.0, cnt = 0.0;
+    for (long c = 0; c < n; c++) {
+        et += U[4 * n + c];
+        double m2 = U[n + c] * U[n + c] + U[2 * n + c] * U[2 * n + c] + U[3 * n + c] * U[3 * n + c];
+        uv += 0.5 * m2 / U[c];
+        double jc[3], bc[3];
+        for (int a = 0; a < 3; a++) {
+            int b = (a + 1) % 3, cc = (a + 2) % 3;
+            ub += 0.5 * B[a * n + c] * B[a * n + c];
+            long cb = shift(&g, c, b, 1), ccc = shift(&g, c, cc, 1), cbc = shift(&g, cb, cc, 1);
+            jc[a] = 0.25 * (J[a * n + c] + J[a * n + cb] + J[a * n + ccc] + J[a * n + cbc]);
+            bc[a] = 0.5 * (B[a * n + c] + B[a * n + shift(&g, c, a, 1)]);
+        }
+        double jm = sqrt(jc[0] * jc[0] + jc[1] * jc[1] + jc[2] * jc[2]);
+        double bm = sqrt(bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]);
+        double r = jm / bm;
+        if (r > rmax) rmax = r;
+        if (r > thr) cnt += 1.0;
+        if (jm > jmax) jmax = jm;
+    }
+    free(J);
+    double v = dx * dx * dx;
+    out[0] = et * v;
+    out[1] = ub * v;
+    out[2] = uv * v;
+    out[3] = rmax;
+    out[4] = cnt;
+    out[5] = jmax / dx;
+}

@@ -71,6 +71,10 @@ def lib():
         L.orc_flux_phys.argtypes = [dp, ctypes.c_double, ctypes.c_double, dp]
         L.orc_recon_cell.restype = None
         L.orc_recon_cell.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double, dp, dp]
+        L.orc_edge_current.restype = None
+        L.orc_edge_current.argtypes = [ctypes.c_int] * 3 + [dp, dp]
+        L.orc_energies.restype = None
+        L.orc_energies.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double, dp, dp, ctypes.c_double, dp]
         _lib = L
     return _lib
 
@@ -166,3 +170,19 @@ def recon_cell(recon, w5, bn5, gamma, trace=False, dtdx=0.0):
     wm = np.zeros(7); wp = np.zeros(7)
     lib().orc_recon_cell(RECONS[recon], int(trace), _p(w5), _p(bn5), gamma, dtdx, _p(wm), _p(wp))
     return wm, wp
+
+
+def edge_current(B) -> np.ndarray:
+    """dx J on the cell edges (layout of the edge E fields)."""
+    nz, ny, nx = B.shape[1:]
+    J = np.zeros((3, nz, ny, nx))
+    lib().orc_edge_current(nx, ny, nz, _p(B), _p(J))
+    return J
+
+
+def energies(U, B, dx, thr) -> dict:
+    """E_T, U_B (face-based), U_V, max dx|J|/|B|, cells above thr, max |J|."""
+    nz, ny, nx = U.shape[1:]
+    out = np.zeros(6)
+    lib().orc_energies(nx, ny, nz, dx, _p(U), _p(B), thr, _p(out))
+    return dict(E_T=out[0], U_B=out[1], U_V=out[2], jb_max=out[3], n_above=int(out[4]), j_max=out[5])

@@ -120,6 +120,124 @@ def abc(n, kmult=1, beta=1.0, gamma=5.0 / 3.0, noise=1e-3, seed=0, L=1.0, shape=
                  dict(kind="abc", k=k, A=a, P0=P0, beta=beta, seed=seed, noise=noise))
 
 
+# Fourier modes of the unstable n = 1 perturbation of the ABC state (Eqs. 21-23):
+# wave vector in units of 2 pi / L, then the cos and sin amplitude vectors
+# (x, y, z components) in units of 1e-2 of the field amplitude.
+ABC_EIGENMODE = (
+    ((1, 1, 0), (2.37, -2.37, -3.23), (2.10, -2.10, 3.66)),
+    ((1, 0, 1), (-3.48, -4.90, 3.48), (-3.18, 5.37, 3.18)),
+    ((0, -1, 1), (-5.86, 3.60, 3.60), (5.60, 3.80, 3.80)),
+    ((1, 0, -1), (2.08, -3.00, 2.08), (1.94, 3.22, 1.94)),
+)
+
+
+def _sinc(u):
+    return np.where(np.abs(u) < 1e-300, 1.0, np.sin(u) / np.where(np.abs(u) < 1e-300, 1.0, u))
+
+
+def abc_eigenmode_potential(nx, ny, nz, dx, amp, L=1.0):
+    """Edge averages of a vector potential of the perturbation of Eqs. 21-23,
+    scaled by amp (the paper's 1e-2 sqrt(P0) is amp = 1e-2 A at its beta = 1).
+
+    Every mode a cos(k.x) + b sin(k.x) has k.a = k.b = 0, so it is the curl of
+    (a x k) sin(k.x)/|k|^2 - (b x k) cos(k.x)/|k|^2.  The average of
+    sin(k.x) along an edge of length dx in direction d is its midpoint value
+    times sinc(k_d dx / 2).
+    """
+    xc, yc, zc, xf, yf, zf = _coords(nx, ny, nz, dx)
+    pts = [np.meshgrid(zf, yf, xc, indexing="ij"),      # x-edges (z, y, x)
+           np.meshgrid(zf, yc, xf, indexing="ij"),      # y-edges
+           np.meshgrid(zc, yf, xf, indexing="ij")]      # z-edges
+    A = [np.zeros((nz, ny, nx)) for _ in range(3)]
+    for kv, a, b in ABC_EIGENMODE:
+        k = 2.0 * math.pi / L * np.array(kv, dtype=float)
+        k2 = float(k @ k)
+        a = amp * 1e-2 * np.array(a)
+        b = amp * 1e-2 * np.array(b)
+        ca = np.cross(a, k) / k2
+        cb = np.cross(b, k) / k2
+        for d in range(3):
+            Z, Y, X = pts[d]
+            ph = k[0] * X + k[1] * Y + k[2] * Z
+            w = float(_sinc(0.5 * k[d] * dx))
+            A[d] += w * (ca[d] * np.sin(ph) - cb[d] * np.cos(ph))
+    return A[0], A[1], A[2]
+
+
+def abc_perturbed(n, kmult=2, beta=1.0, gamma=5.0 / 3.0, amp=None, drift=True, noise=0.0, seed=0, L=1.0):
+    """The ABC relaxation run's initial state (Sec. 4.5): the n = kmult ABC
+    field plus the perturbation of Eqs. 21-23 (amplitude 1e-2 of the field
+    amplitude A by default), and a uniform drift along the box diagonal of
+    magnitude c_s / (8 sqrt(gamma)) when drift is true."""
+    a = 1.0 / math.sqrt(3.0)
+    dx = L / n
+    k = 2.0 * math.pi * kmult / L
+    P0 = beta * a * a
+    Ax, Ay, Az = abc_potential(n, n, n, dx, k, a, a, a)
+    px, py, pz = abc_eigenmode_potential(n, n, n, dx, a if amp is None else amp, L)
+    B = curl_edges(Ax + px, Ay + py, Az + pz, dx)
+    cs = math.sqrt(gamma * P0)
+    v0 = cs / (8.0 * math.sqrt(gamma)) / math.sqrt(3.0) if drift else 0.0
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal((3, n, n, n)) * (noise * cs) + v0
+    U = conserved(np.ones((n, n, n)), v[0], v[1], v[2], np.full((n, n, n), P0), B, gamma)
+    return State(U, np.ascontiguousarray(B), dx, gamma,
+                 dict(kind="abc_perturbed", k=k, A=a, P0=P0, beta=beta, drift=v0, seed=seed))
+
+
+def _rotation_to_z(bhat):
+    """rotation about the axis x + y = 0, z = 0 (direction (1, -1, 0)/sqrt 2)
+    that takes the unit vector bhat (whose x-y projection lies along
+    (1, 1, 0)) onto z"""
+    u = np.array([1.0, -1.0, 0.0]) / math.sqrt(2.0)
+    th = math.acos(max(-1.0, min(1.0, float(bhat[2]))))
+    K = np.array([[0, -u[2], u[1]], [u[2], 0, -u[0]], [-u[1], u[0], 0]])
+    best = None
+    for ang in (th, -th):
+        R = np.eye(3) + math.sin(ang) * K + (1.0 - math.cos(ang)) * (K @ K)
+        err = float(np.abs(R @ bhat - np.array([0.0, 0.0, 1.0])).max())
+        if best is None or err < best[0]:
+            best = (err, R)
+    return best[1]
+
+
+def mhd_blast(n, r0=0.05, theta0=90.0, phi0=45.0, beta_amb=0.2, P_in=1.0, ratio=1e-2, rho0=1.0,
+              gamma=5.0 / 3.0, density_noise=False, L=1.0):
+    """Magnetised blast (Sec. 4.4): a static sphere of radius r0 at the box
+    centre with pressure P_in in an ambient medium of pressure ratio * P_in,
+    uniform density rho0, and a uniform field B0 along (cos phi0 sin theta0,
+    sin phi0 sin theta0, cos theta0) with ambient beta = 2 P_amb / B0^2.
+    With density_noise, the density inside 1.5 r0 carries the perturbation
+    of Eq. 19 in coordinates rotated so that B is along z' (no pressure
+    perturbation).  The paper takes r0, rho0, P and B0 from a reference it
+    cites; these defaults keep its beta and its pressure contrast."""
+    dx = L / n
+    xc = (np.arange(n) + 0.5) * dx
+    Z, Y, X = np.meshgrid(xc, xc, xc, indexing="ij")
+    c = 0.5 * L
+    dX, dY, dZ = X - c, Y - c, Z - c
+    r = np.sqrt(dX * dX + dY * dY + dZ * dZ)
+    P_amb = ratio * P_in
+    B0 = math.sqrt(2.0 * P_amb / beta_amb)
+    th, ph = math.radians(theta0), math.radians(phi0)
+    bhat = np.array([math.cos(ph) * math.sin(th), math.sin(ph) * math.sin(th), math.cos(th)])
+    rho = np.full((n, n, n), rho0)
+    if density_noise:
+        R = _rotation_to_z(bhat)
+        xp = R[0, 0] * dX + R[0, 1] * dY + R[0, 2] * dZ
+        yp = R[1, 0] * dX + R[1, 1] * dY + R[1, 2] * dZ
+        tp = 2.0 * math.pi / r0
+        d = (np.sin(tp / 0.08 * xp + math.pi / 4) + np.sin(tp / 0.10 * xp) + np.sin(tp / 0.12 * xp - math.pi / 4)
+             + np.cos(tp / 0.08 * yp + math.pi / 4) + np.cos(tp / 0.10 * yp) + np.cos(tp / 0.12 * yp - math.pi / 4))
+        rho = np.where(r < 1.5 * r0, rho0 * (1.0 + 2e-2 * d), rho)
+    P = np.where(r < r0, P_in, P_amb)
+    B = np.stack([np.full((n, n, n), B0 * bhat[d]) for d in range(3)])
+    z = np.zeros((n, n, n))
+    U = conserved(rho, z, z, z, P, B, gamma)
+    return State(U, np.ascontiguousarray(B), dx, gamma,
+                 dict(kind="mhd_blast", r0=r0, B0=B0, bhat=bhat, P_amb=P_amb, density_noise=density_noise))
+
+
 # --- linear waves ----------------------------------------------------------
 
 WAVES = {"fast": 6, "alfven": 5, "slow": 4, "entropy": 3}

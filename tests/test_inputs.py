@@ -74,3 +74,75 @@ def test_linear_wave_eigenvector_and_period():
     assert math.isclose(lam, 0.5, rel_tol=1e-12)
     st = I.linear_wave(8, "fast")
     assert math.isclose(st.meta["period"], 1 / math.sqrt(3) / 2.0, rel_tol=1e-12)
+
+
+def test_abc_eigenmode_perturbation_matches_eqs_21_23():
+    """face averages of the perturbation (Eqs. 21-23) against a midpoint-rule
+    quadrature of the printed Fourier modes over a few faces, and a discrete
+    divergence at round-off"""
+    n = 16
+    amp = 0.4
+    st0 = I.abc(n, kmult=2, beta=1.0, noise=0.0)
+    st = I.abc_perturbed(n, kmult=2, beta=1.0, amp=amp, drift=False)
+    dB = st.B - st0.B
+    dx = st.dx
+
+    def point(x, y, z):
+        out = np.zeros(3)
+        for kv, a, b in I.ABC_EIGENMODE:
+            ph = 2 * np.pi * (kv[0] * x + kv[1] * y + kv[2] * z)
+            out += 1e-2 * amp * (np.array(a) * np.cos(ph) + np.array(b) * np.sin(ph))
+        return out
+
+    q = (np.arange(40) + 0.5) / 40
+    rng = np.random.default_rng(0)
+    for _ in range(6):
+        i, j, k = rng.integers(0, n, 3)
+        # Bx face at x_{i-1/2}, averaged over y, z
+        v = np.mean([point(i * dx, (j + a) * dx, (k + b) * dx)[0] for a in q for b in q])
+        assert abs(dB[0, k, j, i] - v) <= 1e-5 * amp
+        v = np.mean([point((i + a) * dx, j * dx, (k + b) * dx)[1] for a in q for b in q])
+        assert abs(dB[1, k, j, i] - v) <= 1e-5 * amp
+        v = np.mean([point((i + a) * dx, (j + b) * dx, k * dx)[2] for a in q for b in q])
+        assert abs(dB[2, k, j, i] - v) <= 1e-5 * amp
+    div = (np.roll(st.B[0], -1, 2) - st.B[0]) + (np.roll(st.B[1], -1, 1) - st.B[1]) + (np.roll(st.B[2], -1, 0) - st.B[2])
+    assert np.abs(div).max() <= 1e-14
+
+
+def test_eigenmode_amplitude_vectors_are_transverse():
+    for kv, a, b in I.ABC_EIGENMODE:
+        assert abs(np.dot(kv, a)) < 1e-12 and abs(np.dot(kv, b)) < 1e-12
+
+
+def test_abc_perturbed_drift():
+    st = I.abc_perturbed(8, kmult=2, beta=1.0)
+    v = st.U[1:4] / st.U[0]
+    cs = np.sqrt(st.gamma * st.meta["P0"])
+    mag = np.sqrt((v ** 2).sum(axis=0))
+    assert np.allclose(mag, cs / (8 * np.sqrt(st.gamma)), rtol=1e-12)
+    assert np.allclose(v[0], v[1]) and np.allclose(v[1], v[2])
+
+
+@pytest.mark.parametrize("theta0", [90.0, 35.26438968, 85.0])
+def test_mhd_blast(theta0):
+    n = 32
+    st = I.mhd_blast(n, r0=0.1, theta0=theta0, phi0=45.0, density_noise=True)
+    W_P = (st.gamma - 1) * (st.U[4] - 0.5 * (st.U[1] ** 2 + st.U[2] ** 2 + st.U[3] ** 2) / st.U[0]
+                            - 0.5 * (st.B ** 2).sum(axis=0))
+    assert np.isclose(W_P.max(), 1.0) and np.isclose(W_P.min(), 1e-2)
+    B0 = st.meta["B0"]
+    assert np.isclose(2 * 1e-2 / B0 ** 2, 0.2)
+    bh = st.B[:, 0, 0, 0] / B0
+    assert np.allclose(bh, st.meta["bhat"])
+    # the rotation maps the field direction onto z' and preserves lengths
+    R = I._rotation_to_z(st.meta["bhat"])
+    assert np.allclose(R @ st.meta["bhat"], [0, 0, 1], atol=1e-12)
+    assert np.allclose(R @ R.T, np.eye(3), atol=1e-12)
+    # density perturbation: only inside 1.5 r0, of at most 6 x 2e-2
+    rho = st.U[0]
+    c = (np.arange(n) + 0.5) / n - 0.5
+    Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+    r = np.sqrt(X * X + Y * Y + Z * Z)
+    assert np.all(rho[r >= 0.15] == 1.0)
+    assert np.abs(rho - 1.0).max() <= 0.12 + 1e-12
+    assert np.abs(rho[r < 0.15] - 1.0).max() > 1e-3

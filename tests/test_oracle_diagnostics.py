@@ -1,0 +1,72 @@
+"""Pins of the oracle's diagnostics (Sec. 4.3 and 4.5): the edge current
+density of the discrete ABC field against its closed form, the face-based
+magnetic energy U_B against (A^2+B^2+C^2) L^3/2 sinc^2(k dx/2), the flow and
+total energies of a uniform drift, and the |J|/|B| refinement test of the
+force-free field (|J|/|B| = k up to O((k dx)^2))."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1804_03479_b300 import inputs as I
+
+
+def sinc(u):
+    return math.sin(u) / u
+
+
+@pytest.mark.parametrize("n,kmult", [(16, 1), (24, 2)])
+def test_abc_edge_current_closed_form(n, kmult):
+    # area-averaged face B of the ABC field: dx J_edge = 2 sin(k dx/2) sinc(k dx/2) B(edge point)
+    st = I.abc(n, kmult=kmult, beta=1.0, noise=0.0)
+    k, a, dx = st.meta["k"], st.meta["A"], st.dx
+    J = orc.edge_current(st.B)
+    fac = 2.0 * math.sin(0.5 * k * dx) * sinc(0.5 * k * dx)
+    c = (np.arange(n) + 0.5) * dx          # cell centres
+    f = np.arange(n) * dx                  # lower faces
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    zf, yf, xf = np.meshgrid(f, f, f, indexing="ij")
+    # J_x at (x_i, y_{j-1/2}, z_{k-1/2}), J_y at (x_{i-1/2}, y_j, z_{k-1/2}), J_z at (x_{i-1/2}, y_{j-1/2}, z_k)
+    Bx = a * np.sin(k * zf) + a * np.cos(k * yf)
+    By = a * np.sin(k * xf) + a * np.cos(k * zf)
+    Bz = a * np.sin(k * yf) + a * np.cos(k * xf)
+    assert np.max(np.abs(J[0] - fac * Bx)) <= 1e-13
+    assert np.max(np.abs(J[1] - fac * By)) <= 1e-13
+    assert np.max(np.abs(J[2] - fac * Bz)) <= 1e-13
+
+
+@pytest.mark.parametrize("n,kmult", [(16, 1), (32, 2)])
+def test_abc_magnetic_energy_closed_form(n, kmult):
+    st = I.abc(n, kmult=kmult, beta=1.0, noise=0.0)
+    k, a, dx = st.meta["k"], st.meta["A"], st.dx
+    d = orc.energies(st.U, st.B, dx, 1.0)
+    ub = 3 * a * a / 2.0 * sinc(0.5 * k * dx) ** 2
+    assert abs(d["U_B"] - ub) <= 1e-13 * ub
+    assert d["U_V"] == 0.0
+
+
+def test_uniform_drift_energies():
+    st = I.abc(16, kmult=1, beta=0.7, noise=0.0, drift=(0.3, -0.2, 0.5), rho0=1.7)
+    d = orc.energies(st.U, st.B, st.dx, 1.0)
+    uv = 0.5 * 1.7 * (0.09 + 0.04 + 0.25)
+    assert abs(d["U_V"] - uv) <= 1e-13 * uv
+    P0 = st.meta["P0"]
+    et = P0 / (st.gamma - 1.0) + uv + d["U_B"]      # the face-based U_B equals the cell-average sum only on average
+    # e carries the cell-centred magnetic energy; the two differ at O((k dx)^2)
+    assert abs(d["E_T"] - et) <= 0.05 * d["U_B"]
+    assert abs(d["E_T"] - float(st.U[4].sum()) * st.dx ** 3) <= 1e-13 * d["E_T"]
+
+
+def test_force_free_refinement_ratio():
+    n, kmult = 32, 1
+    st = I.abc(n, kmult=kmult, beta=1.0, noise=0.0)
+    kdx = st.meta["k"] * st.dx
+    d = orc.energies(st.U, st.B, st.dx, 0.9 * kdx)
+    assert abs(d["jb_max"] / kdx - 1.0) <= 0.5 * kdx ** 2
+    assert d["n_above"] == n ** 3
+    assert orc.energies(st.U, st.B, st.dx, 1.1 * kdx)["n_above"] == 0
+    # max |J| ~ k max |B| (|B| <= sqrt(3) * 2 a... bounded by k * max|B_cc|)
+    W = orc.prim(st.U, st.B, st.gamma)
+    bmax = float(np.sqrt(W[5] ** 2 + W[6] ** 2 + W[7] ** 2).max())
+    assert d["j_max"] <= st.meta["k"] * bmax * 1.001
