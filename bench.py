@@ -37,18 +37,18 @@ PAPER_P100 = {"fp32": 1.2e8, "fp64": 5.5e7}   # Sec. 5.2 (i), Tesla P100, VL + P
 GROUPS = ["prim_cfl", "predictor_sweeps", "emf1", "half_update", "corrector_sweeps", "emf2", "full_update"]
 SIZES = {"fp64": (8, 8, 8), "fp32": (4, 4, 4), "mixed": (4, 8, 4)}   # (rho/M, e/B, arithmetic) bytes
 # Algorithmic floating-point operations per face of one corrector sweep launch
-# (one cell's reconstruction and one Riemann solve): the FADD + FMUL + 2 FFMA
-# count that ncu reports for the FP32 build at 160^3 (mean of the x and y
-# launches: 1251.1 and 1232.7), where every divide and square root is a single
-# MUFU op.  The same algorithm runs in the FP64 build, which expands divides
-# and square roots into FMA iterations (2394 executed FP64 flops per face at
-# 128^3), so the algorithmic figure is used for all precisions.
-FLOPS_PER_FACE = {"fp32": 1242.0, "fp64": 1242.0, "mixed": 1242.0}
+# (one cell's characteristic PLM reconstruction and one Roe solve): the
+# FADD + FMUL + 2 FFMA count that ncu reports for the FP32 build at 160^3
+# (x sweep), where every divide and square root is a single MUFU op.  The
+# same algorithm runs in the FP64 build, whose divides and square roots
+# expand into FMA iterations (1632 executed FP64 flops per face at 128^3), so
+# the algorithmic figure is used for all precisions.
+FLOPS_PER_FACE = {"fp32": 1002.0, "fp64": 1002.0, "mixed": 1002.0}
 # DRAM bytes (read + write) per face of one corrector sweep launch, from
 # dram__bytes_read.sum + dram__bytes_write.sum of the same captures
-# (FP32: 238.2 MB per launch at 160^3; FP64: 237.8 MB per launch at 128^3),
+# (FP32: 237.1 MB per launch at 160^3; FP64: 238.8 MB per launch at 128^3),
 # scaled to other sizes by the number of faces.
-TRAFFIC_PER_FACE = {"fp32": 58.15, "fp64": 113.4}
+TRAFFIC_PER_FACE = {"fp32": 57.9, "fp64": 113.9}
 
 
 def peaks():
@@ -595,7 +595,8 @@ def main():
             variants[prec] = {"value": vv, "unit": UNIT, "ms_per_step": msv / kv, "steps": kv,
                               "vs_p100_paper": vv / PAPER_P100[prec] if prec in PAPER_P100 else None,
                               "roofline": roofline(prec, gv, recv, n, pk, sm_mhz) if recv else None,
-                              "hbm_roofline_step": step_hbm(prec, n, msv / kv, pk)}
+                              "hbm_roofline_step": step_hbm(prec, n, msv / kv, pk),
+                              "kernel_ms_per_step": {k: v / recv for k, v in gv.items()} if recv else None}
         if not args.no_matrix:
             variants["schemes256"] = scheme_matrix(torch, mhd, st, max(3, min(args.steps, 10)), stream, pk)
         if not args.no_batch:

@@ -130,6 +130,28 @@ mhd_status mhd_divB(mhd_ctx* ctx, double* maxabs, double* brms);
  * Bx, By, Bz over faces; sums8 has 8 * nbox entries.  Synchronises. */
 mhd_status mhd_sums(mhd_ctx* ctx, double* sums8);
 
+/* Diagnostics of Sec. 4.3 / 4.5 per box (FP64, fixed-order reduction), out
+ * has 6 * nbox entries:
+ *   [0] E_T = sum e dx^3            [1] U_B = sum over faces B_f^2/2 dx^3
+ *   [2] U_V = sum |M|^2/(2 rho) dx^3
+ *   [3] max over cells of dx |J| / |B|   (J = curl B: dx J on an edge is the
+ *       circulation of the face B around it; the cell value is the mean of
+ *       its four edges per axis, |B| the mean of its two faces per axis)
+ *   [4] number of cells with dx |J| / |B| > jb_threshold (the refinement
+ *       test |J|/|B| > thr / dx of the Orszag-Tang and ABC runs)
+ *   [5] max over cells of |J|.
+ * jb_threshold >= 0, else MHD_EINVAL.  Synchronises. */
+mhd_status mhd_energies(mhd_ctx* ctx, double jb_threshold, double* out);
+
+/* Magnetic helicity H = sum A.B dx^3 per box (Sec. 4.5; h has nbox entries),
+ * of the cell-centre field (mean of the two faces per axis), with A in the
+ * Coulomb gauge of the periodic box: A_k = i k x B_k / |k|^2 from the
+ * discrete Fourier transform (cuFFT, FP64), the mean field carrying no A;
+ * H by Parseval.  Uses the flux scratch (no state is touched); cuFFT
+ * allocates its work area.  MHD_ENOMEM if a box's transform does not fit
+ * the scratch (3n doubles + 3 half spectra).  Synchronises. */
+mhd_status mhd_helicity(mhd_ctx* ctx, double* h);
+
 /* Face-sweep tiling: tiles of 32 x tile_len faces (tile_len 4, 8 or 16),
  * blocks_per_sm x SMs persistent blocks.  mhd_autotune times every pair on
  * the context's own batch (reps steps each, the state restored after each

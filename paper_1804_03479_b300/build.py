@@ -72,7 +72,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for obj, log in results:
             sys.stderr.write(log)
     objs = [o for o, _ in results]
-    cmd = [NVCC, *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"]
+    cmd = [NVCC, *ARCH, "-shared", "-o", LIB, *objs, "-lcudart", "-lcufft"]
     subprocess.run(cmd, check=True)
     return LIB
 

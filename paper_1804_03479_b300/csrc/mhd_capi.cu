@@ -2,6 +2,7 @@
 #include <stdarg.h>
 #include <stdlib.h>
 #include <string.h>
+#include <cufft.h>
 #include "mhd_engine.cuh"
 
 using namespace mhd;
@@ -58,16 +59,19 @@ static cudaError_t dalloc(mhd_ctx* c, void** p, size_t bytes)
 // tile prefix sums of the box table for tile length tl; uploads the table
 static cudaError_t layout_tiles(mhd_ctx* c, int tl)
 {
-    int t0[3] = {0, 0, 0};
+    int t0[3] = {0, 0, 0}, e0 = 0;
     for (int b = 0; b < c->nbox; b++) {
         BoxDev& x = c->hbox[b];
         for (int d = 0; d < 3; d++) {
             x.tile0[d] = t0[d];
             t0[d] += tiles_of_box(x.nx, x.ny, x.nz, d, tl);
         }
+        x.etile0 = e0;
+        e0 += emf_tiles_of_box(x.nx, x.ny, x.nz);
     }
     c->B.tl = tl;
     for (int d = 0; d < 3; d++) c->B.ntile[d] = t0[d];
+    c->B.netile = e0;
     if (c->have_graph) {   // a captured step holds the old tile layout
         cudaGraphExecDestroy(c->gexec);
         c->have_graph = false;
@@ -396,6 +400,74 @@ extern "C" mhd_status mhd_sums(mhd_ctx* c, double* sums8)
         for (int f = 0; f < 8; f++) sums8[b * 8 + f] = d[b * 10 + 2 + f];
     free(d);
     return s;
+}
+
+extern "C" mhd_status mhd_energies(mhd_ctx* c, double jb_threshold, double* out)
+{
+    if (!c || !out) return fail(c, MHD_EINVAL, "null pointer");
+    if (!(jb_threshold >= 0.0)) return fail(c, MHD_EINVAL, "jb_threshold must be >= 0");
+    const int nb = c->cell_grid;
+    switch (c->sch.precision) {
+        case MHD_FP64: k_energies<double, double><<<nb, CELL_THREADS, 0, c->stream>>>(c->B, state_of<double, double>(c), jb_threshold, c->part); break;
+        case MHD_FP32: k_energies<float, float><<<nb, CELL_THREADS, 0, c->stream>>>(c->B, state_of<float, float>(c), jb_threshold, c->part); break;
+        default:       k_energies<float, double><<<nb, CELL_THREADS, 0, c->stream>>>(c->B, state_of<float, double>(c), jb_threshold, c->part); break;
+    }
+    k_finish_energies<<<c->nbox, 32, 0, c->stream>>>(c->B, c->part, c->diag);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out, c->diag, (size_t)c->nbox * 6 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int b = 0; b < c->nbox; b++) {
+        const double dx = c->hbox[b].dx, v = dx * dx * dx;
+        out[b * 6 + 0] *= v;
+        out[b * 6 + 1] *= v;
+        out[b * 6 + 2] *= v;
+        out[b * 6 + 5] /= dx;
+    }
+    return check_device_flags(c);
+}
+
+extern "C" mhd_status mhd_helicity(mhd_ctx* c, double* h)
+{
+    if (!c || !h) return fail(c, MHD_EINVAL, "null pointer");
+    const size_t rsz = c->sch.precision == MHD_FP64 ? sizeof(double) : sizeof(float);
+    const size_t f1_bytes = (size_t)21 * (size_t)c->B.N * rsz;
+    const int nblk = (int)(c->B.nvblk * 10 < 1024 ? c->B.nvblk * 10 : 1024);   // c->part holds nvblk * 10
+    double parts[1024];
+    for (int b = 0; b < c->nbox; b++) {
+        const BoxDev& g = c->hbox[b];
+        const long long n = g.n;
+        const long long m = (long long)g.nz * g.ny * (g.nx / 2 + 1);
+        const size_t in_bytes = ((size_t)3 * n * sizeof(double) + 255) / 256 * 256;
+        if (in_bytes + (size_t)3 * m * sizeof(double2) > f1_bytes)
+            return fail(c, MHD_ENOMEM, "mhd_helicity: box %d does not fit the flux scratch", b);
+        double* in = (double*)c->F1;
+        double2* out = (double2*)((char*)c->F1 + in_bytes);
+        switch (c->sch.precision) {
+            case MHD_FP32: k_bcc<float><<<256, 256, 0, c->stream>>>(g, (float*)c->b[0], (float*)c->b[1], (float*)c->b[2], in); break;
+            default:       k_bcc<double><<<256, 256, 0, c->stream>>>(g, (double*)c->b[0], (double*)c->b[1], (double*)c->b[2], in); break;
+        }
+        CK(cudaGetLastError());
+        cufftHandle plan;
+        int dims[3] = {g.nz, g.ny, g.nx};
+        if (cufftPlanMany(&plan, 3, dims, nullptr, 1, (int)n, nullptr, 1, (int)m, CUFFT_D2Z, 3) != CUFFT_SUCCESS)
+            return fail(c, MHD_ECUDA, "mhd_helicity: cuFFT plan failed for box %d", b);
+        cufftResult fr = cufftSetStream(plan, c->stream);
+        if (fr == CUFFT_SUCCESS) fr = cufftExecD2Z(plan, in, (cufftDoubleComplex*)out);
+        if (fr != CUFFT_SUCCESS) {
+            cufftDestroy(plan);
+            return fail(c, MHD_ECUDA, "mhd_helicity: cuFFT transform failed for box %d", b);
+        }
+        k_helicity_part<<<nblk, 256, 0, c->stream>>>(g.nx, g.ny, g.nz, g.dx, out, c->part);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(parts, c->part, nblk * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        cufftDestroy(plan);
+        if (e != cudaSuccess) return fail(c, MHD_ECUDA, "mhd_helicity: %s", cudaGetErrorString(e));
+        double s = 0.0;
+        for (int q = 0; q < nblk; q++) s += parts[q];
+        h[b] = s * g.dx * g.dx * g.dx / (double)n;
+    }
+    return check_device_flags(c);
 }
 
 extern "C" mhd_status mhd_sync(mhd_ctx* c)

@@ -80,17 +80,20 @@ __device__ __forceinline__ R fast_speed(R rho, R a2, R bn, R bt1, R bt2)
 // ---- seven-wave eigensystem of the 1-D primitive system -----------------
 // Roe-Balsara normalisation; waves v-cf, v-ca, v-cs, v, v+cs, v+ca, v+cf.
 template <class R> struct Eig {
-    R rho, sr, a2, a, cf, cs, ca, af, as, by, bz, s, vn, nrm;
+    R rho, irho, sr, isr, a2, ia2, a, cf, cs, ca, af, as, by, bz, s, vn, nrm;
 };
 
+// a2 = gamma P / rho (primitive sound speed squared, Roe-averaged for Roe)
 template <class R>
 __device__ __forceinline__ void eig_setup(R rho, R vn, R a2, R bn, R bt1, R bt2, Eig<R>& e)
 {
     e.rho = rho;
+    e.irho = R(1) / rho;
     e.vn = vn;
     e.sr = Num<R>::sqrt_(rho);
-    R ca2 = bn * bn / rho;
-    R bt2s = (bt1 * bt1 + bt2 * bt2) / rho;
+    e.isr = e.sr * e.irho;
+    R ca2 = bn * bn * e.irho;
+    R bt2s = (bt1 * bt1 + bt2 * bt2) * e.irho;
     R t = a2 - ca2 - bt2s;
     R disc = t * t + R(4) * a2 * bt2s;
     R cf2 = R(0.5) * (a2 + ca2 + bt2s + Num<R>::sqrt_(disc));
@@ -100,24 +103,27 @@ __device__ __forceinline__ void eig_setup(R rho, R vn, R a2, R bn, R bt1, R bt2,
     e.ca = Num<R>::sqrt_(ca2);
     e.a = Num<R>::sqrt_(a2);
     e.a2 = a2;
+    e.ia2 = R(1) / a2;
     R dd = cf2 - cs2;
     if (dd > R(0)) {
-        e.af = Num<R>::sqrt_(rmax(R(0), a2 - cs2) / dd);
-        e.as = Num<R>::sqrt_(rmax(R(0), cf2 - a2) / dd);
+        R idd = R(1) / dd;
+        e.af = Num<R>::sqrt_(rmax(R(0), a2 - cs2) * idd);
+        e.as = Num<R>::sqrt_(rmax(R(0), cf2 - a2) * idd);
     } else {
         e.af = R(1);
         e.as = R(0);
     }
-    R btm = Num<R>::sqrt_(bt1 * bt1 + bt2 * bt2);
-    if (btm > R(0)) {
-        e.by = bt1 / btm;
-        e.bz = bt2 / btm;
+    R btm2 = bt1 * bt1 + bt2 * bt2;
+    if (btm2 > R(0)) {
+        R ibt = R(1) / Num<R>::sqrt_(btm2);
+        e.by = bt1 * ibt;
+        e.bz = bt2 * ibt;
     } else {
         e.by = Num<R>::sqrt_(R(0.5));
         e.bz = e.by;
     }
     e.s = sgn1(bn);
-    e.nrm = R(0.5) / a2;
+    e.nrm = R(0.5) * e.ia2;
 }
 
 template <class R>
@@ -132,10 +138,10 @@ template <class R>
 __device__ __forceinline__ void eig_project(const Eig<R>& e, const R dw[7], R da[7])
 {
     R q = e.by * dw[2] + e.bz * dw[3];              // transverse velocity along beta
-    R qb = (e.by * dw[5] + e.bz * dw[6]) / e.sr;    // transverse field along beta
+    R qb = (e.by * dw[5] + e.bz * dw[6]) * e.isr;   // transverse field along beta
     R av = -e.bz * dw[2] + e.by * dw[3];            // rotational velocity
-    R ab = (e.bz * dw[5] - e.by * dw[6]) / e.sr;    // rotational field
-    R pr = dw[4] / e.rho;
+    R ab = (e.bz * dw[5] - e.by * dw[6]) * e.isr;   // rotational field
+    R pr = dw[4] * e.irho;
     R Cf = e.af * e.cf, Cs = e.as * e.cs;
     R fq = e.as * e.cs * e.s, sq = e.af * e.cf * e.s;
     da[0] = e.nrm * (-Cf * dw[1] + fq * q + e.af * pr + e.as * e.a * qb);
@@ -144,7 +150,7 @@ __device__ __forceinline__ void eig_project(const Eig<R>& e, const R dw[7], R da
     da[4] = e.nrm * ( Cs * dw[1] + sq * q + e.as * pr - e.af * e.a * qb);
     da[1] = R(0.5) * (av - e.s * ab);
     da[5] = R(0.5) * (av + e.s * ab);
-    da[3] = dw[0] - dw[4] / e.a2;
+    da[3] = dw[0] - dw[4] * e.ia2;
 }
 
 // dw = R a, using the sparsity of the right eigenvectors
@@ -165,13 +171,37 @@ __device__ __forceinline__ void eig_expand(const Eig<R>& e, const R da[7], R dw[
     dw[6] = e.bz * bf - e.s * e.sr * e.by * ad;
 }
 
-// one right eigenvector (column k), primitive variables
-template <class R>
-__device__ __forceinline__ void eig_column(const Eig<R>& e, int k, R r[7])
+// P += c r_K: column K of the right eigenvectors (eig_expand of the unit
+// amplitude e_K), with its zero entries left out
+template <int K, class R>
+__device__ __forceinline__ void eig_add_col(const Eig<R>& e, R c, R P[7])
 {
-    R da[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
-    da[k] = R(1);
-    eig_expand(e, da, r);
+    if (K == 3) {                              // entropy wave
+        P[0] += c;
+        return;
+    }
+    if (K == 1 || K == 5) {                    // Alfven waves
+        const R t = (K == 1 ? R(-1) : R(1)) * e.s * e.sr * c;
+        P[2] -= c * e.bz;
+        P[3] += c * e.by;
+        P[5] += t * e.bz;
+        P[6] -= t * e.by;
+        return;
+    }
+    // magnetosonic waves: K = 0, 6 fast, K = 2, 4 slow; sg = -1 on the left-going one
+    const bool fast = K == 0 || K == 6;
+    const R sg = (K == 0 || K == 2) ? R(-1) : R(1);
+    const R A = fast ? e.af : e.as;
+    const R Cn = fast ? e.af * e.cf : e.as * e.cs;
+    const R tr = fast ? -sg * e.as * e.cs : sg * e.af * e.cf;
+    const R bf = fast ? e.a * e.sr * e.as : -(e.a * e.sr * e.af);
+    P[0] += c * (e.rho * A);
+    P[1] += c * (sg * Cn);
+    P[2] += c * (e.s * e.by * tr);
+    P[3] += c * (e.s * e.bz * tr);
+    P[4] += c * (e.rho * e.a2 * A);
+    P[5] += c * (e.by * bf);
+    P[6] += c * (e.bz * bf);
 }
 
 // ---- Riemann solvers ------------------------------------------------------
@@ -238,7 +268,41 @@ __device__ __forceinline__ void hlle_flux(const R wl[7], const R wr[7], R bn, R 
     hlle_core(wl, wr, bn, gm1, gam, ok, m.u, cf, f);
 }
 
-// Roe flux with the exact linearisation; returns true when it fell back to HLLE
+// conserved image M q of a primitive-space vector q under the Roe state
+// (the X term of the linearisation enters through q4 - X q0); the full
+// vector, or only the density, momentum, energy and B_t parts used by the
+// intermediate-state check (the same thing: all seven)
+template <class R>
+__device__ __forceinline__ void roe_to_cons(const RoeAvg<R>& m, R ke, R igm1, const R q[7], R u[7])
+{
+    u[0] = q[0];
+    u[1] = m.u * q[0] + m.rho * q[1];
+    u[2] = m.v * q[0] + m.rho * q[2];
+    u[3] = m.w * q[0] + m.rho * q[3];
+    u[4] = (q[4] - m.X * q[0]) * igm1 + ke * q[0] + m.rho * (m.u * q[1] + m.v * q[2] + m.w * q[3])
+           + m.b1 * q[5] + m.b2 * q[6];
+    u[5] = q[5];
+    u[6] = q[6];
+}
+
+// intermediate state U_L + M P of the Roe fan: false when rho <= 0 or P <= 0
+template <class R>
+__device__ __forceinline__ bool roe_state_ok(const RoeAvg<R>& m, R ke, R igm1, const R ul[7], const R P[7], R bn,
+                                             R gm1)
+{
+    R d[7];
+    roe_to_cons(m, ke, igm1, P, d);
+    R rho = ul[0] + d[0];
+    R m1 = ul[1] + d[1], m2 = ul[2] + d[2], m3 = ul[3] + d[3];
+    R en = ul[4] + d[4], b1 = ul[5] + d[5], b2 = ul[6] + d[6];
+    R p = gm1 * (en - R(0.5) * (m1 * m1 + m2 * m2 + m3 * m3) / rho - R(0.5) * (bn * bn + b1 * b1 + b2 * b2));
+    return rho > R(0) && p > R(0);
+}
+
+// Roe flux with the exact linearisation; returns true when it fell back to HLLE.
+// F = (F_L + F_R)/2 - (1/2) M R (|lambda| eta): the dissipation is one
+// eigenvector expansion of |lambda| eta; the intermediate states
+// U_L + M sum_{b<=a} eta_b r_b are accumulated wave by wave in primitive space.
 template <class R>
 __device__ __forceinline__ bool roe_flux(const R wl[7], const R wr[7], R bn, R gm1, R gam, R f[7])
 {
@@ -262,44 +326,28 @@ __device__ __forceinline__ bool roe_flux(const R wl[7], const R wr[7], R bn, R g
     dq[6] = wr[6] - wl[6];
     R eta[7];
     eig_project(e, dq, eta);
+    const R igm1 = R(1) / gm1;
+    const R ke = R(0.5) * (m.u * m.u + m.v * m.v + m.w * m.w) + m.X;
     R ul[7];
     to_cons(wl, bn, gm1, ul);
-    R us[7], dis[7];
-#pragma unroll
-    for (int k = 0; k < 7; k++) { us[k] = ul[k]; dis[k] = R(0); }
-    R ke = R(0.5) * (m.u * m.u + m.v * m.v + m.w * m.w) + m.X;
-    bool bad = false;
-#pragma unroll
-    for (int a = 0; a < 7; a++) {
-        R q[7];
-        eig_column(e, a, q);
-        q[4] -= m.X * q[0];
-        // conserved eigenvector M q
-        R ru[7];
-        ru[0] = q[0];
-        ru[1] = m.u * q[0] + m.rho * q[1];
-        ru[2] = m.v * q[0] + m.rho * q[2];
-        ru[3] = m.w * q[0] + m.rho * q[3];
-        ru[4] = q[4] / gm1 + ke * q[0] + m.rho * (m.u * q[1] + m.v * q[2] + m.w * q[3]) + m.b1 * q[5] + m.b2 * q[6];
-        ru[5] = q[5];
-        ru[6] = q[6];
-        R c = eta[a], cd = Num<R>::abs_(lam[a]) * eta[a];
-#pragma unroll
-        for (int k = 0; k < 7; k++) dis[k] += cd * ru[k];
-        if (a < 6) {
-#pragma unroll
-            for (int k = 0; k < 7; k++) us[k] += c * ru[k];
-            R rho = us[0];
-            R p = gm1 * (us[4] - R(0.5) * (us[1] * us[1] + us[2] * us[2] + us[3] * us[3]) / rho
-                         - R(0.5) * (bn * bn + us[5] * us[5] + us[6] * us[6]));
-            bad = bad || !(rho > R(0)) || !(p > R(0));
-        }
-    }
-    if (bad) {
+    R P[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+    bool ok = true;
+    eig_add_col<0>(e, eta[0], P); ok &= roe_state_ok(m, ke, igm1, ul, P, bn, gm1);
+    eig_add_col<1>(e, eta[1], P); ok &= roe_state_ok(m, ke, igm1, ul, P, bn, gm1);
+    eig_add_col<2>(e, eta[2], P); ok &= roe_state_ok(m, ke, igm1, ul, P, bn, gm1);
+    eig_add_col<3>(e, eta[3], P); ok &= roe_state_ok(m, ke, igm1, ul, P, bn, gm1);
+    eig_add_col<4>(e, eta[4], P); ok &= roe_state_ok(m, ke, igm1, ul, P, bn, gm1);
+    eig_add_col<5>(e, eta[5], P); ok &= roe_state_ok(m, ke, igm1, ul, P, bn, gm1);
+    if (!ok) {
         R cf = fast_speed(m.rho, m.a2, bn, m.b1, m.b2);
         hlle_core(wl, wr, bn, gm1, gam, true, m.u, cf, f);
         return true;
     }
+    R ae[7], D[7], dis[7];
+#pragma unroll
+    for (int a = 0; a < 7; a++) ae[a] = Num<R>::abs_(lam[a]) * eta[a];
+    eig_expand(e, ae, D);
+    roe_to_cons(m, ke, igm1, D, dis);
     R fl[7], fr[7];
     phys_flux(wl, bn, gm1, fl);
     phys_flux(wr, bn, gm1, fr);
@@ -433,19 +481,18 @@ __device__ __forceinline__ void char_slope(const R wm[7], const R w0[7], const R
 {
     Eig<R> e;
     eig_setup(w0[0], w0[1], gam * w0[4] / w0[0], bn, w0[5], w0[6], e);
-    R dl[7], dr[7], dc[7], al[7], ar[7], ac[7];
+    R dl[7], dr[7], al[7], ar[7];
 #pragma unroll
     for (int k = 0; k < 7; k++) {
         dl[k] = w0[k] - wm[k];
         dr[k] = wp[k] - w0[k];
-        dc[k] = R(0.5) * (wp[k] - wm[k]);
     }
     eig_project(e, dl, al);
     eig_project(e, dr, ar);
-    eig_project(e, dc, ac);
+    // the centred difference (w_{+1} - w_{-1})/2 projects to (al + ar)/2 (L is linear)
     R da[7];
 #pragma unroll
-    for (int a = 0; a < 7; a++) da[a] = mc(al[a], ar[a], ac[a]);
+    for (int a = 0; a < 7; a++) da[a] = mc(al[a], ar[a], R(0.5) * (al[a] + ar[a]));
     eig_expand(e, da, dw);
 }
 
@@ -471,19 +518,17 @@ __device__ __forceinline__ void recon_cell(const R wm1[7], const R w0[7], const 
     eig_setup(w0[0], w0[1], gam * w0[4] / w0[0], bn, w0[5], w0[6], e);
     R pl[7], pr[7];
     if (RECON == PLM) {
-        R dl[7], dr[7], dc[7], al[7], ar[7], ac[7];
+        R dl[7], dr[7], al[7], ar[7];
 #pragma unroll
         for (int k = 0; k < 7; k++) {
             dl[k] = w0[k] - wm1[k];
             dr[k] = wp1[k] - w0[k];
-            dc[k] = R(0.5) * (wp1[k] - wm1[k]);
         }
         eig_project(e, dl, al);
         eig_project(e, dr, ar);
-        eig_project(e, dc, ac);
 #pragma unroll
         for (int a = 0; a < 7; a++) {
-            R d = mc(al[a], ar[a], ac[a]);
+            R d = mc(al[a], ar[a], R(0.5) * (al[a] + ar[a]));
             pl[a] = R(-0.5) * d;
             pr[a] = R(0.5) * d;
         }
@@ -491,8 +536,8 @@ __device__ __forceinline__ void recon_cell(const R wm1[7], const R w0[7], const 
         R fm[7], fp[7];
 #pragma unroll
         for (int k = 0; k < 7; k++) {
-            R vm = R(0.5) * (wm1[k] + w0[k]) - (dw0[k] - dwm[k]) / R(6);
-            R vp = R(0.5) * (w0[k] + wp1[k]) - (dwp[k] - dw0[k]) / R(6);
+            R vm = R(0.5) * (wm1[k] + w0[k]) - (dw0[k] - dwm[k]) * R(1.0 / 6.0);
+            R vp = R(0.5) * (w0[k] + wp1[k]) - (dwp[k] - dw0[k]) * R(1.0 / 6.0);
             fm[k] = clamp_between(vm, wm1[k], w0[k]) - w0[k];
             fp[k] = clamp_between(vp, w0[k], wp1[k]) - w0[k];
         }
@@ -530,8 +575,14 @@ __device__ __forceinline__ void recon_cell(const R wm1[7], const R w0[7], const 
         }
     }
     R dm[7], dp[7];
-    eig_expand(e, pl, dm);
     eig_expand(e, pr, dp);
+    if (RECON == PLM && !TRACE) {
+        // pl = -pr, and the expansion is odd in its argument
+#pragma unroll
+        for (int k = 0; k < 7; k++) dm[k] = -dp[k];
+    } else {
+        eig_expand(e, pl, dm);
+    }
 #pragma unroll
     for (int k = 0; k < 7; k++) {
         wm[k] = w0[k] + dm[k];

@@ -86,6 +86,23 @@ inline StateP<TU, TE> state_of(mhd_ctx* c)
     return s;
 }
 
+// persistent grid of the edge-field kernel: the blocks one SM keeps resident
+// (registers and shared memory; asked once per precision) times the SMs
+template <class R>
+inline int emf_grid(const mhd_ctx* c)
+{
+    static int per = 0;
+    if (per <= 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_emf<R>, EMF_THREADS, emf_smem_bytes<R>()) !=
+                cudaSuccess || nb < 1)
+            nb = 1;
+        per = nb;
+    }
+    int cap = per * c->nsm;
+    return c->B.netile < cap ? c->B.netile : cap;
+}
+
 inline int sweep_grid(const mhd_ctx* c, int d)
 {
     int cap = c->sweep_bps * c->nsm;
@@ -121,7 +138,7 @@ void run_step(mhd_ctx* c, bool device_dt)
             k_sweep<R, RECON, SOLVER, 0, TE><<<sweep_grid(c, d), SWEEP_THREADS, 0, st>>>(
                 g, d, W, s.b[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam);
         prof_mark(c, 2);
-        k_emf<R><<<nb, CELL_THREADS, 0, st>>>(g, F1, W, E);
+        k_emf<R><<<emf_grid<R>(c), EMF_THREADS, emf_smem_bytes<R>(), st>>>(g, F1, W, E);
         prof_mark(c, 3);
         k_half<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2], Wh, c->sch.pfloor);
         prof_mark(c, 4);
@@ -130,7 +147,7 @@ void run_step(mhd_ctx* c, bool device_dt)
             k_sweep<R, RECON, SOLVER, 1, TE><<<sweep_grid(c, d), SWEEP_THREADS, smem, st>>>(
                 g, d, Wh, Bh[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam);
         prof_mark(c, 5);
-        k_emf<R><<<nb, CELL_THREADS, 0, st>>>(g, F1, Wh, E);
+        k_emf<R><<<emf_grid<R>(c), EMF_THREADS, emf_smem_bytes<R>(), st>>>(g, F1, Wh, E);
         prof_mark(c, 6);
         k_full<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc);
         prof_mark(c, 7);
@@ -144,7 +161,7 @@ void run_step(mhd_ctx* c, bool device_dt)
                 c->dtc, gam);
         prof_mark(c, 2);
         // steps 3-4: edge E at t^n, dt/2 update of face B and cell state
-        k_emf<R><<<nb, CELL_THREADS, 0, st>>>(g, F1, W, E);
+        k_emf<R><<<emf_grid<R>(c), EMF_THREADS, emf_smem_bytes<R>(), st>>>(g, F1, W, E);
         prof_mark(c, 3);
         k_half<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2], Wh, c->sch.pfloor);
         prof_mark(c, 4);
@@ -155,7 +172,7 @@ void run_step(mhd_ctx* c, bool device_dt)
                                                               F2 + (long long)d * 7 * n, c->dtc, gam);
         prof_mark(c, 5);
         // steps 7-8
-        k_emf<R><<<nb, CELL_THREADS, 0, st>>>(g, F2, Wh, E);
+        k_emf<R><<<emf_grid<R>(c), EMF_THREADS, emf_smem_bytes<R>(), st>>>(g, F2, Wh, E);
         prof_mark(c, 6);
         k_full<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F2, E, c->dtc);
         prof_mark(c, 7);
@@ -167,7 +184,9 @@ template <class R, class TE, int RECON, int SOLVER, int MODE>
 inline cudaError_t allow_smem()
 {
     size_t b = sweep_smem_bytes<R>(RECON, TL_MAX);
-    if (MODE == 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_emf<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)emf_smem_bytes<R>());
+    if (e != cudaSuccess || MODE == 0) return e;
     return cudaFuncSetAttribute(k_sweep<R, RECON, SOLVER, MODE, TE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
 }
 

@@ -34,6 +34,7 @@ struct BoxDev {
     double dx;
     int tile0[3];       // first sweep tile of the box, per axis
     float inv_dx;       // 1/dx in single precision
+    int etile0;         // first edge-field tile of the box
 };
 
 // dt of a box and its ratios to dx, in both precisions; written once per
@@ -78,7 +79,7 @@ struct Boxes {
     long long N;        // cells of the batch (field stride)
     long long nvblk;    // virtual blocks of the batch
     int ntile[3];       // sweep tiles of the batch, per axis
-    int pad;
+    int netile;         // edge-field tiles of the batch
 };
 
 template <class TU, class TE> struct StateP {
@@ -192,7 +193,8 @@ __global__ void __launch_bounds__(CELL_THREADS) k_prim(Boxes B, StateP<TU, TE> s
             TE bz = TE(0.5) * (s.b[2][c] + s.b[2][nbr(g, i, j, k, 2, 1)]);
             TE rho = TE(s.rho[c]);
             TE mx = TE(s.m[0][c]), my = TE(s.m[1][c]), mz = TE(s.m[2][c]);
-            TE vx = mx / rho, vy = my / rho, vz = mz / rho;
+            const TE irho = TE(1) / rho;     // one division (FP64 is slow on this part)
+            TE vx = mx * irho, vy = my * irho, vz = mz * irho;
             // pressure recovery in the precision of the stored energy
             TE p = TE(gam - 1.0) * (s.e[c] - TE(0.5) * rho * (vx * vx + vy * vy + vz * vz)
                                     - TE(0.5) * (bx * bx + by * by + bz * bz));
@@ -456,9 +458,46 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(Boxes B, int d, const R
 }
 
 // ---------------------------------------------------------------------------
-// a7: edge electric fields, upwinded corner average (one cell -> its three
-// lower edges).  F[d] = F + d*7*N.
+// a7: edge electric fields, upwinded corner average (Sec. 2, Eqs. 13-14 with
+// the Gardiner-Stone reference field).  Every cell gets its three lower
+// edges: E_c at the corner of the faces a = c+1, b = c+2,
+//   E = (ea0 + ea1 + eb0 + eb1)/4 + (lob - hib)/4 + (loa - hia)/4,
+// the face values ea = -F_a[B_b], eb = F_b[B_a], the corrections upwinded by
+// the sign of the mass flux through the face (mean on a tie), against the
+// cell-centre reference -(v x B).
+//
+// Tiled: a block owns 32 x 8 cells of an x-y slab and marches EZC planes
+// along z.  Each plane is staged once in shared memory with a one-cell halo
+// on its lower x and y sides (297 cells x 12 values: the three reference
+// components and, per axis, the mass flux and the two B fluxes), three plane
+// slots deep so that one barrier per plane suffices.  F[d] = F + d*7*N.
 // ---------------------------------------------------------------------------
+constexpr int ETX = 32, ETY = 8, EZC = 16;
+constexpr int EHX = ETX + 1, EPL = EHX * (ETY + 1);   // halo'd plane cells
+constexpr int ENV = 12;                               // values per staged cell
+constexpr int EMF_THREADS = 320;                     // >= EPL: one staged cell per thread
+
+__host__ __device__ __forceinline__ int emf_tiles_of_box(int nx, int ny, int nz)
+{
+    return ((nx + ETX - 1) / ETX) * ((ny + ETY - 1) / ETY) * ((nz + EZC - 1) / EZC);
+}
+
+template <class R>
+constexpr size_t emf_smem_bytes()
+{
+    return (size_t)3 * ENV * EPL * sizeof(R);
+}
+
+__device__ __forceinline__ int box_of_etile(const Boxes& B, int t)
+{
+    int lo = 0, hi = B.nbox - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (B.b[mid].etile0 <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 template <class R>
 __device__ __forceinline__ R upwind(R f, R xm, R xp)
 {
@@ -467,43 +506,116 @@ __device__ __forceinline__ R upwind(R f, R xm, R xp)
     return R(0.5) * (xm + xp);
 }
 
+// one edge from the staged planes: P1 the cell's plane, P0 the plane below;
+// sa / sb the staged offsets of the shift by -1 along a / b (plane shifts
+// select P0 instead)
 template <class R>
-__global__ void __launch_bounds__(CELL_THREADS) k_emf(Boxes B, const R* __restrict__ F, const R* __restrict__ W,
-                                                      R* __restrict__ E)
+__device__ __forceinline__ R edge_e(const R* cc11, const R* cc01, const R* cc10, const R* cc00,
+                                    R ea0, R ea1, R eb0, R eb1, R fa0, R fa1, R fb0, R fb1)
 {
-    const long long N = B.N;
-    for (long long v = blockIdx.x; v < B.nvblk; v += gridDim.x) {
-    const BoxDev g = B.b[box_of_vblk(B, v)];
-    const long long lc = (v - g.vblk0) * CELL_THREADS + threadIdx.x;
-    if (lc >= g.n) continue;
-    int i, j, k;
-    coords(g, lc, i, j, k);
-    const long long q = g.off + lc;
+    R hib = upwind(fa1, *cc01 - eb0, *cc11 - eb1);
+    R lob = upwind(fa0, eb0 - *cc00, eb1 - *cc10);
+    R hia = upwind(fb1, *cc10 - ea0, *cc11 - ea1);
+    R loa = upwind(fb0, ea0 - *cc00, ea1 - *cc01);
+    return R(0.25) * (ea0 + ea1 + eb0 + eb1) + R(0.25) * (lob - hib) + R(0.25) * (loa - hia);
+}
+
+// staged values of one cell: the reference field -(v x B) and, per axis d,
+// the mass flux and the two B fluxes of F_d
+template <class R>
+struct EmfStage {
+    R v[ENV];
+};
+
+template <class R>
+__device__ __forceinline__ void emf_load(const R* __restrict__ F, const R* __restrict__ W, long long N, long long c,
+                                         EmfStage<R>& s)
+{
+    const R v0 = W[N + c], v1 = W[2 * N + c], v2 = W[3 * N + c];
+    const R b0 = W[5 * N + c], b1 = W[6 * N + c], b2 = W[7 * N + c];
+    s.v[0] = -(v1 * b2 - v2 * b1);
+    s.v[1] = -(v2 * b0 - v0 * b2);
+    s.v[2] = -(v0 * b1 - v1 * b0);
 #pragma unroll
-    for (int cax = 0; cax < 3; cax++) {
-        const int a = cax == 2 ? 0 : cax + 1, bb = cax == 0 ? 2 : cax - 1;
-        const R* Fa = F + (long long)a * 7 * N;
-        const R* Fb = F + (long long)bb * 7 * N;
-        long long c11 = q;
-        long long c01 = nbr(g, i, j, k, a, -1);
-        long long c10 = nbr(g, i, j, k, bb, -1);
-        int i2 = i, j2 = j, k2 = k;
-        if (a == 0) i2 = wrapi(i - 1, g.nx); else if (a == 1) j2 = wrapi(j - 1, g.ny); else k2 = wrapi(k - 1, g.nz);
-        long long c00 = nbr(g, i2, j2, k2, bb, -1);
-        R ea0 = -Fa[5 * N + c10], ea1 = -Fa[5 * N + c11];
-        R eb0 = Fb[6 * N + c01], eb1 = Fb[6 * N + c11];
-        R fa0 = Fa[c10], fa1 = Fa[c11];
-        R fb0 = Fb[c01], fb1 = Fb[c11];
-        R cc00 = -(W[(1 + a) * N + c00] * W[(5 + bb) * N + c00] - W[(1 + bb) * N + c00] * W[(5 + a) * N + c00]);
-        R cc10 = -(W[(1 + a) * N + c10] * W[(5 + bb) * N + c10] - W[(1 + bb) * N + c10] * W[(5 + a) * N + c10]);
-        R cc01 = -(W[(1 + a) * N + c01] * W[(5 + bb) * N + c01] - W[(1 + bb) * N + c01] * W[(5 + a) * N + c01]);
-        R cc11 = -(W[(1 + a) * N + c11] * W[(5 + bb) * N + c11] - W[(1 + bb) * N + c11] * W[(5 + a) * N + c11]);
-        R hib = upwind(fa1, cc01 - eb0, cc11 - eb1);
-        R lob = upwind(fa0, eb0 - cc00, eb1 - cc10);
-        R hia = upwind(fb1, cc10 - ea0, cc11 - ea1);
-        R loa = upwind(fb0, ea0 - cc00, ea1 - cc01);
-        E[cax * N + q] = R(0.25) * (ea0 + ea1 + eb0 + eb1) + R(0.25) * (lob - hib) + R(0.25) * (loa - hia);
+    for (int d = 0; d < 3; d++) {
+        const R* Fd = F + (long long)d * 7 * N;
+        s.v[3 + 3 * d] = Fd[c];
+        s.v[4 + 3 * d] = Fd[5 * N + c];
+        s.v[5 + 3 * d] = Fd[6 * N + c];
     }
+}
+
+// EMF_THREADS = 320 >= EPL = 297: one staged cell per thread, so a plane
+// is one round of loads; the loads of plane k+1 are issued before the edges
+// of plane k are computed and stored to shared memory after them.
+template <class R>
+__global__ void __launch_bounds__(EMF_THREADS) k_emf(Boxes B, const R* __restrict__ F, const R* __restrict__ W,
+                                                     R* __restrict__ E)
+{
+    extern __shared__ unsigned char smem_raw[];
+    R* sm = reinterpret_cast<R*>(smem_raw);    // [3 slots][ENV][EPL]
+    const long long N = B.N;
+    const int tid = threadIdx.x;
+    const int tx = tid % ETX, ty = tid / ETX;  // edge cell of the threads tid < ETX * ETY
+    const int q = (ty + 1) * EHX + (tx + 1);   // its index in the staged plane
+    const bool stager = tid < EPL;
+    const int hx = tid % EHX, hy = tid / EHX;  // staged cell of the threads tid < EPL
+    for (int tile = blockIdx.x; tile < B.netile; tile += gridDim.x) {
+        const BoxDev g = B.b[box_of_etile(B, tile)];
+        const int ntx = (g.nx + ETX - 1) / ETX, nty = (g.ny + ETY - 1) / ETY;
+        int bl = tile - g.etile0;
+        const int x0 = (bl % ntx) * ETX;
+        bl /= ntx;
+        const int y0 = (bl % nty) * ETY;
+        const int z0 = (bl / nty) * EZC;
+        const int z1 = z0 + EZC < g.nz ? z0 + EZC : g.nz;
+        const bool mine = tid < ETX * ETY && x0 + tx < g.nx && y0 + ty < g.ny;
+        const int si = wrapi(x0 - 1 + hx, g.nx), sj = wrapi(y0 - 1 + hy, g.ny);
+        EmfStage<R> st;
+        if (stager) emf_load(F, W, N, cell_of(g, si, sj, wrapi(z0 - 1, g.nz)), st);
+        for (int k = z0 - 1; k < z1; k++) {
+            R* P = sm + ((k + 3) % 3) * ENV * EPL;
+            if (stager) {
+#pragma unroll
+                for (int f = 0; f < ENV; f++) P[f * EPL + tid] = st.v[f];
+            }
+            __syncthreads();
+            if (stager && k + 1 < z1) emf_load(F, W, N, cell_of(g, si, sj, k + 1), st);
+            if (k >= z0 && mine) {
+                const R* P1 = P;
+                const R* P0 = sm + ((k + 2) % 3) * ENV * EPL;
+                const long long c = cell_of(g, x0 + tx, y0 + ty, k);
+                // Ex: a = y, b = z.  c01 = y-1, c10 = z-1
+                {
+                    const R* X1 = P1 + 0 * EPL; const R* X0 = P0 + 0 * EPL;
+                    R ea0 = -P0[7 * EPL + q], ea1 = -P1[7 * EPL + q];            // -F_y[B_z]
+                    R eb0 = P1[11 * EPL + q - EHX], eb1 = P1[11 * EPL + q];      //  F_z[B_y]
+                    R fa0 = P0[6 * EPL + q], fa1 = P1[6 * EPL + q];
+                    R fb0 = P1[9 * EPL + q - EHX], fb1 = P1[9 * EPL + q];
+                    E[c] = edge_e(X1 + q, X1 + q - EHX, X0 + q, X0 + q - EHX, ea0, ea1, eb0, eb1, fa0, fa1, fb0, fb1);
+                }
+                // Ey: a = z, b = x.  c01 = z-1, c10 = x-1
+                {
+                    const R* Y1 = P1 + 1 * EPL; const R* Y0 = P0 + 1 * EPL;
+                    R ea0 = -P1[10 * EPL + q - 1], ea1 = -P1[10 * EPL + q];      // -F_z[B_x]
+                    R eb0 = P0[5 * EPL + q], eb1 = P1[5 * EPL + q];              //  F_x[B_z]
+                    R fa0 = P1[9 * EPL + q - 1], fa1 = P1[9 * EPL + q];
+                    R fb0 = P0[3 * EPL + q], fb1 = P1[3 * EPL + q];
+                    E[N + c] = edge_e(Y1 + q, Y0 + q, Y1 + q - 1, Y0 + q - 1, ea0, ea1, eb0, eb1, fa0, fa1, fb0, fb1);
+                }
+                // Ez: a = x, b = y.  c01 = x-1, c10 = y-1
+                {
+                    const R* Z1 = P1 + 2 * EPL;
+                    R ea0 = -P1[4 * EPL + q - EHX], ea1 = -P1[4 * EPL + q];      // -F_x[B_y]
+                    R eb0 = P1[8 * EPL + q - 1], eb1 = P1[8 * EPL + q];          //  F_y[B_x]
+                    R fa0 = P1[3 * EPL + q - EHX], fa1 = P1[3 * EPL + q];
+                    R fb0 = P1[6 * EPL + q - 1], fb1 = P1[6 * EPL + q];
+                    E[2 * N + c] = edge_e(Z1 + q, Z1 + q - 1, Z1 + q - EHX, Z1 + q - 1 - EHX, ea0, ea1, eb0, eb1, fa0,
+                                          fa1, fb0, fb1);
+                }
+            }
+        }
+        __syncthreads();   // the next tile restages every slot
     }
 }
 
@@ -567,7 +679,8 @@ __global__ void __launch_bounds__(CELL_THREADS) k_half(Boxes B, StateP<TU, TE> s
     TE rho = TE(s.rho[c]) - r * du[0];
     TE mx = TE(s.m[0][c]) - r * du[1], my = TE(s.m[1][c]) - r * du[2], mz = TE(s.m[2][c]) - r * du[3];
     TE e = s.e[c] - r * du[4];
-    TE vx = mx / rho, vy = my / rho, vz = mz / rho;
+    const TE irho = TE(1) / rho;
+    TE vx = mx * irho, vy = my * irho, vz = mz * irho;
     TE p = TE(gam - 1.0) * (e - TE(0.5) * rho * (vx * vx + vy * vy + vz * vz)
                             - TE(0.5) * (bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]));
     if (pfloor > 0.0 && p < TE(pfloor)) p = TE(pfloor);
@@ -679,7 +792,8 @@ __global__ void __launch_bounds__(CELL_THREADS) k_ctu_correct(Boxes B, int d, co
             q[5 + e2] -= r * df[6];
         }
         R rho = q[0];
-        R vx = q[1] / rho, vy = q[2] / rho, vz = q[3] / rho;
+        const R irho = R(1) / rho;
+        R vx = q[1] * irho, vy = q[2] * irho, vz = q[3] * irho;
         R p = gm1 * (q[4] - R(0.5) * rho * (vx * vx + vy * vy + vz * vz)
                      - R(0.5) * (q[5] * q[5] + q[6] * q[6] + q[7] * q[7]));
         R vg[3] = {vx, vy, vz};
@@ -762,6 +876,155 @@ static __global__ void k_finish_diag(Boxes B, const double* __restrict__ part, d
         a = f == 0 ? fmax(a, x) : a + x;
     }
     out[b * 10 + f] = a;
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostics of the ABC relaxation and the refinement tests (Sec. 4.3, 4.5):
+// per virtual block the sums of e, of B_f^2/2 over the cell's three faces and
+// of |M|^2/(2 rho), the maximum of dx |J_cc| / |B_cc| and of dx |J_cc|, and
+// the count of cells with dx |J_cc| / |B_cc| > thr.  dx J on an edge along a
+// is (B_c(c) - B_c(c - e_b)) - (B_b(c) - B_b(c - e_c)), b = a+1, c = a+2
+// (Stokes on the four faces around the edge); J_cc is the mean of the cell's
+// four edges along each axis.  All in FP64.
+// ---------------------------------------------------------------------------
+template <class TE>
+__device__ __forceinline__ double edge_j(const BoxDev& g, TE* const* b, int i, int j, int k, int a)
+{
+    const int bb = a == 2 ? 0 : a + 1, cc = a == 0 ? 2 : a - 1;
+    const long long c = cell_of(g, i, j, k);
+    return ((double)b[cc][c] - (double)b[cc][nbr(g, i, j, k, bb, -1)])
+         - ((double)b[bb][c] - (double)b[bb][nbr(g, i, j, k, cc, -1)]);
+}
+
+template <class TU, class TE>
+__global__ void __launch_bounds__(CELL_THREADS) k_energies(Boxes B, StateP<TU, TE> s, double thr,
+                                                           double* __restrict__ part)
+{
+    // part: [nvblk][6]: sum e, sum B_f^2/2, sum |M|^2/(2 rho), max dx|J|/|B|, count, max dx|J|
+    __shared__ double red[CELL_THREADS];
+    for (long long v = blockIdx.x; v < B.nvblk; v += gridDim.x) {
+        const BoxDev g = B.b[box_of_vblk(B, v)];
+        const long long lc = (v - g.vblk0) * CELL_THREADS + threadIdx.x;
+        double acc[6] = {0, 0, 0, 0, 0, 0};
+        if (lc < g.n) {
+            int i, j, k;
+            coords(g, lc, i, j, k);
+            const long long c = g.off + lc;
+            const double rho = (double)s.rho[c];
+            const double m0 = (double)s.m[0][c], m1 = (double)s.m[1][c], m2 = (double)s.m[2][c];
+            acc[0] = (double)s.e[c];
+            acc[2] = 0.5 * (m0 * m0 + m1 * m1 + m2 * m2) / rho;
+            double jc2 = 0.0, bc2 = 0.0, ub = 0.0;
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                const int bb = a == 2 ? 0 : a + 1, cc = a == 0 ? 2 : a - 1;
+                const double bf = (double)s.b[a][c];
+                ub += 0.5 * bf * bf;
+                int ib = i, jb = j, kb = k, ic = i, jc = j, kc = k;
+                if (bb == 0) ib = wrapi(i + 1, g.nx); else if (bb == 1) jb = wrapi(j + 1, g.ny); else kb = wrapi(k + 1, g.nz);
+                if (cc == 0) ic = wrapi(i + 1, g.nx); else if (cc == 1) jc = wrapi(j + 1, g.ny); else kc = wrapi(k + 1, g.nz);
+                int ibc = ib, jbc = jb, kbc = kb;
+                if (cc == 0) ibc = wrapi(ib + 1, g.nx); else if (cc == 1) jbc = wrapi(jb + 1, g.ny); else kbc = wrapi(kb + 1, g.nz);
+                const double ja = 0.25 * (edge_j(g, s.b, i, j, k, a) + edge_j(g, s.b, ib, jb, kb, a) +
+                                          edge_j(g, s.b, ic, jc, kc, a) + edge_j(g, s.b, ibc, jbc, kbc, a));
+                const double bcen = 0.5 * (bf + (double)s.b[a][nbr(g, i, j, k, a, 1)]);
+                jc2 += ja * ja;
+                bc2 += bcen * bcen;
+            }
+            acc[1] = ub;
+            const double jm = sqrt(jc2), r = jm / sqrt(bc2);
+            acc[3] = r;
+            acc[4] = r > thr ? 1.0 : 0.0;
+            acc[5] = jm;
+        }
+        for (int f = 0; f < 6; f++) {
+            red[threadIdx.x] = acc[f];
+            __syncthreads();
+            const bool mx = f == 3 || f == 5;
+            for (int o = CELL_THREADS / 2; o > 0; o >>= 1) {
+                if (threadIdx.x < o)
+                    red[threadIdx.x] = mx ? fmax(red[threadIdx.x], red[threadIdx.x + o]) : red[threadIdx.x] + red[threadIdx.x + o];
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) part[v * 6 + f] = red[0];
+            __syncthreads();
+        }
+    }
+}
+
+static __global__ void k_finish_energies(Boxes B, const double* __restrict__ part, double* __restrict__ out)
+{
+    const int b = blockIdx.x;
+    const int f = threadIdx.x;
+    if (b >= B.nbox || f >= 6) return;
+    const long long v0 = B.b[b].vblk0;
+    const long long v1 = b + 1 < B.nbox ? B.b[b + 1].vblk0 : B.nvblk;
+    const bool mx = f == 3 || f == 5;
+    double a = 0.0;
+    for (long long v = v0; v < v1; v++) {
+        double x = part[v * 6 + f];
+        a = mx ? fmax(a, x) : a + x;
+    }
+    out[b * 6 + f] = a;
+}
+
+// ---------------------------------------------------------------------------
+// Magnetic helicity (Sec. 4.5) of one box: the cell-centre field in FP64
+// (mean of the two faces per axis) is transformed by a real-to-complex 3-D
+// DFT (cuFFT); on the half spectrum, A_k = i k x B_k / |k|^2 (Coulomb gauge,
+// no A for k = 0) and H = dx^3 / n sum_k w_k Re(conj(A_k) . B_k), w_k = 2 for
+// the modes whose conjugates the half spectrum leaves out, else 1.
+// ---------------------------------------------------------------------------
+template <class TE>
+__global__ void k_bcc(BoxDev g, const TE* __restrict__ b0, const TE* __restrict__ b1, const TE* __restrict__ b2,
+                      double* __restrict__ out)
+{
+    for (long long lc = blockIdx.x * (long long)blockDim.x + threadIdx.x; lc < g.n;
+         lc += (long long)gridDim.x * blockDim.x) {
+        int i, j, k;
+        coords(g, lc, i, j, k);
+        const long long c = g.off + lc;
+        out[lc] = 0.5 * ((double)b0[c] + (double)b0[nbr(g, i, j, k, 0, 1)]);
+        out[g.n + lc] = 0.5 * ((double)b1[c] + (double)b1[nbr(g, i, j, k, 1, 1)]);
+        out[2 * g.n + lc] = 0.5 * ((double)b2[c] + (double)b2[nbr(g, i, j, k, 2, 1)]);
+    }
+}
+
+// Bk: 3 half spectra of nz x ny x (nx/2+1) complex values (re, im pairs)
+static __global__ void k_helicity_part(int nx, int ny, int nz, double dx, const double2* __restrict__ Bk,
+                                       double* __restrict__ part)
+{
+    __shared__ double red[256];
+    const int nxh = nx / 2 + 1;
+    const long long m = (long long)nz * ny * nxh;
+    const double two_pi = 6.283185307179586;
+    const double kfx = two_pi / (nx * dx), kfy = two_pi / (ny * dx), kfz = two_pi / (nz * dx);
+    double acc = 0.0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < m; q += (long long)gridDim.x * blockDim.x) {
+        const int ix = (int)(q % nxh);
+        const long long r = q / nxh;
+        const int iy = (int)(r % ny), iz = (int)(r / ny);
+        const int my = iy <= ny / 2 ? iy : iy - ny, mz = iz <= nz / 2 ? iz : iz - nz;
+        if (ix == 0 && my == 0 && mz == 0) continue;
+        const double kx = kfx * ix, ky = kfy * my, kz = kfz * mz;
+        const double k2 = kx * kx + ky * ky + kz * kz;
+        const double2 bx = Bk[q], by = Bk[m + q], bz = Bk[2 * m + q];
+        // c = k x B (complex); A = i c / k2 = (-Im c, Re c) / k2
+        const double cxr = ky * bz.x - kz * by.x, cxi = ky * bz.y - kz * by.y;
+        const double cyr = kz * bx.x - kx * bz.x, cyi = kz * bx.y - kx * bz.y;
+        const double czr = kx * by.x - ky * bx.x, czi = kx * by.y - ky * bx.y;
+        // Re(conj(A).B) = (A_re B_re + A_im B_im) summed, A_re = -c_im/k2, A_im = c_re/k2
+        const double v = (-cxi * bx.x + cxr * bx.y - cyi * by.x + cyr * by.y - czi * bz.x + czr * bz.y) / k2;
+        const double w = (ix == 0 || (nx % 2 == 0 && ix == nx / 2)) ? 1.0 : 2.0;
+        acc += w * v;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
 // ---------------------------------------------------------------------------

@@ -324,7 +324,7 @@ static void run_step_learned(mhd_ctx* c, bool device_dt)
             c->sel_cnt + 2 * d + 1);
     }
     prof_mark(c, 2);
-    k_emf<R><<<nb, CELL_THREADS, 0, st>>>(g, F1, W, E);
+    k_emf<R><<<emf_grid<R>(c), EMF_THREADS, emf_smem_bytes<R>(), st>>>(g, F1, W, E);
     prof_mark(c, 3);
     k_half<R, float, float><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2], Wh, c->sch.pfloor);
     prof_mark(c, 4);
@@ -337,7 +337,7 @@ static void run_step_learned(mhd_ctx* c, bool device_dt)
             c->sel_cnt + 2 * d + 1);
     }
     prof_mark(c, 5);
-    k_emf<R><<<nb, CELL_THREADS, 0, st>>>(g, F1, Wh, E);
+    k_emf<R><<<emf_grid<R>(c), EMF_THREADS, emf_smem_bytes<R>(), st>>>(g, F1, Wh, E);
     prof_mark(c, 6);
     k_full<R, float, float><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc);
     prof_mark(c, 7);

@@ -114,12 +114,14 @@ extern "C" mhd_status mhd_step_noalloc(const mhd_grid* grid, double gamma, const
     hb.inv_dx = (float)(1.0 / grid->dx);
     const int tl = 8;
     hb.tile0[0] = hb.tile0[1] = hb.tile0[2] = 0;
+    hb.etile0 = 0;
     c.B.b = dbox;
     c.B.nbox = 1;
     c.B.tl = tl;
     c.B.N = n;
     c.B.nvblk = (n + CELL_THREADS - 1) / CELL_THREADS;
     for (int d = 0; d < 3; d++) c.B.ntile[d] = tiles_of_box(hb.nx, hb.ny, hb.nz, d, tl);
+    c.B.netile = emf_tiles_of_box(hb.nx, hb.ny, hb.nz);
     int nsm = 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return reject(MHD_ECUDA, "mhd_step_noalloc: device query failed");

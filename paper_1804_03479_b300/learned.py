@@ -6,8 +6,10 @@ path (PLM in primitive variables + HLLE) from that state stays within tau of
 one step of the full path (characteristic PPM + HLLD) on every stored field
 of the block (mhd_block_error), else 0.  The states come from the method
 itself: ABC fields (Eq. 20) at several wave numbers and plasma beta, ABC
-fields with Sedov-type blasts, and Orszag-Tang vortices (Eq. 18), each
-advanced by the full path and sampled at several times.  The network is
+fields with Sedov-type blasts, Orszag-Tang vortices (Eq. 18), the perturbed
+ABC state of the relaxation run (Eqs. 21-23) and the magnetised blast with
+its density noise (Eq. 19), each advanced by the full path and sampled at
+several times.  The network is
 trained on the GPU by the library's own forward, backward and Adam kernels.
 """
 from __future__ import annotations
@@ -37,6 +39,10 @@ def training_ics(n=128, seed=7):
         ics.append(I.abc_blasts(n, kmult=int(rng.integers(1, 4)), beta=float(rng.choice([0.1, 0.5])), nblast=nb, E=E,
                                 radius=0.05, seed=int(rng.integers(1 << 30))))
     ics.append(I.orszag_tang(n, nz=n))
+    # the ABC relaxation run's perturbed state (Eqs. 21-23) and the magnetised
+    # blast with its density noise (Eq. 19)
+    ics.append(I.abc_perturbed(n, kmult=2, beta=1.0))
+    ics.append(I.mhd_blast(n, r0=0.08, theta0=85.0, phi0=45.0, density_noise=True))
     return ics
 
 

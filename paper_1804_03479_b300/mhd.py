@@ -32,7 +32,7 @@ EXPORTS = ["mhd_init", "mhd_set_state", "mhd_get_state", "mhd_cfl_dt", "mhd_step
            "mhd_get_sweep_config", "mhd_autotune", "mhd_mlp_create", "mhd_mlp_free", "mhd_mlp_nparam",
            "mhd_mlp_set_weights", "mhd_mlp_get_weights", "mhd_mlp_grad", "mhd_mlp_train_step",
            "mhd_mlp_predict", "mhd_nblocks", "mhd_block_features", "mhd_block_error", "mhd_set_selector",
-           "mhd_selector_stats", "mhd_floor_count"]
+           "mhd_selector_stats", "mhd_floor_count", "mhd_energies", "mhd_helicity"]
 GROUPS = ["prim_cfl", "predictor_sweeps", "emf1", "half_update", "corrector_sweeps", "emf2", "full_update"]
 
 
@@ -126,15 +126,17 @@ def lib():
         getattr(L, name).restype = ctypes.c_int
     L.mhd_profile_begin.argtypes = [vp, ip]
     L.mhd_profile_end.argtypes = [vp, dp, ip, ctypes.POINTER(ctypes.c_int)]
-    for name in ["mhd_init", "mhd_set_state", "mhd_get_state", "mhd_cfl_dt", "mhd_step", "mhd_advance",
-                 "mhd_last_dt", "mhd_divB", "mhd_sums", "mhd_sync", "mhd_launches_per_step",
-                 "mhd_profile_begin", "mhd_profile_end", "mhd_step_noalloc", "mhd_init_batch", "mhd_nbox",
-           "mhd_set_state_box", "mhd_get_state_box", "mhd_step_boxes", "mhd_set_sweep_config",
-           "mhd_get_sweep_config", "mhd_autotune", "mhd_mlp_create", "mhd_mlp_free", "mhd_mlp_nparam",
-           "mhd_mlp_set_weights", "mhd_mlp_get_weights", "mhd_mlp_grad", "mhd_mlp_train_step",
-           "mhd_mlp_predict", "mhd_nblocks", "mhd_block_features", "mhd_block_error", "mhd_set_selector",
-           "mhd_selector_stats", "mhd_floor_count"]:
-        getattr(L, name).restype = ctypes.c_int
+    L.mhd_energies.argtypes = [vp, ctypes.c_double, dp]
+    L.mhd_helicity.argtypes = [vp, dp]
+    # every entry point that returns an mhd_status; the others got their
+    # restype above (long long, int, void, const char*)
+    other = {"mhd_bad_cell", "mhd_clear_error", "mhd_device_bytes", "mhd_floor_count", "mhd_free",
+             "mhd_last_error", "mhd_launches_per_step", "mhd_mlp_free", "mhd_mlp_nparam", "mhd_nblocks",
+             "mhd_nbox"}
+    for name in EXPORTS:
+        if name not in other:
+            getattr(L, name).restype = ctypes.c_int
+    L.mhd_launches_per_step.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -257,6 +259,25 @@ class Solver:
 
     def sums(self):
         return self.sums_boxes()[0]
+
+    def energies_boxes(self, jb_threshold=1.0):
+        """per box: E_T, U_B, U_V, max dx|J|/|B|, cells above jb_threshold, max |J|"""
+        out = (ctypes.c_double * (6 * self.nbox))()
+        self._check(lib().mhd_energies(self.h, ctypes.c_double(jb_threshold), out))
+        return np.array(out[:]).reshape(self.nbox, 6)
+
+    def helicities(self):
+        """magnetic helicity of every box (cuFFT, Coulomb gauge)"""
+        out = (ctypes.c_double * self.nbox)()
+        self._check(lib().mhd_helicity(self.h, out))
+        return np.array(out[:])
+
+    def helicity(self):
+        return float(self.helicities()[0])
+
+    def energies(self, jb_threshold=1.0):
+        e = self.energies_boxes(jb_threshold)[0]
+        return dict(E_T=e[0], U_B=e[1], U_V=e[2], jb_max=e[3], n_above=int(e[4]), j_max=e[5])
 
     def set_sweep_config(self, tile_len, blocks_per_sm):
         self._check(lib().mhd_set_sweep_config(self.h, tile_len, blocks_per_sm))

@@ -58,3 +58,15 @@ def test_null_context_calls_are_safe(lib):
     assert lib.mhd_step(None, 0.1) == mhd.MHD_EINVAL
     assert lib.mhd_sync(None) == mhd.MHD_EINVAL
     lib.mhd_free(None)
+
+
+def test_binding_return_types_match_header(lib):
+    """the ctypes restype of every entry point is the header's return type"""
+    src = open(os.path.join(ROOT, "include", "mhd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    want = {"mhd_status": ctypes.c_int, "int": ctypes.c_int, "long long": ctypes.c_longlong,
+            "void": None, "const char*": ctypes.c_char_p}
+    decls = re.findall(r"^(mhd_status|int|long long|void|const char\*)\s+(mhd_[a-zA-Z0-9_]+)\s*\(", src, flags=re.M)
+    assert len(decls) == len(header_functions())
+    for ret, name in decls:
+        assert getattr(lib, name).restype == want[ret], (name, ret, getattr(lib, name).restype)

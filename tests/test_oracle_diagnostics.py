@@ -70,3 +70,37 @@ def test_force_free_refinement_ratio():
     W = orc.prim(st.U, st.B, st.gamma)
     bmax = float(np.sqrt(W[5] ** 2 + W[6] ** 2 + W[7] ** 2).max())
     assert d["j_max"] <= st.meta["k"] * bmax * 1.001
+
+
+@pytest.mark.parametrize("n,kmult", [(16, 1), (24, 2), (32, 3)])
+def test_abc_helicity_closed_form(n, kmult):
+    """H = (A^2+B^2+C^2) L^4 / (2 pi n) (Sec. 4.5) for the ABC field; the
+    cell-centre field of the discrete state is sinc(k dx/2) times the point
+    field, so the discrete helicity carries sinc^2"""
+    st = I.abc(n, kmult=kmult, beta=1.0, noise=0.0)
+    k, a, dx = st.meta["k"], st.meta["A"], st.dx
+    h = orc.helicity(st.B, dx)
+    want = 3 * a * a / (2 * math.pi * kmult) * sinc(0.5 * k * dx) ** 2
+    assert abs(h - want) <= 1e-12 * want
+    # U_B = H k / 2 for the force-free state (both carry sinc^2)
+    assert abs(orc.energies(st.U, st.B, dx, 1.0)["U_B"] - 0.5 * k * h) <= 1e-12 * h * k
+
+
+def test_helicity_of_plane_polarised_and_mean_fields_is_zero():
+    n = 16
+    dx = 1.0 / n
+    st = I.uniform(n)                                   # uniform B: the mean field has no potential
+    assert abs(orc.helicity(st.B, dx)) <= 1e-15
+    xf = np.arange(n) * dx
+    B = np.zeros((3, n, n, n))
+    B[1] = np.sin(2 * np.pi * (xf + 0.5 * dx))[None, None, :] * np.ones((n, n, 1))   # By(x): linear polarisation
+    assert abs(orc.helicity(B, dx)) <= 1e-15
+    # a circularly polarised wave (By, Bz) = (cos kx, sin kx) has H = -/+ L^3 / k
+    c = (np.arange(n) + 0.5) * dx
+    k = 2 * np.pi
+    Bc = np.zeros((3, n, n, n))
+    Bc[1] = np.cos(k * c)[None, None, :]
+    Bc[2] = np.sin(k * c)[None, None, :]
+    # faces hold the same values (By, Bz do not vary along y, z)
+    h = orc.helicity(Bc, dx)
+    assert abs(abs(h) - 1.0 / k) <= 1e-12
