@@ -34,21 +34,38 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-updates/s at 256³ ABC MHD (FP64 plain vs FP32/learned) + HBM roofline %"
 UNIT = "cell-updates/s"
 PAPER_P100 = {"fp32": 1.2e8, "fp64": 5.5e7}   # Sec. 5.2 (i), Tesla P100, VL + PLM + Roe
-GROUPS = ["prim_cfl", "predictor_sweeps", "emf1", "half_update", "corrector_sweeps", "emf2", "full_update"]
+# the step's kernel groups as the library's profiler reports them (one per
+# sweep axis) and their aggregation into the seven stages of the step
+AXES = ("x", "y", "z")
+STAGES = ["prim_cfl", "predictor_sweeps", "emf1", "half_update", "corrector_sweeps", "emf2", "full_update"]
+
+
+def stages_of(groups):
+    """per-axis sweep groups summed into the seven stages"""
+    out = {}
+    for k, v in groups.items():
+        for st in ("predictor", "corrector"):
+            if k.startswith(st + "_"):
+                k = st + "_sweeps"
+        out[k] = out.get(k, 0.0) + v
+    return {k: out[k] for k in STAGES if k in out}
 SIZES = {"fp64": (8, 8, 8), "fp32": (4, 4, 4), "mixed": (4, 8, 4)}   # (rho/M, e/B, arithmetic) bytes
-# Algorithmic floating-point operations per face of one corrector sweep launch
-# (one cell's characteristic PLM reconstruction and one Roe solve): the
-# FADD + FMUL + 2 FFMA count that ncu reports for the FP32 build at 160^3
-# (x sweep), where every divide and square root is a single MUFU op.  The
-# same algorithm runs in the FP64 build, whose divides and square roots
-# expand into FMA iterations (1632 executed FP64 flops per face at 128^3), so
-# the algorithmic figure is used for all precisions.
-FLOPS_PER_FACE = {"fp32": 1002.0, "fp64": 1002.0, "mixed": 1002.0}
-# DRAM bytes (read + write) per face of one corrector sweep launch, from
-# dram__bytes_read.sum + dram__bytes_write.sum of the same captures
-# (FP32: 237.1 MB per launch at 160^3; FP64: 238.8 MB per launch at 128^3),
-# scaled to other sizes by the number of faces.
-TRAFFIC_PER_FACE = {"fp32": 57.9, "fp64": 113.9}
+# Algorithmic floating-point operations per face of one VL + PLM + Roe sweep
+# launch: corrector = one cell's characteristic PLM reconstruction and one
+# Roe solve, predictor = one Roe solve.  They are the FADD + FMUL + 2 FFMA
+# counts that ncu reports for the FP32 build at 160^3 (x sweeps), where every
+# divide and square root is a single MUFU op.  The same algorithm runs in the
+# FP64 build, whose divides and square roots expand into FMA iterations (1632
+# executed FP64 flops per corrector face at 128^3), so the algorithmic
+# figures are used for all precisions.
+FLOPS_PER_FACE = {"corrector": {"fp32": 1002.0, "fp64": 1002.0, "mixed": 1002.0},
+                  "predictor": {"fp32": 689.0, "fp64": 689.0, "mixed": 689.0}}
+# DRAM bytes (read + write) per face of one sweep launch, per kernel, from
+# dram__bytes_read.sum + dram__bytes_write.sum of the ncu captures in
+# profiles/ (tile corrector FP32 237.1 MB at 160^3, FP64 238.8 MB at 128^3;
+# tile predictor FP32 217.8 MB at 160^3), scaled to other sizes by faces.
+TRAFFIC_PER_FACE = {"corrector_tile": {"fp32": 57.9, "fp64": 113.9},
+                    "predictor_tile": {"fp32": 53.2}}
 
 
 def peaks():
@@ -143,8 +160,10 @@ def aggregate_value(world, cells, steps, ms_max):
     return world * cells * steps / (ms_max * 1e-3)
 
 
-def time_variant(torch, mhd, st, prec, scheme, K, W, dist, stream, profile=True):
-    """Device-timed steps of one precision; returns ms/step, group ms and the solver."""
+def time_variant(torch, mhd, st, prec, scheme, K, W, dist, stream, profile=True, tune=True):
+    """Device-timed steps of one precision; returns ms/step, group ms and the
+    solver.  With tune, the library's autotuner first picks the sweep tiling
+    (and, for VL, pencils) on this state; its choice is in s.tuned."""
     integ, recon, riemann = scheme
     cast = torch.float32 if prec == "fp32" else torch.float64
     U = torch.from_numpy(st.U).to(device="cuda", dtype=cast).contiguous()
@@ -152,6 +171,11 @@ def time_variant(torch, mhd, st, prec, scheme, K, W, dist, stream, profile=True)
     s = mhd.Solver(st.U.shape[1:], st.dx, st.gamma, integ, recon, riemann, prec, 0.3, stream=stream.cuda_stream)
     s.set_state(U, B)
     del U, B
+    s.tuned = None
+    if tune:
+        tl, bps, _ = s.autotune(reps=2)
+        mask, plen = s.sweep_pencils()
+        s.tuned = {"tile_len": tl, "blocks_per_sm": bps, "pencil_mask": mask, "pencil_len": plen}
     s.advance(W)
     s.sync()
     if profile:
@@ -173,9 +197,9 @@ def time_variant(torch, mhd, st, prec, scheme, K, W, dist, stream, profile=True)
 
 
 def group_bytes(prec, n):
-    """algorithmic HBM bytes of each kernel group of one VL step on n cells:
-    every array element a kernel needs is read once and every result written
-    once (neighbour re-reads assumed to hit in cache)"""
+    """algorithmic HBM bytes of each stage of one VL step on n cells: every
+    array element a kernel needs is read once and every result written once
+    (neighbour re-reads assumed to hit in cache)"""
     szu, sze, szr = SIZES[prec]
     u = 4 * szu + 4 * sze          # rho, M (TU) and e, B faces (TE)
     sweep = 8 * szr + sze + 7 * szr    # W and B_n in, 7 flux components out
@@ -183,6 +207,11 @@ def group_bytes(prec, n):
     return {"prim_cfl": n * (u + 8 * szr), "predictor_sweeps": 3 * n * sweep, "emf1": n * emf,
             "half_update": n * (u + 18 * szr + 3 * sze + 8 * szr), "corrector_sweeps": 3 * n * sweep,
             "emf2": n * emf, "full_update": n * (2 * u + 18 * szr)}
+
+
+def sweep_bytes_per_face(prec):
+    szu, sze, szr = SIZES[prec]
+    return 8 * szr + sze + 7 * szr
 
 
 # state bytes per cell update when the state is read once and written once
@@ -214,40 +243,61 @@ def scheme_matrix(torch, mhd, st, steps, stream, pk):
             for recon in ("plm", "ppm"):
                 for riem in ("hlld", "roe"):
                     ms, _, _, s = time_variant(torch, mhd, st, prec, (integ, recon, riem), k, 2, None, stream,
-                                               profile=False)
+                                               profile=False, tune=prec == "fp32")
                     s.free()
                     v = n * k / (ms * 1e-3)
                     out[f"{integ}+{recon}+{riem}/{prec}"] = {
-                        "value": v, "ms_per_step": ms / k, "steps": k,
+                        "value": v, "ms_per_step": ms / k, "steps": k, "sweep": s.tuned,
                         "frac_of_state_roofline": v * STATE_BYTES[prec] / (pk["hbm_gbs"] * 1e9)}
     return out
 
 
-def roofline(prec, groups, steps, n, pk, sm_mhz):
-    """dominant kernel group and its achieved fraction of the roofline that bounds it"""
-    dom = max(groups, key=groups.get)
-    ms = groups[dom] / steps
-    gb = group_bytes(prec, n)
-    out = {"kernel": dom, "ms_per_step": ms, "share": groups[dom] / sum(groups.values())}
-    fpf = FLOPS_PER_FACE.get(prec)
-    if dom.endswith("sweeps") and fpf:
-        flops = 3 * n * fpf
-        ach = flops / (ms * 1e-3) / 1e12
+def kernels_of(groups, tuned):
+    """the step's launches grouped by kernel: each sweep axis belongs to the
+    tile or the pencil kernel of its stage (from the sweep configuration);
+    returns {kernel: (ms summed over its launches, launches per step)}"""
+    mask = (tuned or {}).get("pencil_mask", 0) or 0
+    out = {}
+    for k, v in groups.items():
+        name, nl = k, 1
+        for st in ("predictor", "corrector"):
+            if k.startswith(st + "_"):
+                d = AXES.index(k.split("_")[1])
+                name = f"{st}_{'pencil' if mask >> d & 1 else 'tile'}"
+        ms, cnt = out.get(name, (0.0, 0))
+        out[name] = (ms + v, cnt + nl)
+    return out
+
+
+def roofline(prec, groups, steps, n, pk, sm_mhz, tuned=None):
+    """dominant kernel of the step and its achieved fraction of the roofline
+    that bounds it"""
+    ks = kernels_of(groups, tuned)
+    dom = max(ks, key=lambda k: ks[k][0])
+    tot, launches = ks[dom]
+    ms = tot / steps
+    out = {"kernel": dom, "ms_per_step": ms, "share": tot / sum(groups.values()), "launches": launches,
+           "ms_per_launch": ms / launches}
+    sweep = dom.split("_")[0]
+    fpf = FLOPS_PER_FACE.get(sweep, {}).get(prec)
+    if sweep in ("predictor", "corrector") and fpf:
+        ach = n * fpf / (ms / launches * 1e-3) / 1e12          # per launch: n faces
         peak = alu_peak_tflops(prec, sm_mhz)
-        tpf = TRAFFIC_PER_FACE.get(prec)
-        hbm = gb[dom] / (ms * 1e-3) / 1e9
+        tpf = TRAFFIC_PER_FACE.get(dom, {}).get(prec)
+        bpf = sweep_bytes_per_face(prec)
+        hbm = n * bpf / (ms / launches * 1e-3) / 1e9
         out.update(bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
                    peak_src=f"{'FP64' if prec == 'fp64' else 'FP32'} peak derived from unit counts at {sm_mhz:.0f} MHz",
                    traffic=(tpf * n if tpf else None),
-                   algorithmic=f"{fpf:.0f} flops per face x {n} faces per launch, 3 launches",
-                   launches=3, ms_per_launch=ms / 3,
-                   hbm_view={"algorithmic_bytes_per_launch": gb[dom] // 3, "achieved_gbs": hbm,
+                   algorithmic=f"{fpf:.0f} flops per face x {n} faces per launch",
+                   hbm_view={"algorithmic_bytes_per_launch": n * bpf, "achieved_gbs": hbm,
                              "frac_of_measured": hbm / pk["hbm_gbs"]})
     else:
-        b = gb[dom]
-        ach = b / (ms * 1e-3) / 1e9
+        stage = {"emf1": "emf1", "emf2": "emf2"}.get(dom, dom)
+        b = group_bytes(prec, n)[stage] / launches
+        ach = b / (ms / launches * 1e-3) / 1e9
         out.update(bound="hbm", achieved=ach, peak=pk["hbm_gbs"], unit="GB/s", frac=ach / pk["hbm_gbs"],
-                   peak_src=pk["src"], traffic=None, algorithmic_bytes_per_launch_group=b)
+                   peak_src=pk["src"], traffic=None, algorithmic_bytes_per_launch=b)
     return out
 
 
@@ -385,7 +435,7 @@ def learned_variant(torch, mhd, K, stream):
         s.get_state(U, B)
         states[name] = (U, B)
         out[name] = {"value": st.U[0].size / (ms * 1e-3), "ms_per_step": ms,
-                     "kernel_ms_per_step": {k: v / rec for k, v in groups.items()},
+                     "kernel_ms_per_step": {k: v / rec for k, v in stages_of(groups).items()},
                      "floored_cell_steps": s.floor_count()}
         s.free()
     net.free()
@@ -530,6 +580,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-matrix", action="store_true", help="skip the 16 scheme x precision combinations")
+    ap.add_argument("--no-autotune", action="store_true", help="default sweep tiling instead of the autotuned one")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--stress", action="store_true", help="mixed-precision stress run (not a bench line)")
     ap.add_argument("--stress-steps", type=int, default=500)
@@ -562,7 +613,8 @@ def main():
     stream = torch.cuda.Stream()
     clk = Clocks(local)
     clk.start()
-    ms, groups, rec, s = time_variant(torch, mhd, st, args.precision, scheme, args.steps, args.warmup, dist, stream)
+    ms, groups, rec, s = time_variant(torch, mhd, st, args.precision, scheme, args.steps, args.warmup, dist, stream,
+                                      tune=not args.no_autotune)
     clocks = clk.stop()
     launches = s.launches_per_step() * args.steps
     dev_bytes = s.device_bytes()
@@ -578,10 +630,12 @@ def main():
         "config": {"workload": f"abc{args.n}_k4pi_beta0.5", "grid": [args.n] * 3, "scheme": "+".join(scheme),
                    "precision": args.precision, "cfl": 0.3, "dt": "CFL on device every step",
                    "l2": "state larger than L2 (no flush)", "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
-                   "device_bytes": dev_bytes},
-        "roofline": roofline(args.precision, groups, rec, n, pk, sm_mhz) if rec else None,
+                   "device_bytes": dev_bytes, "sweep": s.tuned},
+        "roofline": roofline(args.precision, groups, rec, n, pk, sm_mhz, s.tuned) if rec else None,
         "hbm_roofline_step": step_hbm(args.precision, n, ms / args.steps, pk),
-        "kernel_ms_per_step": {k: v / rec for k, v in groups.items()} if rec else None,
+        "kernel_ms_per_step": {k: v / rec for k, v in stages_of(groups).items()} if rec else None,
+        "sweep_ms_per_step": {k: v / rec for k, v in groups.items() if "_" in k and k.split("_")[1] in AXES}
+        if rec else None,
         "gpu_launches": launches,
         "clocks": clocks,
     }
@@ -589,14 +643,16 @@ def main():
         variants = {}
         for prec in [p for p in args.variants.split(",") if p and p != args.precision]:
             kv = max(3, min(args.steps, 10))
-            msv, gv, recv, sv = time_variant(torch, mhd, st, prec, scheme, kv, 2, None, stream)
+            msv, gv, recv, sv = time_variant(torch, mhd, st, prec, scheme, kv, 2, None, stream,
+                                             tune=not args.no_autotune)
             sv.free()
             vv = n * kv / (msv * 1e-3)
             variants[prec] = {"value": vv, "unit": UNIT, "ms_per_step": msv / kv, "steps": kv,
                               "vs_p100_paper": vv / PAPER_P100[prec] if prec in PAPER_P100 else None,
-                              "roofline": roofline(prec, gv, recv, n, pk, sm_mhz) if recv else None,
+                              "roofline": roofline(prec, gv, recv, n, pk, sm_mhz, sv.tuned) if recv else None,
                               "hbm_roofline_step": step_hbm(prec, n, msv / kv, pk),
-                              "kernel_ms_per_step": {k: v / recv for k, v in gv.items()} if recv else None}
+                              "kernel_ms_per_step": {k: v / recv for k, v in stages_of(gv).items()} if recv else None,
+                              "sweep": sv.tuned}
         if not args.no_matrix:
             variants["schemes256"] = scheme_matrix(torch, mhd, st, max(3, min(args.steps, 10)), stream, pk)
         if not args.no_batch:

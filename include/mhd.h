@@ -155,24 +155,41 @@ mhd_status mhd_helicity(mhd_ctx* ctx, double* h);
 /* Face-sweep tiling: tiles of 32 x tile_len faces (tile_len 4, 8 or 16),
  * blocks_per_sm x SMs persistent blocks.  mhd_autotune times every pair on
  * the context's own batch (reps steps each, the state restored after each
- * trial), keeps the fastest and reports it (ms per step in *ms_best).  The
- * autotuner allocates a temporary copy of the state. */
+ * trial), and for the VL integrator also the pencil sweeps below (on all
+ * axes or on y and z, segment lengths 8, 16, 32); it keeps the fastest and
+ * reports the tiling (ms per step in *ms_best; the pencil choice through
+ * mhd_get_sweep_pencils).  The autotuner allocates a temporary copy of the
+ * state. */
 mhd_status mhd_set_sweep_config(mhd_ctx* ctx, int tile_len, int blocks_per_sm);
 mhd_status mhd_get_sweep_config(mhd_ctx* ctx, int* tile_len, int* blocks_per_sm);
 mhd_status mhd_autotune(mhd_ctx* ctx, int reps, int* tile_len, int* blocks_per_sm, double* ms_best);
+
+/* Pencil sweeps (VL integrator): on every axis d with bit d of pencil_mask
+ * set, the predictor and corrector face sweeps keep the cells around each
+ * face in registers (no shared memory): along y and z one thread walks a
+ * segment of pencil_len consecutive faces of a grid line; along x the 32
+ * lanes of a warp hold 32 consecutive cells of a row and exchange
+ * neighbour states by shuffles (27 to 31 faces per warp).  The results are
+ * those of the tile sweeps (the same arithmetic per face).  pencil_mask in
+ * [0, 7] (0: tiles everywhere; default 6 = y and z, with pencil_len 32, for
+ * VL contexts, 0 for CTU), pencil_len in [1, 1024], else MHD_EINVAL; a
+ * non-zero mask with the CTU integrator: MHD_EUNSUPPORTED. */
+mhd_status mhd_set_sweep_pencils(mhd_ctx* ctx, int pencil_mask, int pencil_len);
+mhd_status mhd_get_sweep_pencils(mhd_ctx* ctx, int* pencil_mask, int* pencil_len);
 
 /* Wait for all work queued on the context's stream; reports recorded
  * device-side anomalies. */
 mhd_status mhd_sync(mhd_ctx* ctx);
 
 /* Kernel-group timing.  mhd_profile_begin arms CUDA events (on the
- * context's stream) at the boundaries of the 7 kernel groups of each of the
- * next max_steps directly launched steps (not graph replays): 0 primitives
- * + CFL dt, 1 predictor sweeps (3 launches), 2 edge E, 3 half update,
- * 4 corrector sweeps / CTU corrections (3 launches), 5 edge E, 6 full
- * update.  mhd_profile_end synchronises, stops recording and writes the
- * summed milliseconds of each group (ms[ngroups], ngroups <= 7) and the
- * number of steps recorded. */
+ * context's stream) at the boundaries of the 11 kernel groups of each of
+ * the next max_steps directly launched steps (not graph replays):
+ * 0 primitives + CFL dt, 1-3 predictor sweep along x, y, z (CTU: the
+ * traced first-stage sweeps), 4 edge E, 5 half update, 6-8 corrector sweep
+ * along x, y, z (CTU: transverse corrections), 9 edge E, 10 full update.
+ * mhd_profile_end synchronises, stops recording and writes the summed
+ * milliseconds of each group (ms[ngroups], ngroups <= 11) and the number
+ * of steps recorded. */
 mhd_status mhd_profile_begin(mhd_ctx* ctx, int max_steps);
 mhd_status mhd_profile_end(mhd_ctx* ctx, double* ms, int ngroups, int* steps);
 

@@ -31,13 +31,16 @@ static const char* g_init_err = "no error";
 // mhd_last_error(NULL)
 void mhd_internal_set_init_error(const char* msg) { g_init_err = msg; }
 
+// the learned selector's lists follow the sweep layout (mhd_learned.cu)
+mhd_status mhd_internal_selector_lists(mhd_ctx* c);
+
 static void release(mhd_ctx* c)
 {
     void* bufs[] = {c->rho, c->m[0], c->m[1], c->m[2], c->e, c->b[0], c->b[1], c->b[2], c->W, c->Wh,
                     c->F1, c->F2, c->E, c->Bh[0], c->Bh[1], c->Bh[2], c->WM, c->WP, c->stage,
                     c->dt, c->dtc, c->smax, c->smax_part, c->bad, c->nfloor, c->part, c->diag, c->dbox, c->sel_feats,
                     c->sel_flags, c->sel_cnt, c->sel_list[0], c->sel_list[1], c->sel_list[2], c->sel_list[3],
-                    c->sel_list[4], c->sel_list[5]};
+                    c->sel_list[4], c->sel_list[5], c->sel_list[6], c->sel_list[7]};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (c->have_graph) cudaGraphExecDestroy(c->gexec);
@@ -60,6 +63,7 @@ static cudaError_t dalloc(mhd_ctx* c, void** p, size_t bytes)
 static cudaError_t layout_tiles(mhd_ctx* c, int tl)
 {
     int t0[3] = {0, 0, 0}, e0 = 0;
+    long long p0[3] = {0, 0, 0}, w0[3] = {0, 0, 0};
     for (int b = 0; b < c->nbox; b++) {
         BoxDev& x = c->hbox[b];
         for (int d = 0; d < 3; d++) {
@@ -68,7 +72,18 @@ static cudaError_t layout_tiles(mhd_ctx* c, int tl)
         }
         x.etile0 = e0;
         e0 += emf_tiles_of_box(x.nx, x.ny, x.nz);
+        for (int d = 0; d < 3; d++) {
+            x.pth0[d] = p0[d];
+            p0[d] += pencil_threads_of_box(x.nx, x.ny, x.nz, d, c->pencil_len);
+        }
+        for (int q = 0; q < 3; q++) {
+            x.xw0[q] = w0[q];
+            w0[q] += xwarp_items_of_box(x.nx, x.ny, x.nz, q);
+        }
     }
+    c->B.pl = c->pencil_len;
+    for (int d = 0; d < 3; d++) c->B.npth[d] = p0[d];
+    for (int q = 0; q < 3; q++) c->B.nxw[q] = w0[q];
     c->B.tl = tl;
     for (int d = 0; d < 3; d++) c->B.ntile[d] = t0[d];
     c->B.netile = e0;
@@ -143,6 +158,9 @@ static mhd_status init_common(int nbox, const mhd_grid* grids, double gamma, con
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev);
     c->sweep_bps = 4;
+    // VL: pencil sweeps along y and z, tiles along x (the autotuner may change it)
+    c->pencil_mask = scheme->integrator == MHD_VL ? 6 : 0;
+    c->pencil_len = 32;
     c->cell_grid = (int)(vb < 16LL * c->nsm ? vb : 16LL * c->nsm);
     if (c->cell_grid < 1) c->cell_grid = 1;
     if (e == cudaSuccess) {
@@ -496,6 +514,28 @@ extern "C" mhd_status mhd_get_sweep_config(mhd_ctx* c, int* tile_len, int* block
     return MHD_OK;
 }
 
+extern "C" mhd_status mhd_set_sweep_pencils(mhd_ctx* c, int pencil_mask, int pencil_len)
+{
+    if (!c) return MHD_EINVAL;
+    if (pencil_mask < 0 || pencil_mask > 7 || pencil_len < 1 || pencil_len > 1024)
+        return fail(c, MHD_EINVAL, "pencil_mask must be in [0, 7] and pencil_len in [1, 1024]");
+    if (pencil_mask && c->sch.integrator != MHD_VL)
+        return fail(c, MHD_EUNSUPPORTED, "pencil sweeps are built for the VL integrator only");
+    c->pencil_mask = pencil_mask;
+    c->pencil_len = pencil_len;
+    CK(layout_tiles(c, c->B.tl));
+    if (c->sel && mhd_internal_selector_lists(c) != MHD_OK) return fail(c, MHD_ENOMEM, "selector lists");
+    return MHD_OK;
+}
+
+extern "C" mhd_status mhd_get_sweep_pencils(mhd_ctx* c, int* pencil_mask, int* pencil_len)
+{
+    if (!c || !pencil_mask || !pencil_len) return fail(c, MHD_EINVAL, "null pointer");
+    *pencil_mask = c->pencil_mask;
+    *pencil_len = c->pencil_len;
+    return MHD_OK;
+}
+
 // time `reps` directly launched steps of the current configuration
 static mhd_status time_steps(mhd_ctx* c, int reps, float* ms)
 {
@@ -533,25 +573,50 @@ extern "C" mhd_status mhd_autotune(mhd_ctx* c, int reps, int* tile_len, int* blo
     const int tls[3] = {4, 8, 16};
     const int bpss[4] = {1, 2, 4, 8};
     float best = 1e30f;
-    int btl = c->B.tl, bbps = c->sweep_bps;
+    int btl = c->B.tl, bbps = c->sweep_bps, bmask = 0, blen = c->pencil_len;
     mhd_status st = e == cudaSuccess ? MHD_OK : fail(c, MHD_ECUDA, "autotune copy: %s", cudaGetErrorString(e));
+    // one trial: warm-up step, `reps` timed steps, state restored
+    auto trial = [&](float* ms) -> mhd_status {
+        mhd_status s2 = time_steps(c, 1, ms);
+        if (s2 == MHD_OK) s2 = time_steps(c, reps, ms);
+        for (int f = 0; f < 4; f++)
+            cudaMemcpyAsync(fu[f], sv + f * N * c->szu, N * c->szu, cudaMemcpyDeviceToDevice, c->stream);
+        for (int f = 0; f < 4; f++)
+            cudaMemcpyAsync(fe[f], sv + ub + f * N * c->sze, N * c->sze, cudaMemcpyDeviceToDevice, c->stream);
+        return s2;
+    };
+    // tiles on every axis: (tile length, blocks per SM)
+    c->pencil_mask = 0;
     for (int i = 0; i < 3 && st == MHD_OK; i++)
         for (int j = 0; j < 4 && st == MHD_OK; j++) {
             c->sweep_bps = bpss[j];
             if (layout_tiles(c, tls[i]) != cudaSuccess) { st = fail(c, MHD_ECUDA, "autotune layout"); break; }
             float ms = 0.0f;
-            st = time_steps(c, 1, &ms);              // warm-up
-            if (st == MHD_OK) st = time_steps(c, reps, &ms);
-            for (int f = 0; f < 4; f++)
-                cudaMemcpyAsync(fu[f], sv + f * N * c->szu, N * c->szu, cudaMemcpyDeviceToDevice, c->stream);
-            for (int f = 0; f < 4; f++)
-                cudaMemcpyAsync(fe[f], sv + ub + f * N * c->sze, N * c->sze, cudaMemcpyDeviceToDevice, c->stream);
+            st = trial(&ms);
             if (st == MHD_OK && ms < best) { best = ms; btl = tls[i]; bbps = bpss[j]; }
         }
+    // VL: pencils on all axes or on y and z only (x keeps the best tiles), per segment length
+    if (c->sch.integrator == MHD_VL) {
+        const int masks[2] = {7, 6};
+        const int lens[3] = {8, 16, 32};
+        c->sweep_bps = bbps;
+        for (int i = 0; i < 2 && st == MHD_OK; i++)
+            for (int j = 0; j < 3 && st == MHD_OK; j++) {
+                c->pencil_mask = masks[i];
+                c->pencil_len = lens[j];
+                if (layout_tiles(c, btl) != cudaSuccess) { st = fail(c, MHD_ECUDA, "autotune layout"); break; }
+                if (c->sel && mhd_internal_selector_lists(c) != MHD_OK) { st = fail(c, MHD_ENOMEM, "selector lists"); break; }
+                float ms = 0.0f;
+                st = trial(&ms);
+                if (st == MHD_OK && ms < best) { best = ms; bmask = masks[i]; blen = lens[j]; }
+            }
+    }
     cudaStreamSynchronize(c->stream);
     cudaFree(saved);
     if (st != MHD_OK) return st;
     c->sweep_bps = bbps;
+    c->pencil_mask = bmask;
+    c->pencil_len = blen;
     CK(layout_tiles(c, btl));
     if (tile_len) *tile_len = btl;
     if (blocks_per_sm) *blocks_per_sm = bbps;

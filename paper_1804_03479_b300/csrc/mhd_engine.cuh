@@ -21,6 +21,8 @@ struct mhd_ctx {
     mhd::Boxes B;                   // kernel view (points at dbox)
     int nsm;                        // SMs of the device
     int sweep_bps;                  // persistent sweep blocks per SM
+    int pencil_mask;                // VL sweeps by pencils on the axes of these bits
+    int pencil_len;                 // faces per pencil-segment thread
     size_t szu, sze, szr;          // element sizes: rho/M storage, e/B storage, arithmetic
     void* rho;
     void* m[3];
@@ -52,8 +54,10 @@ struct mhd_ctx {
     mhd_mlp* sel;
     float* sel_feats;               // [nblocks][48]
     unsigned char* sel_flags;       // [nblocks], 1 = full path
-    int* sel_cnt;                   // per axis: cheap, full tile counts
-    int* sel_list[6];               // per axis: cheap list, full list
+    int* sel_cnt;                   // per list: entries
+    int* sel_list[8];               // per axis: cheap list, full list (tiles, pencil segments or x-warp
+                                    // items; 6/7: the x corrector's items when x runs by warps)
+    long long sel_cap;              // entries of each list
     cudaGraphExec_t gexec;
     bool have_graph;
     // kernel-group timing (CUDA events on the context stream)
@@ -64,7 +68,7 @@ struct mhd_ctx {
     char err[256];
 };
 
-#define MHD_NGROUPS 7   // prim+dt, predictor sweeps, emf, half, corrector sweeps, emf, full
+#define MHD_NGROUPS 11  // prim+dt, predictor sweeps x/y/z, emf, half, corrector sweeps x/y/z, emf, full
 
 // record the boundary event `b` of the current step when timing is on
 inline void prof_mark(mhd_ctx* c, int b)
@@ -103,6 +107,16 @@ inline int emf_grid(const mhd_ctx* c)
     return c->B.netile < cap ? c->B.netile : cap;
 }
 
+inline int xwarp_grid(const mhd_ctx* c, int slot)
+{
+    return (int)((c->B.nxw[slot] * 32 + PENCIL_THREADS - 1) / PENCIL_THREADS);
+}
+
+inline int pencil_grid(const mhd_ctx* c, int d)
+{
+    return (int)((c->B.npth[d] + PENCIL_THREADS - 1) / PENCIL_THREADS);
+}
+
 inline int sweep_grid(const mhd_ctx* c, int d)
 {
     int cap = c->sweep_bps * c->nsm;
@@ -134,48 +148,66 @@ void run_step(mhd_ctx* c, bool device_dt)
 
     if (INTEG == VL) {
         // VL steps 1-3: first-order fluxes with the face B_n, edge E, half update
-        for (int d = 0; d < 3; d++)
-            k_sweep<R, RECON, SOLVER, 0, TE><<<sweep_grid(c, d), SWEEP_THREADS, 0, st>>>(
-                g, d, W, s.b[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam);
-        prof_mark(c, 2);
+        for (int d = 0; d < 3; d++) {
+            if ((c->pencil_mask >> d & 1) && d == 0)
+                k_xwarp<R, RECON, SOLVER, 0, TE><<<xwarp_grid(c, XW<RECON, 0>::slot), PENCIL_THREADS, 0, st>>>(
+                    g, W, s.b[d], F1, gam, XW<RECON, 0>::slot);
+            else if (c->pencil_mask >> d & 1)
+                k_pencil<R, RECON, SOLVER, 0, TE><<<pencil_grid(c, d), PENCIL_THREADS, 0, st>>>(
+                    g, d, W, s.b[d], F1 + (long long)d * 7 * n, gam);
+            else
+                k_sweep<R, RECON, SOLVER, 0, TE><<<sweep_grid(c, d), SWEEP_THREADS, 0, st>>>(
+                    g, d, W, s.b[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam);
+            prof_mark(c, 2 + d);
+        }
         k_emf<R><<<emf_grid<R>(c), EMF_THREADS, emf_smem_bytes<R>(), st>>>(g, F1, W, E);
-        prof_mark(c, 3);
-        k_half<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2], Wh, c->sch.pfloor);
-        prof_mark(c, 4);
-        // VL steps 4-7: reconstruct at the half step, Riemann, edge E, full update
-        for (int d = 0; d < 3; d++)
-            k_sweep<R, RECON, SOLVER, 1, TE><<<sweep_grid(c, d), SWEEP_THREADS, smem, st>>>(
-                g, d, Wh, Bh[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam);
         prof_mark(c, 5);
-        k_emf<R><<<emf_grid<R>(c), EMF_THREADS, emf_smem_bytes<R>(), st>>>(g, F1, Wh, E);
+        k_half<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2], Wh, c->sch.pfloor);
         prof_mark(c, 6);
+        // VL steps 4-7: reconstruct at the half step, Riemann, edge E, full update
+        for (int d = 0; d < 3; d++) {
+            if ((c->pencil_mask >> d & 1) && d == 0)
+                k_xwarp<R, RECON, SOLVER, 1, TE><<<xwarp_grid(c, XW<RECON, 1>::slot), PENCIL_THREADS, 0, st>>>(
+                    g, Wh, Bh[d], F1, gam, XW<RECON, 1>::slot);
+            else if (c->pencil_mask >> d & 1)
+                k_pencil<R, RECON, SOLVER, 1, TE><<<pencil_grid(c, d), PENCIL_THREADS, 0, st>>>(
+                    g, d, Wh, Bh[d], F1 + (long long)d * 7 * n, gam);
+            else
+                k_sweep<R, RECON, SOLVER, 1, TE><<<sweep_grid(c, d), SWEEP_THREADS, smem, st>>>(
+                    g, d, Wh, Bh[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam);
+            prof_mark(c, 7 + d);
+        }
+        k_emf<R><<<emf_grid<R>(c), EMF_THREADS, emf_smem_bytes<R>(), st>>>(g, F1, Wh, E);
+        prof_mark(c, 10);
         k_full<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc);
-        prof_mark(c, 7);
+        prof_mark(c, 11);
     } else {
         R* WM = (R*)c->WM;
         R* WP = (R*)c->WP;
         // CTU steps 1-2: traced states (+ source terms) and their fluxes
-        for (int d = 0; d < 3; d++)
+        for (int d = 0; d < 3; d++) {
             k_sweep<R, RECON, SOLVER, 2, TE><<<sweep_grid(c, d), SWEEP_THREADS, smem, st>>>(
                 g, d, W, s.b[d], F1 + (long long)d * 7 * n, WM + (long long)d * 7 * n, WP + (long long)d * 7 * n,
                 c->dtc, gam);
-        prof_mark(c, 2);
+            prof_mark(c, 2 + d);
+        }
         // steps 3-4: edge E at t^n, dt/2 update of face B and cell state
         k_emf<R><<<emf_grid<R>(c), EMF_THREADS, emf_smem_bytes<R>(), st>>>(g, F1, W, E);
-        prof_mark(c, 3);
+        prof_mark(c, 5);
         k_half<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2], Wh, c->sch.pfloor);
-        prof_mark(c, 4);
+        prof_mark(c, 6);
         // steps 5-6: transverse correction and corrector fluxes
-        for (int d = 0; d < 3; d++)
+        for (int d = 0; d < 3; d++) {
             k_ctu_correct<R, SOLVER, TE><<<nb, CELL_THREADS, 0, st>>>(g, d, WM + (long long)d * 7 * n,
                                                               WP + (long long)d * 7 * n, W, F1, Bh[d],
                                                               F2 + (long long)d * 7 * n, c->dtc, gam);
-        prof_mark(c, 5);
+            prof_mark(c, 7 + d);
+        }
         // steps 7-8
         k_emf<R><<<emf_grid<R>(c), EMF_THREADS, emf_smem_bytes<R>(), st>>>(g, F2, Wh, E);
-        prof_mark(c, 6);
+        prof_mark(c, 10);
         k_full<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F2, E, c->dtc);
-        prof_mark(c, 7);
+        prof_mark(c, 11);
     }
     if (c->prof_on && c->prof_steps < c->prof_cap) c->prof_steps++;
 }

@@ -25,6 +25,7 @@ constexpr int CELL_THREADS = 256;
 constexpr int TX = 32;             // sweep tile extent along x
 constexpr int SWEEP_THREADS = 256;
 constexpr int TL_MAX = 16;         // largest tile extent along the second tiled axis
+constexpr int PENCIL_THREADS = 128;
 
 struct BoxDev {
     int nx, ny, nz, pad;
@@ -35,6 +36,8 @@ struct BoxDev {
     int tile0[3];       // first sweep tile of the box, per axis
     float inv_dx;       // 1/dx in single precision
     int etile0;         // first edge-field tile of the box
+    long long pth0[3];  // first pencil-segment thread of the box, per axis
+    long long xw0[3];   // first x-warp item of the box: predictor, PLM corrector, PPM corrector
 };
 
 // dt of a box and its ratios to dx, in both precisions; written once per
@@ -80,6 +83,9 @@ struct Boxes {
     long long nvblk;    // virtual blocks of the batch
     int ntile[3];       // sweep tiles of the batch, per axis
     int netile;         // edge-field tiles of the batch
+    int pl;             // pencil segment length (faces per thread)
+    long long npth[3];  // pencil-segment threads of the batch, per axis
+    long long nxw[3];   // x-warp items of the batch: predictor, PLM corrector, PPM corrector
 };
 
 template <class TU, class TE> struct StateP {
@@ -162,6 +168,18 @@ __device__ __forceinline__ void load_rot(const R* __restrict__ W, long long N, l
     bn = W[(5 + d) * N + c];
 }
 
+// kinetic energy |M|^2 / (2 rho) in the energy's type TE: from the velocities
+// when the state has one type, else (the mixed form: FP32 rho, M with an
+// FP64 energy) by one FP64 division, so the pressure recovery is exact to
+// FP64 for the stored FP32 momentum
+template <class TU, class TE>
+__device__ __forceinline__ TE kinetic(TU rho, TU mx, TU my, TU mz, TU vx, TU vy, TU vz)
+{
+    if (sizeof(TU) == sizeof(TE))
+        return TE(0.5) * (TE(mx) * TE(vx) + TE(my) * TE(vy) + TE(mz) * TE(vz));
+    return TE(0.5) * (TE(mx) * TE(mx) + TE(my) * TE(my) + TE(mz) * TE(mz)) / TE(rho);
+}
+
 // positive doubles order like unsigned integers: max-reduce their bits
 __device__ __forceinline__ void atomic_max_pos(unsigned long long* p, double v)
 {
@@ -191,12 +209,12 @@ __global__ void __launch_bounds__(CELL_THREADS) k_prim(Boxes B, StateP<TU, TE> s
             TE bx = TE(0.5) * (s.b[0][c] + s.b[0][nbr(g, i, j, k, 0, 1)]);
             TE by = TE(0.5) * (s.b[1][c] + s.b[1][nbr(g, i, j, k, 1, 1)]);
             TE bz = TE(0.5) * (s.b[2][c] + s.b[2][nbr(g, i, j, k, 2, 1)]);
-            TE rho = TE(s.rho[c]);
-            TE mx = TE(s.m[0][c]), my = TE(s.m[1][c]), mz = TE(s.m[2][c]);
-            const TE irho = TE(1) / rho;     // one division (FP64 is slow on this part)
-            TE vx = mx * irho, vy = my * irho, vz = mz * irho;
+            const TU rho = s.rho[c];
+            const TU mx = s.m[0][c], my = s.m[1][c], mz = s.m[2][c];
+            const TU irho = TU(1) / rho;     // one division (FP64 is slow on this part)
+            const TU vx = mx * irho, vy = my * irho, vz = mz * irho;
             // pressure recovery in the precision of the stored energy
-            TE p = TE(gam - 1.0) * (s.e[c] - TE(0.5) * rho * (vx * vx + vy * vy + vz * vz)
+            TE p = TE(gam - 1.0) * (s.e[c] - kinetic<TU, TE>(rho, mx, my, mz, vx, vy, vz)
                                     - TE(0.5) * (bx * bx + by * by + bz * bz));
             if (pfloor > 0.0 && p < TE(pfloor)) {
                 // optional pressure floor.  At the start of a step (nfloor given)
@@ -458,6 +476,257 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(Boxes B, int d, const R
 }
 
 // ---------------------------------------------------------------------------
+// a3/a4 + a6 by pencils (VL predictor and corrector): one thread walks pl
+// consecutive faces of one grid line along the sweep axis d, keeping the
+// states of the cells around the current face in registers, so every cell
+// is loaded and reconstructed once per segment (plus the segment's one- or
+// two-cell lead-in) and no shared memory or barrier is involved.  Lanes run
+// along the first transverse axis (x for d = 1, 2; y for d = 0).
+// ---------------------------------------------------------------------------
+struct Pencil {
+    long long base, stride;   // cell of line position i: base + wrap(i) * stride
+    int n;                    // cells along the line
+};
+
+__host__ __device__ __forceinline__ void pencil_dims(int nx, int ny, int nz, int d, int pl, int& na, int& nb, int& ns)
+{
+    if (d == 0) { na = ny; nb = nz; ns = (nx + pl - 1) / pl; }
+    else if (d == 1) { na = nx; nb = nz; ns = (ny + pl - 1) / pl; }
+    else { na = nx; nb = ny; ns = (nz + pl - 1) / pl; }
+}
+
+__host__ __device__ __forceinline__ long long pencil_threads_of_box(int nx, int ny, int nz, int d, int pl)
+{
+    int na, nb, ns;
+    pencil_dims(nx, ny, nz, d, pl, na, nb, ns);
+    return (long long)na * nb * ns;
+}
+
+__device__ __forceinline__ int box_of_pth(const Boxes& B, int d, long long t)
+{
+    int lo = 0, hi = B.nbox - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (B.b[mid].pth0[d] <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ long long pcell(const Pencil& p, int i)
+{
+    return p.base + (long long)wrapi(i, p.n) * p.stride;
+}
+
+template <class R>
+__device__ __forceinline__ void copy7(R d[7], const R s[7])
+{
+#pragma unroll
+    for (int m = 0; m < 7; m++) d[m] = s[m];
+}
+
+// seg_list / seg_count: only the segments of a list (the learned selector's),
+// the grid covering every segment of the axis
+template <class R, int RECON, int SOLVER, int MODE, class TE>
+__global__ void __launch_bounds__(PENCIL_THREADS) k_pencil(Boxes B, int d, const R* __restrict__ W,
+                                                           const TE* __restrict__ Bd, R* __restrict__ F, double gam,
+                                                           const int* __restrict__ seg_list = nullptr,
+                                                           const int* __restrict__ seg_count = nullptr)
+{
+    long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (seg_list) {
+        if (gt >= *seg_count) return;
+        gt = seg_list[gt];
+    }
+    if (gt >= B.npth[d]) return;
+    const BoxDev g = B.b[box_of_pth(B, d, gt)];
+    int na, nb, ns;
+    pencil_dims(g.nx, g.ny, g.nz, d, B.pl, na, nb, ns);
+    long long t = gt - g.pth0[d];
+    const int ia = (int)(t % na);
+    t /= na;
+    const int ib = (int)(t % nb);
+    const int sg = (int)(t / nb);
+    Pencil p;
+    if (d == 0) { p.base = g.off + ((long long)ib * g.ny + ia) * g.nx; p.stride = 1; p.n = g.nx; }
+    else if (d == 1) { p.base = g.off + (long long)ib * g.ny * g.nx + ia; p.stride = g.nx; p.n = g.ny; }
+    else { p.base = g.off + (long long)ib * g.nx + ia; p.stride = (long long)g.nx * g.ny; p.n = g.nz; }
+    const int i0 = sg * B.pl;
+    const int i1 = i0 + B.pl < p.n ? i0 + B.pl : p.n;
+    const long long N = B.N;
+    const R gr = R(gam), gm1 = R(gam - 1.0);
+    R f[7];
+    if (MODE == 0) {
+        // first-order states: the face i sees cells i-1 and i
+        R wl[7], wr[7], bdum;
+        load_rot(W, N, pcell(p, i0 - 1), d, wl, bdum);
+        for (int i = i0; i < i1; i++) {
+            const long long ci = p.base + (long long)i * p.stride;
+            load_rot(W, N, ci, d, wr, bdum);
+            riemann<SOLVER>(wl, wr, R(Bd[ci]), gm1, gr, f);
+#pragma unroll
+            for (int m = 0; m < 7; m++) F[(long long)m * N + ci] = f[m];
+            copy7(wl, wr);
+        }
+    } else if (RECON != PPM) {
+        // PLM: cells i-1, i, i+1 in registers; wpp the "+" state of cell i-1
+        R wa[7], wb[7], wc[7], bna, bnb, bnc, wpp[7], wm[7], wp[7], dum[7];
+        load_rot(W, N, pcell(p, i0 - 2), d, wa, bna);
+        load_rot(W, N, pcell(p, i0 - 1), d, wb, bnb);
+        load_rot(W, N, pcell(p, i0), d, wc, bnc);
+        recon_cell<RECON, false>(wa, wb, wc, bnb, gr, dum, dum, dum, R(0), wm, wpp);
+        copy7(wa, wb); bna = bnb;
+        copy7(wb, wc); bnb = bnc;
+        for (int i = i0; i < i1; i++) {
+            const long long ci = p.base + (long long)i * p.stride;
+            load_rot(W, N, pcell(p, i + 1), d, wc, bnc);
+            recon_cell<RECON, false>(wa, wb, wc, bnb, gr, dum, dum, dum, R(0), wm, wp);
+            riemann<SOLVER>(wpp, wm, R(Bd[ci]), gm1, gr, f);
+#pragma unroll
+            for (int m = 0; m < 7; m++) F[(long long)m * N + ci] = f[m];
+            copy7(wpp, wp);
+            copy7(wa, wb); bna = bnb;
+            copy7(wb, wc); bnb = bnc;
+        }
+    } else {
+        // PPM: cells i-1 .. i+2 and the characteristic slopes of i-1 .. i+1
+        R w0[7], w1[7], w2[7], w3[7], b0, b1, b2, b3;      // cells i-1, i, i+1, i+2
+        R s0[7], s1[7], s2[7];                              // slopes of i-1, i, i+1
+        R wpp[7], wm[7], wp[7];
+        {
+            R wq[7], bq;                                    // cell i0-3 (lead-in only)
+            load_rot(W, N, pcell(p, i0 - 3), d, wq, bq);
+            load_rot(W, N, pcell(p, i0 - 2), d, w0, b0);
+            load_rot(W, N, pcell(p, i0 - 1), d, w1, b1);
+            load_rot(W, N, pcell(p, i0), d, w2, b2);
+            load_rot(W, N, pcell(p, i0 + 1), d, w3, b3);
+            char_slope(wq, w0, w1, b0, gr, s0);             // slope of i0-2
+        }
+        char_slope(w0, w1, w2, b1, gr, s1);                 // i0-1
+        char_slope(w1, w2, w3, b2, gr, s2);                 // i0
+        recon_cell<PPM, false>(w0, w1, w2, b1, gr, s0, s1, s2, R(0), wm, wpp);   // cell i0-1
+        // shift so that w0..w2 = cells i0-1 .. i0+1, s0, s1 = slopes of i0-1, i0
+        copy7(w0, w1); b0 = b1;
+        copy7(w1, w2); b1 = b2;
+        copy7(w2, w3); b2 = b3;
+        copy7(s0, s1);
+        copy7(s1, s2);
+        for (int i = i0; i < i1; i++) {
+            const long long ci = p.base + (long long)i * p.stride;
+            load_rot(W, N, pcell(p, i + 2), d, w3, b3);
+            char_slope(w1, w2, w3, b2, gr, s2);             // slope of i+1
+            recon_cell<PPM, false>(w0, w1, w2, b1, gr, s0, s1, s2, R(0), wm, wp);
+            riemann<SOLVER>(wpp, wm, R(Bd[ci]), gm1, gr, f);
+#pragma unroll
+            for (int m = 0; m < 7; m++) F[(long long)m * N + ci] = f[m];
+            copy7(wpp, wp);
+            copy7(w0, w1); b0 = b1;
+            copy7(w1, w2); b1 = b2;
+            copy7(w2, w3); b2 = b3;
+            copy7(s0, s1);
+            copy7(s1, s2);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a3/a4 + a6 along x by warps: the lanes of a warp hold 32 consecutive cells
+// of one grid row (coalesced loads, x fastest in memory) and take their
+// neighbours' states and slopes by register shuffles, so the x sweep also
+// runs without shared memory or barriers.  A warp item yields XW_FW faces:
+// 31 for the first-order predictor (lanes 1..31), 29 for PLM (reconstruction
+// valid on lanes 1..30, faces on lanes 2..30), 27 for PPM (slopes on lanes
+// 1..30, reconstruction on 2..29, faces on 3..29).
+// ---------------------------------------------------------------------------
+template <int RECON, int MODE> struct XW {
+    static constexpr int slot = MODE == 0 ? 0 : (RECON == PPM ? 2 : 1);
+    static constexpr int lead = MODE == 0 ? 1 : (RECON == PPM ? 3 : 2);   // lane 0's cell: x0 - lead
+};
+__host__ __device__ constexpr int xw_faces(int slot) { return slot == 0 ? 31 : (slot == 1 ? 29 : 27); }
+
+__host__ __device__ __forceinline__ long long xwarp_items_of_box(int nx, int ny, int nz, int slot)
+{
+    const int fw = xw_faces(slot);
+    return (long long)ny * nz * ((nx + fw - 1) / fw);
+}
+
+__device__ __forceinline__ int box_of_xw(const Boxes& B, int slot, long long t)
+{
+    int lo = 0, hi = B.nbox - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (B.b[mid].xw0[slot] <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <class R>
+__device__ __forceinline__ void shfl7(R o[7], const R v[7], int up)
+{
+#pragma unroll
+    for (int m = 0; m < 7; m++)
+        o[m] = up ? __shfl_up_sync(0xffffffffu, v[m], 1) : __shfl_down_sync(0xffffffffu, v[m], 1);
+}
+
+// dslot: the item decomposition (faces per warp xw_faces(dslot), at most the
+// kernel's own); item_list / item_count: only the items of a list (the
+// learned selector's, whose cheap and full kernels share one decomposition)
+template <class R, int RECON, int SOLVER, int MODE, class TE>
+__global__ void __launch_bounds__(PENCIL_THREADS) k_xwarp(Boxes B, const R* __restrict__ W,
+                                                          const TE* __restrict__ Bd, R* __restrict__ F, double gam,
+                                                          int dslot, const int* __restrict__ item_list = nullptr,
+                                                          const int* __restrict__ item_count = nullptr)
+{
+    constexpr int LEAD = XW<RECON, MODE>::lead;
+    const int FW = xw_faces(dslot);
+    long long item = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (item_list) {
+        if (item >= *item_count) return;             // uniform over the warp
+        item = item_list[item];
+    }
+    if (item >= B.nxw[dslot]) return;
+    const BoxDev g = B.b[box_of_xw(B, dslot, item)];
+    const int nseg = (g.nx + FW - 1) / FW;
+    long long t = item - g.xw0[dslot];
+    const int sg = (int)(t % nseg);
+    t /= nseg;
+    const int j = (int)(t % g.ny), k = (int)(t / g.ny);
+    const long long row = g.off + ((long long)k * g.ny + j) * g.nx;
+    const int xi = sg * FW - LEAD + lane;            // this lane's cell (and the face below it)
+    const long long ci = row + wrapi(xi, g.nx);
+    const long long N = B.N;
+    const R gr = R(gam), gm1 = R(gam - 1.0);
+    R w[7], bn, f[7];
+    load_rot(W, N, ci, 0, w, bn);
+    const bool face = lane >= LEAD && lane < LEAD + FW;
+    R wl[7], wr[7];
+    if (MODE == 0) {
+        shfl7(wl, w, 1);
+        copy7(wr, w);
+    } else {
+        R wm1[7], wp1[7], wpf[7];
+        shfl7(wm1, w, 1);
+        shfl7(wp1, w, 0);
+        if (RECON == PPM) {
+            R s0[7], sm1[7], sp1[7];
+            char_slope(wm1, w, wp1, bn, gr, s0);
+            shfl7(sm1, s0, 1);
+            shfl7(sp1, s0, 0);
+            recon_cell<PPM, false>(wm1, w, wp1, bn, gr, sm1, s0, sp1, R(0), wr, wpf);
+        } else {
+            R dum[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};   // slopes: unused by PLM
+            recon_cell<RECON, false>(wm1, w, wp1, bn, gr, dum, dum, dum, R(0), wr, wpf);
+        }
+        shfl7(wl, wpf, 1);                           // the "+" state of the cell below
+    }
+    if (face && xi < g.nx) {
+        riemann<SOLVER>(wl, wr, R(Bd[ci]), gm1, gr, f);
+#pragma unroll
+        for (int m = 0; m < 7; m++) F[(long long)m * N + ci] = f[m];
+    }
+}
+
+// ---------------------------------------------------------------------------
 // a7: edge electric fields, upwinded corner average (Sec. 2, Eqs. 13-14 with
 // the Gardiner-Stone reference field).  Every cell gets its three lower
 // edges: E_c at the corner of the faces a = c+1, b = c+2,
@@ -663,25 +932,28 @@ __global__ void __launch_bounds__(CELL_THREADS) k_half(Boxes B, StateP<TU, TE> s
         Bh[d][c] = lo;
         bc[d] = TE(0.5) * (lo + hi);
     }
-    // divergence of the fluxes, sweep frames back to x, y, z
-    TE du[5] = {TE(0), TE(0), TE(0), TE(0), TE(0)};
+    // divergence of the fluxes, sweep frames back to x, y, z: rho and M in
+    // their storage type TU, the energy in TE
+    TU du[4] = {TU(0), TU(0), TU(0), TU(0)};
+    TE due = TE(0);
 #pragma unroll
     for (int d = 0; d < 3; d++) {
         const int t1 = d == 2 ? 0 : d + 1, t2 = d == 0 ? 2 : d - 1;
         const R* Fd = F + (long long)d * 7 * N;
         long long cp = nbr(g, i, j, k, d, 1);
-        du[0] += TE(Fd[cp] - Fd[c]);
-        du[1 + d] += TE(Fd[N + cp] - Fd[N + c]);
-        du[1 + t1] += TE(Fd[2 * N + cp] - Fd[2 * N + c]);
-        du[1 + t2] += TE(Fd[3 * N + cp] - Fd[3 * N + c]);
-        du[4] += TE(Fd[4 * N + cp] - Fd[4 * N + c]);
+        du[0] += TU(Fd[cp] - Fd[c]);
+        du[1 + d] += TU(Fd[N + cp] - Fd[N + c]);
+        du[1 + t1] += TU(Fd[2 * N + cp] - Fd[2 * N + c]);
+        du[1 + t2] += TU(Fd[3 * N + cp] - Fd[3 * N + c]);
+        due += TE(Fd[4 * N + cp] - Fd[4 * N + c]);
     }
-    TE rho = TE(s.rho[c]) - r * du[0];
-    TE mx = TE(s.m[0][c]) - r * du[1], my = TE(s.m[1][c]) - r * du[2], mz = TE(s.m[2][c]) - r * du[3];
-    TE e = s.e[c] - r * du[4];
-    const TE irho = TE(1) / rho;
-    TE vx = mx * irho, vy = my * irho, vz = mz * irho;
-    TE p = TE(gam - 1.0) * (e - TE(0.5) * rho * (vx * vx + vy * vy + vz * vz)
+    const TU ru = DtOf<TU>::hdtdx(dtb[bi]);
+    TU rho = s.rho[c] - ru * du[0];
+    TU mx = s.m[0][c] - ru * du[1], my = s.m[1][c] - ru * du[2], mz = s.m[2][c] - ru * du[3];
+    TE e = s.e[c] - r * due;
+    const TU irho = TU(1) / rho;
+    TU vx = mx * irho, vy = my * irho, vz = mz * irho;
+    TE p = TE(gam - 1.0) * (e - kinetic<TU, TE>(rho, mx, my, mz, vx, vy, vz)
                             - TE(0.5) * (bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]));
     if (pfloor > 0.0 && p < TE(pfloor)) p = TE(pfloor);
     Wh[c] = R(rho); Wh[N + c] = R(vx); Wh[2 * N + c] = R(vy); Wh[3 * N + c] = R(vz);
@@ -707,23 +979,26 @@ __global__ void __launch_bounds__(CELL_THREADS) k_full(Boxes B, StateP<TU, TE> s
     int i, j, k;
     coords(g, lc, i, j, k);
     const long long c = g.off + lc;
-    TE du[5] = {TE(0), TE(0), TE(0), TE(0), TE(0)};
+    TU du[4] = {TU(0), TU(0), TU(0), TU(0)};
+    TE due = TE(0);
 #pragma unroll
     for (int d = 0; d < 3; d++) {
         const int t1 = d == 2 ? 0 : d + 1, t2 = d == 0 ? 2 : d - 1;
         const R* Fd = F + (long long)d * 7 * N;
         long long cp = nbr(g, i, j, k, d, 1);
-        du[0] += TE(Fd[cp] - Fd[c]);
-        du[1 + d] += TE(Fd[N + cp] - Fd[N + c]);
-        du[1 + t1] += TE(Fd[2 * N + cp] - Fd[2 * N + c]);
-        du[1 + t2] += TE(Fd[3 * N + cp] - Fd[3 * N + c]);
-        du[4] += TE(Fd[4 * N + cp] - Fd[4 * N + c]);
+        du[0] += TU(Fd[cp] - Fd[c]);
+        du[1 + d] += TU(Fd[N + cp] - Fd[N + c]);
+        du[1 + t1] += TU(Fd[2 * N + cp] - Fd[2 * N + c]);
+        du[1 + t2] += TU(Fd[3 * N + cp] - Fd[3 * N + c]);
+        due += TE(Fd[4 * N + cp] - Fd[4 * N + c]);
     }
-    s.rho[c] = TU(TE(s.rho[c]) - r * du[0]);
-    s.m[0][c] = TU(TE(s.m[0][c]) - r * du[1]);
-    s.m[1][c] = TU(TE(s.m[1][c]) - r * du[2]);
-    s.m[2][c] = TU(TE(s.m[2][c]) - r * du[3]);
-    s.e[c] = s.e[c] - r * du[4];
+    // rho and M in their storage type, the energy in TE (Eq. 10)
+    const TU ru = DtOf<TU>::dtdx(dtb[bi]);
+    s.rho[c] = s.rho[c] - ru * du[0];
+    s.m[0][c] = s.m[0][c] - ru * du[1];
+    s.m[1][c] = s.m[1][c] - ru * du[2];
+    s.m[2][c] = s.m[2][c] - ru * du[3];
+    s.e[c] = s.e[c] - r * due;
 #pragma unroll
     for (int d = 0; d < 3; d++) s.b[d][c] = s.b[d][c] - r * curl_face<TE>(g, N, E, i, j, k, d);
     }

@@ -308,40 +308,114 @@ static void run_step_learned(mhd_ctx* c, bool device_dt)
     k_block_features<R><<<fgrid, 256, 0, st>>>(c->hbox[0], W, n, (float)gam, c->sel_feats);
     const int igrid = (int)((nblk / 16 + 8) / 8 < 1184 ? (nblk / 16 + 8) / 8 : 1184);
     k_mlp_infer<<<igrid, 256, 0, st>>>(mlp_dev(c->sel), c->sel_feats, nblk, nullptr, c->sel_flags);
-    cudaMemsetAsync(c->sel_cnt, 0, 6 * sizeof(int), st);
-    for (int d = 0; d < 3; d++)
-        k_tile_classify<<<(g.ntile[d] + 255) / 256, 256, 0, st>>>(c->hbox[0], d, g.tl, c->sel_flags,
-                                                                   c->sel_list[2 * d], c->sel_cnt + 2 * d,
-                                                                   c->sel_list[2 * d + 1], c->sel_cnt + 2 * d + 1,
-                                                                   g.ntile[d]);
+    cudaMemsetAsync(c->sel_cnt, 0, 8 * sizeof(int), st);
+    const bool xw = c->pencil_mask & 1;
+    for (int d = 0; d < 3; d++) {
+        if (d == 0 && xw) {
+            // x by warps: the predictor's items (31 faces) in lists 0/1, the
+            // corrector's (27 faces, shared by the cheap PLM and full PPM kernels) in 6/7
+            k_xw_classify<<<(int)((g.nxw[0] + 255) / 256 < 4096 ? (g.nxw[0] + 255) / 256 : 4096), 256, 0, st>>>(
+                c->hbox[0], 0, c->sel_flags, c->sel_list[0], c->sel_cnt + 0, c->sel_list[1], c->sel_cnt + 1, g.nxw[0]);
+            k_xw_classify<<<(int)((g.nxw[2] + 255) / 256 < 4096 ? (g.nxw[2] + 255) / 256 : 4096), 256, 0, st>>>(
+                c->hbox[0], 2, c->sel_flags, c->sel_list[6], c->sel_cnt + 6, c->sel_list[7], c->sel_cnt + 7, g.nxw[2]);
+        } else if (c->pencil_mask >> d & 1)
+            k_seg_classify<<<(int)((g.npth[d] + 255) / 256 < 4096 ? (g.npth[d] + 255) / 256 : 4096), 256, 0, st>>>(
+                c->hbox[0], d, g.pl, c->sel_flags, c->sel_list[2 * d], c->sel_cnt + 2 * d, c->sel_list[2 * d + 1],
+                c->sel_cnt + 2 * d + 1, g.npth[d]);
+        else
+            k_tile_classify<<<(g.ntile[d] + 255) / 256, 256, 0, st>>>(c->hbox[0], d, g.tl, c->sel_flags,
+                                                                       c->sel_list[2 * d], c->sel_cnt + 2 * d,
+                                                                       c->sel_list[2 * d + 1], c->sel_cnt + 2 * d + 1,
+                                                                       g.ntile[d]);
+    }
     prof_mark(c, 1);
     // VL steps 1-3
     for (int d = 0; d < 3; d++) {
-        k_sweep<R, PLM_PRIM, HLLE, 0, float><<<sweep_grid(c, d), SWEEP_THREADS, 0, st>>>(
-            g, d, W, s.b[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam, c->sel_list[2 * d], c->sel_cnt + 2 * d);
-        k_sweep<R, PPM, HLLD, 0, float><<<sweep_grid(c, d), SWEEP_THREADS, 0, st>>>(
-            g, d, W, s.b[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam, c->sel_list[2 * d + 1],
-            c->sel_cnt + 2 * d + 1);
+        if (d == 0 && xw) {
+            k_xwarp<R, PLM_PRIM, HLLE, 0, float><<<xwarp_grid(c, 0), PENCIL_THREADS, 0, st>>>(
+                g, W, s.b[0], F1, gam, 0, c->sel_list[0], c->sel_cnt + 0);
+            k_xwarp<R, PPM, HLLD, 0, float><<<xwarp_grid(c, 0), PENCIL_THREADS, 0, st>>>(
+                g, W, s.b[0], F1, gam, 0, c->sel_list[1], c->sel_cnt + 1);
+        } else if (c->pencil_mask >> d & 1) {
+            k_pencil<R, PLM_PRIM, HLLE, 0, float><<<pencil_grid(c, d), PENCIL_THREADS, 0, st>>>(
+                g, d, W, s.b[d], F1 + (long long)d * 7 * n, gam, c->sel_list[2 * d], c->sel_cnt + 2 * d);
+            k_pencil<R, PPM, HLLD, 0, float><<<pencil_grid(c, d), PENCIL_THREADS, 0, st>>>(
+                g, d, W, s.b[d], F1 + (long long)d * 7 * n, gam, c->sel_list[2 * d + 1], c->sel_cnt + 2 * d + 1);
+        } else {
+            k_sweep<R, PLM_PRIM, HLLE, 0, float><<<sweep_grid(c, d), SWEEP_THREADS, 0, st>>>(
+                g, d, W, s.b[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam, c->sel_list[2 * d],
+                c->sel_cnt + 2 * d);
+            k_sweep<R, PPM, HLLD, 0, float><<<sweep_grid(c, d), SWEEP_THREADS, 0, st>>>(
+                g, d, W, s.b[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam, c->sel_list[2 * d + 1],
+                c->sel_cnt + 2 * d + 1);
+        }
+        prof_mark(c, 2 + d);
     }
-    prof_mark(c, 2);
     k_emf<R><<<emf_grid<R>(c), EMF_THREADS, emf_smem_bytes<R>(), st>>>(g, F1, W, E);
-    prof_mark(c, 3);
+    prof_mark(c, 5);
     k_half<R, float, float><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2], Wh, c->sch.pfloor);
-    prof_mark(c, 4);
+    prof_mark(c, 6);
     // VL steps 4-7
     for (int d = 0; d < 3; d++) {
-        k_sweep<R, PLM_PRIM, HLLE, 1, float><<<sweep_grid(c, d), SWEEP_THREADS, sweep_smem_bytes<R>(PLM_PRIM, g.tl), st>>>(
-            g, d, Wh, Bh[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam, c->sel_list[2 * d], c->sel_cnt + 2 * d);
-        k_sweep<R, PPM, HLLD, 1, float><<<sweep_grid(c, d), SWEEP_THREADS, smem, st>>>(
-            g, d, Wh, Bh[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam, c->sel_list[2 * d + 1],
-            c->sel_cnt + 2 * d + 1);
+        if (d == 0 && xw) {
+            k_xwarp<R, PLM_PRIM, HLLE, 1, float><<<xwarp_grid(c, 2), PENCIL_THREADS, 0, st>>>(
+                g, Wh, Bh[0], F1, gam, 2, c->sel_list[6], c->sel_cnt + 6);
+            k_xwarp<R, PPM, HLLD, 1, float><<<xwarp_grid(c, 2), PENCIL_THREADS, 0, st>>>(
+                g, Wh, Bh[0], F1, gam, 2, c->sel_list[7], c->sel_cnt + 7);
+        } else if (c->pencil_mask >> d & 1) {
+            k_pencil<R, PLM_PRIM, HLLE, 1, float><<<pencil_grid(c, d), PENCIL_THREADS, 0, st>>>(
+                g, d, Wh, Bh[d], F1 + (long long)d * 7 * n, gam, c->sel_list[2 * d], c->sel_cnt + 2 * d);
+            k_pencil<R, PPM, HLLD, 1, float><<<pencil_grid(c, d), PENCIL_THREADS, 0, st>>>(
+                g, d, Wh, Bh[d], F1 + (long long)d * 7 * n, gam, c->sel_list[2 * d + 1], c->sel_cnt + 2 * d + 1);
+        } else {
+            k_sweep<R, PLM_PRIM, HLLE, 1, float><<<sweep_grid(c, d), SWEEP_THREADS,
+                                                   sweep_smem_bytes<R>(PLM_PRIM, g.tl), st>>>(
+                g, d, Wh, Bh[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam, c->sel_list[2 * d],
+                c->sel_cnt + 2 * d);
+            k_sweep<R, PPM, HLLD, 1, float><<<sweep_grid(c, d), SWEEP_THREADS, smem, st>>>(
+                g, d, Wh, Bh[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam, c->sel_list[2 * d + 1],
+                c->sel_cnt + 2 * d + 1);
+        }
+        prof_mark(c, 7 + d);
     }
-    prof_mark(c, 5);
     k_emf<R><<<emf_grid<R>(c), EMF_THREADS, emf_smem_bytes<R>(), st>>>(g, F1, Wh, E);
-    prof_mark(c, 6);
+    prof_mark(c, 10);
     k_full<R, float, float><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc);
-    prof_mark(c, 7);
+    prof_mark(c, 11);
     if (c->prof_on && c->prof_steps < c->prof_cap) c->prof_steps++;
+}
+
+// selector tile / segment lists large enough for the current sweep layout:
+// the tiles of the shortest tile length and the pencil segments of the
+// current length, whichever is more (grown when the layout needs more)
+mhd_status mhd_internal_selector_lists(mhd_ctx* c)
+{
+    long long need = 0;
+    const BoxDev& b0 = c->hbox[0];
+    for (int d = 0; d < 3; d++) {
+        long long nt = tiles_of_box(b0.nx, b0.ny, b0.nz, d, 4);
+        long long np = pencil_threads_of_box(b0.nx, b0.ny, b0.nz, d, c->pencil_len);
+        long long nw = xwarp_items_of_box(b0.nx, b0.ny, b0.nz, d);
+        need = nt > need ? nt : need;
+        need = np > need ? np : need;
+        need = nw > need ? nw : need;
+    }
+    if (c->sel_list[0] && need <= c->sel_cap) return MHD_OK;
+    if (c->have_graph) { cudaGraphExecDestroy(c->gexec); c->have_graph = false; }
+    cudaStreamSynchronize(c->stream);
+    for (int q = 0; q < 8; q++)
+        if (c->sel_list[q]) {
+            cudaFree(c->sel_list[q]);
+            c->sel_list[q] = nullptr;
+            c->bytes -= c->sel_cap * 4;
+        }
+    c->sel_cap = 0;
+    for (int q = 0; q < 8; q++) {
+        if (cudaMalloc((void**)&c->sel_list[q], (size_t)need * sizeof(int)) != cudaSuccess) return MHD_ENOMEM;
+        c->bytes += need * 4;
+    }
+    c->sel_cap = need;
+    return MHD_OK;
 }
 
 extern "C" mhd_status mhd_set_selector(mhd_ctx* c, mhd_mlp* m)
@@ -360,21 +434,15 @@ extern "C" mhd_status mhd_set_selector(mhd_ctx* c, mhd_mlp* m)
     }
     if (!c->sel_feats) {
         const long long nblk = mhd_nblocks(c);
-        int ntmax = 0;
-        for (int d = 0; d < 3; d++) {
-            // the tile counts of the largest tile length bound every layout
-            int nt = tiles_of_box(c->hbox[0].nx, c->hbox[0].ny, c->hbox[0].nz, d, 4);
-            ntmax = nt > ntmax ? nt : ntmax;
-        }
         cudaError_t e = cudaMalloc((void**)&c->sel_feats, nblk * NF * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc((void**)&c->sel_flags, nblk);
-        if (e == cudaSuccess) e = cudaMalloc((void**)&c->sel_cnt, 6 * sizeof(int));
-        for (int q = 0; q < 6 && e == cudaSuccess; q++) e = cudaMalloc((void**)&c->sel_list[q], (size_t)ntmax * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&c->sel_cnt, 8 * sizeof(int));
         if (e != cudaSuccess) return MHD_ENOMEM;
-        c->bytes += nblk * (NF * 4 + 1) + 24 + 6LL * ntmax * 4;
+        c->bytes += nblk * (NF * 4 + 1) + 24;
         cudaFuncSetAttribute(k_sweep<float, PPM, HLLD, 1, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sweep_smem_bytes<float>(PPM, TL_MAX));
     }
+    if (mhd_internal_selector_lists(c) != MHD_OK) return MHD_ENOMEM;
     c->sel = m;
     c->step = run_step_learned;
     c->launches = 12 + 3 + 3 + 6;   // + features, MLP, 3 tile lists, 6 sweeps of the other path

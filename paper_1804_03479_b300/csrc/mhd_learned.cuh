@@ -535,4 +535,65 @@ __global__ void k_tile_classify(BoxDev g, int d, int tl, const unsigned char* __
     }
 }
 
+// pencil segments of axis d (length pl) into cheap and full lists: full when
+// any 4^3 block holding one of the cells beside the segment's faces (cells
+// i0-1 .. i1-1 of its line) is flagged
+__global__ void k_seg_classify(BoxDev g, int d, int pl, const unsigned char* __restrict__ full_flag,
+                               int* __restrict__ list_cheap, int* __restrict__ cnt_cheap, int* __restrict__ list_full,
+                               int* __restrict__ cnt_full, long long nseg)
+{
+    int na, nb, ns;
+    pencil_dims(g.nx, g.ny, g.nz, d, pl, na, nb, ns);
+    const int nbx = g.nx / 4, nby = g.ny / 4;
+    const int nd = d == 0 ? g.nx : (d == 1 ? g.ny : g.nz);
+    const int nbd = nd / 4;
+    for (long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; t0 < nseg;
+         t0 += (long long)gridDim.x * blockDim.x) {
+        long long t = t0;
+        const int ia = (int)(t % na);
+        t /= na;
+        const int ib = (int)(t % nb);
+        const int sg = (int)(t / nb);
+        const int i0 = sg * pl, i1 = i0 + pl < nd ? i0 + pl : nd;
+        const int q0 = (i0 + 3) / 4 - 1, q1 = (i1 - 1) / 4;     // blocks of cells i0-1 and i1-1
+        bool full = false;
+        for (int q = q0; q <= q1 && !full; q++) {
+            const int qb = wrapi(q, nbd);
+            int bi, bj, bk;
+            if (d == 0) { bi = qb; bj = ia / 4; bk = ib / 4; }
+            else if (d == 1) { bi = ia / 4; bj = qb; bk = ib / 4; }
+            else { bi = ia / 4; bj = ib / 4; bk = qb; }
+            full = full_flag[((long long)bk * nby + bj) * nbx + bi] != 0;
+        }
+        if (full) list_full[atomicAdd(cnt_full, 1)] = (int)t0;
+        else list_cheap[atomicAdd(cnt_cheap, 1)] = (int)t0;
+    }
+}
+
+// x-warp items (decomposition dslot) into cheap and full lists: full when any
+// 4^3 block holding one of the cells beside the item's faces (cells x0-1 ..
+// x1-1 of its row) is flagged
+__global__ void k_xw_classify(BoxDev g, int dslot, const unsigned char* __restrict__ full_flag,
+                              int* __restrict__ list_cheap, int* __restrict__ cnt_cheap, int* __restrict__ list_full,
+                              int* __restrict__ cnt_full, long long nitem)
+{
+    const int fw = xw_faces(dslot);
+    const int nseg = (g.nx + fw - 1) / fw;
+    const int nbx = g.nx / 4, nby = g.ny / 4;
+    for (long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; t0 < nitem;
+         t0 += (long long)gridDim.x * blockDim.x) {
+        long long t = t0;
+        const int sg = (int)(t % nseg);
+        t /= nseg;
+        const int j = (int)(t % g.ny), k = (int)(t / g.ny);
+        const int x0 = sg * fw, x1 = x0 + fw < g.nx ? x0 + fw : g.nx;
+        const int q0 = (x0 + 3) / 4 - 1, q1 = (x1 - 1) / 4;
+        bool full = false;
+        for (int q = q0; q <= q1 && !full; q++)
+            full = full_flag[((long long)(k / 4) * nby + j / 4) * nbx + wrapi(q, nbx)] != 0;
+        if (full) list_full[atomicAdd(cnt_full, 1)] = (int)t0;
+        else list_cheap[atomicAdd(cnt_cheap, 1)] = (int)t0;
+    }
+}
+
 }  // namespace mhd

@@ -122,6 +122,15 @@ extern "C" mhd_status mhd_step_noalloc(const mhd_grid* grid, double gamma, const
     c.B.nvblk = (n + CELL_THREADS - 1) / CELL_THREADS;
     for (int d = 0; d < 3; d++) c.B.ntile[d] = tiles_of_box(hb.nx, hb.ny, hb.nz, d, tl);
     c.B.netile = emf_tiles_of_box(hb.nx, hb.ny, hb.nz);
+    c.pencil_mask = 0;                 // tile sweeps only
+    c.pencil_len = 16;
+    c.B.pl = 16;
+    for (int d = 0; d < 3; d++) {
+        hb.pth0[d] = 0;
+        c.B.npth[d] = pencil_threads_of_box(hb.nx, hb.ny, hb.nz, d, 16);
+        hb.xw0[d] = 0;
+        c.B.nxw[d] = xwarp_items_of_box(hb.nx, hb.ny, hb.nz, d);
+    }
     int nsm = 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return reject(MHD_ECUDA, "mhd_step_noalloc: device query failed");

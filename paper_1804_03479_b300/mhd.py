@@ -32,8 +32,10 @@ EXPORTS = ["mhd_init", "mhd_set_state", "mhd_get_state", "mhd_cfl_dt", "mhd_step
            "mhd_get_sweep_config", "mhd_autotune", "mhd_mlp_create", "mhd_mlp_free", "mhd_mlp_nparam",
            "mhd_mlp_set_weights", "mhd_mlp_get_weights", "mhd_mlp_grad", "mhd_mlp_train_step",
            "mhd_mlp_predict", "mhd_nblocks", "mhd_block_features", "mhd_block_error", "mhd_set_selector",
-           "mhd_selector_stats", "mhd_floor_count", "mhd_energies", "mhd_helicity"]
-GROUPS = ["prim_cfl", "predictor_sweeps", "emf1", "half_update", "corrector_sweeps", "emf2", "full_update"]
+           "mhd_selector_stats", "mhd_floor_count", "mhd_energies", "mhd_helicity",
+           "mhd_set_sweep_pencils", "mhd_get_sweep_pencils"]
+GROUPS = ["prim_cfl", "predictor_x", "predictor_y", "predictor_z", "emf1", "half_update", "corrector_x",
+          "corrector_y", "corrector_z", "emf2", "full_update"]
 
 
 class MHDError(RuntimeError):
@@ -128,6 +130,8 @@ def lib():
     L.mhd_profile_end.argtypes = [vp, dp, ip, ctypes.POINTER(ctypes.c_int)]
     L.mhd_energies.argtypes = [vp, ctypes.c_double, dp]
     L.mhd_helicity.argtypes = [vp, dp]
+    L.mhd_set_sweep_pencils.argtypes = [vp, ip, ip]
+    L.mhd_get_sweep_pencils.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip)]
     # every entry point that returns an mhd_status; the others got their
     # restype above (long long, int, void, const char*)
     other = {"mhd_bad_cell", "mhd_clear_error", "mhd_device_bytes", "mhd_floor_count", "mhd_free",
@@ -282,6 +286,15 @@ class Solver:
     def set_sweep_config(self, tile_len, blocks_per_sm):
         self._check(lib().mhd_set_sweep_config(self.h, tile_len, blocks_per_sm))
 
+    def set_sweep_pencils(self, pencil_mask, pencil_len=16):
+        """VL face sweeps by pencils on the axes of pencil_mask (bit d: axis d)"""
+        self._check(lib().mhd_set_sweep_pencils(self.h, pencil_mask, pencil_len))
+
+    def sweep_pencils(self):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        self._check(lib().mhd_get_sweep_pencils(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
     def sweep_config(self):
         a, b = ctypes.c_int(), ctypes.c_int()
         self._check(lib().mhd_get_sweep_config(self.h, ctypes.byref(a), ctypes.byref(b)))
@@ -317,9 +330,9 @@ class Solver:
 
     def profile_end(self):
         """summed ms per kernel group (GROUPS) and the number of steps recorded"""
-        ms = (ctypes.c_double * 7)()
+        ms = (ctypes.c_double * len(GROUPS))()
         steps = ctypes.c_int()
-        self._check(lib().mhd_profile_end(self.h, ms, 7, ctypes.byref(steps)))
+        self._check(lib().mhd_profile_end(self.h, ms, len(GROUPS), ctypes.byref(steps)))
         return dict(zip(GROUPS, ms[:])), steps.value
 
     # --- learned path selector -------------------------------------------

@@ -171,14 +171,17 @@ def constant_net(mhd, logit):
     return net
 
 
+@pytest.mark.parametrize("mask", [0, 6, 7])
 @pytest.mark.parametrize("logit,scheme", [(-50.0, ("vl", "ppm", "hlld")), (50.0, ("vl", "plm_prim", "hlle"))])
-def test_selector_limits_equal_plain_schemes(env, logit, scheme):
+def test_selector_limits_equal_plain_schemes(env, logit, scheme, mask):
     """a network that always says 'full' (or always 'cheap') must reproduce the
-    plain full (or cheap) scheme bit for bit"""
+    plain full (or cheap) scheme bit for bit, with tile sweeps (mask 0) or
+    pencil segments (the selector's segment lists) on the masked axes"""
     torch, mhd = env
     st = I.abc_blasts(32, kmult=2, beta=0.3, nblast=2, radius=0.1, seed=8, noise=1e-2)
     U = st.U.astype(np.float32); Bf = st.B.astype(np.float32)
     plain = mhd.Solver(U.shape[1:], st.dx, st.gamma, *scheme, "fp32", 0.3)
+    plain.set_sweep_pencils(mask, 8)
     plain.set_state(U, Bf)
     plain.advance(3)
     ref = plain.get_state()
@@ -187,6 +190,7 @@ def test_selector_limits_equal_plain_schemes(env, logit, scheme):
     s = mhd.Solver(U.shape[1:], st.dx, st.gamma, "vl", "ppm", "hlld", "fp32", 0.3)
     s.set_state(U, Bf)
     s.set_selector(net)
+    s.set_sweep_pencils(mask, 8)     # after the selector: its lists grow with the segment count
     s.advance(3)
     got = s.get_state()
     fb, ft = s.selector_stats()
