@@ -53,19 +53,22 @@ SIZES = {"fp64": (8, 8, 8), "fp32": (4, 4, 4), "mixed": (4, 8, 4)}   # (rho/M, e
 # Algorithmic floating-point operations per face of one VL + PLM + Roe sweep
 # launch: corrector = one cell's characteristic PLM reconstruction and one
 # Roe solve, predictor = one Roe solve.  They are the FADD + FMUL + 2 FFMA
-# counts that ncu reports for the FP32 build at 160^3 (x sweeps), where every
+# counts that ncu reports for the FP32 pencil kernels at 160^3 (y sweeps: one
+# reconstruction per face plus the segment's 1/32 lead-in), where every
 # divide and square root is a single MUFU op.  The same algorithm runs in the
-# FP64 build, whose divides and square roots expand into FMA iterations (1632
-# executed FP64 flops per corrector face at 128^3), so the algorithmic
-# figures are used for all precisions.
-FLOPS_PER_FACE = {"corrector": {"fp32": 1002.0, "fp64": 1002.0, "mixed": 1002.0},
-                  "predictor": {"fp32": 689.0, "fp64": 689.0, "mixed": 689.0}}
+# FP64 build, whose divides and square roots expand into FMA iterations, so
+# the algorithmic figures are used for all precisions.
+FLOPS_PER_FACE = {"corrector": {"fp32": 959.0, "fp64": 959.0, "mixed": 959.0},
+                  "predictor": {"fp32": 688.0, "fp64": 688.0, "mixed": 688.0}}
 # DRAM bytes (read + write) per face of one sweep launch, per kernel, from
 # dram__bytes_read.sum + dram__bytes_write.sum of the ncu captures in
-# profiles/ (tile corrector FP32 237.1 MB at 160^3, FP64 238.8 MB at 128^3;
-# tile predictor FP32 217.8 MB at 160^3), scaled to other sizes by faces.
-TRAFFIC_PER_FACE = {"corrector_tile": {"fp32": 57.9, "fp64": 113.9},
-                    "predictor_tile": {"fp32": 53.2}}
+# profiles/ (FP32 at 160^3: pencil corrector 263.5 MB, x-warp corrector
+# 219.4 MB, pencil predictor 237.5 MB, tile corrector 237.1 MB, tile
+# predictor 217.8 MB; FP64 tile corrector 238.8 MB at 128^3), scaled to other
+# sizes by faces.
+TRAFFIC_PER_FACE = {"corrector_pencil": {"fp32": 64.3}, "corrector_xwarp": {"fp32": 53.6},
+                    "predictor_pencil": {"fp32": 58.0},
+                    "corrector_tile": {"fp32": 57.9, "fp64": 113.9}, "predictor_tile": {"fp32": 53.2}}
 
 
 def peaks():
@@ -263,7 +266,7 @@ def kernels_of(groups, tuned):
         for st in ("predictor", "corrector"):
             if k.startswith(st + "_"):
                 d = AXES.index(k.split("_")[1])
-                name = f"{st}_{'pencil' if mask >> d & 1 else 'tile'}"
+                name = f"{st}_{('xwarp' if d == 0 else 'pencil') if mask >> d & 1 else 'tile'}"
         ms, cnt = out.get(name, (0.0, 0))
         out[name] = (ms + v, cnt + nl)
     return out

@@ -171,8 +171,8 @@ mhd_status mhd_autotune(mhd_ctx* ctx, int reps, int* tile_len, int* blocks_per_s
  * lanes of a warp hold 32 consecutive cells of a row and exchange
  * neighbour states by shuffles (27 to 31 faces per warp).  The results are
  * those of the tile sweeps (the same arithmetic per face).  pencil_mask in
- * [0, 7] (0: tiles everywhere; default 6 = y and z, with pencil_len 32, for
- * VL contexts, 0 for CTU), pencil_len in [1, 1024], else MHD_EINVAL; a
+ * [0, 7] (0: tiles everywhere; default 7, with pencil_len 32, for VL
+ * contexts, 0 for CTU), pencil_len in [1, 1024], else MHD_EINVAL; a
  * non-zero mask with the CTU integrator: MHD_EUNSUPPORTED. */
 mhd_status mhd_set_sweep_pencils(mhd_ctx* ctx, int pencil_mask, int pencil_len);
 mhd_status mhd_get_sweep_pencils(mhd_ctx* ctx, int* pencil_mask, int* pencil_len);

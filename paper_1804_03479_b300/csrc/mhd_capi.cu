@@ -63,7 +63,7 @@ static cudaError_t dalloc(mhd_ctx* c, void** p, size_t bytes)
 static cudaError_t layout_tiles(mhd_ctx* c, int tl)
 {
     int t0[3] = {0, 0, 0}, e0 = 0;
-    long long p0[3] = {0, 0, 0}, w0[3] = {0, 0, 0};
+    long long p0[3] = {0, 0, 0}, w0[3] = {0, 0, 0}, r0 = 0;
     for (int b = 0; b < c->nbox; b++) {
         BoxDev& x = c->hbox[b];
         for (int d = 0; d < 3; d++) {
@@ -80,7 +80,10 @@ static cudaError_t layout_tiles(mhd_ctx* c, int tl)
             x.xw0[q] = w0[q];
             w0[q] += xwarp_items_of_box(x.nx, x.ny, x.nz, q);
         }
+        x.xr0 = r0;
+        r0 += (long long)x.ny * x.nz;
     }
+    c->B.nxr = r0;
     c->B.pl = c->pencil_len;
     for (int d = 0; d < 3; d++) c->B.npth[d] = p0[d];
     for (int q = 0; q < 3; q++) c->B.nxw[q] = w0[q];
@@ -158,8 +161,9 @@ static mhd_status init_common(int nbox, const mhd_grid* grids, double gamma, con
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev);
     c->sweep_bps = 4;
-    // VL: pencil sweeps along y and z, tiles along x (the autotuner may change it)
-    c->pencil_mask = scheme->integrator == MHD_VL ? 6 : 0;
+    // VL: register sweeps on every axis (pencils along y and z, warps along x;
+    // the autotuner may change it)
+    c->pencil_mask = scheme->integrator == MHD_VL ? 7 : 0;
     c->pencil_len = 32;
     c->cell_grid = (int)(vb < 16LL * c->nsm ? vb : 16LL * c->nsm);
     if (c->cell_grid < 1) c->cell_grid = 1;

@@ -107,6 +107,11 @@ inline int emf_grid(const mhd_ctx* c)
     return c->B.netile < cap ? c->B.netile : cap;
 }
 
+inline int xrow_grid(const mhd_ctx* c)
+{
+    return (int)((c->B.nxr * 32 + PENCIL_THREADS - 1) / PENCIL_THREADS);
+}
+
 inline int xwarp_grid(const mhd_ctx* c, int slot)
 {
     return (int)((c->B.nxw[slot] * 32 + PENCIL_THREADS - 1) / PENCIL_THREADS);
@@ -150,7 +155,7 @@ void run_step(mhd_ctx* c, bool device_dt)
         // VL steps 1-3: first-order fluxes with the face B_n, edge E, half update
         for (int d = 0; d < 3; d++) {
             if ((c->pencil_mask >> d & 1) && d == 0)
-                k_xwarp<R, RECON, SOLVER, 0, TE><<<xwarp_grid(c, XW<RECON, 0>::slot), PENCIL_THREADS, 0, st>>>(
+                k_xwarp<R, RECON, SOLVER, 0, TE><<<xrow_grid(c), PENCIL_THREADS, 0, st>>>(
                     g, W, s.b[d], F1, gam, XW<RECON, 0>::slot);
             else if (c->pencil_mask >> d & 1)
                 k_pencil<R, RECON, SOLVER, 0, TE><<<pencil_grid(c, d), PENCIL_THREADS, 0, st>>>(
@@ -167,7 +172,7 @@ void run_step(mhd_ctx* c, bool device_dt)
         // VL steps 4-7: reconstruct at the half step, Riemann, edge E, full update
         for (int d = 0; d < 3; d++) {
             if ((c->pencil_mask >> d & 1) && d == 0)
-                k_xwarp<R, RECON, SOLVER, 1, TE><<<xwarp_grid(c, XW<RECON, 1>::slot), PENCIL_THREADS, 0, st>>>(
+                k_xwarp<R, RECON, SOLVER, 1, TE><<<xrow_grid(c), PENCIL_THREADS, 0, st>>>(
                     g, Wh, Bh[d], F1, gam, XW<RECON, 1>::slot);
             else if (c->pencil_mask >> d & 1)
                 k_pencil<R, RECON, SOLVER, 1, TE><<<pencil_grid(c, d), PENCIL_THREADS, 0, st>>>(

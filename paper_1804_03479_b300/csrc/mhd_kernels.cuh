@@ -38,6 +38,7 @@ struct BoxDev {
     int etile0;         // first edge-field tile of the box
     long long pth0[3];  // first pencil-segment thread of the box, per axis
     long long xw0[3];   // first x-warp item of the box: predictor, PLM corrector, PPM corrector
+    long long xr0;      // first grid row (j, k) of the box
 };
 
 // dt of a box and its ratios to dx, in both precisions; written once per
@@ -86,6 +87,7 @@ struct Boxes {
     int pl;             // pencil segment length (faces per thread)
     long long npth[3];  // pencil-segment threads of the batch, per axis
     long long nxw[3];   // x-warp items of the batch: predictor, PLM corrector, PPM corrector
+    long long nxr;      // grid rows of the batch
 };
 
 template <class TU, class TE> struct StateP {
@@ -244,13 +246,17 @@ __global__ void __launch_bounds__(CELL_THREADS) k_prim(Boxes B, StateP<TU, TE> s
         }
         if (smax_part) {
             // virtual-block maximum (the block lies in one box); no atomics
-            red[threadIdx.x] = local;
+            // warp maxima by shuffles, then the 8 warps' through shared memory
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) local = fmax(local, __shfl_xor_sync(0xffffffffu, local, o));
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = local;
             __syncthreads();
-            for (int o = CELL_THREADS / 2; o > 0; o >>= 1) {
-                if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
-                __syncthreads();
+            if (threadIdx.x < 32) {
+                double m = threadIdx.x < CELL_THREADS / 32 ? red[threadIdx.x] : 0.0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+                if (threadIdx.x == 0) smax_part[v] = m;
             }
-            if (threadIdx.x == 0) smax_part[v] = red[0];
             __syncthreads();
         }
     }
@@ -667,9 +673,21 @@ __device__ __forceinline__ void shfl7(R o[7], const R v[7], int up)
         o[m] = up ? __shfl_up_sync(0xffffffffu, v[m], 1) : __shfl_down_sync(0xffffffffu, v[m], 1);
 }
 
-// dslot: the item decomposition (faces per warp xw_faces(dslot), at most the
-// kernel's own); item_list / item_count: only the items of a list (the
-// learned selector's, whose cheap and full kernels share one decomposition)
+__device__ __forceinline__ int box_of_row(const Boxes& B, long long t)
+{
+    int lo = 0, hi = B.nbox - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (B.b[mid].xr0 <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// One warp per grid row, marching its segments of xw_faces(dslot) faces
+// (dslot: the segment length, at most the kernel's own), the next segment's
+// cell loaded while the current one is computed.  With item_list /
+// item_count a warp takes one listed segment instead (the learned
+// selector's lists, whose cheap and full kernels share one decomposition).
 template <class R, int RECON, int SOLVER, int MODE, class TE>
 __global__ void __launch_bounds__(PENCIL_THREADS) k_xwarp(Boxes B, const R* __restrict__ W,
                                                           const TE* __restrict__ Bd, R* __restrict__ F, double gam,
@@ -678,51 +696,72 @@ __global__ void __launch_bounds__(PENCIL_THREADS) k_xwarp(Boxes B, const R* __re
 {
     constexpr int LEAD = XW<RECON, MODE>::lead;
     const int FW = xw_faces(dslot);
-    long long item = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
+    int bi, j, k, sg0, sg1;
     if (item_list) {
-        if (item >= *item_count) return;             // uniform over the warp
-        item = item_list[item];
+        if (wid >= *item_count) return;              // uniform over the warp
+        const long long item = item_list[wid];
+        bi = box_of_xw(B, dslot, item);
+        const BoxDev& gb = B.b[bi];
+        const int nseg = (gb.nx + FW - 1) / FW;
+        long long t = item - gb.xw0[dslot];
+        sg0 = (int)(t % nseg);
+        sg1 = sg0 + 1;
+        t /= nseg;
+        j = (int)(t % gb.ny);
+        k = (int)(t / gb.ny);
+    } else {
+        if (wid >= B.nxr) return;
+        bi = box_of_row(B, wid);
+        const BoxDev& gb = B.b[bi];
+        const long long t = wid - gb.xr0;
+        j = (int)(t % gb.ny);
+        k = (int)(t / gb.ny);
+        sg0 = 0;
+        sg1 = (gb.nx + FW - 1) / FW;
     }
-    if (item >= B.nxw[dslot]) return;
-    const BoxDev g = B.b[box_of_xw(B, dslot, item)];
-    const int nseg = (g.nx + FW - 1) / FW;
-    long long t = item - g.xw0[dslot];
-    const int sg = (int)(t % nseg);
-    t /= nseg;
-    const int j = (int)(t % g.ny), k = (int)(t / g.ny);
-    const long long row = g.off + ((long long)k * g.ny + j) * g.nx;
-    const int xi = sg * FW - LEAD + lane;            // this lane's cell (and the face below it)
-    const long long ci = row + wrapi(xi, g.nx);
+    const int nx = B.b[bi].nx;
+    const long long row = B.b[bi].off + ((long long)k * B.b[bi].ny + j) * nx;
     const long long N = B.N;
     const R gr = R(gam), gm1 = R(gam - 1.0);
-    R w[7], bn, f[7];
-    load_rot(W, N, ci, 0, w, bn);
     const bool face = lane >= LEAD && lane < LEAD + FW;
-    R wl[7], wr[7];
-    if (MODE == 0) {
-        shfl7(wl, w, 1);
-        copy7(wr, w);
-    } else {
-        R wm1[7], wp1[7], wpf[7];
-        shfl7(wm1, w, 1);
-        shfl7(wp1, w, 0);
-        if (RECON == PPM) {
-            R s0[7], sm1[7], sp1[7];
-            char_slope(wm1, w, wp1, bn, gr, s0);
-            shfl7(sm1, s0, 1);
-            shfl7(sp1, s0, 0);
-            recon_cell<PPM, false>(wm1, w, wp1, bn, gr, sm1, s0, sp1, R(0), wr, wpf);
+    R w[7], bn, f[7];
+    load_rot(W, N, row + wrapi(sg0 * FW - LEAD + lane, nx), 0, w, bn);
+    for (int sg = sg0; sg < sg1; sg++) {
+        const int xi = sg * FW - LEAD + lane;        // this lane's cell (and the face below it)
+        const long long ci = row + wrapi(xi, nx);
+        R wn[7], bnn;
+        if (sg + 1 < sg1) load_rot(W, N, row + wrapi(xi + FW, nx), 0, wn, bnn);
+        R wl[7], wr[7];
+        if (MODE == 0) {
+            shfl7(wl, w, 1);
+            copy7(wr, w);
         } else {
-            R dum[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};   // slopes: unused by PLM
-            recon_cell<RECON, false>(wm1, w, wp1, bn, gr, dum, dum, dum, R(0), wr, wpf);
+            R wm1[7], wp1[7], wpf[7];
+            shfl7(wm1, w, 1);
+            shfl7(wp1, w, 0);
+            if (RECON == PPM) {
+                R s0[7], sm1[7], sp1[7];
+                char_slope(wm1, w, wp1, bn, gr, s0);
+                shfl7(sm1, s0, 1);
+                shfl7(sp1, s0, 0);
+                recon_cell<PPM, false>(wm1, w, wp1, bn, gr, sm1, s0, sp1, R(0), wr, wpf);
+            } else {
+                R dum[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};   // slopes: unused by PLM
+                recon_cell<RECON, false>(wm1, w, wp1, bn, gr, dum, dum, dum, R(0), wr, wpf);
+            }
+            shfl7(wl, wpf, 1);                       // the "+" state of the cell below
         }
-        shfl7(wl, wpf, 1);                           // the "+" state of the cell below
-    }
-    if (face && xi < g.nx) {
-        riemann<SOLVER>(wl, wr, R(Bd[ci]), gm1, gr, f);
+        if (face && xi < nx) {
+            riemann<SOLVER>(wl, wr, R(Bd[ci]), gm1, gr, f);
 #pragma unroll
-        for (int m = 0; m < 7; m++) F[(long long)m * N + ci] = f[m];
+            for (int m = 0; m < 7; m++) F[(long long)m * N + ci] = f[m];
+        }
+        if (sg + 1 < sg1) {
+            copy7(w, wn);
+            bn = bnn;
+        }
     }
 }
 

@@ -348,91 +348,104 @@ __global__ void k_mlp_refresh(const float* __restrict__ p, unsigned short* __res
 // ---------------------------------------------------------------------------
 template <class R>
 __global__ void __launch_bounds__(256) k_block_features(BoxDev g, const R* __restrict__ W, long long N, float gam,
-                                                        float* __restrict__ feats)
+                                                           float* __restrict__ feats)
 {
-    const int lane = threadIdx.x & 31;
+    // one thread per 4^3 block, one field at a time: the block's 64 values in
+    // registers, the one-cell halo of its six faces read for the differences
     const int nbx = g.nx / 4, nby = g.ny / 4, nbz = g.nz / 4;
     const long long nblk = (long long)nbx * nby * nbz;
-    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long b = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); b < nblk; b += warps) {
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nblk;
+         b += (long long)gridDim.x * blockDim.x) {
         const int ib = (int)(b % nbx), jb = (int)((b / nbx) % nby), kb = (int)(b / ((long long)nbx * nby));
-        float sum[8], mn[8], mx[8], dm[3][8], wv[2][8], vabs = 0.f, b2s = 0.f;
+        const int i0 = 4 * ib, j0 = 4 * jb, k0 = 4 * kb;
+        const int im = wrapi(i0 - 1, g.nx), ip = wrapi(i0 + 4, g.nx);
+        const int jm = wrapi(j0 - 1, g.ny), jp = wrapi(j0 + 4, g.ny);
+        const int km = wrapi(k0 - 1, g.nz), kp = wrapi(k0 + 4, g.nz);
+        float mean[8], rng[8], dd[3][8], sd[8];
+        for (int f = 0; f < 8; f++) {
+            const R* Wf = W + (long long)f * N;
+            const R* bp = Wf + cell_of(g, i0, j0, k0);     // the block never wraps (sides % 4 == 0)
+            const int sy = g.nx, sz = g.nx * g.ny;
+            float v[64];
+            float sum = 0.f, mn = 3e38f, mx = -3e38f;
 #pragma unroll
-        for (int f = 0; f < 8; f++) { sum[f] = 0.f; mn[f] = 3e38f; mx[f] = -3e38f; dm[0][f] = dm[1][f] = dm[2][f] = 0.f; }
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const int li = lane & 3, lj = (lane >> 2) & 3, lk = (lane >> 4) + 2 * h;
-            const int i = 4 * ib + li, j = 4 * jb + lj, k = 4 * kb + lk;
-            const long long c = cell_of(g, i, j, k);
-#pragma unroll
-            for (int f = 0; f < 8; f++) {
-                const float w = (float)W[f * N + c];
-                wv[h][f] = w;
-                sum[f] += w;
-                mn[f] = fminf(mn[f], w);
-                mx[f] = fmaxf(mx[f], w);
+            for (int q = 0; q < 64; q++) {
+                v[q] = (float)bp[(q >> 4) * sz + ((q >> 2) & 3) * sy + (q & 3)];
+                sum += v[q];
+                mn = fminf(mn, v[q]);
+                mx = fmaxf(mx, v[q]);
             }
-            vabs += sqrtf(wv[h][1] * wv[h][1] + wv[h][2] * wv[h][2] + wv[h][3] * wv[h][3]);
-            b2s += wv[h][5] * wv[h][5] + wv[h][6] * wv[h][6] + wv[h][7] * wv[h][7];
+            float dx = 0.f, dy = 0.f, dz = 0.f;
 #pragma unroll
-            for (int d = 0; d < 3; d++) {
-                const long long cp = nbr(g, i, j, k, d, 1);
-                const int lo = d == 0 ? li : (d == 1 ? lj : lk);
-                const long long cm = lo == 0 ? nbr(g, i, j, k, d, -1) : -1;
+            for (int q = 0; q < 64; q++) {
+                if ((q & 3) < 3) dx = fmaxf(dx, fabsf(v[q + 1] - v[q]));
+                if (((q >> 2) & 3) < 3) dy = fmaxf(dy, fabsf(v[q + 4] - v[q]));
+                if ((q >> 4) < 3) dz = fmaxf(dz, fabsf(v[q + 16] - v[q]));
+            }
+            // differences across the six faces: the face cell and its halo
+            // neighbour, both read from memory (no dynamic index into v)
+#pragma unroll 1
+            for (int a = 0; a < 4; a++) {
 #pragma unroll
-                for (int f = 0; f < 8; f++) {
-                    dm[d][f] = fmaxf(dm[d][f], fabsf((float)W[f * N + cp] - wv[h][f]));
-                    if (cm >= 0) dm[d][f] = fmaxf(dm[d][f], fabsf(wv[h][f] - (float)W[f * N + cm]));
+                for (int c2 = 0; c2 < 4; c2++) {
+                    const float x0v = (float)Wf[cell_of(g, i0, j0 + a, k0 + c2)];
+                    const float x3v = (float)Wf[cell_of(g, i0 + 3, j0 + a, k0 + c2)];
+                    const float xl = (float)Wf[cell_of(g, im, j0 + a, k0 + c2)];
+                    const float xh = (float)Wf[cell_of(g, ip, j0 + a, k0 + c2)];
+                    const float y0v = (float)Wf[cell_of(g, i0 + a, j0, k0 + c2)];
+                    const float y3v = (float)Wf[cell_of(g, i0 + a, j0 + 3, k0 + c2)];
+                    const float yl = (float)Wf[cell_of(g, i0 + a, jm, k0 + c2)];
+                    const float yh = (float)Wf[cell_of(g, i0 + a, jp, k0 + c2)];
+                    const float z0v = (float)Wf[cell_of(g, i0 + a, j0 + c2, k0)];
+                    const float z3v = (float)Wf[cell_of(g, i0 + a, j0 + c2, k0 + 3)];
+                    const float zl = (float)Wf[cell_of(g, i0 + a, j0 + c2, km)];
+                    const float zh = (float)Wf[cell_of(g, i0 + a, j0 + c2, kp)];
+                    dx = fmaxf(dx, fmaxf(fabsf(x0v - xl), fabsf(xh - x3v)));
+                    dy = fmaxf(dy, fmaxf(fabsf(y0v - yl), fabsf(yh - y3v)));
+                    dz = fmaxf(dz, fmaxf(fabsf(z0v - zl), fabsf(zh - z3v)));
                 }
             }
+            const float m = sum * (1.f / 64.f);
+            float sq = 0.f;
+#pragma unroll
+            for (int q = 0; q < 64; q++) {
+                const float e = v[q] - m;
+                sq += e * e;
+            }
+            mean[f] = m;
+            rng[f] = mx - mn;
+            dd[0][f] = dx;
+            dd[1][f] = dy;
+            dd[2][f] = dz;
+            sd[f] = sqrtf(sq * (1.f / 64.f));
         }
-        // warp reductions; the variance takes a second pass about the mean
-        float sq[8];
+        float vabs = 0.f, b2s = 0.f;
+        for (int q = 0; q < 64; q++) {
+            const long long c = cell_of(g, i0 + (q & 3), j0 + ((q >> 2) & 3), k0 + (q >> 4));
+            const float vx = (float)W[N + c], vy = (float)W[2 * N + c], vz = (float)W[3 * N + c];
+            const float bx = (float)W[5 * N + c], by = (float)W[6 * N + c], bz = (float)W[7 * N + c];
+            vabs += sqrtf(vx * vx + vy * vy + vz * vz);
+            b2s += bx * bx + by * by + bz * bz;
+        }
+        const float inv = 1.f / 64.f;
+        const float rho = mean[0], P = fmaxf(mean[4], 1e-30f);
+        const float b2 = b2s * inv;
+        const float cref = sqrtf((gam * P + b2) / fmaxf(rho, 1e-30f));
+        const float bref = sqrtf(b2 + P);
+        const float scale[8] = {rho, cref, cref, cref, P, bref, bref, bref};
+        float* out = feats + b * NF;
 #pragma unroll
         for (int f = 0; f < 8; f++) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                sum[f] += __shfl_xor_sync(0xffffffffu, sum[f], o);
-                mn[f] = fminf(mn[f], __shfl_xor_sync(0xffffffffu, mn[f], o));
-                mx[f] = fmaxf(mx[f], __shfl_xor_sync(0xffffffffu, mx[f], o));
-                dm[0][f] = fmaxf(dm[0][f], __shfl_xor_sync(0xffffffffu, dm[0][f], o));
-                dm[1][f] = fmaxf(dm[1][f], __shfl_xor_sync(0xffffffffu, dm[1][f], o));
-                dm[2][f] = fmaxf(dm[2][f], __shfl_xor_sync(0xffffffffu, dm[2][f], o));
-            }
-            const float mean = sum[f] * (1.f / 64.f);
-            const float d0 = wv[0][f] - mean, d1 = wv[1][f] - mean;
-            sq[f] = d0 * d0 + d1 * d1;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) sq[f] += __shfl_xor_sync(0xffffffffu, sq[f], o);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            vabs += __shfl_xor_sync(0xffffffffu, vabs, o);
-            b2s += __shfl_xor_sync(0xffffffffu, b2s, o);
-        }
-        if (lane == 0) {
-            const float inv = 1.f / 64.f;
-            const float rho = sum[0] * inv, P = fmaxf(sum[4] * inv, 1e-30f);
-            const float b2 = b2s * inv;
-            const float cref = sqrtf((gam * P + b2) / fmaxf(rho, 1e-30f));
-            const float bref = sqrtf(b2 + P);
-            const float scale[8] = {rho, cref, cref, cref, P, bref, bref, bref};
-            float* out = feats + b * NF;
-#pragma unroll
-            for (int f = 0; f < 8; f++) {
-                const float is = 1.f / fmaxf(scale[f], 1e-30f);
-                const float mean = sum[f] * inv;
-                const float var = sq[f] * inv;
-                float m0 = mean * is;
-                if (f == 0) m0 = fminf(fmaxf(log10f(2.f * P / fmaxf(b2, 1e-30f)), -6.f), 6.f) / 6.f;
-                if (f == 4) m0 = vabs * inv / cref;
-                out[f * 6 + 0] = m0;
-                out[f * 6 + 1] = (mx[f] - mn[f]) * is;
-                out[f * 6 + 2] = dm[0][f] * is;
-                out[f * 6 + 3] = dm[1][f] * is;
-                out[f * 6 + 4] = dm[2][f] * is;
-                out[f * 6 + 5] = sqrtf(var) * is;
-            }
+            const float is = 1.f / fmaxf(scale[f], 1e-30f);
+            float m0 = mean[f] * is;
+            if (f == 0) m0 = fminf(fmaxf(log10f(2.f * P / fmaxf(b2, 1e-30f)), -6.f), 6.f) / 6.f;
+            if (f == 4) m0 = vabs * inv / cref;
+            out[f * 6 + 0] = m0;
+            out[f * 6 + 1] = rng[f] * is;
+            out[f * 6 + 2] = dd[0][f] * is;
+            out[f * 6 + 3] = dd[1][f] * is;
+            out[f * 6 + 4] = dd[2][f] * is;
+            out[f * 6 + 5] = sd[f] * is;
         }
     }
 }

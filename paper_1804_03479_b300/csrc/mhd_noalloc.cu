@@ -131,6 +131,8 @@ extern "C" mhd_status mhd_step_noalloc(const mhd_grid* grid, double gamma, const
         hb.xw0[d] = 0;
         c.B.nxw[d] = xwarp_items_of_box(hb.nx, hb.ny, hb.nz, d);
     }
+    hb.xr0 = 0;
+    c.B.nxr = (long long)hb.ny * hb.nz;
     int nsm = 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return reject(MHD_ECUDA, "mhd_step_noalloc: device query failed");
