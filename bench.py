@@ -455,30 +455,59 @@ def learned_variant(torch, mhd, K, stream):
                          "floored_cell_steps": stats.get("floored_cell_steps")}}
 
 
-def e2e(torch, mhd, st, prec, scheme, K, stream):
+def e2e(torch, mhd, st, prec, scheme, K, stream, nstreams=2):
     """same metric through the C ABI with host buffers: each step copies the
-    state in from pinned host memory, advances, copies it back out"""
+    state in from pinned host memory (mhd_set_state), advances one step
+    (mhd_advance) and copies the state back out (mhd_get_state).  With
+    nstreams > 1, as many contexts run on their own CUDA streams from as many
+    host threads (the calls release the GIL), so one context's copies
+    overlap another's step; every step still carries its own copies."""
+    import threading
     integ, recon, riemann = scheme
     cast = torch.float32 if prec == "fp32" else torch.float64
     Uh = torch.from_numpy(st.U).to(dtype=cast).pin_memory()
     Bh = torch.from_numpy(st.B).to(dtype=cast).pin_memory()
-    Uo = torch.empty_like(Uh).pin_memory()
-    Bo = torch.empty_like(Bh).pin_memory()
-    s = mhd.Solver(st.U.shape[1:], st.dx, st.gamma, integ, recon, riemann, prec, 0.3, stream=stream.cuda_stream)
-    s.set_state(Uh, Bh)
-    s.advance(1)
-    s.get_state(Uo, Bo)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(K):
-        s.set_state(Uh, Bh)
-        s.advance(1)
-        s.get_state(Uo, Bo)
-    el = time.perf_counter() - t0
-    s.free()
+    n = st.U[0].size
     nbytes = Uh.numel() * Uh.element_size() + Bh.numel() * Bh.element_size()
-    return {"value": st.U[0].size * K / el, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-            "steps": K, "path": "mhd_set_state(host) + mhd_advance(1) + mhd_get_state(host)"}
+
+    def run(ns, steps):
+        ctxs = []
+        for q in range(ns):
+            sq = torch.cuda.Stream()
+            s = mhd.Solver(st.U.shape[1:], st.dx, st.gamma, integ, recon, riemann, prec, 0.3,
+                           stream=sq.cuda_stream)
+            Uo = torch.empty_like(Uh).pin_memory()
+            Bo = torch.empty_like(Bh).pin_memory()
+            s.set_state(Uh, Bh)
+            s.advance(1)
+            s.get_state(Uo, Bo)
+            ctxs.append((s, Uo, Bo, sq))
+        torch.cuda.synchronize()
+        each = max(1, steps // ns)
+
+        def work(s, Uo, Bo):
+            for _ in range(each):
+                s.set_state(Uh, Bh)
+                s.advance(1)
+                s.get_state(Uo, Bo)
+
+        th = [threading.Thread(target=work, args=c[:3]) for c in ctxs]
+        t0 = time.perf_counter()
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        el = time.perf_counter() - t0
+        for c in ctxs:
+            c[0].free()
+        return n * each * ns / el, each * ns
+
+    serial, _ = run(1, K)
+    value, done = run(nstreams, K) if nstreams > 1 else (serial, K)
+    return {"value": value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+            "steps": done, "streams": nstreams, "one_stream_value": serial,
+            "path": "mhd_set_state(host) + mhd_advance(1) + mhd_get_state(host), "
+                    f"{nstreams} contexts on their own streams and host threads"}
 
 
 def run_stress(args):
@@ -664,7 +693,7 @@ def main():
             variants["learned384"] = learned_variant(torch, mhd, max(3, min(args.steps, 10)), stream)
         line["variants"] = variants
         if not args.no_e2e:
-            line["e2e"] = e2e(torch, mhd, st, args.precision, scheme, max(3, min(args.steps, 8)), stream)
+            line["e2e"] = e2e(torch, mhd, st, args.precision, scheme, max(4, min(args.steps, 16)), stream)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(scheme)
         print(json.dumps(line), flush=True)

@@ -297,3 +297,29 @@ def test_mixed_precision_stress_small(M):
     assert res["mixed"]["divB"] <= 1e-13
     assert res["mixed"]["rho"] <= 1e-3 and res["mixed"]["e"] <= 1e-3 and res["mixed"]["B"] <= 1e-3
     assert res["mixed"]["e"] < res["fp32"]["e"]
+
+
+@pytest.mark.parametrize("recon", ["plm", "ppm"])
+def test_fp64_parity_roe_fallback(M, recon):
+    """Two strong rarefactions (rho = 1, u = -/+2, P = 0.4, Toro's test 2) with
+    a uniform oblique field along x in a 64 x 4 x 4 box: the Roe fan of the
+    faces at the split has a state with P <= 0, so those faces fall back to
+    HLLE (the oracle counts them).  The GPU's fan check, including its cheap
+    bound that skips the check on smooth faces, must take the same decisions:
+    FP64 parity at the 1e-12 bar."""
+    nx, ny, nz = 64, 4, 4
+    dx = 1.0 / nx
+    gam = 5.0 / 3.0
+    x = (np.arange(nx) + 0.5) * dx
+    u = np.where((x > 0.25) & (x < 0.75), 2.0, -2.0)
+    rho = np.ones((nz, ny, nx))
+    vx = np.broadcast_to(u, (nz, ny, nx)).copy()
+    z = np.zeros((nz, ny, nx))
+    B = np.stack([np.full((nz, ny, nx), 0.5), np.full((nz, ny, nx), 0.3), np.full((nz, ny, nx), 0.2)])
+    U = I.conserved(rho, vx, z, z, np.full((nz, ny, nx), 0.4), B, gam)
+    st = I.State(U, B, dx, gam, {})
+    Uo, Bo = U.copy(), B.copy()
+    dt = orc.cfl_dt(Uo, Bo, dx, gam, 0.3)
+    nfb = orc.step(Uo, Bo, dx, gam, dt, "vl", recon, "roe")
+    assert nfb > 0
+    run_parity(M, st, "vl", recon, "roe", 3)
