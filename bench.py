@@ -50,25 +50,25 @@ def stages_of(groups):
         out[k] = out.get(k, 0.0) + v
     return {k: out[k] for k in STAGES if k in out}
 SIZES = {"fp64": (8, 8, 8), "fp32": (4, 4, 4), "mixed": (4, 8, 4)}   # (rho/M, e/B, arithmetic) bytes
-# Algorithmic floating-point operations per face of one VL + PLM + Roe sweep
-# launch: corrector = one cell's characteristic PLM reconstruction and one
-# Roe solve, predictor = one Roe solve.  They are the FADD + FMUL + 2 FFMA
-# counts that ncu reports for the FP32 pencil kernels at 160^3 (y sweeps: one
-# reconstruction per face plus the segment's 1/32 lead-in), where every
-# divide and square root is a single MUFU op.  The same algorithm runs in the
-# FP64 build, whose divides and square roots expand into FMA iterations, so
-# the algorithmic figures are used for all precisions.
-FLOPS_PER_FACE = {"corrector": {"fp32": 959.0, "fp64": 959.0, "mixed": 959.0},
-                  "predictor": {"fp32": 688.0, "fp64": 688.0, "mixed": 688.0}}
+# Floating-point operations per face of one VL + PLM + Roe sweep launch:
+# corrector = one cell's characteristic PLM reconstruction and one Roe solve,
+# predictor = one Roe solve.  They are the FADD + FMUL + 2 FFMA counts that
+# ncu reports for the FP32 pencil kernels at 160^3 (y sweeps: one
+# reconstruction per face plus the segment's 1/32 lead-in; the Roe fan check
+# skipped where its bound proves it passes), where every divide and square
+# root is a single MUFU op.  The same arithmetic runs in the FP64 build, whose
+# divides and square roots expand into FMA iterations (1186 executed FP64
+# flops per corrector face at 128^3), so these figures serve all precisions.
+FLOPS_PER_FACE = {"corrector": {"fp32": 705.0, "fp64": 705.0, "mixed": 705.0},
+                  "predictor": {"fp32": 435.0, "fp64": 435.0, "mixed": 435.0}}
 # DRAM bytes (read + write) per face of one sweep launch, per kernel, from
 # dram__bytes_read.sum + dram__bytes_write.sum of the ncu captures in
-# profiles/ (FP32 at 160^3: pencil corrector 263.5 MB, x-warp corrector
-# 219.4 MB, pencil predictor 237.5 MB, tile corrector 237.1 MB, tile
-# predictor 217.8 MB; FP64 tile corrector 238.8 MB at 128^3), scaled to other
-# sizes by faces.
-TRAFFIC_PER_FACE = {"corrector_pencil": {"fp32": 64.3}, "corrector_xwarp": {"fp32": 53.6},
-                    "predictor_pencil": {"fp32": 58.0},
-                    "corrector_tile": {"fp32": 57.9, "fp64": 113.9}, "predictor_tile": {"fp32": 53.2}}
+# profiles/ (FP32 at 160^3: pencil corrector 263.2 MB, pencil predictor
+# 236.6 MB, x-warp corrector 219.3 MB; FP64 pencil corrector 255.3 MB at
+# 128^3), scaled to other sizes by faces; a kernel changed since its capture
+# has none.
+TRAFFIC_PER_FACE = {"corrector_pencil": {"fp32": 64.3, "fp64": 121.8}, "predictor_pencil": {"fp32": 57.8},
+                    "corrector_xwarp": {"fp32": 53.5}}
 
 
 def peaks():
