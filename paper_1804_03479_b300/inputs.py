@@ -427,6 +427,36 @@ def uniform(n, rho=1.0, v=(0.3, -0.2, 0.1), P=0.7, Bv=(0.4, -0.5, 0.6), gamma=5.
     return State(U, np.ascontiguousarray(B), 1.0 / nx, gamma, dict(kind="uniform"))
 
 
+def shock_tube(wl, wr, bn, n, axis=0, m=2, L=2.0, gamma=5.0 / 3.0):
+    """1-D Riemann problem (Sec. 5.1 (ii), Table 1 states) on a periodic line
+    of length L along `axis`, with m cells across: the left state fills
+    [L/4, 3L/4) and the right state the rest, so the problem itself sits at
+    3L/4 and its mirror image at L/4; both fans stay apart while their speeds
+    times t are below L/4.  wl, wr = (rho, v_n, v_t1, v_t2, P, B_t1, B_t2) in
+    the frame of `axis` (t1 = axis+1, t2 = axis+2 cyclic), bn the uniform
+    normal field.  Face fields are the (piecewise constant) cell values."""
+    dx = L / n
+    shp = [m, m, m]
+    shp[2 - axis] = n                        # array order (z, y, x)
+    line = (np.arange(n) + 0.5) * dx
+    left = (line >= 0.25 * L) & (line < 0.75 * L)
+    wl, wr = np.asarray(wl, float), np.asarray(wr, float)
+    prof = np.where(left[None, :], wl[:, None], wr[:, None])     # (7, n)
+    bshape = [1, 1, 1]
+    bshape[2 - axis] = n
+    def field(v):
+        return np.broadcast_to(v.reshape(bshape), shp).copy()
+    t1, t2 = (axis + 1) % 3, (axis + 2) % 3
+    vel = [None] * 3
+    vel[axis], vel[t1], vel[t2] = field(prof[1]), field(prof[2]), field(prof[3])
+    Bc = [None] * 3
+    Bc[axis] = np.full(shp, float(bn))
+    Bc[t1], Bc[t2] = field(prof[5]), field(prof[6])
+    B = np.stack(Bc)
+    U = conserved(field(prof[0]), vel[0], vel[1], vel[2], field(prof[4]), B, gamma)
+    return State(U, np.ascontiguousarray(B), dx, gamma, dict(kind="shock_tube", axis=axis, L=L))
+
+
 def box_sides(nbox=48, seed=1, choices=(32, 48, 64, 96, 128, 192)):
     """Side lengths of the batched uneven workload: uniform over `choices`."""
     rng = np.random.default_rng(seed)

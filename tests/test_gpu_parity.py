@@ -323,3 +323,29 @@ def test_fp64_parity_roe_fallback(M, recon):
     nfb = orc.step(Uo, Bo, dx, gam, dt, "vl", recon, "roe")
     assert nfb > 0
     run_parity(M, st, "vl", recon, "roe", 3)
+
+
+def _table1(name):
+    import math
+    path = __file__.replace("test_gpu_parity.py", "golden/table1_riemann_states.txt")
+    for line in open(path):
+        if line.startswith(name + " "):
+            v = [float(eval(t, {"math": math})) for t in line.split()[1:]]
+            return np.array(v[0:7]), np.array(v[7:14]), v[14]
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name,axis,scheme", [("torrilhon", 0, ("vl", "plm", "roe")), ("rj2a", 1, ("vl", "ppm", "hlld")),
+                                              ("rj2a", 2, ("vl", "plm", "roe")), ("torrilhon", 1, ("ctu", "ppm", "hlld")),
+                                              ("rj2a", 0, ("ctu", "plm", "roe"))])
+def test_fp64_parity_table1_tubes(M, name, axis, scheme):
+    """the Table 1 Riemann problems along x (warp sweeps), y and z (pencils),
+    on a 192-cell line with 2 x 2 cells across: FP64 parity per step"""
+    wl, wr, bn = _table1(name)
+    st = I.shock_tube(wl, wr, bn, 192, axis=axis, m=2)
+    U, B = st.U.copy(), st.B.copy()
+    # first advance the oracle into the developed fan, then compare step by step
+    for _ in range(20):
+        dt = orc.cfl_dt(U, B, st.dx, st.gamma, 0.3)
+        orc.step(U, B, st.dx, st.gamma, dt, *scheme)
+    run_parity(M, I.State(U, B, st.dx, st.gamma, {}), *scheme, 4)
