@@ -32,17 +32,29 @@ typedef struct {
     long n;
     double dx, gam;
     double pfloor;   /* pressure floor, 0 = none (see prim_floor) */
+    int bc;          /* bit d set: outflow (zero-gradient) boundaries along axis d, else periodic */
 } grid_t;
+
+/* index along an axis of n cells: periodic wrap, or for an outflow axis the */
+/* nearest cell (zero-gradient ghost cells; the same rule maps the face or    */
+/* edge beyond the last cell onto the last one, so the outer face field and   */
+/* edge fields continue the last interior ones)                               */
+static int bidx(int i, int n, int outflow)
+{
+    if (outflow) return i < 0 ? 0 : (i >= n ? n - 1 : i);
+    i %= n;
+    return i < 0 ? i + n : i;
+}
 
 static long cidx(const grid_t *g, int i, int j, int k)
 {
-    i %= g->nx; if (i < 0) i += g->nx;
-    j %= g->ny; if (j < 0) j += g->ny;
-    k %= g->nz; if (k < 0) k += g->nz;
+    i = bidx(i, g->nx, g->bc & 1);
+    j = bidx(j, g->ny, g->bc & 2);
+    k = bidx(k, g->nz, g->bc & 4);
     return ((long)k * g->ny + j) * g->nx + i;
 }
 
-/* neighbour of cell c shifted by s along axis d (periodic) */
+/* neighbour of cell c shifted by s along axis d (periodic or outflow) */
 static long shift(const grid_t *g, long c, int d, int s)
 {
     int i = (int)(c % g->nx), j = (int)((c / g->nx) % g->ny), k = (int)(c / ((long)g->nx * g->ny));
@@ -590,8 +602,21 @@ static void rot_prim(const grid_t *g, const double *W, long c, int d, double w[7
     *bn = W[(5 + d) * n + c];
 }
 
-/* Eq. 10: conservative update U -= h * div F (F[d][7][n] in sweep frames)  */
-static void fv_update(const grid_t *g, double h, const double *Usrc, const double *F, double *Udst)
+/* Eq. 10: conservative update U -= h * div F (F[d][7][n] in sweep frames).  */
+/* Along an outflow axis the last cell's upper face is not stored: its flux  */
+/* is the Riemann flux between the last cell and its zero-gradient ghost.    */
+/* Both face states are the last cell's state Wst (the stage's primitives),  */
+/* since the limited slope against a copied ghost is zero for PLM and PPM,  */
+/* with the normal field of the last face.                                   */
+static int is_last(const grid_t *g, long c, int d)
+{
+    if (d == 0) return (int)(c % g->nx) == g->nx - 1;
+    if (d == 1) return (int)((c / g->nx) % g->ny) == g->ny - 1;
+    return (int)(c / ((long)g->nx * g->ny)) == g->nz - 1;
+}
+
+static void fv_update(const grid_t *g, double h, const double *Usrc, const double *F, double *Udst,
+                      const double *Wst, const double *Bst, int riemann)
 {
     long n = g->n;
     double r = h / g->dx;
@@ -603,7 +628,14 @@ static void fv_update(const grid_t *g, double h, const double *Usrc, const doubl
             long cp = shift(g, c, d, 1);
             const double *Fd = F + (long)d * 7 * n;
             double df[7];
-            for (int k = 0; k < 7; k++) df[k] = Fd[k * n + cp] - Fd[k * n + c];
+            if ((g->bc >> d & 1) && is_last(g, c, d)) {
+                double w[7], bdum, fu[7];
+                rot_prim(g, Wst, c, d, w, &bdum);
+                orc_riemann(riemann, w, w, Bst[d * n + c], g->gam, fu);
+                for (int k = 0; k < 7; k++) df[k] = fu[k] - Fd[k * n + c];
+            } else {
+                for (int k = 0; k < 7; k++) df[k] = Fd[k * n + cp] - Fd[k * n + c];
+            }
             du[0] += df[0];
             du[1 + d] += df[1];
             du[1 + t1] += df[2];
@@ -742,13 +774,13 @@ static long step_vl(const grid_t *g, int recon, int riemann, double dt, double *
     *nfloor += prim_floor(g, U, B, W, U + 4 * n);
     nfb += fluxes(g, recon, riemann, 1, 0, dt, W, B, F, NULL, NULL);
     edge_emf(g, F, W, E);
-    fv_update(g, 0.5 * dt, U, F, Uh);
+    fv_update(g, 0.5 * dt, U, F, Uh, W, B, riemann);
     ct_update(g, 0.5 * dt, B, E, Bh);
     /* steps 4-7: reconstruct at the half step, Riemann, edge E, full update */
     prim_all(g, Uh, Bh, W);
     nfb += fluxes(g, recon, riemann, 0, 0, dt, W, Bh, F, NULL, NULL);
     edge_emf(g, F, W, E);
-    fv_update(g, dt, U, F, U);
+    fv_update(g, dt, U, F, U, W, Bh, riemann);
     ct_update(g, dt, B, E, B);
     free(W); free(F); free(E); free(Uh); free(Bh);
     return nfb;
@@ -813,7 +845,7 @@ static long step_ctu(const grid_t *g, int recon, int riemann, double dt, double 
     edge_emf(g, F, W, E);
     /* step 4: dt/2 CT update of face B and conservative update of U */
     ct_update(g, hdt, B, E, Bh);
-    fv_update(g, hdt, U, F, Uh);
+    fv_update(g, hdt, U, F, Uh, NULL, NULL, riemann);
     /* step 5: transverse flux-gradient correction of the traced states.     */
     /* The state of cell s on a d-face, as 8 conserved components (B_n of    */
     /* cell s at its centre), receives -dt/2 times the divergence of the     */
@@ -883,7 +915,7 @@ static long step_ctu(const grid_t *g, int recon, int riemann, double dt, double 
     prim_all(g, Uh, Bh, W);
     edge_emf(g, F2, W, E);
     /* step 8: full update */
-    fv_update(g, dt, U, F2, U);
+    fv_update(g, dt, U, F2, U, NULL, NULL, riemann);
     ct_update(g, dt, B, E, B);
     free(W); free(F); free(F2); free(E); free(Uh); free(Bh); free(WM); free(WP);
     return nfb;
@@ -893,15 +925,26 @@ static long step_ctu(const grid_t *g, int recon, int riemann, double dt, double 
 /* Exported whole-grid entry points                                          */
 /* ------------------------------------------------------------------------ */
 
-/* advance U, B in place by dt with a pressure floor (0 = none); returns the */
-/* number of Roe->HLLE fallbacks, the floored cells in *nfloor               */
+/* advance U, B in place by dt with a pressure floor (0 = none) and the     */
+/* boundary mask bc (bit d: outflow along axis d; VL only); returns the      */
+/* number of Roe->HLLE fallbacks (-1 for CTU with outflow), the floored      */
+/* cells in *nfloor                                                          */
+long orc_step_full(int nx, int ny, int nz, double dx, double gam, int integrator, int recon, int riemann,
+                   double dt, double pfloor, int bc, double *U, double *B, long *nfloor)
+{
+    grid_t g = {nx, ny, nz, (long)nx * ny * nz, dx, gam, pfloor, bc};
+    *nfloor = 0;
+    if (integrator == CTU) {
+        if (bc) return -1;
+        return step_ctu(&g, recon, riemann, dt, U, B, nfloor);
+    }
+    return step_vl(&g, recon, riemann, dt, U, B, nfloor);
+}
+
 long orc_step_floor(int nx, int ny, int nz, double dx, double gam, int integrator, int recon, int riemann,
                     double dt, double pfloor, double *U, double *B, long *nfloor)
 {
-    grid_t g = {nx, ny, nz, (long)nx * ny * nz, dx, gam, pfloor};
-    *nfloor = 0;
-    if (integrator == CTU) return step_ctu(&g, recon, riemann, dt, U, B, nfloor);
-    return step_vl(&g, recon, riemann, dt, U, B, nfloor);
+    return orc_step_full(nx, ny, nz, dx, gam, integrator, recon, riemann, dt, pfloor, 0, U, B, nfloor);
 }
 
 /* advance U, B in place by dt; returns the number of Roe->HLLE fallbacks */
@@ -909,15 +952,16 @@ long orc_step(int nx, int ny, int nz, double dx, double gam, int integrator, int
               double dt, double *U, double *B)
 {
     long nf = 0;
-    return orc_step_floor(nx, ny, nz, dx, gam, integrator, recon, riemann, dt, 0.0, U, B, &nf);
+    return orc_step_full(nx, ny, nz, dx, gam, integrator, recon, riemann, dt, 0.0, 0, U, B, &nf);
 }
 
 /* CFL time step (Sec. 3.2): cfl * dx / max over cells and axes of |v_d| + c_f,d, */
-/* with the pressure floor of the step applied to P (0 = none)                    */
-double orc_cfl_dt_floor(int nx, int ny, int nz, double dx, double gam, double cfl, double pfloor, const double *U,
-                        const double *B)
+/* with the pressure floor of the step applied to P (0 = none) and the boundary   */
+/* mask of the step (the cell-centre field of the last cell along an outflow axis) */
+double orc_cfl_dt_full(int nx, int ny, int nz, double dx, double gam, double cfl, double pfloor, int bc,
+                       const double *U, const double *B)
 {
-    grid_t g = {nx, ny, nz, (long)nx * ny * nz, dx, gam, pfloor};
+    grid_t g = {nx, ny, nz, (long)nx * ny * nz, dx, gam, pfloor, bc};
     long n = g.n;
     double *W = malloc(sizeof(double) * 8 * n);
     prim_all(&g, U, B, W);
@@ -936,16 +980,22 @@ double orc_cfl_dt_floor(int nx, int ny, int nz, double dx, double gam, double cf
     return cfl * dx / smax;
 }
 
+double orc_cfl_dt_floor(int nx, int ny, int nz, double dx, double gam, double cfl, double pfloor, const double *U,
+                        const double *B)
+{
+    return orc_cfl_dt_full(nx, ny, nz, dx, gam, cfl, pfloor, 0, U, B);
+}
+
 double orc_cfl_dt(int nx, int ny, int nz, double dx, double gam, double cfl, const double *U, const double *B)
 {
-    return orc_cfl_dt_floor(nx, ny, nz, dx, gam, cfl, 0.0, U, B);
+    return orc_cfl_dt_full(nx, ny, nz, dx, gam, cfl, 0.0, 0, U, B);
 }
 
 /* Eq. 16 times dx: max_c |sum_d (B_d(c+e_d) - B_d(c))|, and B_rms of the     */
 /* cell-centred field                                                         */
-void orc_divB(int nx, int ny, int nz, const double *B, double *maxabs, double *brms)
+void orc_divB_bc(int nx, int ny, int nz, int bc, const double *B, double *maxabs, double *brms)
 {
-    grid_t g = {nx, ny, nz, (long)nx * ny * nz, 1.0, 0.0};
+    grid_t g = {nx, ny, nz, (long)nx * ny * nz, 1.0, 0.0, 0.0, bc};
     long n = g.n;
     double m = 0.0, s2 = 0.0;
     for (long c = 0; c < n; c++) {
@@ -953,14 +1003,19 @@ void orc_divB(int nx, int ny, int nz, const double *B, double *maxabs, double *b
         for (int d = 0; d < 3; d++) {
             double bp = B[d * n + shift(&g, c, d, 1)], b0 = B[d * n + c];
             dv += bp - b0;
-            double bc = 0.5 * (bp + b0);
-            b2 += bc * bc;
+            double bc_ = 0.5 * (bp + b0);
+            b2 += bc_ * bc_;
         }
         if (fabs(dv) > m) m = fabs(dv);
         s2 += b2;
     }
     *maxabs = m;
     *brms = sqrt(s2 / (double)n);
+}
+
+void orc_divB(int nx, int ny, int nz, const double *B, double *maxabs, double *brms)
+{
+    orc_divB_bc(nx, ny, nz, 0, B, maxabs, brms);
 }
 
 /* sums of rho, Mx, My, Mz, e over cells and of Bx, By, Bz over faces */
@@ -976,10 +1031,15 @@ void orc_sums(int nx, int ny, int nz, const double *U, const double *B, double o
 }
 
 /* cell-centred primitives, exported for diagnostics */
+void orc_prim_bc(int nx, int ny, int nz, double gam, int bc, const double *U, const double *B, double *W)
+{
+    grid_t g = {nx, ny, nz, (long)nx * ny * nz, 1.0, gam, 0.0, bc};
+    prim_all(&g, U, B, W);
+}
+
 void orc_prim(int nx, int ny, int nz, double gam, const double *U, const double *B, double *W)
 {
-    grid_t g = {nx, ny, nz, (long)nx * ny * nz, 1.0, gam};
-    prim_all(&g, U, B, W);
+    orc_prim_bc(nx, ny, nz, gam, 0, U, B, W);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -53,6 +53,15 @@ def lib():
                                     [ctypes.c_double, ctypes.c_double, dp, dp, ctypes.POINTER(ctypes.c_long)]
         L.orc_cfl_dt_floor.restype = ctypes.c_double
         L.orc_cfl_dt_floor.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double] * 4 + [dp, dp]
+        L.orc_step_full.restype = ctypes.c_long
+        L.orc_step_full.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [ctypes.c_int] * 3 + \
+                                   [ctypes.c_double, ctypes.c_double, ctypes.c_int, dp, dp, ctypes.POINTER(ctypes.c_long)]
+        L.orc_cfl_dt_full.restype = ctypes.c_double
+        L.orc_cfl_dt_full.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double] * 4 + [ctypes.c_int, dp, dp]
+        L.orc_divB_bc.restype = None
+        L.orc_divB_bc.argtypes = [ctypes.c_int] * 4 + [dp, dp, dp]
+        L.orc_prim_bc.restype = None
+        L.orc_prim_bc.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double, ctypes.c_int, dp, dp, dp]
         L.orc_cfl_dt.restype = ctypes.c_double
         L.orc_cfl_dt.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double] * 3 + [dp, dp]
         L.orc_divB.restype = None
@@ -111,18 +120,34 @@ def step_floor(U: np.ndarray, B: np.ndarray, dx: float, gamma: float, dt: float,
     return int(fb), int(nf.value)
 
 
-def cfl_dt(U, B, dx, gamma, cfl, pfloor=0.0) -> float:
+def step_bc(U: np.ndarray, B: np.ndarray, dx: float, gamma: float, dt: float,
+            integrator="vl", recon="plm", riemann="roe", bc=0, pfloor=0.0) -> int:
+    """step() with outflow (zero-gradient) boundaries along the axes of the
+    bit mask bc (bit d: axis d) and periodic ones elsewhere; VL only.
+    Returns the Roe->HLLE fallbacks."""
     nz, ny, nx = U.shape[1:]
-    if pfloor > 0.0:
-        return float(lib().orc_cfl_dt_floor(nx, ny, nz, dx, gamma, cfl, pfloor, _p(U), _p(B)))
+    assert U.shape == (5, nz, ny, nx) and B.shape == (3, nz, ny, nx)
+    nf = ctypes.c_long(0)
+    r = lib().orc_step_full(nx, ny, nz, dx, gamma, INTEGRATORS[integrator], RECONS[recon], SOLVERS[riemann],
+                            dt, pfloor, bc, _p(U), _p(B), ctypes.byref(nf))
+    if r < 0:
+        raise ValueError("outflow boundaries need the VL integrator")
+    return int(r)
+
+
+def cfl_dt(U, B, dx, gamma, cfl, pfloor=0.0, bc=0) -> float:
+    nz, ny, nx = U.shape[1:]
+    if pfloor > 0.0 or bc:
+        return float(lib().orc_cfl_dt_full(nx, ny, nz, dx, gamma, cfl, pfloor, bc, _p(U), _p(B)))
     return float(lib().orc_cfl_dt(nx, ny, nz, dx, gamma, cfl, _p(U), _p(B)))
 
 
-def divB(B) -> tuple[float, float]:
-    """(max_c |sum_d dB_d| (= |div B| dx), B_rms)."""
+def divB(B, bc=0) -> tuple[float, float]:
+    """(max_c |sum_d dB_d| (= |div B| dx), B_rms); along an outflow axis the
+    face beyond the last cell continues the last face."""
     nz, ny, nx = B.shape[1:]
     m = np.zeros(1); r = np.zeros(1)
-    lib().orc_divB(nx, ny, nz, _p(B), _p(m), _p(r))
+    lib().orc_divB_bc(nx, ny, nz, bc, _p(B), _p(m), _p(r))
     return float(m[0]), float(r[0])
 
 
@@ -133,10 +158,10 @@ def sums(U, B) -> np.ndarray:
     return out
 
 
-def prim(U, B, gamma) -> np.ndarray:
+def prim(U, B, gamma, bc=0) -> np.ndarray:
     nz, ny, nx = U.shape[1:]
     W = np.zeros((8, nz, ny, nx))
-    lib().orc_prim(nx, ny, nz, gamma, _p(U), _p(B), _p(W))
+    lib().orc_prim_bc(nx, ny, nz, gamma, bc, _p(U), _p(B), _p(W))
     return W
 
 
