@@ -164,6 +164,17 @@ mhd_status mhd_set_sweep_config(mhd_ctx* ctx, int tile_len, int blocks_per_sm);
 mhd_status mhd_get_sweep_config(mhd_ctx* ctx, int* tile_len, int* blocks_per_sm);
 mhd_status mhd_autotune(mhd_ctx* ctx, int reps, int* tile_len, int* blocks_per_sm, double* ms_best);
 
+/* Boundaries.  Every axis is periodic by default.  mhd_set_boundary makes
+ * the axes of the bits of outflow_mask (bit d: axis d) outflow boundaries
+ * (zero gradient): a cell, face or edge beyond the last one is the last one,
+ * and the flux through the outer face of the last cell is the Riemann flux
+ * between that cell and its copy; CT then keeps the divergence of every
+ * cell.  One-box VL contexts without a selector (else MHD_EUNSUPPORTED);
+ * outflow_mask in [0, 7] (else MHD_EINVAL).  mhd_helicity needs a periodic
+ * box. */
+mhd_status mhd_set_boundary(mhd_ctx* ctx, int outflow_mask);
+mhd_status mhd_get_boundary(mhd_ctx* ctx, int* outflow_mask);
+
 /* Pencil sweeps (VL integrator): on every axis d with bit d of pencil_mask
  * set, the predictor and corrector face sweeps keep the cells around each
  * face in registers (no shared memory): along y and z one thread walks a

@@ -40,7 +40,7 @@ static void release(mhd_ctx* c)
                     c->F1, c->F2, c->E, c->Bh[0], c->Bh[1], c->Bh[2], c->WM, c->WP, c->stage,
                     c->dt, c->dtc, c->smax, c->smax_part, c->bad, c->nfloor, c->part, c->diag, c->dbox, c->sel_feats,
                     c->sel_flags, c->sel_cnt, c->sel_list[0], c->sel_list[1], c->sel_list[2], c->sel_list[3],
-                    c->sel_list[4], c->sel_list[5], c->sel_list[6], c->sel_list[7]};
+                    c->sel_list[4], c->sel_list[5], c->sel_list[6], c->sel_list[7], c->fout};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (c->have_graph) cudaGraphExecDestroy(c->gexec);
@@ -451,6 +451,7 @@ extern "C" mhd_status mhd_energies(mhd_ctx* c, double jb_threshold, double* out)
 extern "C" mhd_status mhd_helicity(mhd_ctx* c, double* h)
 {
     if (!c || !h) return fail(c, MHD_EINVAL, "null pointer");
+    if (c->bc) return fail(c, MHD_EUNSUPPORTED, "mhd_helicity: the Coulomb gauge needs a periodic box");
     const size_t rsz = c->sch.precision == MHD_FP64 ? sizeof(double) : sizeof(float);
     const size_t f1_bytes = (size_t)21 * (size_t)c->B.N * rsz;
     const int nblk = (int)(c->B.nvblk * 10 < 1024 ? c->B.nvblk * 10 : 1024);   // c->part holds nvblk * 10
@@ -515,6 +516,29 @@ extern "C" mhd_status mhd_get_sweep_config(mhd_ctx* c, int* tile_len, int* block
     if (!c || !tile_len || !blocks_per_sm) return fail(c, MHD_EINVAL, "null pointer");
     *tile_len = c->B.tl;
     *blocks_per_sm = c->sweep_bps;
+    return MHD_OK;
+}
+
+extern "C" mhd_status mhd_set_boundary(mhd_ctx* c, int outflow_mask)
+{
+    if (!c) return MHD_EINVAL;
+    if (outflow_mask < 0 || outflow_mask > 7) return fail(c, MHD_EINVAL, "outflow_mask must be in [0, 7]");
+    if (outflow_mask && (c->sch.integrator != MHD_VL || c->nbox != 1 || c->sel))
+        return fail(c, MHD_EUNSUPPORTED, "outflow boundaries are built for one-box VL contexts without a selector");
+    if (outflow_mask && !c->fout) {
+        const BoxDev& b = c->hbox[0];
+        CK(dalloc(c, &c->fout, (size_t)3 * 7 * cross_size(b.nx, b.ny, b.nz) * c->szr));
+    }
+    c->bc = outflow_mask;
+    c->hbox[0].bc = outflow_mask;
+    CK(layout_tiles(c, c->B.tl));   // uploads the box table (and drops a captured step)
+    return MHD_OK;
+}
+
+extern "C" mhd_status mhd_get_boundary(mhd_ctx* c, int* outflow_mask)
+{
+    if (!c || !outflow_mask) return fail(c, MHD_EINVAL, "null pointer");
+    *outflow_mask = c->bc;
     return MHD_OK;
 }
 

@@ -21,6 +21,8 @@ struct mhd_ctx {
     mhd::Boxes B;                   // kernel view (points at dbox)
     int nsm;                        // SMs of the device
     int sweep_bps;                  // persistent sweep blocks per SM
+    int bc;                         // outflow axes (bit d), one-box VL contexts; 0 = periodic
+    void* fout;                     // [3][7][cross-section] outer-face fluxes of the outflow axes
     int pencil_mask;                // VL sweeps by pencils on the axes of these bits
     int pencil_len;                 // faces per pencil-segment thread
     size_t szu, sze, szr;          // element sizes: rho/M storage, e/B storage, arithmetic
@@ -167,7 +169,13 @@ void run_step(mhd_ctx* c, bool device_dt)
         }
         k_emf<R><<<emf_grid<R>(c), EMF_THREADS, emf_smem_bytes<R>(), st>>>(g, F1, W, E);
         prof_mark(c, 5);
-        k_half<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2], Wh, c->sch.pfloor);
+        const int cs = c->bc ? cross_size(c->hbox[0].nx, c->hbox[0].ny, c->hbox[0].nz) : 0;
+        for (int d = 0; d < 3; d++)
+            if (c->bc >> d & 1)
+                k_outer_flux<R, SOLVER, TE><<<(cs + 127) / 128, 128, 0, st>>>(c->hbox[0], d, W, s.b[d], gam, n,
+                                                                             (R*)c->fout, cs);
+        k_half<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2], Wh,
+                                                       c->sch.pfloor, (const R*)c->fout, cs);
         prof_mark(c, 6);
         // VL steps 4-7: reconstruct at the half step, Riemann, edge E, full update
         for (int d = 0; d < 3; d++) {
@@ -184,7 +192,11 @@ void run_step(mhd_ctx* c, bool device_dt)
         }
         k_emf<R><<<emf_grid<R>(c), EMF_THREADS, emf_smem_bytes<R>(), st>>>(g, F1, Wh, E);
         prof_mark(c, 10);
-        k_full<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc);
+        for (int d = 0; d < 3; d++)
+            if (c->bc >> d & 1)
+                k_outer_flux<R, SOLVER, TE><<<(cs + 127) / 128, 128, 0, st>>>(c->hbox[0], d, Wh, Bh[d], gam, n,
+                                                                             (R*)c->fout, cs);
+        k_full<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, (const R*)c->fout, cs);
         prof_mark(c, 11);
     } else {
         R* WM = (R*)c->WM;

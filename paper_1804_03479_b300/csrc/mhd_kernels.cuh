@@ -36,6 +36,7 @@ struct BoxDev {
     int tile0[3];       // first sweep tile of the box, per axis
     float inv_dx;       // 1/dx in single precision
     int etile0;         // first edge-field tile of the box
+    int bc;             // bit d set: outflow (zero-gradient) boundaries along axis d, else periodic
     long long pth0[3];  // first pencil-segment thread of the box, per axis
     long long xw0[3];   // first x-warp item of the box: predictor, PLM corrector, PPM corrector
     long long xr0;      // first grid row (j, k) of the box
@@ -110,6 +111,15 @@ __device__ __forceinline__ int wrapi(int i, int n)
     return i;
 }
 
+// index along an axis of n cells: periodic wrap, or for an outflow axis the
+// nearest cell (zero-gradient ghosts; a face or edge beyond the last one is
+// the last one)
+__device__ __forceinline__ int bidx(int i, int n, int outflow)
+{
+    if (outflow) return i < 0 ? 0 : (i >= n ? n - 1 : i);
+    return wrapi(i, n);
+}
+
 __device__ __forceinline__ long long cell_of(const BoxDev& g, int i, int j, int k)
 {
     return g.off + ((long long)k * g.ny + j) * g.nx + i;
@@ -118,9 +128,9 @@ __device__ __forceinline__ long long cell_of(const BoxDev& g, int i, int j, int 
 // neighbour of (i,j,k) shifted by s along axis d (periodic in the box)
 __device__ __forceinline__ long long nbr(const BoxDev& g, int i, int j, int k, int d, int s)
 {
-    if (d == 0) i = wrapi(i + s, g.nx);
-    else if (d == 1) j = wrapi(j + s, g.ny);
-    else k = wrapi(k + s, g.nz);
+    if (d == 0) i = bidx(i + s, g.nx, g.bc & 1);
+    else if (d == 1) j = bidx(j + s, g.ny, g.bc & 2);
+    else k = bidx(k + s, g.nz, g.bc & 4);
     return cell_of(g, i, j, k);
 }
 
@@ -387,7 +397,8 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(Boxes B, int d, const R
                 const int sx0 = ox - (d == 0), sy0 = oy - (d == 1), sz0 = oz - (d == 2);
                 for (int q = threadIdx.x; q < nsl; q += blockDim.x) {
                     int qx = q % t.sx, qy = (q / t.sx) % t.sy, qz = q / (t.sx * t.sy);
-                    int i = wrapi(sx0 + qx, g.nx), j = wrapi(sy0 + qy, g.ny), k = wrapi(sz0 + qz, g.nz);
+                    int i = bidx(sx0 + qx, g.nx, g.bc & 1), j = bidx(sy0 + qy, g.ny, g.bc & 2),
+                        k = bidx(sz0 + qz, g.nz, g.bc & 4);
                     R wm[7], w0[7], wp[7], bn, bdum;
                     load_rot(W, N, cell_of(g, i, j, k), d, w0, bn);
                     load_rot(W, N, nbr(g, i, j, k, d, -1), d, wm, bdum);
@@ -402,7 +413,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(Boxes B, int d, const R
             for (int q = threadIdx.x; q < nreg; q += blockDim.x) {
                 int qx = q % t.rx, qy = (q / t.rx) % t.ry, qz = q / (t.rx * t.ry);
                 int gi = ox + qx, gj = oy + qy, gk = oz + qz;
-                int i = wrapi(gi, g.nx), j = wrapi(gj, g.ny), k = wrapi(gk, g.nz);
+                int i = bidx(gi, g.nx, g.bc & 1), j = bidx(gj, g.ny, g.bc & 2), k = bidx(gk, g.nz, g.bc & 4);
                 long long c = cell_of(g, i, j, k);
                 R wm1[7], w0[7], wp1[7], bn, bdum;
                 load_rot(W, N, c, d, w0, bn);
@@ -490,8 +501,9 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(Boxes B, int d, const R
 // along the first transverse axis (x for d = 1, 2; y for d = 0).
 // ---------------------------------------------------------------------------
 struct Pencil {
-    long long base, stride;   // cell of line position i: base + wrap(i) * stride
+    long long base, stride;   // cell of line position i: base + bidx(i) * stride
     int n;                    // cells along the line
+    int out;                  // outflow ends (else periodic)
 };
 
 __host__ __device__ __forceinline__ void pencil_dims(int nx, int ny, int nz, int d, int pl, int& na, int& nb, int& ns)
@@ -520,7 +532,7 @@ __device__ __forceinline__ int box_of_pth(const Boxes& B, int d, long long t)
 
 __device__ __forceinline__ long long pcell(const Pencil& p, int i)
 {
-    return p.base + (long long)wrapi(i, p.n) * p.stride;
+    return p.base + (long long)bidx(i, p.n, p.out) * p.stride;
 }
 
 template <class R>
@@ -556,6 +568,7 @@ __global__ void __launch_bounds__(PENCIL_THREADS) k_pencil(Boxes B, int d, const
     if (d == 0) { p.base = g.off + ((long long)ib * g.ny + ia) * g.nx; p.stride = 1; p.n = g.nx; }
     else if (d == 1) { p.base = g.off + (long long)ib * g.ny * g.nx + ia; p.stride = g.nx; p.n = g.ny; }
     else { p.base = g.off + (long long)ib * g.nx + ia; p.stride = (long long)g.nx * g.ny; p.n = g.nz; }
+    p.out = g.bc >> d & 1;
     const int i0 = sg * B.pl;
     const int i1 = i0 + B.pl < p.n ? i0 + B.pl : p.n;
     const long long N = B.N;
@@ -721,18 +734,18 @@ __global__ void __launch_bounds__(PENCIL_THREADS) k_xwarp(Boxes B, const R* __re
         sg0 = 0;
         sg1 = (gb.nx + FW - 1) / FW;
     }
-    const int nx = B.b[bi].nx;
+    const int nx = B.b[bi].nx, xout = B.b[bi].bc & 1;
     const long long row = B.b[bi].off + ((long long)k * B.b[bi].ny + j) * nx;
     const long long N = B.N;
     const R gr = R(gam), gm1 = R(gam - 1.0);
     const bool face = lane >= LEAD && lane < LEAD + FW;
     R w[7], bn, f[7];
-    load_rot(W, N, row + wrapi(sg0 * FW - LEAD + lane, nx), 0, w, bn);
+    load_rot(W, N, row + bidx(sg0 * FW - LEAD + lane, nx, xout), 0, w, bn);
     for (int sg = sg0; sg < sg1; sg++) {
         const int xi = sg * FW - LEAD + lane;        // this lane's cell (and the face below it)
-        const long long ci = row + wrapi(xi, nx);
+        const long long ci = row + bidx(xi, nx, xout);
         R wn[7], bnn;
-        if (sg + 1 < sg1) load_rot(W, N, row + wrapi(xi + FW, nx), 0, wn, bnn);
+        if (sg + 1 < sg1) load_rot(W, N, row + bidx(xi + FW, nx, xout), 0, wn, bnn);
         R wl[7], wr[7];
         if (MODE == 0) {
             shfl7(wl, w, 1);
@@ -878,9 +891,9 @@ __global__ void __launch_bounds__(EMF_THREADS) k_emf(Boxes B, const R* __restric
         const int z0 = (bl / nty) * EZC;
         const int z1 = z0 + EZC < g.nz ? z0 + EZC : g.nz;
         const bool mine = tid < ETX * ETY && x0 + tx < g.nx && y0 + ty < g.ny;
-        const int si = wrapi(x0 - 1 + hx, g.nx), sj = wrapi(y0 - 1 + hy, g.ny);
+        const int si = bidx(x0 - 1 + hx, g.nx, g.bc & 1), sj = bidx(y0 - 1 + hy, g.ny, g.bc & 2);
         EmfStage<R> st;
-        if (stager) emf_load(F, W, N, cell_of(g, si, sj, wrapi(z0 - 1, g.nz)), st);
+        if (stager) emf_load(F, W, N, cell_of(g, si, sj, bidx(z0 - 1, g.nz, g.bc & 4)), st);
         for (int k = z0 - 1; k < z1; k++) {
             R* P = sm + ((k + 3) % 3) * ENV * EPL;
             if (stager) {
@@ -939,6 +952,66 @@ __device__ __forceinline__ TE curl_face(const BoxDev& g, long long N, const R* _
            (TE(E[t1 * N + nbr(g, i, j, k, t2, 1)]) - TE(E[t1 * N + c]));
 }
 
+// Flux through the outer face of the last cell along an outflow axis d: the
+// Riemann flux between the cell and its zero-gradient copy (the limited slope
+// against the copy is zero, so both face states are the cell's stage state
+// Wst), with the normal field of the last face.  One thread per cell of the
+// last layer of a one-box context; Fout[d][7][cs], cs = the largest
+// cross-section, the layer's cell (a, b) at a + b * n_a (a, b the two other
+// axes in increasing order).
+__host__ __device__ __forceinline__ int cross_size(int nx, int ny, int nz)
+{
+    int a = ny * nz, b = nx * nz, c = nx * ny;
+    return a > b ? (a > c ? a : c) : (b > c ? b : c);
+}
+
+template <class R, int SOLVER, class TE>
+__global__ void k_outer_flux(BoxDev g, int d, const R* __restrict__ Wst, const TE* __restrict__ bface, double gam,
+                             long long N, R* __restrict__ Fout, int cs)
+{
+    const int na = d == 0 ? g.ny : g.nx, nb = d == 2 ? g.ny : g.nz;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= na * nb) return;
+    const int a = q % na, b = q / na;
+    int i, j, k;
+    if (d == 0) { i = g.nx - 1; j = a; k = b; }
+    else if (d == 1) { i = a; j = g.ny - 1; k = b; }
+    else { i = a; j = b; k = g.nz - 1; }
+    const long long c = cell_of(g, i, j, k);
+    R w[7], bdum, f[7];
+    load_rot(Wst, N, c, d, w, bdum);
+    riemann<SOLVER>(w, w, R(bface[c]), R(gam - 1.0), R(gam), f);
+    R* Fd = Fout + (long long)d * 7 * cs;
+#pragma unroll
+    for (int m = 0; m < 7; m++) Fd[(long long)m * cs + q] = f[m];
+}
+
+// outflow: for each outflow axis along which (i, j, k) is the last cell, add
+// the outer-face flux minus the cell's own lower-face flux to the divergence
+// (the stencil saw the cell as its own upper neighbour)
+template <class R, class TU, class TE>
+__device__ __forceinline__ void outer_divergence(const BoxDev& g, int i, int j, int k, long long c, long long N,
+                                                 const R* __restrict__ F, const R* __restrict__ Fout, int cs,
+                                                 TU du[4], TE& due)
+{
+#pragma unroll 1
+    for (int d = 0; d < 3; d++) {
+        if (!(g.bc >> d & 1) || (d == 0 ? i : (d == 1 ? j : k)) != (d == 0 ? g.nx : (d == 1 ? g.ny : g.nz)) - 1)
+            continue;
+        const int t1 = d == 2 ? 0 : d + 1, t2 = d == 0 ? 2 : d - 1;
+        const int na = d == 0 ? g.ny : g.nx;
+        const int q = d == 0 ? j + k * na : (d == 1 ? i + k * na : i + j * na);
+        const R* Fo = Fout + (long long)d * 7 * cs;
+        const R* Fd = F + (long long)d * 7 * N;
+        const R f0 = Fo[q], f1 = Fo[cs + q], f2 = Fo[2 * cs + q], f3 = Fo[3 * cs + q], f4 = Fo[4 * cs + q];
+        du[0] += TU(f0 - Fd[c]);
+        du[1 + d] += TU(f1 - Fd[N + c]);
+        du[1 + t1] += TU(f2 - Fd[2 * N + c]);
+        du[1 + t2] += TU(f3 - Fd[3 * N + c]);
+        due += TE(f4 - Fd[4 * N + c]);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // a8 + a1: half-step face field B^{n+1/2} = B^n - (dt/2) curl E (Eq. 13) and
 // the half-step cell primitives from U^{n+1/2} = U^n - (dt/2) div F (Eq. 10)
@@ -948,7 +1021,8 @@ template <class R, class TU, class TE>
 __global__ void __launch_bounds__(CELL_THREADS) k_half(Boxes B, StateP<TU, TE> s, const R* __restrict__ F,
                                                        const R* __restrict__ E, const DtBox* __restrict__ dtb,
                                                        double gam, TE* __restrict__ Bh0, TE* __restrict__ Bh1,
-                                                       TE* __restrict__ Bh2, R* __restrict__ Wh, double pfloor = 0.0)
+                                                       TE* __restrict__ Bh2, R* __restrict__ Wh, double pfloor = 0.0,
+                                                       const R* __restrict__ Fout = nullptr, int cs = 0)
 {
     const long long N = B.N;
     for (long long v = blockIdx.x; v < B.nvblk; v += gridDim.x) {
@@ -966,7 +1040,8 @@ __global__ void __launch_bounds__(CELL_THREADS) k_half(Boxes B, StateP<TU, TE> s
     for (int d = 0; d < 3; d++) {
         TE lo = s.b[d][c] - r * curl_face<TE>(g, N, E, i, j, k, d);
         int i2 = i, j2 = j, k2 = k;
-        if (d == 0) i2 = wrapi(i + 1, g.nx); else if (d == 1) j2 = wrapi(j + 1, g.ny); else k2 = wrapi(k + 1, g.nz);
+        if (d == 0) i2 = bidx(i + 1, g.nx, g.bc & 1); else if (d == 1) j2 = bidx(j + 1, g.ny, g.bc & 2);
+        else k2 = bidx(k + 1, g.nz, g.bc & 4);
         TE hi = s.b[d][cell_of(g, i2, j2, k2)] - r * curl_face<TE>(g, N, E, i2, j2, k2, d);
         Bh[d][c] = lo;
         bc[d] = TE(0.5) * (lo + hi);
@@ -986,6 +1061,9 @@ __global__ void __launch_bounds__(CELL_THREADS) k_half(Boxes B, StateP<TU, TE> s
         du[1 + t2] += TU(Fd[3 * N + cp] - Fd[3 * N + c]);
         due += TE(Fd[4 * N + cp] - Fd[4 * N + c]);
     }
+    // outflow: the last cell's upper neighbour is the cell itself (a zero
+    // difference above); add its outer-face flux instead
+    if (g.bc) outer_divergence(g, i, j, k, c, N, F, Fout, cs, du, due);
     const TU ru = DtOf<TU>::hdtdx(dtb[bi]);
     TU rho = s.rho[c] - ru * du[0];
     TU mx = s.m[0][c] - ru * du[1], my = s.m[1][c] - ru * du[2], mz = s.m[2][c] - ru * du[3];
@@ -1006,7 +1084,8 @@ __global__ void __launch_bounds__(CELL_THREADS) k_half(Boxes B, StateP<TU, TE> s
 // ---------------------------------------------------------------------------
 template <class R, class TU, class TE>
 __global__ void __launch_bounds__(CELL_THREADS) k_full(Boxes B, StateP<TU, TE> s, const R* __restrict__ F,
-                                                       const R* __restrict__ E, const DtBox* __restrict__ dtb)
+                                                       const R* __restrict__ E, const DtBox* __restrict__ dtb,
+                                                       const R* __restrict__ Fout = nullptr, int cs = 0)
 {
     const long long N = B.N;
     for (long long v = blockIdx.x; v < B.nvblk; v += gridDim.x) {
@@ -1031,6 +1110,9 @@ __global__ void __launch_bounds__(CELL_THREADS) k_full(Boxes B, StateP<TU, TE> s
         du[1 + t2] += TU(Fd[3 * N + cp] - Fd[3 * N + c]);
         due += TE(Fd[4 * N + cp] - Fd[4 * N + c]);
     }
+    // outflow: the last cell's upper neighbour is the cell itself (a zero
+    // difference above); add its outer-face flux instead
+    if (g.bc) outer_divergence(g, i, j, k, c, N, F, Fout, cs, du, due);
     // rho and M in their storage type, the energy in TE (Eq. 10)
     const TU ru = DtOf<TU>::dtdx(dtb[bi]);
     s.rho[c] = s.rho[c] - ru * du[0];
@@ -1071,7 +1153,8 @@ __global__ void __launch_bounds__(CELL_THREADS) k_ctu_correct(Boxes B, int d, co
     for (int side = 0; side < 2; side++) {
         int si = i, sj = j, sk = k;
         if (side == 0) {
-            if (d == 0) si = wrapi(i - 1, g.nx); else if (d == 1) sj = wrapi(j - 1, g.ny); else sk = wrapi(k - 1, g.nz);
+            if (d == 0) si = bidx(i - 1, g.nx, g.bc & 1); else if (d == 1) sj = bidx(j - 1, g.ny, g.bc & 2);
+            else sk = bidx(k - 1, g.nz, g.bc & 4);
         }
         long long sc = cell_of(g, si, sj, sk);
         const R* src = side == 0 ? WP : WM;
@@ -1235,10 +1318,13 @@ __global__ void __launch_bounds__(CELL_THREADS) k_energies(Boxes B, StateP<TU, T
                 const double bf = (double)s.b[a][c];
                 ub += 0.5 * bf * bf;
                 int ib = i, jb = j, kb = k, ic = i, jc = j, kc = k;
-                if (bb == 0) ib = wrapi(i + 1, g.nx); else if (bb == 1) jb = wrapi(j + 1, g.ny); else kb = wrapi(k + 1, g.nz);
-                if (cc == 0) ic = wrapi(i + 1, g.nx); else if (cc == 1) jc = wrapi(j + 1, g.ny); else kc = wrapi(k + 1, g.nz);
+                if (bb == 0) ib = bidx(i + 1, g.nx, g.bc & 1); else if (bb == 1) jb = bidx(j + 1, g.ny, g.bc & 2);
+                else kb = bidx(k + 1, g.nz, g.bc & 4);
+                if (cc == 0) ic = bidx(i + 1, g.nx, g.bc & 1); else if (cc == 1) jc = bidx(j + 1, g.ny, g.bc & 2);
+                else kc = bidx(k + 1, g.nz, g.bc & 4);
                 int ibc = ib, jbc = jb, kbc = kb;
-                if (cc == 0) ibc = wrapi(ib + 1, g.nx); else if (cc == 1) jbc = wrapi(jb + 1, g.ny); else kbc = wrapi(kb + 1, g.nz);
+                if (cc == 0) ibc = bidx(ib + 1, g.nx, g.bc & 1); else if (cc == 1) jbc = bidx(jb + 1, g.ny, g.bc & 2);
+                else kbc = bidx(kb + 1, g.nz, g.bc & 4);
                 const double ja = 0.25 * (edge_j(g, s.b, i, j, k, a) + edge_j(g, s.b, ib, jb, kb, a) +
                                           edge_j(g, s.b, ic, jc, kc, a) + edge_j(g, s.b, ibc, jbc, kbc, a));
                 const double bcen = 0.5 * (bf + (double)s.b[a][nbr(g, i, j, k, a, 1)]);

@@ -428,8 +428,8 @@ extern "C" mhd_status mhd_set_selector(mhd_ctx* c, mhd_mlp* m)
         if (c->have_graph) { cudaGraphExecDestroy(c->gexec); c->have_graph = false; }
         return MHD_OK;
     }
-    if (!blockable(c) || c->sch.precision != MHD_FP32 || c->sch.integrator != MHD_VL) {
-        snprintf(c->err, sizeof(c->err), "the selector needs one FP32 VL box with sides divisible by 4");
+    if (!blockable(c) || c->sch.precision != MHD_FP32 || c->sch.integrator != MHD_VL || c->bc) {
+        snprintf(c->err, sizeof(c->err), "the selector needs one periodic FP32 VL box with sides divisible by 4");
         return MHD_EUNSUPPORTED;
     }
     if (!c->sel_feats) {

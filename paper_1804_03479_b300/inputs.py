@@ -427,6 +427,30 @@ def uniform(n, rho=1.0, v=(0.3, -0.2, 0.1), P=0.7, Bv=(0.4, -0.5, 0.6), gamma=5.
     return State(U, np.ascontiguousarray(B), 1.0 / nx, gamma, dict(kind="uniform"))
 
 
+def open_box(shape, seed=0, gamma=5.0 / 3.0):
+    """Smooth state for boxes with outflow (zero-gradient) sides: each field
+    component depends only on the two other coordinates (B_x(y, z), B_y(z, x),
+    B_z(x, y)), so the face fields are divergence-free under any mix of
+    periodic and outflow sides, whatever the box lengths; density, velocity
+    and pressure carry a smooth part plus 5 % (pressure 10 %) uniform noise,
+    with pressure near 0.5 (beta of order one)."""
+    nx, ny, nz = shape
+    dx = 1.0 / max(shape)
+    rng = np.random.default_rng(seed)
+    xc, yc, zc, _, _, _ = _coords(nx, ny, nz, dx)
+    Z, Y, X = np.meshgrid(zc, yc, xc, indexing="ij")
+    ph = rng.uniform(0.0, 2.0 * np.pi, 10)
+    tp = 2.0 * np.pi
+    B = np.stack([0.5 + 0.2 * np.sin(tp * Y + ph[0]) * np.cos(tp * Z + ph[1]),
+                  0.3 + 0.2 * np.sin(tp * Z + ph[2]) * np.cos(tp * X + ph[3]),
+                  -0.2 + 0.2 * np.sin(tp * X + ph[4]) * np.cos(tp * Y + ph[5])])
+    rho = 1.0 + 0.2 * np.sin(tp * (X + Y) + ph[6]) + 0.05 * rng.uniform(-1.0, 1.0, X.shape)
+    v = [0.3 * np.sin(tp * (Y + Z) + ph[7 + m]) + 0.05 * rng.uniform(-1.0, 1.0, X.shape) for m in range(3)]
+    P = 0.5 + 0.05 * rng.uniform(-1.0, 1.0, X.shape)
+    U = conserved(rho, v[0], v[1], v[2], P, B, gamma)
+    return State(U, np.ascontiguousarray(B), dx, gamma, dict(kind="open_box"))
+
+
 def shock_tube(wl, wr, bn, n, axis=0, m=2, L=2.0, gamma=5.0 / 3.0):
     """1-D Riemann problem (Sec. 5.1 (ii), Table 1 states) on a periodic line
     of length L along `axis`, with m cells across: the left state fills

@@ -33,7 +33,7 @@ EXPORTS = ["mhd_init", "mhd_set_state", "mhd_get_state", "mhd_cfl_dt", "mhd_step
            "mhd_mlp_set_weights", "mhd_mlp_get_weights", "mhd_mlp_grad", "mhd_mlp_train_step",
            "mhd_mlp_predict", "mhd_nblocks", "mhd_block_features", "mhd_block_error", "mhd_set_selector",
            "mhd_selector_stats", "mhd_floor_count", "mhd_energies", "mhd_helicity",
-           "mhd_set_sweep_pencils", "mhd_get_sweep_pencils"]
+           "mhd_set_sweep_pencils", "mhd_get_sweep_pencils", "mhd_set_boundary", "mhd_get_boundary"]
 GROUPS = ["prim_cfl", "predictor_x", "predictor_y", "predictor_z", "emf1", "half_update", "corrector_x",
           "corrector_y", "corrector_z", "emf2", "full_update"]
 
@@ -131,6 +131,8 @@ def lib():
     L.mhd_energies.argtypes = [vp, ctypes.c_double, dp]
     L.mhd_helicity.argtypes = [vp, dp]
     L.mhd_set_sweep_pencils.argtypes = [vp, ip, ip]
+    L.mhd_set_boundary.argtypes = [vp, ip]
+    L.mhd_get_boundary.argtypes = [vp, ctypes.POINTER(ip)]
     L.mhd_get_sweep_pencils.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip)]
     # every entry point that returns an mhd_status; the others got their
     # restype above (long long, int, void, const char*)
@@ -285,6 +287,15 @@ class Solver:
 
     def set_sweep_config(self, tile_len, blocks_per_sm):
         self._check(lib().mhd_set_sweep_config(self.h, tile_len, blocks_per_sm))
+
+    def set_boundary(self, outflow_mask):
+        """outflow (zero-gradient) boundaries on the axes of outflow_mask (bit d: axis d)"""
+        self._check(lib().mhd_set_boundary(self.h, outflow_mask))
+
+    def boundary(self):
+        a = ctypes.c_int()
+        self._check(lib().mhd_get_boundary(self.h, ctypes.byref(a)))
+        return a.value
 
     def set_sweep_pencils(self, pencil_mask, pencil_len=16):
         """VL face sweeps by pencils on the axes of pencil_mask (bit d: axis d)"""

@@ -146,3 +146,16 @@ def test_mhd_blast(theta0):
     assert np.all(rho[r >= 0.15] == 1.0)
     assert np.abs(rho - 1.0).max() <= 0.12 + 1e-12
     assert np.abs(rho[r < 0.15] - 1.0).max() > 1e-3
+
+
+def test_open_box_divergence_free_under_any_boundary_mix():
+    """each component is independent of its own coordinate, so the face
+    differences along its axis vanish whether that side wraps or not"""
+    st = I.open_box((24, 20, 18), seed=3)
+    B = st.B
+    assert np.abs(np.diff(B[0], axis=2)).max() < 1e-15
+    assert np.abs(np.diff(B[1], axis=1)).max() < 1e-15
+    assert np.abs(np.diff(B[2], axis=0)).max() < 1e-15
+    assert np.abs(divergence(B)).max() < 1e-15
+    assert np.all(st.U[0] > 0.7)
+    assert st.U.shape == (5, 18, 20, 24) and abs(st.dx - 1.0 / 24) < 1e-16
