@@ -304,14 +304,27 @@ extern "C" mhd_status mhd_get_state(mhd_ctx* c, void* U, void* B, int on_device)
     return mhd_get_state_box(c, 0, U, B, on_device);
 }
 
+// primitives and per-box signal-speed maxima of the current state (no floor
+// raise of e), with the boundary handling the context was set to
+template <class R, class TU, class TE>
+static void prim_pass(mhd_ctx* c)
+{
+    const int nb = c->cell_grid;
+    if (c->bc)
+        k_prim<R, TU, TE, true><<<nb, CELL_THREADS, 0, c->stream>>>(c->B, state_of<TU, TE>(c), (R*)c->W, c->gamma,
+                                                                    c->smax_part, c->bad, c->sch.pfloor);
+    else
+        k_prim<R, TU, TE><<<nb, CELL_THREADS, 0, c->stream>>>(c->B, state_of<TU, TE>(c), (R*)c->W, c->gamma,
+                                                              c->smax_part, c->bad, c->sch.pfloor);
+}
+
 extern "C" mhd_status mhd_cfl_dt(mhd_ctx* c, double* dt)
 {
     if (!c || !dt) return fail(c, MHD_EINVAL, "null pointer");
-    const int nb = c->cell_grid;
     switch (c->sch.precision) {
-        case MHD_FP64: k_prim<double, double, double><<<nb, CELL_THREADS, 0, c->stream>>>(c->B, state_of<double, double>(c), (double*)c->W, c->gamma, c->smax_part, c->bad, c->sch.pfloor); break;
-        case MHD_FP32: k_prim<float, float, float><<<nb, CELL_THREADS, 0, c->stream>>>(c->B, state_of<float, float>(c), (float*)c->W, c->gamma, c->smax_part, c->bad, c->sch.pfloor); break;
-        default:       k_prim<float, float, double><<<nb, CELL_THREADS, 0, c->stream>>>(c->B, state_of<float, double>(c), (float*)c->W, c->gamma, c->smax_part, c->bad, c->sch.pfloor); break;
+        case MHD_FP64: prim_pass<double, double, double>(c); break;
+        case MHD_FP32: prim_pass<float, float, float>(c); break;
+        default:       prim_pass<float, float, double>(c); break;
     }
     k_finalize_dt<<<c->nbox, 256, 0, c->stream>>>(c->B, c->smax_part, c->sch.cfl, nullptr, c->smax, nullptr);
     CK(cudaGetLastError());

@@ -148,8 +148,12 @@ void run_step(mhd_ctx* c, bool device_dt)
     const size_t smem = sweep_smem_bytes<R>(RECON, g.tl);
 
     prof_mark(c, 0);
-    k_prim<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, W, gam, device_dt ? c->smax_part : nullptr, c->bad,
-                                                   c->sch.pfloor, c->nfloor);
+    if (c->bc)
+        k_prim<R, TU, TE, true><<<nb, CELL_THREADS, 0, st>>>(g, s, W, gam, device_dt ? c->smax_part : nullptr,
+                                                             c->bad, c->sch.pfloor, c->nfloor);
+    else
+        k_prim<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, W, gam, device_dt ? c->smax_part : nullptr, c->bad,
+                                                       c->sch.pfloor, c->nfloor);
     if (device_dt) k_finalize_dt<<<c->nbox, 256, 0, st>>>(g, c->smax_part, c->sch.cfl, c->dt, c->smax, c->dtc);
     prof_mark(c, 1);
 
@@ -174,8 +178,12 @@ void run_step(mhd_ctx* c, bool device_dt)
             if (c->bc >> d & 1)
                 k_outer_flux<R, SOLVER, TE><<<(cs + 127) / 128, 128, 0, st>>>(c->hbox[0], d, W, s.b[d], gam, n,
                                                                              (R*)c->fout, cs);
-        k_half<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2], Wh,
-                                                       c->sch.pfloor, (const R*)c->fout, cs);
+        if (c->bc)
+            k_half<R, TU, TE, true><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2], Wh,
+                                                                 c->sch.pfloor, (const R*)c->fout, cs);
+        else
+            k_half<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2], Wh,
+                                                           c->sch.pfloor);
         prof_mark(c, 6);
         // VL steps 4-7: reconstruct at the half step, Riemann, edge E, full update
         for (int d = 0; d < 3; d++) {
@@ -196,7 +204,10 @@ void run_step(mhd_ctx* c, bool device_dt)
             if (c->bc >> d & 1)
                 k_outer_flux<R, SOLVER, TE><<<(cs + 127) / 128, 128, 0, st>>>(c->hbox[0], d, Wh, Bh[d], gam, n,
                                                                              (R*)c->fout, cs);
-        k_full<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, (const R*)c->fout, cs);
+        if (c->bc)
+            k_full<R, TU, TE, true><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, (const R*)c->fout, cs);
+        else
+            k_full<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc);
         prof_mark(c, 11);
     } else {
         R* WM = (R*)c->WM;

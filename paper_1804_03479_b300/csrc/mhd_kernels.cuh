@@ -202,7 +202,7 @@ __device__ __forceinline__ void atomic_max_pos(unsigned long long* p, double v)
 // a1 + a2: primitives of every cell, the per-box CFL signal-speed maximum and
 // a record of the first cell with rho <= 0 or P <= 0 (or not finite).
 // ---------------------------------------------------------------------------
-template <class R, class TU, class TE>
+template <class R, class TU, class TE, bool OUT = false>
 __global__ void __launch_bounds__(CELL_THREADS) k_prim(Boxes B, StateP<TU, TE> s, R* __restrict__ W, double gam,
                                                        double* smax_part, unsigned long long* bad_cell,
                                                        double pfloor = 0.0, unsigned long long* nfloor = nullptr)
@@ -211,7 +211,8 @@ __global__ void __launch_bounds__(CELL_THREADS) k_prim(Boxes B, StateP<TU, TE> s
     __shared__ double red[CELL_THREADS];
     for (long long v = blockIdx.x; v < B.nvblk; v += gridDim.x) {
         const int bi = box_of_vblk(B, v);
-        const BoxDev g = B.b[bi];
+        BoxDev g = B.b[bi];
+        if (!OUT) g.bc = 0;     // periodic instantiation: the wrap is compiled in
         const long long lc = (v - g.vblk0) * CELL_THREADS + threadIdx.x;
         double local = 0.0;
         if (lc < g.n) {
@@ -1017,7 +1018,7 @@ __device__ __forceinline__ void outer_divergence(const BoxDev& g, int i, int j, 
 // the half-step cell primitives from U^{n+1/2} = U^n - (dt/2) div F (Eq. 10)
 // with the cell-centre B of the updated faces.  Only Bh and Wh are stored.
 // ---------------------------------------------------------------------------
-template <class R, class TU, class TE>
+template <class R, class TU, class TE, bool OUT = false>
 __global__ void __launch_bounds__(CELL_THREADS) k_half(Boxes B, StateP<TU, TE> s, const R* __restrict__ F,
                                                        const R* __restrict__ E, const DtBox* __restrict__ dtb,
                                                        double gam, TE* __restrict__ Bh0, TE* __restrict__ Bh1,
@@ -1027,7 +1028,8 @@ __global__ void __launch_bounds__(CELL_THREADS) k_half(Boxes B, StateP<TU, TE> s
     const long long N = B.N;
     for (long long v = blockIdx.x; v < B.nvblk; v += gridDim.x) {
     const int bi = box_of_vblk(B, v);
-    const BoxDev g = B.b[bi];
+    BoxDev g = B.b[bi];
+    if (!OUT) g.bc = 0;     // periodic instantiation: the wrap is compiled in
     const long long lc = (v - g.vblk0) * CELL_THREADS + threadIdx.x;
     if (lc >= g.n) continue;
     const TE r = DtOf<TE>::hdtdx(dtb[bi]);
@@ -1082,7 +1084,7 @@ __global__ void __launch_bounds__(CELL_THREADS) k_half(Boxes B, StateP<TU, TE> s
 // a10: full update U^{n+1} = U^n - dt div F (Eq. 10), B^{n+1} = B^n - dt curl E
 // (Eq. 13), in place.
 // ---------------------------------------------------------------------------
-template <class R, class TU, class TE>
+template <class R, class TU, class TE, bool OUT = false>
 __global__ void __launch_bounds__(CELL_THREADS) k_full(Boxes B, StateP<TU, TE> s, const R* __restrict__ F,
                                                        const R* __restrict__ E, const DtBox* __restrict__ dtb,
                                                        const R* __restrict__ Fout = nullptr, int cs = 0)
@@ -1090,7 +1092,8 @@ __global__ void __launch_bounds__(CELL_THREADS) k_full(Boxes B, StateP<TU, TE> s
     const long long N = B.N;
     for (long long v = blockIdx.x; v < B.nvblk; v += gridDim.x) {
     const int bi = box_of_vblk(B, v);
-    const BoxDev g = B.b[bi];
+    BoxDev g = B.b[bi];
+    if (!OUT) g.bc = 0;     // periodic instantiation: the wrap is compiled in
     const long long lc = (v - g.vblk0) * CELL_THREADS + threadIdx.x;
     if (lc >= g.n) continue;
     const TE r = DtOf<TE>::dtdx(dtb[bi]);
