@@ -213,6 +213,30 @@ def energies(U, B, dx, thr) -> dict:
     return dict(E_T=out[0], U_B=out[1], U_V=out[2], jb_max=out[3], n_above=int(out[4]), j_max=out[5])
 
 
+def pressure_gradient(U, B, dx, gamma, scale, thr, nlev=3, bc=0) -> dict:
+    """Refinement indicator of the magnetised blast run (Sec. 5.1): per cell
+    the normalised pressure gradient scale * |grad P| / P (scale = 100 r0 in
+    that run), grad P by centred differences of the cell pressure of prim()
+    over 2 dx, a neighbour beyond an outflow side being the cell itself.
+    Returns its maximum and, for l < nlev, the number of cells above
+    thr * 2^l (the run refines to level n above 1.25 * 2^(n-1))."""
+    P = prim(U, B, gamma, bc=bc)[4]
+    g2 = np.zeros_like(P)
+    for d in range(3):
+        ax = 2 - d                                   # array order (z, y, x)
+        n = P.shape[ax]
+        if bc >> d & 1:
+            up = np.take(P, np.minimum(np.arange(n) + 1, n - 1), axis=ax)
+            dn = np.take(P, np.maximum(np.arange(n) - 1, 0), axis=ax)
+        else:
+            up = np.roll(P, -1, axis=ax)
+            dn = np.roll(P, 1, axis=ax)
+        g2 += (up - dn) ** 2
+    score = scale * (np.sqrt(g2) * (0.5 / dx)) / P
+    return dict(max=float(score.max()), counts=[int(np.count_nonzero(score > thr * 2.0 ** l)) for l in range(nlev)],
+                score=score)
+
+
 def helicity(B, dx) -> float:
     """Magnetic helicity H = sum A.B dx^3 (Sec. 4.5) of the cell-centre field
     (mean of the two faces per axis) on the periodic box: A in the Coulomb

@@ -104,3 +104,80 @@ def test_helicity_of_plane_polarised_and_mean_fields_is_zero():
     # faces hold the same values (By, Bz do not vary along y, z)
     h = orc.helicity(Bc, dx)
     assert abs(abs(h) - 1.0 / k) <= 1e-12
+
+
+def _static_state(P, shape, dx, gam=5.0 / 3.0, Bv=(0.3, -0.2, 0.5), rho=1.0):
+    nx, ny, nz = shape
+    shp = (nz, ny, nx)
+    Bf = np.stack([np.full(shp, b) for b in Bv])
+    z = np.zeros(shp)
+    U = I.conserved(np.full(shp, rho), z, z, z, P, Bf, gam)
+    return U, np.ascontiguousarray(Bf), gam
+
+
+def test_pressure_gradient_of_sines_closed_form():
+    """P = P0 + sum_d a_d sin(k_d x_d + phi_d): the centred difference over
+    2 dx is a_d cos(k_d x_d + phi_d) sin(k_d dx) / dx exactly"""
+    shape = (24, 20, 16)
+    dx = 1.0 / 24
+    x = (np.arange(24) + 0.5) * dx
+    y = (np.arange(20) + 0.5) * dx
+    z = (np.arange(16) + 0.5) * dx
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    k = [2 * np.pi, 2 * np.pi * 24 / 20 * 2, 2 * np.pi * 24 / 16]   # whole periods on each side
+    a = [0.2, 0.07, 0.11]
+    ph = [0.3, 1.1, -0.4]
+    P0 = 1.0
+    P = P0 + a[0] * np.sin(k[0] * X + ph[0]) + a[1] * np.sin(k[1] * Y + ph[1]) + a[2] * np.sin(k[2] * Z + ph[2])
+    U, Bf, gam = _static_state(P, shape, dx)
+    gx = a[0] * np.cos(k[0] * X + ph[0]) * np.sin(k[0] * dx) / dx
+    gy = a[1] * np.cos(k[1] * Y + ph[1]) * np.sin(k[1] * dx) / dx
+    gz = a[2] * np.cos(k[2] * Z + ph[2]) * np.sin(k[2] * dx) / dx
+    scale = 0.05
+    want = scale * np.sqrt(gx ** 2 + gy ** 2 + gz ** 2) / P
+    thr = 0.04
+    r = orc.pressure_gradient(U, Bf, dx, gam, scale, thr, nlev=3)
+    assert np.max(np.abs(r["score"] - want)) <= 1e-12 * want.max()
+    assert abs(r["max"] - want.max()) <= 1e-12 * want.max()
+    for l in range(3):
+        t = thr * 2.0 ** l
+        assert np.min(np.abs(want - t)) > 1e-9          # no cell sits on a threshold
+        assert r["counts"][l] == int(np.count_nonzero(want > t))
+    assert r["counts"][0] > r["counts"][1] > 0
+
+
+def test_pressure_gradient_outflow_ramp():
+    """P linear in x with outflow along x: the interior centred difference is
+    the slope, the two end cells see half of it (their outer neighbour is
+    the cell itself); y and z periodic and uniform contribute nothing"""
+    shape = (12, 4, 4)
+    dx = 1.0 / 12
+    x = (np.arange(12) + 0.5) * dx
+    P = np.broadcast_to(0.5 + 2.0 * x, (4, 4, 12)).copy()
+    U, Bf, gam = _static_state(P, shape, dx)
+    r = orc.pressure_gradient(U, Bf, dx, gam, 1.0, 1.0, nlev=2, bc=1)
+    want = 2.0 / P
+    want[:, :, 0] *= 0.5
+    want[:, :, -1] *= 0.5
+    assert np.max(np.abs(r["score"] - want)) <= 1e-12
+    # periodic along x: the wrap turns the ends into a jump of -2 over 2 dx
+    rp = orc.pressure_gradient(U, Bf, dx, gam, 1.0, 1.0, nlev=2, bc=0)
+    jump = (P[:, :, 0] - P[:, :, -2]) * (0.5 / dx) / P[:, :, -1]
+    assert np.max(np.abs(rp["score"][:, :, -1] - np.abs(jump))) <= 1e-12
+
+
+def test_pressure_gradient_uniform_and_scale_free():
+    shape = (8, 8, 8)
+    dx = 1.0 / 8
+    U, Bf, gam = _static_state(np.full((8, 8, 8), 0.7), shape, dx)
+    r = orc.pressure_gradient(U, Bf, dx, gam, 100.0 * 0.05, 1.25, nlev=3)
+    assert r["max"] < 1e-12 and r["counts"] == [0, 0, 0]
+    # blast state: the score does not depend on the unit of pressure
+    st = I.mhd_blast(24, r0=0.1)
+    a = orc.pressure_gradient(st.U, st.B, st.dx, st.gamma, 10.0, 1.25)
+    U2 = st.U.copy()
+    U2[1:4] *= np.sqrt(3.0)         # M scales with v ~ sqrt(P / rho) at fixed rho
+    U2[4] *= 3.0
+    b = orc.pressure_gradient(U2, st.B * np.sqrt(3.0), st.dx, st.gamma, 10.0, 1.25)
+    assert np.max(np.abs(a["score"] - b["score"])) <= 1e-12 * a["max"]
+    assert a["counts"] == b["counts"] and a["counts"][0] > 0
