@@ -143,6 +143,18 @@ mhd_status mhd_sums(mhd_ctx* ctx, double* sums8);
  * jb_threshold >= 0, else MHD_EINVAL.  Synchronises. */
 mhd_status mhd_energies(mhd_ctx* ctx, double jb_threshold, double* out);
 
+/* Pressure-gradient refinement indicator of the magnetised blast run
+ * (Sec. 5.1) per box, in FP64 from the stored state: per cell
+ * scale * |grad P| / P (scale = 100 r0 there), grad P by centred
+ * differences of the cell pressure over 2 dx (cell-centre B the mean of the
+ * two faces; a neighbour beyond an outflow side is the cell itself).  out
+ * has (1 + nlev) * nbox entries: per box the maximum, then for l < nlev the
+ * number of cells above thr * 2^l (the run refines to level n above
+ * 1.25 * 2^(n-1)).  scale > 0, thr >= 0 and 1 <= nlev <= 4, else
+ * MHD_EINVAL.  Uses the primitive scratch, which every step rewrites
+ * before reading (the state is not touched).  Synchronises. */
+mhd_status mhd_pressure_gradient(mhd_ctx* ctx, double scale, double thr, int nlev, double* out);
+
 /* Magnetic helicity H = sum A.B dx^3 per box (Sec. 4.5; h has nbox entries),
  * of the cell-centre field (mean of the two faces per axis), with A in the
  * Coulomb gauge of the periodic box: A_k = i k x B_k / |k|^2 from the

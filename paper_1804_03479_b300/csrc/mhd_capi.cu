@@ -447,7 +447,7 @@ extern "C" mhd_status mhd_energies(mhd_ctx* c, double jb_threshold, double* out)
         case MHD_FP32: k_energies<float, float><<<nb, CELL_THREADS, 0, c->stream>>>(c->B, state_of<float, float>(c), jb_threshold, c->part); break;
         default:       k_energies<float, double><<<nb, CELL_THREADS, 0, c->stream>>>(c->B, state_of<float, double>(c), jb_threshold, c->part); break;
     }
-    k_finish_energies<<<c->nbox, 32, 0, c->stream>>>(c->B, c->part, c->diag);
+    k_finish_parts<<<c->nbox, 32, 0, c->stream>>>(c->B, c->part, 6, 0x28u, c->diag);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(out, c->diag, (size_t)c->nbox * 6 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -457,6 +457,39 @@ extern "C" mhd_status mhd_energies(mhd_ctx* c, double jb_threshold, double* out)
         out[b * 6 + 1] *= v;
         out[b * 6 + 2] *= v;
         out[b * 6 + 5] /= dx;
+    }
+    return check_device_flags(c);
+}
+
+template <class TU, class TE>
+static void pressure_pass(mhd_ctx* c, double* P)
+{
+    if (c->bc) k_pressure<TU, TE, true><<<c->cell_grid, CELL_THREADS, 0, c->stream>>>(c->B, state_of<TU, TE>(c), c->gamma, P);
+    else k_pressure<TU, TE, false><<<c->cell_grid, CELL_THREADS, 0, c->stream>>>(c->B, state_of<TU, TE>(c), c->gamma, P);
+}
+
+extern "C" mhd_status mhd_pressure_gradient(mhd_ctx* c, double scale, double thr, int nlev, double* out)
+{
+    if (!c || !out) return fail(c, MHD_EINVAL, "null pointer");
+    if (!(scale > 0.0) || !(thr >= 0.0) || nlev < 1 || nlev > 4)
+        return fail(c, MHD_EINVAL, "mhd_pressure_gradient: scale > 0, thr >= 0 and 1 <= nlev <= 4 required");
+    // the cell pressures (FP64) go to the primitive scratch, which every step
+    // and every CFL pass rewrite before reading
+    double* P = (double*)c->W;
+    switch (c->sch.precision) {
+        case MHD_FP64: pressure_pass<double, double>(c, P); break;
+        case MHD_FP32: pressure_pass<float, float>(c, P); break;
+        default:       pressure_pass<float, double>(c, P); break;
+    }
+    if (c->bc) k_pgrad<true><<<c->cell_grid, CELL_THREADS, 0, c->stream>>>(c->B, P, scale, thr, nlev, c->part);
+    else k_pgrad<false><<<c->cell_grid, CELL_THREADS, 0, c->stream>>>(c->B, P, scale, thr, nlev, c->part);
+    k_finish_parts<<<c->nbox, 32, 0, c->stream>>>(c->B, c->part, 5, 0x1u, c->diag);
+    CK(cudaGetLastError());
+    double d[5];
+    for (int b = 0; b < c->nbox; b++) {
+        CK(cudaMemcpyAsync(d, c->diag + (size_t)b * 5, sizeof(d), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        for (int f = 0; f <= nlev; f++) out[(size_t)b * (nlev + 1) + f] = d[f];
     }
     return check_device_flags(c);
 }

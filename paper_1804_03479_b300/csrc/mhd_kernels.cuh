@@ -1296,6 +1296,25 @@ __device__ __forceinline__ double edge_j(const BoxDev& g, TE* const* b, int i, i
          - ((double)b[bb][c] - (double)b[bb][nbr(g, i, j, k, cc, -1)]);
 }
 
+// block reduction of NF per-thread values (bit f of maxmask: maximum, else
+// sum; fixed order) stored at out[0 .. NF-1] by thread 0
+template <int NF>
+__device__ __forceinline__ void block_reduce_store(const double* acc, unsigned maxmask, double* red, double* out)
+{
+    for (int f = 0; f < NF; f++) {
+        red[threadIdx.x] = acc[f];
+        __syncthreads();
+        const bool mx = maxmask >> f & 1;
+        for (int o = CELL_THREADS / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o)
+                red[threadIdx.x] = mx ? fmax(red[threadIdx.x], red[threadIdx.x + o]) : red[threadIdx.x] + red[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[f] = red[0];
+        __syncthreads();
+    }
+}
+
 template <class TU, class TE>
 __global__ void __launch_bounds__(CELL_THREADS) k_energies(Boxes B, StateP<TU, TE> s, double thr,
                                                            double* __restrict__ part)
@@ -1340,35 +1359,88 @@ __global__ void __launch_bounds__(CELL_THREADS) k_energies(Boxes B, StateP<TU, T
             acc[4] = r > thr ? 1.0 : 0.0;
             acc[5] = jm;
         }
-        for (int f = 0; f < 6; f++) {
-            red[threadIdx.x] = acc[f];
-            __syncthreads();
-            const bool mx = f == 3 || f == 5;
-            for (int o = CELL_THREADS / 2; o > 0; o >>= 1) {
-                if (threadIdx.x < o)
-                    red[threadIdx.x] = mx ? fmax(red[threadIdx.x], red[threadIdx.x + o]) : red[threadIdx.x] + red[threadIdx.x + o];
-                __syncthreads();
-            }
-            if (threadIdx.x == 0) part[v * 6 + f] = red[0];
-            __syncthreads();
-        }
+        block_reduce_store<6>(acc, 0x28u, red, part + v * 6);
     }
 }
 
-static __global__ void k_finish_energies(Boxes B, const double* __restrict__ part, double* __restrict__ out)
+// per-box totals of per-virtual-block parts [nvblk][nf] (bit f of maxmask:
+// maximum, else sum), in block order
+static __global__ void k_finish_parts(Boxes B, const double* __restrict__ part, int nf, unsigned maxmask,
+                                      double* __restrict__ out)
 {
     const int b = blockIdx.x;
     const int f = threadIdx.x;
-    if (b >= B.nbox || f >= 6) return;
+    if (b >= B.nbox || f >= nf) return;
     const long long v0 = B.b[b].vblk0;
     const long long v1 = b + 1 < B.nbox ? B.b[b + 1].vblk0 : B.nvblk;
-    const bool mx = f == 3 || f == 5;
+    const bool mx = maxmask >> f & 1;
     double a = 0.0;
     for (long long v = v0; v < v1; v++) {
-        double x = part[v * 6 + f];
+        double x = part[v * nf + f];
         a = mx ? fmax(a, x) : a + x;
     }
-    out[b * 6 + f] = a;
+    out[b * nf + f] = a;
+}
+
+// ---------------------------------------------------------------------------
+// Pressure-gradient refinement indicator of the magnetised blast run
+// (Sec. 5.1): the FP64 gas pressure of every cell from the stored state
+// (cell-centre B the mean of the two faces), then per cell
+// scale |grad P| / P with grad P by centred differences over 2 dx (a
+// neighbour beyond an outflow side is the cell itself), reduced per box to
+// its maximum and the numbers of cells above thr * 2^l, l < nlev <= 4.
+// ---------------------------------------------------------------------------
+template <class TU, class TE, bool OUT>
+__global__ void __launch_bounds__(CELL_THREADS) k_pressure(Boxes B, StateP<TU, TE> s, double gam,
+                                                           double* __restrict__ P)
+{
+    for (long long v = blockIdx.x; v < B.nvblk; v += gridDim.x) {
+        BoxDev g = B.b[box_of_vblk(B, v)];
+        if (!OUT) g.bc = 0;
+        const long long lc = (v - g.vblk0) * CELL_THREADS + threadIdx.x;
+        if (lc >= g.n) continue;
+        int i, j, k;
+        coords(g, lc, i, j, k);
+        const long long c = g.off + lc;
+        const double bx = 0.5 * ((double)s.b[0][c] + (double)s.b[0][nbr(g, i, j, k, 0, 1)]);
+        const double by = 0.5 * ((double)s.b[1][c] + (double)s.b[1][nbr(g, i, j, k, 1, 1)]);
+        const double bz = 0.5 * ((double)s.b[2][c] + (double)s.b[2][nbr(g, i, j, k, 2, 1)]);
+        const double rho = (double)s.rho[c];
+        const double mx = (double)s.m[0][c], my = (double)s.m[1][c], mz = (double)s.m[2][c];
+        P[c] = (gam - 1.0) * ((double)s.e[c] - 0.5 * (mx * mx + my * my + mz * mz) / rho
+                              - 0.5 * (bx * bx + by * by + bz * bz));
+    }
+}
+
+template <bool OUT>
+__global__ void __launch_bounds__(CELL_THREADS) k_pgrad(Boxes B, const double* __restrict__ P, double scale,
+                                                        double thr, int nlev, double* __restrict__ part)
+{
+    // part: [nvblk][5]: max score, then the counts above thr * 2^l
+    __shared__ double red[CELL_THREADS];
+    for (long long v = blockIdx.x; v < B.nvblk; v += gridDim.x) {
+        BoxDev g = B.b[box_of_vblk(B, v)];
+        if (!OUT) g.bc = 0;
+        const long long lc = (v - g.vblk0) * CELL_THREADS + threadIdx.x;
+        double acc[5] = {0, 0, 0, 0, 0};
+        if (lc < g.n) {
+            int i, j, k;
+            coords(g, lc, i, j, k);
+            const long long c = g.off + lc;
+            double g2 = 0.0;
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                const double df = P[nbr(g, i, j, k, d, 1)] - P[nbr(g, i, j, k, d, -1)];
+                g2 += df * df;
+            }
+            const double sc = scale * (sqrt(g2) * (0.5 / g.dx)) / P[c];
+            acc[0] = sc;
+            double t = thr;
+#pragma unroll
+            for (int l = 0; l < 4; l++, t *= 2.0) acc[1 + l] = l < nlev && sc > t ? 1.0 : 0.0;
+        }
+        block_reduce_store<5>(acc, 0x1u, red, part + v * 5);
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -33,7 +33,8 @@ EXPORTS = ["mhd_init", "mhd_set_state", "mhd_get_state", "mhd_cfl_dt", "mhd_step
            "mhd_mlp_set_weights", "mhd_mlp_get_weights", "mhd_mlp_grad", "mhd_mlp_train_step",
            "mhd_mlp_predict", "mhd_nblocks", "mhd_block_features", "mhd_block_error", "mhd_set_selector",
            "mhd_selector_stats", "mhd_floor_count", "mhd_energies", "mhd_helicity",
-           "mhd_set_sweep_pencils", "mhd_get_sweep_pencils", "mhd_set_boundary", "mhd_get_boundary"]
+           "mhd_set_sweep_pencils", "mhd_get_sweep_pencils", "mhd_set_boundary", "mhd_get_boundary",
+           "mhd_pressure_gradient"]
 GROUPS = ["prim_cfl", "predictor_x", "predictor_y", "predictor_z", "emf1", "half_update", "corrector_x",
           "corrector_y", "corrector_z", "emf2", "full_update"]
 
@@ -130,6 +131,7 @@ def lib():
     L.mhd_profile_end.argtypes = [vp, dp, ip, ctypes.POINTER(ctypes.c_int)]
     L.mhd_energies.argtypes = [vp, ctypes.c_double, dp]
     L.mhd_helicity.argtypes = [vp, dp]
+    L.mhd_pressure_gradient.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, dp]
     L.mhd_set_sweep_pencils.argtypes = [vp, ip, ip]
     L.mhd_set_boundary.argtypes = [vp, ip]
     L.mhd_get_boundary.argtypes = [vp, ctypes.POINTER(ip)]
@@ -284,6 +286,16 @@ class Solver:
     def energies(self, jb_threshold=1.0):
         e = self.energies_boxes(jb_threshold)[0]
         return dict(E_T=e[0], U_B=e[1], U_V=e[2], jb_max=e[3], n_above=int(e[4]), j_max=e[5])
+
+    def pressure_gradient_boxes(self, scale, thr, nlev=3):
+        """per box: max of scale |grad P| / P, then the cells above thr * 2^l, l < nlev"""
+        out = (ctypes.c_double * ((nlev + 1) * self.nbox))()
+        self._check(lib().mhd_pressure_gradient(self.h, ctypes.c_double(scale), ctypes.c_double(thr), nlev, out))
+        return np.array(out[:]).reshape(self.nbox, nlev + 1)
+
+    def pressure_gradient(self, scale, thr, nlev=3):
+        r = self.pressure_gradient_boxes(scale, thr, nlev)[0]
+        return dict(max=float(r[0]), counts=[int(x) for x in r[1:]])
 
     def set_sweep_config(self, tile_len, blocks_per_sm):
         self._check(lib().mhd_set_sweep_config(self.h, tile_len, blocks_per_sm))

@@ -1,6 +1,7 @@
 """Diagnostics on the GPU (mhd_energies: E_T, U_B, U_V and the |J|/|B|
-refinement test of Sec. 4.3 / 4.5) against the FP64 oracle, on single boxes
-and a ragged batch, in FP64 and FP32."""
+refinement test of Sec. 4.3 / 4.5; mhd_helicity; mhd_pressure_gradient, the
+refinement test of the blast run of Sec. 5.1) against the FP64 oracle, on
+single boxes and a ragged batch, in FP64 and FP32."""
 import numpy as np
 import pytest
 
@@ -123,5 +124,97 @@ def test_helicity_batch_ragged(M):
         # the state is untouched: a step after the diagnostic equals a step without it
         U0, B0 = s.get_state(box=0)
         assert np.array_equal(U0, boxes[0].U)
+    finally:
+        s.free()
+
+
+def blast_evolved(n=32, r0=0.1, nsteps=3):
+    st = I.mhd_blast(n, r0=r0, density_noise=True)
+    U, B = evolved(st, nsteps, ("vl", "plm", "roe"))
+    return st, U, B
+
+
+def check_pgrad(g, o, tol):
+    assert abs(g["max"] - o["max"]) <= tol * o["max"], (g["max"], o["max"])
+    assert g["counts"] == o["counts"], (g["counts"], o["counts"])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed"])
+def test_pressure_gradient_matches_oracle(M, prec):
+    """the indicator is computed in FP64 from the stored state on both sides,
+    so the counts agree exactly and the maximum to rounding order"""
+    st, U, B = blast_evolved()
+    s = M.Solver(U.shape[1:], st.dx, st.gamma, "vl", "plm", "roe", prec, 0.3)
+    try:
+        if prec == "fp32":
+            U, B = U.astype(np.float32), B.astype(np.float32)
+        elif prec == "mixed":
+            U = U.copy()
+            U[:4] = U[:4].astype(np.float32)     # rho and M are stored in FP32
+        s.set_state(U, B)
+        Ur, Br = U.astype(np.float64), B.astype(np.float64)
+        for scale, thr, nlev in [(10.0, 1.25, 4), (10.0, 40.0, 2), (0.5, 0.3, 1)]:
+            o = orc.pressure_gradient(Ur, Br, st.dx, st.gamma, scale, thr, nlev)
+            g = s.pressure_gradient(scale, thr, nlev)
+            check_pgrad(g, o, 1e-12)
+        assert o["counts"][0] > 0
+    finally:
+        s.free()
+
+
+def test_pressure_gradient_batch_and_outflow(M):
+    _, U1, B1 = blast_evolved(24, 0.12, 2)
+    ob = I.open_box((20, 12, 9), seed=4)
+    boxes = [(U1, B1, 1.0 / 24), (ob.U, ob.B, ob.dx)]
+    s = M.Solver(None, None, 5 / 3, "vl", "plm", "roe", "fp64", 0.3,
+                 shapes=[b[0].shape[1:] for b in boxes], dxs=[b[2] for b in boxes])
+    try:
+        for k, (U, B, dx) in enumerate(boxes):
+            s.set_state(U, B, box=k)
+        got = s.pressure_gradient_boxes(5.0, 0.5, 3)
+        for k, (U, B, dx) in enumerate(boxes):
+            o = orc.pressure_gradient(U, B, dx, 5 / 3, 5.0, 0.5, 3)
+            check_pgrad(dict(max=got[k, 0], counts=[int(x) for x in got[k, 1:]]), o, 1e-12)
+    finally:
+        s.free()
+    s = M.Solver(ob.U.shape[1:], ob.dx, ob.gamma, "vl", "plm", "roe", "fp64", 0.3)
+    try:
+        s.set_boundary(7)
+        s.set_state(ob.U, ob.B)
+        for bc in (7,):
+            o = orc.pressure_gradient(ob.U, ob.B, ob.dx, ob.gamma, 2.0, 0.2, 3, bc=bc)
+            check_pgrad(s.pressure_gradient(2.0, 0.2, 3), o, 1e-12)
+    finally:
+        s.free()
+
+
+def test_pressure_gradient_leaves_the_step_unchanged(M):
+    st, U, B = blast_evolved(24, 0.12, 1)
+    out = []
+    for call in (False, True):
+        s = M.Solver(U.shape[1:], st.dx, st.gamma, "vl", "ppm", "hlld", "fp64", 0.3)
+        try:
+            s.set_state(U, B)
+            s.advance(1)
+            if call:
+                s.pressure_gradient(10.0, 1.25)
+            s.advance(1)
+            out.append(s.get_state())
+        finally:
+            s.free()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_pressure_gradient_rejects_bad_arguments(M):
+    st = I.uniform(8)
+    s = M.Solver(st.U.shape[1:], st.dx, st.gamma, "vl", "plm", "roe", "fp64", 0.3)
+    try:
+        s.set_state(st.U, st.B)
+        for args in [(0.0, 1.0, 1), (1.0, -1.0, 1), (1.0, 1.0, 0), (1.0, 1.0, 5)]:
+            with pytest.raises(RuntimeError):
+                s.pressure_gradient(*args)
+            s.clear_error()                   # errors stay until cleared
+        r = s.pressure_gradient(1.0, 0.0, 4)
+        assert r["max"] < 1e-12 and r["counts"] == [0, 0, 0, 0]
     finally:
         s.free()
