@@ -135,6 +135,48 @@ def step_bc(U: np.ndarray, B: np.ndarray, dx: float, gamma: float, dt: float,
     return int(r)
 
 
+def fix_layers(U, B, gamma, axis, nl, wlo, whi):
+    """Dirichlet sides (the shock tubes of Sec. 5.1 hold the left and right
+    states at the ends of the box): the nl outermost cells at each end of
+    `axis` are ghost cells kept at a fixed state, written here in place.
+    w = (rho, vx, vy, vz, P, Bx, By, Bz) in box axes; a ghost cell gets the
+    conserved state of w and its three lower faces the field of w, except
+    the lower face along `axis` of the first upper ghost cell, which is the
+    upper boundary face of the interior (advanced by CT like every interior
+    face).  Cells and faces beyond the box continue the last ones (the
+    outflow rule).  With nl >= 2 for PLM and nl >= 3 for PPM the interior
+    sees an unbounded region of the fixed state (more layers change nothing):
+    in a VL step only the first ghost cell's half-step state moves, and PPM
+    reads one cell further than the PLM slope."""
+    nd = U.shape[3 - axis]
+    assert nd >= 2 * nl + 1
+
+    def layer(sl):
+        idx = [slice(None)] * 3
+        idx[2 - axis] = sl
+        return tuple(idx)
+
+    for w, sl in ((wlo, slice(0, nl)), (whi, slice(nd - nl, nd))):
+        rho, v, P, b = w[0], np.asarray(w[1:4], float), w[4], np.asarray(w[5:8], float)
+        e = P / (gamma - 1.0) + 0.5 * rho * float(v @ v) + 0.5 * float(b @ b)
+        for f, val in enumerate((rho, rho * v[0], rho * v[1], rho * v[2], e)):
+            U[f][layer(sl)] = val
+        for m in range(3):
+            if m == axis and sl.start == nd - nl:
+                B[m][layer(slice(nd - nl + 1, nd))] = b[m]      # keep the interior's upper face
+            else:
+                B[m][layer(sl)] = b[m]
+
+
+def step_dirichlet(U, B, dx, gamma, dt, integrator, recon, riemann, axis, nl, wlo, whi, bc=0, pfloor=0.0) -> int:
+    """One step with Dirichlet sides along `axis` (fix_layers), outflow
+    clamping beyond them and the boundaries of the mask bc elsewhere; the
+    ghost layers are put back to the fixed state after the step."""
+    fb = step_bc(U, B, dx, gamma, dt, integrator, recon, riemann, bc=bc | (1 << axis), pfloor=pfloor)
+    fix_layers(U, B, gamma, axis, nl, wlo, whi)
+    return fb
+
+
 def cfl_dt(U, B, dx, gamma, cfl, pfloor=0.0, bc=0) -> float:
     nz, ny, nx = U.shape[1:]
     if pfloor > 0.0 or bc:
