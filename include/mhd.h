@@ -187,6 +187,25 @@ mhd_status mhd_autotune(mhd_ctx* ctx, int reps, int* tile_len, int* blocks_per_s
 mhd_status mhd_set_boundary(mhd_ctx* ctx, int outflow_mask);
 mhd_status mhd_get_boundary(mhd_ctx* ctx, int* outflow_mask);
 
+/* Dirichlet sides (the shock tubes of Sec. 5.1 hold the left and right
+ * states at the ends of the box), held as ghost layers inside the box: the
+ * nlayers outermost cells at each end of `axis` are put back to a fixed
+ * state when the call is made, after every mhd_set_state and after every
+ * step, and the axis becomes an outflow axis (the outflow rule holds beyond
+ * the layers).  w_lo, w_hi: 8 doubles each, (rho, vx, vy, vz, P, Bx, By, Bz)
+ * in box axes, for the lower and upper end (host memory, copied).  A ghost
+ * cell gets the conserved state of w and its three lower faces the field of
+ * w, except the lower face along `axis` of the first upper ghost cell: that
+ * is the interior's upper boundary face, which CT advances.  With nlayers
+ * >= 2 (PLM, PLM_PRIM) or >= 3 (PPM) the interior sees an unbounded region
+ * of the fixed state; fewer is MHD_EINVAL, as is 2 nlayers >= the cells
+ * along `axis`, rho <= 0, P <= 0 or a non-finite value.  nlayers = 0
+ * removes the side (the axis stays outflow).  One-box VL contexts without
+ * a selector (else MHD_EUNSUPPORTED).  mhd_set_boundary with the axis's bit
+ * cleared removes the side too.  mhd_get_dirichlet reports nlayers. */
+mhd_status mhd_set_dirichlet(mhd_ctx* ctx, int axis, int nlayers, const double* w_lo, const double* w_hi);
+mhd_status mhd_get_dirichlet(mhd_ctx* ctx, int axis, int* nlayers);
+
 /* Pencil sweeps (VL integrator): on every axis d with bit d of pencil_mask
  * set, the predictor and corrector face sweeps keep the cells around each
  * face in registers (no shared memory): along y and z one thread walks a

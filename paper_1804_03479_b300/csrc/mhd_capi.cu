@@ -1,5 +1,6 @@
 // mhd_capi.cu -- the C ABI declared in include/mhd.h.
 #include <stdarg.h>
+#include <cmath>
 #include <stdlib.h>
 #include <string.h>
 #include <cufft.h>
@@ -60,6 +61,8 @@ static cudaError_t dalloc(mhd_ctx* c, void** p, size_t bytes)
 }
 
 // tile prefix sums of the box table for tile length tl; uploads the table
+static void apply_fixed_layers(mhd_ctx* c);
+
 static cudaError_t layout_tiles(mhd_ctx* c, int tl)
 {
     int t0[3] = {0, 0, 0}, e0 = 0;
@@ -259,6 +262,10 @@ extern "C" mhd_status mhd_set_state_box(mhd_ctx* c, int box, const void* U, cons
         float* dst[4] = {(float*)c->rho, (float*)c->m[0], (float*)c->m[1], (float*)c->m[2]};
         for (int f = 0; f < 4; f++)
             k_convert<float, double><<<1184, 256, 0, c->stream>>>(dst[f] + off, stg + f * N + off, n);
+        CK(cudaGetLastError());
+    }
+    if (c->fix_nl[0] | c->fix_nl[1] | c->fix_nl[2]) {   // the ghost layers hold their fixed states
+        apply_fixed_layers(c);
         CK(cudaGetLastError());
     }
     if (!on_device) CK(cudaStreamSynchronize(c->stream));
@@ -565,6 +572,24 @@ extern "C" mhd_status mhd_get_sweep_config(mhd_ctx* c, int* tile_len, int* block
     return MHD_OK;
 }
 
+// kernels per step of a one-box context: the scheme's 12, an outer-face flux
+// pass per outflow axis and stage, a layer reset per Dirichlet axis
+static void count_launches(mhd_ctx* c)
+{
+    int n = 12;
+    for (int d = 0; d < 3; d++) n += 2 * (c->bc >> d & 1) + (c->fix_nl[d] > 0);
+    c->launches = n;
+}
+
+static void apply_fixed_layers(mhd_ctx* c)
+{
+    switch (c->sch.precision) {
+        case MHD_FP64: fix_layers<double, double>(c, state_of<double, double>(c), c->stream); break;
+        case MHD_FP32: fix_layers<float, float>(c, state_of<float, float>(c), c->stream); break;
+        default:       fix_layers<float, double>(c, state_of<float, double>(c), c->stream); break;
+    }
+}
+
 extern "C" mhd_status mhd_set_boundary(mhd_ctx* c, int outflow_mask)
 {
     if (!c) return MHD_EINVAL;
@@ -577,7 +602,65 @@ extern "C" mhd_status mhd_set_boundary(mhd_ctx* c, int outflow_mask)
     }
     c->bc = outflow_mask;
     c->hbox[0].bc = outflow_mask;
+    for (int d = 0; d < 3; d++)
+        if (!(outflow_mask >> d & 1)) c->fix_nl[d] = 0;   // a Dirichlet side needs the clamp beyond it
+    count_launches(c);
     CK(layout_tiles(c, c->B.tl));   // uploads the box table (and drops a captured step)
+    return MHD_OK;
+}
+
+extern "C" mhd_status mhd_set_dirichlet(mhd_ctx* c, int axis, int nlayers, const double* w_lo, const double* w_hi)
+{
+    if (!c) return MHD_EINVAL;
+    if (axis < 0 || axis > 2) return fail(c, MHD_EINVAL, "axis must be 0, 1 or 2");
+    if (nlayers == 0) {
+        c->fix_nl[axis] = 0;
+        count_launches(c);
+        CK(layout_tiles(c, c->B.tl));
+        return MHD_OK;
+    }
+    if (!w_lo || !w_hi) return fail(c, MHD_EINVAL, "null pointer");
+    if (c->sch.integrator != MHD_VL || c->nbox != 1 || c->sel)
+        return fail(c, MHD_EUNSUPPORTED, "Dirichlet sides are built for one-box VL contexts without a selector");
+    const int need = c->sch.recon == MHD_PPM ? 3 : 2;
+    const BoxDev& g = c->hbox[0];
+    const int nd = axis == 0 ? g.nx : (axis == 1 ? g.ny : g.nz);
+    if (nlayers < need || 2 * nlayers + 1 > nd)
+        return fail(c, MHD_EINVAL, "nlayers must be >= %d for this reconstruction and leave an interior (2 nlayers < %d)",
+                    need, nd);
+    const double* w[2] = {w_lo, w_hi};
+    FixedState f[2];
+    for (int side = 0; side < 2; side++) {
+        const double* q = w[side];
+        for (int m = 0; m < 8; m++)
+            if (!std::isfinite(q[m])) return fail(c, MHD_EINVAL, "non-finite Dirichlet state");
+        if (!(q[0] > 0.0) || !(q[4] > 0.0)) return fail(c, MHD_EINVAL, "Dirichlet state needs rho > 0 and P > 0");
+        f[side].u[0] = q[0];
+        f[side].u[1] = q[0] * q[1];
+        f[side].u[2] = q[0] * q[2];
+        f[side].u[3] = q[0] * q[3];
+        f[side].u[4] = q[4] / (c->gamma - 1.0) + 0.5 * q[0] * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3])
+                     + 0.5 * (q[5] * q[5] + q[6] * q[6] + q[7] * q[7]);
+        for (int m = 0; m < 3; m++) f[side].b[m] = q[5 + m];
+    }
+    if (!(c->bc >> axis & 1)) {
+        mhd_status st = mhd_set_boundary(c, c->bc | (1 << axis));
+        if (st != MHD_OK) return st;
+    }
+    c->fix[axis][0] = f[0];
+    c->fix[axis][1] = f[1];
+    c->fix_nl[axis] = nlayers;
+    count_launches(c);
+    CK(layout_tiles(c, c->B.tl));   // drops a captured step
+    apply_fixed_layers(c);
+    CK(cudaGetLastError());
+    return MHD_OK;
+}
+
+extern "C" mhd_status mhd_get_dirichlet(mhd_ctx* c, int axis, int* nlayers)
+{
+    if (!c || !nlayers || axis < 0 || axis > 2) return fail(c, MHD_EINVAL, "bad arguments");
+    *nlayers = c->fix_nl[axis];
     return MHD_OK;
 }
 

@@ -23,6 +23,8 @@ struct mhd_ctx {
     int sweep_bps;                  // persistent sweep blocks per SM
     int bc;                         // outflow axes (bit d), one-box VL contexts; 0 = periodic
     void* fout;                     // [3][7][cross-section] outer-face fluxes of the outflow axes
+    int fix_nl[3];                  // Dirichlet sides: fixed ghost layers at each end of axis d (0: none)
+    mhd::FixedState fix[3][2];      // their states, lower and upper end
     int pencil_mask;                // VL sweeps by pencils on the axes of these bits
     int pencil_len;                 // faces per pencil-segment thread
     size_t szu, sze, szr;          // element sizes: rho/M storage, e/B storage, arithmetic
@@ -130,6 +132,20 @@ inline int sweep_grid(const mhd_ctx* c, int d)
     return c->B.ntile[d] < cap ? c->B.ntile[d] : cap;
 }
 
+// put the ghost layers of the Dirichlet sides back to their fixed states
+template <class TU, class TE>
+void fix_layers(mhd_ctx* c, const StateP<TU, TE>& s, cudaStream_t st)
+{
+    for (int d = 0; d < 3; d++) {
+        const int nl = c->fix_nl[d];
+        if (!nl) continue;
+        const BoxDev& g = c->hbox[0];
+        const int na = d == 0 ? g.ny : g.nx, nb = d == 2 ? g.ny : g.nz;
+        const long long nt = 2LL * nl * na * nb;
+        k_fix_layers<TU, TE><<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(g, d, nl, c->fix[d][0], c->fix[d][1], s);
+    }
+}
+
 template <class R, class TU, class TE, int INTEG, int RECON, int SOLVER>
 void run_step(mhd_ctx* c, bool device_dt)
 {
@@ -208,6 +224,7 @@ void run_step(mhd_ctx* c, bool device_dt)
             k_full<R, TU, TE, true><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, (const R*)c->fout, cs);
         else
             k_full<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc);
+        fix_layers(c, s, st);
         prof_mark(c, 11);
     } else {
         R* WM = (R*)c->WM;

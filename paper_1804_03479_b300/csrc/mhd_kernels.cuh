@@ -987,6 +987,48 @@ __global__ void k_outer_flux(BoxDev g, int d, const R* __restrict__ Wst, const T
     for (int m = 0; m < 7; m++) Fd[(long long)m * cs + q] = f[m];
 }
 
+// Dirichlet sides (the shock tubes of Sec. 5.1 hold the left and right
+// states at the ends of the box): the nl outermost cells at each end of axis
+// d are ghost cells put back to a fixed state after every step; beyond them
+// the outflow rule holds.  A ghost cell gets the fixed conserved state and
+// its three lower faces the fixed field, except the lower face along d of the
+// first upper ghost cell: that is the interior's upper boundary face, which
+// CT advances.  One thread per ghost cell (2 nl layers of the cross-section,
+// a + b * n_a as in k_outer_flux).
+struct FixedState {
+    double u[5];   // rho, Mx, My, Mz, e
+    double b[3];   // Bx, By, Bz
+};
+
+template <class TU, class TE>
+__global__ void k_fix_layers(BoxDev g, int d, int nl, FixedState lo, FixedState hi, StateP<TU, TE> s)
+{
+    const int nd = d == 0 ? g.nx : (d == 1 ? g.ny : g.nz);
+    const int na = d == 0 ? g.ny : g.nx, nb = d == 2 ? g.ny : g.nz;
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= 2LL * nl * na * nb) return;
+    const int a = (int)(q % na);
+    const long long r = q / na;
+    const int b = (int)(r % nb);
+    const int l = (int)(r / nb);                 // 0 .. 2 nl - 1
+    const bool up = l >= nl;
+    const int p = up ? nd - 2 * nl + l : l;      // position along d
+    int i, j, k;
+    if (d == 0) { i = p; j = a; k = b; }
+    else if (d == 1) { i = a; j = p; k = b; }
+    else { i = a; j = b; k = p; }
+    const long long c = cell_of(g, i, j, k);
+    const FixedState& f = up ? hi : lo;
+    s.rho[c] = TU(f.u[0]);
+    s.m[0][c] = TU(f.u[1]);
+    s.m[1][c] = TU(f.u[2]);
+    s.m[2][c] = TU(f.u[3]);
+    s.e[c] = TE(f.u[4]);
+#pragma unroll
+    for (int m = 0; m < 3; m++)
+        if (m != d || p != nd - nl) s.b[m][c] = TE(f.b[m]);
+}
+
 // outflow: for each outflow axis along which (i, j, k) is the last cell, add
 // the outer-face flux minus the cell's own lower-face flux to the divergence
 // (the stencil saw the cell as its own upper neighbour)

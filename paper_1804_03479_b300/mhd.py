@@ -34,7 +34,7 @@ EXPORTS = ["mhd_init", "mhd_set_state", "mhd_get_state", "mhd_cfl_dt", "mhd_step
            "mhd_mlp_predict", "mhd_nblocks", "mhd_block_features", "mhd_block_error", "mhd_set_selector",
            "mhd_selector_stats", "mhd_floor_count", "mhd_energies", "mhd_helicity",
            "mhd_set_sweep_pencils", "mhd_get_sweep_pencils", "mhd_set_boundary", "mhd_get_boundary",
-           "mhd_pressure_gradient"]
+           "mhd_pressure_gradient", "mhd_set_dirichlet", "mhd_get_dirichlet"]
 GROUPS = ["prim_cfl", "predictor_x", "predictor_y", "predictor_z", "emf1", "half_update", "corrector_x",
           "corrector_y", "corrector_z", "emf2", "full_update"]
 
@@ -134,6 +134,8 @@ def lib():
     L.mhd_pressure_gradient.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, dp]
     L.mhd_set_sweep_pencils.argtypes = [vp, ip, ip]
     L.mhd_set_boundary.argtypes = [vp, ip]
+    L.mhd_set_dirichlet.argtypes = [vp, ip, ip, dp, dp]
+    L.mhd_get_dirichlet.argtypes = [vp, ip, ctypes.POINTER(ip)]
     L.mhd_get_boundary.argtypes = [vp, ctypes.POINTER(ip)]
     L.mhd_get_sweep_pencils.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip)]
     # every entry point that returns an mhd_status; the others got their
@@ -303,6 +305,18 @@ class Solver:
     def set_boundary(self, outflow_mask):
         """outflow (zero-gradient) boundaries on the axes of outflow_mask (bit d: axis d)"""
         self._check(lib().mhd_set_boundary(self.h, outflow_mask))
+
+    def set_dirichlet(self, axis, nlayers, w_lo=None, w_hi=None):
+        """Dirichlet sides along axis: nlayers ghost layers at each end held at
+        w_lo / w_hi = (rho, vx, vy, vz, P, Bx, By, Bz); nlayers = 0 removes them"""
+        lo = (ctypes.c_double * 8)(*([0.0] * 8 if w_lo is None else [float(v) for v in w_lo]))
+        hi = (ctypes.c_double * 8)(*([0.0] * 8 if w_hi is None else [float(v) for v in w_hi]))
+        self._check(lib().mhd_set_dirichlet(self.h, axis, nlayers, lo, hi))
+
+    def dirichlet(self, axis):
+        a = ctypes.c_int()
+        self._check(lib().mhd_get_dirichlet(self.h, axis, ctypes.byref(a)))
+        return a.value
 
     def boundary(self):
         a = ctypes.c_int()
