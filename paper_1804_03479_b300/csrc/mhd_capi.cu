@@ -195,7 +195,8 @@ static mhd_status init_common(int nbox, const mhd_grid* grids, double gamma, con
     if (e == cudaSuccess) e = dalloc(c, (void**)&c->dt, sizeof(double) * nbox);
     if (e == cudaSuccess) e = dalloc(c, (void**)&c->dtc, sizeof(DtBox) * nbox);
     if (e == cudaSuccess) e = dalloc(c, (void**)&c->smax, sizeof(double) * nbox);
-    if (e == cudaSuccess) e = dalloc(c, (void**)&c->smax_part, sizeof(double) * vb);
+    if (e == cudaSuccess) e = dalloc(c, (void**)&c->smax_part, sizeof(unsigned long long) * nbox);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->smax_part, 0, sizeof(unsigned long long) * nbox, c->stream);
     if (e == cudaSuccess) e = dalloc(c, (void**)&c->bad, sizeof(unsigned long long));
     if (e == cudaSuccess) e = dalloc(c, (void**)&c->nfloor, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemsetAsync(c->nfloor, 0, sizeof(unsigned long long), c->stream);
@@ -333,7 +334,7 @@ extern "C" mhd_status mhd_cfl_dt(mhd_ctx* c, double* dt)
         case MHD_FP32: prim_pass<float, float, float>(c); break;
         default:       prim_pass<float, float, double>(c); break;
     }
-    k_finalize_dt<<<c->nbox, 256, 0, c->stream>>>(c->B, c->smax_part, c->sch.cfl, nullptr, c->smax, nullptr);
+    k_finalize_dt<<<(c->nbox + 127) / 128, 128, 0, c->stream>>>(c->B, c->smax_part, c->sch.cfl, nullptr, c->smax, nullptr);
     CK(cudaGetLastError());
     double* s = (double*)malloc(sizeof(double) * c->nbox);
     if (!s) return fail(c, MHD_ENOMEM, "host allocation failed");

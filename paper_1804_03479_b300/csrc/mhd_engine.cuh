@@ -44,7 +44,8 @@ struct mhd_ctx {
     double* dt;                     // [nbox]
     mhd::DtBox* dtc;                // [nbox] dt and its ratios to dx
     double* smax;                   // [nbox] signal-speed maximum of each box
-    double* smax_part;              // [nvblk] maximum of each virtual block
+    unsigned long long* smax_part;  // [nbox] signal-speed maximum accumulators (bits of a double >= 0;
+                                    // cleared by k_finalize_dt)
     int cell_grid;                  // persistent grid of the per-cell kernels
     unsigned long long* bad;
     unsigned long long* nfloor;     // cells raised to the pressure floor
@@ -170,7 +171,7 @@ void run_step(mhd_ctx* c, bool device_dt)
     else
         k_prim<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, W, gam, device_dt ? c->smax_part : nullptr, c->bad,
                                                        c->sch.pfloor, c->nfloor);
-    if (device_dt) k_finalize_dt<<<c->nbox, 256, 0, st>>>(g, c->smax_part, c->sch.cfl, c->dt, c->smax, c->dtc);
+    if (device_dt) k_finalize_dt<<<(c->nbox + 127) / 128, 128, 0, st>>>(g, c->smax_part, c->sch.cfl, c->dt, c->smax, c->dtc);
     prof_mark(c, 1);
 
     if (INTEG == VL) {

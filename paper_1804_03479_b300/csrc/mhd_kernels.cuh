@@ -202,15 +202,44 @@ __device__ __forceinline__ void atomic_max_pos(unsigned long long* p, double v)
 // a1 + a2: primitives of every cell, the per-box CFL signal-speed maximum and
 // a record of the first cell with rho <= 0 or P <= 0 (or not finite).
 // ---------------------------------------------------------------------------
+// block maximum of the threads' values v >= 0, folded into *acc by an atomic
+// maximum on the bits of the double (monotone for values >= 0); every thread
+// of the block calls it
+__device__ __forceinline__ void block_max_to(double v, double* red, unsigned long long* acc)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double m = threadIdx.x < blockDim.x / 32 ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (!(m > 0.0)) m = 0.0;      // -0 (and NaN) as +0: the bits then order as the values
+        if (threadIdx.x == 0) atomicMax(acc, (unsigned long long)__double_as_longlong(m));
+    }
+    __syncthreads();
+}
+
 template <class R, class TU, class TE, bool OUT = false>
 __global__ void __launch_bounds__(CELL_THREADS) k_prim(Boxes B, StateP<TU, TE> s, R* __restrict__ W, double gam,
-                                                       double* smax_part, unsigned long long* bad_cell,
+                                                       unsigned long long* smax_acc, unsigned long long* bad_cell,
                                                        double pfloor = 0.0, unsigned long long* nfloor = nullptr)
 {
     const long long N = B.N;
-    __shared__ double red[CELL_THREADS];
+    __shared__ double red[CELL_THREADS / 32];
+    // CFL signal speeds: a running maximum per thread over the cells of one
+    // box, folded into the box's accumulator when the (block-uniform) box
+    // changes and at the end; no barrier per virtual block
+    double run = 0.0;
+    int cur = -1;
     for (long long v = blockIdx.x; v < B.nvblk; v += gridDim.x) {
         const int bi = box_of_vblk(B, v);
+        if (smax_acc && bi != cur) {
+            if (cur >= 0) block_max_to(run, red, smax_acc + cur);
+            run = 0.0;
+            cur = bi;
+        }
         BoxDev g = B.b[bi];
         if (!OUT) g.bc = 0;     // periodic instantiation: the wrap is compiled in
         const long long lc = (v - g.vblk0) * CELL_THREADS + threadIdx.x;
@@ -243,7 +272,7 @@ __global__ void __launch_bounds__(CELL_THREADS) k_prim(Boxes B, StateP<TU, TE> s
 #pragma unroll
             for (int f = 0; f < 8; f++) W[f * N + c] = w[f];
             if (!(w[0] > R(0)) || !(w[4] > R(0))) atomicMin(bad_cell, (unsigned long long)c);
-            if (smax_part) {
+            if (smax_acc) {
                 R a2 = R(gam) * w[4] / w[0];
                 R sm = R(0);
 #pragma unroll
@@ -255,48 +284,24 @@ __global__ void __launch_bounds__(CELL_THREADS) k_prim(Boxes B, StateP<TU, TE> s
                 local = (double)sm;
             }
         }
-        if (smax_part) {
-            // virtual-block maximum (the block lies in one box); no atomics
-            // warp maxima by shuffles, then the 8 warps' through shared memory
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) local = fmax(local, __shfl_xor_sync(0xffffffffu, local, o));
-            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = local;
-            __syncthreads();
-            if (threadIdx.x < 32) {
-                double m = threadIdx.x < CELL_THREADS / 32 ? red[threadIdx.x] : 0.0;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-                if (threadIdx.x == 0) smax_part[v] = m;
-            }
-            __syncthreads();
-        }
+        run = fmax(run, local);
     }
+    if (smax_acc && cur >= 0) block_max_to(run, red, smax_acc + cur);
 }
 
-// dt of every box from the maxima of its virtual blocks (one block per box)
-static __global__ void k_finalize_dt(Boxes B, const double* __restrict__ smax_part, double cfl, double* dt,
+// dt of every box from its signal-speed maximum (the accumulator, which is
+// cleared for the next primitive pass); one thread per box
+static __global__ void k_finalize_dt(Boxes B, unsigned long long* __restrict__ smax_acc, double cfl, double* dt,
                                      double* smax_box, DtBox* dtb)
 {
-    const int b = blockIdx.x;
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B.nbox) return;
-    const long long v0 = B.b[b].vblk0;
-    const long long v1 = b + 1 < B.nbox ? B.b[b + 1].vblk0 : B.nvblk;
-    __shared__ double red[256];
-    double m = 0.0;
-    for (long long v = v0 + threadIdx.x; v < v1; v += blockDim.x) m = fmax(m, smax_part[v]);
-    red[threadIdx.x] = m;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        double sm = red[0];
-        if (smax_box) smax_box[b] = sm;
-        const double d = sm > 0.0 ? cfl * B.b[b].dx / sm : 0.0;
-        if (dt) dt[b] = d;
-        if (dtb) write_dtbox(dtb + b, d, B.b[b].dx);
-    }
+    const double sm = __longlong_as_double((long long)smax_acc[b]);
+    smax_acc[b] = 0ull;
+    if (smax_box) smax_box[b] = sm;
+    const double d = sm > 0.0 ? cfl * B.b[b].dx / sm : 0.0;
+    if (dt) dt[b] = d;
+    if (dtb) write_dtbox(dtb + b, d, B.b[b].dx);
 }
 
 // dt of every box from a host value (v > 0) or from dt[] (v <= 0)
@@ -1142,31 +1147,59 @@ __global__ void __launch_bounds__(CELL_THREADS) k_full(Boxes B, StateP<TU, TE> s
     int i, j, k;
     coords(g, lc, i, j, k);
     const long long c = g.off + lc;
+    const long long cp[3] = {nbr(g, i, j, k, 0, 1), nbr(g, i, j, k, 1, 1), nbr(g, i, j, k, 2, 1)};
+    // every operand is loaded before any arithmetic: the ~45 loads are
+    // independent, and issued together they keep the memory system busy
+    // (interleaved with the arithmetic, a few at a time, the kernel waited
+    // on each group in turn)
+    R fc[3][5], fn[3][5];
+#pragma unroll
+    for (int d = 0; d < 3; d++)
+#pragma unroll
+        for (int m = 0; m < 5; m++) {
+            fc[d][m] = F[((long long)d * 7 + m) * N + c];
+            fn[d][m] = F[((long long)d * 7 + m) * N + cp[d]];
+        }
+    R ec[3], en[3][3];      // E_m at the cell's edges and at those shifted by +1 along a != m
+#pragma unroll
+    for (int m = 0; m < 3; m++) {
+        ec[m] = E[m * N + c];
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+            if (a != m) en[m][a] = E[m * N + cp[a]];
+    }
+    const TU rho0 = s.rho[c], mx0 = s.m[0][c], my0 = s.m[1][c], mz0 = s.m[2][c];
+    const TE e0 = s.e[c], b00 = s.b[0][c], b10 = s.b[1][c], b20 = s.b[2][c];
     TU du[4] = {TU(0), TU(0), TU(0), TU(0)};
     TE due = TE(0);
 #pragma unroll
     for (int d = 0; d < 3; d++) {
         const int t1 = d == 2 ? 0 : d + 1, t2 = d == 0 ? 2 : d - 1;
-        const R* Fd = F + (long long)d * 7 * N;
-        long long cp = nbr(g, i, j, k, d, 1);
-        du[0] += TU(Fd[cp] - Fd[c]);
-        du[1 + d] += TU(Fd[N + cp] - Fd[N + c]);
-        du[1 + t1] += TU(Fd[2 * N + cp] - Fd[2 * N + c]);
-        du[1 + t2] += TU(Fd[3 * N + cp] - Fd[3 * N + c]);
-        due += TE(Fd[4 * N + cp] - Fd[4 * N + c]);
+        du[0] += TU(fn[d][0] - fc[d][0]);
+        du[1 + d] += TU(fn[d][1] - fc[d][1]);
+        du[1 + t1] += TU(fn[d][2] - fc[d][2]);
+        du[1 + t2] += TU(fn[d][3] - fc[d][3]);
+        due += TE(fn[d][4] - fc[d][4]);
     }
     // outflow: the last cell's upper neighbour is the cell itself (a zero
     // difference above); add its outer-face flux instead
     if (g.bc) outer_divergence(g, i, j, k, c, N, F, Fout, cs, du, due);
     // rho and M in their storage type, the energy in TE (Eq. 10)
     const TU ru = DtOf<TU>::dtdx(dtb[bi]);
-    s.rho[c] = s.rho[c] - ru * du[0];
-    s.m[0][c] = s.m[0][c] - ru * du[1];
-    s.m[1][c] = s.m[1][c] - ru * du[2];
-    s.m[2][c] = s.m[2][c] - ru * du[3];
-    s.e[c] = s.e[c] - r * due;
+    s.rho[c] = rho0 - ru * du[0];
+    s.m[0][c] = mx0 - ru * du[1];
+    s.m[1][c] = my0 - ru * du[2];
+    s.m[2][c] = mz0 - ru * du[3];
+    s.e[c] = e0 - r * due;
+    // face field by CT (Eq. 13): the circulation of E around face d, in the
+    // order of curl_face
+    const TE bo[3] = {b00, b10, b20};
 #pragma unroll
-    for (int d = 0; d < 3; d++) s.b[d][c] = s.b[d][c] - r * curl_face<TE>(g, N, E, i, j, k, d);
+    for (int d = 0; d < 3; d++) {
+        const int t1 = d == 2 ? 0 : d + 1, t2 = d == 0 ? 2 : d - 1;
+        const TE curl = (TE(en[t2][t1]) - TE(ec[t2])) - (TE(en[t1][t2]) - TE(ec[t1]));
+        s.b[d][c] = bo[d] - r * curl;
+    }
     }
 }
 

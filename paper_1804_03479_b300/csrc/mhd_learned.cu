@@ -302,7 +302,7 @@ static void run_step_learned(mhd_ctx* c, bool device_dt)
     prof_mark(c, 0);
     k_prim<R, float, float><<<nb, CELL_THREADS, 0, st>>>(g, s, W, gam, device_dt ? c->smax_part : nullptr, c->bad,
                                                          c->sch.pfloor, c->nfloor);
-    if (device_dt) k_finalize_dt<<<c->nbox, 256, 0, st>>>(g, c->smax_part, c->sch.cfl, c->dt, c->smax, c->dtc);
+    if (device_dt) k_finalize_dt<<<(c->nbox + 127) / 128, 128, 0, st>>>(g, c->smax_part, c->sch.cfl, c->dt, c->smax, c->dtc);
     // selector: features of the current state, one inference, tile lists
     const int fgrid = (int)((nblk + 255) / 256 < 148 * 16 ? (nblk + 255) / 256 : 148 * 16);
     k_block_features<R><<<fgrid, 256, 0, st>>>(c->hbox[0], W, n, (float)gam, c->sel_feats);
