@@ -1084,14 +1084,52 @@ __global__ void __launch_bounds__(CELL_THREADS) k_half(Boxes B, StateP<TU, TE> s
     int i, j, k;
     coords(g, lc, i, j, k);
     const long long c = g.off + lc;
+    // every operand is loaded before any arithmetic (independent loads
+    // issued together, as in k_full).  Edge fields: E_m at the cell (ec),
+    // shifted by +1 along a != m (en), and on the three diagonals the upper
+    // faces' circulations need: E_2 at (i+1, j+1, k), E_1 at (i+1, j, k+1),
+    // E_0 at (i, j+1, k+1)
+    const int ip = bidx(i + 1, g.nx, g.bc & 1), jp = bidx(j + 1, g.ny, g.bc & 2), kp = bidx(k + 1, g.nz, g.bc & 4);
+    const long long cp[3] = {cell_of(g, ip, j, k), cell_of(g, i, jp, k), cell_of(g, i, j, kp)};
+    R fc[3][5], fn[3][5];
+#pragma unroll
+    for (int d = 0; d < 3; d++)
+#pragma unroll
+        for (int m = 0; m < 5; m++) {
+            fc[d][m] = F[((long long)d * 7 + m) * N + c];
+            fn[d][m] = F[((long long)d * 7 + m) * N + cp[d]];
+        }
+    R ec[3], en[3][3];
+#pragma unroll
+    for (int m = 0; m < 3; m++) {
+        ec[m] = E[m * N + c];
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+            if (a != m) en[m][a] = E[m * N + cp[a]];
+    }
+    const R e2xy = E[2 * N + cell_of(g, ip, jp, k)], e1xz = E[N + cell_of(g, ip, j, kp)],
+            e0yz = E[cell_of(g, i, jp, kp)];
+    TE blo[3], bhi[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        blo[d] = s.b[d][c];
+        bhi[d] = s.b[d][cp[d]];
+    }
+    const TU rho0 = s.rho[c], mx0 = s.m[0][c], my0 = s.m[1][c], mz0 = s.m[2][c];
+    const TE e0 = s.e[c];
+    // half-step face field (Eq. 13 with dt/2) of the lower and upper faces,
+    // each circulation in the order of curl_face
     TE bc[3];
 #pragma unroll
     for (int d = 0; d < 3; d++) {
-        TE lo = s.b[d][c] - r * curl_face<TE>(g, N, E, i, j, k, d);
-        int i2 = i, j2 = j, k2 = k;
-        if (d == 0) i2 = bidx(i + 1, g.nx, g.bc & 1); else if (d == 1) j2 = bidx(j + 1, g.ny, g.bc & 2);
-        else k2 = bidx(k + 1, g.nz, g.bc & 4);
-        TE hi = s.b[d][cell_of(g, i2, j2, k2)] - r * curl_face<TE>(g, N, E, i2, j2, k2, d);
+        const int t1 = d == 2 ? 0 : d + 1, t2 = d == 0 ? 2 : d - 1;
+        // E_t2 at c + e_d + e_t1 and E_t1 at c + e_d + e_t2
+        const R et2d = d == 0 ? e2xy : (d == 1 ? e0yz : e1xz);
+        const R et1d = d == 0 ? e1xz : (d == 1 ? e2xy : e0yz);
+        const TE clo = (TE(en[t2][t1]) - TE(ec[t2])) - (TE(en[t1][t2]) - TE(ec[t1]));
+        const TE chi = (TE(et2d) - TE(en[t2][d])) - (TE(et1d) - TE(en[t1][d]));
+        const TE lo = blo[d] - r * clo;
+        const TE hi = bhi[d] - r * chi;
         Bh[d][c] = lo;
         bc[d] = TE(0.5) * (lo + hi);
     }
@@ -1102,21 +1140,19 @@ __global__ void __launch_bounds__(CELL_THREADS) k_half(Boxes B, StateP<TU, TE> s
 #pragma unroll
     for (int d = 0; d < 3; d++) {
         const int t1 = d == 2 ? 0 : d + 1, t2 = d == 0 ? 2 : d - 1;
-        const R* Fd = F + (long long)d * 7 * N;
-        long long cp = nbr(g, i, j, k, d, 1);
-        du[0] += TU(Fd[cp] - Fd[c]);
-        du[1 + d] += TU(Fd[N + cp] - Fd[N + c]);
-        du[1 + t1] += TU(Fd[2 * N + cp] - Fd[2 * N + c]);
-        du[1 + t2] += TU(Fd[3 * N + cp] - Fd[3 * N + c]);
-        due += TE(Fd[4 * N + cp] - Fd[4 * N + c]);
+        du[0] += TU(fn[d][0] - fc[d][0]);
+        du[1 + d] += TU(fn[d][1] - fc[d][1]);
+        du[1 + t1] += TU(fn[d][2] - fc[d][2]);
+        du[1 + t2] += TU(fn[d][3] - fc[d][3]);
+        due += TE(fn[d][4] - fc[d][4]);
     }
     // outflow: the last cell's upper neighbour is the cell itself (a zero
     // difference above); add its outer-face flux instead
     if (g.bc) outer_divergence(g, i, j, k, c, N, F, Fout, cs, du, due);
     const TU ru = DtOf<TU>::hdtdx(dtb[bi]);
-    TU rho = s.rho[c] - ru * du[0];
-    TU mx = s.m[0][c] - ru * du[1], my = s.m[1][c] - ru * du[2], mz = s.m[2][c] - ru * du[3];
-    TE e = s.e[c] - r * due;
+    TU rho = rho0 - ru * du[0];
+    TU mx = mx0 - ru * du[1], my = my0 - ru * du[2], mz = mz0 - ru * du[3];
+    TE e = e0 - r * due;
     const TU irho = TU(1) / rho;
     TU vx = mx * irho, vy = my * irho, vz = mz * irho;
     TE p = TE(gam - 1.0) * (e - kinetic<TU, TE>(rho, mx, my, mz, vx, vy, vz)
