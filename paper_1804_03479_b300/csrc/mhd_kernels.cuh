@@ -793,16 +793,16 @@ __global__ void __launch_bounds__(PENCIL_THREADS) k_xwarp(Boxes B, const R* __re
 // the sign of the mass flux through the face (mean on a tie), against the
 // cell-centre reference -(v x B).
 //
-// Tiled: a block owns 32 x 8 cells of an x-y slab and marches EZC planes
+// Tiled: a block owns 32 x 16 cells of an x-y slab and marches EZC planes
 // along z.  Each plane is staged once in shared memory with a one-cell halo
-// on its lower x and y sides (297 cells x 12 values: the three reference
+// on its lower x and y sides (561 cells x 12 values: the three reference
 // components and, per axis, the mass flux and the two B fluxes), three plane
 // slots deep so that one barrier per plane suffices.  F[d] = F + d*7*N.
 // ---------------------------------------------------------------------------
-constexpr int ETX = 32, ETY = 8, EZC = 16;
+constexpr int ETX = 32, ETY = 16, EZC = 16;
 constexpr int EHX = ETX + 1, EPL = EHX * (ETY + 1);   // halo'd plane cells
 constexpr int ENV = 12;                               // values per staged cell
-constexpr int EMF_THREADS = 320;                     // >= EPL: one staged cell per thread
+constexpr int EMF_THREADS = 576;                     // >= EPL: one staged cell per thread
 
 __host__ __device__ __forceinline__ int emf_tiles_of_box(int nx, int ny, int nz)
 {
@@ -872,7 +872,7 @@ __device__ __forceinline__ void emf_load(const R* __restrict__ F, const R* __res
     }
 }
 
-// EMF_THREADS = 320 >= EPL = 297: one staged cell per thread, so a plane
+// EMF_THREADS = 576 >= EPL = 561: one staged cell per thread, so a plane
 // is one round of loads; the loads of plane k+1 are issued before the edges
 // of plane k are computed and stored to shared memory after them.
 template <class R>
