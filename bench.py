@@ -174,11 +174,13 @@ def time_variant(torch, mhd, st, prec, scheme, K, W, dist, stream, profile=True,
     s = mhd.Solver(st.U.shape[1:], st.dx, st.gamma, integ, recon, riemann, prec, 0.3, stream=stream.cuda_stream)
     s.set_state(U, B)
     del U, B
-    s.tuned = None
     if tune:
-        tl, bps, _ = s.autotune(reps=2)
-        mask, plen = s.sweep_pencils()
-        s.tuned = {"tile_len": tl, "blocks_per_sm": bps, "pencil_mask": mask, "pencil_len": plen}
+        s.autotune(reps=2)
+    # the sweep configuration the steps run with (autotuned or the default)
+    tl, bps = s.sweep_config()
+    mask, plen = s.sweep_pencils()
+    s.tuned = {"tile_len": tl, "blocks_per_sm": bps, "pencil_mask": mask, "pencil_len": plen,
+               "autotuned": bool(tune)}
     s.advance(W)
     s.sync()
     if profile:
