@@ -442,6 +442,11 @@ extern "C" mhd_status mhd_set_selector(mhd_ctx* c, mhd_mlp* m)
         cudaFuncSetAttribute(k_sweep<float, PPM, HLLD, 1, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sweep_smem_bytes<float>(PPM, TL_MAX));
     }
+    // this unit's own instantiation of the edge-field kernel (its planes take
+    // more than the default 48 KB of shared memory)
+    if (cudaFuncSetAttribute(k_emf<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)emf_smem_bytes<float>()) !=
+        cudaSuccess)
+        return MHD_ECUDA;
     if (mhd_internal_selector_lists(c) != MHD_OK) return MHD_ENOMEM;
     c->sel = m;
     c->step = run_step_learned;
