@@ -604,10 +604,11 @@ static void rot_prim(const grid_t *g, const double *W, long c, int d, double w[7
 
 /* Eq. 10: conservative update U -= h * div F (F[d][7][n] in sweep frames).  */
 /* Along an outflow axis the last cell's upper face is not stored: its flux  */
-/* is the Riemann flux between the last cell and its zero-gradient ghost.    */
-/* Both face states are the last cell's state Wst (the stage's primitives),  */
-/* since the limited slope against a copied ghost is zero for PLM and PPM,  */
-/* with the normal field of the last face.                                   */
+/* is the Riemann flux between the last cell and its zero-gradient ghost,    */
+/* taken from Fout[d][7][n] at the last cell when given (CTU), else formed   */
+/* here (VL): both face states are then the last cell's state Wst (the       */
+/* stage's primitives), since the limited slope against a copied ghost is    */
+/* zero for PLM and PPM, with the normal field of the last face.             */
 static int is_last(const grid_t *g, long c, int d)
 {
     if (d == 0) return (int)(c % g->nx) == g->nx - 1;
@@ -616,7 +617,7 @@ static int is_last(const grid_t *g, long c, int d)
 }
 
 static void fv_update(const grid_t *g, double h, const double *Usrc, const double *F, double *Udst,
-                      const double *Wst, const double *Bst, int riemann)
+                      const double *Wst, const double *Bst, int riemann, const double *Fout)
 {
     long n = g->n;
     double r = h / g->dx;
@@ -629,9 +630,14 @@ static void fv_update(const grid_t *g, double h, const double *Usrc, const doubl
             const double *Fd = F + (long)d * 7 * n;
             double df[7];
             if ((g->bc >> d & 1) && is_last(g, c, d)) {
-                double w[7], bdum, fu[7];
-                rot_prim(g, Wst, c, d, w, &bdum);
-                orc_riemann(riemann, w, w, Bst[d * n + c], g->gam, fu);
+                double fu[7];
+                if (Fout) {
+                    for (int k = 0; k < 7; k++) fu[k] = Fout[((long)d * 7 + k) * n + c];
+                } else {
+                    double w[7], bdum;
+                    rot_prim(g, Wst, c, d, w, &bdum);
+                    orc_riemann(riemann, w, w, Bst[d * n + c], g->gam, fu);
+                }
                 for (int k = 0; k < 7; k++) df[k] = fu[k] - Fd[k * n + c];
             } else {
                 for (int k = 0; k < 7; k++) df[k] = Fd[k * n + cp] - Fd[k * n + c];
@@ -774,13 +780,13 @@ static long step_vl(const grid_t *g, int recon, int riemann, double dt, double *
     *nfloor += prim_floor(g, U, B, W, U + 4 * n);
     nfb += fluxes(g, recon, riemann, 1, 0, dt, W, B, F, NULL, NULL);
     edge_emf(g, F, W, E);
-    fv_update(g, 0.5 * dt, U, F, Uh, W, B, riemann);
+    fv_update(g, 0.5 * dt, U, F, Uh, W, B, riemann, NULL);
     ct_update(g, 0.5 * dt, B, E, Bh);
     /* steps 4-7: reconstruct at the half step, Riemann, edge E, full update */
     prim_all(g, Uh, Bh, W);
     nfb += fluxes(g, recon, riemann, 0, 0, dt, W, Bh, F, NULL, NULL);
     edge_emf(g, F, W, E);
-    fv_update(g, dt, U, F, U, W, Bh, riemann);
+    fv_update(g, dt, U, F, U, W, Bh, riemann, NULL);
     ct_update(g, dt, B, E, B);
     free(W); free(F); free(E); free(Uh); free(Bh);
     return nfb;
@@ -789,6 +795,96 @@ static long step_vl(const grid_t *g, int recon, int riemann, double dt, double *
 /* ------------------------------------------------------------------------ */
 /* One step of the CTU scheme (Sec. 3.2, CTU steps 1-8).                     */
 /* ------------------------------------------------------------------------ */
+
+/* CTU step 5 for one traced state: the state w of cell s on a d-face (from  */
+/* WM or WP), as 8 conserved components with B_n of cell s at its centre,    */
+/* receives -dt/2 times the divergence of the other two axes' stage-1 fluxes */
+/* across cell s, and goes back to primitives.  Along an outflow axis e the  */
+/* last cell's upper e-face flux is Fo1[e] at that cell.                     */
+static void ctu_corrected(const grid_t *g, int d, long s, const double *wsrc, const double *W, const double *F,
+                          const double *Fo1, double hdt, double wout[7])
+{
+    long n = g->n;
+    double gam = g->gam;
+    int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+    double w[7];
+    for (int k = 0; k < 7; k++) w[k] = wsrc[k * n + s];
+    /* global-frame conserved vector: rho, M(3), e, B(3) */
+    double bcc[3] = {W[5 * n + s], W[6 * n + s], W[7 * n + s]};
+    double q[8];
+    double bglob[3];
+    bglob[d] = bcc[d]; bglob[t1] = w[5]; bglob[t2] = w[6];
+    double vglob[3];
+    vglob[d] = w[1]; vglob[t1] = w[2]; vglob[t2] = w[3];
+    q[0] = w[0];
+    for (int m = 0; m < 3; m++) q[1 + m] = w[0] * vglob[m];
+    q[4] = w[4] / (gam - 1.0) + 0.5 * w[0] * (vglob[0] * vglob[0] + vglob[1] * vglob[1] + vglob[2] * vglob[2])
+           + 0.5 * (bglob[0] * bglob[0] + bglob[1] * bglob[1] + bglob[2] * bglob[2]);
+    for (int m = 0; m < 3; m++) q[5 + m] = bglob[m];
+    int axes[2] = {t1, t2};
+    for (int m = 0; m < 2; m++) {
+        int e = axes[m];
+        int e1 = (e + 1) % 3, e2 = (e + 2) % 3;
+        const double *Fe = F + (long)e * 7 * n;
+        double df[7];
+        if ((g->bc >> e & 1) && is_last(g, s, e)) {
+            for (int k = 0; k < 7; k++) df[k] = Fo1[((long)e * 7 + k) * n + s] - Fe[k * n + s];
+        } else {
+            long sp = shift(g, s, e, 1);
+            for (int k = 0; k < 7; k++) df[k] = Fe[k * n + sp] - Fe[k * n + s];
+        }
+        double r = hdt / g->dx;
+        q[0] -= r * df[0];
+        q[1 + e] -= r * df[1];
+        q[1 + e1] -= r * df[2];
+        q[1 + e2] -= r * df[3];
+        q[4] -= r * df[4];
+        q[5 + e1] -= r * df[5];
+        q[5 + e2] -= r * df[6];
+    }
+    double rho = q[0];
+    double vx = q[1] / rho, vy = q[2] / rho, vz = q[3] / rho;
+    double p = (gam - 1.0) * (q[4] - 0.5 * rho * (vx * vx + vy * vy + vz * vz)
+                              - 0.5 * (q[5] * q[5] + q[6] * q[6] + q[7] * q[7]));
+    double vg[3] = {vx, vy, vz};
+    wout[0] = rho;
+    wout[1] = vg[d];
+    wout[2] = vg[t1];
+    wout[3] = vg[t2];
+    wout[4] = p;
+    wout[5] = q[5 + t1];
+    wout[6] = q[5 + t2];
+}
+
+/* outflow: the flux through the outer (upper) face of each last cell along   */
+/* each outflow axis, into Fo[d][7][n] at that cell.  The ghost beyond it is  */
+/* the last cell itself (reading of the zero-gradient rule used throughout),  */
+/* so the face states are the cell's own upper (plus) and lower (minus)       */
+/* states of the stage; stage 2 corrects both as in step 5.                   */
+static long ctu_outer_fluxes(const grid_t *g, int riemann, const double *WM, const double *WP, const double *Bn,
+                             const double *W, const double *F, const double *Fo1, double hdt, double *Fo)
+{
+    long n = g->n, nfb = 0;
+    for (int d = 0; d < 3; d++) {
+        if (!(g->bc >> d & 1)) continue;
+        const double *WMd = WM + (long)d * 7 * n, *WPd = WP + (long)d * 7 * n;
+#pragma omp parallel for schedule(static) reduction(+ : nfb)
+        for (long c = 0; c < n; c++) {
+            if (!is_last(g, c, d)) continue;
+            double wl[7], wr[7], f[7];
+            if (F) {
+                ctu_corrected(g, d, c, WPd, W, F, Fo1, hdt, wl);
+                ctu_corrected(g, d, c, WMd, W, F, Fo1, hdt, wr);
+            } else {
+                for (int k = 0; k < 7; k++) { wl[k] = WPd[k * n + c]; wr[k] = WMd[k * n + c]; }
+            }
+            nfb += orc_riemann(riemann, wl, wr, Bn[d * n + c], g->gam, f);
+            for (int k = 0; k < 7; k++) Fo[((long)d * 7 + k) * n + c] = f[k];
+        }
+    }
+    return nfb;
+}
+
 static long step_ctu(const grid_t *g, int recon, int riemann, double dt, double *U, double *B, long *nfloor)
 {
     long n = g->n;
@@ -841,82 +937,41 @@ static long step_ctu(const grid_t *g, int recon, int riemann, double dt, double 
             for (int k = 0; k < 7; k++) Fd[k * n + c] = f[k];
         }
     }
+    /* outflow: the stage-1 fluxes through the outer faces */
+    double *Fo1 = NULL, *Fo2 = NULL;
+    if (g->bc) {
+        Fo1 = calloc((size_t)21 * n, sizeof(double));
+        Fo2 = calloc((size_t)21 * n, sizeof(double));
+        nfb += ctu_outer_fluxes(g, riemann, WM, WP, B, W, NULL, NULL, hdt, Fo1);
+    }
     /* step 3: edge E from these fluxes and the cell-centre E at t^n */
     edge_emf(g, F, W, E);
     /* step 4: dt/2 CT update of face B and conservative update of U */
     ct_update(g, hdt, B, E, Bh);
-    fv_update(g, hdt, U, F, Uh, NULL, NULL, riemann);
-    /* step 5: transverse flux-gradient correction of the traced states.     */
-    /* The state of cell s on a d-face, as 8 conserved components (B_n of    */
-    /* cell s at its centre), receives -dt/2 times the divergence of the     */
-    /* other two axes' fluxes across cell s; then back to primitives.        */
+    fv_update(g, hdt, U, F, Uh, NULL, NULL, riemann, Fo1);
+    /* step 5: transverse flux-gradient correction of the traced states     */
+    /* (ctu_corrected), and step 6: Riemann with the half-step face B_n     */
     for (int d = 0; d < 3; d++) {
-        int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
         double *Fd = F2 + (long)d * 7 * n;
         const double *WMd = WM + (long)d * 7 * n, *WPd = WP + (long)d * 7 * n;
 #pragma omp parallel for schedule(static) reduction(+ : nfb)
         for (long c = 0; c < n; c++) {
-            long cell[2] = {shift(g, c, d, -1), c};
             double wface[2][7];
-            for (int side = 0; side < 2; side++) {
-                long s = cell[side];
-                const double *src = side == 0 ? WPd : WMd;
-                double w[7];
-                for (int k = 0; k < 7; k++) w[k] = src[k * n + s];
-                /* global-frame conserved vector: rho, M(3), e, B(3) */
-                double bcc[3] = {W[5 * n + s], W[6 * n + s], W[7 * n + s]};
-                double q[8];
-                double bglob[3];
-                bglob[d] = bcc[d]; bglob[t1] = w[5]; bglob[t2] = w[6];
-                double vglob[3];
-                vglob[d] = w[1]; vglob[t1] = w[2]; vglob[t2] = w[3];
-                q[0] = w[0];
-                for (int m = 0; m < 3; m++) q[1 + m] = w[0] * vglob[m];
-                q[4] = w[4] / (gam - 1.0) + 0.5 * w[0] * (vglob[0] * vglob[0] + vglob[1] * vglob[1] + vglob[2] * vglob[2])
-                       + 0.5 * (bglob[0] * bglob[0] + bglob[1] * bglob[1] + bglob[2] * bglob[2]);
-                for (int m = 0; m < 3; m++) q[5 + m] = bglob[m];
-                int axes[2] = {t1, t2};
-                for (int m = 0; m < 2; m++) {
-                    int e = axes[m];
-                    int e1 = (e + 1) % 3, e2 = (e + 2) % 3;
-                    const double *Fe = F + (long)e * 7 * n;
-                    long sp = shift(g, s, e, 1);
-                    double df[7];
-                    for (int k = 0; k < 7; k++) df[k] = Fe[k * n + sp] - Fe[k * n + s];
-                    double r = hdt / g->dx;
-                    q[0] -= r * df[0];
-                    q[1 + e] -= r * df[1];
-                    q[1 + e1] -= r * df[2];
-                    q[1 + e2] -= r * df[3];
-                    q[4] -= r * df[4];
-                    q[5 + e1] -= r * df[5];
-                    q[5 + e2] -= r * df[6];
-                }
-                double rho = q[0];
-                double vx = q[1] / rho, vy = q[2] / rho, vz = q[3] / rho;
-                double p = (gam - 1.0) * (q[4] - 0.5 * rho * (vx * vx + vy * vy + vz * vz)
-                                          - 0.5 * (q[5] * q[5] + q[6] * q[6] + q[7] * q[7]));
-                double vg[3] = {vx, vy, vz};
-                wface[side][0] = rho;
-                wface[side][1] = vg[d];
-                wface[side][2] = vg[t1];
-                wface[side][3] = vg[t2];
-                wface[side][4] = p;
-                wface[side][5] = q[5 + t1];
-                wface[side][6] = q[5 + t2];
-            }
-            /* step 6: Riemann with the half-step face B_n */
+            ctu_corrected(g, d, shift(g, c, d, -1), WPd, W, F, Fo1, hdt, wface[0]);
+            ctu_corrected(g, d, c, WMd, W, F, Fo1, hdt, wface[1]);
             double f[7];
             nfb += orc_riemann(riemann, wface[0], wface[1], Bh[d * n + c], gam, f);
             for (int k = 0; k < 7; k++) Fd[k * n + c] = f[k];
         }
     }
+    if (g->bc) nfb += ctu_outer_fluxes(g, riemann, WM, WP, Bh, W, F, Fo1, hdt, Fo2);
     /* step 7: edge E from the corrected fluxes and the half-step cell state */
     prim_all(g, Uh, Bh, W);
     edge_emf(g, F2, W, E);
     /* step 8: full update */
-    fv_update(g, dt, U, F2, U, NULL, NULL, riemann);
+    fv_update(g, dt, U, F2, U, NULL, NULL, riemann, Fo2);
     ct_update(g, dt, B, E, B);
+    free(Fo1); free(Fo2);
     free(W); free(F); free(F2); free(E); free(Uh); free(Bh); free(WM); free(WP);
     return nfb;
 }
@@ -926,18 +981,14 @@ static long step_ctu(const grid_t *g, int recon, int riemann, double dt, double 
 /* ------------------------------------------------------------------------ */
 
 /* advance U, B in place by dt with a pressure floor (0 = none) and the     */
-/* boundary mask bc (bit d: outflow along axis d; VL only); returns the      */
-/* number of Roe->HLLE fallbacks (-1 for CTU with outflow), the floored      */
-/* cells in *nfloor                                                          */
+/* boundary mask bc (bit d: outflow along axis d); returns the number of     */
+/* Roe->HLLE fallbacks, the floored cells in *nfloor                         */
 long orc_step_full(int nx, int ny, int nz, double dx, double gam, int integrator, int recon, int riemann,
                    double dt, double pfloor, int bc, double *U, double *B, long *nfloor)
 {
     grid_t g = {nx, ny, nz, (long)nx * ny * nz, dx, gam, pfloor, bc};
     *nfloor = 0;
-    if (integrator == CTU) {
-        if (bc) return -1;
-        return step_ctu(&g, recon, riemann, dt, U, B, nfloor);
-    }
+    if (integrator == CTU) return step_ctu(&g, recon, riemann, dt, U, B, nfloor);
     return step_vl(&g, recon, riemann, dt, U, B, nfloor);
 }
 

@@ -123,15 +123,13 @@ def step_floor(U: np.ndarray, B: np.ndarray, dx: float, gamma: float, dt: float,
 def step_bc(U: np.ndarray, B: np.ndarray, dx: float, gamma: float, dt: float,
             integrator="vl", recon="plm", riemann="roe", bc=0, pfloor=0.0) -> int:
     """step() with outflow (zero-gradient) boundaries along the axes of the
-    bit mask bc (bit d: axis d) and periodic ones elsewhere; VL only.
+    bit mask bc (bit d: axis d) and periodic ones elsewhere, VL or CTU.
     Returns the Roe->HLLE fallbacks."""
     nz, ny, nx = U.shape[1:]
     assert U.shape == (5, nz, ny, nx) and B.shape == (3, nz, ny, nx)
     nf = ctypes.c_long(0)
     r = lib().orc_step_full(nx, ny, nz, dx, gamma, INTEGRATORS[integrator], RECONS[recon], SOLVERS[riemann],
                             dt, pfloor, bc, _p(U), _p(B), ctypes.byref(nf))
-    if r < 0:
-        raise ValueError("outflow boundaries need the VL integrator")
     return int(r)
 
 
@@ -144,10 +142,10 @@ def fix_layers(U, B, gamma, axis, nl, wlo, whi):
     the lower face along `axis` of the first upper ghost cell, which is the
     upper boundary face of the interior (advanced by CT like every interior
     face).  Cells and faces beyond the box continue the last ones (the
-    outflow rule).  With nl >= 2 for PLM and nl >= 3 for PPM the interior
-    sees an unbounded region of the fixed state (more layers change nothing):
-    in a VL step only the first ghost cell's half-step state moves, and PPM
-    reads one cell further than the PLM slope."""
+    outflow rule).  With nl >= 2 (VL with PPM: 3) the interior sees an
+    unbounded region of the fixed state (more layers change nothing): only
+    the first ghost cell's state moves within a step, and in VL PPM reads the
+    half-step states one cell further than the PLM slope."""
     nd = U.shape[3 - axis]
     assert nd >= 2 * nl + 1
 

@@ -6,7 +6,8 @@ the same inflow from a wide upstream region of the fixed state on a periodic
 line (no boundary at all); a box fed by a supersonic stream through both
 sides relaxing to that stream; the minimum layer counts (2 for PLM, 3 for
 PPM), beyond which more layers change nothing; and the Table 1 RJ2a tube,
-whose result equals the outflow one until its waves reach the ends."""
+whose result equals the outflow one until its waves reach the ends.  Both
+integrators, VL and CTU (the paper's accuracy tests use CTU)."""
 import math
 
 import numpy as np
@@ -66,23 +67,27 @@ W_IN = np.array([1.0, 1.5, 0.1, 0.0, 1.0, 0.7, 0.6, 0.2])       # subsonic inflo
 W_BOX = np.array([0.5, 0.2, 0.0, 0.0, 0.4, 0.7, 0.3, -0.1])
 
 
-@pytest.mark.parametrize("recon,nmin", [("plm", 2), ("plm_prim", 2), ("ppm", 3)])
-def test_layers_beyond_the_minimum_change_nothing(recon, nmin):
+@pytest.mark.parametrize("integ,recon,nmin", [("vl", "plm", 2), ("vl", "plm_prim", 2), ("vl", "ppm", 3),
+                                              ("ctu", "plm", 2), ("ctu", "ppm", 2)])
+def test_layers_beyond_the_minimum_change_nothing(integ, recon, nmin):
     """the interior after six steps, with a Riemann problem at the left side,
-    is the same bit for bit for nmin and 6 layers; with nmin - 1 it is not
-    (the first ghost cell's upper face is an interior face, so its cell-centre
-    field already differs from the fixed state at the start of a step, and
-    PPM's interface value reaches one cell further than the PLM slope)"""
+    is the same bit for bit for nmin and 6 layers; with nmin - 1 it is not.
+    The first ghost cell's upper face is an interior face, so its cell-centre
+    field already differs from the fixed state at the start of a step.  In a
+    VL step PPM's interface value at the half step reaches one cell further
+    than the PLM slope; CTU reconstructs once, at t^n, so two layers serve
+    both."""
     out = {}
     for nl in (nmin - 1, nmin, 6):
         U, B, dx = boundary_problem(48, nl, W_IN, W_BOX)
-        U, B = run_dirichlet(U, B, dx, nl, W_IN, W_BOX, 6, ("vl", recon, "roe"))
+        U, B = run_dirichlet(U, B, dx, nl, W_IN, W_BOX, 6, (integ, recon, "roe"))
         out[nl] = (U[..., nl:nl + 48], B[..., nl:nl + 49])
     assert np.array_equal(out[nmin][0], out[6][0]) and np.array_equal(out[nmin][1], out[6][1])
     assert np.abs(out[nmin - 1][0] - out[6][0]).max() > 1e-10
 
 
-@pytest.mark.parametrize("scheme", [("vl", "plm", "roe"), ("vl", "ppm", "hlld"), ("vl", "plm_prim", "hlle")])
+@pytest.mark.parametrize("scheme", [("vl", "plm", "roe"), ("vl", "ppm", "hlld"), ("vl", "plm_prim", "hlle"),
+                                    ("ctu", "ppm", "roe"), ("ctu", "plm", "hlld")])
 def test_supersonic_inflow_equals_a_wide_upstream_region(scheme):
     """every wave of the problem at the left side moves into the box, so the
     interior of this 1-D problem cannot tell the Dirichlet side from a wide
@@ -137,10 +142,11 @@ def test_box_relaxes_to_a_supersonic_stream():
     assert np.abs(B[1] - w[6]).max() <= 1e-7 and np.abs(B[0] - w[5]).max() <= 1e-7
 
 
-def test_rj2a_tube_equals_the_outflow_tube_until_its_waves_arrive():
+@pytest.mark.parametrize("integ", ["ctu", "vl"])
+def test_rj2a_tube_equals_the_outflow_tube_until_its_waves_arrive(integ):
     """Table 1 RJ2a with Dirichlet sides (the paper's setup: box length 1,
-    PPM, Roe, FP64): while its fastest waves are inside the box the ghost
-    layers stay at the end states, so the result is the outflow one"""
+    CTU, PPM, Roe, FP64): while its fastest waves are inside the box the
+    ghost layers stay at the end states, so the result is the outflow one"""
     rows = {}
     for line in open(GOLDEN):
         if line.startswith("#") or not line.strip():
@@ -161,8 +167,8 @@ def test_rj2a_tube_equals_the_outflow_tube_until_its_waves_arrive():
     t = 0.0
     while t < 0.1:            # fast waves of RJ2a travel below 2.4: they stay inside [0, 1]
         dt = orc.cfl_dt(U, B, dx, GAM, 0.3, bc=1)
-        orc.step_dirichlet(U, B, dx, GAM, dt, "vl", "ppm", "roe", 0, nl, wl, wr)
-        orc.step_bc(Uo, Bo, dx, GAM, dt, "vl", "ppm", "roe", bc=1)
+        orc.step_dirichlet(U, B, dx, GAM, dt, integ, "ppm", "roe", 0, nl, wl, wr)
+        orc.step_bc(Uo, Bo, dx, GAM, dt, integ, "ppm", "roe", bc=1)
         t += dt
     # to round-off: the uniform end regions of the outflow run pick up an
     # ulp here and there, the ghost layers of the Dirichlet run are rewritten
