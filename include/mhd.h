@@ -180,10 +180,11 @@ mhd_status mhd_autotune(mhd_ctx* ctx, int reps, int* tile_len, int* blocks_per_s
  * the axes of the bits of outflow_mask (bit d: axis d) outflow boundaries
  * (zero gradient): a cell, face or edge beyond the last one is the last one,
  * and the flux through the outer face of the last cell is the Riemann flux
- * between that cell and its copy; CT then keeps the divergence of every
- * cell.  One-box VL contexts without a selector (else MHD_EUNSUPPORTED);
- * outflow_mask in [0, 7] (else MHD_EINVAL).  mhd_helicity needs a periodic
- * box. */
+ * between that cell and its copy (for CTU, of the cell's own upper and
+ * lower traced states, corrected in the second stage); CT then keeps the
+ * divergence of every cell.  One-box contexts (VL or CTU) without a selector
+ * (else MHD_EUNSUPPORTED); outflow_mask in [0, 7] (else MHD_EINVAL).
+ * mhd_helicity needs a periodic box. */
 mhd_status mhd_set_boundary(mhd_ctx* ctx, int outflow_mask);
 mhd_status mhd_get_boundary(mhd_ctx* ctx, int* outflow_mask);
 
@@ -197,11 +198,11 @@ mhd_status mhd_get_boundary(mhd_ctx* ctx, int* outflow_mask);
  * cell gets the conserved state of w and its three lower faces the field of
  * w, except the lower face along `axis` of the first upper ghost cell: that
  * is the interior's upper boundary face, which CT advances.  With nlayers
- * >= 2 (PLM, PLM_PRIM) or >= 3 (PPM) the interior sees an unbounded region
- * of the fixed state; fewer is MHD_EINVAL, as is 2 nlayers >= the cells
- * along `axis`, rho <= 0, P <= 0 or a non-finite value.  nlayers = 0
- * removes the side (the axis stays outflow).  One-box VL contexts without
- * a selector (else MHD_EUNSUPPORTED).  mhd_set_boundary with the axis's bit
+ * >= 2 (VL with PPM: >= 3) the interior sees an unbounded region of the
+ * fixed state; fewer is MHD_EINVAL, as is 2 nlayers >= the cells along
+ * `axis`, rho <= 0, P <= 0 or a non-finite value.  nlayers = 0 removes the
+ * side (the axis stays outflow).  One-box contexts (VL or CTU) without a
+ * selector (else MHD_EUNSUPPORTED).  mhd_set_boundary with the axis's bit
  * cleared removes the side too.  mhd_get_dirichlet reports nlayers. */
 mhd_status mhd_set_dirichlet(mhd_ctx* ctx, int axis, int nlayers, const double* w_lo, const double* w_hi);
 mhd_status mhd_get_dirichlet(mhd_ctx* ctx, int axis, int* nlayers);

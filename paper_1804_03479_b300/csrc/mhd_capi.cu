@@ -577,8 +577,11 @@ extern "C" mhd_status mhd_get_sweep_config(mhd_ctx* c, int* tile_len, int* block
 // pass per outflow axis and stage, a layer reset per Dirichlet axis
 static void count_launches(mhd_ctx* c)
 {
+    // (CTU: one stage-1 outer-face pass per outflow axis; the stage-2 ones
+    // are part of the corrections)
     int n = 12;
-    for (int d = 0; d < 3; d++) n += 2 * (c->bc >> d & 1) + (c->fix_nl[d] > 0);
+    const int per_axis = c->sch.integrator == MHD_VL ? 2 : 1;
+    for (int d = 0; d < 3; d++) n += per_axis * (c->bc >> d & 1) + (c->fix_nl[d] > 0);
     c->launches = n;
 }
 
@@ -595,11 +598,13 @@ extern "C" mhd_status mhd_set_boundary(mhd_ctx* c, int outflow_mask)
 {
     if (!c) return MHD_EINVAL;
     if (outflow_mask < 0 || outflow_mask > 7) return fail(c, MHD_EINVAL, "outflow_mask must be in [0, 7]");
-    if (outflow_mask && (c->sch.integrator != MHD_VL || c->nbox != 1 || c->sel))
-        return fail(c, MHD_EUNSUPPORTED, "outflow boundaries are built for one-box VL contexts without a selector");
+    if (outflow_mask && (c->nbox != 1 || c->sel))
+        return fail(c, MHD_EUNSUPPORTED, "outflow boundaries are built for one-box contexts without a selector");
     if (outflow_mask && !c->fout) {
+        // two stages of outer-face fluxes (CTU keeps the first while the
+        // corrections write the second; VL uses the first half only)
         const BoxDev& b = c->hbox[0];
-        CK(dalloc(c, &c->fout, (size_t)3 * 7 * cross_size(b.nx, b.ny, b.nz) * c->szr));
+        CK(dalloc(c, &c->fout, (size_t)2 * 3 * 7 * cross_size(b.nx, b.ny, b.nz) * c->szr));
     }
     c->bc = outflow_mask;
     c->hbox[0].bc = outflow_mask;
@@ -621,9 +626,11 @@ extern "C" mhd_status mhd_set_dirichlet(mhd_ctx* c, int axis, int nlayers, const
         return MHD_OK;
     }
     if (!w_lo || !w_hi) return fail(c, MHD_EINVAL, "null pointer");
-    if (c->sch.integrator != MHD_VL || c->nbox != 1 || c->sel)
-        return fail(c, MHD_EUNSUPPORTED, "Dirichlet sides are built for one-box VL contexts without a selector");
-    const int need = c->sch.recon == MHD_PPM ? 3 : 2;
+    if (c->nbox != 1 || c->sel)
+        return fail(c, MHD_EUNSUPPORTED, "Dirichlet sides are built for one-box contexts without a selector");
+    // layers the interior needs to see an unbounded fixed region: VL's
+    // half-step PPM reads one cell further
+    const int need = c->sch.integrator == MHD_VL && c->sch.recon == MHD_PPM ? 3 : 2;
     const BoxDev& g = c->hbox[0];
     const int nd = axis == 0 ? g.nx : (axis == 1 ? g.ny : g.nz);
     if (nlayers < need || 2 * nlayers + 1 > nd)

@@ -240,19 +240,43 @@ void run_step(mhd_ctx* c, bool device_dt)
         // steps 3-4: edge E at t^n, dt/2 update of face B and cell state
         k_emf<R><<<emf_grid<R>(c), EMF_THREADS, emf_smem_bytes<R>(), st>>>(g, F1, W, E);
         prof_mark(c, 5);
-        k_half<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2], Wh, c->sch.pfloor);
+        // outflow: stage-1 fluxes through the outer faces (the last cells'
+        // own traced states) into the first half of the outer-flux buffer;
+        // the corrections write the stage-2 ones into the second half
+        const int cs = c->bc ? cross_size(c->hbox[0].nx, c->hbox[0].ny, c->hbox[0].nz) : 0;
+        R* fo1 = (R*)c->fout;
+        R* fo2 = c->bc ? fo1 + (long long)21 * cs : nullptr;
+        for (int d = 0; d < 3; d++)
+            if (c->bc >> d & 1)
+                k_outer_flux_traced<R, SOLVER, TE><<<(cs + 127) / 128, 128, 0, st>>>(
+                    c->hbox[0], d, WP + (long long)d * 7 * n, WM + (long long)d * 7 * n, s.b[d], gam, n, fo1, cs);
+        if (c->bc)
+            k_half<R, TU, TE, true><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2], Wh,
+                                                                 c->sch.pfloor, fo1, cs);
+        else
+            k_half<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2], Wh,
+                                                           c->sch.pfloor);
         prof_mark(c, 6);
         // steps 5-6: transverse correction and corrector fluxes
         for (int d = 0; d < 3; d++) {
-            k_ctu_correct<R, SOLVER, TE><<<nb, CELL_THREADS, 0, st>>>(g, d, WM + (long long)d * 7 * n,
-                                                              WP + (long long)d * 7 * n, W, F1, Bh[d],
-                                                              F2 + (long long)d * 7 * n, c->dtc, gam);
+            if (c->bc)
+                k_ctu_correct<R, SOLVER, TE, true><<<nb, CELL_THREADS, 0, st>>>(
+                    g, d, WM + (long long)d * 7 * n, WP + (long long)d * 7 * n, W, F1, Bh[d],
+                    F2 + (long long)d * 7 * n, c->dtc, gam, fo1, cs, fo2);
+            else
+                k_ctu_correct<R, SOLVER, TE><<<nb, CELL_THREADS, 0, st>>>(g, d, WM + (long long)d * 7 * n,
+                                                                  WP + (long long)d * 7 * n, W, F1, Bh[d],
+                                                                  F2 + (long long)d * 7 * n, c->dtc, gam);
             prof_mark(c, 7 + d);
         }
         // steps 7-8
         k_emf<R><<<emf_grid<R>(c), EMF_THREADS, emf_smem_bytes<R>(), st>>>(g, F2, Wh, E);
         prof_mark(c, 10);
-        k_full<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F2, E, c->dtc);
+        if (c->bc)
+            k_full<R, TU, TE, true><<<nb, CELL_THREADS, 0, st>>>(g, s, F2, E, c->dtc, fo2, cs);
+        else
+            k_full<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F2, E, c->dtc);
+        fix_layers(c, s, st);
         prof_mark(c, 11);
     }
     if (c->prof_on && c->prof_steps < c->prof_cap) c->prof_steps++;

@@ -1034,6 +1034,44 @@ __global__ void k_fix_layers(BoxDev g, int d, int nl, FixedState lo, FixedState 
         if (m != d || p != nd - nl) s.b[m][c] = TE(f.b[m]);
 }
 
+// CTU stage 1: the outer face's states are the last cell's own traced upper
+// (WP) and lower (WM) states along d (sweep frame; the ghost beyond it is the
+// cell itself), with the normal field of the last face
+template <class R, int SOLVER, class TE>
+__global__ void k_outer_flux_traced(BoxDev g, int d, const R* __restrict__ WPd, const R* __restrict__ WMd,
+                                    const TE* __restrict__ bface, double gam, long long N, R* __restrict__ Fout, int cs)
+{
+    const int na = d == 0 ? g.ny : g.nx, nb = d == 2 ? g.ny : g.nz;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= na * nb) return;
+    const int a = q % na, b = q / na;
+    int i, j, k;
+    if (d == 0) { i = g.nx - 1; j = a; k = b; }
+    else if (d == 1) { i = a; j = g.ny - 1; k = b; }
+    else { i = a; j = b; k = g.nz - 1; }
+    const long long c = cell_of(g, i, j, k);
+    R wl[7], wr[7], f[7];
+#pragma unroll
+    for (int m = 0; m < 7; m++) {
+        wl[m] = WPd[(long long)m * N + c];
+        wr[m] = WMd[(long long)m * N + c];
+    }
+    riemann<SOLVER>(wl, wr, R(bface[c]), R(gam - 1.0), R(gam), f);
+    R* Fd = Fout + (long long)d * 7 * cs;
+#pragma unroll
+    for (int m = 0; m < 7; m++) Fd[(long long)m * cs + q] = f[m];
+}
+
+// index of cell (i, j, k) in the last layer along d (a + b * n_a, as in
+// k_outer_flux), and whether it is in that layer along an outflow axis
+__device__ __forceinline__ bool outer_cell(const BoxDev& g, int d, int i, int j, int k, int& q)
+{
+    const int p = d == 0 ? i : (d == 1 ? j : k);
+    const int nd = d == 0 ? g.nx : (d == 1 ? g.ny : g.nz);
+    q = d == 0 ? j + k * g.ny : (d == 1 ? i + k * g.nx : i + j * g.nx);
+    return (g.bc >> d & 1) && p == nd - 1;
+}
+
 // outflow: for each outflow axis along which (i, j, k) is the last cell, add
 // the outer-face flux minus the cell's own lower-face flux to the divergence
 // (the stencil saw the cell as its own upper neighbour)
@@ -1243,83 +1281,116 @@ __global__ void __launch_bounds__(CELL_THREADS) k_full(Boxes B, StateP<TU, TE> s
 // a9 + a6: CTU transverse correction of the traced states of the two cells
 // on each d-face, then the corrector Riemann solve with the half-step B_n.
 // ---------------------------------------------------------------------------
-template <class R, int SOLVER, class TE>
+// the traced state w (from WM or WP along d) of cell (si, sj, sk), as 8
+// global-frame conserved components with the cell-centre B_n of the cell,
+// minus dt/2 times the divergence of the other two axes' stage-1 fluxes
+// across the cell (along an outflow axis the last cell's upper face flux is
+// the outer one, Fo1), back to sweep-frame primitives
+template <class R, bool OUT>
+__device__ __forceinline__ void ctu_corrected(const BoxDev& g, int d, int si, int sj, int sk, long long sc,
+                                              const R* __restrict__ src, const R* __restrict__ W,
+                                              const R* __restrict__ F1, const R* __restrict__ Fo1, int cs,
+                                              long long N, R r, R gm1, R wf[7])
+{
+    const int t1 = d == 2 ? 0 : d + 1, t2 = d == 0 ? 2 : d - 1;
+    R w[7];
+#pragma unroll
+    for (int m = 0; m < 7; m++) w[m] = src[(long long)m * N + sc];
+    // global-frame conserved state with the cell-centre B_n of the cell
+    R v[3], bg[3];
+    v[d] = w[1]; v[t1] = w[2]; v[t2] = w[3];
+    bg[d] = W[(5 + d) * N + sc]; bg[t1] = w[5]; bg[t2] = w[6];
+    R q[8];
+    q[0] = w[0];
+    q[1] = w[0] * v[0]; q[2] = w[0] * v[1]; q[3] = w[0] * v[2];
+    q[4] = w[4] / gm1 + R(0.5) * w[0] * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2])
+           + R(0.5) * (bg[0] * bg[0] + bg[1] * bg[1] + bg[2] * bg[2]);
+    q[5] = bg[0]; q[6] = bg[1]; q[7] = bg[2];
+#pragma unroll
+    for (int mm = 0; mm < 2; mm++) {
+        const int e = mm == 0 ? t1 : t2;
+        const int e1 = e == 2 ? 0 : e + 1, e2 = e == 0 ? 2 : e - 1;
+        const R* Fe = F1 + (long long)e * 7 * N;
+        R df[7];
+        int qe;
+        if (OUT && outer_cell(g, e, si, sj, sk, qe)) {
+            const R* Fo = Fo1 + (long long)e * 7 * cs;
+#pragma unroll
+            for (int m = 0; m < 7; m++) df[m] = Fo[(long long)m * cs + qe] - Fe[(long long)m * N + sc];
+        } else {
+            long long sp = nbr(g, si, sj, sk, e, 1);
+#pragma unroll
+            for (int m = 0; m < 7; m++) df[m] = Fe[(long long)m * N + sp] - Fe[(long long)m * N + sc];
+        }
+        q[0] -= r * df[0];
+        q[1 + e] -= r * df[1];
+        q[1 + e1] -= r * df[2];
+        q[1 + e2] -= r * df[3];
+        q[4] -= r * df[4];
+        q[5 + e1] -= r * df[5];
+        q[5 + e2] -= r * df[6];
+    }
+    R rho = q[0];
+    const R irho = R(1) / rho;
+    R vx = q[1] * irho, vy = q[2] * irho, vz = q[3] * irho;
+    R p = gm1 * (q[4] - R(0.5) * rho * (vx * vx + vy * vy + vz * vz)
+                 - R(0.5) * (q[5] * q[5] + q[6] * q[6] + q[7] * q[7]));
+    R vg[3] = {vx, vy, vz};
+    wf[0] = rho;
+    wf[1] = vg[d];
+    wf[2] = vg[t1];
+    wf[3] = vg[t2];
+    wf[4] = p;
+    wf[5] = q[5 + t1];
+    wf[6] = q[5 + t2];
+}
+
+// Outflow instantiation (OUT): the transverse corrections of last cells take
+// the stage-1 outer fluxes Fo1, and the last cell along an outflow d also
+// writes the stage-2 flux of its outer face into Fo2: the Riemann flux of
+// its own corrected upper and lower states with the half-step B_n of the
+// last face.
+template <class R, int SOLVER, class TE, bool OUT = false>
 __global__ void __launch_bounds__(CELL_THREADS) k_ctu_correct(Boxes B, int d, const R* __restrict__ WM,
                                                               const R* __restrict__ WP, const R* __restrict__ W,
                                                               const R* __restrict__ F1, const TE* __restrict__ Bhd,
                                                               R* __restrict__ F2, const DtBox* __restrict__ dtb,
-                                                              double gam)
+                                                              double gam, const R* __restrict__ Fo1 = nullptr,
+                                                              int cs = 0, R* __restrict__ Fo2 = nullptr)
 {
     const long long N = B.N;
     for (long long v = blockIdx.x; v < B.nvblk; v += gridDim.x) {
     const int bi = box_of_vblk(B, v);
-    const BoxDev g = B.b[bi];
+    BoxDev g = B.b[bi];
+    if (!OUT) g.bc = 0;     // periodic instantiation: the wrap is compiled in
     const long long lc = (v - g.vblk0) * CELL_THREADS + threadIdx.x;
     if (lc >= g.n) continue;
-    const int t1 = d == 2 ? 0 : d + 1, t2 = d == 0 ? 2 : d - 1;
     const R gm1 = R(gam - 1.0), gr = R(gam);
     const R r = DtOf<R>::hdtdx(dtb[bi]);
     int i, j, k;
     coords(g, lc, i, j, k);
     const long long c = g.off + lc;
     R wf[2][7];
-#pragma unroll
-    for (int side = 0; side < 2; side++) {
+    {
         int si = i, sj = j, sk = k;
-        if (side == 0) {
-            if (d == 0) si = bidx(i - 1, g.nx, g.bc & 1); else if (d == 1) sj = bidx(j - 1, g.ny, g.bc & 2);
-            else sk = bidx(k - 1, g.nz, g.bc & 4);
-        }
-        long long sc = cell_of(g, si, sj, sk);
-        const R* src = side == 0 ? WP : WM;
-        R w[7];
-#pragma unroll
-        for (int m = 0; m < 7; m++) w[m] = src[(long long)m * N + sc];
-        // global-frame conserved state with the cell-centre B_n of the cell
-        R v[3], bg[3];
-        v[d] = w[1]; v[t1] = w[2]; v[t2] = w[3];
-        bg[d] = W[(5 + d) * N + sc]; bg[t1] = w[5]; bg[t2] = w[6];
-        R q[8];
-        q[0] = w[0];
-        q[1] = w[0] * v[0]; q[2] = w[0] * v[1]; q[3] = w[0] * v[2];
-        q[4] = w[4] / gm1 + R(0.5) * w[0] * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2])
-               + R(0.5) * (bg[0] * bg[0] + bg[1] * bg[1] + bg[2] * bg[2]);
-        q[5] = bg[0]; q[6] = bg[1]; q[7] = bg[2];
-#pragma unroll
-        for (int mm = 0; mm < 2; mm++) {
-            const int e = mm == 0 ? t1 : t2;
-            const int e1 = e == 2 ? 0 : e + 1, e2 = e == 0 ? 2 : e - 1;
-            const R* Fe = F1 + (long long)e * 7 * N;
-            long long sp = nbr(g, si, sj, sk, e, 1);
-            R df[7];
-#pragma unroll
-            for (int m = 0; m < 7; m++) df[m] = Fe[(long long)m * N + sp] - Fe[(long long)m * N + sc];
-            q[0] -= r * df[0];
-            q[1 + e] -= r * df[1];
-            q[1 + e1] -= r * df[2];
-            q[1 + e2] -= r * df[3];
-            q[4] -= r * df[4];
-            q[5 + e1] -= r * df[5];
-            q[5 + e2] -= r * df[6];
-        }
-        R rho = q[0];
-        const R irho = R(1) / rho;
-        R vx = q[1] * irho, vy = q[2] * irho, vz = q[3] * irho;
-        R p = gm1 * (q[4] - R(0.5) * rho * (vx * vx + vy * vy + vz * vz)
-                     - R(0.5) * (q[5] * q[5] + q[6] * q[6] + q[7] * q[7]));
-        R vg[3] = {vx, vy, vz};
-        wf[side][0] = rho;
-        wf[side][1] = vg[d];
-        wf[side][2] = vg[t1];
-        wf[side][3] = vg[t2];
-        wf[side][4] = p;
-        wf[side][5] = q[5 + t1];
-        wf[side][6] = q[5 + t2];
+        if (d == 0) si = bidx(i - 1, g.nx, g.bc & 1); else if (d == 1) sj = bidx(j - 1, g.ny, g.bc & 2);
+        else sk = bidx(k - 1, g.nz, g.bc & 4);
+        ctu_corrected<R, OUT>(g, d, si, sj, sk, cell_of(g, si, sj, sk), WP, W, F1, Fo1, cs, N, r, gm1, wf[0]);
     }
+    ctu_corrected<R, OUT>(g, d, i, j, k, c, WM, W, F1, Fo1, cs, N, r, gm1, wf[1]);
     R f[7];
     riemann<SOLVER>(wf[0], wf[1], R(Bhd[c]), gm1, gr, f);
 #pragma unroll
     for (int m = 0; m < 7; m++) F2[(long long)m * N + c] = f[m];
+    int qd;
+    if (OUT && outer_cell(g, d, i, j, k, qd)) {
+        R wu[7], fo[7];
+        ctu_corrected<R, OUT>(g, d, i, j, k, c, WP, W, F1, Fo1, cs, N, r, gm1, wu);
+        riemann<SOLVER>(wu, wf[1], R(Bhd[c]), gm1, gr, fo);
+        R* Fo = Fo2 + (long long)d * 7 * cs;
+#pragma unroll
+        for (int m = 0; m < 7; m++) Fo[(long long)m * cs + qd] = fo[m];
+    }
     }
 }
 

@@ -1,10 +1,11 @@
 """Dirichlet sides on the GPU (mhd_set_dirichlet: fixed-state ghost layers
 inside the box, put back after every step) against the oracle's: FP64
 parity at the 1e-12 bar along every axis and for each reconstruction and
-solver; the interior independent of the layer count beyond the minimum (the
-GPU with the fewest layers against the oracle with six); the Table 1 RJ2a
-tube of the paper's setup (box length 1, PPM, Roe, FP64) advanced on the
-GPU alone; the FP32 form's L1 against the FP64 oracle; the refusals."""
+solver, VL and CTU; the interior independent of the layer count beyond the
+minimum (the GPU with the fewest layers against the oracle with six); the
+Table 1 RJ2a tube of the paper's setup (box length 1, CTU, PPM, Roe, FP64)
+advanced on the GPU alone; the FP32 form's L1 against the FP64 oracle; the
+refusals."""
 import math
 
 import numpy as np
@@ -93,7 +94,8 @@ def parity(M, U, B, dx, scheme, axis, nl, w_lo, w_hi, nsteps, sweeps=None, tol=1
 
 @pytest.mark.parametrize("axis", [0, 1, 2])
 @pytest.mark.parametrize("scheme,nl", [(("vl", "plm", "roe"), 2), (("vl", "ppm", "hlld"), 3),
-                                       (("vl", "plm_prim", "hlle"), 2), (("vl", "ppm", "roe"), 4)])
+                                       (("vl", "plm_prim", "hlle"), 2), (("vl", "ppm", "roe"), 4),
+                                       (("ctu", "ppm", "roe"), 2), (("ctu", "plm", "hlld"), 3)])
 def test_dirichlet_fp64_parity(M, axis, scheme, nl):
     U, B, dx = x_problem(40, nl, W_IN, W_BOX)
     U, B, lo, hi = relabel(U, B, W_IN, W_BOX, axis)
@@ -106,7 +108,8 @@ def test_dirichlet_fp64_parity_sweep_forms(M, sweeps):
     parity(M, U, B, dx, ("vl", "ppm", "roe"), 0, 3, W_IN, W_BOX, 3, sweeps=sweeps)
 
 
-@pytest.mark.parametrize("scheme,nl", [(("vl", "plm", "roe"), 2), (("vl", "ppm", "hlld"), 3)])
+@pytest.mark.parametrize("scheme,nl", [(("vl", "plm", "roe"), 2), (("vl", "ppm", "hlld"), 3),
+                                       (("ctu", "ppm", "roe"), 2)])
 def test_fewest_layers_match_six(M, scheme, nl):
     """the GPU with the minimum layer count, advanced on its own (its own
     CFL dt, device graph), against the oracle with six layers: the interior
@@ -150,16 +153,18 @@ def rj2a_line(n, nl):
     return I.conserved(f[0], f[1], f[2], f[3], f[4], Bf, GAM), np.ascontiguousarray(Bf), dx, wl, wr
 
 
-def test_rj2a_paper_setup_on_the_gpu(M):
+@pytest.mark.parametrize("integ", ["ctu", "vl"])
+def test_rj2a_paper_setup_on_the_gpu(M, integ):
     """RJ2a (Table 1) in a box of length 1 with Dirichlet ends, PPM + Roe in
-    FP64, advanced by the GPU alone to t = 0.2 (the fast waves reach the ends
-    at about t = 0.2): against the oracle's run at every 40th step, and the
-    end states kept in the ghost layers"""
+    FP64 (the paper's accuracy tests use CTU), advanced by the GPU alone to
+    t = 0.2 (the fast waves reach the ends at about t = 0.2): against the
+    oracle's run at every 40th step, and the end states kept in the ghost
+    layers"""
     n, nl = 192, 3
     U, B, dx, wl, wr = rj2a_line(n, nl)
     Uo, Bo = U.copy(), B.copy()
     orc.fix_layers(Uo, Bo, GAM, 0, nl, wl, wr)
-    s = M.Solver(U.shape[1:], dx, GAM, "vl", "ppm", "roe", "fp64", 0.3)
+    s = M.Solver(U.shape[1:], dx, GAM, integ, "ppm", "roe", "fp64", 0.3)
     try:
         s.set_dirichlet(0, nl, wl, wr)
         s.set_state(U, B)
@@ -169,7 +174,7 @@ def test_rj2a_paper_setup_on_the_gpu(M):
             do = orc.cfl_dt(Uo, Bo, dx, GAM, 0.3, bc=1)
             assert abs(min(do, 0.2 - t) - dt) <= 1e-12 * dt
             s.step(dt)
-            orc.step_dirichlet(Uo, Bo, dx, GAM, dt, "vl", "ppm", "roe", 0, nl, wl, wr)
+            orc.step_dirichlet(Uo, Bo, dx, GAM, dt, integ, "ppm", "roe", 0, nl, wl, wr)
             t += dt
             it += 1
             if it % 40 == 0:
@@ -229,9 +234,18 @@ def test_dirichlet_refusals(M):
         assert s.dirichlet(0) == 0 and s.boundary() == 0
     finally:
         s.free()
-    s = M.Solver(U.shape[1:], dx, GAM, "ctu", "plm", "roe", "fp64", 0.3)
+    # CTU needs two layers whatever the reconstruction; batches are refused
+    s = M.Solver(U.shape[1:], dx, GAM, "ctu", "ppm", "roe", "fp64", 0.3)
+    try:
+        s.set_dirichlet(0, 2, W_IN, W_BOX)
+        assert s.dirichlet(0) == 2
+        with pytest.raises(RuntimeError):
+            s.set_dirichlet(0, 1, W_IN, W_BOX)
+    finally:
+        s.free()
+    s = M.Solver(None, None, GAM, "vl", "plm", "roe", "fp64", 0.3, shapes=[(16, 8, 8), (16, 8, 8)], dxs=[0.1, 0.1])
     try:
         with pytest.raises(RuntimeError):
-            s.set_dirichlet(0, 3, W_IN, W_BOX)
+            s.set_dirichlet(0, 2, W_IN, W_BOX)
     finally:
         s.free()
