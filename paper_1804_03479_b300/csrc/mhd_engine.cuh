@@ -147,6 +147,20 @@ void fix_layers(mhd_ctx* c, const StateP<TU, TE>& s, cudaStream_t st)
     }
 }
 
+// CTU steps 5-6 along axis D (periodic or outflow instantiation)
+template <class R, int SOLVER, class TE, int D>
+void ctu_correct_axis(mhd_ctx* c, const Boxes& g, const R* WM, const R* WP, const R* W, const R* F1, const TE* BhD,
+                      R* F2, double gam, const R* fo1, int cs, R* fo2, cudaStream_t st)
+{
+    const long long o = (long long)D * 7 * g.N;
+    if (c->bc)
+        k_ctu_correct<R, SOLVER, TE, D, true><<<c->cell_grid, CELL_THREADS, 0, st>>>(
+            g, WM + o, WP + o, W, F1, BhD, F2 + o, c->dtc, gam, fo1, cs, fo2);
+    else
+        k_ctu_correct<R, SOLVER, TE, D><<<c->cell_grid, CELL_THREADS, 0, st>>>(g, WM + o, WP + o, W, F1, BhD, F2 + o,
+                                                                           c->dtc, gam);
+}
+
 template <class R, class TU, class TE, int INTEG, int RECON, int SOLVER>
 void run_step(mhd_ctx* c, bool device_dt)
 {
@@ -181,8 +195,8 @@ void run_step(mhd_ctx* c, bool device_dt)
                 k_xwarp<R, RECON, SOLVER, 0, TE><<<xrow_grid(c), PENCIL_THREADS, 0, st>>>(
                     g, W, s.b[d], F1, gam, XW<RECON, 0>::slot);
             else if (c->pencil_mask >> d & 1)
-                k_pencil<R, RECON, SOLVER, 0, TE><<<pencil_grid(c, d), PENCIL_THREADS, 0, st>>>(
-                    g, d, W, s.b[d], F1 + (long long)d * 7 * n, gam);
+                launch_pencil<R, RECON, SOLVER, 0, TE>(d, pencil_grid(c, d), st, g, W, s.b[d],
+                                                       F1 + (long long)d * 7 * n, gam);
             else
                 k_sweep<R, RECON, SOLVER, 0, TE><<<sweep_grid(c, d), SWEEP_THREADS, 0, st>>>(
                     g, d, W, s.b[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam);
@@ -208,8 +222,8 @@ void run_step(mhd_ctx* c, bool device_dt)
                 k_xwarp<R, RECON, SOLVER, 1, TE><<<xrow_grid(c), PENCIL_THREADS, 0, st>>>(
                     g, Wh, Bh[d], F1, gam, XW<RECON, 1>::slot);
             else if (c->pencil_mask >> d & 1)
-                k_pencil<R, RECON, SOLVER, 1, TE><<<pencil_grid(c, d), PENCIL_THREADS, 0, st>>>(
-                    g, d, Wh, Bh[d], F1 + (long long)d * 7 * n, gam);
+                launch_pencil<R, RECON, SOLVER, 1, TE>(d, pencil_grid(c, d), st, g, Wh, Bh[d],
+                                                       F1 + (long long)d * 7 * n, gam);
             else
                 k_sweep<R, RECON, SOLVER, 1, TE><<<sweep_grid(c, d), SWEEP_THREADS, smem, st>>>(
                     g, d, Wh, Bh[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam);
@@ -258,17 +272,12 @@ void run_step(mhd_ctx* c, bool device_dt)
                                                            c->sch.pfloor);
         prof_mark(c, 6);
         // steps 5-6: transverse correction and corrector fluxes
-        for (int d = 0; d < 3; d++) {
-            if (c->bc)
-                k_ctu_correct<R, SOLVER, TE, true><<<nb, CELL_THREADS, 0, st>>>(
-                    g, d, WM + (long long)d * 7 * n, WP + (long long)d * 7 * n, W, F1, Bh[d],
-                    F2 + (long long)d * 7 * n, c->dtc, gam, fo1, cs, fo2);
-            else
-                k_ctu_correct<R, SOLVER, TE><<<nb, CELL_THREADS, 0, st>>>(g, d, WM + (long long)d * 7 * n,
-                                                                  WP + (long long)d * 7 * n, W, F1, Bh[d],
-                                                                  F2 + (long long)d * 7 * n, c->dtc, gam);
-            prof_mark(c, 7 + d);
-        }
+        ctu_correct_axis<R, SOLVER, TE, 0>(c, g, WM, WP, W, F1, Bh[0], F2, gam, fo1, cs, fo2, st);
+        prof_mark(c, 7);
+        ctu_correct_axis<R, SOLVER, TE, 1>(c, g, WM, WP, W, F1, Bh[1], F2, gam, fo1, cs, fo2, st);
+        prof_mark(c, 8);
+        ctu_correct_axis<R, SOLVER, TE, 2>(c, g, WM, WP, W, F1, Bh[2], F2, gam, fo1, cs, fo2, st);
+        prof_mark(c, 9);
         // steps 7-8
         k_emf<R><<<emf_grid<R>(c), EMF_THREADS, emf_smem_bytes<R>(), st>>>(g, F2, Wh, E);
         prof_mark(c, 10);

@@ -550,12 +550,15 @@ __device__ __forceinline__ void copy7(R d[7], const R s[7])
 
 // seg_list / seg_count: only the segments of a list (the learned selector's),
 // the grid covering every segment of the axis
-template <class R, int RECON, int SOLVER, int MODE, class TE>
-__global__ void __launch_bounds__(PENCIL_THREADS) k_pencil(Boxes B, int d, const R* __restrict__ W,
+// The sweep axis D is a template parameter: with a run-time axis the
+// compiler kept the cell windows in local memory (a 240-byte stack frame).
+template <class R, int RECON, int SOLVER, int MODE, class TE, int D>
+__global__ void __launch_bounds__(PENCIL_THREADS) k_pencil(Boxes B, const R* __restrict__ W,
                                                            const TE* __restrict__ Bd, R* __restrict__ F, double gam,
                                                            const int* __restrict__ seg_list = nullptr,
                                                            const int* __restrict__ seg_count = nullptr)
 {
+    constexpr int d = D;
     long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (seg_list) {
         if (gt >= *seg_count) return;
@@ -651,6 +654,19 @@ __global__ void __launch_bounds__(PENCIL_THREADS) k_pencil(Boxes B, int d, const
             copy7(s1, s2);
         }
     }
+}
+
+// launch the pencil sweep along a run-time axis d
+template <class R, int RECON, int SOLVER, int MODE, class TE>
+inline void launch_pencil(int d, int grid, cudaStream_t st, const Boxes& g, const R* W, const TE* Bd, R* F,
+                          double gam, const int* seg_list = nullptr, const int* seg_count = nullptr)
+{
+    if (d == 0)
+        k_pencil<R, RECON, SOLVER, MODE, TE, 0><<<grid, PENCIL_THREADS, 0, st>>>(g, W, Bd, F, gam, seg_list, seg_count);
+    else if (d == 1)
+        k_pencil<R, RECON, SOLVER, MODE, TE, 1><<<grid, PENCIL_THREADS, 0, st>>>(g, W, Bd, F, gam, seg_list, seg_count);
+    else
+        k_pencil<R, RECON, SOLVER, MODE, TE, 2><<<grid, PENCIL_THREADS, 0, st>>>(g, W, Bd, F, gam, seg_list, seg_count);
 }
 
 // ---------------------------------------------------------------------------
@@ -1286,8 +1302,8 @@ __global__ void __launch_bounds__(CELL_THREADS) k_full(Boxes B, StateP<TU, TE> s
 // minus dt/2 times the divergence of the other two axes' stage-1 fluxes
 // across the cell (along an outflow axis the last cell's upper face flux is
 // the outer one, Fo1), back to sweep-frame primitives
-template <class R, bool OUT>
-__device__ __forceinline__ void ctu_corrected(const BoxDev& g, int d, int si, int sj, int sk, long long sc,
+template <class R, bool OUT, int d>
+__device__ __forceinline__ void ctu_corrected(const BoxDev& g, int si, int sj, int sk, long long sc,
                                               const R* __restrict__ src, const R* __restrict__ W,
                                               const R* __restrict__ F1, const R* __restrict__ Fo1, int cs,
                                               long long N, R r, R gm1, R wf[7])
@@ -1349,9 +1365,10 @@ __device__ __forceinline__ void ctu_corrected(const BoxDev& g, int d, int si, in
 // the stage-1 outer fluxes Fo1, and the last cell along an outflow d also
 // writes the stage-2 flux of its outer face into Fo2: the Riemann flux of
 // its own corrected upper and lower states with the half-step B_n of the
-// last face.
-template <class R, int SOLVER, class TE, bool OUT = false>
-__global__ void __launch_bounds__(CELL_THREADS) k_ctu_correct(Boxes B, int d, const R* __restrict__ WM,
+// last face.  The axis d is a template parameter: every frame rotation is
+// then static, and the per-state arrays stay in registers.
+template <class R, int SOLVER, class TE, int d, bool OUT = false>
+__global__ void __launch_bounds__(CELL_THREADS) k_ctu_correct(Boxes B, const R* __restrict__ WM,
                                                               const R* __restrict__ WP, const R* __restrict__ W,
                                                               const R* __restrict__ F1, const TE* __restrict__ Bhd,
                                                               R* __restrict__ F2, const DtBox* __restrict__ dtb,
@@ -1375,9 +1392,9 @@ __global__ void __launch_bounds__(CELL_THREADS) k_ctu_correct(Boxes B, int d, co
         int si = i, sj = j, sk = k;
         if (d == 0) si = bidx(i - 1, g.nx, g.bc & 1); else if (d == 1) sj = bidx(j - 1, g.ny, g.bc & 2);
         else sk = bidx(k - 1, g.nz, g.bc & 4);
-        ctu_corrected<R, OUT>(g, d, si, sj, sk, cell_of(g, si, sj, sk), WP, W, F1, Fo1, cs, N, r, gm1, wf[0]);
+        ctu_corrected<R, OUT, d>(g, si, sj, sk, cell_of(g, si, sj, sk), WP, W, F1, Fo1, cs, N, r, gm1, wf[0]);
     }
-    ctu_corrected<R, OUT>(g, d, i, j, k, c, WM, W, F1, Fo1, cs, N, r, gm1, wf[1]);
+    ctu_corrected<R, OUT, d>(g, i, j, k, c, WM, W, F1, Fo1, cs, N, r, gm1, wf[1]);
     R f[7];
     riemann<SOLVER>(wf[0], wf[1], R(Bhd[c]), gm1, gr, f);
 #pragma unroll
@@ -1385,7 +1402,7 @@ __global__ void __launch_bounds__(CELL_THREADS) k_ctu_correct(Boxes B, int d, co
     int qd;
     if (OUT && outer_cell(g, d, i, j, k, qd)) {
         R wu[7], fo[7];
-        ctu_corrected<R, OUT>(g, d, i, j, k, c, WP, W, F1, Fo1, cs, N, r, gm1, wu);
+        ctu_corrected<R, OUT, d>(g, i, j, k, c, WP, W, F1, Fo1, cs, N, r, gm1, wu);
         riemann<SOLVER>(wu, wf[1], R(Bhd[c]), gm1, gr, fo);
         R* Fo = Fo2 + (long long)d * 7 * cs;
 #pragma unroll

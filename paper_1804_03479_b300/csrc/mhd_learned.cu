@@ -337,10 +337,12 @@ static void run_step_learned(mhd_ctx* c, bool device_dt)
             k_xwarp<R, PPM, HLLD, 0, float><<<xwarp_grid(c, 0), PENCIL_THREADS, 0, st>>>(
                 g, W, s.b[0], F1, gam, 0, c->sel_list[1], c->sel_cnt + 1);
         } else if (c->pencil_mask >> d & 1) {
-            k_pencil<R, PLM_PRIM, HLLE, 0, float><<<pencil_grid(c, d), PENCIL_THREADS, 0, st>>>(
-                g, d, W, s.b[d], F1 + (long long)d * 7 * n, gam, c->sel_list[2 * d], c->sel_cnt + 2 * d);
-            k_pencil<R, PPM, HLLD, 0, float><<<pencil_grid(c, d), PENCIL_THREADS, 0, st>>>(
-                g, d, W, s.b[d], F1 + (long long)d * 7 * n, gam, c->sel_list[2 * d + 1], c->sel_cnt + 2 * d + 1);
+            launch_pencil<R, PLM_PRIM, HLLE, 0, float>(d, pencil_grid(c, d), st, g, W, s.b[d],
+                                                          F1 + (long long)d * 7 * n, gam, c->sel_list[2 * d],
+                                                          c->sel_cnt + 2 * d);
+            launch_pencil<R, PPM, HLLD, 0, float>(d, pencil_grid(c, d), st, g, W, s.b[d],
+                                                          F1 + (long long)d * 7 * n, gam, c->sel_list[2 * d + 1],
+                                                          c->sel_cnt + 2 * d + 1);
         } else {
             k_sweep<R, PLM_PRIM, HLLE, 0, float><<<sweep_grid(c, d), SWEEP_THREADS, 0, st>>>(
                 g, d, W, s.b[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam, c->sel_list[2 * d],
@@ -363,10 +365,12 @@ static void run_step_learned(mhd_ctx* c, bool device_dt)
             k_xwarp<R, PPM, HLLD, 1, float><<<xwarp_grid(c, 2), PENCIL_THREADS, 0, st>>>(
                 g, Wh, Bh[0], F1, gam, 2, c->sel_list[7], c->sel_cnt + 7);
         } else if (c->pencil_mask >> d & 1) {
-            k_pencil<R, PLM_PRIM, HLLE, 1, float><<<pencil_grid(c, d), PENCIL_THREADS, 0, st>>>(
-                g, d, Wh, Bh[d], F1 + (long long)d * 7 * n, gam, c->sel_list[2 * d], c->sel_cnt + 2 * d);
-            k_pencil<R, PPM, HLLD, 1, float><<<pencil_grid(c, d), PENCIL_THREADS, 0, st>>>(
-                g, d, Wh, Bh[d], F1 + (long long)d * 7 * n, gam, c->sel_list[2 * d + 1], c->sel_cnt + 2 * d + 1);
+            launch_pencil<R, PLM_PRIM, HLLE, 1, float>(d, pencil_grid(c, d), st, g, Wh, Bh[d],
+                                                          F1 + (long long)d * 7 * n, gam, c->sel_list[2 * d],
+                                                          c->sel_cnt + 2 * d);
+            launch_pencil<R, PPM, HLLD, 1, float>(d, pencil_grid(c, d), st, g, Wh, Bh[d],
+                                                          F1 + (long long)d * 7 * n, gam, c->sel_list[2 * d + 1],
+                                                          c->sel_cnt + 2 * d + 1);
         } else {
             k_sweep<R, PLM_PRIM, HLLE, 1, float><<<sweep_grid(c, d), SWEEP_THREADS,
                                                    sweep_smem_bytes<R>(PLM_PRIM, g.tl), st>>>(
