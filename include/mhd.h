@@ -207,16 +207,16 @@ mhd_status mhd_get_boundary(mhd_ctx* ctx, int* outflow_mask);
 mhd_status mhd_set_dirichlet(mhd_ctx* ctx, int axis, int nlayers, const double* w_lo, const double* w_hi);
 mhd_status mhd_get_dirichlet(mhd_ctx* ctx, int axis, int* nlayers);
 
-/* Pencil sweeps (VL integrator): on every axis d with bit d of pencil_mask
- * set, the predictor and corrector face sweeps keep the cells around each
- * face in registers (no shared memory): along y and z one thread walks a
- * segment of pencil_len consecutive faces of a grid line; along x the 32
- * lanes of a warp hold 32 consecutive cells of a row and exchange
- * neighbour states by shuffles (27 to 31 faces per warp).  The results are
- * those of the tile sweeps (the same arithmetic per face).  pencil_mask in
- * [0, 7] (0: tiles everywhere; default 7, with pencil_len 32, for VL
- * contexts, 0 for CTU), pencil_len in [1, 1024], else MHD_EINVAL; a
- * non-zero mask with the CTU integrator: MHD_EUNSUPPORTED. */
+/* Pencil sweeps: on every axis d with bit d of pencil_mask set, the face
+ * sweeps (VL predictor and corrector; CTU tracing sweeps) keep the cells
+ * around each face in registers (no shared memory): one thread walks a
+ * segment of pencil_len consecutive faces of a grid line.  For VL the x
+ * axis runs by warps instead: the 32 lanes of a warp hold 32 consecutive
+ * cells of a row and exchange neighbour states by shuffles (27 to 31 faces
+ * per warp).  The results are those of the tile sweeps (the same
+ * arithmetic per face).  pencil_mask in [0, 7] (0: tiles everywhere;
+ * default 7 for VL contexts, 6 (y and z) for CTU, with pencil_len 32),
+ * pencil_len in [1, 1024], else MHD_EINVAL. */
 mhd_status mhd_set_sweep_pencils(mhd_ctx* ctx, int pencil_mask, int pencil_len);
 mhd_status mhd_get_sweep_pencils(mhd_ctx* ctx, int* pencil_mask, int* pencil_len);
 

@@ -166,7 +166,7 @@ static mhd_status init_common(int nbox, const mhd_grid* grids, double gamma, con
     c->sweep_bps = 4;
     // VL: register sweeps on every axis (pencils along y and z, warps along x;
     // the autotuner may change it)
-    c->pencil_mask = scheme->integrator == MHD_VL ? 7 : 0;
+    c->pencil_mask = scheme->integrator == MHD_VL ? 7 : 6;
     c->pencil_len = 32;
     c->cell_grid = (int)(vb < 16LL * c->nsm ? vb : 16LL * c->nsm);
     if (c->cell_grid < 1) c->cell_grid = 1;
@@ -684,8 +684,6 @@ extern "C" mhd_status mhd_set_sweep_pencils(mhd_ctx* c, int pencil_mask, int pen
     if (!c) return MHD_EINVAL;
     if (pencil_mask < 0 || pencil_mask > 7 || pencil_len < 1 || pencil_len > 1024)
         return fail(c, MHD_EINVAL, "pencil_mask must be in [0, 7] and pencil_len in [1, 1024]");
-    if (pencil_mask && c->sch.integrator != MHD_VL)
-        return fail(c, MHD_EUNSUPPORTED, "pencil sweeps are built for the VL integrator only");
     c->pencil_mask = pencil_mask;
     c->pencil_len = pencil_len;
     CK(layout_tiles(c, c->B.tl));
@@ -760,8 +758,9 @@ extern "C" mhd_status mhd_autotune(mhd_ctx* c, int reps, int* tile_len, int* blo
             st = trial(&ms);
             if (st == MHD_OK && ms < best) { best = ms; btl = tls[i]; bbps = bpss[j]; }
         }
-    // VL: pencils on all axes or on y and z only (x keeps the best tiles), per segment length
-    if (c->sch.integrator == MHD_VL) {
+    // pencils on all axes or on y and z only (x keeps the best tiles), per
+    // segment length (VL: x by warps; CTU: x by pencil threads)
+    {
         const int masks[2] = {7, 6};
         const int lens[3] = {8, 16, 32};
         c->sweep_bps = bbps;

@@ -244,11 +244,17 @@ void run_step(mhd_ctx* c, bool device_dt)
     } else {
         R* WM = (R*)c->WM;
         R* WP = (R*)c->WP;
-        // CTU steps 1-2: traced states (+ source terms) and their fluxes
+        // CTU steps 1-2: traced states (+ source terms) and their fluxes, by
+        // pencils on the axes of the pencil mask, else by tiles
         for (int d = 0; d < 3; d++) {
-            k_sweep<R, RECON, SOLVER, 2, TE><<<sweep_grid(c, d), SWEEP_THREADS, smem, st>>>(
-                g, d, W, s.b[d], F1 + (long long)d * 7 * n, WM + (long long)d * 7 * n, WP + (long long)d * 7 * n,
-                c->dtc, gam);
+            if (c->pencil_mask >> d & 1)
+                launch_pencil<R, RECON, SOLVER, 2, TE>(d, pencil_grid(c, d), st, g, W, s.b[d],
+                                                       F1 + (long long)d * 7 * n, gam, nullptr, nullptr,
+                                                       WM + (long long)d * 7 * n, WP + (long long)d * 7 * n, c->dtc);
+            else
+                k_sweep<R, RECON, SOLVER, 2, TE><<<sweep_grid(c, d), SWEEP_THREADS, smem, st>>>(
+                    g, d, W, s.b[d], F1 + (long long)d * 7 * n, WM + (long long)d * 7 * n,
+                    WP + (long long)d * 7 * n, c->dtc, gam);
             prof_mark(c, 2 + d);
         }
         // steps 3-4: edge E at t^n, dt/2 update of face B and cell state

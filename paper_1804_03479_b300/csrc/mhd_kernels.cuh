@@ -552,11 +552,17 @@ __device__ __forceinline__ void copy7(R d[7], const R s[7])
 // the grid covering every segment of the axis
 // The sweep axis D is a template parameter: with a run-time axis the
 // compiler kept the cell windows in local memory (a 240-byte stack frame).
+// MODE 2 (CTU step 1-2): the states are traced to t + dt/2 (recon_cell with
+// tracing, plus the dB_n/dn source terms of the 1-D sweep, as in k_sweep);
+// each owned cell's lower and upper traced states go to WMg / WPg, and the
+// face flux uses the previous cell's upper and this cell's lower state.
 template <class R, int RECON, int SOLVER, int MODE, class TE, int D>
 __global__ void __launch_bounds__(PENCIL_THREADS) k_pencil(Boxes B, const R* __restrict__ W,
                                                            const TE* __restrict__ Bd, R* __restrict__ F, double gam,
                                                            const int* __restrict__ seg_list = nullptr,
-                                                           const int* __restrict__ seg_count = nullptr)
+                                                           const int* __restrict__ seg_count = nullptr,
+                                                           R* __restrict__ WMg = nullptr, R* __restrict__ WPg = nullptr,
+                                                           const DtBox* __restrict__ dtb = nullptr)
 {
     constexpr int d = D;
     long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -565,7 +571,8 @@ __global__ void __launch_bounds__(PENCIL_THREADS) k_pencil(Boxes B, const R* __r
         gt = seg_list[gt];
     }
     if (gt >= B.npth[d]) return;
-    const BoxDev g = B.b[box_of_pth(B, d, gt)];
+    const int bi = box_of_pth(B, d, gt);
+    const BoxDev g = B.b[bi];
     int na, nb, ns;
     pencil_dims(g.nx, g.ny, g.nz, d, B.pl, na, nb, ns);
     long long t = gt - g.pth0[d];
@@ -582,6 +589,22 @@ __global__ void __launch_bounds__(PENCIL_THREADS) k_pencil(Boxes B, const R* __r
     const int i1 = i0 + B.pl < p.n ? i0 + B.pl : p.n;
     const long long N = B.N;
     const R gr = R(gam), gm1 = R(gam - 1.0);
+    constexpr bool TR = MODE == 2;
+    const R dtdx = TR ? DtOf<R>::dtdx(dtb[bi]) : R(0);
+    const R hdt = TR ? DtOf<R>::hdt(dtb[bi]) : R(0);
+    // MODE 2: the dB_n/dn source terms of cell i (state w0, cell-centre B_n
+    // bn) over dt/2, added to both traced states
+    auto trace_src = [&](int i, const R w0[7], R bn, R wm[7], R wp[7]) {
+        const long long c0 = pcell(p, i), c1 = pcell(p, i + 1);
+        R dbn = sizeof(R) == 8 ? R((double)(Bd[c1] - Bd[c0]) / g.dx) : R(Bd[c1] - Bd[c0]) * R(g.inv_dx);
+        R vb = w0[1] * bn + w0[2] * w0[5] + w0[3] * w0[6];
+        R src[7] = {R(0), bn / w0[0], w0[5] / w0[0], w0[6] / w0[0], -gm1 * vb, w0[2], w0[3]};
+#pragma unroll
+        for (int m = 0; m < 7; m++) {
+            wm[m] = wm[m] + hdt * src[m] * dbn;
+            wp[m] = wp[m] + hdt * src[m] * dbn;
+        }
+    };
     R f[7];
     if (MODE == 0) {
         // first-order states: the face i sees cells i-1 and i
@@ -598,16 +621,28 @@ __global__ void __launch_bounds__(PENCIL_THREADS) k_pencil(Boxes B, const R* __r
     } else if (RECON != PPM) {
         // PLM: cells i-1, i, i+1 in registers; wpp the "+" state of cell i-1
         R wa[7], wb[7], wc[7], bna, bnb, bnc, wpp[7], wm[7], wp[7], dum[7];
-        load_rot(W, N, pcell(p, i0 - 2), d, wa, bna);
-        load_rot(W, N, pcell(p, i0 - 1), d, wb, bnb);
-        load_rot(W, N, pcell(p, i0), d, wc, bnc);
-        recon_cell<RECON, false>(wa, wb, wc, bnb, gr, dum, dum, dum, R(0), wm, wpp);
-        copy7(wa, wb); bna = bnb;
-        copy7(wb, wc); bnb = bnc;
+        // lead-in: the "+" state of cell i0-1, i.e. of the cell it maps to (at
+        // a lower outflow side, cell 0 with its own stencil and source term)
+        const int li = bidx(i0 - 1, p.n, p.out);
+        load_rot(W, N, pcell(p, li - 1), d, wa, bna);
+        load_rot(W, N, pcell(p, li), d, wb, bnb);
+        load_rot(W, N, pcell(p, li + 1), d, wc, bnc);
+        recon_cell<RECON, TR>(wa, wb, wc, bnb, gr, dum, dum, dum, dtdx, wm, wpp);
+        if (TR) trace_src(li, wb, bnb, wm, wpp);
+        load_rot(W, N, pcell(p, i0 - 1), d, wa, bna);
+        load_rot(W, N, pcell(p, i0), d, wb, bnb);
         for (int i = i0; i < i1; i++) {
             const long long ci = p.base + (long long)i * p.stride;
             load_rot(W, N, pcell(p, i + 1), d, wc, bnc);
-            recon_cell<RECON, false>(wa, wb, wc, bnb, gr, dum, dum, dum, R(0), wm, wp);
+            recon_cell<RECON, TR>(wa, wb, wc, bnb, gr, dum, dum, dum, dtdx, wm, wp);
+            if (TR) {
+                trace_src(i, wb, bnb, wm, wp);
+#pragma unroll
+                for (int m = 0; m < 7; m++) {
+                    WMg[(long long)m * N + ci] = wm[m];
+                    WPg[(long long)m * N + ci] = wp[m];
+                }
+            }
             riemann<SOLVER>(wpp, wm, R(Bd[ci]), gm1, gr, f);
 #pragma unroll
             for (int m = 0; m < 7; m++) F[(long long)m * N + ci] = f[m];
@@ -621,28 +656,45 @@ __global__ void __launch_bounds__(PENCIL_THREADS) k_pencil(Boxes B, const R* __r
         R s0[7], s1[7], s2[7];                              // slopes of i-1, i, i+1
         R wpp[7], wm[7], wp[7];
         {
-            R wq[7], bq;                                    // cell i0-3 (lead-in only)
-            load_rot(W, N, pcell(p, i0 - 3), d, wq, bq);
-            load_rot(W, N, pcell(p, i0 - 2), d, w0, b0);
-            load_rot(W, N, pcell(p, i0 - 1), d, w1, b1);
-            load_rot(W, N, pcell(p, i0), d, w2, b2);
-            load_rot(W, N, pcell(p, i0 + 1), d, w3, b3);
-            char_slope(wq, w0, w1, b0, gr, s0);             // slope of i0-2
+            // lead-in: the "+" state of cell i0-1, i.e. of the cell li it maps to
+            // (at a lower outflow side, cell 0 with its own stencil and source)
+            const int li = bidx(i0 - 1, p.n, p.out);
+            R wq[7], bq;
+            load_rot(W, N, pcell(p, li - 2), d, wq, bq);
+            load_rot(W, N, pcell(p, li - 1), d, w0, b0);
+            load_rot(W, N, pcell(p, li), d, w1, b1);
+            load_rot(W, N, pcell(p, li + 1), d, w2, b2);
+            load_rot(W, N, pcell(p, li + 2), d, w3, b3);
+            char_slope(wq, w0, w1, b0, gr, s0);             // slope of li-1
+            char_slope(w0, w1, w2, b1, gr, s1);             // li
+            char_slope(w1, w2, w3, b2, gr, s2);             // li+1
+            recon_cell<PPM, TR>(w0, w1, w2, b1, gr, s0, s1, s2, dtdx, wm, wpp);
+            if (TR) trace_src(li, w1, b1, wm, wpp);
         }
-        char_slope(w0, w1, w2, b1, gr, s1);                 // i0-1
-        char_slope(w1, w2, w3, b2, gr, s2);                 // i0
-        recon_cell<PPM, false>(w0, w1, w2, b1, gr, s0, s1, s2, R(0), wm, wpp);   // cell i0-1
-        // shift so that w0..w2 = cells i0-1 .. i0+1, s0, s1 = slopes of i0-1, i0
-        copy7(w0, w1); b0 = b1;
-        copy7(w1, w2); b1 = b2;
-        copy7(w2, w3); b2 = b3;
-        copy7(s0, s1);
-        copy7(s1, s2);
+        // window of the loop: w0..w2 = cells i0-1 .. i0+1, s0, s1 = slopes of
+        // i0-1, i0
+        {
+            R wq[7], bq;
+            load_rot(W, N, pcell(p, i0 - 2), d, wq, bq);
+            load_rot(W, N, pcell(p, i0 - 1), d, w0, b0);
+            load_rot(W, N, pcell(p, i0), d, w1, b1);
+            load_rot(W, N, pcell(p, i0 + 1), d, w2, b2);
+            char_slope(wq, w0, w1, b0, gr, s0);
+            char_slope(w0, w1, w2, b1, gr, s1);
+        }
         for (int i = i0; i < i1; i++) {
             const long long ci = p.base + (long long)i * p.stride;
             load_rot(W, N, pcell(p, i + 2), d, w3, b3);
             char_slope(w1, w2, w3, b2, gr, s2);             // slope of i+1
-            recon_cell<PPM, false>(w0, w1, w2, b1, gr, s0, s1, s2, R(0), wm, wp);
+            recon_cell<PPM, TR>(w0, w1, w2, b1, gr, s0, s1, s2, dtdx, wm, wp);
+            if (TR) {
+                trace_src(i, w1, b1, wm, wp);
+#pragma unroll
+                for (int m = 0; m < 7; m++) {
+                    WMg[(long long)m * N + ci] = wm[m];
+                    WPg[(long long)m * N + ci] = wp[m];
+                }
+            }
             riemann<SOLVER>(wpp, wm, R(Bd[ci]), gm1, gr, f);
 #pragma unroll
             for (int m = 0; m < 7; m++) F[(long long)m * N + ci] = f[m];
@@ -659,14 +711,18 @@ __global__ void __launch_bounds__(PENCIL_THREADS) k_pencil(Boxes B, const R* __r
 // launch the pencil sweep along a run-time axis d
 template <class R, int RECON, int SOLVER, int MODE, class TE>
 inline void launch_pencil(int d, int grid, cudaStream_t st, const Boxes& g, const R* W, const TE* Bd, R* F,
-                          double gam, const int* seg_list = nullptr, const int* seg_count = nullptr)
+                          double gam, const int* seg_list = nullptr, const int* seg_count = nullptr,
+                          R* WMg = nullptr, R* WPg = nullptr, const DtBox* dtb = nullptr)
 {
     if (d == 0)
-        k_pencil<R, RECON, SOLVER, MODE, TE, 0><<<grid, PENCIL_THREADS, 0, st>>>(g, W, Bd, F, gam, seg_list, seg_count);
+        k_pencil<R, RECON, SOLVER, MODE, TE, 0><<<grid, PENCIL_THREADS, 0, st>>>(g, W, Bd, F, gam, seg_list, seg_count,
+                                                                              WMg, WPg, dtb);
     else if (d == 1)
-        k_pencil<R, RECON, SOLVER, MODE, TE, 1><<<grid, PENCIL_THREADS, 0, st>>>(g, W, Bd, F, gam, seg_list, seg_count);
+        k_pencil<R, RECON, SOLVER, MODE, TE, 1><<<grid, PENCIL_THREADS, 0, st>>>(g, W, Bd, F, gam, seg_list, seg_count,
+                                                                              WMg, WPg, dtb);
     else
-        k_pencil<R, RECON, SOLVER, MODE, TE, 2><<<grid, PENCIL_THREADS, 0, st>>>(g, W, Bd, F, gam, seg_list, seg_count);
+        k_pencil<R, RECON, SOLVER, MODE, TE, 2><<<grid, PENCIL_THREADS, 0, st>>>(g, W, Bd, F, gam, seg_list, seg_count,
+                                                                              WMg, WPg, dtb);
 }
 
 // ---------------------------------------------------------------------------

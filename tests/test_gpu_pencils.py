@@ -1,8 +1,9 @@
-"""Pencil sweeps (mhd_set_sweep_pencils, VL only; the VL default is pencils
-along y and z): one thread per segment of consecutive faces along the sweep
-axis.  FP64 parity with the oracle at the 1e-12 bar on cubic, ragged and thin
-boxes, segment lengths that do and do not divide the lines, and the tile
-sweeps everywhere (mask 0); agreement with the tile sweeps; argument checks."""
+"""Pencil sweeps (mhd_set_sweep_pencils): one thread per segment of
+consecutive faces along the sweep axis (VL: x by warps), for the VL
+predictor and corrector and the CTU tracing sweeps.  FP64 parity with the
+oracle at the 1e-12 bar on cubic, ragged and thin boxes, segment lengths
+that do and do not divide the lines, and the tile sweeps everywhere
+(mask 0); agreement with the tile sweeps; argument checks."""
 import numpy as np
 import pytest
 
@@ -12,6 +13,7 @@ from paper_1804_03479_b300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 VL = [("vl", r, s) for r in ("plm", "ppm", "plm_prim") for s in ("roe", "hlld", "hlle")]
+CTU = [("ctu", r, s) for r in ("plm", "ppm") for s in ("roe", "hlld", "hlle")]
 
 
 @pytest.fixture(scope="module")
@@ -53,6 +55,13 @@ def parity(M, st, scheme, mask, plen, nsteps, tol=1e-12):
 def test_pencil_fp64_parity_abc32(M, scheme):
     st = I.abc(32, kmult=1, beta=1.0, seed=0)
     parity(M, st, scheme, 7, 16, 4)
+
+
+@pytest.mark.parametrize("scheme", CTU)
+@pytest.mark.parametrize("mask,plen", [(7, 16), (6, 5), (1, 7)])
+def test_ctu_tracing_pencils_fp64_parity(M, scheme, mask, plen):
+    st = I.abc(None, kmult=1, beta=0.5, seed=6, noise=3e-2, shape=(24, 20, 18))
+    parity(M, st, scheme, mask, plen, 3)
 
 
 @pytest.mark.parametrize("mask,plen", [(0, 16), (7, 5), (6, 32), (1, 7), (7, 64)])
@@ -122,8 +131,9 @@ def test_pencil_arguments(M):
         s.free()
     s = M.Solver(st.U.shape[1:], st.dx, st.gamma, "ctu", "plm", "roe", "fp64", 0.3)
     try:
-        with pytest.raises(M.MHDError):
-            s.set_sweep_pencils(7, 16)
+        assert s.sweep_pencils() == (6, 32)       # the CTU default: y and z
+        s.set_sweep_pencils(7, 16)
+        assert s.sweep_pencils() == (7, 16)
     finally:
         s.free()
 
