@@ -251,10 +251,17 @@ void run_step(mhd_ctx* c, bool device_dt)
                 launch_pencil<R, RECON, SOLVER, 2, TE>(d, pencil_grid(c, d), st, g, W, s.b[d],
                                                        F1 + (long long)d * 7 * n, gam, nullptr, nullptr,
                                                        WM + (long long)d * 7 * n, WP + (long long)d * 7 * n, c->dtc);
+            else if (d == 0)
+                k_sweep<R, RECON, SOLVER, 2, TE, 0><<<sweep_grid(c, d), SWEEP_THREADS, smem, st>>>(
+                    g, d, W, s.b[d], F1, WM, WP, c->dtc, gam);
+            else if (d == 1)
+                k_sweep<R, RECON, SOLVER, 2, TE, 1><<<sweep_grid(c, d), SWEEP_THREADS, smem, st>>>(
+                    g, d, W, s.b[d], F1 + (long long)7 * n, WM + (long long)7 * n, WP + (long long)7 * n, c->dtc,
+                    gam);
             else
-                k_sweep<R, RECON, SOLVER, 2, TE><<<sweep_grid(c, d), SWEEP_THREADS, smem, st>>>(
-                    g, d, W, s.b[d], F1 + (long long)d * 7 * n, WM + (long long)d * 7 * n,
-                    WP + (long long)d * 7 * n, c->dtc, gam);
+                k_sweep<R, RECON, SOLVER, 2, TE, 2><<<sweep_grid(c, d), SWEEP_THREADS, smem, st>>>(
+                    g, d, W, s.b[d], F1 + (long long)14 * n, WM + (long long)14 * n, WP + (long long)14 * n,
+                    c->dtc, gam);
             prof_mark(c, 2 + d);
         }
         // steps 3-4: edge E at t^n, dt/2 update of face B and cell state
@@ -304,7 +311,20 @@ inline cudaError_t allow_smem()
     cudaError_t e = cudaFuncSetAttribute(k_emf<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)emf_smem_bytes<R>());
     if (e != cudaSuccess || MODE == 0) return e;
-    return cudaFuncSetAttribute(k_sweep<R, RECON, SOLVER, MODE, TE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
+    if constexpr (MODE == 2) {   // the CTU tracing sweeps run with the axis fixed at compile time
+        e = cudaFuncSetAttribute(k_sweep<R, RECON, SOLVER, MODE, TE, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)b);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_sweep<R, RECON, SOLVER, MODE, TE, 1>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_sweep<R, RECON, SOLVER, MODE, TE, 2>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
+        return e;
+    } else {
+        return cudaFuncSetAttribute(k_sweep<R, RECON, SOLVER, MODE, TE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)b);
+    }
 }
 
 // pick the step function of one precision; returns nullptr if not built

@@ -362,14 +362,17 @@ size_t sweep_smem_bytes(int recon, int tl)
     return b;
 }
 
-template <class R, int RECON, int SOLVER, int MODE, class TE>
-__global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(Boxes B, int d, const R* __restrict__ W,
+// D >= 0 fixes the sweep axis at compile time (the CTU tracing launches):
+// with the run-time axis the compiler keeps per-thread arrays in local memory.
+template <class R, int RECON, int SOLVER, int MODE, class TE, int D = -1>
+__global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(Boxes B, int d_run, const R* __restrict__ W,
                                                          const TE* __restrict__ Bd, R* __restrict__ F,
                                                          R* __restrict__ WMg, R* __restrict__ WPg,
                                                          const DtBox* __restrict__ dtb, double gam,
                                                          const int* __restrict__ tile_list = nullptr,
                                                          const int* __restrict__ tile_count = nullptr)
 {
+    const int d = D >= 0 ? D : d_run;
     extern __shared__ unsigned char smem_raw[];
     R* sm = reinterpret_cast<R*>(smem_raw);
     const long long N = B.N;
