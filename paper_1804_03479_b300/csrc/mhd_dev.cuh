@@ -456,10 +456,15 @@ __device__ __forceinline__ void hlld_flux(const R wl[7], const R wr[7], R bn, R 
     R SsL = SM - Num<R>::abs_(bn) / sql;
     R SsR = SM + Num<R>::abs_(bn) / sqr;
     const bool left = SM >= R(0);
-    // the outer side whose fan we are in
-    const R* wo = left ? wl : wr;
-    const R* fo = left ? fl : fr;
-    const R* uso = left ? usl : usr;
+    // the outer side whose fan we are in, selected element by element (a
+    // pointer to either array would put both in local memory)
+    R wo[7], fo[7], uso[7];
+#pragma unroll
+    for (int k = 0; k < 7; k++) {
+        wo[k] = left ? wl[k] : wr[k];
+        fo[k] = left ? fl[k] : fr[k];
+        uso[k] = left ? usl[k] : usr[k];
+    }
     R So = left ? SL : SR;
     R uo[7];
     to_cons(wo, bn, gm1, uo);
