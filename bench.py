@@ -63,11 +63,11 @@ FLOPS_PER_FACE = {"corrector": {"fp32": 705.0, "fp64": 705.0, "mixed": 705.0},
                   "predictor": {"fp32": 435.0, "fp64": 435.0, "mixed": 435.0}}
 # DRAM bytes (read + write) per face of one sweep launch, per kernel, from
 # dram__bytes_read.sum + dram__bytes_write.sum of the ncu captures in
-# profiles/ (FP32 at 160^3: pencil corrector 263.2 MB, pencil predictor
-# 236.6 MB, x-warp corrector 219.3 MB; FP64 pencil corrector 255.3 MB at
+# profiles/ (FP32 at 160^3: pencil corrector 233.7 MB, pencil predictor
+# 209.2 MB, x-warp corrector 219.3 MB; FP64 pencil corrector 240.4 MB at
 # 128^3), scaled to other sizes by faces; a kernel changed since its capture
 # has none.
-TRAFFIC_PER_FACE = {"corrector_pencil": {"fp32": 64.3, "fp64": 121.8}, "predictor_pencil": {"fp32": 57.8},
+TRAFFIC_PER_FACE = {"corrector_pencil": {"fp32": 57.1, "fp64": 114.6}, "predictor_pencil": {"fp32": 51.1},
                     "corrector_xwarp": {"fp32": 53.5}}
 
 
