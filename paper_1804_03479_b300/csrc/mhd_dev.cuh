@@ -19,18 +19,26 @@ template <class R> struct Num;
 template <> struct Num<double> {
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
     static __device__ __forceinline__ double abs_(double x) { return fabs(x); }
+    static __device__ __forceinline__ double min_(double a, double b) { return fmin(a, b); }
+    static __device__ __forceinline__ double max_(double a, double b) { return fmax(a, b); }
+    static __device__ __forceinline__ double copysign_(double a, double b) { return copysign(a, b); }
     static constexpr double hlld_degen = 1e-8;
     static constexpr double fan_margin = 1e-10;   // relative margin of the Roe fan bound
 };
 template <> struct Num<float> {
     static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
     static __device__ __forceinline__ float abs_(float x) { return fabsf(x); }
+    static __device__ __forceinline__ float min_(float a, float b) { return fminf(a, b); }
+    static __device__ __forceinline__ float max_(float a, float b) { return fmaxf(a, b); }
+    static __device__ __forceinline__ float copysign_(float a, float b) { return copysignf(a, b); }
     static constexpr float hlld_degen = 1e-5f;
     static constexpr float fan_margin = 1e-4f;
 };
 
-template <class R> __device__ __forceinline__ R rmin(R a, R b) { return a < b ? a : b; }
-template <class R> __device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
+// one min/max instruction each; for ordered operands the value of a < b ? a : b
+// (at most the sign of a zero result differs)
+template <class R> __device__ __forceinline__ R rmin(R a, R b) { return Num<R>::min_(a, b); }
+template <class R> __device__ __forceinline__ R rmax(R a, R b) { return Num<R>::max_(a, b); }
 template <class R> __device__ __forceinline__ R sgn1(R a) { return a >= R(0) ? R(1) : R(-1); }
 
 // ---- Eq. 5 and Eqs. 7-9 in the sweep frame ------------------------------
@@ -504,7 +512,10 @@ __device__ __forceinline__ void riemann(const R wl[7], const R wr[7], R bn, R gm
 template <class R>
 __device__ __forceinline__ R mc(R l, R r, R c)
 {
-    if (l * r > R(0)) return sgn1(c) * rmin(rmin(R(2) * Num<R>::abs_(l), R(2) * Num<R>::abs_(r)), Num<R>::abs_(c));
+    // sign of c on the limited magnitude (c = -0 gives -0 where the sign
+    // factor gave +0: the same value)
+    if (l * r > R(0))
+        return Num<R>::copysign_(rmin(rmin(R(2) * Num<R>::abs_(l), R(2) * Num<R>::abs_(r)), Num<R>::abs_(c)), c);
     return R(0);
 }
 
