@@ -310,9 +310,9 @@ __device__ __forceinline__ bool roe_state_ok(const RoeAvg<R>& m, R ke, R igm1, c
 }
 
 // Roe flux with the exact linearisation; returns true when it fell back to HLLE.
-// F = (F_L + F_R)/2 - (1/2) M R (|lambda| eta): the dissipation is one
-// eigenvector expansion of |lambda| eta; the intermediate states
-// U_L + M sum_{b<=a} eta_b r_b are accumulated wave by wave in primitive space.
+// F = F_L + M R (min(lambda, 0) eta): one eigenvector expansion of the
+// left-going waves' strengths; the intermediate states U_L + M sum_{b<=a}
+// eta_b r_b are accumulated wave by wave in primitive space.
 template <class R>
 __device__ __forceinline__ bool roe_flux(const R wl[7], const R wr[7], R bn, R gm1, R gam, R f[7])
 {
@@ -386,16 +386,18 @@ __device__ __forceinline__ bool roe_flux(const R wl[7], const R wr[7], R bn, R g
         hlle_core(wl, wr, bn, gm1, gam, true, m.u, cf, f);
         return true;
     }
+    // F = (F_L + F_R)/2 - (1/2) M R (|lambda| eta) equals F_L + M R (min(lambda, 0) eta)
+    // exactly, since the exact linearisation gives F_R - F_L = M R (lambda eta):
+    // one physical flux instead of two
     R ae[7], D[7], dis[7];
 #pragma unroll
-    for (int a = 0; a < 7; a++) ae[a] = Num<R>::abs_(lam[a]) * eta[a];
+    for (int a = 0; a < 7; a++) ae[a] = rmin(lam[a], R(0)) * eta[a];
     eig_expand(e, ae, D);
     roe_to_cons(m, ke, igm1, D, dis);
-    R fl[7], fr[7];
+    R fl[7];
     phys_flux(wl, bn, gm1, fl);
-    phys_flux(wr, bn, gm1, fr);
 #pragma unroll
-    for (int k = 0; k < 7; k++) f[k] = R(0.5) * (fl[k] + fr[k]) - R(0.5) * dis[k];
+    for (int k = 0; k < 7; k++) f[k] = fl[k] + dis[k];
     return false;
 }
 
