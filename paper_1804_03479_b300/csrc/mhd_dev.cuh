@@ -18,6 +18,7 @@ enum { ROE = 0, HLLD = 1, HLLE = 2 };
 template <class R> struct Num;
 template <> struct Num<double> {
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+    static __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
     static __device__ __forceinline__ double abs_(double x) { return fabs(x); }
     static __device__ __forceinline__ double min_(double a, double b) { return fmin(a, b); }
     static __device__ __forceinline__ double max_(double a, double b) { return fmax(a, b); }
@@ -27,6 +28,7 @@ template <> struct Num<double> {
 };
 template <> struct Num<float> {
     static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
     static __device__ __forceinline__ float abs_(float x) { return fabsf(x); }
     static __device__ __forceinline__ float min_(float a, float b) { return fminf(a, b); }
     static __device__ __forceinline__ float max_(float a, float b) { return fmaxf(a, b); }
@@ -77,11 +79,13 @@ __device__ __forceinline__ void phys_flux(const R w[7], R bn, R gm1, R f[7])
     f[6] = w[6] * w[1] - bn * w[3];
 }
 
+// fast magnetosonic speed; FP32 multiplies by 1/rho (one reciprocal serves
+// both field terms), FP64 divides by rho as the oracle does
 template <class R>
-__device__ __forceinline__ R fast_speed(R rho, R a2, R bn, R bt1, R bt2)
+__device__ __forceinline__ R fast_speed(R rho, R irho, R a2, R bn, R bt1, R bt2)
 {
-    R ca2 = bn * bn / rho;
-    R bt2s = (bt1 * bt1 + bt2 * bt2) / rho;
+    R ca2 = sizeof(R) == 4 ? bn * bn * irho : bn * bn / rho;
+    R bt2s = sizeof(R) == 4 ? (bt1 * bt1 + bt2 * bt2) * irho : (bt1 * bt1 + bt2 * bt2) / rho;
     R t = a2 - ca2 - bt2s;
     R disc = t * t + R(4) * a2 * bt2s;
     return Num<R>::sqrt_(R(0.5) * (a2 + ca2 + bt2s + Num<R>::sqrt_(disc)));
@@ -93,27 +97,55 @@ template <class R> struct Eig {
     R rho, irho, sr, isr, a2, ia2, a, cf, cs, ca, af, as, by, bz, s, vn, nrm;
 };
 
-// a2 = gamma P / rho (primitive sound speed squared, Roe-averaged for Roe)
+// a2 = gamma P / rho (primitive sound speed squared, Roe-averaged for Roe);
+// rsr = 1/sqrt(rho)
 template <class R>
-__device__ __forceinline__ void eig_setup(R rho, R vn, R a2, R bn, R bt1, R bt2, Eig<R>& e)
+__device__ __forceinline__ void eig_setup_r(R rho, R rsr, R vn, R a2, R bn, R bt1, R bt2, Eig<R>& e)
 {
     e.rho = rho;
-    e.irho = R(1) / rho;
     e.vn = vn;
-    e.sr = Num<R>::sqrt_(rho);
-    e.isr = e.sr * e.irho;
-    R ca2 = bn * bn * e.irho;
-    R bt2s = (bt1 * bt1 + bt2 * bt2) * e.irho;
-    R t = a2 - ca2 - bt2s;
-    R disc = t * t + R(4) * a2 * bt2s;
-    R cf2 = R(0.5) * (a2 + ca2 + bt2s + Num<R>::sqrt_(disc));
-    R cs2 = a2 * ca2 / cf2;
-    e.cf = Num<R>::sqrt_(cf2);
-    e.cs = Num<R>::sqrt_(cs2);
-    e.ca = Num<R>::sqrt_(ca2);
-    e.a = Num<R>::sqrt_(a2);
+    R cf2, cs2;
+    if constexpr (sizeof(R) == 4) {
+        // FP32: square roots and reciprocals from three reciprocal square
+        // roots: 1/sqrt(rho) gives sqrt(rho), 1/rho and c_a = |B_n|/sqrt(rho);
+        // 1/c_f and 1/a give c_f, a, 1/a^2 and c_s = a c_a / c_f
+        // (c_s^2 c_f^2 = a^2 c_a^2)
+        e.isr = rsr;
+        e.irho = rsr * rsr;
+        e.sr = rho * rsr;
+        R ca2 = bn * bn * e.irho;
+        R bt2s = (bt1 * bt1 + bt2 * bt2) * e.irho;
+        R t = a2 - ca2 - bt2s;
+        R disc = t * t + R(4) * a2 * bt2s;
+        cf2 = R(0.5) * (a2 + ca2 + bt2s + Num<R>::sqrt_(disc));
+        const R rcf = Num<R>::rsqrt_(cf2), ra = Num<R>::rsqrt_(a2);
+        e.cf = cf2 * rcf;
+        e.a = a2 * ra;
+        e.ia2 = ra * ra;
+        e.ca = Num<R>::abs_(bn) * rsr;
+        e.cs = e.a * e.ca * rcf;
+        cs2 = e.cs * e.cs;
+    } else {
+        // FP64: the oracle's chain of correctly rounded divisions and square
+        // roots.  Near c_f = c_s the amplitudes below hang on the difference
+        // c_f^2 - c_s^2; the few extra ulps of the reciprocal-square-root
+        // forms grow there past the 1e-12 parity bar.
+        e.irho = R(1) / rho;
+        e.sr = Num<R>::sqrt_(rho);
+        e.isr = e.sr * e.irho;
+        R ca2 = bn * bn * e.irho;
+        R bt2s = (bt1 * bt1 + bt2 * bt2) * e.irho;
+        R t = a2 - ca2 - bt2s;
+        R disc = t * t + R(4) * a2 * bt2s;
+        cf2 = R(0.5) * (a2 + ca2 + bt2s + Num<R>::sqrt_(disc));
+        cs2 = a2 * ca2 / cf2;
+        e.cf = Num<R>::sqrt_(cf2);
+        e.cs = Num<R>::sqrt_(cs2);
+        e.ca = Num<R>::sqrt_(ca2);
+        e.a = Num<R>::sqrt_(a2);
+        e.ia2 = R(1) / a2;
+    }
     e.a2 = a2;
-    e.ia2 = R(1) / a2;
     R dd = cf2 - cs2;
     if (dd > R(0)) {
         R idd = R(1) / dd;
@@ -125,7 +157,7 @@ __device__ __forceinline__ void eig_setup(R rho, R vn, R a2, R bn, R bt1, R bt2,
     }
     R btm2 = bt1 * bt1 + bt2 * bt2;
     if (btm2 > R(0)) {
-        R ibt = R(1) / Num<R>::sqrt_(btm2);
+        R ibt = sizeof(R) == 4 ? Num<R>::rsqrt_(btm2) : R(1) / Num<R>::sqrt_(btm2);
         e.by = bt1 * ibt;
         e.bz = bt2 * ibt;
     } else {
@@ -134,6 +166,25 @@ __device__ __forceinline__ void eig_setup(R rho, R vn, R a2, R bn, R bt1, R bt2,
     }
     e.s = sgn1(bn);
     e.nrm = R(0.5) * e.ia2;
+}
+
+template <class R>
+__device__ __forceinline__ void eig_setup(R rho, R vn, R a2, R bn, R bt1, R bt2, Eig<R>& e)
+{
+    eig_setup_r(rho, sizeof(R) == 4 ? Num<R>::rsqrt_(rho) : R(0), vn, a2, bn, bt1, bt2, e);
+}
+
+// the eigensystem of a cell state from its pressure: a^2 = gamma P / rho with
+// the 1/rho of the reciprocal square root
+template <class R>
+__device__ __forceinline__ void eig_setup_p(R rho, R vn, R gam, R P, R bn, R bt1, R bt2, Eig<R>& e)
+{
+    if constexpr (sizeof(R) == 4) {
+        const R rsr = Num<R>::rsqrt_(rho);
+        eig_setup_r(rho, rsr, vn, gam * P * (rsr * rsr), bn, bt1, bt2, e);
+    } else {
+        eig_setup_r(rho, R(0), vn, gam * P / rho, bn, bt1, bt2, e);   // FP64: the oracle's a^2
+    }
 }
 
 template <class R>
@@ -224,8 +275,11 @@ __device__ __forceinline__ void hlle_core(const R wl[7], const R wr[7], R bn, R 
     phys_flux(wr, bn, gm1, fr);
     to_cons(wl, bn, gm1, ul);
     to_cons(wr, bn, gm1, ur);
-    R cfl = fast_speed(wl[0], gam * wl[4] / wl[0], bn, wl[5], wl[6]);
-    R cfr = fast_speed(wr[0], gam * wr[4] / wr[0], bn, wr[5], wr[6]);
+    const R irl = R(1) / wl[0], irr = R(1) / wr[0];
+    const R a2l = sizeof(R) == 4 ? gam * wl[4] * irl : gam * wl[4] / wl[0];
+    const R a2r = sizeof(R) == 4 ? gam * wr[4] * irr : gam * wr[4] / wr[0];
+    R cfl = fast_speed(wl[0], irl, a2l, bn, wl[5], wl[6]);
+    R cfr = fast_speed(wr[0], irr, a2r, bn, wr[5], wr[6]);
     R sL = wl[1] - cfl, sR = wr[1] + cfr;
     if (have_roe) {
         sL = rmin(sL, roe_vn - roe_cf);
@@ -244,28 +298,42 @@ __device__ __forceinline__ void hlle_core(const R wl[7], const R wr[7], R bn, R 
 
 // Roe averages of the linearisation used by the Roe and HLLE solvers
 template <class R> struct RoeAvg {
-    R rho, u, v, w, b1, b2, X, a2;
+    R rho, irho, u, v, w, b1, b2, X, a2;
 };
 
 template <class R>
 __device__ __forceinline__ void roe_average(const R wl[7], const R wr[7], R bn, R gm1, R gam, RoeAvg<R>& m)
 {
-    R sl = Num<R>::sqrt_(wl[0]), sr = Num<R>::sqrt_(wr[0]);
+    // FP32: sqrt(rho) and 1/sqrt(rho) of each side from one reciprocal square
+    // root; sqrt(rho) h = (E + p_T) / sqrt(rho) and 1/(sqrt(rho_L) sqrt(rho_R))
+    // = 1/rho_Roe without a division.  FP64: the oracle's divisions and
+    // square roots (the parity bar; see eig_setup_r)
+    constexpr bool F32 = sizeof(R) == 4;
+    const R rsl = F32 ? Num<R>::rsqrt_(wl[0]) : R(0), rsr = F32 ? Num<R>::rsqrt_(wr[0]) : R(0);
+    R sl = F32 ? wl[0] * rsl : Num<R>::sqrt_(wl[0]), sr = F32 ? wr[0] * rsr : Num<R>::sqrt_(wr[0]);
     R isum = R(1) / (sl + sr);
     m.rho = sl * sr;
+    m.irho = F32 ? rsl * rsr : R(1) / m.rho;
     m.u = (sl * wl[1] + sr * wr[1]) * isum;
     m.v = (sl * wl[2] + sr * wr[2]) * isum;
     m.w = (sl * wl[3] + sr * wr[3]) * isum;
     R el = total_energy(wl, bn, gm1), er = total_energy(wr, bn, gm1);
-    R hl = (el + wl[4] + R(0.5) * (bn * bn + wl[5] * wl[5] + wl[6] * wl[6])) / wl[0];
-    R hr = (er + wr[4] + R(0.5) * (bn * bn + wr[5] * wr[5] + wr[6] * wr[6])) / wr[0];
-    R h = (sl * hl + sr * hr) * isum;
+    R h;
+    if constexpr (F32) {
+        R shl = (el + wl[4] + R(0.5) * (bn * bn + wl[5] * wl[5] + wl[6] * wl[6])) * rsl;   // sqrt(rho_L) h_L
+        R shr = (er + wr[4] + R(0.5) * (bn * bn + wr[5] * wr[5] + wr[6] * wr[6])) * rsr;   // sqrt(rho_R) h_R
+        h = (shl + shr) * isum;
+    } else {
+        R hl = (el + wl[4] + R(0.5) * (bn * bn + wl[5] * wl[5] + wl[6] * wl[6])) / wl[0];
+        R hr = (er + wr[4] + R(0.5) * (bn * bn + wr[5] * wr[5] + wr[6] * wr[6])) / wr[0];
+        h = (sl * hl + sr * hr) * isum;
+    }
     m.b1 = (sr * wl[5] + sl * wr[5]) * isum;
     m.b2 = (sr * wl[6] + sl * wr[6]) * isum;
     R d5 = wl[5] - wr[5], d6 = wl[6] - wr[6];
     m.X = R(0.5) * (d5 * d5 + d6 * d6) * isum * isum;
-    m.a2 = gm1 * (h - R(0.5) * (m.u * m.u + m.v * m.v + m.w * m.w) - (bn * bn + m.b1 * m.b1 + m.b2 * m.b2) / m.rho)
-           - (gam - R(2)) * m.X;
+    const R mag = F32 ? (bn * bn + m.b1 * m.b1 + m.b2 * m.b2) * m.irho : (bn * bn + m.b1 * m.b1 + m.b2 * m.b2) / m.rho;
+    m.a2 = gm1 * (h - R(0.5) * (m.u * m.u + m.v * m.v + m.w * m.w) - mag) - (gam - R(2)) * m.X;
 }
 
 template <class R>
@@ -274,7 +342,7 @@ __device__ __forceinline__ void hlle_flux(const R wl[7], const R wr[7], R bn, R 
     RoeAvg<R> m;
     roe_average(wl, wr, bn, gm1, gam, m);
     bool ok = m.a2 > R(0);
-    R cf = ok ? fast_speed(m.rho, m.a2, bn, m.b1, m.b2) : R(0);
+    R cf = ok ? fast_speed(m.rho, m.irho, m.a2, bn, m.b1, m.b2) : R(0);
     hlle_core(wl, wr, bn, gm1, gam, ok, m.u, cf, f);
 }
 
@@ -382,7 +450,7 @@ __device__ __forceinline__ bool roe_flux(const R wl[7], const R wr[7], R bn, R g
     eig_add_col<5>(e, eta[5], P); ok &= roe_state_ok(m, ke, igm1, ul, P, bn, gm1);
     }
     if (!ok) {
-        R cf = fast_speed(m.rho, m.a2, bn, m.b1, m.b2);
+        R cf = fast_speed(m.rho, m.irho, m.a2, bn, m.b1, m.b2);
         hlle_core(wl, wr, bn, gm1, gam, true, m.u, cf, f);
         return true;
     }
@@ -437,8 +505,11 @@ __device__ __forceinline__ void hlld_flux(const R wl[7], const R wr[7], R bn, R 
     R fl[7], fr[7];
     phys_flux(wl, bn, gm1, fl);
     phys_flux(wr, bn, gm1, fr);
-    R cfl = fast_speed(wl[0], gam * wl[4] / wl[0], bn, wl[5], wl[6]);
-    R cfr = fast_speed(wr[0], gam * wr[4] / wr[0], bn, wr[5], wr[6]);
+    const R irl = R(1) / wl[0], irr = R(1) / wr[0];
+    const R a2l = sizeof(R) == 4 ? gam * wl[4] * irl : gam * wl[4] / wl[0];
+    const R a2r = sizeof(R) == 4 ? gam * wr[4] * irr : gam * wr[4] / wr[0];
+    R cfl = fast_speed(wl[0], irl, a2l, bn, wl[5], wl[6]);
+    R cfr = fast_speed(wr[0], irr, a2r, bn, wr[5], wr[6]);
     R cmax = rmax(cfl, cfr);
     R SL = rmin(wl[1], wr[1]) - cmax;
     R SR = rmax(wl[1], wr[1]) + cmax;
@@ -533,7 +604,7 @@ template <class R>
 __device__ __forceinline__ void char_slope(const R wm[7], const R w0[7], const R wp[7], R bn, R gam, R dw[7])
 {
     Eig<R> e;
-    eig_setup(w0[0], w0[1], gam * w0[4] / w0[0], bn, w0[5], w0[6], e);
+    eig_setup_p(w0[0], w0[1], gam, w0[4], bn, w0[5], w0[6], e);
     R dl[7], dr[7], al[7], ar[7];
 #pragma unroll
     for (int k = 0; k < 7; k++) {
@@ -568,7 +639,7 @@ __device__ __forceinline__ void recon_cell(const R wm1[7], const R w0[7], const 
         return;
     }
     Eig<R> e;
-    eig_setup(w0[0], w0[1], gam * w0[4] / w0[0], bn, w0[5], w0[6], e);
+    eig_setup_p(w0[0], w0[1], gam, w0[4], bn, w0[5], w0[6], e);
     R pl[7], pr[7];
     if (RECON == PLM) {
         R dl[7], dr[7], al[7], ar[7];

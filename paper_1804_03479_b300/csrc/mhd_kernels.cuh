@@ -273,12 +273,13 @@ __global__ void __launch_bounds__(CELL_THREADS) k_prim(Boxes B, StateP<TU, TE> s
             for (int f = 0; f < 8; f++) W[f * N + c] = w[f];
             if (!(w[0] > R(0)) || !(w[4] > R(0))) atomicMin(bad_cell, (unsigned long long)c);
             if (smax_acc) {
-                R a2 = R(gam) * w[4] / w[0];
+                const R iw0 = R(1) / w[0];
+                R a2 = sizeof(R) == 4 ? R(gam) * w[4] * iw0 : R(gam) * w[4] / w[0];
                 R sm = R(0);
 #pragma unroll
                 for (int d = 0; d < 3; d++) {
                     const int t1 = d == 2 ? 0 : d + 1, t2 = d == 0 ? 2 : d - 1;
-                    R cf = fast_speed(w[0], a2, w[5 + d], w[5 + t1], w[5 + t2]);
+                    R cf = fast_speed(w[0], iw0, a2, w[5 + d], w[5 + t1], w[5 + t2]);
                     sm = rmax(sm, Num<R>::abs_(w[1 + d]) + cf);
                 }
                 local = (double)sm;
