@@ -57,18 +57,18 @@ SIZES = {"fp64": (8, 8, 8), "fp32": (4, 4, 4), "mixed": (4, 8, 4)}   # (rho/M, e
 # reconstruction per face plus the segment's 1/32 lead-in; the Roe fan check
 # skipped where its bound proves it passes), where every divide and square
 # root is a single MUFU op.  The same arithmetic runs in the FP64 build, whose
-# divides and square roots expand into FMA iterations (1186 executed FP64
+# divides and square roots expand into FMA iterations (1125 executed FP64
 # flops per corrector face at 128^3), so these figures serve all precisions.
-FLOPS_PER_FACE = {"corrector": {"fp32": 705.0, "fp64": 705.0, "mixed": 705.0},
-                  "predictor": {"fp32": 435.0, "fp64": 435.0, "mixed": 435.0}}
+FLOPS_PER_FACE = {"corrector": {"fp32": 657.0, "fp64": 657.0, "mixed": 657.0},
+                  "predictor": {"fp32": 393.0, "fp64": 393.0, "mixed": 393.0}}
 # DRAM bytes (read + write) per face of one sweep launch, per kernel, from
 # dram__bytes_read.sum + dram__bytes_write.sum of the ncu captures in
-# profiles/ (FP32 at 160^3: pencil corrector 233.7 MB, pencil predictor
-# 209.2 MB, x-warp corrector 219.3 MB; FP64 pencil corrector 240.4 MB at
+# profiles/ (FP32 at 160^3: pencil corrector 233.8 MB, pencil predictor
+# 208.2 MB, x-warp corrector 219.4 MB; FP64 pencil corrector 240.0 MB at
 # 128^3), scaled to other sizes by faces; a kernel changed since its capture
 # has none.
-TRAFFIC_PER_FACE = {"corrector_pencil": {"fp32": 57.1, "fp64": 114.6}, "predictor_pencil": {"fp32": 51.1},
-                    "corrector_xwarp": {"fp32": 53.5}}
+TRAFFIC_PER_FACE = {"corrector_pencil": {"fp32": 57.1, "fp64": 114.4}, "predictor_pencil": {"fp32": 50.8},
+                    "corrector_xwarp": {"fp32": 53.6}}
 
 
 def peaks():
