@@ -601,10 +601,8 @@ __device__ __forceinline__ R clamp_between(R x, R a, R b)
 
 // characteristic-MC-limited slope dw of the cell with neighbours m, p
 template <class R>
-__device__ __forceinline__ void char_slope(const R wm[7], const R w0[7], const R wp[7], R bn, R gam, R dw[7])
+__device__ __forceinline__ void char_slope_e(const Eig<R>& e, const R wm[7], const R w0[7], const R wp[7], R dw[7])
 {
-    Eig<R> e;
-    eig_setup_p(w0[0], w0[1], gam, w0[4], bn, w0[5], w0[6], e);
     R dl[7], dr[7], al[7], ar[7];
 #pragma unroll
     for (int k = 0; k < 7; k++) {
@@ -620,26 +618,31 @@ __device__ __forceinline__ void char_slope(const R wm[7], const R w0[7], const R
     eig_expand(e, da, dw);
 }
 
+// the eigensystem of a cell state (w, B_n) for the reconstruction and the
+// PPM slopes: one set-up serves both
+template <class R>
+__device__ __forceinline__ void cell_eig(const R w0[7], R bn, R gam, Eig<R>& e)
+{
+    eig_setup_p(w0[0], w0[1], gam, w0[4], bn, w0[5], w0[6], e);
+}
+
+template <class R>
+__device__ __forceinline__ void char_slope(const R wm[7], const R w0[7], const R wp[7], R bn, R gam, R dw[7])
+{
+    Eig<R> e;
+    cell_eig(w0, bn, gam, e);
+    char_slope_e(e, wm, w0, wp, dw);
+}
+
 // Face states of one cell: wm on its face -1/2, wp on its face +1/2.
 // w0 the cell, wm1/wp1 its neighbours; for PPM, dwm/dw0/dwp are the
 // characteristic-limited slopes of cells -1, 0, +1.  trace: CTU tracing
 // with dtdx = dt/dx.
 template <int RECON, bool TRACE, class R>
-__device__ __forceinline__ void recon_cell(const R wm1[7], const R w0[7], const R wp1[7], R bn, R gam,
-                                           const R dwm[7], const R dw0[7], const R dwp[7], R dtdx,
-                                           R wm[7], R wp[7])
+__device__ __forceinline__ void recon_cell_e(const Eig<R>& e, const R wm1[7], const R w0[7], const R wp1[7],
+                                             const R dwm[7], const R dw0[7], const R dwp[7], R dtdx,
+                                             R wm[7], R wp[7])
 {
-    if (RECON == PLM_PRIM) {
-#pragma unroll
-        for (int k = 0; k < 7; k++) {
-            R d = mc(w0[k] - wm1[k], wp1[k] - w0[k], R(0.5) * (wp1[k] - wm1[k]));
-            wm[k] = w0[k] - R(0.5) * d;
-            wp[k] = w0[k] + R(0.5) * d;
-        }
-        return;
-    }
-    Eig<R> e;
-    eig_setup_p(w0[0], w0[1], gam, w0[4], bn, w0[5], w0[6], e);
     R pl[7], pr[7];
     if (RECON == PLM) {
         R dl[7], dr[7], al[7], ar[7];
@@ -716,6 +719,25 @@ __device__ __forceinline__ void recon_cell(const R wm1[7], const R w0[7], const 
             wp[k] = clamp_between(wp[k], w0[k], wp1[k]);
         }
     }
+}
+
+template <int RECON, bool TRACE, class R>
+__device__ __forceinline__ void recon_cell(const R wm1[7], const R w0[7], const R wp1[7], R bn, R gam,
+                                           const R dwm[7], const R dw0[7], const R dwp[7], R dtdx,
+                                           R wm[7], R wp[7])
+{
+    if (RECON == PLM_PRIM) {
+#pragma unroll
+        for (int k = 0; k < 7; k++) {
+            R d = mc(w0[k] - wm1[k], wp1[k] - w0[k], R(0.5) * (wp1[k] - wm1[k]));
+            wm[k] = w0[k] - R(0.5) * d;
+            wp[k] = w0[k] + R(0.5) * d;
+        }
+        return;
+    }
+    Eig<R> e;
+    cell_eig(w0, bn, gam, e);
+    recon_cell_e<RECON, TRACE>(e, wm1, w0, wp1, dwm, dw0, dwp, dtdx, wm, wp);
 }
 
 }  // namespace mhd

@@ -837,11 +837,14 @@ __global__ void __launch_bounds__(PENCIL_THREADS) k_xwarp(Boxes B, const R* __re
             shfl7(wm1, w, 1);
             shfl7(wp1, w, 0);
             if (RECON == PPM) {
+                // the lane's cell eigensystem serves its slope and its reconstruction
                 R s0[7], sm1[7], sp1[7];
-                char_slope(wm1, w, wp1, bn, gr, s0);
+                Eig<R> e;
+                cell_eig(w, bn, gr, e);
+                char_slope_e(e, wm1, w, wp1, s0);
                 shfl7(sm1, s0, 1);
                 shfl7(sp1, s0, 0);
-                recon_cell<PPM, false>(wm1, w, wp1, bn, gr, sm1, s0, sp1, R(0), wr, wpf);
+                recon_cell_e<PPM, false>(e, wm1, w, wp1, sm1, s0, sp1, R(0), wr, wpf);
             } else {
                 R dum[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};   // slopes: unused by PLM
                 recon_cell<RECON, false>(wm1, w, wp1, bn, gr, dum, dum, dum, R(0), wr, wpf);
