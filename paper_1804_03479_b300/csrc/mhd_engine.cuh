@@ -21,7 +21,7 @@ struct mhd_ctx {
     mhd::Boxes B;                   // kernel view (points at dbox)
     int nsm;                        // SMs of the device
     int sweep_bps;                  // persistent sweep blocks per SM
-    int bc;                         // outflow axes (bit d), one-box VL contexts; 0 = periodic
+    int bc;                         // outflow axes (bit d), one-box contexts; 0 = periodic
     void* fout;                     // [3][7][cross-section] outer-face fluxes of the outflow axes
     int fix_nl[3];                  // Dirichlet sides: fixed ghost layers at each end of axis d (0: none)
     mhd::FixedState fix[3][2];      // their states, lower and upper end
