@@ -1,0 +1,54 @@
+"""The benchmark's host logic on CPU: the reference arm (the oracle timed on
+the host) prints the contract's JSON line, and the roofline picks the
+dominant kernel from the per-group times and computes its fraction from the
+flops per face and the event time."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def test_reference_arm_prints_the_contract_line():
+    env = dict(os.environ, OMP_NUM_THREADS="2")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "1"], capture_output=True, text=True, cwd=ROOT, env=env, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 2
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    assert d["metric"] == json.load(open(os.path.join(ROOT, "BASELINE.json")))["metric"]
+
+
+def test_roofline_of_the_dominant_kernel():
+    import bench
+    n = 256 ** 3
+    steps = 10
+    # per-group totals over 10 steps (ms): the y and z corrector pencils dominate
+    groups = {"prim_cfl": 2.3, "predictor_x": 4.8, "predictor_y": 3.0, "predictor_z": 3.0, "emf1": 3.0,
+              "half_update": 5.0, "corrector_x": 6.2, "corrector_y": 4.9, "corrector_z": 4.9, "emf2": 3.0,
+              "full_update": 4.8}
+    tuned = {"pencil_mask": 7}
+    ks = bench.kernels_of(groups, tuned)
+    assert ks["corrector_pencil"] == (9.8, 2) and ks["corrector_xwarp"] == (6.2, 1)
+    pk = {"hbm_gbs": 6442.9, "src": "measured"}
+    r = bench.roofline("fp32", groups, steps, n, pk, 2032.0, tuned)
+    assert r["kernel"] == "corrector_pencil" and r["launches"] == 2 and r["bound"] == "alu"
+    per_launch_s = 9.8 / steps / 2 * 1e-3
+    want = n * bench.FLOPS_PER_FACE["corrector"]["fp32"] / per_launch_s / 1e12
+    assert abs(r["achieved"] - want) <= 1e-9 * want
+    assert abs(r["peak"] - 148 * 128 * 2 * 2.032e9 / 1e12) <= 1e-6
+    assert abs(r["frac"] - want / r["peak"]) <= 1e-12
+    assert r["traffic"] == pytest.approx(bench.TRAFFIC_PER_FACE["corrector_pencil"]["fp32"] * n)
+    # without pencils the same groups belong to the tile kernels
+    assert "corrector_tile" in bench.kernels_of(groups, {"pencil_mask": 0})
