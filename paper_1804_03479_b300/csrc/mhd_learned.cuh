@@ -361,7 +361,11 @@ __global__ void __launch_bounds__(256) k_block_features(BoxDev g, const R* __res
         const int im = wrapi(i0 - 1, g.nx), ip = wrapi(i0 + 4, g.nx);
         const int jm = wrapi(j0 - 1, g.ny), jp = wrapi(j0 + 4, g.ny);
         const int km = wrapi(k0 - 1, g.nz), kp = wrapi(k0 + 4, g.nz);
-        float mean[8], rng[8], dd[3][8], sd[8];
+        // each field's raw statistics go straight to the block's feature row
+        // and are scaled in place once the block's scales are known (arrays
+        // indexed by the field would sit in local memory)
+        float* out = feats + b * NF;
+        float mrho = 0.f, mP = 0.f;
         for (int f = 0; f < 8; f++) {
             const R* Wf = W + (long long)f * N;
             const R* bp = Wf + cell_of(g, i0, j0, k0);     // the block never wraps (sides % 4 == 0)
@@ -412,12 +416,14 @@ __global__ void __launch_bounds__(256) k_block_features(BoxDev g, const R* __res
                 const float e = v[q] - m;
                 sq += e * e;
             }
-            mean[f] = m;
-            rng[f] = mx - mn;
-            dd[0][f] = dx;
-            dd[1][f] = dy;
-            dd[2][f] = dz;
-            sd[f] = sqrtf(sq * (1.f / 64.f));
+            if (f == 0) mrho = m;
+            if (f == 4) mP = m;
+            out[f * 6 + 0] = m;
+            out[f * 6 + 1] = mx - mn;
+            out[f * 6 + 2] = dx;
+            out[f * 6 + 3] = dy;
+            out[f * 6 + 4] = dz;
+            out[f * 6 + 5] = sqrtf(sq * (1.f / 64.f));
         }
         float vabs = 0.f, b2s = 0.f;
         for (int q = 0; q < 64; q++) {
@@ -428,24 +434,20 @@ __global__ void __launch_bounds__(256) k_block_features(BoxDev g, const R* __res
             b2s += bx * bx + by * by + bz * bz;
         }
         const float inv = 1.f / 64.f;
-        const float rho = mean[0], P = fmaxf(mean[4], 1e-30f);
+        const float rho = mrho, P = fmaxf(mP, 1e-30f);
         const float b2 = b2s * inv;
         const float cref = sqrtf((gam * P + b2) / fmaxf(rho, 1e-30f));
         const float bref = sqrtf(b2 + P);
-        const float scale[8] = {rho, cref, cref, cref, P, bref, bref, bref};
-        float* out = feats + b * NF;
 #pragma unroll
         for (int f = 0; f < 8; f++) {
-            const float is = 1.f / fmaxf(scale[f], 1e-30f);
-            float m0 = mean[f] * is;
+            const float sc = f == 0 ? rho : (f < 4 ? cref : (f == 4 ? P : bref));
+            const float is = 1.f / fmaxf(sc, 1e-30f);
+            float m0 = out[f * 6 + 0] * is;
             if (f == 0) m0 = fminf(fmaxf(log10f(2.f * P / fmaxf(b2, 1e-30f)), -6.f), 6.f) / 6.f;
             if (f == 4) m0 = vabs * inv / cref;
             out[f * 6 + 0] = m0;
-            out[f * 6 + 1] = rng[f] * is;
-            out[f * 6 + 2] = dd[0][f] * is;
-            out[f * 6 + 3] = dd[1][f] * is;
-            out[f * 6 + 4] = dd[2][f] * is;
-            out[f * 6 + 5] = sd[f] * is;
+#pragma unroll
+            for (int k = 1; k < 6; k++) out[f * 6 + k] = out[f * 6 + k] * is;
         }
     }
 }
