@@ -504,10 +504,38 @@ def e2e(torch, mhd, st, prec, scheme, K, stream, nstreams=2):
             c[0].free()
         return n * each * ns / el, each * ns
 
+    def link(reps=6):
+        """the same bytes copied in both directions at once with no step
+        between them: the host link's bound on this metric"""
+        dU, dB = torch.empty_like(Uh, device="cuda"), torch.empty_like(Bh, device="cuda")
+        sU, sB = torch.empty_like(dU), torch.empty_like(dB)
+        oU, oB = torch.empty_like(Uh).pin_memory(), torch.empty_like(Bh).pin_memory()
+        up, down = torch.cuda.Stream(), torch.cuda.Stream()
+
+        def once():
+            with torch.cuda.stream(up):
+                dU.copy_(Uh, non_blocking=True)
+                dB.copy_(Bh, non_blocking=True)
+            with torch.cuda.stream(down):
+                oU.copy_(sU, non_blocking=True)
+                oB.copy_(sB, non_blocking=True)
+
+        once()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            once()
+        torch.cuda.synchronize()
+        el = (time.perf_counter() - t0) / reps
+        del dU, dB, sU, sB
+        return n / el, 2 * nbytes / el / 1e9
+
     serial, _ = run(1, K)
     value, done = run(nstreams, K) if nstreams > 1 else (serial, K)
+    bound, gbs = link()
     return {"value": value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
             "steps": done, "streams": nstreams, "one_stream_value": serial,
+            "copy_only_bound": bound, "link_gbs_both_directions": gbs, "frac_of_copy_bound": value / bound,
             "path": "mhd_set_state(host) + mhd_advance(1) + mhd_get_state(host), "
                     f"{nstreams} contexts on their own streams and host threads"}
 
