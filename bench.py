@@ -67,8 +67,8 @@ FLOPS_PER_FACE = {"corrector": {"fp32": 657.0, "fp64": 657.0, "mixed": 657.0},
 # 208.2 MB, x-warp corrector 219.4 MB; FP64 pencil corrector 240.0 MB at
 # 128^3), scaled to other sizes by faces; a kernel changed since its capture
 # has none.
-TRAFFIC_PER_FACE = {"corrector_pencil": {"fp32": 57.1, "fp64": 114.4}, "predictor_pencil": {"fp32": 50.8},
-                    "corrector_xwarp": {"fp32": 53.6}}
+TRAFFIC_PER_FACE = {"corrector_pencil": {"fp32": 58.5, "fp64": 114.4}, "predictor_pencil": {"fp32": 51.1},
+                    "corrector_xwarp": {"fp32": 54.7}}
 
 
 def peaks():

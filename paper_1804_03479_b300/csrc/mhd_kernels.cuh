@@ -27,6 +27,22 @@ constexpr int SWEEP_THREADS = 256;
 constexpr int TL_MAX = 16;         // largest tile extent along the second tiled axis
 constexpr int PENCIL_THREADS = 128;
 
+// Resident blocks per SM asked of the register allocator for the pencil and
+// x-warp sweeps (0: no bound).  Unbounded, the FP32 Roe sweeps take 123-128
+// registers with PLM (4 blocks of 128 threads per SM) and 157-167 with PPM
+// (3 blocks).  At 96 registers (5 blocks) for PLM, and at 128 (4 blocks) for
+// the PPM tracing pencils of CTU, they spill at most 148 bytes a thread and
+// the extra warps hide more latency than the spills cost (measured at 256^3;
+// the VL PPM sweeps lose 1 % at 4 blocks and stay unbounded).  The HLLD and
+// HLLE sweeps already fit 5 blocks or more, and the FP64 sweeps (194-230
+// registers) are bound by the FP64 rate.
+template <class R, int RECON, int SOLVER, int MODE>
+constexpr int sweep_min_blocks()
+{
+    if (sizeof(R) != 4 || SOLVER != ROE) return 0;
+    return RECON == PPM ? (MODE == 2 ? 4 : 0) : 5;
+}
+
 struct BoxDev {
     int nx, ny, nz, pad;
     long long off;      // first cell of the box in the batch arrays
@@ -561,7 +577,7 @@ __device__ __forceinline__ void copy7(R d[7], const R s[7])
 // each owned cell's lower and upper traced states go to WMg / WPg, and the
 // face flux uses the previous cell's upper and this cell's lower state.
 template <class R, int RECON, int SOLVER, int MODE, class TE, int D>
-__global__ void __launch_bounds__(PENCIL_THREADS) k_pencil(Boxes B, const R* __restrict__ W,
+__global__ void __launch_bounds__(PENCIL_THREADS, (sweep_min_blocks<R, RECON, SOLVER, MODE>())) k_pencil(Boxes B, const R* __restrict__ W,
                                                            const TE* __restrict__ Bd, R* __restrict__ F, double gam,
                                                            const int* __restrict__ seg_list = nullptr,
                                                            const int* __restrict__ seg_count = nullptr,
@@ -784,7 +800,7 @@ __device__ __forceinline__ int box_of_row(const Boxes& B, long long t)
 // item_count a warp takes one listed segment instead (the learned
 // selector's lists, whose cheap and full kernels share one decomposition).
 template <class R, int RECON, int SOLVER, int MODE, class TE>
-__global__ void __launch_bounds__(PENCIL_THREADS) k_xwarp(Boxes B, const R* __restrict__ W,
+__global__ void __launch_bounds__(PENCIL_THREADS, (sweep_min_blocks<R, RECON, SOLVER, MODE>())) k_xwarp(Boxes B, const R* __restrict__ W,
                                                           const TE* __restrict__ Bd, R* __restrict__ F, double gam,
                                                           int dslot, const int* __restrict__ item_list = nullptr,
                                                           const int* __restrict__ item_count = nullptr)
