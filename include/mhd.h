@@ -210,7 +210,10 @@ mhd_status mhd_get_dirichlet(mhd_ctx* ctx, int axis, int* nlayers);
 /* Pencil sweeps: on every axis d with bit d of pencil_mask set, the face
  * sweeps (VL predictor and corrector; CTU tracing sweeps) keep the cells
  * around each face in registers (no shared memory): one thread walks a
- * segment of pencil_len consecutive faces of a grid line.  For VL the x
+ * segment of pencil_len consecutive faces of a grid line.  For CTU the bits
+ * of y and z also select the pencil form of the transverse correction and
+ * corrector solve (each cell's transverse flux differences loaded once for
+ * both of its traced states).  For VL the x
  * axis runs by warps instead: the 32 lanes of a warp hold 32 consecutive
  * cells of a row and exchange neighbour states by shuffles (27 to 31 faces
  * per warp).  The results are those of the tile sweeps (the same

@@ -147,12 +147,24 @@ void fix_layers(mhd_ctx* c, const StateP<TU, TE>& s, cudaStream_t st)
     }
 }
 
-// CTU steps 5-6 along axis D (periodic or outflow instantiation)
+// CTU steps 5-6 along axis D (periodic or outflow instantiation): by
+// pencils along y and z where the pencil mask has the axis, else per cell
 template <class R, int SOLVER, class TE, int D>
 void ctu_correct_axis(mhd_ctx* c, const Boxes& g, const R* WM, const R* WP, const R* W, const R* F1, const TE* BhD,
                       R* F2, double gam, const R* fo1, int cs, R* fo2, cudaStream_t st)
 {
     const long long o = (long long)D * 7 * g.N;
+    if constexpr (D > 0) {
+        if (c->pencil_mask >> D & 1) {
+            if (c->bc)
+                k_ctu_pencil<R, SOLVER, TE, D, true><<<pencil_grid(c, D), PENCIL_THREADS, 0, st>>>(
+                    g, WM + o, WP + o, W, F1, BhD, F2 + o, c->dtc, gam, fo1, cs, fo2);
+            else
+                k_ctu_pencil<R, SOLVER, TE, D><<<pencil_grid(c, D), PENCIL_THREADS, 0, st>>>(
+                    g, WM + o, WP + o, W, F1, BhD, F2 + o, c->dtc, gam);
+            return;
+        }
+    }
     if (c->bc)
         k_ctu_correct<R, SOLVER, TE, D, true><<<c->cell_grid, CELL_THREADS, 0, st>>>(
             g, WM + o, WP + o, W, F1, BhD, F2 + o, c->dtc, gam, fo1, cs, fo2);
