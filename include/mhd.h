@@ -223,6 +223,24 @@ mhd_status mhd_get_dirichlet(mhd_ctx* ctx, int axis, int* nlayers);
 mhd_status mhd_set_sweep_pencils(mhd_ctx* ctx, int pencil_mask, int pencil_len);
 mhd_status mhd_get_sweep_pencils(mhd_ctx* ctx, int* pencil_mask, int* pencil_len);
 
+/* Staging of the edge-field kernel (Sec. 2, Eqs. 13-14; the corner-averaged
+ * edge fields of both stages).  mode 0 (the default): each thread of the
+ * kernel loads its staged cell of every plane (32 x 16 cells per block, two
+ * blocks per SM).  mode 1: the planes are staged by the tensor memory
+ * accelerator where the context allows it -- bulk tensor copies of whole
+ * field planes into a ring of three shared-memory plane slots per block
+ * (32 x 8 cells, three blocks per SM), refilled by a producer warp while
+ * the block computes.  That needs one box, FP32 or MIXED precision, nx a
+ * multiple of 4, nx >= 40 and ny >= 9; elsewhere mode 1 falls back to the
+ * per-thread loads.  Both forms give the same edge fields bit for bit; on
+ * the B300 the per-thread form is the faster (0.30 against 0.45 ms per
+ * launch at 256^3).  mode in {0, 1}, else MHD_EINVAL.  mhd_get_emf_staging
+ * reports the requested mode and whether the tensor copies are in use
+ * (active = 1).  A plane wait that gives up (after about 2 s) sets a device
+ * flag, and the next call that reads the device flags returns MHD_ECUDA. */
+mhd_status mhd_set_emf_staging(mhd_ctx* ctx, int mode);
+mhd_status mhd_get_emf_staging(mhd_ctx* ctx, int* mode, int* active);
+
 /* Wait for all work queued on the context's stream; reports recorded
  * device-side anomalies. */
 mhd_status mhd_sync(mhd_ctx* ctx);

@@ -4,6 +4,7 @@
 #include <stdlib.h>
 #include <string.h>
 #include <cufft.h>
+#include <cudaTypedefs.h>
 #include "mhd_engine.cuh"
 
 using namespace mhd;
@@ -41,9 +42,10 @@ static void release(mhd_ctx* c)
                     c->F1, c->F2, c->E, c->Bh[0], c->Bh[1], c->Bh[2], c->WM, c->WP, c->stage,
                     c->dt, c->dtc, c->smax, c->smax_part, c->bad, c->nfloor, c->part, c->diag, c->dbox, c->sel_feats,
                     c->sel_flags, c->sel_cnt, c->sel_list[0], c->sel_list[1], c->sel_list[2], c->sel_list[3],
-                    c->sel_list[4], c->sel_list[5], c->sel_list[6], c->sel_list[7], c->fout};
+                    c->sel_list[4], c->sel_list[5], c->sel_list[6], c->sel_list[7], c->fout, c->perr};
     for (void* p : bufs)
         if (p) cudaFree(p);
+    free(c->tmaps);
     if (c->have_graph) cudaGraphExecDestroy(c->gexec);
     if (c->prof_ev) {
         for (int q = 0; q < c->prof_cap * (MHD_NGROUPS + 1); q++) cudaEventDestroy(c->prof_ev[q]);
@@ -58,6 +60,84 @@ static cudaError_t dalloc(mhd_ctx* c, void** p, size_t bytes)
     cudaError_t e = cudaMalloc(p, bytes);
     if (e == cudaSuccess) c->bytes += (long long)bytes;
     return e;
+}
+
+// the driver's tensor-map encoder, looked up once through the runtime (no
+// link against the driver library)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// nf fields of a one-box array of 4-byte values as a 4-D tensor
+// (nx, ny, nz, nf), copied in boxes of one staged plane of bf fields
+static bool encode_planes(CUtensorMap* m, void* base, const BoxDev& b, int nf, int bf)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || !base) return false;
+    const cuuint64_t dim[4] = {(cuuint64_t)b.nx, (cuuint64_t)b.ny, (cuuint64_t)b.nz, (cuuint64_t)nf};
+    const cuuint64_t stride[3] = {(cuuint64_t)b.nx * 4, (cuuint64_t)b.nx * b.ny * 4, (cuuint64_t)b.n * 4};
+    const cuuint32_t box[4] = {(cuuint32_t)TMA_X, (cuuint32_t)TmaPlane<TMA_TY>::Y, 1, (cuuint32_t)bf};
+    const cuuint32_t step[4] = {1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dim, stride, box, step, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// k_emf_tma where the context allows it: one box, 4-byte arithmetic, rows a
+// multiple of 16 bytes (nx % 4 == 0; every stride of the tensors is then one
+// too) and planes at least one staged plane wide; else k_emf
+static void setup_emf_tma(mhd_ctx* c)
+{
+    const int was = c->emf_tma;
+    c->emf_tma = 0;
+    if (c->emf_stage_req && c->nbox == 1 && c->szr == 4) {
+        const BoxDev& b = c->hbox[0];
+        if (b.nx % 4 == 0 && b.nx >= TMA_X && b.ny >= TmaPlane<TMA_TY>::Y) {
+            if (!c->tmaps) c->tmaps = (CUtensorMap*)aligned_alloc(64, 6 * sizeof(CUtensorMap));
+            // W, Wh: 3 fields a copy (v, B); F1, F2: the mass flux, then the two B fluxes
+            bool ok = c->tmaps && encode_planes(&c->tmaps[0], c->W, b, 8, 3) &&
+                      encode_planes(&c->tmaps[1], c->Wh, b, 8, 3) && encode_planes(&c->tmaps[2], c->F1, b, 21, 1) &&
+                      encode_planes(&c->tmaps[3], c->F1, b, 21, 2);
+            if (ok && c->F2)
+                ok = encode_planes(&c->tmaps[4], c->F2, b, 21, 1) && encode_planes(&c->tmaps[5], c->F2, b, 21, 2);
+            else if (ok) {
+                c->tmaps[4] = c->tmaps[2];
+                c->tmaps[5] = c->tmaps[3];
+            }
+            // resident blocks per SM, by this unit's instance (the others have
+            // the same resources and get the same attribute where they launch)
+            int per = 0;
+            ok = ok &&
+                 cudaFuncSetAttribute(k_emf_tma<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)emf_tma_smem_bytes()) == cudaSuccess &&
+                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_emf_tma<float>, EMF_TMA_THREADS,
+                                                               emf_tma_smem_bytes()) == cudaSuccess &&
+                 per >= 1;
+            if (ok) {
+                const long long nt = (long long)((b.nx + ETX - 1) / ETX) * ((b.ny + TMA_TY - 1) / TMA_TY) *
+                                     ((b.nz + EZC - 1) / EZC);
+                const long long cap = (long long)per * c->nsm;
+                c->emf_tma_grid = (int)(nt < cap ? nt : cap);
+                c->emf_tma = 1;
+            }
+        }
+    }
+    if (c->emf_tma != was && c->have_graph) {   // a captured step holds the other kernel
+        cudaGraphExecDestroy(c->gexec);
+        c->have_graph = false;
+    }
 }
 
 // tile prefix sums of the box table for tile length tl; uploads the table
@@ -205,8 +285,11 @@ static mhd_status init_common(int nbox, const mhd_grid* grids, double gamma, con
     if (e == cudaSuccess) e = dalloc(c, (void**)&c->dbox, sizeof(BoxDev) * nbox);
     c->B.b = c->dbox;
     if (e == cudaSuccess) e = cudaMemsetAsync(c->bad, 0xff, sizeof(unsigned long long), c->stream);
+    if (e == cudaSuccess) e = dalloc(c, (void**)&c->perr, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->perr, 0, sizeof(unsigned), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->dt, 0, sizeof(double) * nbox, c->stream);
     if (e == cudaSuccess) e = layout_tiles(c, 8);
+    c->emf_stage_req = 0;   // per-thread loads: faster on the B300 (see mhd_set_emf_staging)
     if (e != cudaSuccess) {
         g_init_err = e == cudaErrorMemoryAllocation ? "device allocation failed" : cudaGetErrorString(e);
         mhd_status s = e == cudaErrorMemoryAllocation ? MHD_ENOMEM : MHD_ECUDA;
@@ -235,8 +318,11 @@ extern "C" int mhd_nbox(mhd_ctx* c) { return c ? c->nbox : 0; }
 static mhd_status check_device_flags(mhd_ctx* c)
 {
     unsigned long long bad = ~0ull;
+    unsigned perr = 0;
     CK(cudaMemcpyAsync(&bad, c->bad, sizeof(bad), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&perr, c->perr, sizeof(perr), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    if (perr) return fail(c, MHD_ECUDA, "a staged-plane wait of the edge-field kernel gave up (flags %u)", perr);
     if (bad != ~0ull) return fail(c, MHD_ENEGATIVE, "rho <= 0 or P <= 0 in cell %llu", bad);
     return c->sticky;
 }
@@ -699,6 +785,23 @@ extern "C" mhd_status mhd_get_sweep_pencils(mhd_ctx* c, int* pencil_mask, int* p
     return MHD_OK;
 }
 
+extern "C" mhd_status mhd_set_emf_staging(mhd_ctx* c, int mode)
+{
+    if (!c) return MHD_EINVAL;
+    if (mode != 0 && mode != 1) return fail(c, MHD_EINVAL, "mode must be 0 or 1");
+    c->emf_stage_req = mode;
+    setup_emf_tma(c);
+    return MHD_OK;
+}
+
+extern "C" mhd_status mhd_get_emf_staging(mhd_ctx* c, int* mode, int* active)
+{
+    if (!c || !mode || !active) return fail(c, MHD_EINVAL, "null pointer");
+    *mode = c->emf_stage_req;
+    *active = c->emf_tma;
+    return MHD_OK;
+}
+
 // time `reps` directly launched steps of the current configuration
 static mhd_status time_steps(mhd_ctx* c, int reps, float* ms)
 {
@@ -845,6 +948,7 @@ extern "C" void mhd_clear_error(mhd_ctx* c)
 {
     if (!c) return;
     cudaMemsetAsync(c->bad, 0xff, sizeof(unsigned long long), c->stream);
+    cudaMemsetAsync(c->perr, 0, sizeof(unsigned), c->stream);
     cudaStreamSynchronize(c->stream);
     c->sticky = MHD_OK;
     strcpy(c->err, "no error");

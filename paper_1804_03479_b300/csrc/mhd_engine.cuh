@@ -4,6 +4,7 @@
 #include <stdio.h>
 #include "mhd.h"
 #include "mhd_kernels.cuh"
+#include "mhd_tma.cuh"
 
 struct mhd_ctx;
 struct mhd_mlp;
@@ -26,6 +27,12 @@ struct mhd_ctx {
     int fix_nl[3];                  // Dirichlet sides: fixed ghost layers at each end of axis d (0: none)
     mhd::FixedState fix[3][2];      // their states, lower and upper end
     int pencil_mask;                // VL sweeps by pencils on the axes of these bits
+    int emf_stage_req;              // edge fields: 1 = planes by the tensor memory accelerator where eligible
+    int emf_tma;                    // 1 when the context runs k_emf_tma
+    int emf_tma_grid;               // its grid: min(SMs, tiles)
+    CUtensorMap* tmaps;             // [6] 64-byte aligned 4-D tensors of k_emf_tma: W, Wh (3-field copies),
+                                    // F1 (1-, 2-field copies), F2 (the same)
+    unsigned* perr;                 // device: bit 0 = a staged-plane wait of k_emf_tma gave up
     int pencil_len;                 // faces per pencil-segment thread
     size_t szu, sze, szr;          // element sizes: rho/M storage, e/B storage, arithmetic
     void* rho;
@@ -147,6 +154,23 @@ void fix_layers(mhd_ctx* c, const StateP<TU, TE>& s, cudaStream_t st)
     }
 }
 
+// the edge fields of one stage: by k_emf_tma when the context runs it (FP32
+// arithmetic, one box), else by k_emf
+template <class R>
+void launch_emf(mhd_ctx* c, const Boxes& g, const R* F, const R* W, R* E, cudaStream_t st)
+{
+    if constexpr (sizeof(R) == 4) {
+        if (c->emf_tma) {
+            const CUtensorMap& mw = c->tmaps[W == (const R*)c->W ? 0 : 1];
+            const int f = F == (const R*)c->F1 ? 2 : 4;
+            k_emf_tma<R><<<c->emf_tma_grid, EMF_TMA_THREADS, emf_tma_smem_bytes(), st>>>(
+                g, mw, c->tmaps[f], c->tmaps[f + 1], F, W, E, c->perr);
+            return;
+        }
+    }
+    k_emf<R><<<emf_grid<R>(c), EMF_THREADS, emf_smem_bytes<R>(), st>>>(g, F, W, E);
+}
+
 // CTU steps 5-6 along axis D (periodic or outflow instantiation): by
 // pencils along y and z where the pencil mask has the axis, else per cell
 template <class R, int SOLVER, class TE, int D>
@@ -214,7 +238,7 @@ void run_step(mhd_ctx* c, bool device_dt)
                     g, d, W, s.b[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam);
             prof_mark(c, 2 + d);
         }
-        k_emf<R><<<emf_grid<R>(c), EMF_THREADS, emf_smem_bytes<R>(), st>>>(g, F1, W, E);
+        launch_emf<R>(c, g, F1, W, E, st);
         prof_mark(c, 5);
         const int cs = c->bc ? cross_size(c->hbox[0].nx, c->hbox[0].ny, c->hbox[0].nz) : 0;
         for (int d = 0; d < 3; d++)
@@ -241,7 +265,7 @@ void run_step(mhd_ctx* c, bool device_dt)
                     g, d, Wh, Bh[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam);
             prof_mark(c, 7 + d);
         }
-        k_emf<R><<<emf_grid<R>(c), EMF_THREADS, emf_smem_bytes<R>(), st>>>(g, F1, Wh, E);
+        launch_emf<R>(c, g, F1, Wh, E, st);
         prof_mark(c, 10);
         for (int d = 0; d < 3; d++)
             if (c->bc >> d & 1)
@@ -277,7 +301,7 @@ void run_step(mhd_ctx* c, bool device_dt)
             prof_mark(c, 2 + d);
         }
         // steps 3-4: edge E at t^n, dt/2 update of face B and cell state
-        k_emf<R><<<emf_grid<R>(c), EMF_THREADS, emf_smem_bytes<R>(), st>>>(g, F1, W, E);
+        launch_emf<R>(c, g, F1, W, E, st);
         prof_mark(c, 5);
         // outflow: stage-1 fluxes through the outer faces (the last cells'
         // own traced states) into the first half of the outer-flux buffer;
@@ -304,7 +328,7 @@ void run_step(mhd_ctx* c, bool device_dt)
         ctu_correct_axis<R, SOLVER, TE, 2>(c, g, WM, WP, W, F1, Bh[2], F2, gam, fo1, cs, fo2, st);
         prof_mark(c, 9);
         // steps 7-8
-        k_emf<R><<<emf_grid<R>(c), EMF_THREADS, emf_smem_bytes<R>(), st>>>(g, F2, Wh, E);
+        launch_emf<R>(c, g, F2, Wh, E, st);
         prof_mark(c, 10);
         if (c->bc)
             k_full<R, TU, TE, true><<<nb, CELL_THREADS, 0, st>>>(g, s, F2, E, c->dtc, fo2, cs);
@@ -322,6 +346,11 @@ inline cudaError_t allow_smem()
     size_t b = sweep_smem_bytes<R>(RECON, TL_MAX);
     cudaError_t e = cudaFuncSetAttribute(k_emf<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)emf_smem_bytes<R>());
+    if constexpr (sizeof(R) == 4) {
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_emf_tma<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)emf_tma_smem_bytes());
+    }
     if (e != cudaSuccess || MODE == 0) return e;
     if constexpr (MODE == 2) {   // the CTU tracing sweeps run with the axis fixed at compile time
         e = cudaFuncSetAttribute(k_sweep<R, RECON, SOLVER, MODE, TE, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,

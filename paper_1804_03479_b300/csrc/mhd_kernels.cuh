@@ -949,15 +949,22 @@ struct EmfStage {
     R v[ENV];
 };
 
+// the cell-centre reference field -(v x B) (both staging forms)
+template <class R>
+__device__ __forceinline__ void ref_field(R v0, R v1, R v2, R b0, R b1, R b2, R& e0, R& e1, R& e2)
+{
+    e0 = -(v1 * b2 - v2 * b1);
+    e1 = -(v2 * b0 - v0 * b2);
+    e2 = -(v0 * b1 - v1 * b0);
+}
+
 template <class R>
 __device__ __forceinline__ void emf_load(const R* __restrict__ F, const R* __restrict__ W, long long N, long long c,
                                          EmfStage<R>& s)
 {
     const R v0 = W[N + c], v1 = W[2 * N + c], v2 = W[3 * N + c];
     const R b0 = W[5 * N + c], b1 = W[6 * N + c], b2 = W[7 * N + c];
-    s.v[0] = -(v1 * b2 - v2 * b1);
-    s.v[1] = -(v2 * b0 - v0 * b2);
-    s.v[2] = -(v0 * b1 - v1 * b0);
+    ref_field(v0, v1, v2, b0, b1, b2, s.v[0], s.v[1], s.v[2]);
 #pragma unroll
     for (int d = 0; d < 3; d++) {
         const R* Fd = F + (long long)d * 7 * N;

@@ -353,7 +353,7 @@ static void run_step_learned(mhd_ctx* c, bool device_dt)
         }
         prof_mark(c, 2 + d);
     }
-    k_emf<R><<<emf_grid<R>(c), EMF_THREADS, emf_smem_bytes<R>(), st>>>(g, F1, W, E);
+    launch_emf<R>(c, g, F1, W, E, st);
     prof_mark(c, 5);
     k_half<R, float, float><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2], Wh, c->sch.pfloor);
     prof_mark(c, 6);
@@ -382,7 +382,7 @@ static void run_step_learned(mhd_ctx* c, bool device_dt)
         }
         prof_mark(c, 7 + d);
     }
-    k_emf<R><<<emf_grid<R>(c), EMF_THREADS, emf_smem_bytes<R>(), st>>>(g, F1, Wh, E);
+    launch_emf<R>(c, g, F1, Wh, E, st);
     prof_mark(c, 10);
     k_full<R, float, float><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc);
     prof_mark(c, 11);
@@ -446,10 +446,12 @@ extern "C" mhd_status mhd_set_selector(mhd_ctx* c, mhd_mlp* m)
         cudaFuncSetAttribute(k_sweep<float, PPM, HLLD, 1, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sweep_smem_bytes<float>(PPM, TL_MAX));
     }
-    // this unit's own instantiation of the edge-field kernel (its planes take
-    // more than the default 48 KB of shared memory)
+    // this unit's own instantiations of the edge-field kernels (their planes
+    // take more than the default 48 KB of shared memory)
     if (cudaFuncSetAttribute(k_emf<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)emf_smem_bytes<float>()) !=
-        cudaSuccess)
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_emf_tma<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)emf_tma_smem_bytes()) != cudaSuccess)
         return MHD_ECUDA;
     if (mhd_internal_selector_lists(c) != MHD_OK) return MHD_ENOMEM;
     c->sel = m;

@@ -34,7 +34,8 @@ EXPORTS = ["mhd_init", "mhd_set_state", "mhd_get_state", "mhd_cfl_dt", "mhd_step
            "mhd_mlp_predict", "mhd_nblocks", "mhd_block_features", "mhd_block_error", "mhd_set_selector",
            "mhd_selector_stats", "mhd_floor_count", "mhd_energies", "mhd_helicity",
            "mhd_set_sweep_pencils", "mhd_get_sweep_pencils", "mhd_set_boundary", "mhd_get_boundary",
-           "mhd_pressure_gradient", "mhd_set_dirichlet", "mhd_get_dirichlet"]
+           "mhd_pressure_gradient", "mhd_set_dirichlet", "mhd_get_dirichlet", "mhd_set_emf_staging",
+           "mhd_get_emf_staging"]
 GROUPS = ["prim_cfl", "predictor_x", "predictor_y", "predictor_z", "emf1", "half_update", "corrector_x",
           "corrector_y", "corrector_z", "emf2", "full_update"]
 
@@ -138,6 +139,8 @@ def lib():
     L.mhd_get_dirichlet.argtypes = [vp, ip, ctypes.POINTER(ip)]
     L.mhd_get_boundary.argtypes = [vp, ctypes.POINTER(ip)]
     L.mhd_get_sweep_pencils.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip)]
+    L.mhd_set_emf_staging.argtypes = [vp, ip]
+    L.mhd_get_emf_staging.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip)]
     # every entry point that returns an mhd_status; the others got their
     # restype above (long long, int, void, const char*)
     other = {"mhd_bad_cell", "mhd_clear_error", "mhd_device_bytes", "mhd_floor_count", "mhd_free",
@@ -330,6 +333,17 @@ class Solver:
     def sweep_pencils(self):
         a, b = ctypes.c_int(), ctypes.c_int()
         self._check(lib().mhd_get_sweep_pencils(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def set_emf_staging(self, mode):
+        """edge-field planes staged by the tensor memory accelerator (1, where
+        the context allows it) or by per-thread loads (0)"""
+        self._check(lib().mhd_set_emf_staging(self.h, mode))
+
+    def emf_staging(self):
+        """(requested mode, 1 if the tensor copies are in use)"""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        self._check(lib().mhd_get_emf_staging(self.h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
 
     def sweep_config(self):
