@@ -213,12 +213,12 @@ mhd_status mhd_get_dirichlet(mhd_ctx* ctx, int axis, int* nlayers);
  * segment of pencil_len consecutive faces of a grid line.  For CTU the bits
  * of y and z also select the pencil form of the transverse correction and
  * corrector solve (each cell's transverse flux differences loaded once for
- * both of its traced states).  For VL the x
- * axis runs by warps instead: the 32 lanes of a warp hold 32 consecutive
- * cells of a row and exchange neighbour states by shuffles (27 to 31 faces
- * per warp).  The results are those of the tile sweeps (the same
- * arithmetic per face).  pencil_mask in [0, 7] (0: tiles everywhere;
- * default 7 for VL contexts, 6 (y and z) for CTU, with pencil_len 32),
+ * both of its traced states).  The x axis runs by warps instead (VL; CTU
+ * where x is periodic, else by tiles): the 32 lanes of a warp hold 32
+ * consecutive cells of a row and exchange neighbour states by shuffles (27
+ * to 31 faces per warp).  The results are those of the tile sweeps (the
+ * same arithmetic per face).  pencil_mask in [0, 7] (0: tiles everywhere;
+ * default 7, with pencil_len 32),
  * pencil_len in [1, 1024], else MHD_EINVAL. */
 mhd_status mhd_set_sweep_pencils(mhd_ctx* ctx, int pencil_mask, int pencil_len);
 mhd_status mhd_get_sweep_pencils(mhd_ctx* ctx, int* pencil_mask, int* pencil_len);

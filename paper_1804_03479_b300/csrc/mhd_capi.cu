@@ -244,9 +244,9 @@ static mhd_status init_common(int nbox, const mhd_grid* grids, double gamma, con
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev);
     c->sweep_bps = 4;
-    // VL: register sweeps on every axis (pencils along y and z, warps along x;
-    // the autotuner may change it)
-    c->pencil_mask = scheme->integrator == MHD_VL ? 7 : 6;
+    // register sweeps on every axis: pencils along y and z, warps along x
+    // (CTU with an outflow x axis: tiles along x); the autotuner may change it
+    c->pencil_mask = 7;
     c->pencil_len = 32;
     c->cell_grid = (int)(vb < 16LL * c->nsm ? vb : 16LL * c->nsm);
     if (c->cell_grid < 1) c->cell_grid = 1;

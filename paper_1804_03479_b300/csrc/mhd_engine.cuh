@@ -281,9 +281,13 @@ void run_step(mhd_ctx* c, bool device_dt)
         R* WM = (R*)c->WM;
         R* WP = (R*)c->WP;
         // CTU steps 1-2: traced states (+ source terms) and their fluxes, by
-        // pencils on the axes of the pencil mask, else by tiles
+        // pencils on y and z and warps on x (x periodic) where the pencil
+        // mask has the axis, else by tiles
         for (int d = 0; d < 3; d++) {
-            if (c->pencil_mask >> d & 1)
+            if ((c->pencil_mask & 1) && d == 0 && !(c->bc & 1))
+                k_xwarp<R, RECON, SOLVER, 2, TE><<<xrow_grid(c), PENCIL_THREADS, 0, st>>>(
+                    g, W, s.b[0], F1, gam, XW<RECON, 2>::slot, nullptr, nullptr, WM, WP, c->dtc);
+            else if ((c->pencil_mask >> d & 1) && d > 0)
                 launch_pencil<R, RECON, SOLVER, 2, TE>(d, pencil_grid(c, d), st, g, W, s.b[d],
                                                        F1 + (long long)d * 7 * n, gam, nullptr, nullptr,
                                                        WM + (long long)d * 7 * n, WP + (long long)d * 7 * n, c->dtc);

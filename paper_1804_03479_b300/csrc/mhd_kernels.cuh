@@ -561,6 +561,28 @@ __device__ __forceinline__ long long pcell(const Pencil& p, int i)
     return p.base + (long long)bidx(i, p.n, p.out) * p.stride;
 }
 
+// CTU tracing (Sec. 3.2, steps 1-2): the dB_n/dn source terms of a cell
+// (state w0, cell-centre B_n bn) over dt/2, added to both traced states;
+// dbn = (B_n(upper face) - B_n(lower face)) / dx
+template <class R>
+__device__ __forceinline__ void trace_source(const R w0[7], R bn, R dbn, R hdt, R gm1, R wm[7], R wp[7])
+{
+    R vb = w0[1] * bn + w0[2] * w0[5] + w0[3] * w0[6];
+    R src[7] = {R(0), bn / w0[0], w0[5] / w0[0], w0[6] / w0[0], -gm1 * vb, w0[2], w0[3]};
+#pragma unroll
+    for (int m = 0; m < 7; m++) {
+        wm[m] = wm[m] + hdt * src[m] * dbn;
+        wp[m] = wp[m] + hdt * src[m] * dbn;
+    }
+}
+
+// (B_n(c1) - B_n(c0)) / dx of the face field, in the arithmetic type
+template <class R, class TE>
+__device__ __forceinline__ R face_gradient(const TE* __restrict__ Bd, long long c0, long long c1, const BoxDev& g)
+{
+    return sizeof(R) == 8 ? R((double)(Bd[c1] - Bd[c0]) / g.dx) : R(Bd[c1] - Bd[c0]) * R(g.inv_dx);
+}
+
 template <class R>
 __device__ __forceinline__ void copy7(R d[7], const R s[7])
 {
@@ -615,15 +637,7 @@ __global__ void __launch_bounds__(PENCIL_THREADS, (sweep_min_blocks<R, RECON, SO
     // MODE 2: the dB_n/dn source terms of cell i (state w0, cell-centre B_n
     // bn) over dt/2, added to both traced states
     auto trace_src = [&](int i, const R w0[7], R bn, R wm[7], R wp[7]) {
-        const long long c0 = pcell(p, i), c1 = pcell(p, i + 1);
-        R dbn = sizeof(R) == 8 ? R((double)(Bd[c1] - Bd[c0]) / g.dx) : R(Bd[c1] - Bd[c0]) * R(g.inv_dx);
-        R vb = w0[1] * bn + w0[2] * w0[5] + w0[3] * w0[6];
-        R src[7] = {R(0), bn / w0[0], w0[5] / w0[0], w0[6] / w0[0], -gm1 * vb, w0[2], w0[3]};
-#pragma unroll
-        for (int m = 0; m < 7; m++) {
-            wm[m] = wm[m] + hdt * src[m] * dbn;
-            wp[m] = wp[m] + hdt * src[m] * dbn;
-        }
+        trace_source(w0, bn, face_gradient<R>(Bd, pcell(p, i), pcell(p, i + 1), g), hdt, gm1, wm, wp);
     };
     R f[7];
     if (MODE == 0) {
@@ -799,12 +813,22 @@ __device__ __forceinline__ int box_of_row(const Boxes& B, long long t)
 // cell loaded while the current one is computed.  With item_list /
 // item_count a warp takes one listed segment instead (the learned
 // selector's lists, whose cheap and full kernels share one decomposition).
+//
+// MODE 2 (CTU steps 1-2, x periodic): the lanes reconstruct with tracing and
+// add the dB_n/dn source terms, as the tracing pencils do; each face lane
+// writes its cell's traced lower and upper states to WMg / WPg.  (At a lower
+// outflow side the lanes left of x = 0 would see a clamped stencil, where the
+// CTU lead-in is cell 0 with its own stencil and source term; such boxes
+// keep the tile sweep along x.)
 template <class R, int RECON, int SOLVER, int MODE, class TE>
 __global__ void __launch_bounds__(PENCIL_THREADS, (sweep_min_blocks<R, RECON, SOLVER, MODE>())) k_xwarp(Boxes B, const R* __restrict__ W,
                                                           const TE* __restrict__ Bd, R* __restrict__ F, double gam,
                                                           int dslot, const int* __restrict__ item_list = nullptr,
-                                                          const int* __restrict__ item_count = nullptr)
+                                                          const int* __restrict__ item_count = nullptr,
+                                                          R* __restrict__ WMg = nullptr, R* __restrict__ WPg = nullptr,
+                                                          const DtBox* __restrict__ dtb = nullptr)
 {
+    constexpr bool TR = MODE == 2;
     constexpr int LEAD = XW<RECON, MODE>::lead;
     const int FW = xw_faces(dslot);
     const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -836,6 +860,8 @@ __global__ void __launch_bounds__(PENCIL_THREADS, (sweep_min_blocks<R, RECON, SO
     const long long row = B.b[bi].off + ((long long)k * B.b[bi].ny + j) * nx;
     const long long N = B.N;
     const R gr = R(gam), gm1 = R(gam - 1.0);
+    const R dtdx = TR ? DtOf<R>::dtdx(dtb[bi]) : R(0);
+    const R hdt = TR ? DtOf<R>::hdt(dtb[bi]) : R(0);
     const bool face = lane >= LEAD && lane < LEAD + FW;
     R w[7], bn, f[7];
     load_rot(W, N, row + bidx(sg0 * FW - LEAD + lane, nx, xout), 0, w, bn);
@@ -860,10 +886,21 @@ __global__ void __launch_bounds__(PENCIL_THREADS, (sweep_min_blocks<R, RECON, SO
                 char_slope_e(e, wm1, w, wp1, s0);
                 shfl7(sm1, s0, 1);
                 shfl7(sp1, s0, 0);
-                recon_cell_e<PPM, false>(e, wm1, w, wp1, sm1, s0, sp1, R(0), wr, wpf);
+                recon_cell_e<PPM, TR>(e, wm1, w, wp1, sm1, s0, sp1, dtdx, wr, wpf);
             } else {
                 R dum[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};   // slopes: unused by PLM
-                recon_cell<RECON, false>(wm1, w, wp1, bn, gr, dum, dum, dum, R(0), wr, wpf);
+                recon_cell<RECON, TR>(wm1, w, wp1, bn, gr, dum, dum, dum, dtdx, wr, wpf);
+            }
+            if (TR) {
+                trace_source(w, bn, face_gradient<R>(Bd, ci, row + bidx(xi + 1, nx, xout), B.b[bi]), hdt, gm1, wr,
+                             wpf);
+                if (face && xi < nx) {
+#pragma unroll
+                    for (int m = 0; m < 7; m++) {
+                        WMg[(long long)m * N + ci] = wr[m];
+                        WPg[(long long)m * N + ci] = wpf[m];
+                    }
+                }
             }
             shfl7(wl, wpf, 1);                       // the "+" state of the cell below
         }

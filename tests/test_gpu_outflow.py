@@ -67,6 +67,16 @@ def test_outflow_fp64_parity_sweep_forms(M, sweeps):
     parity(M, st.U, st.B, st.dx, st.gamma, ("vl", "ppm", "roe"), 7, 3, sweeps=sweeps)
 
 
+@pytest.mark.parametrize("bc,sweeps", [(6, (7, 16)), (2, (7, 32)), (7, (7, 16)), (5, (1, 8))])
+@pytest.mark.parametrize("scheme", [("ctu", "plm", "roe"), ("ctu", "ppm", "hlld")])
+def test_outflow_fp64_parity_ctu_sweep_forms(M, bc, sweeps, scheme):
+    """CTU with the x bit in the pencil mask: tracing by warps along x where
+    x is periodic (bc 6, 2), by tiles where it is an outflow axis (bc 7, 5);
+    several warp segments per row (nx = 64)"""
+    st = I.open_box((64, 20, 18), seed=13)
+    parity(M, st.U, st.B, st.dx, st.gamma, scheme, bc, 3, sweeps=sweeps)
+
+
 @pytest.mark.parametrize("axis", [0, 1, 2])
 def test_outflow_tube_waves_leave(M, axis):
     """an MHD Riemann problem (Table 1, RJ2a) centred in a 160-cell line with

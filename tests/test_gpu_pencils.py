@@ -64,6 +64,14 @@ def test_ctu_tracing_pencils_fp64_parity(M, scheme, mask, plen):
     parity(M, st, scheme, mask, plen, 3)
 
 
+@pytest.mark.parametrize("scheme", [("ctu", "plm", "roe"), ("ctu", "ppm", "hlld"), ("ctu", "plm", "hlle")])
+def test_ctu_xwarp_tracing_fp64_parity_long_rows(M, scheme):
+    """CTU tracing by warps along x over several warp segments per row
+    (nx = 70: 29 + 29 + 12 faces for PLM, 27 + 27 + 16 for PPM)"""
+    st = I.abc(None, kmult=1, beta=0.5, seed=7, noise=3e-2, shape=(70, 12, 10))
+    parity(M, st, scheme, 7, 16, 3)
+
+
 @pytest.mark.parametrize("mask,plen", [(0, 16), (7, 5), (6, 32), (1, 7), (7, 64)])
 def test_pencil_fp64_parity_ragged(M, mask, plen):
     st = I.abc(None, kmult=1, beta=0.5, seed=5, noise=3e-2, shape=(40, 24, 20))
@@ -131,9 +139,9 @@ def test_pencil_arguments(M):
         s.free()
     s = M.Solver(st.U.shape[1:], st.dx, st.gamma, "ctu", "plm", "roe", "fp64", 0.3)
     try:
-        assert s.sweep_pencils() == (6, 32)       # the CTU default: y and z
-        s.set_sweep_pencils(7, 16)
-        assert s.sweep_pencils() == (7, 16)
+        assert s.sweep_pencils() == (7, 32)       # the CTU default: warps on x, pencils on y and z
+        s.set_sweep_pencils(6, 16)
+        assert s.sweep_pencils() == (6, 16)
     finally:
         s.free()
 
