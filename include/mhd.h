@@ -211,9 +211,9 @@ mhd_status mhd_get_dirichlet(mhd_ctx* ctx, int axis, int* nlayers);
  * sweeps (VL predictor and corrector; CTU tracing sweeps) keep the cells
  * around each face in registers (no shared memory): one thread walks a
  * segment of pencil_len consecutive faces of a grid line.  For CTU the bits
- * of y and z also select the pencil form of the transverse correction and
- * corrector solve (each cell's transverse flux differences loaded once for
- * both of its traced states).  The x axis runs by warps instead (VL; CTU
+ * also select the register forms of the transverse correction and corrector
+ * solve (pencils on y and z, warps on a periodic x; each cell's transverse
+ * flux differences loaded once for both of its traced states).  The x axis runs by warps instead (VL; CTU
  * where x is periodic, else by tiles): the 32 lanes of a warp hold 32
  * consecutive cells of a row and exchange neighbour states by shuffles (27
  * to 31 faces per warp).  The results are those of the tile sweeps (the

@@ -172,12 +172,24 @@ void launch_emf(mhd_ctx* c, const Boxes& g, const R* F, const R* W, R* E, cudaSt
 }
 
 // CTU steps 5-6 along axis D (periodic or outflow instantiation): by
-// pencils along y and z where the pencil mask has the axis, else per cell
+// pencils along y and z and by warps along a periodic x where the pencil
+// mask has the axis, else per cell
 template <class R, int SOLVER, class TE, int D>
 void ctu_correct_axis(mhd_ctx* c, const Boxes& g, const R* WM, const R* WP, const R* W, const R* F1, const TE* BhD,
                       R* F2, double gam, const R* fo1, int cs, R* fo2, cudaStream_t st)
 {
     const long long o = (long long)D * 7 * g.N;
+    if constexpr (D == 0) {
+        if ((c->pencil_mask & 1) && !(c->bc & 1)) {   // by warps along a periodic x
+            if (c->bc)
+                k_ctu_xwarp<R, SOLVER, TE, true><<<xrow_grid(c), PENCIL_THREADS, 0, st>>>(
+                    g, WM, WP, W, F1, BhD, F2, c->dtc, gam, fo1, cs);
+            else
+                k_ctu_xwarp<R, SOLVER, TE><<<xrow_grid(c), PENCIL_THREADS, 0, st>>>(g, WM, WP, W, F1, BhD, F2,
+                                                                                   c->dtc, gam);
+            return;
+        }
+    }
     if constexpr (D > 0) {
         if (c->pencil_mask >> D & 1) {
             if (c->bc)

@@ -1640,6 +1640,54 @@ __global__ void __launch_bounds__(PENCIL_THREADS, (sizeof(R) == 4 && SOLVER == R
     }
 }
 
+// Warp form of steps 5-6 along x (x periodic), selected by bit 0 of the
+// pencil mask: one warp per grid row marches segments of 31 faces; lane l
+// holds cell x0 - 1 + l, loads its transverse flux differences once and
+// corrects both of its traced states; the corrected upper state goes to the
+// next lane by a shuffle, and lanes 1-31 solve their lower faces.  Same
+// arithmetic per state as k_ctu_correct.
+template <class R, int SOLVER, class TE, bool OUT = false>
+__global__ void __launch_bounds__(PENCIL_THREADS, (sizeof(R) == 4 && SOLVER == ROE ? 4 : 0))
+    k_ctu_xwarp(Boxes B, const R* __restrict__ WM, const R* __restrict__ WP, const R* __restrict__ W,
+                const R* __restrict__ F1, const TE* __restrict__ Bhd, R* __restrict__ F2,
+                const DtBox* __restrict__ dtb, double gam, const R* __restrict__ Fo1 = nullptr, int cs = 0)
+{
+    constexpr int FW = 31;
+    const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= B.nxr) return;                        // uniform over the warp
+    const int bi = box_of_row(B, wid);
+    BoxDev g = B.b[bi];
+    if (!OUT) g.bc = 0;     // periodic instantiation: the wrap is compiled in
+    const long long t = wid - g.xr0;
+    const int j = (int)(t % g.ny), k = (int)(t / g.ny);
+    const long long N = B.N;
+    const R gm1 = R(gam - 1.0), gr = R(gam);
+    const R r = DtOf<R>::hdtdx(dtb[bi]);
+    const int nseg = (g.nx + FW - 1) / FW;
+    for (int sg = 0; sg < nseg; sg++) {
+        const int xi = sg * FW - 1 + lane;           // this lane's cell (and the face below it)
+        const int i = wrapi(xi, g.nx);
+        const long long c = cell_of(g, i, j, k);
+        R df[2][7], w[7], wm[7], wp[7], wl[7];
+        ctu_tdiff<R, OUT, 0>(g, i, j, k, c, F1, Fo1, cs, N, df);
+        const R bnc = W[5 * N + c];
+#pragma unroll
+        for (int m = 0; m < 7; m++) w[m] = WM[(long long)m * N + c];
+        ctu_apply<R, 0>(w, bnc, df, r, gm1, wm);
+#pragma unroll
+        for (int m = 0; m < 7; m++) w[m] = WP[(long long)m * N + c];
+        ctu_apply<R, 0>(w, bnc, df, r, gm1, wp);
+        shfl7(wl, wp, 1);                            // the corrected upper state of the cell below
+        if (lane >= 1 && xi < g.nx) {
+            R f[7];
+            riemann<SOLVER>(wl, wm, R(Bhd[c]), gm1, gr, f);
+#pragma unroll
+            for (int m = 0; m < 7; m++) F2[(long long)m * N + c] = f[m];
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // a11: per virtual block: |div B| dx maximum, sum of |B_cc|^2 and sums of
 // the conserved fields; finished per box in fixed order by k_finish_diag.
