@@ -59,8 +59,14 @@ SIZES = {"fp64": (8, 8, 8), "fp32": (4, 4, 4), "mixed": (4, 8, 4)}   # (rho/M, e
 # root is a single MUFU op.  The same arithmetic runs in the FP64 build, whose
 # divides and square roots expand into FMA iterations (1125 executed FP64
 # flops per corrector face at 128^3), so these figures serve all precisions.
+# CTU: tracing = one reconstruction with characteristic tracing, the dB_n/dn
+# source terms and one Roe solve per face (the y tracing pencil, 894.6);
+# ctucorr = the transverse corrections of a cell's two traced states and one
+# Roe solve (the y correction pencil, 523.5); FP32 at 160^3 the same way.
 FLOPS_PER_FACE = {"corrector": {"fp32": 657.0, "fp64": 657.0, "mixed": 657.0},
-                  "predictor": {"fp32": 393.0, "fp64": 393.0, "mixed": 393.0}}
+                  "predictor": {"fp32": 393.0, "fp64": 393.0, "mixed": 393.0},
+                  "tracing": {"fp32": 895.0, "fp64": 895.0, "mixed": 895.0},
+                  "ctucorr": {"fp32": 524.0, "fp64": 524.0, "mixed": 524.0}}
 # DRAM bytes (read + write) per face of one sweep launch, per kernel, from
 # dram__bytes_read.sum + dram__bytes_write.sum of the ncu captures in
 # profiles/ (FP32 at 160^3: pencil corrector 233.8 MB, pencil predictor
@@ -68,7 +74,9 @@ FLOPS_PER_FACE = {"corrector": {"fp32": 657.0, "fp64": 657.0, "mixed": 657.0},
 # 128^3), scaled to other sizes by faces; a kernel changed since its capture
 # has none.
 TRAFFIC_PER_FACE = {"corrector_pencil": {"fp32": 58.5, "fp64": 114.4}, "predictor_pencil": {"fp32": 51.1},
-                    "corrector_xwarp": {"fp32": 54.7}}
+                    "corrector_xwarp": {"fp32": 54.7}, "tracing_pencil": {"fp32": 111.7},
+                    "tracing_xwarp": {"fp32": 113.6}, "ctucorr_pencil": {"fp32": 147.0},
+                    "ctucorr_xwarp": {"fp32": 146.6}}
 
 
 def peaks():
@@ -201,22 +209,28 @@ def time_variant(torch, mhd, st, prec, scheme, K, W, dist, stream, profile=True,
     return ms, groups, rec, s
 
 
-def group_bytes(prec, n):
-    """algorithmic HBM bytes of each stage of one VL step on n cells: every
+def sweep_bytes_per_face(prec, kind="vl"):
+    """algorithmic bytes per face of one sweep launch: VL (either stage) W and
+    B_n in, 7 flux components out; CTU tracing the same in, the flux and the
+    two traced states out; CTU correction both traced states, the cell's B_n,
+    the 14 transverse fluxes and the half-step face B_n in, 7 fluxes out"""
+    szu, sze, szr = SIZES[prec]
+    return {"vl": 8 * szr + sze + 7 * szr, "tracing": 8 * szr + sze + 21 * szr,
+            "ctucorr": 29 * szr + sze + 7 * szr}[kind]
+
+
+def group_bytes(prec, n, integ="vl"):
+    """algorithmic HBM bytes of each stage of one step on n cells: every
     array element a kernel needs is read once and every result written once
     (neighbour re-reads assumed to hit in cache)"""
     szu, sze, szr = SIZES[prec]
     u = 4 * szu + 4 * sze          # rho, M (TU) and e, B faces (TE)
-    sweep = 8 * szr + sze + 7 * szr    # W and B_n in, 7 flux components out
     emf = (9 + 6 + 3) * szr        # F_rho and the two E fluxes of 3 axes, v and B_cc, E out
-    return {"prim_cfl": n * (u + 8 * szr), "predictor_sweeps": 3 * n * sweep, "emf1": n * emf,
-            "half_update": n * (u + 18 * szr + 3 * sze + 8 * szr), "corrector_sweeps": 3 * n * sweep,
-            "emf2": n * emf, "full_update": n * (2 * u + 18 * szr)}
-
-
-def sweep_bytes_per_face(prec):
-    szu, sze, szr = SIZES[prec]
-    return 8 * szr + sze + 7 * szr
+    s1, s2 = ("vl", "vl") if integ == "vl" else ("tracing", "ctucorr")
+    return {"prim_cfl": n * (u + 8 * szr), "predictor_sweeps": 3 * n * sweep_bytes_per_face(prec, s1),
+            "emf1": n * emf, "half_update": n * (u + 18 * szr + 3 * sze + 8 * szr),
+            "corrector_sweeps": 3 * n * sweep_bytes_per_face(prec, s2), "emf2": n * emf,
+            "full_update": n * (2 * u + 18 * szr)}
 
 
 # state bytes per cell update when the state is read once and written once
@@ -224,11 +238,11 @@ def sweep_bytes_per_face(prec):
 STATE_BYTES = {"fp64": 128, "fp32": 64, "mixed": 96}
 
 
-def step_hbm(prec, n, ms_per_step, pk):
+def step_hbm(prec, n, ms_per_step, pk, integ="vl"):
     """the whole step against the HBM roofline, two ways: (1) the state read
     once and written once (the ceiling of a fully fused step), (2) the
     algorithmic bytes of this multi-kernel step (sum over the kernel groups)"""
-    bpc = sum(group_bytes(prec, n).values()) / n
+    bpc = sum(group_bytes(prec, n, integ).values()) / n
     gbs = bpc * n / (ms_per_step * 1e-3) / 1e9
     cups = n / (ms_per_step * 1e-3)
     ceil = pk["hbm_gbs"] * 1e9 / STATE_BYTES[prec]
@@ -257,10 +271,12 @@ def scheme_matrix(torch, mhd, st, steps, stream, pk):
     return out
 
 
-def kernels_of(groups, tuned):
+def kernels_of(groups, tuned, integ="vl"):
     """the step's launches grouped by kernel: each sweep axis belongs to the
-    tile or the pencil kernel of its stage (from the sweep configuration);
-    returns {kernel: (ms summed over its launches, launches per step)}"""
+    tile, pencil or warp kernel of its stage (from the sweep configuration;
+    CTU's stages are the tracing sweeps and the corrections, per cell where
+    the axis has no register form); returns {kernel: (ms summed over its
+    launches, launches per step)}"""
     mask = (tuned or {}).get("pencil_mask", 0) or 0
     out = {}
     for k, v in groups.items():
@@ -268,16 +284,18 @@ def kernels_of(groups, tuned):
         for st in ("predictor", "corrector"):
             if k.startswith(st + "_"):
                 d = AXES.index(k.split("_")[1])
-                name = f"{st}_{('xwarp' if d == 0 else 'pencil') if mask >> d & 1 else 'tile'}"
+                stage = st if integ == "vl" else ("tracing" if st == "predictor" else "ctucorr")
+                other = "cell" if stage == "ctucorr" else "tile"
+                name = f"{stage}_{('xwarp' if d == 0 else 'pencil') if mask >> d & 1 else other}"
         ms, cnt = out.get(name, (0.0, 0))
         out[name] = (ms + v, cnt + nl)
     return out
 
 
-def roofline(prec, groups, steps, n, pk, sm_mhz, tuned=None):
+def roofline(prec, groups, steps, n, pk, sm_mhz, tuned=None, integ="vl"):
     """dominant kernel of the step and its achieved fraction of the roofline
     that bounds it"""
-    ks = kernels_of(groups, tuned)
+    ks = kernels_of(groups, tuned, integ)
     dom = max(ks, key=lambda k: ks[k][0])
     tot, launches = ks[dom]
     ms = tot / steps
@@ -285,11 +303,11 @@ def roofline(prec, groups, steps, n, pk, sm_mhz, tuned=None):
            "ms_per_launch": ms / launches}
     sweep = dom.split("_")[0]
     fpf = FLOPS_PER_FACE.get(sweep, {}).get(prec)
-    if sweep in ("predictor", "corrector") and fpf:
+    if sweep in ("predictor", "corrector", "tracing", "ctucorr") and fpf:
         ach = n * fpf / (ms / launches * 1e-3) / 1e12          # per launch: n faces
         peak = alu_peak_tflops(prec, sm_mhz)
         tpf = TRAFFIC_PER_FACE.get(dom, {}).get(prec)
-        bpf = sweep_bytes_per_face(prec)
+        bpf = sweep_bytes_per_face(prec, {"tracing": "tracing", "ctucorr": "ctucorr"}.get(sweep, "vl"))
         hbm = n * bpf / (ms / launches * 1e-3) / 1e9
         out.update(bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
                    peak_src=f"{'FP64' if prec == 'fp64' else 'FP32'} peak derived from unit counts at {sm_mhz:.0f} MHz",
@@ -299,7 +317,7 @@ def roofline(prec, groups, steps, n, pk, sm_mhz, tuned=None):
                              "frac_of_measured": hbm / pk["hbm_gbs"]})
     else:
         stage = {"emf1": "emf1", "emf2": "emf2"}.get(dom, dom)
-        b = group_bytes(prec, n)[stage] / launches
+        b = group_bytes(prec, n, integ)[stage] / launches
         ach = b / (ms / launches * 1e-3) / 1e9
         out.update(bound="hbm", achieved=ach, peak=pk["hbm_gbs"], unit="GB/s", frac=ach / pk["hbm_gbs"],
                    peak_src=pk["src"], traffic=None, algorithmic_bytes_per_launch=b)
@@ -693,8 +711,8 @@ def main():
                    "precision": args.precision, "cfl": 0.3, "dt": "CFL on device every step",
                    "l2": "state larger than L2 (no flush)", "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
                    "device_bytes": dev_bytes, "sweep": s.tuned},
-        "roofline": roofline(args.precision, groups, rec, n, pk, sm_mhz, s.tuned) if rec else None,
-        "hbm_roofline_step": step_hbm(args.precision, n, ms / args.steps, pk),
+        "roofline": roofline(args.precision, groups, rec, n, pk, sm_mhz, s.tuned, args.integrator) if rec else None,
+        "hbm_roofline_step": step_hbm(args.precision, n, ms / args.steps, pk, args.integrator),
         "kernel_ms_per_step": {k: v / rec for k, v in stages_of(groups).items()} if rec else None,
         "sweep_ms_per_step": {k: v / rec for k, v in groups.items() if "_" in k and k.split("_")[1] in AXES}
         if rec else None,
@@ -711,8 +729,9 @@ def main():
             vv = n * kv / (msv * 1e-3)
             variants[prec] = {"value": vv, "unit": UNIT, "ms_per_step": msv / kv, "steps": kv,
                               "vs_p100_paper": vv / PAPER_P100[prec] if prec in PAPER_P100 else None,
-                              "roofline": roofline(prec, gv, recv, n, pk, sm_mhz, sv.tuned) if recv else None,
-                              "hbm_roofline_step": step_hbm(prec, n, msv / kv, pk),
+                              "roofline": roofline(prec, gv, recv, n, pk, sm_mhz, sv.tuned, args.integrator)
+                              if recv else None,
+                              "hbm_roofline_step": step_hbm(prec, n, msv / kv, pk, args.integrator),
                               "kernel_ms_per_step": {k: v / recv for k, v in stages_of(gv).items()} if recv else None,
                               "sweep": sv.tuned}
         if not args.no_matrix:

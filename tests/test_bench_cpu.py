@@ -52,3 +52,28 @@ def test_roofline_of_the_dominant_kernel():
     assert r["traffic"] == pytest.approx(bench.TRAFFIC_PER_FACE["corrector_pencil"]["fp32"] * n)
     # without pencils the same groups belong to the tile kernels
     assert "corrector_tile" in bench.kernels_of(groups, {"pencil_mask": 0})
+
+
+def test_roofline_of_a_ctu_step():
+    """CTU's stages are the tracing sweeps and the transverse corrections:
+    their own kernel names, flop counts and algorithmic bytes"""
+    import bench
+    n = 256 ** 3
+    steps = 10
+    groups = {"prim_cfl": 2.3, "predictor_x": 8.1, "predictor_y": 6.7, "predictor_z": 7.2, "emf1": 3.0,
+              "half_update": 5.0, "corrector_x": 6.4, "corrector_y": 5.9, "corrector_z": 5.8, "emf2": 3.0,
+              "full_update": 4.8}
+    tuned = {"pencil_mask": 7}
+    ks = bench.kernels_of(groups, tuned, "ctu")
+    assert ks["tracing_pencil"] == (pytest.approx(13.9), 2) and ks["tracing_xwarp"] == (8.1, 1)
+    assert ks["ctucorr_pencil"] == (pytest.approx(11.7), 2) and ks["ctucorr_xwarp"] == (6.4, 1)
+    assert "ctucorr_cell" in bench.kernels_of(groups, {"pencil_mask": 6}, "ctu")
+    pk = {"hbm_gbs": 6442.9, "src": "measured"}
+    r = bench.roofline("fp32", groups, steps, n, pk, 2032.0, tuned, "ctu")
+    assert r["kernel"] == "tracing_pencil" and r["bound"] == "alu"
+    want = n * bench.FLOPS_PER_FACE["tracing"]["fp32"] / (13.9 / steps / 2 * 1e-3) / 1e12
+    assert r["achieved"] == pytest.approx(want, rel=1e-12)
+    # tracing: W (8) and B_n in, the flux and both traced states (21) out
+    assert bench.sweep_bytes_per_face("fp32", "tracing") == 4 * (8 + 1 + 21)
+    assert r["hbm_view"]["algorithmic_bytes_per_launch"] == n * 4 * 30
+    assert bench.group_bytes("fp32", n, "ctu")["corrector_sweeps"] == 3 * n * 4 * 37
