@@ -102,23 +102,6 @@ inline StateP<TU, TE> state_of(mhd_ctx* c)
     return s;
 }
 
-// persistent grid of the edge-field kernel: the blocks one SM keeps resident
-// (registers and shared memory; asked once per precision) times the SMs
-template <class R>
-inline int emf_grid(const mhd_ctx* c)
-{
-    static int per = 0;
-    if (per <= 0) {
-        int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_emf<R>, EMF_THREADS, emf_smem_bytes<R>()) !=
-                cudaSuccess || nb < 1)
-            nb = 1;
-        per = nb;
-    }
-    int cap = per * c->nsm;
-    return c->B.netile < cap ? c->B.netile : cap;
-}
-
 inline int xrow_grid(const mhd_ctx* c)
 {
     return (int)((c->B.nxr * 32 + PENCIL_THREADS - 1) / PENCIL_THREADS);
@@ -156,11 +139,21 @@ void fix_layers(mhd_ctx* c, const StateP<TU, TE>& s, cudaStream_t st)
 
 // the edge fields of one stage: by k_emf_tma when the context runs it (FP32
 // arithmetic, one box), else by k_emf
+//
+// Every compilation unit that launches these kernels holds its own instance of
+// them, while the linker keeps a single copy of this inline function for all
+// units with the same R (the FP32, mixed and learned steps share R = float).
+// The instance launched here may therefore belong to another unit than the
+// one whose step function raised its shared-memory limit, so the limit is
+// raised here, on the instance this copy launches (a host-side attribute
+// call, not a stream operation), and the occupancy is asked of it too.
 template <class R>
 void launch_emf(mhd_ctx* c, const Boxes& g, const R* F, const R* W, R* E, cudaStream_t st)
 {
     if constexpr (sizeof(R) == 4) {
         if (c->emf_tma) {
+            cudaFuncSetAttribute(k_emf_tma<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)emf_tma_smem_bytes());
             const CUtensorMap& mw = c->tmaps[W == (const R*)c->W ? 0 : 1];
             const int f = F == (const R*)c->F1 ? 2 : 4;
             k_emf_tma<R><<<c->emf_tma_grid, EMF_TMA_THREADS, emf_tma_smem_bytes(), st>>>(
@@ -168,7 +161,20 @@ void launch_emf(mhd_ctx* c, const Boxes& g, const R* F, const R* W, R* E, cudaSt
             return;
         }
     }
-    k_emf<R><<<emf_grid<R>(c), EMF_THREADS, emf_smem_bytes<R>(), st>>>(g, F, W, E);
+    cudaFuncSetAttribute(k_emf<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)emf_smem_bytes<R>());
+    // persistent grid: the blocks one SM keeps resident (registers and shared
+    // memory) times the SMs
+    static int per = 0;
+    if (per <= 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_emf<R>, EMF_THREADS, emf_smem_bytes<R>()) !=
+                cudaSuccess || nb < 1)
+            nb = 1;
+        per = nb;
+    }
+    const long long cap = (long long)per * c->nsm;
+    const int grid = (int)(g.netile < cap ? g.netile : cap);
+    k_emf<R><<<grid, EMF_THREADS, emf_smem_bytes<R>(), st>>>(g, F, W, E);
 }
 
 // CTU steps 5-6 along axis D (periodic or outflow instantiation): by
