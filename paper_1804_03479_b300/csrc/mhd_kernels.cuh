@@ -196,6 +196,53 @@ __device__ __forceinline__ void load_rot(const R* __restrict__ W, long long N, l
     bn = W[(5 + d) * N + c];
 }
 
+// FP32 operand widened to the energy and face-field type TE (FP64 in the mixed
+// form) on the integer units.  A hardware FP32 -> FP64 conversion issues on the
+// FP64 pipe, which runs at 1/64 of the FP32 rate on this part and bounds the
+// mixed per-cell kernels; the IEEE-754 binary32 and binary64 layouts give the
+// same exact value with a few integer instructions: the sign stays, the
+// exponent is re-biased by 1023 - 127 = 896 (by 2047 - 255 = 1792 for
+// infinities and NaNs, which keep their class) and the 23 fraction bits become
+// the top of the 52.  Zeros and FP32 subnormals (which this build's FP32
+// arithmetic flushes) give a signed zero.
+template <class TE, class R>
+__device__ __forceinline__ TE widen(R x)
+{
+    if constexpr (sizeof(TE) == 8 && sizeof(R) == 4) {
+        const unsigned u = __float_as_uint(x);
+        const unsigned a = u & 0x7fffffffu, sgn = u & 0x80000000u;
+        const bool tiny = a < 0x00800000u;
+        const unsigned hi = tiny ? sgn : (sgn | ((a >> 3) + (a >= 0x7f800000u ? 0x70000000u : 0x38000000u)));
+        const unsigned lo = tiny ? 0u : (a << 29);
+        return __hiloint2double((int)hi, (int)lo);
+    } else {
+        return TE(x);
+    }
+}
+
+// FP64 value rounded to the FP32 arithmetic type R on the integer units (the
+// counterpart of widen, for the same reason): round to nearest, ties to even,
+// on the 29 fraction bits that FP32 drops; a carry out of the fraction moves
+// into the exponent, and past the largest finite FP32 value to infinity.
+// Results below the FP32 normal range give a signed zero (this build flushes
+// subnormals); NaNs stay NaNs.
+template <class R, class TE>
+__device__ __forceinline__ R narrow(TE x)
+{
+    if constexpr (sizeof(TE) == 8 && sizeof(R) == 4) {
+        const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+        const unsigned sgn = hi & 0x80000000u, ex = (hi >> 20) & 0x7ffu;
+        unsigned v = ((ex - 896u) << 23) + (((hi & 0xfffffu) << 3) | (lo >> 29));
+        const unsigned rem = lo & 0x1fffffffu;
+        v += (rem > 0x10000000u || (rem == 0x10000000u && (v & 1u))) ? 1u : 0u;
+        v = ex <= 896u ? 0u : (ex >= 1151u ? 0x7f800000u : v);
+        if (ex == 0x7ffu && ((hi & 0xfffffu) | lo)) v = 0x7fc00000u;
+        return __uint_as_float(sgn | v);
+    } else {
+        return R(x);
+    }
+}
+
 // kinetic energy |M|^2 / (2 rho) in the energy's type TE: from the velocities
 // when the state has one type, else (the mixed form: FP32 rho, M with an
 // FP64 energy) by one FP64 division, so the pressure recovery is exact to
@@ -205,7 +252,8 @@ __device__ __forceinline__ TE kinetic(TU rho, TU mx, TU my, TU mz, TU vx, TU vy,
 {
     if (sizeof(TU) == sizeof(TE))
         return TE(0.5) * (TE(mx) * TE(vx) + TE(my) * TE(vy) + TE(mz) * TE(vz));
-    return TE(0.5) * (TE(mx) * TE(mx) + TE(my) * TE(my) + TE(mz) * TE(mz)) / TE(rho);
+    const TE dx = widen<TE>(mx), dy = widen<TE>(my), dz = widen<TE>(mz);
+    return TE(0.5) * (dx * dx + dy * dy + dz * dz) / widen<TE>(rho);
 }
 
 // positive doubles order like unsigned integers: max-reduce their bits
@@ -284,7 +332,7 @@ __global__ void __launch_bounds__(CELL_THREADS) k_prim(Boxes B, StateP<TU, TE> s
                 }
                 p = TE(pfloor);
             }
-            R w[8] = {R(rho), R(vx), R(vy), R(vz), R(p), R(bx), R(by), R(bz)};
+            R w[8] = {R(rho), R(vx), R(vy), R(vz), narrow<R>(p), narrow<R>(bx), narrow<R>(by), narrow<R>(bz)};
 #pragma unroll
             for (int f = 0; f < 8; f++) W[f * N + c] = w[f];
             if (!(w[0] > R(0)) || !(w[4] > R(0))) atomicMin(bad_cell, (unsigned long long)c);
@@ -1303,8 +1351,8 @@ __global__ void __launch_bounds__(CELL_THREADS) k_half(Boxes B, StateP<TU, TE> s
         // E_t2 at c + e_d + e_t1 and E_t1 at c + e_d + e_t2
         const R et2d = d == 0 ? e2xy : (d == 1 ? e0yz : e1xz);
         const R et1d = d == 0 ? e1xz : (d == 1 ? e2xy : e0yz);
-        const TE clo = (TE(en[t2][t1]) - TE(ec[t2])) - (TE(en[t1][t2]) - TE(ec[t1]));
-        const TE chi = (TE(et2d) - TE(en[t2][d])) - (TE(et1d) - TE(en[t1][d]));
+        const TE clo = (widen<TE>(en[t2][t1]) - widen<TE>(ec[t2])) - (widen<TE>(en[t1][t2]) - widen<TE>(ec[t1]));
+        const TE chi = (widen<TE>(et2d) - widen<TE>(en[t2][d])) - (widen<TE>(et1d) - widen<TE>(en[t1][d]));
         const TE lo = blo[d] - r * clo;
         const TE hi = bhi[d] - r * chi;
         Bh[d][c] = lo;
@@ -1321,7 +1369,7 @@ __global__ void __launch_bounds__(CELL_THREADS) k_half(Boxes B, StateP<TU, TE> s
         du[1 + d] += TU(fn[d][1] - fc[d][1]);
         du[1 + t1] += TU(fn[d][2] - fc[d][2]);
         du[1 + t2] += TU(fn[d][3] - fc[d][3]);
-        due += TE(fn[d][4] - fc[d][4]);
+        due += widen<TE>(fn[d][4] - fc[d][4]);
     }
     // outflow: the last cell's upper neighbour is the cell itself (a zero
     // difference above); add its outer-face flux instead
@@ -1336,7 +1384,8 @@ __global__ void __launch_bounds__(CELL_THREADS) k_half(Boxes B, StateP<TU, TE> s
                             - TE(0.5) * (bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]));
     if (pfloor > 0.0 && p < TE(pfloor)) p = TE(pfloor);
     Wh[c] = R(rho); Wh[N + c] = R(vx); Wh[2 * N + c] = R(vy); Wh[3 * N + c] = R(vz);
-    Wh[4 * N + c] = R(p); Wh[5 * N + c] = R(bc[0]); Wh[6 * N + c] = R(bc[1]); Wh[7 * N + c] = R(bc[2]);
+    Wh[4 * N + c] = narrow<R>(p); Wh[5 * N + c] = narrow<R>(bc[0]); Wh[6 * N + c] = narrow<R>(bc[1]);
+    Wh[7 * N + c] = narrow<R>(bc[2]);
     }
 }
 
@@ -1392,7 +1441,7 @@ __global__ void __launch_bounds__(CELL_THREADS) k_full(Boxes B, StateP<TU, TE> s
         du[1 + d] += TU(fn[d][1] - fc[d][1]);
         du[1 + t1] += TU(fn[d][2] - fc[d][2]);
         du[1 + t2] += TU(fn[d][3] - fc[d][3]);
-        due += TE(fn[d][4] - fc[d][4]);
+        due += widen<TE>(fn[d][4] - fc[d][4]);
     }
     // outflow: the last cell's upper neighbour is the cell itself (a zero
     // difference above); add its outer-face flux instead
@@ -1410,7 +1459,7 @@ __global__ void __launch_bounds__(CELL_THREADS) k_full(Boxes B, StateP<TU, TE> s
 #pragma unroll
     for (int d = 0; d < 3; d++) {
         const int t1 = d == 2 ? 0 : d + 1, t2 = d == 0 ? 2 : d - 1;
-        const TE curl = (TE(en[t2][t1]) - TE(ec[t2])) - (TE(en[t1][t2]) - TE(ec[t1]));
+        const TE curl = (widen<TE>(en[t2][t1]) - widen<TE>(ec[t2])) - (widen<TE>(en[t1][t2]) - widen<TE>(ec[t1]));
         s.b[d][c] = bo[d] - r * curl;
     }
     }
