@@ -234,7 +234,8 @@ extern "C" long long mhd_nblocks(mhd_ctx* c)
 static void launch_features(mhd_ctx* c, float* feats)
 {
     const long long nblk = mhd_nblocks(c);
-    const int grid = (int)((nblk + 255) / 256 < 148 * 16 ? (nblk + 255) / 256 : 148 * 16);
+    const int grid = features_grid(c->hbox[0]);
+    (void)nblk;
     const int nb = c->cell_grid;
     if (c->sch.precision == MHD_FP64) {
         k_prim<double, double, double><<<nb, CELL_THREADS, 0, c->stream>>>(c->B, state_of<double, double>(c), (double*)c->W, c->gamma, nullptr, c->bad, c->sch.pfloor);
@@ -304,7 +305,7 @@ static void run_step_learned(mhd_ctx* c, bool device_dt)
                                                          c->sch.pfloor, c->nfloor);
     if (device_dt) k_finalize_dt<<<(c->nbox + 127) / 128, 128, 0, st>>>(g, c->smax_part, c->sch.cfl, c->dt, c->smax, c->dtc);
     // selector: features of the current state, one inference, tile lists
-    const int fgrid = (int)((nblk + 255) / 256 < 148 * 16 ? (nblk + 255) / 256 : 148 * 16);
+    const int fgrid = features_grid(c->hbox[0]);
     k_block_features<R><<<fgrid, 256, 0, st>>>(c->hbox[0], W, n, (float)gam, c->sel_feats);
     const int igrid = (int)((nblk / 16 + 8) / 8 < 1184 ? (nblk / 16 + 8) / 8 : 1184);
     k_mlp_infer<<<igrid, 256, 0, st>>>(mlp_dev(c->sel), c->sel_feats, nblk, nullptr, c->sel_flags);
