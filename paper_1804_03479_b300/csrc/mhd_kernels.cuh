@@ -317,16 +317,20 @@ __global__ void __launch_bounds__(CELL_THREADS) k_prim(Boxes B, StateP<TU, TE> s
             int i, j, k;
             coords(g, lc, i, j, k);
             const long long c = g.off + lc;
-            TE bx = TE(0.5) * (s.b[0][c] + s.b[0][nbr(g, i, j, k, 0, 1)]);
-            TE by = TE(0.5) * (s.b[1][c] + s.b[1][nbr(g, i, j, k, 1, 1)]);
-            TE bz = TE(0.5) * (s.b[2][c] + s.b[2][nbr(g, i, j, k, 2, 1)]);
+            // twice the cell-centred field (the sum of the two faces): the
+            // halving is folded into the magnetic energy's factor and done in
+            // the arithmetic type for the primitives, both exact (powers of
+            // two), which saves three FP64 multiplications in the mixed form
+            const TE sx = s.b[0][c] + s.b[0][nbr(g, i, j, k, 0, 1)];
+            const TE sy = s.b[1][c] + s.b[1][nbr(g, i, j, k, 1, 1)];
+            const TE sz = s.b[2][c] + s.b[2][nbr(g, i, j, k, 2, 1)];
             const TU rho = s.rho[c];
             const TU mx = s.m[0][c], my = s.m[1][c], mz = s.m[2][c];
             const TU irho = TU(1) / rho;     // one division (FP64 is slow on this part)
             const TU vx = mx * irho, vy = my * irho, vz = mz * irho;
             // pressure recovery in the precision of the stored energy
             TE p = TE(gam - 1.0) * (s.e[c] - kinetic<TU, TE>(rho, irho, mx, my, mz, vx, vy, vz)
-                                    - TE(0.5) * (bx * bx + by * by + bz * bz));
+                                    - TE(0.125) * (sx * sx + sy * sy + sz * sz));
             if (pfloor > 0.0 && p < TE(pfloor)) {
                 // optional pressure floor.  At the start of a step (nfloor given)
                 // e is raised so that P = pfloor (not conservative); read-only
@@ -337,7 +341,8 @@ __global__ void __launch_bounds__(CELL_THREADS) k_prim(Boxes B, StateP<TU, TE> s
                 }
                 p = TE(pfloor);
             }
-            R w[8] = {R(rho), R(vx), R(vy), R(vz), narrow<R>(p), narrow<R>(bx), narrow<R>(by), narrow<R>(bz)};
+            R w[8] = {R(rho), R(vx), R(vy), R(vz), narrow<R>(p), R(0.5) * narrow<R>(sx), R(0.5) * narrow<R>(sy),
+                      R(0.5) * narrow<R>(sz)};
 #pragma unroll
             for (int f = 0; f < 8; f++) W[f * N + c] = w[f];
             if (!(w[0] > R(0)) || !(w[4] > R(0))) atomicMin(bad_cell, (unsigned long long)c);
@@ -1361,7 +1366,7 @@ __global__ void __launch_bounds__(CELL_THREADS) k_half(Boxes B, StateP<TU, TE> s
         const TE lo = blo[d] - r * clo;
         const TE hi = bhi[d] - r * chi;
         Bh[d][c] = lo;
-        bc[d] = TE(0.5) * (lo + hi);
+        bc[d] = lo + hi;                  // twice the cell-centred component (see k_prim)
     }
     // divergence of the fluxes, sweep frames back to x, y, z: rho and M in
     // their storage type TU, the energy in TE
@@ -1386,11 +1391,11 @@ __global__ void __launch_bounds__(CELL_THREADS) k_half(Boxes B, StateP<TU, TE> s
     const TU irho = TU(1) / rho;
     TU vx = mx * irho, vy = my * irho, vz = mz * irho;
     TE p = TE(gam - 1.0) * (e - kinetic<TU, TE>(rho, irho, mx, my, mz, vx, vy, vz)
-                            - TE(0.5) * (bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]));
+                            - TE(0.125) * (bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]));
     if (pfloor > 0.0 && p < TE(pfloor)) p = TE(pfloor);
     Wh[c] = R(rho); Wh[N + c] = R(vx); Wh[2 * N + c] = R(vy); Wh[3 * N + c] = R(vz);
-    Wh[4 * N + c] = narrow<R>(p); Wh[5 * N + c] = narrow<R>(bc[0]); Wh[6 * N + c] = narrow<R>(bc[1]);
-    Wh[7 * N + c] = narrow<R>(bc[2]);
+    Wh[4 * N + c] = narrow<R>(p); Wh[5 * N + c] = R(0.5) * narrow<R>(bc[0]);
+    Wh[6 * N + c] = R(0.5) * narrow<R>(bc[1]); Wh[7 * N + c] = R(0.5) * narrow<R>(bc[2]);
     }
 }
 
