@@ -352,9 +352,18 @@ static void hlld_star(const double w[7], double bn, double gam, double S, double
     *rhos = rs;
 }
 
-static void hlld_flux(const double wl[7], const double wr[7], double bn, double gam, double f[7])
+/* The HLLD fan (MK05): wave speeds S[0..4] = S_L, S*_L, S_M, S*_R, S_R and */
+/* the six conserved states U[0..5] = U_L, U*_L, U**_L, U**_R, U*_R, U_R     */
+/* between them, with the outer physical fluxes fl, fr.  S_L/S_R =          */
+/* min/max(u) -/+ max(c_f); S_M and p_T* from the HLL averages; the single-  */
+/* star states from hlld_star; S*_{L,R} = S_M -/+ |B_n|/sqrt(rho*); the      */
+/* double-star transverse v and B are the sqrt(rho*)-weighted averages with  */
+/* the rotational jump conditions, and each side's e** follows from the     */
+/* jump of v.B across its Alfven wave.  When S_L >= 0 or S_R <= 0 the       */
+/* interior states are not used (the flux is the upwind one).               */
+static void hlld_fan(const double wl[7], const double wr[7], double bn, double gam, double S[5],
+                     double U[6][7], double fl[7], double fr[7])
 {
-    double fl[7], fr[7], ul[7], ur[7];
     orc_flux_phys(wl, bn, gam, fl);
     orc_flux_phys(wr, bn, gam, fr);
     double cfl = fast_speed(wl[0], gam * wl[4] / wl[0], bn, wl[5], wl[6]);
@@ -362,8 +371,7 @@ static void hlld_flux(const double wl[7], const double wr[7], double bn, double 
     double cmax = dmax(cfl, cfr);
     double SL = dmin(wl[1], wr[1]) - cmax;
     double SR = dmax(wl[1], wr[1]) + cmax;
-    if (SL >= 0.0) { for (int k = 0; k < 7; k++) f[k] = fl[k]; return; }
-    if (SR <= 0.0) { for (int k = 0; k < 7; k++) f[k] = fr[k]; return; }
+    double *ul = U[0], *ur = U[5], *usl = U[1], *usr = U[4];
     cons_of(wl, bn, gam, ul);
     cons_of(wr, bn, gam, ur);
     double ptl = wl[4] + 0.5 * (bn * bn + wl[5] * wl[5] + wl[6] * wl[6]);
@@ -373,20 +381,12 @@ static void hlld_flux(const double wl[7], const double wr[7], double bn, double 
     double idd = 1.0 / (dr - dl);
     double SM = (dr * wr[1] - dl * wl[1] - ptr + ptl) * idd;
     double pts = (dr * ptl - dl * ptr + dl * dr * (wr[1] - wl[1])) * idd;
-    double usl[7], usr[7], rsl, rsr;
+    double rsl, rsr;
     hlld_star(wl, bn, gam, SL, SM, pts, usl, &rsl);
     hlld_star(wr, bn, gam, SR, SM, pts, usr, &rsr);
     double sql = sqrt(rsl), sqr = sqrt(rsr);
     double SsL = SM - fabs(bn) / sql;
     double SsR = SM + fabs(bn) / sqr;
-    if (SsL >= 0.0) {
-        for (int k = 0; k < 7; k++) f[k] = fl[k] + SL * (usl[k] - ul[k]);
-        return;
-    }
-    if (SsR <= 0.0) {
-        for (int k = 0; k < 7; k++) f[k] = fr[k] + SR * (usr[k] - ur[k]);
-        return;
-    }
     /* double-star states (rotational discontinuities) */
     double s = sgn1(bn);
     double inv = 1.0 / (sql + sqr);
@@ -396,15 +396,64 @@ static void hlld_flux(const double wl[7], const double wr[7], double bn, double 
     double b1 = (sql * usr[5] + sqr * usl[5] + sql * sqr * (vr1 - vl1) * s) * inv;
     double b2 = (sql * usr[6] + sqr * usl[6] + sql * sqr * (vr2 - vl2) * s) * inv;
     double vbss = SM * bn + v1 * b1 + v2 * b2;
-    if (SM >= 0.0) {
-        double vbs = SM * bn + vl1 * usl[5] + vl2 * usl[6];
-        double uss[7] = {rsl, rsl * SM, rsl * v1, rsl * v2, usl[4] - sql * (vbs - vbss) * s, b1, b2};
-        for (int k = 0; k < 7; k++) f[k] = fl[k] + SL * (usl[k] - ul[k]) + SsL * (uss[k] - usl[k]);
-    } else {
-        double vbs = SM * bn + vr1 * usr[5] + vr2 * usr[6];
-        double uss[7] = {rsr, rsr * SM, rsr * v1, rsr * v2, usr[4] + sqr * (vbs - vbss) * s, b1, b2};
-        for (int k = 0; k < 7; k++) f[k] = fr[k] + SR * (usr[k] - ur[k]) + SsR * (uss[k] - usr[k]);
+    double vbsl = SM * bn + vl1 * usl[5] + vl2 * usl[6];
+    double vbsr = SM * bn + vr1 * usr[5] + vr2 * usr[6];
+    double ussl[7] = {rsl, rsl * SM, rsl * v1, rsl * v2, usl[4] - sql * (vbsl - vbss) * s, b1, b2};
+    double ussr[7] = {rsr, rsr * SM, rsr * v1, rsr * v2, usr[4] + sqr * (vbsr - vbss) * s, b1, b2};
+    for (int k = 0; k < 7; k++) { U[2][k] = ussl[k]; U[3][k] = ussr[k]; }
+    S[0] = SL; S[1] = SsL; S[2] = SM; S[3] = SsR; S[4] = SR;
+}
+
+/* HLLD flux: the upwind flux plus the jumps across the waves on the side  */
+/* of x/t = 0 it is taken from (Rankine-Hugoniot across each wave).         */
+static void hlld_flux(const double wl[7], const double wr[7], double bn, double gam, double f[7])
+{
+    double fl[7], fr[7], S[5], U[6][7];
+    hlld_fan(wl, wr, bn, gam, S, U, fl, fr);
+    if (S[0] >= 0.0) { for (int k = 0; k < 7; k++) f[k] = fl[k]; return; }
+    if (S[4] <= 0.0) { for (int k = 0; k < 7; k++) f[k] = fr[k]; return; }
+    if (S[1] >= 0.0) {
+        for (int k = 0; k < 7; k++) f[k] = fl[k] + S[0] * (U[1][k] - U[0][k]);
+        return;
     }
+    if (S[3] <= 0.0) {
+        for (int k = 0; k < 7; k++) f[k] = fr[k] + S[4] * (U[4][k] - U[5][k]);
+        return;
+    }
+    if (S[2] >= 0.0) {
+        for (int k = 0; k < 7; k++) f[k] = fl[k] + S[0] * (U[1][k] - U[0][k]) + S[1] * (U[2][k] - U[1][k]);
+    } else {
+        for (int k = 0; k < 7; k++) f[k] = fr[k] + S[4] * (U[4][k] - U[5][k]) + S[3] * (U[3][k] - U[4][k]);
+    }
+}
+
+/* exported: the HLLD fan (speeds S[5], states U[6][7] as in hlld_fan)      */
+void orc_hlld_fan(const double wl[7], const double wr[7], double bn, double gam, double S[5], double U[42])
+{
+    double fl[7], fr[7];
+    hlld_fan(wl, wr, bn, gam, S, (double (*)[7])U, fl, fr);
+}
+
+/* exported: the HLLE fan, Einfeldt speeds S[0] = S_L, S[1] = S_R (before   */
+/* the clamp at 0 the flux applies) and the HLL average state between them */
+/* U_hll = (S_R U_R - S_L U_L - (F_R - F_L)) / (S_R - S_L)                   */
+void orc_hlle_fan(const double wl[7], const double wr[7], double bn, double gam, double S[2], double Uhll[7])
+{
+    double fl[7], fr[7], ul[7], ur[7];
+    orc_flux_phys(wl, bn, gam, fl);
+    orc_flux_phys(wr, bn, gam, fr);
+    cons_of(wl, bn, gam, ul);
+    cons_of(wr, bn, gam, ur);
+    double cfl = fast_speed(wl[0], gam * wl[4] / wl[0], bn, wl[5], wl[6]);
+    double cfr = fast_speed(wr[0], gam * wr[4] / wr[0], bn, wr[5], wr[6]);
+    double sL = wl[1] - cfl, sR = wr[1] + cfr;
+    roe_t r;
+    if (roe_linearise(wl, wr, bn, gam, &r)) {
+        sL = dmin(sL, r.vn - r.cf);
+        sR = dmax(sR, r.vn + r.cf);
+    }
+    S[0] = sL; S[1] = sR;
+    for (int k = 0; k < 7; k++) Uhll[k] = (sR * ur[k] - sL * ul[k] - (fr[k] - fl[k])) / (sR - sL);
 }
 
 /* exported: solver 0 Roe, 1 HLLD, 2 HLLE; returns 1 if Roe fell back to HLLE */

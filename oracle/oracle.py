@@ -74,6 +74,10 @@ def lib():
         L.orc_eigen.argtypes = [dp, ctypes.c_double, ctypes.c_double, dp, dp, dp]
         L.orc_riemann.restype = ctypes.c_int
         L.orc_riemann.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double, dp]
+        L.orc_hlld_fan.restype = None
+        L.orc_hlld_fan.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double, dp, dp]
+        L.orc_hlle_fan.restype = None
+        L.orc_hlle_fan.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double, dp, dp]
         L.orc_roe_waves.restype = ctypes.c_int
         L.orc_roe_waves.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double, dp, dp, dp]
         L.orc_flux_phys.restype = None
@@ -215,6 +219,22 @@ def riemann(solver, wl, wr, bn, gamma):
     wl = _f64(wl); wr = _f64(wr); f = np.zeros(7)
     fb = lib().orc_riemann(SOLVERS[solver], _p(wl), _p(wr), bn, gamma, _p(f))
     return f, int(fb)
+
+
+def hlld_fan(wl, wr, bn, gamma):
+    """HLLD fan: speeds (S_L, S*_L, S_M, S*_R, S_R) and the six conserved
+    states (U_L, U*_L, U**_L, U**_R, U*_R, U_R), rows (rho, M_n, M_t1, M_t2,
+    e, B_t1, B_t2)."""
+    S = np.zeros(5); Uf = np.zeros((6, 7))
+    lib().orc_hlld_fan(_p(_f64(wl)), _p(_f64(wr)), bn, gamma, _p(S), _p(Uf))
+    return S, Uf
+
+
+def hlle_fan(wl, wr, bn, gamma):
+    """HLLE fan: Einfeldt speeds (S_L, S_R) and the HLL average state."""
+    S = np.zeros(2); Uh = np.zeros(7)
+    lib().orc_hlle_fan(_p(_f64(wl)), _p(_f64(wr)), bn, gamma, _p(S), _p(Uh))
+    return S, Uh
 
 
 def roe_waves(wl, wr, bn, gamma):
