@@ -237,7 +237,10 @@ mhd_status mhd_get_sweep_pencils(mhd_ctx* ctx, int* pencil_mask, int* pencil_len
  * launch at 256^3).  mode in {0, 1}, else MHD_EINVAL.  mhd_get_emf_staging
  * reports the requested mode and whether the tensor copies are in use
  * (active = 1).  A plane wait that gives up (after about 2 s) sets a device
- * flag, and the next call that reads the device flags returns MHD_ECUDA. */
+ * flag (bit 0: a consumer's wait for a filled slot, bit 1: the producer's
+ * wait for a free one), and the next call that reads the device flags
+ * (mhd_sync, mhd_cfl_dt, mhd_divB, mhd_sums, mhd_get_state, ...) returns
+ * MHD_ETIMEOUT until mhd_clear_error. */
 mhd_status mhd_set_emf_staging(mhd_ctx* ctx, int mode);
 mhd_status mhd_get_emf_staging(mhd_ctx* ctx, int* mode, int* active);
 
@@ -259,6 +262,12 @@ mhd_status mhd_profile_end(mhd_ctx* ctx, double* ms, int ngroups, int* steps);
 
 /* Cell-steps raised to the pressure floor since mhd_init.  Synchronises. */
 long long mhd_floor_count(mhd_ctx* ctx);
+
+/* Host-side fault injection for tests of the error path: writes `bits`
+ * (1, 2 or 3) into the context's device wait flag, exactly as a bounded
+ * device wait that gave up would, so that the mapping to MHD_ETIMEOUT can be
+ * checked without making any wait on the GPU fail.  Synchronises. */
+mhd_status mhd_inject_wait_flag(mhd_ctx* ctx, unsigned bits);
 
 /* Cell index of the first anomaly found (or -1) and reset of the error. */
 long long mhd_bad_cell(mhd_ctx* ctx);
@@ -325,19 +334,29 @@ mhd_status mhd_selector_stats(mhd_ctx* ctx, double* frac_blocks, double* frac_ti
  * plug-in inside another application whose allocator owns all device
  * memory, or a loop that cannot afford the device-wide synchronisation
  * cudaMalloc / cudaFree can cause).  It advances the caller's state by one
- * FP64 VL step (any recon, any Riemann solver) with the given dt, in place:
- * U and B are DEVICE pointers in the layout above (double).  All scratch
- * lives in one fixed array built into the library, sized for at most
- * MHD_NOALLOC_MAX_CELLS cells (about 11 MB, held on every GPU that loads
- * the library until the process exits).  The call allocates nothing and
- * calls no allocating routine.
- *   - Larger grids: MHD_EINVAL; other integrators or precisions:
- *     MHD_EUNSUPPORTED; the reason is in mhd_last_error(NULL).
+ * FP64 VL step (any recon, any Riemann solver, scheme->pfloor as in
+ * mhd_step) with the given dt, in place: U and B are DEVICE pointers in the
+ * layout above (double).  All scratch lives in one fixed array built into
+ * the library, sized for at most MHD_NOALLOC_MAX_CELLS cells (about 11 MB,
+ * held on every GPU that has loaded the library's device code until the
+ * process exits).  The call allocates nothing and calls no allocating
+ * routine.
+ *   - Larger grids: MHD_EINVAL (each side is bounded before the cell count
+ *     is formed); other integrators or precisions: MHD_EUNSUPPORTED; the
+ *     reason is in mhd_last_error(NULL).
  *   - The first call on a device looks up the array's device address (with
  *     that device current); make that first call before any stream capture.
+ *     Under CUDA's default lazy module loading that first lookup is also
+ *     when the driver loads the library's device code on that device and
+ *     reserves the array, which can synchronise the device: a caller whose
+ *     allocator will take all free memory makes one warm-up call per device
+ *     before it does (or sets CUDA_MODULE_LOADING=EAGER, which reserves the
+ *     array when the context is created).
  *   - Every call, on any stream, shares the one array, which keeps the last
  *     call's contents: calls that overlap on the GPU race and corrupt each
- *     other.  Serialise them (one stream, or events).
+ *     other.  Serialise them (one stream, or events).  Each call resets
+ *     what must start at zero (the flag word and the floor count) from its
+ *     own kernel arguments.
  *   - Asynchronous on `stream` (NULL = the default stream); a cell with
  *     rho <= 0 or P <= 0 is not reported by this call. */
 #define MHD_NOALLOC_MAX_CELLS 32768

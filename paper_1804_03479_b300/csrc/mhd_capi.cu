@@ -182,6 +182,16 @@ static cudaError_t layout_tiles(mhd_ctx* c, int tl)
     return e;
 }
 
+// nx*ny*nz < limit, decided without forming a product that could wrap
+static bool cells_below(int nx, int ny, int nz, long long limit)
+{
+    const long long a = nx, b = ny, c = nz;
+    if (a >= limit) return false;
+    if (b >= (limit + a - 1) / a) return false;            // a*b < limit, a*b fits
+    const long long ab = a * b;
+    return c < (limit + ab - 1) / ab;                       // a*b*c < limit
+}
+
 static mhd_status init_common(int nbox, const mhd_grid* grids, double gamma, const mhd_scheme* scheme, void* stream,
                               mhd_ctx** out)
 {
@@ -190,7 +200,7 @@ static mhd_status init_common(int nbox, const mhd_grid* grids, double gamma, con
     if (nbox < 1 || !grids || !scheme) { g_init_err = "null grid or scheme, or no box"; return MHD_EINVAL; }
     for (int b = 0; b < nbox; b++)
         if (grids[b].nx < 1 || grids[b].ny < 1 || grids[b].nz < 1 || !(grids[b].dx > 0.0) ||
-            (long long)grids[b].nx * grids[b].ny * grids[b].nz >= (1LL << 31)) {
+            !cells_below(grids[b].nx, grids[b].ny, grids[b].nz, 1LL << 31)) {
             g_init_err = "bad grid (sides >= 1, dx > 0, fewer than 2^31 cells per box)";
             return MHD_EINVAL;
         }
@@ -322,7 +332,7 @@ static mhd_status check_device_flags(mhd_ctx* c)
     CK(cudaMemcpyAsync(&bad, c->bad, sizeof(bad), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(&perr, c->perr, sizeof(perr), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    if (perr) return fail(c, MHD_ECUDA, "a staged-plane wait of the edge-field kernel gave up (flags %u)", perr);
+    if (perr) return fail(c, MHD_ETIMEOUT, "a staged-plane wait of the edge-field kernel gave up (flags %u)", perr);
     if (bad != ~0ull) return fail(c, MHD_ENEGATIVE, "rho <= 0 or P <= 0 in cell %llu", bad);
     return c->sticky;
 }
@@ -952,6 +962,16 @@ extern "C" void mhd_clear_error(mhd_ctx* c)
     cudaStreamSynchronize(c->stream);
     c->sticky = MHD_OK;
     strcpy(c->err, "no error");
+}
+
+extern "C" mhd_status mhd_inject_wait_flag(mhd_ctx* c, unsigned bits)
+{
+    if (!c || bits == 0u || bits > 3u) return fail(c, MHD_EINVAL, "bits must be 1, 2 or 3");
+    // the word a kernel's bounded wait sets when it gives up, written from the
+    // host: the error path is exercised without making any device wait fail
+    CK(cudaMemcpyAsync(c->perr, &bits, sizeof(bits), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return MHD_OK;
 }
 
 extern "C" const char* mhd_last_error(mhd_ctx* c) { return c ? c->err : g_init_err; }

@@ -17,7 +17,8 @@ using namespace mhd;
 void mhd_internal_set_init_error(const char* msg);   // defined with the other entry points
 
 // per cell: W (8) + Wh (8) + fluxes (21) + edge E (3) + half-step faces (3);
-// then dt, the CFL word, the flag word and the one-entry box table
+// then dt, the CFL word, the flag word, the floor count and the one-entry
+// box table
 static constexpr size_t kDoublesPerCell = 43;
 static constexpr size_t kScratchBytes = kDoublesPerCell * MHD_NOALLOC_MAX_CELLS * sizeof(double) + 1024;
 static_assert(sizeof(mhd::BoxDev) <= 256 && sizeof(mhd::DtBox) <= 256, "tables must fit the slack");
@@ -44,6 +45,20 @@ static void* scratch_address(int dev, cudaError_t* err)
     return g_scratch_addr[dev];
 }
 
+// Writes this call's box table, dt and its ratios, and resets the flag word
+// and the floor count: everything the array must hold before the step, set
+// from kernel arguments, so no host buffer is read after the call returns.
+static __global__ void k_noalloc_setup(BoxDev hb, BoxDev* dbox, double* dt, double v, DtBox* dtb,
+                                       unsigned long long* bad, unsigned long long* nfloor)
+{
+    if (threadIdx.x != 0) return;
+    *dbox = hb;
+    dt[0] = v;
+    write_dtbox(dtb, v, hb.dx);
+    *bad = ~0ULL;       // no anomaly recorded
+    *nfloor = 0ULL;
+}
+
 static mhd_status reject(mhd_status s, const char* msg)
 {
     mhd_internal_set_init_error(msg);
@@ -56,13 +71,15 @@ extern "C" mhd_status mhd_step_noalloc(const mhd_grid* grid, double gamma, const
     if (!grid || !scheme || !U || !B) return reject(MHD_EINVAL, "mhd_step_noalloc: null argument");
     if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || !(grid->dx > 0.0))
         return reject(MHD_EINVAL, "mhd_step_noalloc: bad grid");
-    const long long n = (long long)grid->nx * grid->ny * grid->nz;
-    if (n > MHD_NOALLOC_MAX_CELLS) {
-        static char msg[160];
-        snprintf(msg, sizeof(msg), "mhd_step_noalloc: %lld cells exceed the fixed scratch of %d cells", n,
-                 MHD_NOALLOC_MAX_CELLS);
+    // bound each side before forming the product, so that it cannot wrap
+    const long long lim = MHD_NOALLOC_MAX_CELLS;
+    if (grid->nx > lim || grid->ny > lim / grid->nx || grid->nz > lim / ((long long)grid->nx * grid->ny)) {
+        static char msg[200];
+        snprintf(msg, sizeof(msg), "mhd_step_noalloc: %d x %d x %d cells exceed the fixed scratch of %d cells",
+                 grid->nx, grid->ny, grid->nz, MHD_NOALLOC_MAX_CELLS);
         return reject(MHD_EINVAL, msg);
     }
+    const long long n = (long long)grid->nx * grid->ny * grid->nz;
     if (!(gamma > 1.0)) return reject(MHD_EINVAL, "mhd_step_noalloc: gamma must exceed 1");
     if (!(dt > 0.0) || !(dt < 1e300)) return reject(MHD_EINVAL, "mhd_step_noalloc: dt must be positive and finite");
     if (scheme->integrator != MHD_VL || scheme->precision != MHD_FP64)
@@ -100,10 +117,10 @@ extern "C" mhd_status mhd_step_noalloc(const mhd_grid* grid, double gamma, const
     c.dt = s + 43 * n;
     c.smax = nullptr;          // steps with the caller's dt: no CFL reduction
     c.smax_part = nullptr;
-    c.nfloor = nullptr;
     c.bad = (unsigned long long*)(s + 43 * n + 2);
+    c.nfloor = (unsigned long long*)(s + 43 * n + 3);   // pfloor > 0 raises e as mhd_step does
     // the one-entry box table lives in the array too, 64-byte aligned
-    size_t tab = ((43 * (size_t)n + 3) * sizeof(double) + 63) / 64 * 64;
+    size_t tab = ((43 * (size_t)n + 4) * sizeof(double) + 63) / 64 * 64;
     BoxDev* dbox = (BoxDev*)(base + tab);
     c.dtc = (DtBox*)(base + tab + 256);
     BoxDev hb;
@@ -139,16 +156,12 @@ extern "C" mhd_status mhd_step_noalloc(const mhd_grid* grid, double gamma, const
     c.nsm = nsm;
     c.sweep_bps = 4;
     c.cell_grid = (int)(c.B.nvblk < 16LL * nsm ? c.B.nvblk : 16LL * nsm);
-    // pageable source: the copy has read it by the time the call returns
-    if (cudaMemcpyAsync(dbox, &hb, sizeof(hb), cudaMemcpyHostToDevice, c.stream) != cudaSuccess)
-        return reject(MHD_ECUDA, "mhd_step_noalloc: box table copy failed");
     cudaError_t attr = cudaSuccess;
     c.step = mhd_pick_fp64(scheme->integrator, scheme->recon, scheme->riemann, &attr);
     if (!c.step || attr != cudaSuccess) return reject(MHD_ECUDA, "mhd_step_noalloc: kernel set-up failed");
-    // the array keeps the previous call's contents: reset the flag word
-    if (cudaMemsetAsync(c.bad, 0xff, sizeof(unsigned long long), c.stream) != cudaSuccess)
-        return reject(MHD_ECUDA, "mhd_step_noalloc: cudaMemsetAsync failed");
-    k_set_dt<<<1, 32, 0, c.stream>>>(c.B, c.dt, dt, c.dtc);
+    // the array keeps the previous call's contents: the set-up kernel writes
+    // the table and dt and resets the flag word and the floor count
+    k_noalloc_setup<<<1, 32, 0, c.stream>>>(hb, dbox, c.dt, dt, c.dtc, c.bad, c.nfloor);
     c.step(&c, false);
     e = cudaGetLastError();
     if (e != cudaSuccess) return reject(MHD_ECUDA, cudaGetErrorString(e));

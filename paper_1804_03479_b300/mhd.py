@@ -35,7 +35,7 @@ EXPORTS = ["mhd_init", "mhd_set_state", "mhd_get_state", "mhd_cfl_dt", "mhd_step
            "mhd_selector_stats", "mhd_floor_count", "mhd_energies", "mhd_helicity",
            "mhd_set_sweep_pencils", "mhd_get_sweep_pencils", "mhd_set_boundary", "mhd_get_boundary",
            "mhd_pressure_gradient", "mhd_set_dirichlet", "mhd_get_dirichlet", "mhd_set_emf_staging",
-           "mhd_get_emf_staging"]
+           "mhd_get_emf_staging", "mhd_inject_wait_flag"]
 GROUPS = ["prim_cfl", "predictor_x", "predictor_y", "predictor_z", "emf1", "half_update", "corrector_x",
           "corrector_y", "corrector_z", "emf2", "full_update"]
 
@@ -141,6 +141,7 @@ def lib():
     L.mhd_get_sweep_pencils.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip)]
     L.mhd_set_emf_staging.argtypes = [vp, ip]
     L.mhd_get_emf_staging.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip)]
+    L.mhd_inject_wait_flag.argtypes = [vp, ctypes.c_uint]
     # every entry point that returns an mhd_status; the others got their
     # restype above (long long, int, void, const char*)
     other = {"mhd_bad_cell", "mhd_clear_error", "mhd_device_bytes", "mhd_floor_count", "mhd_free",
@@ -166,7 +167,7 @@ def _ptr(a):
 NOALLOC_MAX_CELLS = 32768
 
 
-def step_noalloc(U, B, dx, dt, gamma=5.0 / 3.0, recon="plm", riemann="roe", stream=None):
+def step_noalloc(U, B, dx, dt, gamma=5.0 / 3.0, recon="plm", riemann="roe", stream=None, pfloor=0.0):
     """One FP64 VL step of a caller-owned device state (torch CUDA float64
     tensors U (5, nz, ny, nx) and B (3, nz, ny, nx)), in place, through
     mhd_step_noalloc: no device memory is allocated (the scratch is a fixed
@@ -174,7 +175,7 @@ def step_noalloc(U, B, dx, dt, gamma=5.0 / 3.0, recon="plm", riemann="roe", stre
     overlap on the GPU share that array and race: serialise them."""
     nz, ny, nx = U.shape[1:]
     g = Grid(nx, ny, nz, dx)
-    s = Scheme(INTEGRATORS["vl"], RECONS[recon], SOLVERS[riemann], PRECISIONS["fp64"], 0.3, 0.0)
+    s = Scheme(INTEGRATORS["vl"], RECONS[recon], SOLVERS[riemann], PRECISIONS["fp64"], 0.3, pfloor)
     pu, du = _ptr(U)
     pb, db = _ptr(B)
     if not (du and db):
@@ -366,6 +367,11 @@ class Solver:
 
     def bad_cell(self):
         return lib().mhd_bad_cell(self.h)
+
+    def inject_wait_flag(self, bits=1):
+        """Test hook: set the device wait flag from the host, as a bounded
+        device wait that gave up would (see mhd_inject_wait_flag)."""
+        self._check(lib().mhd_inject_wait_flag(self.h, bits))
 
     def clear_error(self):
         lib().mhd_clear_error(self.h)
