@@ -23,6 +23,13 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Stage marks: nothing in this build.  The operation-counting build         */
+/* (flopcount.cpp, the same source with a counting scalar type) attributes   */
+/* the operations done since the previous mark to the named stage.           */
+#ifndef ORC_STAGE
+#define ORC_STAGE(name)
+#endif
+
 enum { VL = 0, CTU = 1 };
 enum { PLM = 0, PPM = 1, PLM_PRIM = 2 };
 enum { ROE = 0, HLLD = 1, HLLE = 2 };
@@ -790,6 +797,7 @@ static long fluxes(const grid_t *g, int recon, int riemann, int first_order, int
                 orc_recon_cell(recon, trace, &w5[0][0], b5, g->gam, dt / g->dx, wm, wp);
                 for (int k = 0; k < 7; k++) { tmpM[k * n + c] = wm[k]; tmpP[k * n + c] = wp[k]; }
             }
+            ORC_STAGE("reconstruction");
         }
         double *Fd = F + (long)d * 7 * n;
 #pragma omp parallel for schedule(static) reduction(+ : nfb)
@@ -805,6 +813,7 @@ static long fluxes(const grid_t *g, int recon, int riemann, int first_order, int
             nfb += orc_riemann(riemann, wl, wr, Bface[d * n + c], g->gam, f);
             for (int k = 0; k < 7; k++) Fd[k * n + c] = f[k];
         }
+        ORC_STAGE(first_order ? "riemann_predictor" : "riemann_corrector");
         if (!first_order) {
             if (!WMd) free(tmpM);
             if (!WPd) free(tmpP);
@@ -819,24 +828,30 @@ static long fluxes(const grid_t *g, int recon, int riemann, int first_order, int
 static long step_vl(const grid_t *g, int recon, int riemann, double dt, double *U, double *B, long *nfloor)
 {
     long n = g->n;
-    double *W = malloc(sizeof(double) * 8 * n);
-    double *F = malloc(sizeof(double) * 21 * n);
-    double *E = malloc(sizeof(double) * 3 * n);
-    double *Uh = malloc(sizeof(double) * 5 * n);
-    double *Bh = malloc(sizeof(double) * 3 * n);
+    double *W = (double *)malloc(sizeof(double) * 8 * n);
+    double *F = (double *)malloc(sizeof(double) * 21 * n);
+    double *E = (double *)malloc(sizeof(double) * 3 * n);
+    double *Uh = (double *)malloc(sizeof(double) * 5 * n);
+    double *Bh = (double *)malloc(sizeof(double) * 3 * n);
     long nfb = 0;
     /* steps 1-3: first-order fluxes with face B_n, edge E, half update */
     *nfloor += prim_floor(g, U, B, W, U + 4 * n);
+    ORC_STAGE("primitives");
     nfb += fluxes(g, recon, riemann, 1, 0, dt, W, B, F, NULL, NULL);
     edge_emf(g, F, W, E);
+    ORC_STAGE("edge_emf");
     fv_update(g, 0.5 * dt, U, F, Uh, W, B, riemann, NULL);
     ct_update(g, 0.5 * dt, B, E, Bh);
+    ORC_STAGE("half_update");
     /* steps 4-7: reconstruct at the half step, Riemann, edge E, full update */
     prim_all(g, Uh, Bh, W);
+    ORC_STAGE("primitives");
     nfb += fluxes(g, recon, riemann, 0, 0, dt, W, Bh, F, NULL, NULL);
     edge_emf(g, F, W, E);
+    ORC_STAGE("edge_emf");
     fv_update(g, dt, U, F, U, W, Bh, riemann, NULL);
     ct_update(g, dt, B, E, B);
+    ORC_STAGE("full_update");
     free(W); free(F); free(E); free(Uh); free(Bh);
     return nfb;
 }
@@ -938,18 +953,19 @@ static long step_ctu(const grid_t *g, int recon, int riemann, double dt, double 
 {
     long n = g->n;
     double gam = g->gam;
-    double *W = malloc(sizeof(double) * 8 * n);
-    double *F = malloc(sizeof(double) * 21 * n);
-    double *F2 = malloc(sizeof(double) * 21 * n);
-    double *E = malloc(sizeof(double) * 3 * n);
-    double *Uh = malloc(sizeof(double) * 5 * n);
-    double *Bh = malloc(sizeof(double) * 3 * n);
-    double *WM = malloc(sizeof(double) * 21 * n);
-    double *WP = malloc(sizeof(double) * 21 * n);
+    double *W = (double *)malloc(sizeof(double) * 8 * n);
+    double *F = (double *)malloc(sizeof(double) * 21 * n);
+    double *F2 = (double *)malloc(sizeof(double) * 21 * n);
+    double *E = (double *)malloc(sizeof(double) * 3 * n);
+    double *Uh = (double *)malloc(sizeof(double) * 5 * n);
+    double *Bh = (double *)malloc(sizeof(double) * 3 * n);
+    double *WM = (double *)malloc(sizeof(double) * 21 * n);
+    double *WP = (double *)malloc(sizeof(double) * 21 * n);
     long nfb = 0;
     double hdt = 0.5 * dt;
     /* step 1: traced face states at t+dt/2 along every axis */
     *nfloor += prim_floor(g, U, B, W, U + 4 * n);
+    ORC_STAGE("primitives");
     {
         /* fill WM/WP via the reconstruction pass, then add the source terms  */
         /* the 1-D system leaves out when dB_n/dn != 0: in primitive form     */
@@ -973,6 +989,7 @@ static long step_ctu(const grid_t *g, int recon, int riemann, double dt, double 
             }
         }
     }
+    ORC_STAGE("reconstruction_tracing");
     /* step 2: Riemann fluxes of the traced states with the face B_n at t^n */
     for (int d = 0; d < 3; d++) {
         double *Fd = F + (long)d * 7 * n;
@@ -986,18 +1003,21 @@ static long step_ctu(const grid_t *g, int recon, int riemann, double dt, double 
             for (int k = 0; k < 7; k++) Fd[k * n + c] = f[k];
         }
     }
+    ORC_STAGE("riemann_predictor");
     /* outflow: the stage-1 fluxes through the outer faces */
     double *Fo1 = NULL, *Fo2 = NULL;
     if (g->bc) {
-        Fo1 = calloc((size_t)21 * n, sizeof(double));
-        Fo2 = calloc((size_t)21 * n, sizeof(double));
+        Fo1 = (double *)calloc((size_t)21 * n, sizeof(double));
+        Fo2 = (double *)calloc((size_t)21 * n, sizeof(double));
         nfb += ctu_outer_fluxes(g, riemann, WM, WP, B, W, NULL, NULL, hdt, Fo1);
     }
     /* step 3: edge E from these fluxes and the cell-centre E at t^n */
     edge_emf(g, F, W, E);
+    ORC_STAGE("edge_emf");
     /* step 4: dt/2 CT update of face B and conservative update of U */
     ct_update(g, hdt, B, E, Bh);
     fv_update(g, hdt, U, F, Uh, NULL, NULL, riemann, Fo1);
+    ORC_STAGE("half_update");
     /* step 5: transverse flux-gradient correction of the traced states     */
     /* (ctu_corrected), and step 6: Riemann with the half-step face B_n     */
     for (int d = 0; d < 3; d++) {
@@ -1008,18 +1028,23 @@ static long step_ctu(const grid_t *g, int recon, int riemann, double dt, double 
             double wface[2][7];
             ctu_corrected(g, d, shift(g, c, d, -1), WPd, W, F, Fo1, hdt, wface[0]);
             ctu_corrected(g, d, c, WMd, W, F, Fo1, hdt, wface[1]);
+            ORC_STAGE("transverse_correction");
             double f[7];
             nfb += orc_riemann(riemann, wface[0], wface[1], Bh[d * n + c], gam, f);
             for (int k = 0; k < 7; k++) Fd[k * n + c] = f[k];
+            ORC_STAGE("riemann_corrector");
         }
     }
     if (g->bc) nfb += ctu_outer_fluxes(g, riemann, WM, WP, Bh, W, F, Fo1, hdt, Fo2);
     /* step 7: edge E from the corrected fluxes and the half-step cell state */
     prim_all(g, Uh, Bh, W);
+    ORC_STAGE("primitives");
     edge_emf(g, F2, W, E);
+    ORC_STAGE("edge_emf");
     /* step 8: full update */
     fv_update(g, dt, U, F2, U, NULL, NULL, riemann, Fo2);
     ct_update(g, dt, B, E, B);
+    ORC_STAGE("full_update");
     free(Fo1); free(Fo2);
     free(W); free(F); free(F2); free(E); free(Uh); free(Bh); free(WM); free(WP);
     return nfb;
@@ -1063,7 +1088,7 @@ double orc_cfl_dt_full(int nx, int ny, int nz, double dx, double gam, double cfl
 {
     grid_t g = {nx, ny, nz, (long)nx * ny * nz, dx, gam, pfloor, bc};
     long n = g.n;
-    double *W = malloc(sizeof(double) * 8 * n);
+    double *W = (double *)malloc(sizeof(double) * 8 * n);
     prim_all(&g, U, B, W);
     double smax = 0.0;
     for (long c = 0; c < n; c++) {
@@ -1176,7 +1201,7 @@ void orc_energies(int nx, int ny, int nz, double dx, const double *U, const doub
 {
     grid_t g = {nx, ny, nz, (long)nx * ny * nz, dx, 0.0};
     long n = g.n;
-    double *J = malloc(sizeof(double) * 3 * n);
+    double *J = (double *)malloc(sizeof(double) * 3 * n);
     orc_edge_current(nx, ny, nz, B, J);
     double et = 0.0, ub = 0.0, uv = 0.0, rmax = 0.0, jmax = 0.0, cnt = 0.0;
     for (long c = 0; c < n; c++) {

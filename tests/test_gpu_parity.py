@@ -108,6 +108,38 @@ def test_fp64_parity_linear_wave(M):
     run_parity(M, st, "vl", "ppm", "hlld", 3, mfloor=1e-2)
 
 
+CONFIG2 = [(i, r, s) for i in ("vl", "ctu") for r in ("plm", "ppm") for s in ("roe", "hlld")]
+# stated per-field bound on the FP32 path's relative L1 against the FP64
+# oracle after 10 steps of the 256^3 workload's initial state at 64^3
+# (rho, Mx, My, Mz, e, Bx, By, Bz); the momentum is the 1e-3 c_s noise plus
+# what the ABC field drives, a small denominator
+FP32_TOL64 = np.array([3e-6, 1e-3, 1e-3, 1e-3, 3e-6, 3e-6, 3e-6, 3e-6])
+
+
+@pytest.mark.parametrize("integ,recon,solver", CONFIG2)
+def test_fp32_error_statement_config2_64(M, integ, recon, solver):
+    """The eight FP32 schemes of the 256^3 workload ({VL, CTU} x {PLM, PPM} x
+    {Roe, HLLD}) on its initial state (k = 4 pi, beta = 0.5, seed 0) at 64^3:
+    10 steps with the oracle's dt, relative L1 per field against the FP64
+    oracle within FP32_TOL64."""
+    st = I.abc(64, kmult=2, beta=0.5, seed=0)
+    U, B = st.U.copy(), st.B.copy()
+    s = M.Solver(U.shape[1:], st.dx, st.gamma, integ, recon, solver, "fp32", 0.3)
+    try:
+        s.set_state(U.astype(np.float32), B.astype(np.float32))
+        for _ in range(10):
+            dt = orc.cfl_dt(U, B, st.dx, st.gamma, 0.3)
+            s.step(dt)
+            orc.step(U, B, st.dx, st.gamma, dt, integ, recon, solver)
+        Ug, Bg = s.get_state()
+        errs = np.array([rel_l1(Ug[f].astype(np.float64), U[f]) for f in range(5)] +
+                        [rel_l1(Bg[d].astype(np.float64), B[d]) for d in range(3)])
+        print("fp32-l1", integ, recon, solver, " ".join("%.2e" % e for e in errs))
+        assert np.all(errs <= FP32_TOL64), errs
+    finally:
+        s.free()
+
+
 def neighbourhood(U, B, k, j, i, r):
     idx = lambda c, n: np.arange(c - r, c + r + 1) % n
     nz, ny, nx = U.shape[1:]
