@@ -22,6 +22,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* Stage marks: nothing in this build.  The operation-counting build         */
 /* (flopcount.cpp, the same source with a counting scalar type) attributes   */
@@ -131,6 +134,8 @@ static double fast_speed(double rho, double a2, double bn, double bt1, double bt
 /* R[k][a]: component k of right eigenvector a.  L[a][k]: left eigenvectors, */
 /* normalised so that L R = I.                                                */
 /* ------------------------------------------------------------------------ */
+#define EIG_DEGEN_CF 1e-12
+#define EIG_DEGEN_BT 1e-24
 static void eigen7(double rho, double vn, double a2, double bn, double bt1, double bt2,
                    double lam[7], double R[7][7], double L[7][7])
 {
@@ -144,16 +149,26 @@ static void eigen7(double rho, double vn, double a2, double bn, double bt1, doub
     double cf = sqrt(cf2), cs = sqrt(cs2), ca = sqrt(ca2), a = sqrt(a2);
     double dd = cf2 - cs2;
     double af, as;
-    if (dd > 0.0) {
+    /* degenerate limits, taken where the quantity is zero up to round-off   */
+    /* (a state that is degenerate in exact arithmetic, e.g. B = 0 carried   */
+    /* through a Roe flux, comes out with B_t of 1e-23; the basis would then */
+    /* follow the direction of the rounding noise): c_f = c_s when           */
+    /* c_f^2 - c_s^2 <= EIG_DEGEN_CF c_f^2, B_t = 0 when                     */
+    /* |B_t|^2 <= EIG_DEGEN_BT (rho a^2 + B_n^2)                              */
+    if (dd > EIG_DEGEN_CF * cf2) {
         af = sqrt(dmax(0.0, a2 - cs2) / dd);
         as = sqrt(dmax(0.0, cf2 - a2) / dd);
     } else {
         af = 1.0; as = 0.0;
     }
-    double btm = sqrt(bt1 * bt1 + bt2 * bt2);
+    double btm2 = bt1 * bt1 + bt2 * bt2;
     double by, bz;
-    if (btm > 0.0) { by = bt1 / btm; bz = bt2 / btm; }
-    else { by = sqrt(0.5); bz = sqrt(0.5); }
+    if (btm2 > EIG_DEGEN_BT * (rho * a2 + bn * bn)) {
+        double btm = sqrt(btm2);
+        by = bt1 / btm; bz = bt2 / btm;
+    } else {
+        by = sqrt(0.5); bz = sqrt(0.5);
+    }
     double s = sgn1(bn);
     double nrm = 0.5 / a2;
 
@@ -1231,4 +1246,17 @@ void orc_energies(int nx, int ny, int nz, double dx, const double *U, const doub
     out[3] = rmax;
     out[4] = cnt;
     out[5] = jmax / dx;
+}
+
+/* threads of the OpenMP loops (the CPU-baseline timings run 1 and all);    */
+/* returns the count in effect                                              */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }

@@ -88,8 +88,16 @@ def lib():
         L.orc_edge_current.argtypes = [ctypes.c_int] * 3 + [dp, dp]
         L.orc_energies.restype = None
         L.orc_energies.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double, dp, dp, ctypes.c_double, dp]
+        L.orc_set_threads.restype = ctypes.c_int
+        L.orc_set_threads.argtypes = [ctypes.c_int]
         _lib = L
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """OpenMP threads of the oracle's loops (n <= 0: leave as is); returns
+    the count in effect."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def _p(a: np.ndarray):

@@ -147,7 +147,12 @@ __device__ __forceinline__ void eig_setup_r(R rho, R rsr, R vn, R a2, R bn, R bt
     }
     e.a2 = a2;
     R dd = cf2 - cs2;
-    if (dd > R(0)) {
+    // the degenerate limits hold where the quantity is zero up to round-off
+    // (a state degenerate in exact arithmetic -- B = 0 carried through a Roe
+    // flux -- comes out with B_t of 1e-23, and the basis would follow the
+    // direction of that noise): c_f = c_s when c_f^2 - c_s^2 <= 1e-12 c_f^2,
+    // B_t = 0 when |B_t|^2 <= 1e-24 (rho a^2 + B_n^2)
+    if (dd > R(1e-12) * cf2) {
         R idd = R(1) / dd;
         e.af = Num<R>::sqrt_(rmax(R(0), a2 - cs2) * idd);
         e.as = Num<R>::sqrt_(rmax(R(0), cf2 - a2) * idd);
@@ -156,7 +161,7 @@ __device__ __forceinline__ void eig_setup_r(R rho, R rsr, R vn, R a2, R bn, R bt
         e.as = R(0);
     }
     R btm2 = bt1 * bt1 + bt2 * bt2;
-    if (btm2 > R(0)) {
+    if (btm2 > R(1e-24) * (rho * a2 + bn * bn)) {
         R ibt = sizeof(R) == 4 ? Num<R>::rsqrt_(btm2) : R(1) / Num<R>::sqrt_(btm2);
         e.by = bt1 * ibt;
         e.bz = bt2 * ibt;
