@@ -50,23 +50,16 @@ def stages_of(groups):
         out[k] = out.get(k, 0.0) + v
     return {k: out[k] for k in STAGES if k in out}
 SIZES = {"fp64": (8, 8, 8), "fp32": (4, 4, 4), "mixed": (4, 8, 4)}   # (rho/M, e/B, arithmetic) bytes
-# Floating-point operations per face of one VL + PLM + Roe sweep launch:
-# corrector = one cell's characteristic PLM reconstruction and one Roe solve,
-# predictor = one Roe solve.  They are the FADD + FMUL + 2 FFMA counts that
-# ncu reports for the FP32 pencil kernels at 160^3 (y sweeps: one
-# reconstruction per face plus the segment's 1/32 lead-in; the Roe fan check
-# skipped where its bound proves it passes), where every divide and square
-# root is a single MUFU op.  The same arithmetic runs in the FP64 build, whose
-# divides and square roots expand into FMA iterations (1125 executed FP64
-# flops per corrector face at 128^3), so these figures serve all precisions.
-# CTU: tracing = one reconstruction with characteristic tracing, the dB_n/dn
-# source terms and one Roe solve per face (the y tracing pencil, 894.6);
-# ctucorr = the transverse corrections of a cell's two traced states and one
-# Roe solve (the y correction pencil, 523.5); FP32 at 160^3 the same way.
-FLOPS_PER_FACE = {"corrector": {"fp32": 657.0, "fp64": 657.0, "mixed": 657.0},
-                  "predictor": {"fp32": 393.0, "fp64": 393.0, "mixed": 393.0},
-                  "tracing": {"fp32": 895.0, "fp64": 895.0, "mixed": 895.0},
-                  "ctucorr": {"fp32": 524.0, "fp64": 524.0, "mixed": 524.0}}
+# EXECUTED floating-point operations per face of the FP32 sweep kernels: the
+# FADD + FMUL + 2 FFMA counts ncu reports for the pencil kernels at 160^3
+# (corrector = one characteristic PLM reconstruction and one Roe solve,
+# predictor = one Roe solve; CTU tracing and correction pencils likewise),
+# every divide and square root a single MUFU op.  These are what the
+# kernels run, after their exact identities (one-sided Roe flux, sparse
+# eigenvectors, the fan-check bound); the ALGORITHMIC counts of the method
+# come from the oracle (oracle/flops_per_cell.json) and are the roofline's
+# numerator.
+EXEC_FLOPS_PER_FACE = {"corrector": 657.0, "predictor": 393.0, "tracing": 895.0, "ctucorr": 524.0}
 # DRAM bytes (read + write) per face of one sweep launch, per kernel, from
 # dram__bytes_read.sum + dram__bytes_write.sum of the ncu captures in
 # profiles/ (FP32 at 160^3: pencil corrector 233.8 MB, pencil predictor
@@ -87,13 +80,52 @@ def peaks():
     return dict(hbm_gbs=6400.0, src="fallback", sm_max_mhz=2032.0)
 
 
-def alu_peak_tflops(prec, sm_mhz):
-    """dense FP32 / FP64 ALU peak from the unit counts: 148 SMs x 128 FP32
-    lanes x 2 flops per FMA x clock; FP64 at the part's nominal 1.25 TFLOP/s
-    scaled by the clock."""
-    if prec == "fp64":
-        return 1.25 * sm_mhz / 2032.0
-    return 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def alu_peaks(mhd):
+    """FP32 and FP64 FMA throughput measured on this device now
+    (mhd_fma_peak: best of 5 launches of independent FMA chains, CUDA events,
+    at the clocks the device runs); the arithmetic roofline's peak"""
+    return {"fp32": mhd.fma_peak("fp32", 5), "fp64": mhd.fma_peak("fp64", 5),
+            "src": "measured by mhd_fma_peak in this run"}
+
+
+def alu_peak_of(prec, apk):
+    """MIXED runs its arithmetic in FP32 (FP64 only per cell: pressure, CT)"""
+    return apk["fp64"] if prec == "fp64" else apk["fp32"]
+
+
+FLOP_TABLE = os.path.join(ROOT, "oracle", "flops_per_cell.json")
+_flop_table = None
+
+
+def flop_table():
+    """the oracle's operation counts per cell-update, per scheme and stage
+    (written by oracle/flops.py from the oracle's own source compiled with a
+    counting scalar type; read here as data)"""
+    global _flop_table
+    if _flop_table is None:
+        with open(FLOP_TABLE) as fh:
+            _flop_table = json.load(fh)
+    return _flop_table
+
+
+def alg_flops(scheme, kind="nontrivial"):
+    """per-stage algorithmic flops per cell-update of one scheme, with the
+    sweep stages also per face (three faces per cell-update)"""
+    c = flop_table()["combos"]["-".join(scheme)]
+    f = {k: v[kind] for k, v in c.items()}
+    integ = scheme[0]
+    if integ == "vl":
+        per_face = {"predictor": f["riemann_predictor"] / 3,
+                    "corrector": (f["reconstruction"] + f["riemann_corrector"]) / 3}
+    else:
+        per_face = {"tracing": (f["reconstruction_tracing"] + f["riemann_predictor"]) / 3,
+                    "ctucorr": (f["transverse_correction"] + f["riemann_corrector"]) / 3}
+    # per cell of the per-cell kernel groups: the primitive pass is counted
+    # twice in the step (t^n with the CFL maximum, t^{n+1/2} in the half update)
+    per_cell = {"prim_cfl": f["primitives"] / 2 + f["cfl"], "emf1": f["edge_emf"] / 2,
+                "emf2": f["edge_emf"] / 2, "half_update": f["half_update"] + f["primitives"] / 2,
+                "full_update": f["full_update"]}
+    return {"total": f["total"], "per_face": per_face, "per_cell": per_cell}
 
 
 class Clocks:
@@ -238,26 +270,41 @@ def group_bytes(prec, n, integ="vl"):
 STATE_BYTES = {"fp64": 128, "fp32": 64, "mixed": 96}
 
 
-def step_hbm(prec, n, ms_per_step, pk, integ="vl"):
-    """the whole step against the HBM roofline, two ways: (1) the state read
-    once and written once (the ceiling of a fully fused step), (2) the
-    algorithmic bytes of this multi-kernel step (sum over the kernel groups)"""
-    bpc = sum(group_bytes(prec, n, integ).values()) / n
-    gbs = bpc * n / (ms_per_step * 1e-3) / 1e9
+def step_roofline(prec, n, ms_per_step, pk, apk, scheme, flops_per_cell=None):
+    """The whole step against its two ceilings, both from the method, not
+    from this implementation's kernel split: HBM (the state read once and
+    written once: 64 / 96 / 128 B per cell-update) and the arithmetic pipe
+    (the oracle-counted algorithmic flops per cell-update over the measured
+    FMA peak).  The lower ceiling binds; frac = value / that ceiling.  The
+    multi-kernel step's own global traffic (design bytes) is reported beside
+    it, not as a roofline."""
     cups = n / (ms_per_step * 1e-3)
-    ceil = pk["hbm_gbs"] * 1e9 / STATE_BYTES[prec]
-    return {"state_bytes_per_cell_update": STATE_BYTES[prec], "state_roofline_cell_updates_per_s": ceil,
-            "frac_of_state_roofline": cups / ceil,
-            "step_bytes_per_cell_update": bpc, "step_achieved_gbs": gbs, "peak_gbs": pk["hbm_gbs"],
-            "frac": gbs / pk["hbm_gbs"], "peak_src": pk["src"]}
+    hbm_ceil = pk["hbm_gbs"] * 1e9 / STATE_BYTES[prec]
+    fl = flops_per_cell if flops_per_cell is not None else alg_flops(scheme)["total"]
+    fl_raw = alg_flops(scheme, "flops")["total"] if flops_per_cell is None else None
+    alu_peak = alu_peak_of(prec, apk)
+    alu_ceil = alu_peak * 1e12 / fl
+    bound = "alu" if alu_ceil < hbm_ceil else "hbm"
+    design = sum(group_bytes(prec, n, scheme[0]).values()) / n
+    return {"bound": bound, "frac": cups / min(alu_ceil, hbm_ceil),
+            "hbm": {"bytes_per_cell_update": STATE_BYTES[prec], "ceiling_cell_updates_per_s": hbm_ceil,
+                    "frac": cups / hbm_ceil, "peak_gbs": pk["hbm_gbs"], "peak_src": pk["src"]},
+            "alu": {"flops_per_cell_update": fl, "flops_per_cell_update_with_trivial": fl_raw,
+                    "ceiling_cell_updates_per_s": alu_ceil, "frac": cups / alu_ceil, "peak_tflops": alu_peak,
+                    "peak_src": apk["src"], "flops_src": "oracle count, nontrivial operations"},
+            "design_bytes_per_cell_update": design,
+            "design_bytes_achieved_gbs": design * cups / 1e9}
 
 
-def scheme_matrix(torch, mhd, st, steps, stream, pk):
-    """{CTU, VL} x {PLM, PPM} x {HLLD, Roe} x {FP64, FP32} on the same box"""
+def scheme_matrix(torch, mhd, st, steps_fp32, steps_fp64, stream, pk, apk):
+    """{CTU, VL} x {PLM, PPM} x {HLLD, Roe} x {FP64, FP32} on the same box.
+    FP32 runs the 100 steps of the 256^3 workload's statement; FP64 (15-40 x
+    slower, bound by the FP64 rate) fewer, so that the default run stays
+    within minutes."""
     n = int(np.prod(st.U.shape[1:]))
     out = {}
     for prec in ("fp32", "fp64"):
-        k = steps if prec == "fp32" else max(2, steps // 4)
+        k = steps_fp32 if prec == "fp32" else steps_fp64
         for integ in ("ctu", "vl"):
             for recon in ("plm", "ppm"):
                 for riem in ("hlld", "roe"):
@@ -267,7 +314,7 @@ def scheme_matrix(torch, mhd, st, steps, stream, pk):
                     v = n * k / (ms * 1e-3)
                     out[f"{integ}+{recon}+{riem}/{prec}"] = {
                         "value": v, "ms_per_step": ms / k, "steps": k, "sweep": s.tuned,
-                        "frac_of_state_roofline": v * STATE_BYTES[prec] / (pk["hbm_gbs"] * 1e9)}
+                        "step_roofline": step_roofline(prec, n, ms / k, pk, apk, (integ, recon, riem))}
     return out
 
 
@@ -292,35 +339,62 @@ def kernels_of(groups, tuned, integ="vl"):
     return out
 
 
-def roofline(prec, groups, steps, n, pk, sm_mhz, tuned=None, integ="vl"):
-    """dominant kernel of the step and its achieved fraction of the roofline
-    that bounds it"""
+def roofline(prec, groups, steps, n, pk, apk, scheme, tuned=None):
+    """Dominant kernel of the step and its achieved fraction of the roofline
+    that bounds it.  Algorithmic work per launch: the oracle-counted flops
+    and the algorithmic bytes of its units (faces for a sweep, cells for a
+    per-cell kernel).  The bound is picked by that arithmetic intensity
+    against the ridge (measured FMA peak / measured HBM bandwidth); the other
+    side and the kernel's executed flops (ncu counts) are reported beside."""
+    integ = scheme[0]
     ks = kernels_of(groups, tuned, integ)
     dom = max(ks, key=lambda k: ks[k][0])
     tot, launches = ks[dom]
     ms = tot / steps
+    t_launch = ms / launches * 1e-3
     out = {"kernel": dom, "ms_per_step": ms, "share": tot / sum(groups.values()), "launches": launches,
            "ms_per_launch": ms / launches}
+    af = alg_flops(scheme)
     sweep = dom.split("_")[0]
-    fpf = FLOPS_PER_FACE.get(sweep, {}).get(prec)
-    if sweep in ("predictor", "corrector", "tracing", "ctucorr") and fpf:
-        ach = n * fpf / (ms / launches * 1e-3) / 1e12          # per launch: n faces
-        peak = alu_peak_tflops(prec, sm_mhz)
+    alu_peak = alu_peak_of(prec, apk)
+    if sweep in ("predictor", "corrector", "tracing", "ctucorr"):
+        bpu = sweep_bytes_per_face(prec, {"tracing": "tracing", "ctucorr": "ctucorr"}.get(sweep, "vl"))
+        fpu = af["per_face"][sweep]
+        unit_name = "faces"
         tpf = TRAFFIC_PER_FACE.get(dom, {}).get(prec)
-        bpf = sweep_bytes_per_face(prec, {"tracing": "tracing", "ctucorr": "ctucorr"}.get(sweep, "vl"))
-        hbm = n * bpf / (ms / launches * 1e-3) / 1e9
-        out.update(bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
-                   peak_src=f"{'FP64' if prec == 'fp64' else 'FP32'} peak derived from unit counts at {sm_mhz:.0f} MHz",
-                   traffic=(tpf * n if tpf else None),
-                   algorithmic=f"{fpf:.0f} flops per face x {n} faces per launch",
-                   hbm_view={"algorithmic_bytes_per_launch": n * bpf, "achieved_gbs": hbm,
-                             "frac_of_measured": hbm / pk["hbm_gbs"]})
+        traffic = tpf * n if tpf else None
+        executed = EXEC_FLOPS_PER_FACE.get(sweep) if prec != "fp64" else None
     else:
-        stage = {"emf1": "emf1", "emf2": "emf2"}.get(dom, dom)
-        b = group_bytes(prec, n, integ)[stage] / launches
-        ach = b / (ms / launches * 1e-3) / 1e9
-        out.update(bound="hbm", achieved=ach, peak=pk["hbm_gbs"], unit="GB/s", frac=ach / pk["hbm_gbs"],
-                   peak_src=pk["src"], traffic=None, algorithmic_bytes_per_launch=b)
+        stage = dom
+        bpu = group_bytes(prec, n, integ)[stage] / launches / n
+        fpu = af["per_cell"].get(stage, 0.0)
+        unit_name = "cells"
+        traffic, executed = None, None
+    flops, byts = fpu * n, bpu * n
+    ridge = alu_peak * 1e12 / (pk["hbm_gbs"] * 1e9)
+    intensity = flops / byts
+    ach_tf = flops / t_launch / 1e12
+    ach_gbs = byts / t_launch / 1e9
+    hbm_view = {"achieved": ach_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach_gbs / pk["hbm_gbs"],
+                "algorithmic_bytes_per_launch": byts}
+    alu_view = {"achieved": ach_tf, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach_tf / alu_peak,
+                "algorithmic_flops_per_launch": flops}
+    if intensity > ridge:
+        out.update(bound="alu", achieved=ach_tf, peak=alu_peak, unit="TFLOP/s", frac=ach_tf / alu_peak,
+                   peak_src=f"{'FP64' if prec == 'fp64' else 'FP32'} FMA peak, {apk['src']}")
+    else:
+        out.update(bound="hbm", achieved=ach_gbs, peak=pk["hbm_gbs"], unit="GB/s", frac=ach_gbs / pk["hbm_gbs"],
+                   peak_src=f"{pk['src']} copy bandwidth (MEASURED_PEAKS.json)")
+    out.update(traffic=traffic,
+               algorithmic=f"{fpu:.0f} flops (oracle count) and {bpu:.0f} B per {unit_name[:-1]} x {n} {unit_name}"
+                           " per launch",
+               intensity_flop_per_byte=intensity, ridge_flop_per_byte=ridge, hbm_view=hbm_view, alu_view=alu_view)
+    if executed:
+        ex_tf = executed * n / t_launch / 1e12
+        out["executed_view"] = {"flops_per_face": executed, "achieved": ex_tf, "frac": ex_tf / alu_peak,
+                                "intensity_flop_per_byte": executed / bpu,
+                                "note": "FADD + FMUL + 2 FFMA per face from ncu; the kernel's identities run "
+                                        "fewer operations than the method's count"}
     return out
 
 
@@ -334,29 +408,69 @@ def cpu_model():
     return "unknown"
 
 
-def cpu_baseline(scheme, target_s=12.0):
-    """the FP64 oracle as it stands, all host cores, on a 64^3 sample"""
-    from oracle import oracle as O
-    integ, recon, riemann = scheme
-    st = workload(64)
+def _oracle_steps(O, st, scheme, m):
     U, B = st.U.copy(), st.B.copy()
-    t0 = time.perf_counter()
-    dt = O.cfl_dt(U, B, st.dx, st.gamma, 0.3)
-    O.step(U, B, st.dx, st.gamma, dt, integ, recon, riemann)
-    t1 = time.perf_counter() - t0
-    m = max(1, min(40, int(target_s / max(t1, 1e-3))))
     t0 = time.perf_counter()
     for _ in range(m):
         dt = O.cfl_dt(U, B, st.dx, st.gamma, 0.3)
-        O.step(U, B, st.dx, st.gamma, dt, integ, recon, riemann)
-    el = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": 64 ** 3 * m / el, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
-            "sample": f"64^3 ABC (k=4pi, beta=0.5, seed 0), {m} steps of {integ}+{recon}+{riemann} FP64 "
-                      f"incl. the CFL dt, OpenMP on all host threads"}
+        O.step(U, B, st.dx, st.gamma, dt, *scheme)
+    return time.perf_counter() - t0
 
 
-def batch_variant(torch, mhd, K, stream):
+def oracle_rate(O, n, scheme, threads, runs, steps):
+    """median over `runs` runs of `steps` oracle steps (CFL dt included), after
+    one warm-up step, on the n^3 sample of the workload family with
+    `threads` OpenMP threads (0: all host threads); cell-updates/s"""
+    used = O.set_threads(threads if threads > 0 else (os.cpu_count() or 1))
+    st = workload(n)
+    _oracle_steps(O, st, scheme, 1)
+    rates = [n ** 3 * steps / _oracle_steps(O, st, scheme, steps) for _ in range(runs)]
+    O.set_threads(os.cpu_count() or 1)
+    return {"value": statistics.median(rates), "runs": runs, "steps": steps, "threads": used,
+            "spread": [min(rates), max(rates)]}
+
+
+def cpu_baseline(scheme):
+    """The FP64 oracle as it stands, timed on the host cores on bounded
+    samples of the workload family: 64^3 with all host threads (median of
+    5 runs of 2 steps) and with 1 thread (median of 3 runs of 1 step), and
+    128^3 with all threads (median of 3 runs of 1 step); about 10-20 s of CPU
+    work.  The line's value is the all-thread 64^3 rate."""
+    from oracle import oracle as O
+    allc = oracle_rate(O, 64, scheme, 0, 5, 2)
+    one = oracle_rate(O, 64, scheme, 1, 3, 1)
+    big = oracle_rate(O, 128, scheme, 0, 3, 1)
+    return {"value": allc["value"], "unit": UNIT, "cores": allc["threads"], "kind": "oracle", "cpu": cpu_model(),
+            "nproc": os.cpu_count(),
+            "sample": f"{'+'.join(scheme)} FP64 oracle steps (CFL dt included) on the ABC workload family "
+                      f"(k=4pi, beta=0.5, seed 0): 64^3 all threads, median of 5 runs of 2 steps",
+            "one_thread_64": one, "all_threads_64": allc, "all_threads_128": big}
+
+
+def run_cpu_plan(args):
+    """The CPU-baseline plan in full (not a bench line): the FP64 oracle at
+    64^3 and 128^3, 1 thread and all host threads, median of 5 runs of 10
+    steps after one warm-up step, for VL + PLM + Roe; and the eight
+    {VL, CTU} x {PLM, PPM} x {Roe, HLLD} schemes at 64^3 with all threads
+    (median of 5 runs of 2 steps)."""
+    from oracle import oracle as O
+    O.build()
+    head = ("vl", "plm", "roe")
+    out = {"cpu": cpu_model(), "nproc": os.cpu_count(), "headline": {}, "schemes64_all_threads": {}}
+    for n in (64, 128):
+        for th in (1, 0):
+            key = f"{n}^3/{'1 thread' if th == 1 else 'all threads'}"
+            out["headline"][key] = oracle_rate(O, n, head, th, 5, args.cpu_plan_steps)
+            print(key, out["headline"][key], flush=True)
+    for integ in ("vl", "ctu"):
+        for recon in ("plm", "ppm"):
+            for riem in ("roe", "hlld"):
+                out["schemes64_all_threads"][f"{integ}+{recon}+{riem}"] = oracle_rate(O, 64, (integ, recon, riem),
+                                                                                      0, 5, 2)
+    print(json.dumps({"mode": "cpu_plan", **out}), flush=True)
+
+
+def batch_variant(torch, mhd, K, stream, pk, apk):
     """The batched uneven workload: 48 independent periodic boxes with sides
     drawn from {32, 48, 64, 96, 128, 192} (seed 1), linear waves and ABC
     fields in turn, FP32 VL + PPM + HLLD.  One graph-captured batched step
@@ -403,6 +517,7 @@ def batch_variant(torch, mhd, K, stream):
     for c in ctxs:
         c.free()
     return {"value": ncell / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": K, "boxes": 48,
+            "step_roofline": step_roofline("fp32", ncell, ms, pk, apk, ("vl", "ppm", "hlld")),
             "cells": ncell, "sides": sides, "scheme": "vl+ppm+hlld", "precision": "fp32",
             "sweep_tiling": {"tile_len": tl, "blocks_per_sm": bps, "autotune_ms_per_step": tune_ms},
             "launches_per_step": 12, "graph": True,
@@ -410,7 +525,7 @@ def batch_variant(torch, mhd, K, stream):
             "speedup_vs_per_box_loop": ms_loop / ms}
 
 
-def learned_variant(torch, mhd, K, stream):
+def learned_variant(torch, mhd, K, stream, pk, apk):
     """The learned path select on the 384^3 ABC box (k = 6 pi, beta = 0.1) with
     ten seeded Sedov-type blasts (E = 1 in r < 0.05): the selector network is
     trained here on pairs the method generates at 128^3 (ABC, blast and
@@ -433,9 +548,9 @@ def learned_variant(torch, mhd, K, stream):
     del Xh, yh
     out = {}
     states = {}
-    for name in ("full", "selected"):
-        s = mhd.Solver(st.U.shape[1:], st.dx, st.gamma, *LRN.FULL, "fp32", 0.3, stream=stream.cuda_stream,
-                       pfloor=LRN.PFLOOR)
+    for name in ("full", "selected", "cheap"):
+        s = mhd.Solver(st.U.shape[1:], st.dx, st.gamma, *(LRN.CHEAP if name == "cheap" else LRN.FULL), "fp32",
+                       0.3, stream=stream.cuda_stream, pfloor=LRN.PFLOOR)
         U = torch.from_numpy(st.U).to("cuda", torch.float32)
         B = torch.from_numpy(st.B).to("cuda", torch.float32)
         if name == "selected":
@@ -462,13 +577,27 @@ def learned_variant(torch, mhd, K, stream):
                      "floored_cell_steps": s.floor_count()}
         s.free()
     net.free()
+    names = ["rho", "Mx", "My", "Mz", "e", "Bx", "By", "Bz"]
     l1 = LRN.rel_l1_fields(states["selected"], states["full"])
+    l1c = LRN.rel_l1_fields(states["cheap"], states["full"])
+    ncell = st.U[0].size
+    # algorithmic flops of the selected step: the cheap and full schemes in
+    # the proportion of sweep units each ran, plus the network (2 layers of
+    # 48x64 and 64x64 multiply-adds per 4^3 block)
+    fc = out["cheap_fraction_tiles"]
+    mlp = 2.0 * (48 * 64 + 64 * 64 + 64) / 64.0
+    fl_sel = fc * alg_flops(LRN.CHEAP)["total"] + (1 - fc) * alg_flops(LRN.FULL)["total"] + mlp
     return {"value": out["selected"]["value"], "unit": UNIT, "ms_per_step": out["selected"]["ms_per_step"],
             "steps": K, "workload": "abc384_k6pi_beta0.1 + 10 blasts (E=1, r<0.05, seed 2)",
             "precision": "fp32", "full_path": out["full"], "selected_path": out["selected"],
+            "cheap_path": out["cheap"],
+            "step_roofline": step_roofline("fp32", ncell, out["selected"]["ms_per_step"], pk, apk, LRN.FULL,
+                                           flops_per_cell=fl_sel),
             "speedup_vs_all_full": out["full"]["ms_per_step"] / out["selected"]["ms_per_step"],
+            "speedup_of_all_cheap_vs_all_full": out["full"]["ms_per_step"] / out["cheap"]["ms_per_step"],
             "cheap_fraction_blocks": out["cheap_fraction_blocks"], "cheap_fraction_tiles": out["cheap_fraction_tiles"],
-            "rel_l1_vs_all_full_after_steps": dict(zip(["rho", "Mx", "My", "Mz", "e", "Bx", "By", "Bz"], l1)),
+            "rel_l1_vs_all_full_after_steps": dict(zip(names, l1)),
+            "all_cheap_rel_l1_vs_all_full_after_steps": dict(zip(names, l1c)),
             "tau": LRN.TAU, "pfloor": LRN.PFLOOR,
             "training": {"pairs": npairs, "safe_fraction": safe, "wall_s": t_train, "train": conf_train,
                          "held_out_384": conf_held, "loss_first_last": [hist[0], hist[-1]],
@@ -660,17 +789,22 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-matrix", action="store_true", help="skip the 16 scheme x precision combinations")
+    ap.add_argument("--matrix-steps", type=int, default=100, help="FP32 steps per scheme (FP64: a tenth)")
     ap.add_argument("--no-autotune", action="store_true", help="default sweep tiling instead of the autotuned one")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--stress", action="store_true", help="mixed-precision stress run (not a bench line)")
     ap.add_argument("--stress-steps", type=int, default=500)
     ap.add_argument("--stress-shape", type=int, nargs=3, default=[512, 256, 256])
     ap.add_argument("--stress-pfloor", type=float, default=1e-5)
+    ap.add_argument("--cpu-plan", action="store_true", help="the full CPU-baseline plan (not a bench line)")
+    ap.add_argument("--cpu-plan-steps", type=int, default=10)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.stress:
         return run_stress(args)
+    if args.cpu_plan:
+        return run_cpu_plan(args)
 
     import torch
     from paper_1804_03479_b300 import build as Bld
@@ -687,6 +821,7 @@ def main():
     else:
         torch.cuda.set_device(0)
     pk = peaks()
+    apk = alu_peaks(mhd)
     scheme = (args.integrator, args.recon, args.riemann)
     st = workload(args.n)
     n = args.n ** 3
@@ -711,8 +846,9 @@ def main():
                    "precision": args.precision, "cfl": 0.3, "dt": "CFL on device every step",
                    "l2": "state larger than L2 (no flush)", "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
                    "device_bytes": dev_bytes, "sweep": s.tuned},
-        "roofline": roofline(args.precision, groups, rec, n, pk, sm_mhz, s.tuned, args.integrator) if rec else None,
-        "hbm_roofline_step": step_hbm(args.precision, n, ms / args.steps, pk, args.integrator),
+        "roofline": roofline(args.precision, groups, rec, n, pk, apk, scheme, s.tuned) if rec else None,
+        "step_roofline": step_roofline(args.precision, n, ms / args.steps, pk, apk, scheme),
+        "alu_peaks_tflops": apk,
         "kernel_ms_per_step": {k: v / rec for k, v in stages_of(groups).items()} if rec else None,
         "sweep_ms_per_step": {k: v / rec for k, v in groups.items() if "_" in k and k.split("_")[1] in AXES}
         if rec else None,
@@ -729,17 +865,18 @@ def main():
             vv = n * kv / (msv * 1e-3)
             variants[prec] = {"value": vv, "unit": UNIT, "ms_per_step": msv / kv, "steps": kv,
                               "vs_p100_paper": vv / PAPER_P100[prec] if prec in PAPER_P100 else None,
-                              "roofline": roofline(prec, gv, recv, n, pk, sm_mhz, sv.tuned, args.integrator)
+                              "roofline": roofline(prec, gv, recv, n, pk, apk, scheme, sv.tuned)
                               if recv else None,
-                              "hbm_roofline_step": step_hbm(prec, n, msv / kv, pk, args.integrator),
+                              "step_roofline": step_roofline(prec, n, msv / kv, pk, apk, scheme),
                               "kernel_ms_per_step": {k: v / recv for k, v in stages_of(gv).items()} if recv else None,
                               "sweep": sv.tuned}
         if not args.no_matrix:
-            variants["schemes256"] = scheme_matrix(torch, mhd, st, max(3, min(args.steps, 10)), stream, pk)
+            variants["schemes256"] = scheme_matrix(torch, mhd, st, args.matrix_steps, max(2, args.matrix_steps // 10),
+                                                   stream, pk, apk)
         if not args.no_batch:
-            variants["batch48"] = batch_variant(torch, mhd, max(3, min(args.steps, 10)), stream)
+            variants["batch48"] = batch_variant(torch, mhd, max(3, min(args.steps, 10)), stream, pk, apk)
         if not args.no_learned:
-            variants["learned384"] = learned_variant(torch, mhd, max(3, min(args.steps, 10)), stream)
+            variants["learned384"] = learned_variant(torch, mhd, max(3, min(args.steps, 10)), stream, pk, apk)
         line["variants"] = variants
         if not args.no_e2e:
             line["e2e"] = e2e(torch, mhd, st, args.precision, scheme, max(4, min(args.steps, 16)), stream)

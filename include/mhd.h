@@ -276,6 +276,16 @@ void mhd_clear_error(mhd_ctx* ctx);
 /* One-line description of the last error (never NULL). */
 const char* mhd_last_error(mhd_ctx* ctx);
 
+/* Measured fused multiply-add throughput of the current device in TFLOP/s
+ * (2 flops per FMA), the arithmetic peak the benchmark's roofline divides
+ * by: a grid of one full wave of 256-thread blocks, each thread running 8
+ * independent FMA chains, timed with CUDA events (best of `reps` launches
+ * after one warm-up) at the clocks the device is running.  precision
+ * MHD_FP32 or MHD_FP64, 1 <= reps <= 1000, else MHD_EINVAL.  Not part of
+ * the method (the paper has no counterpart); it allocates nothing on the
+ * device.  Synchronises. */
+mhd_status mhd_fma_peak(int precision, int reps, double* tflops);
+
 /* Device memory the context holds, in bytes. */
 long long mhd_device_bytes(mhd_ctx* ctx);
 

@@ -35,7 +35,7 @@ EXPORTS = ["mhd_init", "mhd_set_state", "mhd_get_state", "mhd_cfl_dt", "mhd_step
            "mhd_selector_stats", "mhd_floor_count", "mhd_energies", "mhd_helicity",
            "mhd_set_sweep_pencils", "mhd_get_sweep_pencils", "mhd_set_boundary", "mhd_get_boundary",
            "mhd_pressure_gradient", "mhd_set_dirichlet", "mhd_get_dirichlet", "mhd_set_emf_staging",
-           "mhd_get_emf_staging", "mhd_inject_wait_flag"]
+           "mhd_get_emf_staging", "mhd_inject_wait_flag", "mhd_fma_peak"]
 GROUPS = ["prim_cfl", "predictor_x", "predictor_y", "predictor_z", "emf1", "half_update", "corrector_x",
           "corrector_y", "corrector_z", "emf2", "full_update"]
 
@@ -142,6 +142,7 @@ def lib():
     L.mhd_set_emf_staging.argtypes = [vp, ip]
     L.mhd_get_emf_staging.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip)]
     L.mhd_inject_wait_flag.argtypes = [vp, ctypes.c_uint]
+    L.mhd_fma_peak.argtypes = [ip, ip, dp]
     # every entry point that returns an mhd_status; the others got their
     # restype above (long long, int, void, const char*)
     other = {"mhd_bad_cell", "mhd_clear_error", "mhd_device_bytes", "mhd_floor_count", "mhd_free",
@@ -184,6 +185,15 @@ def step_noalloc(U, B, dx, dt, gamma=5.0 / 3.0, recon="plm", riemann="roe", stre
                                 ctypes.c_void_p(pb), ctypes.c_void_p(stream or 0))
     if st != MHD_OK:
         raise MHDError(st, lib().mhd_last_error(None).decode())
+
+
+def fma_peak(precision="fp32", reps=5):
+    """measured FMA throughput of the current device in TFLOP/s (mhd_fma_peak)"""
+    out = ctypes.c_double()
+    st = lib().mhd_fma_peak(PRECISIONS[precision], reps, ctypes.byref(out))
+    if st != MHD_OK:
+        raise MHDError(st, "mhd_fma_peak failed")
+    return out.value
 
 
 class Solver:

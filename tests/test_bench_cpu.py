@@ -41,15 +41,29 @@ def test_roofline_of_the_dominant_kernel():
     tuned = {"pencil_mask": 7}
     ks = bench.kernels_of(groups, tuned)
     assert ks["corrector_pencil"] == (9.8, 2) and ks["corrector_xwarp"] == (6.2, 1)
-    pk = {"hbm_gbs": 6442.9, "src": "measured"}
-    r = bench.roofline("fp32", groups, steps, n, pk, 2032.0, tuned)
-    assert r["kernel"] == "corrector_pencil" and r["launches"] == 2 and r["bound"] == "alu"
+    pk = {"hbm_gbs": 6491.2, "src": "measured"}
+    apk = {"fp32": 70.0, "fp64": 1.2, "src": "test"}
+    scheme = ("vl", "plm", "roe")
+    r = bench.roofline("fp32", groups, steps, n, pk, apk, scheme, tuned)
+    assert r["kernel"] == "corrector_pencil" and r["launches"] == 2
     per_launch_s = 9.8 / steps / 2 * 1e-3
-    want = n * bench.FLOPS_PER_FACE["corrector"]["fp32"] / per_launch_s / 1e12
-    assert abs(r["achieved"] - want) <= 1e-9 * want
-    assert abs(r["peak"] - 148 * 128 * 2 * 2.032e9 / 1e12) <= 1e-6
-    assert abs(r["frac"] - want / r["peak"]) <= 1e-12
+    fpf = bench.alg_flops(scheme)["per_face"]["corrector"]
+    # the oracle's nontrivial operations: one reconstruction and one Roe solve per face
+    assert 1200 < fpf < 2500
+    flops, byts = n * fpf, n * bench.sweep_bytes_per_face("fp32")
+    assert r["intensity_flop_per_byte"] == pytest.approx(flops / byts)
+    assert r["ridge_flop_per_byte"] == pytest.approx(70.0e12 / 6491.2e9)
+    # above the ridge: the arithmetic side binds
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s" and r["peak"] == 70.0
+    assert r["achieved"] == pytest.approx(flops / per_launch_s / 1e12, rel=1e-12)
+    assert r["frac"] == pytest.approx(r["achieved"] / 70.0, rel=1e-12)
+    assert r["hbm_view"]["frac"] == pytest.approx(byts / per_launch_s / 6491.2e9, rel=1e-12)
+    ex = r["executed_view"]
+    assert ex["achieved"] == pytest.approx(n * bench.EXEC_FLOPS_PER_FACE["corrector"] / per_launch_s / 1e12)
     assert r["traffic"] == pytest.approx(bench.TRAFFIC_PER_FACE["corrector_pencil"]["fp32"] * n)
+    # with a much faster arithmetic pipe the same kernel is HBM-bound
+    r2 = bench.roofline("fp32", groups, steps, n, pk, {"fp32": 1e4, "fp64": 1.0, "src": "t"}, scheme, tuned)
+    assert r2["bound"] == "hbm" and r2["frac"] == pytest.approx(r["hbm_view"]["frac"])
     # without pencils the same groups belong to the tile kernels
     assert "corrector_tile" in bench.kernels_of(groups, {"pencil_mask": 0})
 
@@ -68,12 +82,33 @@ def test_roofline_of_a_ctu_step():
     assert ks["tracing_pencil"] == (pytest.approx(13.9), 2) and ks["tracing_xwarp"] == (8.1, 1)
     assert ks["ctucorr_pencil"] == (pytest.approx(11.7), 2) and ks["ctucorr_xwarp"] == (6.4, 1)
     assert "ctucorr_cell" in bench.kernels_of(groups, {"pencil_mask": 6}, "ctu")
-    pk = {"hbm_gbs": 6442.9, "src": "measured"}
-    r = bench.roofline("fp32", groups, steps, n, pk, 2032.0, tuned, "ctu")
-    assert r["kernel"] == "tracing_pencil" and r["bound"] == "alu"
-    want = n * bench.FLOPS_PER_FACE["tracing"]["fp32"] / (13.9 / steps / 2 * 1e-3) / 1e12
-    assert r["achieved"] == pytest.approx(want, rel=1e-12)
+    pk = {"hbm_gbs": 6491.2, "src": "measured"}
+    apk = {"fp32": 70.0, "fp64": 1.2, "src": "test"}
+    scheme = ("ctu", "plm", "roe")
+    r = bench.roofline("fp32", groups, steps, n, pk, apk, scheme, tuned)
+    assert r["kernel"] == "tracing_pencil"
+    fpf = bench.alg_flops(scheme)["per_face"]["tracing"]
+    want = n * fpf / (13.9 / steps / 2 * 1e-3) / 1e12
+    assert r["alu_view"]["achieved"] == pytest.approx(want, rel=1e-12)
     # tracing: W (8) and B_n in, the flux and both traced states (21) out
     assert bench.sweep_bytes_per_face("fp32", "tracing") == 4 * (8 + 1 + 21)
     assert r["hbm_view"]["algorithmic_bytes_per_launch"] == n * 4 * 30
     assert bench.group_bytes("fp32", n, "ctu")["corrector_sweeps"] == 3 * n * 4 * 37
+
+
+def test_step_roofline_binds_at_the_lower_ceiling():
+    import bench
+    n = 256 ** 3
+    pk = {"hbm_gbs": 6491.2, "src": "measured"}
+    apk = {"fp32": 70.0, "fp64": 1.2, "src": "test"}
+    scheme = ("vl", "plm", "roe")
+    r = bench.step_roofline("fp32", n, 4.4, pk, apk, scheme)
+    cups = n / 4.4e-3
+    fl = bench.alg_flops(scheme)["total"]
+    assert r["hbm"]["ceiling_cell_updates_per_s"] == pytest.approx(6491.2e9 / 64)
+    assert r["alu"]["ceiling_cell_updates_per_s"] == pytest.approx(70e12 / fl)
+    assert r["bound"] == "alu" and r["frac"] == pytest.approx(cups / (70e12 / fl))
+    r64 = bench.step_roofline("fp64", n, 150.0, pk, apk, scheme)
+    assert r64["bound"] == "alu" and r64["alu"]["peak_tflops"] == 1.2
+    rm = bench.step_roofline("mixed", n, 6.0, pk, apk, scheme)
+    assert rm["hbm"]["bytes_per_cell_update"] == 96 and rm["alu"]["peak_tflops"] == 70.0
