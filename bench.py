@@ -574,6 +574,8 @@ def learned_variant(torch, mhd, K, stream, pk, apk):
         states[name] = (U, B)
         out[name] = {"value": st.U[0].size / (ms * 1e-3), "ms_per_step": ms,
                      "kernel_ms_per_step": {k: v / rec for k, v in stages_of(groups).items()},
+                     "sweep_ms_per_step": {k: v / rec for k, v in groups.items()
+                                           if "_" in k and k.split("_")[1] in AXES},
                      "floored_cell_steps": s.floor_count()}
         s.free()
     net.free()

@@ -67,8 +67,10 @@ struct mhd_ctx {
     float* sel_feats;               // [nblocks][48]
     unsigned char* sel_flags;       // [nblocks], 1 = full path
     int* sel_cnt;                   // per list: entries
-    int* sel_list[8];               // per axis: cheap list, full list (tiles, pencil segments or x-warp
-                                    // items; 6/7: the x corrector's items when x runs by warps)
+    int* sel_list[8];               // per axis d: [2d] one byte per unit (tile, pencil segment or x-warp
+                                    // item), 1 = full path, in the units' order; [2d+1] the list of the
+                                    // full units; [6], [7] the same for the x corrector's items when x
+                                    // runs by warps (sel_cnt[2q], sel_cnt[2q+1]: cheap and full counts)
     long long sel_cap;              // entries of each list
     cudaGraphExec_t gexec;
     bool have_graph;
@@ -115,6 +117,21 @@ inline int xwarp_grid(const mhd_ctx* c, int slot)
 inline int pencil_grid(const mhd_ctx* c, int d)
 {
     return (int)((c->B.npth[d] + PENCIL_THREADS - 1) / PENCIL_THREADS);
+}
+
+// grids of the list forms of the pencil and x-warp sweeps (the learned
+// selector's full units): capped at 8 blocks per SM, the kernels stride over
+// the list, so that a short list does not pay for a grid of idle blocks
+inline int list_grid_pencil(const mhd_ctx* c, int d)
+{
+    const int cap = 8 * c->nsm, g = pencil_grid(c, d);
+    return g < cap ? g : cap;
+}
+
+inline int list_grid_xwarp(const mhd_ctx* c, int slot)
+{
+    const int cap = 8 * c->nsm, g = xwarp_grid(c, slot);
+    return g < cap ? g : cap;
 }
 
 inline int sweep_grid(const mhd_ctx* c, int d)

@@ -290,6 +290,43 @@ __device__ __forceinline__ void block_max_to(double v, double* red, unsigned lon
     __syncthreads();
 }
 
+// Pressure recovery (Eq. 5) of one cell in the precision of the stored
+// energy, from rho, M (TU), their quotient v, e (TE) and twice the
+// cell-centred field (the sum of the cell's two faces per axis): the halving
+// is folded into the magnetic energy's factor and done in the arithmetic type
+// for the primitives, both exact (powers of two), which saves three FP64
+// multiplications in the mixed form.
+template <class TU, class TE>
+__device__ __forceinline__ TE cell_pressure(TU rho, TU irho, TU mx, TU my, TU mz, TU vx, TU vy, TU vz, TE e, TE sx,
+                                            TE sy, TE sz, double gam)
+{
+    return TE(gam - 1.0) * (e - kinetic<TU, TE>(rho, irho, mx, my, mz, vx, vy, vz)
+                            - TE(0.125) * (sx * sx + sy * sy + sz * sz));
+}
+
+// CFL signal speed of one cell's primitives: max over axes of |v_d| + c_f,d
+template <class R>
+__device__ __forceinline__ R cell_signal(const R w[8], double gam)
+{
+    const R iw0 = R(1) / w[0];
+    R a2 = sizeof(R) == 4 ? R(gam) * w[4] * iw0 : R(gam) * w[4] / w[0];
+    R sm = R(0);
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const int t1 = d == 2 ? 0 : d + 1, t2 = d == 0 ? 2 : d - 1;
+        R cf = fast_speed(w[0], iw0, a2, w[5 + d], w[5 + t1], w[5 + t2]);
+        sm = rmax(sm, Num<R>::abs_(w[1 + d]) + cf);
+    }
+    return sm;
+}
+
+// CT face update (Eq. 13): b - r * circulation
+template <class TE>
+__device__ __forceinline__ TE ct_face(TE b, TE r, TE circ)
+{
+    return b - r * circ;
+}
+
 template <class R, class TU, class TE, bool OUT = false>
 __global__ void __launch_bounds__(CELL_THREADS) k_prim(Boxes B, StateP<TU, TE> s, R* __restrict__ W, double gam,
                                                        unsigned long long* smax_acc, unsigned long long* bad_cell,
@@ -317,10 +354,7 @@ __global__ void __launch_bounds__(CELL_THREADS) k_prim(Boxes B, StateP<TU, TE> s
             int i, j, k;
             coords(g, lc, i, j, k);
             const long long c = g.off + lc;
-            // twice the cell-centred field (the sum of the two faces): the
-            // halving is folded into the magnetic energy's factor and done in
-            // the arithmetic type for the primitives, both exact (powers of
-            // two), which saves three FP64 multiplications in the mixed form
+            // twice the cell-centred field (the sum of the two faces)
             const TE sx = s.b[0][c] + s.b[0][nbr(g, i, j, k, 0, 1)];
             const TE sy = s.b[1][c] + s.b[1][nbr(g, i, j, k, 1, 1)];
             const TE sz = s.b[2][c] + s.b[2][nbr(g, i, j, k, 2, 1)];
@@ -328,9 +362,7 @@ __global__ void __launch_bounds__(CELL_THREADS) k_prim(Boxes B, StateP<TU, TE> s
             const TU mx = s.m[0][c], my = s.m[1][c], mz = s.m[2][c];
             const TU irho = TU(1) / rho;     // one division (FP64 is slow on this part)
             const TU vx = mx * irho, vy = my * irho, vz = mz * irho;
-            // pressure recovery in the precision of the stored energy
-            TE p = TE(gam - 1.0) * (s.e[c] - kinetic<TU, TE>(rho, irho, mx, my, mz, vx, vy, vz)
-                                    - TE(0.125) * (sx * sx + sy * sy + sz * sz));
+            TE p = cell_pressure<TU, TE>(rho, irho, mx, my, mz, vx, vy, vz, s.e[c], sx, sy, sz, gam);
             if (pfloor > 0.0 && p < TE(pfloor)) {
                 // optional pressure floor.  At the start of a step (nfloor given)
                 // e is raised so that P = pfloor (not conservative); read-only
@@ -346,18 +378,7 @@ __global__ void __launch_bounds__(CELL_THREADS) k_prim(Boxes B, StateP<TU, TE> s
 #pragma unroll
             for (int f = 0; f < 8; f++) W[f * N + c] = w[f];
             if (!(w[0] > R(0)) || !(w[4] > R(0))) atomicMin(bad_cell, (unsigned long long)c);
-            if (smax_acc) {
-                const R iw0 = R(1) / w[0];
-                R a2 = sizeof(R) == 4 ? R(gam) * w[4] * iw0 : R(gam) * w[4] / w[0];
-                R sm = R(0);
-#pragma unroll
-                for (int d = 0; d < 3; d++) {
-                    const int t1 = d == 2 ? 0 : d + 1, t2 = d == 0 ? 2 : d - 1;
-                    R cf = fast_speed(w[0], iw0, a2, w[5 + d], w[5 + t1], w[5 + t2]);
-                    sm = rmax(sm, Num<R>::abs_(w[1 + d]) + cf);
-                }
-                local = (double)sm;
-            }
+            if (smax_acc) local = (double)cell_signal(w, gam);
         }
         run = fmax(run, local);
     }
@@ -445,7 +466,8 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(Boxes B, int d_run, con
                                                          R* __restrict__ WMg, R* __restrict__ WPg,
                                                          const DtBox* __restrict__ dtb, double gam,
                                                          const int* __restrict__ tile_list = nullptr,
-                                                         const int* __restrict__ tile_count = nullptr)
+                                                         const int* __restrict__ tile_count = nullptr,
+                                                         const unsigned char* __restrict__ skip = nullptr)
 {
     const int d = D >= 0 ? D : d_run;
     extern __shared__ unsigned char smem_raw[];
@@ -458,10 +480,12 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(Boxes B, int d_run, con
     R* SPs = sm + nreg * 7;      // [nreg][7] state on the cell's face +1/2
     R* DWs = sm + nreg * 14;     // [nslope][7] PPM slopes
 
-    // all tiles of the batch, or only those of a list (the learned selector's)
+    // all tiles of the batch, or only those of a list, or all but those
+    // marked in skip (the learned selector's full and cheap tiles)
     const int ntile = tile_list ? *tile_count : B.ntile[d];
     for (int it = blockIdx.x; it < ntile; it += gridDim.x) {
         const int tile = tile_list ? tile_list[it] : it;
+        if (skip && skip[tile]) continue;     // block-uniform
         const int bi = box_of_tile(B, d, tile);
         const BoxDev g = B.b[bi];
         const int ntx = (g.nx + t.ex - 1) / t.ex;
@@ -648,8 +672,10 @@ __device__ __forceinline__ void copy7(R d[7], const R s[7])
     for (int m = 0; m < 7; m++) d[m] = s[m];
 }
 
-// seg_list / seg_count: only the segments of a list (the learned selector's),
-// the grid covering every segment of the axis
+// seg_list / seg_count: only the segments of a list (the learned selector's
+// full ones); skip: every segment but those marked (its cheap ones: the grid
+// covers every segment of the axis, so adjacent lanes keep adjacent
+// segments and coalesced loads)
 // The sweep axis D is a template parameter: with a run-time axis the
 // compiler kept the cell windows in local memory (a 240-byte stack frame).
 // MODE 2 (CTU step 1-2): the states are traced to t + dt/2 (recon_cell with
@@ -662,15 +688,21 @@ __global__ void __launch_bounds__(PENCIL_THREADS, (sweep_min_blocks<R, RECON, SO
                                                            const int* __restrict__ seg_list = nullptr,
                                                            const int* __restrict__ seg_count = nullptr,
                                                            R* __restrict__ WMg = nullptr, R* __restrict__ WPg = nullptr,
-                                                           const DtBox* __restrict__ dtb = nullptr)
+                                                           const DtBox* __restrict__ dtb = nullptr,
+                                                           const unsigned char* __restrict__ skip = nullptr)
 {
     constexpr int d = D;
-    long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    // one segment per thread, or with a list a grid-stride loop over it (the
+    // list's grid is capped: most of the axis's segments are not on it)
+    const long long gstride = (long long)gridDim.x * blockDim.x;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x;; it += gstride) {
+    long long gt = it;
     if (seg_list) {
-        if (gt >= *seg_count) return;
-        gt = seg_list[gt];
+        if (it >= *seg_count) return;
+        gt = seg_list[it];
     }
     if (gt >= B.npth[d]) return;
+    if (skip && skip[gt]) return;
     const int bi = box_of_pth(B, d, gt);
     const BoxDev g = B.b[bi];
     int na, nb, ns;
@@ -798,23 +830,26 @@ __global__ void __launch_bounds__(PENCIL_THREADS, (sweep_min_blocks<R, RECON, SO
             copy7(s1, s2);
         }
     }
+    if (!seg_list) return;
+    }
 }
 
 // launch the pencil sweep along a run-time axis d
 template <class R, int RECON, int SOLVER, int MODE, class TE>
 inline void launch_pencil(int d, int grid, cudaStream_t st, const Boxes& g, const R* W, const TE* Bd, R* F,
                           double gam, const int* seg_list = nullptr, const int* seg_count = nullptr,
-                          R* WMg = nullptr, R* WPg = nullptr, const DtBox* dtb = nullptr)
+                          R* WMg = nullptr, R* WPg = nullptr, const DtBox* dtb = nullptr,
+                          const unsigned char* skip = nullptr)
 {
     if (d == 0)
         k_pencil<R, RECON, SOLVER, MODE, TE, 0><<<grid, PENCIL_THREADS, 0, st>>>(g, W, Bd, F, gam, seg_list, seg_count,
-                                                                              WMg, WPg, dtb);
+                                                                              WMg, WPg, dtb, skip);
     else if (d == 1)
         k_pencil<R, RECON, SOLVER, MODE, TE, 1><<<grid, PENCIL_THREADS, 0, st>>>(g, W, Bd, F, gam, seg_list, seg_count,
-                                                                              WMg, WPg, dtb);
+                                                                              WMg, WPg, dtb, skip);
     else
         k_pencil<R, RECON, SOLVER, MODE, TE, 2><<<grid, PENCIL_THREADS, 0, st>>>(g, W, Bd, F, gam, seg_list, seg_count,
-                                                                              WMg, WPg, dtb);
+                                                                              WMg, WPg, dtb, skip);
 }
 
 // ---------------------------------------------------------------------------
@@ -868,8 +903,9 @@ __device__ __forceinline__ int box_of_row(const Boxes& B, long long t)
 
 // One warp per grid row, marching its segments of xw_faces(dslot) faces
 // (dslot: the segment length, at most the kernel's own), the next segment's
-// cell loaded while the current one is computed.  With item_list /
-// item_count a warp takes one listed segment instead (the learned
+// cell loaded while the current one is computed; with skip, the segments
+// marked there are left out of the march.  With item_list / item_count the
+// warps stride over the listed segments instead, one at a time (the learned
 // selector's lists, whose cheap and full kernels share one decomposition).
 //
 // MODE 2 (CTU steps 1-2, x periodic): the lanes reconstruct with tracing and
@@ -884,14 +920,20 @@ __global__ void __launch_bounds__(PENCIL_THREADS, (sweep_min_blocks<R, RECON, SO
                                                           int dslot, const int* __restrict__ item_list = nullptr,
                                                           const int* __restrict__ item_count = nullptr,
                                                           R* __restrict__ WMg = nullptr, R* __restrict__ WPg = nullptr,
-                                                          const DtBox* __restrict__ dtb = nullptr)
+                                                          const DtBox* __restrict__ dtb = nullptr,
+                                                          const unsigned char* __restrict__ skip = nullptr)
 {
     constexpr bool TR = MODE == 2;
     constexpr int LEAD = XW<RECON, MODE>::lead;
     const int FW = xw_faces(dslot);
-    const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
+    // one row per warp, or with a list a grid-stride loop over its items (the
+    // list's grid is capped: most items are not on it).  One body serves both,
+    // so a listed segment is computed with the very instructions of a march.
+    const long long wstride = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;; wid += wstride) {
     int bi, j, k, sg0, sg1;
+    long long item0 = 0;                             // item of segment 0 of the row (skip)
     if (item_list) {
         if (wid >= *item_count) return;              // uniform over the warp
         const long long item = item_list[wid];
@@ -913,6 +955,7 @@ __global__ void __launch_bounds__(PENCIL_THREADS, (sweep_min_blocks<R, RECON, SO
         k = (int)(t / gb.ny);
         sg0 = 0;
         sg1 = (gb.nx + FW - 1) / FW;
+        item0 = gb.xw0[dslot] + t * sg1;
     }
     const int nx = B.b[bi].nx, xout = B.b[bi].bc & 1;
     const long long row = B.b[bi].off + ((long long)k * B.b[bi].ny + j) * nx;
@@ -928,6 +971,13 @@ __global__ void __launch_bounds__(PENCIL_THREADS, (sweep_min_blocks<R, RECON, SO
         const long long ci = row + bidx(xi, nx, xout);
         R wn[7], bnn;
         if (sg + 1 < sg1) load_rot(W, N, row + bidx(xi + FW, nx, xout), 0, wn, bnn);
+        if (skip && skip[item0 + sg]) {              // warp-uniform: another launch's segment
+            if (sg + 1 < sg1) {
+                copy7(w, wn);
+                bn = bnn;
+            }
+            continue;
+        }
         R wl[7], wr[7];
         if (MODE == 0) {
             shfl7(wl, w, 1);
@@ -971,6 +1021,8 @@ __global__ void __launch_bounds__(PENCIL_THREADS, (sweep_min_blocks<R, RECON, SO
             copy7(w, wn);
             bn = bnn;
         }
+    }
+    if (!item_list) return;
     }
 }
 
@@ -1470,7 +1522,7 @@ __global__ void __launch_bounds__(CELL_THREADS) k_full(Boxes B, StateP<TU, TE> s
     for (int d = 0; d < 3; d++) {
         const int t1 = d == 2 ? 0 : d + 1, t2 = d == 0 ? 2 : d - 1;
         const TE curl = (widen<TE>(en[t2][t1]) - widen<TE>(ec[t2])) - (widen<TE>(en[t1][t2]) - widen<TE>(ec[t1]));
-        s.b[d][c] = bo[d] - r * curl;
+        s.b[d][c] = ct_face(bo[d], r, curl);
     }
     }
 }

@@ -283,6 +283,11 @@ extern "C" mhd_status mhd_block_error(mhd_ctx* a, mhd_ctx* b, float* err)
 // the selected step: features -> MLP -> flags -> tile lists -> cheap (PLM in
 // primitives + HLLE) and full (characteristic PPM + HLLD) sweeps
 // ---------------------------------------------------------------------------
+// the selector's skip bytes of unit kind q (0: x predictor items, 6: x
+// corrector items, 2d: the tiles or pencil segments of axis d), one byte per
+// unit in a buffer sized in ints
+static inline unsigned char* sel_of(mhd_ctx* c, int q) { return (unsigned char*)c->sel_list[q]; }
+
 static void run_step_learned(mhd_ctx* c, bool device_dt)
 {
     typedef float R;
@@ -311,43 +316,46 @@ static void run_step_learned(mhd_ctx* c, bool device_dt)
     k_mlp_infer<<<igrid, 256, 0, st>>>(mlp_dev(c->sel), c->sel_feats, nblk, nullptr, c->sel_flags);
     cudaMemsetAsync(c->sel_cnt, 0, 8 * sizeof(int), st);
     const bool xw = c->pencil_mask & 1;
+    // unit q (2d: axis d; 6: the x corrector's items): skip bytes sel_of(c, q),
+    // full list sel_list[q + 1] with its count sel_cnt[q + 1]
     for (int d = 0; d < 3; d++) {
         if (d == 0 && xw) {
-            // x by warps: the predictor's items (31 faces) in lists 0/1, the
+            // x by warps: the predictor's items (31 faces) in 0/1, the
             // corrector's (27 faces, shared by the cheap PLM and full PPM kernels) in 6/7
             k_xw_classify<<<(int)((g.nxw[0] + 255) / 256 < 4096 ? (g.nxw[0] + 255) / 256 : 4096), 256, 0, st>>>(
-                c->hbox[0], 0, c->sel_flags, c->sel_list[0], c->sel_cnt + 0, c->sel_list[1], c->sel_cnt + 1, g.nxw[0]);
+                c->hbox[0], 0, c->sel_flags, sel_of(c, 0), c->sel_list[1], c->sel_cnt + 0, c->sel_cnt + 1, g.nxw[0]);
             k_xw_classify<<<(int)((g.nxw[2] + 255) / 256 < 4096 ? (g.nxw[2] + 255) / 256 : 4096), 256, 0, st>>>(
-                c->hbox[0], 2, c->sel_flags, c->sel_list[6], c->sel_cnt + 6, c->sel_list[7], c->sel_cnt + 7, g.nxw[2]);
+                c->hbox[0], 2, c->sel_flags, sel_of(c, 6), c->sel_list[7], c->sel_cnt + 6, c->sel_cnt + 7, g.nxw[2]);
         } else if (c->pencil_mask >> d & 1)
             k_seg_classify<<<(int)((g.npth[d] + 255) / 256 < 4096 ? (g.npth[d] + 255) / 256 : 4096), 256, 0, st>>>(
-                c->hbox[0], d, g.pl, c->sel_flags, c->sel_list[2 * d], c->sel_cnt + 2 * d, c->sel_list[2 * d + 1],
+                c->hbox[0], d, g.pl, c->sel_flags, sel_of(c, 2 * d), c->sel_list[2 * d + 1], c->sel_cnt + 2 * d,
                 c->sel_cnt + 2 * d + 1, g.npth[d]);
         else
             k_tile_classify<<<(g.ntile[d] + 255) / 256, 256, 0, st>>>(c->hbox[0], d, g.tl, c->sel_flags,
-                                                                       c->sel_list[2 * d], c->sel_cnt + 2 * d,
-                                                                       c->sel_list[2 * d + 1], c->sel_cnt + 2 * d + 1,
+                                                                       sel_of(c, 2 * d), c->sel_list[2 * d + 1],
+                                                                       c->sel_cnt + 2 * d, c->sel_cnt + 2 * d + 1,
                                                                        g.ntile[d]);
     }
     prof_mark(c, 1);
-    // VL steps 1-3
+    // VL steps 1-3: the cheap kernel over every unit but the marked ones
+    // (x: warps marching their rows), the full kernel over the full list
     for (int d = 0; d < 3; d++) {
         if (d == 0 && xw) {
-            k_xwarp<R, PLM_PRIM, HLLE, 0, float><<<xwarp_grid(c, 0), PENCIL_THREADS, 0, st>>>(
-                g, W, s.b[0], F1, gam, 0, c->sel_list[0], c->sel_cnt + 0);
-            k_xwarp<R, PPM, HLLD, 0, float><<<xwarp_grid(c, 0), PENCIL_THREADS, 0, st>>>(
+            k_xwarp<R, PLM_PRIM, HLLE, 0, float><<<xrow_grid(c), PENCIL_THREADS, 0, st>>>(
+                g, W, s.b[0], F1, gam, 0, nullptr, nullptr, nullptr, nullptr, nullptr, sel_of(c, 0));
+            k_xwarp<R, PPM, HLLD, 0, float><<<list_grid_xwarp(c, 0), PENCIL_THREADS, 0, st>>>(
                 g, W, s.b[0], F1, gam, 0, c->sel_list[1], c->sel_cnt + 1);
         } else if (c->pencil_mask >> d & 1) {
             launch_pencil<R, PLM_PRIM, HLLE, 0, float>(d, pencil_grid(c, d), st, g, W, s.b[d],
-                                                          F1 + (long long)d * 7 * n, gam, c->sel_list[2 * d],
-                                                          c->sel_cnt + 2 * d);
-            launch_pencil<R, PPM, HLLD, 0, float>(d, pencil_grid(c, d), st, g, W, s.b[d],
+                                                          F1 + (long long)d * 7 * n, gam, nullptr, nullptr, nullptr,
+                                                          nullptr, nullptr, sel_of(c, 2 * d));
+            launch_pencil<R, PPM, HLLD, 0, float>(d, list_grid_pencil(c, d), st, g, W, s.b[d],
                                                           F1 + (long long)d * 7 * n, gam, c->sel_list[2 * d + 1],
                                                           c->sel_cnt + 2 * d + 1);
         } else {
             k_sweep<R, PLM_PRIM, HLLE, 0, float><<<sweep_grid(c, d), SWEEP_THREADS, 0, st>>>(
-                g, d, W, s.b[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam, c->sel_list[2 * d],
-                c->sel_cnt + 2 * d);
+                g, d, W, s.b[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam, nullptr, nullptr,
+                sel_of(c, 2 * d));
             k_sweep<R, PPM, HLLD, 0, float><<<sweep_grid(c, d), SWEEP_THREADS, 0, st>>>(
                 g, d, W, s.b[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam, c->sel_list[2 * d + 1],
                 c->sel_cnt + 2 * d + 1);
@@ -361,22 +369,22 @@ static void run_step_learned(mhd_ctx* c, bool device_dt)
     // VL steps 4-7
     for (int d = 0; d < 3; d++) {
         if (d == 0 && xw) {
-            k_xwarp<R, PLM_PRIM, HLLE, 1, float><<<xwarp_grid(c, 2), PENCIL_THREADS, 0, st>>>(
-                g, Wh, Bh[0], F1, gam, 2, c->sel_list[6], c->sel_cnt + 6);
-            k_xwarp<R, PPM, HLLD, 1, float><<<xwarp_grid(c, 2), PENCIL_THREADS, 0, st>>>(
+            k_xwarp<R, PLM_PRIM, HLLE, 1, float><<<xrow_grid(c), PENCIL_THREADS, 0, st>>>(
+                g, Wh, Bh[0], F1, gam, 2, nullptr, nullptr, nullptr, nullptr, nullptr, sel_of(c, 6));
+            k_xwarp<R, PPM, HLLD, 1, float><<<list_grid_xwarp(c, 2), PENCIL_THREADS, 0, st>>>(
                 g, Wh, Bh[0], F1, gam, 2, c->sel_list[7], c->sel_cnt + 7);
         } else if (c->pencil_mask >> d & 1) {
             launch_pencil<R, PLM_PRIM, HLLE, 1, float>(d, pencil_grid(c, d), st, g, Wh, Bh[d],
-                                                          F1 + (long long)d * 7 * n, gam, c->sel_list[2 * d],
-                                                          c->sel_cnt + 2 * d);
-            launch_pencil<R, PPM, HLLD, 1, float>(d, pencil_grid(c, d), st, g, Wh, Bh[d],
+                                                          F1 + (long long)d * 7 * n, gam, nullptr, nullptr, nullptr,
+                                                          nullptr, nullptr, sel_of(c, 2 * d));
+            launch_pencil<R, PPM, HLLD, 1, float>(d, list_grid_pencil(c, d), st, g, Wh, Bh[d],
                                                           F1 + (long long)d * 7 * n, gam, c->sel_list[2 * d + 1],
                                                           c->sel_cnt + 2 * d + 1);
         } else {
             k_sweep<R, PLM_PRIM, HLLE, 1, float><<<sweep_grid(c, d), SWEEP_THREADS,
                                                    sweep_smem_bytes<R>(PLM_PRIM, g.tl), st>>>(
-                g, d, Wh, Bh[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam, c->sel_list[2 * d],
-                c->sel_cnt + 2 * d);
+                g, d, Wh, Bh[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam, nullptr, nullptr,
+                sel_of(c, 2 * d));
             k_sweep<R, PPM, HLLD, 1, float><<<sweep_grid(c, d), SWEEP_THREADS, smem, st>>>(
                 g, d, Wh, Bh[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam, c->sel_list[2 * d + 1],
                 c->sel_cnt + 2 * d + 1);
@@ -390,7 +398,7 @@ static void run_step_learned(mhd_ctx* c, bool device_dt)
     if (c->prof_on && c->prof_steps < c->prof_cap) c->prof_steps++;
 }
 
-// selector tile / segment lists large enough for the current sweep layout:
+// selector unit buffers large enough for the current sweep layout:
 // the tiles of the shortest tile length and the pencil segments of the
 // current length, whichever is more (grown when the layout needs more)
 mhd_status mhd_internal_selector_lists(mhd_ctx* c)

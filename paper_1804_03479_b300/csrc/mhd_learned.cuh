@@ -555,14 +555,30 @@ __global__ void __launch_bounds__(256) k_block_err(BoxDev g, StateP<TU, TE> a, S
 }
 
 // ---------------------------------------------------------------------------
-// Tile lists of the learned step: a sweep tile along d is "full" when any
-// 4^3 block holding a cell next to one of its faces is flagged full (so a
-// face takes the full path whenever either neighbouring block asks for it),
-// else "cheap".  One thread per tile of the (single) box.
+// Unit selection of the learned step: a sweep unit (tile, pencil segment or
+// x-warp segment) along d is "full" when any 4^3 block holding a cell next to
+// one of its faces is flagged full (so a face takes the full path whenever
+// either neighbouring block asks for it), else "cheap".  One byte per unit
+// (1 = full), in the units' own order, and a list of the full units: the
+// cheap kernel runs over every unit and skips the marked ones, so adjacent
+// lanes keep adjacent units and their loads stay coalesced (most units are
+// cheap); the full kernel runs over the list only, its warps busy with full
+// units.
 // ---------------------------------------------------------------------------
+// mark a unit, list it if full, count it (the cheap ones one atomic per warp)
+__device__ __forceinline__ void select_unit(long long t, bool full, unsigned char* sel, int* list_full,
+                                            int* cnt_cheap, int* cnt_full)
+{
+    sel[t] = full;
+    if (full) list_full[atomicAdd(cnt_full, 1)] = (int)t;
+    const unsigned act = __activemask();
+    const unsigned nc = __popc(__ballot_sync(act, !full));
+    if ((threadIdx.x & 31) == __ffs(act) - 1 && nc) atomicAdd(cnt_cheap, (int)nc);
+}
+
 __global__ void k_tile_classify(BoxDev g, int d, int tl, const unsigned char* __restrict__ full_flag,
-                                int* __restrict__ list_cheap, int* __restrict__ cnt_cheap, int* __restrict__ list_full,
-                                int* __restrict__ cnt_full, int ntile)
+                                unsigned char* __restrict__ sel, int* __restrict__ list_full,
+                                int* __restrict__ cnt_cheap, int* __restrict__ cnt_full, int ntile)
 {
     const Tile T = tile_of(d, tl);
     const int ntx = (g.nx + T.ex - 1) / T.ex, nty = (g.ny + T.ey - 1) / T.ey;
@@ -587,8 +603,7 @@ __global__ void k_tile_classify(BoxDev g, int d, int tl, const unsigned char* __
                     const int kb = wrapi(kq, nbz), jb = wrapi(jq, nby), ib = wrapi(iq, nbx);
                     full = full_flag[((long long)kb * nby + jb) * nbx + ib] != 0;
                 }
-        if (full) list_full[atomicAdd(cnt_full, 1)] = tile;
-        else list_cheap[atomicAdd(cnt_cheap, 1)] = tile;
+        select_unit(tile, full, sel, list_full, cnt_cheap, cnt_full);
     }
 }
 
@@ -596,8 +611,8 @@ __global__ void k_tile_classify(BoxDev g, int d, int tl, const unsigned char* __
 // any 4^3 block holding one of the cells beside the segment's faces (cells
 // i0-1 .. i1-1 of its line) is flagged
 __global__ void k_seg_classify(BoxDev g, int d, int pl, const unsigned char* __restrict__ full_flag,
-                               int* __restrict__ list_cheap, int* __restrict__ cnt_cheap, int* __restrict__ list_full,
-                               int* __restrict__ cnt_full, long long nseg)
+                               unsigned char* __restrict__ sel, int* __restrict__ list_full,
+                               int* __restrict__ cnt_cheap, int* __restrict__ cnt_full, long long nseg)
 {
     int na, nb, ns;
     pencil_dims(g.nx, g.ny, g.nz, d, pl, na, nb, ns);
@@ -622,8 +637,7 @@ __global__ void k_seg_classify(BoxDev g, int d, int pl, const unsigned char* __r
             else { bi = ia / 4; bj = ib / 4; bk = qb; }
             full = full_flag[((long long)bk * nby + bj) * nbx + bi] != 0;
         }
-        if (full) list_full[atomicAdd(cnt_full, 1)] = (int)t0;
-        else list_cheap[atomicAdd(cnt_cheap, 1)] = (int)t0;
+        select_unit(t0, full, sel, list_full, cnt_cheap, cnt_full);
     }
 }
 
@@ -631,8 +645,8 @@ __global__ void k_seg_classify(BoxDev g, int d, int pl, const unsigned char* __r
 // 4^3 block holding one of the cells beside the item's faces (cells x0-1 ..
 // x1-1 of its row) is flagged
 __global__ void k_xw_classify(BoxDev g, int dslot, const unsigned char* __restrict__ full_flag,
-                              int* __restrict__ list_cheap, int* __restrict__ cnt_cheap, int* __restrict__ list_full,
-                              int* __restrict__ cnt_full, long long nitem)
+                              unsigned char* __restrict__ sel, int* __restrict__ list_full,
+                              int* __restrict__ cnt_cheap, int* __restrict__ cnt_full, long long nitem)
 {
     const int fw = xw_faces(dslot);
     const int nseg = (g.nx + fw - 1) / fw;
@@ -648,8 +662,7 @@ __global__ void k_xw_classify(BoxDev g, int dslot, const unsigned char* __restri
         bool full = false;
         for (int q = q0; q <= q1 && !full; q++)
             full = full_flag[((long long)(k / 4) * nby + j / 4) * nbx + wrapi(q, nbx)] != 0;
-        if (full) list_full[atomicAdd(cnt_full, 1)] = (int)t0;
-        else list_cheap[atomicAdd(cnt_cheap, 1)] = (int)t0;
+        select_unit(t0, full, sel, list_full, cnt_cheap, cnt_full);
     }
 }
 

@@ -102,3 +102,4 @@ def test_resume_is_bitwise(M, integ, recon, solver, prec, graph):
         c.free()
     assert np.array_equal(Ua, Uc) and np.array_equal(Ba, Bc)
     assert not np.array_equal(Ua, U0.astype(Ua.dtype))   # the steps did something
+
