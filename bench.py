@@ -59,17 +59,15 @@ SIZES = {"fp64": (8, 8, 8), "fp32": (4, 4, 4), "mixed": (4, 8, 4)}   # (rho/M, e
 # eigenvectors, the fan-check bound); the ALGORITHMIC counts of the method
 # come from the oracle (oracle/flops_per_cell.json) and are the roofline's
 # numerator.
-EXEC_FLOPS_PER_FACE = {"corrector": 657.0, "predictor": 393.0, "tracing": 895.0, "ctucorr": 524.0}
+EXEC_FLOPS_PER_FACE = {"corrector": 670.0, "predictor": 393.0, "tracing": 895.0, "ctucorr": 524.0}
 # DRAM bytes (read + write) per face of one sweep launch, per kernel, from
 # dram__bytes_read.sum + dram__bytes_write.sum of the ncu captures in
-# profiles/ (FP32 at 160^3: pencil corrector 233.8 MB, pencil predictor
-# 208.2 MB, x-warp corrector 219.4 MB; FP64 pencil corrector 240.0 MB at
-# 128^3), scaled to other sizes by faces; a kernel changed since its capture
-# has none.
-TRAFFIC_PER_FACE = {"corrector_pencil": {"fp32": 58.5, "fp64": 114.4}, "predictor_pencil": {"fp32": 51.1},
-                    "corrector_xwarp": {"fp32": 54.7}, "tracing_pencil": {"fp32": 111.7},
-                    "tracing_xwarp": {"fp32": 113.6}, "ctucorr_pencil": {"fp32": 147.0},
-                    "ctucorr_xwarp": {"fp32": 146.6}}
+# profiles/ (FP32 at 160^3: pencil corrector 242.1 MB, x-warp corrector
+# 225.8 MB for 4,096,000 faces), scaled to other sizes by faces.  A kernel
+# changed since its capture has none (the predictor, CTU tracing and FP64
+# forms were re-built since theirs).
+TRAFFIC_PER_FACE = {"corrector_pencil": {"fp32": 59.1}, "corrector_xwarp": {"fp32": 55.1},
+                    "ctucorr_pencil": {"fp32": 147.0}, "ctucorr_xwarp": {"fp32": 146.6}}
 
 
 def peaks():
@@ -786,7 +784,8 @@ def main():
     ap.add_argument("--integrator", default="vl")
     ap.add_argument("--recon", default="plm")
     ap.add_argument("--riemann", default="roe")
-    ap.add_argument("--variants", default="fp64,mixed", help="other precisions measured beside the main line")
+    ap.add_argument("--variants", default="fp64,mixed",
+                    help="other precisions measured beside the main line (comma list; none: no others)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
@@ -859,7 +858,7 @@ def main():
     }
     if rank == 0:
         variants = {}
-        for prec in [p for p in args.variants.split(",") if p and p != args.precision]:
+        for prec in [p for p in args.variants.split(",") if p in SIZES and p != args.precision]:
             kv = max(3, min(args.steps, 10))
             msv, gv, recv, sv = time_variant(torch, mhd, st, prec, scheme, kv, 2, None, stream,
                                              tune=not args.no_autotune)
