@@ -37,7 +37,24 @@ PAPER_P100 = {"fp32": 1.2e8, "fp64": 5.5e7}   # Sec. 5.2 (i), Tesla P100, VL + P
 # the step's kernel groups as the library's profiler reports them (one per
 # sweep axis) and their aggregation into the seven stages of the step
 AXES = ("x", "y", "z")
-STAGES = ["prim_cfl", "predictor_sweeps", "emf1", "half_update", "corrector_sweeps", "emf2", "full_update"]
+STAGES = ["prim_cfl", "predictor_fused", "predictor_sweeps", "emf1", "half_update", "corrector_sweeps", "emf2",
+          "full_update"]
+
+
+def is_fused(tuned, integ="vl"):
+    """the VL predictor runs as one kernel (pencil-mask bit 3; periodic boxes)"""
+    return integ == "vl" and bool(((tuned or {}).get("pencil_mask", 0) or 0) & 8)
+
+
+def fold_groups(groups, tuned, integ="vl"):
+    """With the fused VL predictor the library's half-update group times the
+    fused kernel, and the predictor-sweep and first edge-field groups are
+    empty (back-to-back events): name the group for what it ran."""
+    if not is_fused(tuned, integ):
+        return groups
+    out = {k: v for k, v in groups.items() if not (k.startswith("predictor_") or k == "emf1")}
+    out["predictor_fused"] = out.pop("half_update", 0.0)
+    return out
 
 
 def stages_of(groups):
@@ -45,7 +62,7 @@ def stages_of(groups):
     out = {}
     for k, v in groups.items():
         for st in ("predictor", "corrector"):
-            if k.startswith(st + "_"):
+            if k.startswith(st + "_") and k.split("_")[1] in AXES:
                 k = st + "_sweeps"
         out[k] = out.get(k, 0.0) + v
     return {k: out[k] for k in STAGES if k in out}
@@ -234,6 +251,7 @@ def time_variant(torch, mhd, st, prec, scheme, K, W, dist, stream, profile=True,
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     groups, rec = s.profile_end() if profile else ({}, 0)
+    groups = fold_groups(groups, s.tuned, integ)
     s.sync()
     ms = max_over_ranks(torch, ms, dist, "cuda")
     return ms, groups, rec, s
@@ -249,18 +267,24 @@ def sweep_bytes_per_face(prec, kind="vl"):
             "ctucorr": 29 * szr + sze + 7 * szr}[kind]
 
 
-def group_bytes(prec, n, integ="vl"):
+def group_bytes(prec, n, integ="vl", fused=False):
     """algorithmic HBM bytes of each stage of one step on n cells: every
     array element a kernel needs is read once and every result written once
-    (neighbour re-reads assumed to hit in cache)"""
+    (neighbour re-reads assumed to hit in cache).  The fused VL predictor
+    reads W, the face field and rho, M, e and writes Bh and Wh."""
     szu, sze, szr = SIZES[prec]
     u = 4 * szu + 4 * sze          # rho, M (TU) and e, B faces (TE)
     emf = (9 + 6 + 3) * szr        # F_rho and the two E fluxes of 3 axes, v and B_cc, E out
     s1, s2 = ("vl", "vl") if integ == "vl" else ("tracing", "ctucorr")
-    return {"prim_cfl": n * (u + 8 * szr), "predictor_sweeps": 3 * n * sweep_bytes_per_face(prec, s1),
-            "emf1": n * emf, "half_update": n * (u + 18 * szr + 3 * sze + 8 * szr),
-            "corrector_sweeps": 3 * n * sweep_bytes_per_face(prec, s2), "emf2": n * emf,
-            "full_update": n * (2 * u + 18 * szr)}
+    out = {"prim_cfl": n * (u + 8 * szr), "predictor_sweeps": 3 * n * sweep_bytes_per_face(prec, s1),
+           "emf1": n * emf, "half_update": n * (u + 18 * szr + 3 * sze + 8 * szr),
+           "corrector_sweeps": 3 * n * sweep_bytes_per_face(prec, s2), "emf2": n * emf,
+           "full_update": n * (2 * u + 18 * szr)}
+    if fused:
+        for k in ("predictor_sweeps", "emf1", "half_update"):
+            del out[k]
+        out["predictor_fused"] = n * (8 * szr + u + 3 * sze + 8 * szr)
+    return out
 
 
 # state bytes per cell update when the state is read once and written once
@@ -268,7 +292,7 @@ def group_bytes(prec, n, integ="vl"):
 STATE_BYTES = {"fp64": 128, "fp32": 64, "mixed": 96}
 
 
-def step_roofline(prec, n, ms_per_step, pk, apk, scheme, flops_per_cell=None):
+def step_roofline(prec, n, ms_per_step, pk, apk, scheme, flops_per_cell=None, fused=False):
     """The whole step against its two ceilings, both from the method, not
     from this implementation's kernel split: HBM (the state read once and
     written once: 64 / 96 / 128 B per cell-update) and the arithmetic pipe
@@ -283,7 +307,7 @@ def step_roofline(prec, n, ms_per_step, pk, apk, scheme, flops_per_cell=None):
     alu_peak = alu_peak_of(prec, apk)
     alu_ceil = alu_peak * 1e12 / fl
     bound = "alu" if alu_ceil < hbm_ceil else "hbm"
-    design = sum(group_bytes(prec, n, scheme[0]).values()) / n
+    design = sum(group_bytes(prec, n, scheme[0], fused).values()) / n
     return {"bound": bound, "frac": cups / min(alu_ceil, hbm_ceil),
             "hbm": {"bytes_per_cell_update": STATE_BYTES[prec], "ceiling_cell_updates_per_s": hbm_ceil,
                     "frac": cups / hbm_ceil, "peak_gbs": pk["hbm_gbs"], "peak_src": pk["src"]},
@@ -312,7 +336,8 @@ def scheme_matrix(torch, mhd, st, steps_fp32, steps_fp64, stream, pk, apk):
                     v = n * k / (ms * 1e-3)
                     out[f"{integ}+{recon}+{riem}/{prec}"] = {
                         "value": v, "ms_per_step": ms / k, "steps": k, "sweep": s.tuned,
-                        "step_roofline": step_roofline(prec, n, ms / k, pk, apk, (integ, recon, riem))}
+                        "step_roofline": step_roofline(prec, n, ms / k, pk, apk, (integ, recon, riem),
+                                                       fused=is_fused(s.tuned, integ))}
     return out
 
 
@@ -327,7 +352,7 @@ def kernels_of(groups, tuned, integ="vl"):
     for k, v in groups.items():
         name, nl = k, 1
         for st in ("predictor", "corrector"):
-            if k.startswith(st + "_"):
+            if k.startswith(st + "_") and k.split("_")[1] in AXES:
                 d = AXES.index(k.split("_")[1])
                 stage = st if integ == "vl" else ("tracing" if st == "predictor" else "ctucorr")
                 other = "cell" if stage == "ctucorr" else "tile"
@@ -355,7 +380,14 @@ def roofline(prec, groups, steps, n, pk, apk, scheme, tuned=None):
     af = alg_flops(scheme)
     sweep = dom.split("_")[0]
     alu_peak = alu_peak_of(prec, apk)
-    if sweep in ("predictor", "corrector", "tracing", "ctucorr"):
+    if dom == "predictor_fused":
+        # per cell: three first-order faces, the three edges, the dt/2 update
+        # and the half-step primitives
+        bpu = group_bytes(prec, n, integ, True)[dom] / n
+        fpu = 3 * af["per_face"]["predictor"] + af["per_cell"]["emf1"] + af["per_cell"]["half_update"]
+        unit_name = "cells"
+        traffic, executed = None, None
+    elif sweep in ("predictor", "corrector", "tracing", "ctucorr"):
         bpu = sweep_bytes_per_face(prec, {"tracing": "tracing", "ctucorr": "ctucorr"}.get(sweep, "vl"))
         fpu = af["per_face"][sweep]
         unit_name = "faces"
@@ -364,7 +396,7 @@ def roofline(prec, groups, steps, n, pk, apk, scheme, tuned=None):
         executed = EXEC_FLOPS_PER_FACE.get(sweep) if prec != "fp64" else None
     else:
         stage = dom
-        bpu = group_bytes(prec, n, integ)[stage] / launches / n
+        bpu = group_bytes(prec, n, integ, is_fused(tuned, integ))[stage] / launches / n
         fpu = af["per_cell"].get(stage, 0.0)
         unit_name = "cells"
         traffic, executed = None, None
@@ -485,6 +517,8 @@ def batch_variant(torch, mhd, K, stream, pk, apk):
     for k, b in enumerate(boxes):
         s.set_state(torch.from_numpy(b.U).to("cuda", torch.float32), torch.from_numpy(b.B).to("cuda", torch.float32), box=k)
     tl, bps, tune_ms = s.autotune(reps=2)
+    mask = s.sweep_pencils()[0]
+    nl = s.launches_per_step()
     s.advance(2, use_graph=True)
     s.sync()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -502,6 +536,7 @@ def batch_variant(torch, mhd, K, stream, pk, apk):
         c = mhd.Solver(b.U.shape[1:], b.dx, 5 / 3, "vl", "ppm", "hlld", "fp32", 0.3, stream=stream.cuda_stream)
         c.set_state(torch.from_numpy(b.U).to("cuda", torch.float32), torch.from_numpy(b.B).to("cuda", torch.float32))
         ctxs.append(c)
+    nl_loop = ctxs[0].launches_per_step()
     for c in ctxs:
         c.advance(1)
     torch.cuda.synchronize()
@@ -515,11 +550,13 @@ def batch_variant(torch, mhd, K, stream, pk, apk):
     for c in ctxs:
         c.free()
     return {"value": ncell / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": K, "boxes": 48,
-            "step_roofline": step_roofline("fp32", ncell, ms, pk, apk, ("vl", "ppm", "hlld")),
+            "step_roofline": step_roofline("fp32", ncell, ms, pk, apk, ("vl", "ppm", "hlld"),
+                                           fused=bool(mask & 8)),
             "cells": ncell, "sides": sides, "scheme": "vl+ppm+hlld", "precision": "fp32",
             "sweep_tiling": {"tile_len": tl, "blocks_per_sm": bps, "autotune_ms_per_step": tune_ms},
-            "launches_per_step": 12, "graph": True,
-            "per_box_loop": {"value": ncell / (ms_loop * 1e-3), "ms_per_step": ms_loop, "launches_per_step": 12 * 48},
+            "pencil_mask": mask, "launches_per_step": nl, "graph": True,
+            "per_box_loop": {"value": ncell / (ms_loop * 1e-3), "ms_per_step": ms_loop,
+                             "launches_per_step": nl_loop * 48},
             "speedup_vs_per_box_loop": ms_loop / ms}
 
 
@@ -566,6 +603,8 @@ def learned_variant(torch, mhd, K, stream, pk, apk):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / K
         groups, rec = s.profile_end()
+        if name != "selected":            # the plain schemes' own sweep configuration
+            groups = fold_groups(groups, {"pencil_mask": s.sweep_pencils()[0]})
         if name == "selected":
             out["cheap_fraction_blocks"], out["cheap_fraction_tiles"] = s.selector_stats()
         s.get_state(U, B)
@@ -848,7 +887,8 @@ def main():
                    "l2": "state larger than L2 (no flush)", "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
                    "device_bytes": dev_bytes, "sweep": s.tuned},
         "roofline": roofline(args.precision, groups, rec, n, pk, apk, scheme, s.tuned) if rec else None,
-        "step_roofline": step_roofline(args.precision, n, ms / args.steps, pk, apk, scheme),
+        "step_roofline": step_roofline(args.precision, n, ms / args.steps, pk, apk, scheme,
+                                       fused=is_fused(s.tuned, scheme[0])),
         "alu_peaks_tflops": apk,
         "kernel_ms_per_step": {k: v / rec for k, v in stages_of(groups).items()} if rec else None,
         "sweep_ms_per_step": {k: v / rec for k, v in groups.items() if "_" in k and k.split("_")[1] in AXES}
@@ -868,7 +908,8 @@ def main():
                               "vs_p100_paper": vv / PAPER_P100[prec] if prec in PAPER_P100 else None,
                               "roofline": roofline(prec, gv, recv, n, pk, apk, scheme, sv.tuned)
                               if recv else None,
-                              "step_roofline": step_roofline(prec, n, msv / kv, pk, apk, scheme),
+                              "step_roofline": step_roofline(prec, n, msv / kv, pk, apk, scheme,
+                                                             fused=is_fused(sv.tuned, scheme[0])),
                               "kernel_ms_per_step": {k: v / recv for k, v in stages_of(gv).items()} if recv else None,
                               "sweep": sv.tuned}
         if not args.no_matrix:

@@ -168,7 +168,8 @@ mhd_status mhd_helicity(mhd_ctx* ctx, double* h);
  * blocks_per_sm x SMs persistent blocks.  mhd_autotune times every pair on
  * the context's own batch (reps steps each, the state restored after each
  * trial), and for the VL integrator also the pencil sweeps below (on all
- * axes or on y and z, segment lengths 8, 16, 32); it keeps the fastest and
+ * axes or on y and z, segment lengths 8, 16, 32, each with and without the
+ * fused predictor where it applies); it keeps the fastest and
  * reports the tiling (ms per step in *ms_best; the pencil choice through
  * mhd_get_sweep_pencils).  The autotuner allocates a temporary copy of the
  * state. */
@@ -217,9 +218,17 @@ mhd_status mhd_get_dirichlet(mhd_ctx* ctx, int axis, int* nlayers);
  * where x is periodic, else by tiles): the 32 lanes of a warp hold 32
  * consecutive cells of a row and exchange neighbour states by shuffles (27
  * to 31 faces per warp).  The results are those of the tile sweeps (the
- * same arithmetic per face).  pencil_mask in [0, 7] (0: tiles everywhere;
- * default 7, with pencil_len 32),
- * pencil_len in [1, 1024], else MHD_EINVAL. */
+ * same arithmetic per face).
+ * Bit 3 (VL, every box periodic, no learned selector; ignored otherwise):
+ * the predictor (Sec. 3.2, VL steps 1-3: first-order fluxes with the face
+ * B_n on all three axes, the corner edge fields of Eqs. 13-14 and the dt/2
+ * update to B^{n+1/2} and the half-step primitives) runs as one kernel that
+ * marches z planes of 32 x 8-cell tiles through shared memory; the
+ * predictor's fluxes and edge fields then never leave the chip, and the
+ * step is 8 launches instead of 12.  The faces of each tile's one-cell halo
+ * ring are solved by both tiles that use them (the same arithmetic).
+ * pencil_mask in [0, 15] (0: tiles everywhere; default 15 for FP32 VL and 7
+ * otherwise, with pencil_len 32), pencil_len in [1, 1024], else MHD_EINVAL. */
 mhd_status mhd_set_sweep_pencils(mhd_ctx* ctx, int pencil_mask, int pencil_len);
 mhd_status mhd_get_sweep_pencils(mhd_ctx* ctx, int* pencil_mask, int* pencil_len);
 

@@ -142,10 +142,11 @@ static void setup_emf_tma(mhd_ctx* c)
 
 // tile prefix sums of the box table for tile length tl; uploads the table
 static void apply_fixed_layers(mhd_ctx* c);
+static void count_launches(mhd_ctx* c);
 
 static cudaError_t layout_tiles(mhd_ctx* c, int tl)
 {
-    int t0[3] = {0, 0, 0}, e0 = 0;
+    int t0[3] = {0, 0, 0}, e0 = 0, f0 = 0;
     long long p0[3] = {0, 0, 0}, w0[3] = {0, 0, 0}, r0 = 0;
     for (int b = 0; b < c->nbox; b++) {
         BoxDev& x = c->hbox[b];
@@ -155,6 +156,8 @@ static cudaError_t layout_tiles(mhd_ctx* c, int tl)
         }
         x.etile0 = e0;
         e0 += emf_tiles_of_box(x.nx, x.ny, x.nz);
+        x.ftile0 = f0;
+        f0 += pred_tiles_of_box(x.nx, x.ny, x.nz, PRED_FZ);
         for (int d = 0; d < 3; d++) {
             x.pth0[d] = p0[d];
             p0[d] += pencil_threads_of_box(x.nx, x.ny, x.nz, d, c->pencil_len);
@@ -173,6 +176,9 @@ static cudaError_t layout_tiles(mhd_ctx* c, int tl)
     c->B.tl = tl;
     for (int d = 0; d < 3; d++) c->B.ntile[d] = t0[d];
     c->B.netile = e0;
+    c->B.nftile = f0;
+    c->B.fz = PRED_FZ;
+    count_launches(c);
     if (c->have_graph) {   // a captured step holds the old tile layout
         cudaGraphExecDestroy(c->gexec);
         c->have_graph = false;
@@ -249,14 +255,16 @@ static mhd_status init_common(int nbox, const mhd_grid* grids, double gamma, con
     if (!c->step) { free(c->hbox); free(c); g_init_err = "scheme combination not built"; return MHD_EUNSUPPORTED; }
     c->plain_step = c->step;
     if (attr != cudaSuccess) { free(c->hbox); free(c); g_init_err = "cudaFuncSetAttribute failed"; return MHD_ECUDA; }
-    c->launches = 12;   // prim, dt, 3 sweeps, emf, half, 3 sweeps or corrections, emf, full
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev);
     c->sweep_bps = 4;
     // register sweeps on every axis: pencils along y and z, warps along x
-    // (CTU with an outflow x axis: tiles along x); the autotuner may change it
-    c->pencil_mask = 7;
+    // (CTU with an outflow x axis: tiles along x), and for FP32 VL the fused
+    // predictor (periodic boxes; in FP64 its halo solves cost more than the
+    // traffic it saves, and the mixed form's face field in FP64 leaves room
+    // for one block per SM); the autotuner may change it
+    c->pencil_mask = scheme->integrator == MHD_VL && scheme->precision == MHD_FP32 ? 15 : 7;
     c->pencil_len = 32;
     c->cell_grid = (int)(vb < 16LL * c->nsm ? vb : 16LL * c->nsm);
     if (c->cell_grid < 1) c->cell_grid = 1;
@@ -669,13 +677,16 @@ extern "C" mhd_status mhd_get_sweep_config(mhd_ctx* c, int* tile_len, int* block
     return MHD_OK;
 }
 
-// kernels per step of a one-box context: the scheme's 12, an outer-face flux
-// pass per outflow axis and stage, a layer reset per Dirichlet axis
+// kernels per step of a one-box context: the scheme's 12 (8 with the fused
+// VL predictor: prim, dt, predictor, 3 sweeps, emf, full), an outer-face
+// flux pass per outflow axis and stage, a layer reset per Dirichlet axis.
+// A context with a learned selector counts its own.
 static void count_launches(mhd_ctx* c)
 {
+    if (c->sel) return;
     // (CTU: one stage-1 outer-face pass per outflow axis; the stage-2 ones
     // are part of the corrections)
-    int n = 12;
+    int n = fused_predictor(c) ? 8 : 12;
     const int per_axis = c->sch.integrator == MHD_VL ? 2 : 1;
     for (int d = 0; d < 3; d++) n += per_axis * (c->bc >> d & 1) + (c->fix_nl[d] > 0);
     c->launches = n;
@@ -778,8 +789,8 @@ extern "C" mhd_status mhd_get_boundary(mhd_ctx* c, int* outflow_mask)
 extern "C" mhd_status mhd_set_sweep_pencils(mhd_ctx* c, int pencil_mask, int pencil_len)
 {
     if (!c) return MHD_EINVAL;
-    if (pencil_mask < 0 || pencil_mask > 7 || pencil_len < 1 || pencil_len > 1024)
-        return fail(c, MHD_EINVAL, "pencil_mask must be in [0, 7] and pencil_len in [1, 1024]");
+    if (pencil_mask < 0 || pencil_mask > 15 || pencil_len < 1 || pencil_len > 1024)
+        return fail(c, MHD_EINVAL, "pencil_mask must be in [0, 15] and pencil_len in [1, 1024]");
     c->pencil_mask = pencil_mask;
     c->pencil_len = pencil_len;
     CK(layout_tiles(c, c->B.tl));
@@ -874,10 +885,11 @@ extern "C" mhd_status mhd_autotune(mhd_ctx* c, int reps, int* tile_len, int* blo
     // pencils on all axes or on y and z only (x keeps the best tiles), per
     // segment length (VL: x by warps; CTU: x by pencil threads)
     {
-        const int masks[2] = {7, 6};
+        const int masks[4] = {7, 6, 15, 14};
         const int lens[3] = {8, 16, 32};
+        const int nmask = c->sch.integrator == MHD_VL && !c->bc && !c->sel ? 4 : 2;
         c->sweep_bps = bbps;
-        for (int i = 0; i < 2 && st == MHD_OK; i++)
+        for (int i = 0; i < nmask && st == MHD_OK; i++)
             for (int j = 0; j < 3 && st == MHD_OK; j++) {
                 c->pencil_mask = masks[i];
                 c->pencil_len = lens[j];

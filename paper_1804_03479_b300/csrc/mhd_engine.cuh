@@ -4,6 +4,7 @@
 #include <stdio.h>
 #include "mhd.h"
 #include "mhd_kernels.cuh"
+#include "mhd_fused.cuh"
 #include "mhd_tma.cuh"
 
 struct mhd_ctx;
@@ -194,6 +195,37 @@ void launch_emf(mhd_ctx* c, const Boxes& g, const R* F, const R* W, R* E, cudaSt
     k_emf<R><<<grid, EMF_THREADS, emf_smem_bytes<R>(), st>>>(g, F, W, E);
 }
 
+// the VL predictor runs fused (k_vl_predictor) when the pencil mask has bit 3,
+// the scheme is VL without a learned selector and every box is periodic
+inline bool fused_predictor(const mhd_ctx* c)
+{
+    return (c->pencil_mask & 8) && c->sch.integrator == MHD_VL && !c->bc;
+}
+
+// VL steps 1-3 in one launch: persistent grid of the blocks one SM keeps
+// resident (registers and the kernel's shared memory) times the SMs; the
+// shared-memory limit is raised on the instance this copy launches (see
+// launch_emf)
+template <class R, class TU, class TE, int SOLVER>
+void launch_vl_predictor(mhd_ctx* c, const Boxes& g, const StateP<TU, TE>& s, const R* W, TE* const Bh[3], R* Wh,
+                         cudaStream_t st)
+{
+    constexpr size_t smem = PredSmem<R, TE>::bytes;
+    cudaFuncSetAttribute(k_vl_predictor<R, TU, TE, SOLVER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static int per = 0;
+    if (per <= 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_vl_predictor<R, TU, TE, SOLVER>, PRED_THREADS,
+                                                          smem) != cudaSuccess || nb < 1)
+            nb = 1;
+        per = nb;
+    }
+    const long long cap = (long long)per * c->nsm;
+    const int grid = (int)(g.nftile < cap ? g.nftile : cap);
+    k_vl_predictor<R, TU, TE, SOLVER><<<grid, PRED_THREADS, smem, st>>>(g, s, W, c->dtc, c->gamma, Bh[0], Bh[1], Bh[2],
+                                                                       Wh, c->sch.pfloor);
+}
+
 // CTU steps 5-6 along axis D (periodic or outflow instantiation): by
 // pencils along y and z and by warps along a periodic x where the pencil
 // mask has the axis, else per cell
@@ -260,33 +292,40 @@ void run_step(mhd_ctx* c, bool device_dt)
     prof_mark(c, 1);
 
     if (INTEG == VL) {
-        // VL steps 1-3: first-order fluxes with the face B_n, edge E, half update
-        for (int d = 0; d < 3; d++) {
-            if ((c->pencil_mask >> d & 1) && d == 0)
-                k_xwarp<R, RECON, SOLVER, 0, TE><<<xrow_grid(c), PENCIL_THREADS, 0, st>>>(
-                    g, W, s.b[d], F1, gam, XW<RECON, 0>::slot);
-            else if (c->pencil_mask >> d & 1)
-                launch_pencil<R, RECON, SOLVER, 0, TE>(d, pencil_grid(c, d), st, g, W, s.b[d],
-                                                       F1 + (long long)d * 7 * n, gam);
-            else
-                k_sweep<R, RECON, SOLVER, 0, TE><<<sweep_grid(c, d), SWEEP_THREADS, 0, st>>>(
-                    g, d, W, s.b[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam);
-            prof_mark(c, 2 + d);
-        }
-        launch_emf<R>(c, g, F1, W, E, st);
-        prof_mark(c, 5);
         const int cs = c->bc ? cross_size(c->hbox[0].nx, c->hbox[0].ny, c->hbox[0].nz) : 0;
-        for (int d = 0; d < 3; d++)
-            if (c->bc >> d & 1)
-                k_outer_flux<R, SOLVER, TE><<<(cs + 127) / 128, 128, 0, st>>>(c->hbox[0], d, W, s.b[d], gam, n,
-                                                                             (R*)c->fout, cs);
-        if (c->bc)
-            k_half<R, TU, TE, true><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2], Wh,
-                                                                 c->sch.pfloor, (const R*)c->fout, cs);
-        else
-            k_half<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2], Wh,
-                                                           c->sch.pfloor);
-        prof_mark(c, 6);
+        if (fused_predictor(c)) {
+            // VL steps 1-3 in one kernel (its time goes to the half-update group)
+            for (int b = 2; b <= 5; b++) prof_mark(c, b);
+            launch_vl_predictor<R, TU, TE, SOLVER>(c, g, s, W, Bh, Wh, st);
+            prof_mark(c, 6);
+        } else {
+            // VL steps 1-3: first-order fluxes with the face B_n, edge E, half update
+            for (int d = 0; d < 3; d++) {
+                if ((c->pencil_mask >> d & 1) && d == 0)
+                    k_xwarp<R, RECON, SOLVER, 0, TE><<<xrow_grid(c), PENCIL_THREADS, 0, st>>>(
+                        g, W, s.b[d], F1, gam, XW<RECON, 0>::slot);
+                else if (c->pencil_mask >> d & 1)
+                    launch_pencil<R, RECON, SOLVER, 0, TE>(d, pencil_grid(c, d), st, g, W, s.b[d],
+                                                           F1 + (long long)d * 7 * n, gam);
+                else
+                    k_sweep<R, RECON, SOLVER, 0, TE><<<sweep_grid(c, d), SWEEP_THREADS, 0, st>>>(
+                        g, d, W, s.b[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam);
+                prof_mark(c, 2 + d);
+            }
+            launch_emf<R>(c, g, F1, W, E, st);
+            prof_mark(c, 5);
+            for (int d = 0; d < 3; d++)
+                if (c->bc >> d & 1)
+                    k_outer_flux<R, SOLVER, TE><<<(cs + 127) / 128, 128, 0, st>>>(c->hbox[0], d, W, s.b[d], gam,
+                                                                                 n, (R*)c->fout, cs);
+            if (c->bc)
+                k_half<R, TU, TE, true><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2],
+                                                                     Wh, c->sch.pfloor, (const R*)c->fout, cs);
+            else
+                k_half<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2], Wh,
+                                                               c->sch.pfloor);
+            prof_mark(c, 6);
+        }
         // VL steps 4-7: reconstruct at the half step, Riemann, edge E, full update
         for (int d = 0; d < 3; d++) {
             if ((c->pencil_mask >> d & 1) && d == 0)

@@ -53,6 +53,7 @@ struct BoxDev {
     float inv_dx;       // 1/dx in single precision
     int etile0;         // first edge-field tile of the box
     int bc;             // bit d set: outflow (zero-gradient) boundaries along axis d, else periodic
+    int ftile0;         // first tile of the box in the fused VL predictor
     long long pth0[3];  // first pencil-segment thread of the box, per axis
     long long xw0[3];   // first x-warp item of the box: predictor, PLM corrector, PPM corrector
     long long xr0;      // first grid row (j, k) of the box
@@ -105,6 +106,8 @@ struct Boxes {
     long long npth[3];  // pencil-segment threads of the batch, per axis
     long long nxw[3];   // x-warp items of the batch: predictor, PLM corrector, PPM corrector
     long long nxr;      // grid rows of the batch
+    int nftile;         // fused VL predictor tiles of the batch
+    int fz;             // their extent along z (planes per tile)
 };
 
 template <class TU, class TE> struct StateP {
@@ -1347,6 +1350,70 @@ __device__ __forceinline__ void outer_divergence(const BoxDev& g, int i, int j, 
     }
 }
 
+// half-step face field (Eq. 13 with dt/2) of a cell's lower faces lo[d] and
+// twice its cell-centred field bc[d] (the sum of the updated lower and upper
+// faces, see k_prim), each circulation in the order of curl_face.  ec[m]:
+// E_m at the cell's own edges; en[m][a]: E_m at the cell shifted by +1 along
+// a != m; on the diagonals the upper faces' circulations need, E_2 at
+// (i+1, j+1, k), E_1 at (i+1, j, k+1), E_0 at (i, j+1, k+1); blo / bhi the
+// face field of the lower / upper faces; r = (dt/2)/dx.
+template <class TE, class R>
+__device__ __forceinline__ void half_faces(const R ec[3], const R en[3][3], R e2xy, R e1xz, R e0yz, const TE blo[3],
+                                           const TE bhi[3], TE r, TE lo[3], TE bc[3])
+{
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const int t1 = d == 2 ? 0 : d + 1, t2 = d == 0 ? 2 : d - 1;
+        // E_t2 at c + e_d + e_t1 and E_t1 at c + e_d + e_t2
+        const R et2d = d == 0 ? e2xy : (d == 1 ? e0yz : e1xz);
+        const R et1d = d == 0 ? e1xz : (d == 1 ? e2xy : e0yz);
+        const TE clo = (widen<TE>(en[t2][t1]) - widen<TE>(ec[t2])) - (widen<TE>(en[t1][t2]) - widen<TE>(ec[t1]));
+        const TE chi = (widen<TE>(et2d) - widen<TE>(en[t2][d])) - (widen<TE>(et1d) - widen<TE>(en[t1][d]));
+        lo[d] = blo[d] - r * clo;
+        const TE hi = bhi[d] - r * chi;
+        bc[d] = lo[d] + hi;
+    }
+}
+
+// divergence of the hydrodynamic fluxes (Eq. 10) of a cell from its lower
+// (fc) and upper (fn) faces per axis, sweep frames back to x, y, z: rho and
+// M in their storage type TU, the energy in TE
+template <class R, class TU, class TE>
+__device__ __forceinline__ void flux_divergence(const R fc[3][5], const R fn[3][5], TU du[4], TE& due)
+{
+    du[0] = du[1] = du[2] = du[3] = TU(0);
+    due = TE(0);
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const int t1 = d == 2 ? 0 : d + 1, t2 = d == 0 ? 2 : d - 1;
+        du[0] += TU(fn[d][0] - fc[d][0]);
+        du[1 + d] += TU(fn[d][1] - fc[d][1]);
+        du[1 + t1] += TU(fn[d][2] - fc[d][2]);
+        du[1 + t2] += TU(fn[d][3] - fc[d][3]);
+        due += widen<TE>(fn[d][4] - fc[d][4]);
+    }
+}
+
+// half-step cell state U^{n+1/2} = U^n - (dt/2) div F (Eq. 10) and its
+// primitives (Eq. 5) with twice the cell-centred half-step field bc;
+// ru, r = (dt/2)/dx in the types TU and TE
+template <class R, class TU, class TE>
+__device__ __forceinline__ void half_prims(TU rho0, TU mx0, TU my0, TU mz0, TE e0, const TU du[4], TE due, TU ru, TE r,
+                                           const TE bc[3], double gam, double pfloor, R w[8])
+{
+    TU rho = rho0 - ru * du[0];
+    TU mx = mx0 - ru * du[1], my = my0 - ru * du[2], mz = mz0 - ru * du[3];
+    TE e = e0 - r * due;
+    const TU irho = TU(1) / rho;
+    TU vx = mx * irho, vy = my * irho, vz = mz * irho;
+    TE p = TE(gam - 1.0) * (e - kinetic<TU, TE>(rho, irho, mx, my, mz, vx, vy, vz)
+                            - TE(0.125) * (bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]));
+    if (pfloor > 0.0 && p < TE(pfloor)) p = TE(pfloor);
+    w[0] = R(rho); w[1] = R(vx); w[2] = R(vy); w[3] = R(vz);
+    w[4] = narrow<R>(p); w[5] = R(0.5) * narrow<R>(bc[0]);
+    w[6] = R(0.5) * narrow<R>(bc[1]); w[7] = R(0.5) * narrow<R>(bc[2]);
+}
+
 // ---------------------------------------------------------------------------
 // a8 + a1: half-step face field B^{n+1/2} = B^n - (dt/2) curl E (Eq. 13) and
 // the half-step cell primitives from U^{n+1/2} = U^n - (dt/2) div F (Eq. 10)
@@ -1404,50 +1471,20 @@ __global__ void __launch_bounds__(CELL_THREADS) k_half(Boxes B, StateP<TU, TE> s
     }
     const TU rho0 = s.rho[c], mx0 = s.m[0][c], my0 = s.m[1][c], mz0 = s.m[2][c];
     const TE e0 = s.e[c];
-    // half-step face field (Eq. 13 with dt/2) of the lower and upper faces,
-    // each circulation in the order of curl_face
-    TE bc[3];
+    TE lo[3], bc[3];
+    half_faces<TE, R>(ec, en, e2xy, e1xz, e0yz, blo, bhi, r, lo, bc);
 #pragma unroll
-    for (int d = 0; d < 3; d++) {
-        const int t1 = d == 2 ? 0 : d + 1, t2 = d == 0 ? 2 : d - 1;
-        // E_t2 at c + e_d + e_t1 and E_t1 at c + e_d + e_t2
-        const R et2d = d == 0 ? e2xy : (d == 1 ? e0yz : e1xz);
-        const R et1d = d == 0 ? e1xz : (d == 1 ? e2xy : e0yz);
-        const TE clo = (widen<TE>(en[t2][t1]) - widen<TE>(ec[t2])) - (widen<TE>(en[t1][t2]) - widen<TE>(ec[t1]));
-        const TE chi = (widen<TE>(et2d) - widen<TE>(en[t2][d])) - (widen<TE>(et1d) - widen<TE>(en[t1][d]));
-        const TE lo = blo[d] - r * clo;
-        const TE hi = bhi[d] - r * chi;
-        Bh[d][c] = lo;
-        bc[d] = lo + hi;                  // twice the cell-centred component (see k_prim)
-    }
-    // divergence of the fluxes, sweep frames back to x, y, z: rho and M in
-    // their storage type TU, the energy in TE
-    TU du[4] = {TU(0), TU(0), TU(0), TU(0)};
-    TE due = TE(0);
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-        const int t1 = d == 2 ? 0 : d + 1, t2 = d == 0 ? 2 : d - 1;
-        du[0] += TU(fn[d][0] - fc[d][0]);
-        du[1 + d] += TU(fn[d][1] - fc[d][1]);
-        du[1 + t1] += TU(fn[d][2] - fc[d][2]);
-        du[1 + t2] += TU(fn[d][3] - fc[d][3]);
-        due += widen<TE>(fn[d][4] - fc[d][4]);
-    }
+    for (int d = 0; d < 3; d++) Bh[d][c] = lo[d];
+    TU du[4];
+    TE due;
+    flux_divergence<R, TU, TE>(fc, fn, du, due);
     // outflow: the last cell's upper neighbour is the cell itself (a zero
     // difference above); add its outer-face flux instead
     if (g.bc) outer_divergence(g, i, j, k, c, N, F, Fout, cs, du, due);
-    const TU ru = DtOf<TU>::hdtdx(dtb[bi]);
-    TU rho = rho0 - ru * du[0];
-    TU mx = mx0 - ru * du[1], my = my0 - ru * du[2], mz = mz0 - ru * du[3];
-    TE e = e0 - r * due;
-    const TU irho = TU(1) / rho;
-    TU vx = mx * irho, vy = my * irho, vz = mz * irho;
-    TE p = TE(gam - 1.0) * (e - kinetic<TU, TE>(rho, irho, mx, my, mz, vx, vy, vz)
-                            - TE(0.125) * (bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]));
-    if (pfloor > 0.0 && p < TE(pfloor)) p = TE(pfloor);
-    Wh[c] = R(rho); Wh[N + c] = R(vx); Wh[2 * N + c] = R(vy); Wh[3 * N + c] = R(vz);
-    Wh[4 * N + c] = narrow<R>(p); Wh[5 * N + c] = R(0.5) * narrow<R>(bc[0]);
-    Wh[6 * N + c] = R(0.5) * narrow<R>(bc[1]); Wh[7 * N + c] = R(0.5) * narrow<R>(bc[2]);
+    R w[8];
+    half_prims<R, TU, TE>(rho0, mx0, my0, mz0, e0, du, due, DtOf<TU>::hdtdx(dtb[bi]), r, bc, gam, pfloor, w);
+#pragma unroll
+    for (int f = 0; f < 8; f++) Wh[f * N + c] = w[f];
     }
 }
 
@@ -1494,17 +1531,9 @@ __global__ void __launch_bounds__(CELL_THREADS) k_full(Boxes B, StateP<TU, TE> s
     }
     const TU rho0 = s.rho[c], mx0 = s.m[0][c], my0 = s.m[1][c], mz0 = s.m[2][c];
     const TE e0 = s.e[c], b00 = s.b[0][c], b10 = s.b[1][c], b20 = s.b[2][c];
-    TU du[4] = {TU(0), TU(0), TU(0), TU(0)};
-    TE due = TE(0);
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-        const int t1 = d == 2 ? 0 : d + 1, t2 = d == 0 ? 2 : d - 1;
-        du[0] += TU(fn[d][0] - fc[d][0]);
-        du[1 + d] += TU(fn[d][1] - fc[d][1]);
-        du[1 + t1] += TU(fn[d][2] - fc[d][2]);
-        du[1 + t2] += TU(fn[d][3] - fc[d][3]);
-        due += widen<TE>(fn[d][4] - fc[d][4]);
-    }
+    TU du[4];
+    TE due;
+    flux_divergence<R, TU, TE>(fc, fn, du, due);
     // outflow: the last cell's upper neighbour is the cell itself (a zero
     // difference above); add its outer-face flux instead
     if (g.bc) outer_divergence(g, i, j, k, c, N, F, Fout, cs, du, due);

@@ -437,7 +437,7 @@ extern "C" mhd_status mhd_set_selector(mhd_ctx* c, mhd_mlp* m)
     if (!m) {   // back to the plain scheme
         c->sel = nullptr;
         c->step = c->plain_step;
-        c->launches = 12;
+        c->launches = mhd::fused_predictor(c) ? 8 : 12;
         if (c->have_graph) { cudaGraphExecDestroy(c->gexec); c->have_graph = false; }
         return MHD_OK;
     }
