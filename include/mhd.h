@@ -233,23 +233,39 @@ mhd_status mhd_set_sweep_pencils(mhd_ctx* ctx, int pencil_mask, int pencil_len);
 mhd_status mhd_get_sweep_pencils(mhd_ctx* ctx, int* pencil_mask, int* pencil_len);
 
 /* Staging of the edge-field kernel (Sec. 2, Eqs. 13-14; the corner-averaged
- * edge fields of both stages).  mode 0 (the default): each thread of the
- * kernel loads its staged cell of every plane (32 x 16 cells per block, two
- * blocks per SM).  mode 1: the planes are staged by the tensor memory
- * accelerator where the context allows it -- bulk tensor copies of whole
- * field planes into a ring of three shared-memory plane slots per block
- * (32 x 8 cells, three blocks per SM), refilled by a producer warp while
- * the block computes.  That needs one box, FP32 or MIXED precision, nx a
- * multiple of 4, nx >= 40 and ny >= 9; elsewhere mode 1 falls back to the
- * per-thread loads.  Both forms give the same edge fields bit for bit; on
- * the B300 the per-thread form is the faster (0.30 against 0.45 ms per
- * launch at 256^3).  mode in {0, 1}, else MHD_EINVAL.  mhd_get_emf_staging
- * reports the requested mode and whether the tensor copies are in use
- * (active = 1).  A plane wait that gives up (after about 2 s) sets a device
- * flag (bit 0: a consumer's wait for a filled slot, bit 1: the producer's
- * wait for a free one), and the next call that reads the device flags
- * (mhd_sync, mhd_cfl_dt, mhd_divB, mhd_sums, mhd_get_state, ...) returns
- * MHD_ETIMEOUT until mhd_clear_error. */
+ * edge fields of both stages).  mode 2: the edge fields are
+ * computed by the kernel of the update that uses them (the dt/2 update to
+ * B^{n+1/2} with the half-step primitives, or the full update): tiles of
+ * 32 x 8 cells march along z, each plane's v, B and mass and B fluxes are
+ * staged in shared memory by asynchronous copies, the edge fields stay in
+ * shared memory and the cells below are updated from them, so the edge
+ * fields never pass through device memory and the step has one launch
+ * fewer per stage.  That needs periodic boxes; elsewhere mode 2 runs as mode
+ * 0.  It moves 43 values per FP32 cell-update against 52, but on the B300
+ * it is the slower form (0.86 against 0.74 ms for the corrector's edge
+ * fields and full update at 256^3): with 16 resident warps per SM it issues
+ * about three times the instructions of the two separate kernels and
+ * waits on its plane barriers, where the separate kernels stream at close
+ * to the copy bandwidth.  mode 0 (the default): a separate
+ * edge-field kernel in which each thread loads its staged cell of every
+ * plane (32 x 16 cells per block, two blocks per SM), then the update
+ * kernel.  mode 1: the planes of that separate kernel are staged by the
+ * tensor memory accelerator where the context allows it -- bulk tensor
+ * copies of whole field planes into a ring of three shared-memory plane
+ * slots per block (32 x 8 cells, three blocks per SM), refilled by a
+ * producer warp while the block computes.  That needs one box, FP32 or
+ * MIXED precision, nx a multiple of 4, nx >= 40 and ny >= 9; elsewhere
+ * mode 1 runs as mode 0.  Modes 0 and 1 give the same edge fields bit for
+ * bit; on the B300 the per-thread form is the faster of the two (0.30
+ * against 0.45 ms per launch at 256^3).  mode in {0, 1, 2}, else
+ * MHD_EINVAL.  mhd_get_emf_staging reports the requested mode and the form
+ * in use (active: 0 separate kernel with per-thread loads, 1 tensor copies,
+ * 2 fused with the update).  A plane wait of the tensor-copy form that
+ * gives up (after about 2 s) sets a device flag (bit 0: a consumer's wait
+ * for a filled slot, bit 1: the producer's wait for a free one), and the
+ * next call that reads the device flags (mhd_sync, mhd_cfl_dt, mhd_divB,
+ * mhd_sums, mhd_get_state, ...) returns MHD_ETIMEOUT until
+ * mhd_clear_error. */
 mhd_status mhd_set_emf_staging(mhd_ctx* ctx, int mode);
 mhd_status mhd_get_emf_staging(mhd_ctx* ctx, int* mode, int* active);
 

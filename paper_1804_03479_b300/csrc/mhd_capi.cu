@@ -102,7 +102,7 @@ static void setup_emf_tma(mhd_ctx* c)
 {
     const int was = c->emf_tma;
     c->emf_tma = 0;
-    if (c->emf_stage_req && c->nbox == 1 && c->szr == 4) {
+    if (c->emf_stage_req == 1 && c->nbox == 1 && c->szr == 4) {
         const BoxDev& b = c->hbox[0];
         if (b.nx % 4 == 0 && b.nx >= TMA_X && b.ny >= TmaPlane<TMA_TY>::Y) {
             if (!c->tmaps) c->tmaps = (CUtensorMap*)aligned_alloc(64, 6 * sizeof(CUtensorMap));
@@ -306,8 +306,10 @@ static mhd_status init_common(int nbox, const mhd_grid* grids, double gamma, con
     if (e == cudaSuccess) e = dalloc(c, (void**)&c->perr, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemsetAsync(c->perr, 0, sizeof(unsigned), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->dt, 0, sizeof(double) * nbox, c->stream);
-    if (e == cudaSuccess) e = layout_tiles(c, 8);
-    c->emf_stage_req = 0;   // per-thread loads: faster on the B300 (see mhd_set_emf_staging)
+    // edge fields by their own kernel with per-thread loads: on the B300 the
+    // faster of the three forms (see mhd_set_emf_staging)
+    c->emf_stage_req = 0;
+    if (e == cudaSuccess) e = layout_tiles(c, 8);   // (counts the launches of the step)
     if (e != cudaSuccess) {
         g_init_err = e == cudaErrorMemoryAllocation ? "device allocation failed" : cudaGetErrorString(e);
         mhd_status s = e == cudaErrorMemoryAllocation ? MHD_ENOMEM : MHD_ECUDA;
@@ -678,19 +680,27 @@ extern "C" mhd_status mhd_get_sweep_config(mhd_ctx* c, int* tile_len, int* block
 }
 
 // kernels per step of a one-box context: the scheme's 12 (8 with the fused
-// VL predictor: prim, dt, predictor, 3 sweeps, emf, full), an outer-face
-// flux pass per outflow axis and stage, a layer reset per Dirichlet axis.
-// A context with a learned selector counts its own.
+// VL predictor: prim, dt, predictor, 3 sweeps, emf, full; one fewer per
+// edge-field kernel fused with its update), an outer-face flux pass per
+// outflow axis and stage, a layer reset per Dirichlet axis.  With a learned
+// selector: the scheme's 12, the features, the network, the three lists and
+// the other path's six sweeps.
 static void count_launches(mhd_ctx* c)
 {
-    if (c->sel) return;
+    if (c->sel) {
+        c->launches = 12 + 3 + 3 + 6 - (emf_form(c) == 2 ? 2 : 0);
+        return;
+    }
     // (CTU: one stage-1 outer-face pass per outflow axis; the stage-2 ones
     // are part of the corrections)
     int n = fused_predictor(c) ? 8 : 12;
+    if (emf_form(c) == 2) n -= fused_predictor(c) ? 1 : 2;   // each edge-field kernel takes its update
     const int per_axis = c->sch.integrator == MHD_VL ? 2 : 1;
     for (int d = 0; d < 3; d++) n += per_axis * (c->bc >> d & 1) + (c->fix_nl[d] > 0);
     c->launches = n;
 }
+
+void mhd_internal_count_launches(mhd_ctx* c) { count_launches(c); }
 
 static void apply_fixed_layers(mhd_ctx* c)
 {
@@ -809,9 +819,15 @@ extern "C" mhd_status mhd_get_sweep_pencils(mhd_ctx* c, int* pencil_mask, int* p
 extern "C" mhd_status mhd_set_emf_staging(mhd_ctx* c, int mode)
 {
     if (!c) return MHD_EINVAL;
-    if (mode != 0 && mode != 1) return fail(c, MHD_EINVAL, "mode must be 0 or 1");
+    if (mode < 0 || mode > 2) return fail(c, MHD_EINVAL, "mode must be 0, 1 or 2");
+    const int was = emf_form(c);
     c->emf_stage_req = mode;
     setup_emf_tma(c);
+    if (emf_form(c) != was && c->have_graph) {   // a captured step holds the other kernels
+        cudaGraphExecDestroy(c->gexec);
+        c->have_graph = false;
+    }
+    count_launches(c);
     return MHD_OK;
 }
 
@@ -819,7 +835,7 @@ extern "C" mhd_status mhd_get_emf_staging(mhd_ctx* c, int* mode, int* active)
 {
     if (!c || !mode || !active) return fail(c, MHD_EINVAL, "null pointer");
     *mode = c->emf_stage_req;
-    *active = c->emf_tma;
+    *active = emf_form(c);
     return MHD_OK;
 }
 

@@ -28,7 +28,8 @@ struct mhd_ctx {
     int fix_nl[3];                  // Dirichlet sides: fixed ghost layers at each end of axis d (0: none)
     mhd::FixedState fix[3][2];      // their states, lower and upper end
     int pencil_mask;                // VL sweeps by pencils on the axes of these bits
-    int emf_stage_req;              // edge fields: 1 = planes by the tensor memory accelerator where eligible
+    int emf_stage_req;              // edge fields: 0 = k_emf, 1 = planes by the tensor memory accelerator
+                                    // where eligible, 2 = fused with the update (k_emf_update) where eligible
     int emf_tma;                    // 1 when the context runs k_emf_tma
     int emf_tma_grid;               // its grid: min(SMs, tiles)
     CUtensorMap* tmaps;             // [6] 64-byte aligned 4-D tensors of k_emf_tma: W, Wh (3-field copies),
@@ -202,6 +203,38 @@ inline bool fused_predictor(const mhd_ctx* c)
     return (c->pencil_mask & 8) && c->sch.integrator == MHD_VL && !c->bc;
 }
 
+// the edge-field form a step runs: 1 = k_emf_tma, 2 = k_emf_update (the
+// edge fields fused with the update; periodic boxes), 0 = k_emf followed by
+// the update kernel
+inline int emf_form(const mhd_ctx* c)
+{
+    if (c->emf_tma) return 1;
+    return c->emf_stage_req == 2 && !c->bc ? 2 : 0;
+}
+
+// k_emf_update: the edge fields of F and W, then the half (HALF: into Bh and
+// Wh) or full update; persistent grid as launch_vl_predictor
+template <class R, class TU, class TE, bool HALF>
+void launch_emf_update(mhd_ctx* c, const Boxes& g, const StateP<TU, TE>& s, const R* F, const R* W, TE* const* Bh,
+                       R* Wh, cudaStream_t st)
+{
+    constexpr size_t smem = emf_update_smem_bytes<R>();
+    cudaFuncSetAttribute(k_emf_update<R, TU, TE, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static int per = 0;
+    if (per <= 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_emf_update<R, TU, TE, HALF>, EU_THREADS, smem) !=
+                cudaSuccess || nb < 1)
+            nb = 1;
+        per = nb;
+    }
+    const long long cap = (long long)per * c->nsm;
+    const int grid = (int)(g.nftile < cap ? g.nftile : cap);
+    k_emf_update<R, TU, TE, HALF><<<grid, EU_THREADS, smem, st>>>(g, s, F, W, c->dtc, c->gamma, HALF ? Bh[0] : nullptr,
+                                                                 HALF ? Bh[1] : nullptr, HALF ? Bh[2] : nullptr, Wh,
+                                                                 c->sch.pfloor);
+}
+
 // VL steps 1-3 in one launch: persistent grid of the blocks one SM keeps
 // resident (registers and the kernel's shared memory) times the SMs; the
 // shared-memory limit is raised on the instance this copy launches (see
@@ -312,18 +345,24 @@ void run_step(mhd_ctx* c, bool device_dt)
                         g, d, W, s.b[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam);
                 prof_mark(c, 2 + d);
             }
-            launch_emf<R>(c, g, F1, W, E, st);
-            prof_mark(c, 5);
-            for (int d = 0; d < 3; d++)
-                if (c->bc >> d & 1)
-                    k_outer_flux<R, SOLVER, TE><<<(cs + 127) / 128, 128, 0, st>>>(c->hbox[0], d, W, s.b[d], gam,
-                                                                                 n, (R*)c->fout, cs);
-            if (c->bc)
-                k_half<R, TU, TE, true><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2],
-                                                                     Wh, c->sch.pfloor, (const R*)c->fout, cs);
-            else
-                k_half<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2], Wh,
-                                                               c->sch.pfloor);
+            if (emf_form(c) == 2) {   // edge fields and half update in one kernel (its time: the half group)
+                prof_mark(c, 5);
+                launch_emf_update<R, TU, TE, true>(c, g, s, F1, W, Bh, Wh, st);
+            } else {
+                launch_emf<R>(c, g, F1, W, E, st);
+                prof_mark(c, 5);
+                for (int d = 0; d < 3; d++)
+                    if (c->bc >> d & 1)
+                        k_outer_flux<R, SOLVER, TE><<<(cs + 127) / 128, 128, 0, st>>>(c->hbox[0], d, W, s.b[d],
+                                                                                     gam, n, (R*)c->fout, cs);
+                if (c->bc)
+                    k_half<R, TU, TE, true><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1],
+                                                                         Bh[2], Wh, c->sch.pfloor,
+                                                                         (const R*)c->fout, cs);
+                else
+                    k_half<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2],
+                                                                   Wh, c->sch.pfloor);
+            }
             prof_mark(c, 6);
         }
         // VL steps 4-7: reconstruct at the half step, Riemann, edge E, full update
@@ -339,16 +378,21 @@ void run_step(mhd_ctx* c, bool device_dt)
                     g, d, Wh, Bh[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam);
             prof_mark(c, 7 + d);
         }
-        launch_emf<R>(c, g, F1, Wh, E, st);
-        prof_mark(c, 10);
-        for (int d = 0; d < 3; d++)
-            if (c->bc >> d & 1)
-                k_outer_flux<R, SOLVER, TE><<<(cs + 127) / 128, 128, 0, st>>>(c->hbox[0], d, Wh, Bh[d], gam, n,
-                                                                             (R*)c->fout, cs);
-        if (c->bc)
-            k_full<R, TU, TE, true><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, (const R*)c->fout, cs);
-        else
-            k_full<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc);
+        if (emf_form(c) == 2) {       // edge fields and full update in one kernel (the full group)
+            prof_mark(c, 10);
+            launch_emf_update<R, TU, TE, false>(c, g, s, F1, Wh, nullptr, nullptr, st);
+        } else {
+            launch_emf<R>(c, g, F1, Wh, E, st);
+            prof_mark(c, 10);
+            for (int d = 0; d < 3; d++)
+                if (c->bc >> d & 1)
+                    k_outer_flux<R, SOLVER, TE><<<(cs + 127) / 128, 128, 0, st>>>(c->hbox[0], d, Wh, Bh[d], gam,
+                                                                                 n, (R*)c->fout, cs);
+            if (c->bc)
+                k_full<R, TU, TE, true><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, (const R*)c->fout, cs);
+            else
+                k_full<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc);
+        }
         fix_layers(c, s, st);
         prof_mark(c, 11);
     } else {
@@ -379,8 +423,14 @@ void run_step(mhd_ctx* c, bool device_dt)
             prof_mark(c, 2 + d);
         }
         // steps 3-4: edge E at t^n, dt/2 update of face B and cell state
-        launch_emf<R>(c, g, F1, W, E, st);
-        prof_mark(c, 5);
+        const bool eu = emf_form(c) == 2;
+        if (eu) {
+            prof_mark(c, 5);
+            launch_emf_update<R, TU, TE, true>(c, g, s, F1, W, Bh, Wh, st);
+        } else {
+            launch_emf<R>(c, g, F1, W, E, st);
+            prof_mark(c, 5);
+        }
         // outflow: stage-1 fluxes through the outer faces (the last cells'
         // own traced states) into the first half of the outer-flux buffer;
         // the corrections write the stage-2 ones into the second half
@@ -394,7 +444,7 @@ void run_step(mhd_ctx* c, bool device_dt)
         if (c->bc)
             k_half<R, TU, TE, true><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2], Wh,
                                                                  c->sch.pfloor, fo1, cs);
-        else
+        else if (!eu)
             k_half<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2], Wh,
                                                            c->sch.pfloor);
         prof_mark(c, 6);
@@ -406,12 +456,17 @@ void run_step(mhd_ctx* c, bool device_dt)
         ctu_correct_axis<R, SOLVER, TE, 2>(c, g, WM, WP, W, F1, Bh[2], F2, gam, fo1, cs, fo2, st);
         prof_mark(c, 9);
         // steps 7-8
-        launch_emf<R>(c, g, F2, Wh, E, st);
-        prof_mark(c, 10);
-        if (c->bc)
-            k_full<R, TU, TE, true><<<nb, CELL_THREADS, 0, st>>>(g, s, F2, E, c->dtc, fo2, cs);
-        else
-            k_full<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F2, E, c->dtc);
+        if (eu) {
+            prof_mark(c, 10);
+            launch_emf_update<R, TU, TE, false>(c, g, s, F2, Wh, nullptr, nullptr, st);
+        } else {
+            launch_emf<R>(c, g, F2, Wh, E, st);
+            prof_mark(c, 10);
+            if (c->bc)
+                k_full<R, TU, TE, true><<<nb, CELL_THREADS, 0, st>>>(g, s, F2, E, c->dtc, fo2, cs);
+            else
+                k_full<R, TU, TE><<<nb, CELL_THREADS, 0, st>>>(g, s, F2, E, c->dtc);
+        }
         fix_layers(c, s, st);
         prof_mark(c, 11);
     }

@@ -1488,6 +1488,28 @@ __global__ void __launch_bounds__(CELL_THREADS) k_half(Boxes B, StateP<TU, TE> s
     }
 }
 
+// full update of cell c in place: rho and M in their storage type, the
+// energy in TE (Eq. 10) from the flux divergence du, due; the face field by
+// CT (Eq. 13), the circulation of E around each lower face d in the order of
+// curl_face (ec, en as in half_faces); ru, r = dt/dx in the types TU and TE
+template <class R, class TU, class TE>
+__device__ __forceinline__ void full_cell(const StateP<TU, TE>& s, long long c, TU rho0, TU mx0, TU my0, TU mz0, TE e0,
+                                          const TE bo[3], const TU du[4], TE due, const R ec[3], const R en[3][3],
+                                          TU ru, TE r)
+{
+    s.rho[c] = rho0 - ru * du[0];
+    s.m[0][c] = mx0 - ru * du[1];
+    s.m[1][c] = my0 - ru * du[2];
+    s.m[2][c] = mz0 - ru * du[3];
+    s.e[c] = e0 - r * due;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const int t1 = d == 2 ? 0 : d + 1, t2 = d == 0 ? 2 : d - 1;
+        const TE curl = (widen<TE>(en[t2][t1]) - widen<TE>(ec[t2])) - (widen<TE>(en[t1][t2]) - widen<TE>(ec[t1]));
+        s.b[d][c] = ct_face(bo[d], r, curl);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // a10: full update U^{n+1} = U^n - dt div F (Eq. 10), B^{n+1} = B^n - dt curl E
 // (Eq. 13), in place.
@@ -1537,22 +1559,8 @@ __global__ void __launch_bounds__(CELL_THREADS) k_full(Boxes B, StateP<TU, TE> s
     // outflow: the last cell's upper neighbour is the cell itself (a zero
     // difference above); add its outer-face flux instead
     if (g.bc) outer_divergence(g, i, j, k, c, N, F, Fout, cs, du, due);
-    // rho and M in their storage type, the energy in TE (Eq. 10)
-    const TU ru = DtOf<TU>::dtdx(dtb[bi]);
-    s.rho[c] = rho0 - ru * du[0];
-    s.m[0][c] = mx0 - ru * du[1];
-    s.m[1][c] = my0 - ru * du[2];
-    s.m[2][c] = mz0 - ru * du[3];
-    s.e[c] = e0 - r * due;
-    // face field by CT (Eq. 13): the circulation of E around face d, in the
-    // order of curl_face
     const TE bo[3] = {b00, b10, b20};
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-        const int t1 = d == 2 ? 0 : d + 1, t2 = d == 0 ? 2 : d - 1;
-        const TE curl = (widen<TE>(en[t2][t1]) - widen<TE>(ec[t2])) - (widen<TE>(en[t1][t2]) - widen<TE>(ec[t1]));
-        s.b[d][c] = ct_face(bo[d], r, curl);
-    }
+    full_cell<R, TU, TE>(s, c, rho0, mx0, my0, mz0, e0, bo, du, due, ec, en, DtOf<TU>::dtdx(dtb[bi]), r);
     }
 }
 

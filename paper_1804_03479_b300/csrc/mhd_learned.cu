@@ -8,6 +8,7 @@
 using namespace mhd;
 
 void mhd_internal_set_init_error(const char* msg);
+void mhd_internal_count_launches(mhd_ctx* c);
 
 struct mhd_mlp {
     cudaStream_t stream;
@@ -362,9 +363,16 @@ static void run_step_learned(mhd_ctx* c, bool device_dt)
         }
         prof_mark(c, 2 + d);
     }
-    launch_emf<R>(c, g, F1, W, E, st);
-    prof_mark(c, 5);
-    k_half<R, float, float><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2], Wh, c->sch.pfloor);
+    const bool eu = emf_form(c) == 2;   // edge fields fused with the update that uses them
+    if (eu) {
+        prof_mark(c, 5);
+        launch_emf_update<R, float, float, true>(c, g, s, F1, W, Bh, Wh, st);
+    } else {
+        launch_emf<R>(c, g, F1, W, E, st);
+        prof_mark(c, 5);
+        k_half<R, float, float><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2], Wh,
+                                                             c->sch.pfloor);
+    }
     prof_mark(c, 6);
     // VL steps 4-7
     for (int d = 0; d < 3; d++) {
@@ -391,9 +399,14 @@ static void run_step_learned(mhd_ctx* c, bool device_dt)
         }
         prof_mark(c, 7 + d);
     }
-    launch_emf<R>(c, g, F1, Wh, E, st);
-    prof_mark(c, 10);
-    k_full<R, float, float><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc);
+    if (eu) {
+        prof_mark(c, 10);
+        launch_emf_update<R, float, float, false>(c, g, s, F1, Wh, nullptr, nullptr, st);
+    } else {
+        launch_emf<R>(c, g, F1, Wh, E, st);
+        prof_mark(c, 10);
+        k_full<R, float, float><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc);
+    }
     prof_mark(c, 11);
     if (c->prof_on && c->prof_steps < c->prof_cap) c->prof_steps++;
 }
@@ -437,7 +450,7 @@ extern "C" mhd_status mhd_set_selector(mhd_ctx* c, mhd_mlp* m)
     if (!m) {   // back to the plain scheme
         c->sel = nullptr;
         c->step = c->plain_step;
-        c->launches = mhd::fused_predictor(c) ? 8 : 12;
+        mhd_internal_count_launches(c);
         if (c->have_graph) { cudaGraphExecDestroy(c->gexec); c->have_graph = false; }
         return MHD_OK;
     }
@@ -465,7 +478,7 @@ extern "C" mhd_status mhd_set_selector(mhd_ctx* c, mhd_mlp* m)
     if (mhd_internal_selector_lists(c) != MHD_OK) return MHD_ENOMEM;
     c->sel = m;
     c->step = run_step_learned;
-    c->launches = 12 + 3 + 3 + 6;   // + features, MLP, 3 tile lists, 6 sweeps of the other path
+    mhd_internal_count_launches(c);
     if (c->have_graph) { cudaGraphExecDestroy(c->gexec); c->have_graph = false; }
     return MHD_OK;
 }

@@ -347,12 +347,14 @@ class Solver:
         return a.value, b.value
 
     def set_emf_staging(self, mode):
-        """edge-field planes staged by the tensor memory accelerator (1, where
-        the context allows it) or by per-thread loads (0)"""
+        """edge fields fused with the update that uses them (2, periodic
+        boxes), a separate kernel whose planes are staged by the tensor
+        memory accelerator (1, where the context allows it) or by per-thread
+        loads (0, the default)"""
         self._check(lib().mhd_set_emf_staging(self.h, mode))
 
     def emf_staging(self):
-        """(requested mode, 1 if the tensor copies are in use)"""
+        """(requested mode, form in use: 0 per-thread loads, 1 tensor copies, 2 fused)"""
         a, b = ctypes.c_int(), ctypes.c_int()
         self._check(lib().mhd_get_emf_staging(self.h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value

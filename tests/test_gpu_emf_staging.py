@@ -3,7 +3,9 @@ kernel (Sec. 2, Eqs. 13-14) staged by bulk tensor copies into a ring of
 shared-memory slots, against per-thread loads.  Both forms compute the
 same edges with the same arithmetic, so whole multi-step runs agree bit for
 bit; the copied form is also held to the FP32 error statement against the
-FP64 oracle.  Which contexts use the copies, and argument checks."""
+FP64 oracle.  Which contexts use which form, and argument checks.  (The
+edge fields fused with their update, mode 2, are covered by
+test_gpu_emf_update.py.)"""
 import numpy as np
 import pytest
 
@@ -120,7 +122,7 @@ def test_batches_use_per_thread_loads(M):
 def test_staging_arguments(M):
     s = M.Solver((40, 48, 64), 1.0 / 48, 5.0 / 3.0, "vl", "plm", "roe", "fp32", 0.3)
     try:
-        for bad in (-1, 2):
+        for bad in (-1, 3):
             with pytest.raises(M.MHDError):
                 s.set_emf_staging(bad)
             M.lib().mhd_clear_error(s.h)
