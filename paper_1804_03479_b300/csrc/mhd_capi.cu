@@ -147,7 +147,7 @@ static void count_launches(mhd_ctx* c);
 static cudaError_t layout_tiles(mhd_ctx* c, int tl)
 {
     int t0[3] = {0, 0, 0}, e0 = 0, f0 = 0;
-    long long p0[3] = {0, 0, 0}, w0[3] = {0, 0, 0}, r0 = 0;
+    long long p0[3] = {0, 0, 0}, w0[3] = {0, 0, 0}, r0 = 0, xq = 0;
     for (int b = 0; b < c->nbox; b++) {
         BoxDev& x = c->hbox[b];
         for (int d = 0; d < 3; d++) {
@@ -168,7 +168,10 @@ static cudaError_t layout_tiles(mhd_ctx* c, int tl)
         }
         x.xr0 = r0;
         r0 += (long long)x.ny * x.nz;
+        x.xp0 = xq;
+        xq += xpencil_threads_of_box(x.nx, x.ny, x.nz, c->pencil_len);
     }
+    c->B.nxp = xq;
     c->B.nxr = r0;
     c->B.pl = c->pencil_len;
     for (int d = 0; d < 3; d++) c->B.npth[d] = p0[d];
@@ -264,7 +267,9 @@ static mhd_status init_common(int nbox, const mhd_grid* grids, double gamma, con
     // predictor (periodic boxes; in FP64 its halo solves cost more than the
     // traffic it saves, and the mixed form's face field in FP64 leaves room
     // for one block per SM); the autotuner may change it
-    c->pencil_mask = scheme->integrator == MHD_VL && scheme->precision == MHD_FP32 ? 15 : 7;
+    // and for FP64 VL x by staged pencils (bit 4)
+    c->pencil_mask = scheme->integrator != MHD_VL ? 7 : (scheme->precision == MHD_FP32 ? 15 :
+                                                         (scheme->precision == MHD_FP64 ? 23 : 7));
     c->pencil_len = 32;
     c->cell_grid = (int)(vb < 16LL * c->nsm ? vb : 16LL * c->nsm);
     if (c->cell_grid < 1) c->cell_grid = 1;
@@ -799,8 +804,8 @@ extern "C" mhd_status mhd_get_boundary(mhd_ctx* c, int* outflow_mask)
 extern "C" mhd_status mhd_set_sweep_pencils(mhd_ctx* c, int pencil_mask, int pencil_len)
 {
     if (!c) return MHD_EINVAL;
-    if (pencil_mask < 0 || pencil_mask > 15 || pencil_len < 1 || pencil_len > 1024)
-        return fail(c, MHD_EINVAL, "pencil_mask must be in [0, 15] and pencil_len in [1, 1024]");
+    if (pencil_mask < 0 || pencil_mask > 31 || pencil_len < 1 || pencil_len > 1024)
+        return fail(c, MHD_EINVAL, "pencil_mask must be in [0, 31] and pencil_len in [1, 1024]");
     c->pencil_mask = pencil_mask;
     c->pencil_len = pencil_len;
     CK(layout_tiles(c, c->B.tl));
@@ -901,9 +906,11 @@ extern "C" mhd_status mhd_autotune(mhd_ctx* c, int reps, int* tile_len, int* blo
     // pencils on all axes or on y and z only (x keeps the best tiles), per
     // segment length (VL: x by warps; CTU: x by pencil threads)
     {
-        const int masks[4] = {7, 6, 15, 14};
+        // (VL without a selector: also with x by staged pencils, bit 4, and
+        // for periodic boxes with the fused predictor, bit 3)
+        const int masks[5] = {7, 6, 23, 15, 31};
         const int lens[3] = {8, 16, 32};
-        const int nmask = c->sch.integrator == MHD_VL && !c->bc && !c->sel ? 4 : 2;
+        const int nmask = c->sch.integrator != MHD_VL || c->sel ? 2 : (!c->bc ? 5 : 3);
         c->sweep_bps = bbps;
         for (int i = 0; i < nmask && st == MHD_OK; i++)
             for (int j = 0; j < 3 && st == MHD_OK; j++) {

@@ -5,6 +5,7 @@
 #include "mhd.h"
 #include "mhd_kernels.cuh"
 #include "mhd_fused.cuh"
+#include "mhd_xpencil.cuh"
 #include "mhd_tma.cuh"
 
 struct mhd_ctx;
@@ -27,7 +28,8 @@ struct mhd_ctx {
     void* fout;                     // [3][7][cross-section] outer-face fluxes of the outflow axes
     int fix_nl[3];                  // Dirichlet sides: fixed ghost layers at each end of axis d (0: none)
     mhd::FixedState fix[3][2];      // their states, lower and upper end
-    int pencil_mask;                // VL sweeps by pencils on the axes of these bits
+    int pencil_mask;                // VL sweeps by pencils on the axes of bits 0-2; bit 3: fused VL
+                                    // predictor; bit 4: x by staged pencils instead of warps (VL)
     int emf_stage_req;              // edge fields: 0 = k_emf, 1 = planes by the tensor memory accelerator
                                     // where eligible, 2 = fused with the update (k_emf_update) where eligible
     int emf_tma;                    // 1 when the context runs k_emf_tma
@@ -196,6 +198,22 @@ void launch_emf(mhd_ctx* c, const Boxes& g, const R* F, const R* W, R* E, cudaSt
     k_emf<R><<<grid, EMF_THREADS, emf_smem_bytes<R>(), st>>>(g, F, W, E);
 }
 
+// the VL x sweeps by staged pencils (k_xpencil) instead of warps
+inline bool x_pencils(const mhd_ctx* c)
+{
+    return (c->pencil_mask & 17) == 17;
+}
+
+template <class R, int RECON, int SOLVER, int MODE, class TE>
+void launch_xpencil(mhd_ctx* c, const Boxes& g, const R* W, const TE* Bd, R* F, cudaStream_t st)
+{
+    constexpr size_t smem = (PENCIL_THREADS / 32) * xpencil_warp_bytes<R, TE>();
+    cudaFuncSetAttribute(k_xpencil<R, RECON, SOLVER, MODE, TE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    const int grid = (int)((g.nxp + PENCIL_THREADS - 1) / PENCIL_THREADS);
+    k_xpencil<R, RECON, SOLVER, MODE, TE><<<grid, PENCIL_THREADS, smem, st>>>(g, W, Bd, F, c->gamma);
+}
+
 // the VL predictor runs fused (k_vl_predictor) when the pencil mask has bit 3,
 // the scheme is VL without a learned selector and every box is periodic
 inline bool fused_predictor(const mhd_ctx* c)
@@ -334,7 +352,9 @@ void run_step(mhd_ctx* c, bool device_dt)
         } else {
             // VL steps 1-3: first-order fluxes with the face B_n, edge E, half update
             for (int d = 0; d < 3; d++) {
-                if ((c->pencil_mask >> d & 1) && d == 0)
+                if (d == 0 && x_pencils(c))
+                    launch_xpencil<R, RECON, SOLVER, 0, TE>(c, g, W, s.b[0], F1, st);
+                else if ((c->pencil_mask >> d & 1) && d == 0)
                     k_xwarp<R, RECON, SOLVER, 0, TE><<<xrow_grid(c), PENCIL_THREADS, 0, st>>>(
                         g, W, s.b[d], F1, gam, XW<RECON, 0>::slot);
                 else if (c->pencil_mask >> d & 1)
@@ -367,7 +387,9 @@ void run_step(mhd_ctx* c, bool device_dt)
         }
         // VL steps 4-7: reconstruct at the half step, Riemann, edge E, full update
         for (int d = 0; d < 3; d++) {
-            if ((c->pencil_mask >> d & 1) && d == 0)
+            if (d == 0 && x_pencils(c))
+                launch_xpencil<R, RECON, SOLVER, 1, TE>(c, g, Wh, Bh[0], F1, st);
+            else if ((c->pencil_mask >> d & 1) && d == 0)
                 k_xwarp<R, RECON, SOLVER, 1, TE><<<xrow_grid(c), PENCIL_THREADS, 0, st>>>(
                     g, Wh, Bh[d], F1, gam, XW<RECON, 1>::slot);
             else if (c->pencil_mask >> d & 1)

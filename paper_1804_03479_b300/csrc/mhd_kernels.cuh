@@ -57,6 +57,7 @@ struct BoxDev {
     long long pth0[3];  // first pencil-segment thread of the box, per axis
     long long xw0[3];   // first x-warp item of the box: predictor, PLM corrector, PPM corrector
     long long xr0;      // first grid row (j, k) of the box
+    long long xp0;      // first x-pencil thread of the box
 };
 
 // dt of a box and its ratios to dx, in both precisions; written once per
@@ -106,6 +107,7 @@ struct Boxes {
     long long npth[3];  // pencil-segment threads of the batch, per axis
     long long nxw[3];   // x-warp items of the batch: predictor, PLM corrector, PPM corrector
     long long nxr;      // grid rows of the batch
+    long long nxp;      // x-pencil threads of the batch
     int nftile;         // fused VL predictor tiles of the batch
     int fz;             // their extent along z (planes per tile)
 };

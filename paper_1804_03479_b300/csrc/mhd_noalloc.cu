@@ -150,7 +150,9 @@ extern "C" mhd_status mhd_step_noalloc(const mhd_grid* grid, double gamma, const
     }
     hb.xr0 = 0;
     c.B.nxr = (long long)hb.ny * hb.nz;
-    hb.ftile0 = 0;                     // (the fused predictor is off: mask 0)
+    hb.ftile0 = 0;                     // (the fused predictor and the x pencils are off: mask 0)
+    hb.xp0 = 0;
+    c.B.nxp = xpencil_threads_of_box(hb.nx, hb.ny, hb.nz, 16);
     c.B.nftile = pred_tiles_of_box(hb.nx, hb.ny, hb.nz, PRED_FZ);
     c.B.fz = PRED_FZ;
     int nsm = 0;

@@ -174,7 +174,7 @@ def test_fused_bit_is_ignored_where_it_does_not_apply(M):
     st = I.abc(16, kmult=1, beta=0.5, seed=15)
     s = M.Solver(st.U.shape[1:], st.dx, st.gamma, "vl", "plm", "roe", "fp64", 0.3)
     try:
-        assert s.sweep_pencils() == (7, 32)         # the FP64 default: the sweeps
+        assert s.sweep_pencils() == (23, 32)        # the FP64 default: the sweeps, x by staged pencils
         assert s.launches_per_step() == 12
         s.free()
         s = M.Solver(st.U.shape[1:], st.dx, st.gamma, "vl", "plm", "roe", "fp32", 0.3)
