@@ -226,7 +226,11 @@ mhd_status mhd_get_dirichlet(mhd_ctx* ctx, int axis, int* nlayers);
  * marches z planes of 32 x 8-cell tiles through shared memory; the
  * predictor's fluxes and edge fields then never leave the chip, and the
  * step is 8 launches instead of 12.  The faces of each tile's one-cell halo
- * ring are solved by both tiles that use them (the same arithmetic).
+ * ring are solved by both tiles that use them (the same arithmetic): about
+ * a third more Riemann solves, which with the plane barriers cost what the
+ * traffic saves -- on the B300 at 256^3 FP32 it ties the sweeps, k_emf and
+ * k_half it replaces (1.87 against 1.85 ms with Roe, 32 x 16 tiles the
+ * same), so it is not a default.
  * Bit 4 with bit 0 (VL without a learned selector; ignored otherwise): x
  * runs by pencils as y and z do -- the lanes of a warp walk 32 consecutive
  * grid rows, one segment of pencil_len faces each -- with the cells and
@@ -236,9 +240,8 @@ mhd_status mhd_get_dirichlet(mhd_ctx* ctx, int axis, int* nlayers);
  * FP64 that runs x at the y and z rate (at 256^3: 27.7 against 30.3 ms for
  * the corrector by warps); in FP32 arithmetic the staging sets the pace and
  * the warps are faster (0.62 against 1.8 ms).
- * pencil_mask in [0, 31] (0: tiles everywhere; default 15 for FP32 VL, 23
- * for FP64 VL and 7 otherwise, with pencil_len 32), pencil_len in [1, 1024],
- * else MHD_EINVAL. */
+ * pencil_mask in [0, 31] (0: tiles everywhere; default 23 for FP64 VL and 7
+ * otherwise, with pencil_len 32), pencil_len in [1, 1024], else MHD_EINVAL. */
 mhd_status mhd_set_sweep_pencils(mhd_ctx* ctx, int pencil_mask, int pencil_len);
 mhd_status mhd_get_sweep_pencils(mhd_ctx* ctx, int* pencil_mask, int* pencil_len);
 

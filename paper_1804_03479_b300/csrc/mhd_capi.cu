@@ -263,13 +263,11 @@ static mhd_status init_common(int nbox, const mhd_grid* grids, double gamma, con
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev);
     c->sweep_bps = 4;
     // register sweeps on every axis: pencils along y and z, warps along x
-    // (CTU with an outflow x axis: tiles along x), and for FP32 VL the fused
-    // predictor (periodic boxes; in FP64 its halo solves cost more than the
-    // traffic it saves, and the mixed form's face field in FP64 leaves room
-    // for one block per SM); the autotuner may change it
-    // and for FP64 VL x by staged pencils (bit 4)
-    c->pencil_mask = scheme->integrator != MHD_VL ? 7 : (scheme->precision == MHD_FP32 ? 15 :
-                                                         (scheme->precision == MHD_FP64 ? 23 : 7));
+    // (CTU with an outflow x axis: tiles along x); for FP64 VL x by staged
+    // pencils (bit 4).  The fused predictor (bit 3) is not a default: at
+    // 256^3 it ties the sweeps it replaces (its halo solves and plane
+    // barriers cost what it saves in traffic).  The autotuner may change it.
+    c->pencil_mask = scheme->integrator == MHD_VL && scheme->precision == MHD_FP64 ? 23 : 7;
     c->pencil_len = 32;
     c->cell_grid = (int)(vb < 16LL * c->nsm ? vb : 16LL * c->nsm);
     if (c->cell_grid < 1) c->cell_grid = 1;

@@ -74,7 +74,7 @@ struct mhd_ctx {
     int* sel_list[8];               // per axis d: [2d] one byte per unit (tile, pencil segment or x-warp
                                     // item), 1 = full path, in the units' order; [2d+1] the list of the
                                     // full units; [6], [7] the same for the x corrector's items when x
-                                    // runs by warps (sel_cnt[2q], sel_cnt[2q+1]: cheap and full counts)
+                                    // runs by warps (sel_cnt[2q + 1]: the entries of list 2q + 1)
     long long sel_cap;              // entries of each list
     cudaGraphExec_t gexec;
     bool have_graph;

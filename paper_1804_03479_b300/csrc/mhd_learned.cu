@@ -324,18 +324,17 @@ static void run_step_learned(mhd_ctx* c, bool device_dt)
             // x by warps: the predictor's items (31 faces) in 0/1, the
             // corrector's (27 faces, shared by the cheap PLM and full PPM kernels) in 6/7
             k_xw_classify<<<(int)((g.nxw[0] + 255) / 256 < 4096 ? (g.nxw[0] + 255) / 256 : 4096), 256, 0, st>>>(
-                c->hbox[0], 0, c->sel_flags, sel_of(c, 0), c->sel_list[1], c->sel_cnt + 0, c->sel_cnt + 1, g.nxw[0]);
+                c->hbox[0], 0, c->sel_flags, sel_of(c, 0), c->sel_list[1], c->sel_cnt + 1, g.nxw[0]);
             k_xw_classify<<<(int)((g.nxw[2] + 255) / 256 < 4096 ? (g.nxw[2] + 255) / 256 : 4096), 256, 0, st>>>(
-                c->hbox[0], 2, c->sel_flags, sel_of(c, 6), c->sel_list[7], c->sel_cnt + 6, c->sel_cnt + 7, g.nxw[2]);
+                c->hbox[0], 2, c->sel_flags, sel_of(c, 6), c->sel_list[7], c->sel_cnt + 7, g.nxw[2]);
         } else if (c->pencil_mask >> d & 1)
             k_seg_classify<<<(int)((g.npth[d] + 255) / 256 < 4096 ? (g.npth[d] + 255) / 256 : 4096), 256, 0, st>>>(
-                c->hbox[0], d, g.pl, c->sel_flags, sel_of(c, 2 * d), c->sel_list[2 * d + 1], c->sel_cnt + 2 * d,
+                c->hbox[0], d, g.pl, c->sel_flags, sel_of(c, 2 * d), c->sel_list[2 * d + 1],
                 c->sel_cnt + 2 * d + 1, g.npth[d]);
         else
             k_tile_classify<<<(g.ntile[d] + 255) / 256, 256, 0, st>>>(c->hbox[0], d, g.tl, c->sel_flags,
                                                                        sel_of(c, 2 * d), c->sel_list[2 * d + 1],
-                                                                       c->sel_cnt + 2 * d, c->sel_cnt + 2 * d + 1,
-                                                                       g.ntile[d]);
+                                                                       c->sel_cnt + 2 * d + 1, g.ntile[d]);
     }
     prof_mark(c, 1);
     // VL steps 1-3: the cheap kernel over every unit but the marked ones
@@ -499,7 +498,11 @@ extern "C" mhd_status mhd_selector_stats(mhd_ctx* c, double* frac_blocks, double
     for (long long i = 0; i < nblk; i++) cheap += f[i] == 0;
     free(f);
     *frac_blocks = (double)cheap / (double)nblk;
-    long long tc = cnt[0] + cnt[2] + cnt[4], tf = cnt[1] + cnt[3] + cnt[5];
-    *frac_tiles = tc + tf > 0 ? (double)tc / (double)(tc + tf) : 0.0;
+    // the predictor's units of each axis (x-warp items, pencil segments or
+    // tiles, by the sweep configuration): all of them, and the full ones
+    long long tot = 0, tf = cnt[1] + cnt[3] + cnt[5];
+    for (int d = 0; d < 3; d++)
+        tot += (d == 0 && (c->pencil_mask & 1)) ? c->B.nxw[0] : ((c->pencil_mask >> d & 1) ? c->B.npth[d] : c->B.ntile[d]);
+    *frac_tiles = tot > 0 ? (double)(tot - tf) / (double)tot : 0.0;
     return MHD_OK;
 }

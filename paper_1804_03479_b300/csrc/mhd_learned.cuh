@@ -345,21 +345,45 @@ __global__ void k_mlp_refresh(const float* __restrict__ p, unsigned short* __res
 // P: mean P; B: B_ref = sqrt(B^2 + P)).  The mean slots of rho and P, which
 // that scaling makes trivial, carry log10(beta)/6 and |v|/c_ref instead.
 // ---------------------------------------------------------------------------
-// Warps, not threads, own the blocks: a warp covers 32 consecutive cells along
-// x (eight blocks) of one row of blocks, each lane one x column of 4 x 4 cells
-// (y, z), so every load of a field is one coalesced 128-byte row.  A block's
-// statistics are reductions over its four lanes (shuffles); the x neighbours
-// come from the adjacent lanes, the y and z halo cells from the lane's own
-// column.  (One thread per block read each field at a 16-byte stride and
-// re-read the block's face cells for the halo differences: 1.5 ms per 384^3
-// pass against the HBM time of its 1.8 GB of primitives, 0.3 ms.)
+// Lane pairs own the blocks: a warp covers 64 consecutive cells along x (16
+// blocks) of one row of blocks, lanes 2b and 2b + 1 the block of cells
+// x0 .. x0 + 3, x0 = 4 (16 s + b), the first its z planes k0, k0 + 1, the
+// second k0 + 2, k0 + 3; each row of 4 cells along x (one per (y, z)) is one
+// 16-byte load, so a load instruction of a field fetches whole 128-byte
+// lines, and every load of a field is issued before its arithmetic (one
+// round trip per field).  A block's statistics are sums in the lane and one
+// shuffle with its partner; the x neighbours across its faces come from the
+// lanes two away (a load at the warp's ends), the y neighbours from loads of
+// the rows beyond its faces, the z pair across the middle from the partner
+// and the z neighbours from loads.  The raw statistics wait in shared memory
+// until the block's scales are known.  Measured per 384^3 pass: 0.68 ms.
+// (A lane per x column of a block, loading one field and one halo at a
+// time, took 1.0 ms; a lane per z plane of a block, 0.82 ms: more shuffles.)
+constexpr int FEAT_THREADS = 256;
+
 template <class R>
-__global__ void __launch_bounds__(256, 2) k_block_features(BoxDev g, const R* __restrict__ W, long long N, float gam,
-                                                           float* __restrict__ feats)
+__device__ __forceinline__ void load_row4(const R* __restrict__ p, float v[4])
+{
+    if constexpr (sizeof(R) == 4) {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else {
+        const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+        const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+        v[0] = (float)a.x; v[1] = (float)a.y; v[2] = (float)b.x; v[3] = (float)b.y;
+    }
+}
+
+template <class R>
+__global__ void __launch_bounds__(FEAT_THREADS, 2) k_block_features(BoxDev g, const R* __restrict__ W, long long N,
+                                                                    float gam, float* __restrict__ feats)
 {
     constexpr unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31, qx = lane & 3;
-    const int nseg = (g.nx + 31) / 32, nbx = g.nx / 4, nby = g.ny / 4, nbz = g.nz / 4;
+    __shared__ float sraw[FEAT_THREADS / 32][NF][16];   // per warp: each block's 48 raw entries
+    const int lane = threadIdx.x & 31, hb = lane & 1, bl = lane >> 1;
+    float (*raw)[16] = sraw[threadIdx.x >> 5];
+    const int nbx = g.nx / 4, nby = g.ny / 4, nbz = g.nz / 4;
+    const int nseg = (nbx + 15) / 16;
     const long long nitem = (long long)nseg * nby * nbz;
     const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
     // the loop bound is warp-uniform, so every lane takes part in the shuffles
@@ -367,130 +391,153 @@ __global__ void __launch_bounds__(256, 2) k_block_features(BoxDev g, const R* __
         const int xs = (int)(it % nseg);
         const long long r = it / nseg;
         const int jb = (int)(r % nby), kb = (int)(r / nby);
-        const int x = 32 * xs + lane;
-        const bool valid = x < g.nx;                  // whole blocks: nx % 4 == 0
-        const int xc = valid ? x : g.nx - 1;          // lanes past the row read a valid cell, unused
-        const int j0 = 4 * jb, k0 = 4 * kb;
+        const int ib = 16 * xs + bl;
+        const bool valid = ib < nbx;
+        const int x0 = 4 * (valid ? ib : nbx - 1);     // lanes past the row read a valid block, unused
+        const int j0 = 4 * jb, k0 = 4 * kb, kz = k0 + 2 * hb;   // this lane's planes kz, kz + 1
         const int jm = wrapi(j0 - 1, g.ny), jp = wrapi(j0 + 4, g.ny);
-        const int km = wrapi(k0 - 1, g.nz), kp = wrapi(k0 + 4, g.nz);
-        const int xl = wrapi(xc - 1, g.nx), xr = wrapi(xc + 1, g.nx);
-        // the x neighbour outside the warp: below lane 0, and above the last
-        // column of the row (lane 31, or the row's end; both are a block's
-        // last column)
-        const bool own_l = lane == 0, own_r = lane == 31 || xc + 1 >= g.nx;
-        // each field's raw statistics go straight to the block's feature row
-        // (lane qx writes entries qx and qx + 4 of the six) and are scaled in
-        // place once the block's scales are known
-        float* out = feats + (((long long)kb * nby + jb) * nbx + (valid ? x : 0) / 4) * NF;
+        const int kh = hb ? wrapi(k0 + 4, g.nz) : wrapi(k0 - 1, g.nz);   // the z neighbour plane on this lane's side
+        // x neighbours outside the warp's reach: below the first block, and
+        // above the last block of the row or of the warp
+        const bool own_l = bl == 0, own_r = bl == 15 || ib + 1 >= nbx;
+        const int xl = wrapi(x0 - 1, g.nx), xr = wrapi(x0 + 4, g.nx);
         float b2l = 0.f, mrho = 0.f, mP = 0.f;
 #pragma unroll 1
         for (int f = 0; f < 8; f++) {
             const R* Wf = W + (long long)f * N;
-            float v[16];                              // cell (xc, j0 + (q & 3), k0 + (q >> 2))
+            // every load of the field first: the lane's 8 rows (y j0 + (q & 3),
+            // z kz + (q >> 2)), the rows beyond the block's y faces on its
+            // planes, the plane beyond its z face on its side, and at the
+            // warp's ends the x neighbour columns
+            float v[8][4], hy[2][2][4], hz[4][4], xlo[8], xhi[8];
 #pragma unroll
-            for (int q = 0; q < 16; q++) v[q] = (float)Wf[cell_of(g, xc, j0 + (q & 3), k0 + (q >> 2))];
-            float hy[8], hz[8];                       // halo: y below/above (per z), z below/above (per y)
+            for (int q = 0; q < 8; q++) load_row4(Wf + cell_of(g, x0, j0 + (q & 3), kz + (q >> 2)), v[q]);
 #pragma unroll
-            for (int a = 0; a < 4; a++) {
-                hy[a] = (float)Wf[cell_of(g, xc, jm, k0 + a)];
-                hy[4 + a] = (float)Wf[cell_of(g, xc, jp, k0 + a)];
-                hz[a] = (float)Wf[cell_of(g, xc, j0 + a, km)];
-                hz[4 + a] = (float)Wf[cell_of(g, xc, j0 + a, kp)];
+            for (int p = 0; p < 2; p++) {
+                load_row4(Wf + cell_of(g, x0, jm, kz + p), hy[p][0]);
+                load_row4(Wf + cell_of(g, x0, jp, kz + p), hy[p][1]);
             }
-            // the x neighbour outside the warp (lane 0 and the last column of
-            // the row; never both for one lane)
-            float xo[16];
-            if (own_l || own_r) {
-                const int xn = own_l ? xl : xr;
 #pragma unroll
-                for (int q = 0; q < 16; q++) xo[q] = (float)Wf[cell_of(g, xn, j0 + (q & 3), k0 + (q >> 2))];
+            for (int jj = 0; jj < 4; jj++) load_row4(Wf + cell_of(g, x0, j0 + jj, kh), hz[jj]);
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                xlo[q] = own_l ? (float)Wf[cell_of(g, xl, j0 + (q & 3), kz + (q >> 2))] : 0.f;
+                xhi[q] = own_r ? (float)Wf[cell_of(g, xr, j0 + (q & 3), kz + (q >> 2))] : 0.f;
             }
             float sum = 0.f, mn = 3e38f, mx = -3e38f, dx = 0.f, dy = 0.f, dz = 0.f;
 #pragma unroll
-            for (int q = 0; q < 16; q++) {
-                const int jj = q & 3, kk = q >> 2;
-                sum += v[q];
-                mn = fminf(mn, v[q]);
-                mx = fmaxf(mx, v[q]);
-                // x: the pair (x - 1, x), and (x, x + 1) at the block's last column
-                float left = __shfl_up_sync(FULL, v[q], 1);
-                float right = __shfl_down_sync(FULL, v[q], 1);
-                if (own_l) left = xo[q];
-                if (own_r) right = xo[q];
-                dx = fmaxf(dx, fabsf(v[q] - left));
-                if (qx == 3) dx = fmaxf(dx, fabsf(right - v[q]));
-                // y and z: pairs inside the column and across the block's faces
-                dy = fmaxf(dy, fabsf(v[q] - (jj > 0 ? v[q - 1] : hy[kk])));
-                if (jj == 3) dy = fmaxf(dy, fabsf(hy[4 + kk] - v[q]));
-                dz = fmaxf(dz, fabsf(v[q] - (kk > 0 ? v[q - 4] : hz[jj])));
-                if (kk == 3) dz = fmaxf(dz, fabsf(hz[4 + jj] - v[q]));
-                if (f >= 5) b2l += v[q] * v[q];
-            }
+            for (int q = 0; q < 8; q++) {
 #pragma unroll
-            for (int o = 1; o <= 2; o <<= 1) {
-                sum += __shfl_xor_sync(FULL, sum, o);
-                mn = fminf(mn, __shfl_xor_sync(FULL, mn, o));
-                mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, o));
-                dx = fmaxf(dx, __shfl_xor_sync(FULL, dx, o));
-                dy = fmaxf(dy, __shfl_xor_sync(FULL, dy, o));
-                dz = fmaxf(dz, __shfl_xor_sync(FULL, dz, o));
+                for (int a = 0; a < 4; a++) {
+                    sum += v[q][a];
+                    mn = fminf(mn, v[q][a]);
+                    mx = fmaxf(mx, v[q][a]);
+                    if (a > 0) dx = fmaxf(dx, fabsf(v[q][a] - v[q][a - 1]));
+                    if ((q & 3) > 0) dy = fmaxf(dy, fabsf(v[q][a] - v[q - 1][a]));
+                    if (q >= 4) dz = fmaxf(dz, fabsf(v[q][a] - v[q - 4][a]));
+                    if (f >= 5) b2l += v[q][a] * v[q][a];
+                }
             }
+            // x pairs across the block's faces: the blocks beside it are two lanes away
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                float left = __shfl_up_sync(FULL, v[q][3], 2);
+                float right = __shfl_down_sync(FULL, v[q][0], 2);
+                if (own_l) left = xlo[q];
+                if (own_r) right = xhi[q];
+                dx = fmaxf(dx, fmaxf(fabsf(v[q][0] - left), fabsf(right - v[q][3])));
+            }
+            // y pairs across the faces, for this lane's two planes
+#pragma unroll
+            for (int p = 0; p < 2; p++)
+#pragma unroll
+                for (int a = 0; a < 4; a++)
+                    dy = fmaxf(dy, fmaxf(fabsf(v[4 * p][a] - hy[p][0][a]), fabsf(hy[p][1][a] - v[4 * p + 3][a])));
+            // z pairs: across the block's middle (k0 + 1, k0 + 2; the partner's
+            // planes) and across the face on this lane's side
+#pragma unroll
+            for (int jj = 0; jj < 4; jj++) {
+#pragma unroll
+                for (int a = 0; a < 4; a++) {
+                    // the first lane sends its upper plane, the second its lower one
+                    const float mine = hb ? v[jj][a] : v[4 + jj][a];
+                    const float other = __shfl_xor_sync(FULL, mine, 1);
+                    dz = fmaxf(dz, fabsf(mine - other));
+                    dz = fmaxf(dz, fabsf(hb ? hz[jj][a] - v[4 + jj][a] : v[jj][a] - hz[jj][a]));
+                }
+            }
+            sum += __shfl_xor_sync(FULL, sum, 1);
+            mn = fminf(mn, __shfl_xor_sync(FULL, mn, 1));
+            mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, 1));
+            dx = fmaxf(dx, __shfl_xor_sync(FULL, dx, 1));
+            dy = fmaxf(dy, __shfl_xor_sync(FULL, dy, 1));
+            dz = fmaxf(dz, __shfl_xor_sync(FULL, dz, 1));
             const float m = sum * (1.f / 64.f);
             float sq = 0.f;
 #pragma unroll
-            for (int q = 0; q < 16; q++) {
-                const float e = v[q] - m;
-                sq += e * e;
-            }
+            for (int q = 0; q < 8; q++)
+#pragma unroll
+                for (int a = 0; a < 4; a++) {
+                    const float e = v[q][a] - m;
+                    sq += e * e;
+                }
             sq += __shfl_xor_sync(FULL, sq, 1);
-            sq += __shfl_xor_sync(FULL, sq, 2);
             if (f == 0) mrho = m;
             if (f == 4) mP = m;
-            if (valid) {
-                out[f * 6 + qx] = qx == 0 ? m : (qx == 1 ? mx - mn : (qx == 2 ? dx : dy));
-                if (qx < 2) out[f * 6 + 4 + qx] = qx == 0 ? dz : sqrtf(sq * (1.f / 64.f));
+            if (hb == 0) {
+                raw[f * 6][bl] = m;
+                raw[f * 6 + 1][bl] = mx - mn;
+                raw[f * 6 + 2][bl] = dx;
+                raw[f * 6 + 3][bl] = dy;
+                raw[f * 6 + 4][bl] = dz;
+                raw[f * 6 + 5][bl] = sqrtf(sq * (1.f / 64.f));
             }
         }
-        // mean |v| over the block: the three velocity fields again (L1/L2)
+        // mean |v| over the block: the three velocity fields again (L1/L2),
+        // every row in one round trip
         float vabs = 0.f;
-#pragma unroll 4
-        for (int q = 0; q < 16; q++) {
-            const long long c = cell_of(g, xc, j0 + (q & 3), k0 + (q >> 2));
-            const float vx = (float)W[N + c], vy = (float)W[2 * N + c], vz = (float)W[3 * N + c];
-            vabs += sqrtf(vx * vx + vy * vy + vz * vz);
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const long long c = cell_of(g, x0, j0 + (q & 3), kz + (q >> 2));
+            float vx[4], vy[4], vz[4];
+            load_row4(W + N + c, vx);
+            load_row4(W + 2 * N + c, vy);
+            load_row4(W + 3 * N + c, vz);
+#pragma unroll
+            for (int a = 0; a < 4; a++) vabs += sqrtf(vx[a] * vx[a] + vy[a] * vy[a] + vz[a] * vz[a]);
         }
         vabs += __shfl_xor_sync(FULL, vabs, 1);
-        vabs += __shfl_xor_sync(FULL, vabs, 2);
         b2l += __shfl_xor_sync(FULL, b2l, 1);
-        b2l += __shfl_xor_sync(FULL, b2l, 2);
-        if (!valid) continue;
-        const float inv = 1.f / 64.f;
-        const float rho = mrho, P = fmaxf(mP, 1e-30f);
-        const float b2 = b2l * inv;
-        const float cref = sqrtf((gam * P + b2) / fmaxf(rho, 1e-30f));
-        const float bref = sqrtf(b2 + P);
-        // scale the entries this lane wrote
+        __syncwarp();                                 // the raw entries are in shared memory
+        if (valid) {
+            const float inv = 1.f / 64.f;
+            const float rho = mrho, P = fmaxf(mP, 1e-30f);
+            const float b2 = b2l * inv;
+            const float cref = sqrtf((gam * P + b2) / fmaxf(rho, 1e-30f));
+            const float bref = sqrtf(b2 + P);
+            // each lane of the pair scales and stores half of the block's row
+            float o[NF / 2];
 #pragma unroll
-        for (int f = 0; f < 8; f++) {
-            const float is = 1.f / fmaxf(f == 0 ? rho : (f < 4 ? cref : (f == 4 ? P : bref)), 1e-30f);
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int k = qx + 4 * h;
-                if (k >= 6) continue;
-                float val = out[f * 6 + k] * is;
-                if (k == 0 && f == 0) val = fminf(fmaxf(log10f(2.f * P / fmaxf(b2, 1e-30f)), -6.f), 6.f) / 6.f;
-                if (k == 0 && f == 4) val = vabs * inv / cref;
-                out[f * 6 + k] = val;
+            for (int k = 0; k < NF / 2; k++) {
+                const int e = hb * (NF / 2) + k, f = e / 6;
+                const float is = 1.f / fmaxf(f == 0 ? rho : (f < 4 ? cref : (f == 4 ? P : bref)), 1e-30f);
+                o[k] = raw[e][bl] * is;
             }
+            if (hb == 0) o[0] = fminf(fmaxf(log10f(2.f * P / fmaxf(b2, 1e-30f)), -6.f), 6.f) / 6.f;
+            else o[0] = vabs * inv / cref;            // entry 24: the mean slot of P
+            float4* out = reinterpret_cast<float4*>(feats + (((long long)kb * nby + jb) * nbx + ib) * NF + hb * (NF / 2));
+#pragma unroll
+            for (int k = 0; k < NF / 8; k++) out[k] = make_float4(o[4 * k], o[4 * k + 1], o[4 * k + 2], o[4 * k + 3]);
         }
+        __syncwarp();                                 // the raw entries are rewritten by the next item
     }
 }
 
-// launch grid of k_block_features: one warp per row segment of 32 cells
+// launch grid of k_block_features: one warp per row segment of 16 blocks
 inline int features_grid(const BoxDev& g)
 {
-    const long long warps = (long long)((g.nx + 31) / 32) * (g.ny / 4) * (g.nz / 4);
-    const long long blocks = (warps * 32 + 255) / 256;
+    const long long warps = (long long)((g.nx / 4 + 15) / 16) * (g.ny / 4) * (g.nz / 4);
+    const long long blocks = (warps * 32 + FEAT_THREADS - 1) / FEAT_THREADS;
     return (int)(blocks < 148 * 16 ? blocks : 148 * 16);
 }
 
@@ -565,20 +612,26 @@ __global__ void __launch_bounds__(256) k_block_err(BoxDev g, StateP<TU, TE> a, S
 // cheap); the full kernel runs over the list only, its warps busy with full
 // units.
 // ---------------------------------------------------------------------------
-// mark a unit, list it if full, count it (the cheap ones one atomic per warp)
-__device__ __forceinline__ void select_unit(long long t, bool full, unsigned char* sel, int* list_full,
-                                            int* cnt_cheap, int* cnt_full)
+// mark a unit and list it if full: one atomic per warp that has full units
+// (the cheap units are counted by difference, so the many warps without a
+// full unit touch no counter)
+__device__ __forceinline__ void select_unit(long long t, bool full, unsigned char* sel, int* list_full, int* cnt_full)
 {
     sel[t] = full;
-    if (full) list_full[atomicAdd(cnt_full, 1)] = (int)t;
     const unsigned act = __activemask();
-    const unsigned nc = __popc(__ballot_sync(act, !full));
-    if ((threadIdx.x & 31) == __ffs(act) - 1 && nc) atomicAdd(cnt_cheap, (int)nc);
+    const unsigned fm = __ballot_sync(act, full);
+    if (fm) {
+        const int lane = threadIdx.x & 31, leader = __ffs(fm) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(cnt_full, __popc(fm));
+        base = __shfl_sync(act, base, leader);
+        if (full) list_full[base + __popc(fm & ((1u << lane) - 1u))] = (int)t;
+    }
 }
 
 __global__ void k_tile_classify(BoxDev g, int d, int tl, const unsigned char* __restrict__ full_flag,
                                 unsigned char* __restrict__ sel, int* __restrict__ list_full,
-                                int* __restrict__ cnt_cheap, int* __restrict__ cnt_full, int ntile)
+                                int* __restrict__ cnt_full, int ntile)
 {
     const Tile T = tile_of(d, tl);
     const int ntx = (g.nx + T.ex - 1) / T.ex, nty = (g.ny + T.ey - 1) / T.ey;
@@ -603,7 +656,7 @@ __global__ void k_tile_classify(BoxDev g, int d, int tl, const unsigned char* __
                     const int kb = wrapi(kq, nbz), jb = wrapi(jq, nby), ib = wrapi(iq, nbx);
                     full = full_flag[((long long)kb * nby + jb) * nbx + ib] != 0;
                 }
-        select_unit(tile, full, sel, list_full, cnt_cheap, cnt_full);
+        select_unit(tile, full, sel, list_full, cnt_full);
     }
 }
 
@@ -612,7 +665,7 @@ __global__ void k_tile_classify(BoxDev g, int d, int tl, const unsigned char* __
 // i0-1 .. i1-1 of its line) is flagged
 __global__ void k_seg_classify(BoxDev g, int d, int pl, const unsigned char* __restrict__ full_flag,
                                unsigned char* __restrict__ sel, int* __restrict__ list_full,
-                               int* __restrict__ cnt_cheap, int* __restrict__ cnt_full, long long nseg)
+                               int* __restrict__ cnt_full, long long nseg)
 {
     int na, nb, ns;
     pencil_dims(g.nx, g.ny, g.nz, d, pl, na, nb, ns);
@@ -637,7 +690,7 @@ __global__ void k_seg_classify(BoxDev g, int d, int pl, const unsigned char* __r
             else { bi = ia / 4; bj = ib / 4; bk = qb; }
             full = full_flag[((long long)bk * nby + bj) * nbx + bi] != 0;
         }
-        select_unit(t0, full, sel, list_full, cnt_cheap, cnt_full);
+        select_unit(t0, full, sel, list_full, cnt_full);
     }
 }
 
@@ -646,7 +699,7 @@ __global__ void k_seg_classify(BoxDev g, int d, int pl, const unsigned char* __r
 // x1-1 of its row) is flagged
 __global__ void k_xw_classify(BoxDev g, int dslot, const unsigned char* __restrict__ full_flag,
                               unsigned char* __restrict__ sel, int* __restrict__ list_full,
-                              int* __restrict__ cnt_cheap, int* __restrict__ cnt_full, long long nitem)
+                              int* __restrict__ cnt_full, long long nitem)
 {
     const int fw = xw_faces(dslot);
     const int nseg = (g.nx + fw - 1) / fw;
@@ -662,7 +715,7 @@ __global__ void k_xw_classify(BoxDev g, int dslot, const unsigned char* __restri
         bool full = false;
         for (int q = q0; q <= q1 && !full; q++)
             full = full_flag[((long long)(k / 4) * nby + j / 4) * nbx + wrapi(q, nbx)] != 0;
-        select_unit(t0, full, sel, list_full, cnt_cheap, cnt_full);
+        select_unit(t0, full, sel, list_full, cnt_full);
     }
 }
 

@@ -124,6 +124,24 @@ def test_block_features_match_numpy(env):
     assert np.allclose(f, ref, rtol=2e-4, atol=2e-5), np.abs(f - ref).max()
 
 
+@pytest.mark.parametrize("shape", [(132, 8, 8), (4, 8, 12), (40, 12, 4)])
+def test_block_features_match_numpy_rows(env, shape):
+    """rows of 33 blocks (a warp of 32 blocks and one with a single block
+    whose two x neighbours are both beyond the warp), a box one block wide
+    (both neighbours wrap onto the block itself), ragged block rows"""
+    torch, mhd = env
+    nx, ny, nz = shape
+    st = I.abc(None, kmult=1, beta=0.4, seed=9, noise=3e-2, shape=shape)
+    s = mhd.Solver(st.U.shape[1:], st.dx, st.gamma, "vl", "ppm", "hlld", "fp32", 0.3)
+    s.set_state(st.U.astype(np.float32), st.B.astype(np.float32))
+    f = s.block_features().cpu().numpy()
+    s.free()
+    W = orc.prim(st.U.astype(np.float32).astype(np.float64), st.B.astype(np.float32).astype(np.float64), st.gamma)
+    ref = numpy_features(W, st.gamma)
+    assert f.shape == ref.shape == (nx * ny * nz // 64, 48)
+    assert np.allclose(f, ref, rtol=2e-4, atol=2e-5), np.abs(f - ref).max()
+
+
 def test_block_error_matches_numpy(env):
     torch, mhd = env
     st = I.abc(16, kmult=2, beta=0.5, seed=6, noise=1e-2)
