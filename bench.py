@@ -218,10 +218,12 @@ def aggregate_value(world, cells, steps, ms_max):
     return world * cells * steps / (ms_max * 1e-3)
 
 
-def time_variant(torch, mhd, st, prec, scheme, K, W, dist, stream, profile=True, tune=True):
+def time_variant(torch, mhd, st, prec, scheme, K, W, dist, stream, profile=True, tune=True, forms=None):
     """Device-timed steps of one precision; returns ms/step, group ms and the
     solver.  With tune, the library's autotuner first picks the sweep tiling
-    (and, for VL, pencils) on this state; its choice is in s.tuned."""
+    (and, for VL, pencils) on this state; its choice is in s.tuned.  forms:
+    an explicit (pencil_mask, pencil_len, emf_staging), entries None for the
+    autotuned or default choice."""
     integ, recon, riemann = scheme
     cast = torch.float32 if prec == "fp32" else torch.float64
     U = torch.from_numpy(st.U).to(device="cuda", dtype=cast).contiguous()
@@ -231,11 +233,18 @@ def time_variant(torch, mhd, st, prec, scheme, K, W, dist, stream, profile=True,
     del U, B
     if tune:
         s.autotune(reps=2)
+    if forms is not None:
+        fm, fl, fe = forms
+        if fm is not None or fl is not None:
+            m0, l0 = s.sweep_pencils()
+            s.set_sweep_pencils(m0 if fm is None else fm, l0 if fl is None else fl)
+        if fe is not None:
+            s.set_emf_staging(fe)
     # the sweep configuration the steps run with (autotuned or the default)
     tl, bps = s.sweep_config()
     mask, plen = s.sweep_pencils()
     s.tuned = {"tile_len": tl, "blocks_per_sm": bps, "pencil_mask": mask, "pencil_len": plen,
-               "autotuned": bool(tune)}
+               "emf_staging": s.emf_staging()[1], "autotuned": bool(tune)}
     s.advance(W)
     s.sync()
     if profile:
@@ -356,7 +365,8 @@ def kernels_of(groups, tuned, integ="vl"):
                 d = AXES.index(k.split("_")[1])
                 stage = st if integ == "vl" else ("tracing" if st == "predictor" else "ctucorr")
                 other = "cell" if stage == "ctucorr" else "tile"
-                name = f"{stage}_{('xwarp' if d == 0 else 'pencil') if mask >> d & 1 else other}"
+                xform = "xpencil" if (mask & 16) and integ == "vl" else "xwarp"
+                name = f"{stage}_{(xform if d == 0 else 'pencil') if mask >> d & 1 else other}"
         ms, cnt = out.get(name, (0.0, 0))
         out[name] = (ms + v, cnt + nl)
     return out
@@ -498,6 +508,38 @@ def run_cpu_plan(args):
                 out["schemes64_all_threads"][f"{integ}+{recon}+{riem}"] = oracle_rate(O, 64, (integ, recon, riem),
                                                                                       0, 5, 2)
     print(json.dumps({"mode": "cpu_plan", **out}), flush=True)
+
+
+def run_features(args):
+    """The learned selector's block-feature pass alone (mhd_block_features:
+    the primitives, then the 48 features of every 4^3 block) on the n^3
+    member of the 384^3 workload's blast family, timed by CUDA events;
+    prints one JSON line (not a bench line)."""
+    import torch
+    from paper_1804_03479_b300 import build as Bld
+    Bld.build()
+    from paper_1804_03479_b300 import mhd
+    from paper_1804_03479_b300 import inputs as I
+    n = args.features_n
+    st = I.abc_blasts(n, kmult=3, beta=0.1, nblast=10, E=1.0, radius=0.05, seed=2)
+    s = mhd.Solver(st.U.shape[1:], st.dx, st.gamma, "vl", "ppm", "hlld", "fp32", 0.3)
+    s.set_state(torch.from_numpy(st.U).to("cuda", torch.float32), torch.from_numpy(st.B).to("cuda", torch.float32))
+    out = torch.empty((s.nblocks(), 48), dtype=torch.float32, device="cuda")
+    for _ in range(max(1, args.warmup)):
+        s.block_features(out)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps = max(1, min(args.steps, 20))
+    e0.record()
+    for _ in range(reps):
+        s.block_features(out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    s.free()
+    print(json.dumps({"mode": "features", "n": n, "blocks": int(out.shape[0]), "reps": reps,
+                      "ms_per_pass_with_primitives": ms}), flush=True)
 
 
 def batch_variant(torch, mhd, K, stream, pk, apk):
@@ -838,6 +880,14 @@ def main():
     ap.add_argument("--stress-pfloor", type=float, default=1e-5)
     ap.add_argument("--cpu-plan", action="store_true", help="the full CPU-baseline plan (not a bench line)")
     ap.add_argument("--cpu-plan-steps", type=int, default=10)
+    ap.add_argument("--pencil-mask", type=int, default=None,
+                    help="sweep forms of the main line (mhd_set_sweep_pencils), after any autotuning")
+    ap.add_argument("--pencil-len", type=int, default=None)
+    ap.add_argument("--emf-staging", type=int, default=None, choices=[0, 1, 2],
+                    help="edge-field form of the main line (mhd_set_emf_staging)")
+    ap.add_argument("--features-n", type=int, default=None,
+                    help="time only the learned selector's block-feature pass on the n^3 blast state "
+                         "(not a bench line)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -845,6 +895,8 @@ def main():
         return run_stress(args)
     if args.cpu_plan:
         return run_cpu_plan(args)
+    if args.features_n:
+        return run_features(args)
 
     import torch
     from paper_1804_03479_b300 import build as Bld
@@ -869,7 +921,8 @@ def main():
     clk = Clocks(local)
     clk.start()
     ms, groups, rec, s = time_variant(torch, mhd, st, args.precision, scheme, args.steps, args.warmup, dist, stream,
-                                      tune=not args.no_autotune)
+                                      tune=not args.no_autotune,
+                                      forms=(args.pencil_mask, args.pencil_len, args.emf_staging))
     clocks = clk.stop()
     launches = s.launches_per_step() * args.steps
     dev_bytes = s.device_bytes()
