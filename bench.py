@@ -542,6 +542,31 @@ def run_features(args):
                       "ms_per_pass_with_primitives": ms}), flush=True)
 
 
+def graph_node_us(torch, stream, nodes=12, reps=200):
+    """device time per node of a CUDA graph of `nodes` one-element kernels,
+    replayed back to back: the launch gap plus the smallest kernel, an upper
+    bound on what each of a graph-replayed step's launches adds"""
+    x = torch.zeros(1, device="cuda")
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        x.add_(1.0)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=stream):
+            for _ in range(nodes):
+                x.add_(1.0)
+        for _ in range(10):
+            g.replay()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            g.replay()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) * 1e3 / (reps * nodes)
+
+
 def batch_variant(torch, mhd, K, stream, pk, apk):
     """The batched uneven workload: 48 independent periodic boxes with sides
     drawn from {32, 48, 64, 96, 128, 192} (seed 1), linear waves and ABC
@@ -591,7 +616,12 @@ def batch_variant(torch, mhd, K, stream, pk, apk):
     ms_loop = e0.elapsed_time(e1) / K
     for c in ctxs:
         c.free()
+    node_us = graph_node_us(torch, stream)
     return {"value": ncell / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": K, "boxes": 48,
+            "graph_launch_cost": {"us_per_node_upper_bound": node_us,
+                                  "ms_per_step_upper_bound": nl * node_us * 1e-3,
+                                  "frac_of_step_upper_bound": nl * node_us * 1e-3 / ms,
+                                  "how": "12-node graph of one-element kernels replayed back to back"},
             "step_roofline": step_roofline("fp32", ncell, ms, pk, apk, ("vl", "ppm", "hlld"),
                                            fused=bool(mask & 8)),
             "cells": ncell, "sides": sides, "scheme": "vl+ppm+hlld", "precision": "fp32",
