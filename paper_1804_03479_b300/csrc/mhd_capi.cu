@@ -246,9 +246,20 @@ static mhd_status init_common(int nbox, const mhd_grid* grids, double gamma, con
         vb += (x.n + CELL_THREADS - 1) / CELL_THREADS;
     }
     const long long n = off;
+    // the x-quad kernels: a box whose rows, offset and field stride are all
+    // multiples of 4 cells (16-byte aligned in every field array) takes four
+    // cells along x per thread, any other box one
+    long long vq = 0;
+    for (int b = 0; b < nbox; b++) {
+        BoxDev& x = c->hbox[b];
+        x.quad = x.nx % 4 == 0 && x.off % 4 == 0 && n % 4 == 0;
+        x.vq0 = vq;
+        vq += x.quad ? (x.n / 4 + CELL_THREADS - 1) / CELL_THREADS : (x.n + CELL_THREADS - 1) / CELL_THREADS;
+    }
     c->B.nbox = nbox;
     c->B.N = n;
     c->B.nvblk = vb;
+    c->B.nvq = vq;
     cudaError_t attr = cudaSuccess;
     switch (scheme->precision) {
         case MHD_FP64: c->szu = 8; c->sze = 8; c->szr = 8; c->step = mhd_pick_fp64(scheme->integrator, scheme->recon, scheme->riemann, &attr); break;
@@ -271,6 +282,8 @@ static mhd_status init_common(int nbox, const mhd_grid* grids, double gamma, con
     c->pencil_len = 32;
     c->cell_grid = (int)(vb < 16LL * c->nsm ? vb : 16LL * c->nsm);
     if (c->cell_grid < 1) c->cell_grid = 1;
+    c->quad_grid = (int)(vq < 16LL * c->nsm ? vq : 16LL * c->nsm);
+    if (c->quad_grid < 1) c->quad_grid = 1;
     if (e == cudaSuccess) {
         if (stream) {
             c->stream = (cudaStream_t)stream;

@@ -58,6 +58,9 @@ struct BoxDev {
     long long xw0[3];   // first x-warp item of the box: predictor, PLM corrector, PPM corrector
     long long xr0;      // first grid row (j, k) of the box
     long long xp0;      // first x-pencil thread of the box
+    long long vq0;      // first virtual block of the box in the x-quad kernels
+    int quad;           // 1: those kernels take the box's cells four along x per thread (16-byte aligned)
+    int qpad;
 };
 
 // dt of a box and its ratios to dx, in both precisions; written once per
@@ -108,6 +111,7 @@ struct Boxes {
     long long nxw[3];   // x-warp items of the batch: predictor, PLM corrector, PPM corrector
     long long nxr;      // grid rows of the batch
     long long nxp;      // x-pencil threads of the batch
+    long long nvq;      // virtual blocks of the x-quad kernels
     int nftile;         // fused VL predictor tiles of the batch
     int fz;             // their extent along z (planes per tile)
 };
@@ -183,6 +187,42 @@ __device__ __forceinline__ int box_of_tile(const Boxes& B, int d, int t)
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
         if (B.b[mid].tile0[d] <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// four consecutive elements from / to a 16-byte aligned address (FP32: one
+// 16-byte access; FP64: two)
+template <class T>
+__device__ __forceinline__ void ld4(const T* __restrict__ p, T v[4])
+{
+    if constexpr (sizeof(T) == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else {
+        const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void st4(T* __restrict__ p, const T v[4])
+{
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+        reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+    }
+}
+
+// box of a virtual block of the x-quad kernels
+__device__ __forceinline__ int box_of_vq(const Boxes& B, long long v)
+{
+    int lo = 0, hi = B.nbox - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (B.b[mid].vq0 <= v) lo = mid; else hi = mid - 1;
     }
     return lo;
 }
@@ -384,6 +424,104 @@ __global__ void __launch_bounds__(CELL_THREADS) k_prim(Boxes B, StateP<TU, TE> s
             for (int f = 0; f < 8; f++) W[f * N + c] = w[f];
             if (!(w[0] > R(0)) || !(w[4] > R(0))) atomicMin(bad_cell, (unsigned long long)c);
             if (smax_acc) local = (double)cell_signal(w, gam);
+        }
+        run = fmax(run, local);
+    }
+    if (smax_acc && cur >= 0) block_max_to(run, red, smax_acc + cur);
+}
+
+// a1 + a2 by x-quads (periodic boxes, FP32 state): k_prim's arithmetic for
+// four consecutive cells along x per thread, 16-byte loads and stores, the x
+// neighbour faces from the same vectors; one cell per thread in a box that
+// is not 16-byte aligned.  The CFL maximum runs per box as in k_prim (the
+// quad virtual blocks never straddle two boxes).
+template <class R, class TU, class TE>
+__global__ void __launch_bounds__(CELL_THREADS) k_prim4(Boxes B, StateP<TU, TE> s, R* __restrict__ W, double gam,
+                                                        unsigned long long* smax_acc, unsigned long long* bad_cell,
+                                                        double pfloor = 0.0, unsigned long long* nfloor = nullptr)
+{
+    const long long N = B.N;
+    __shared__ double red[CELL_THREADS / 32];
+    double run = 0.0;
+    int cur = -1;
+    // one cell: the primitives (Eq. 5) from rho, M, e and twice the
+    // cell-centred field, the optional floor, the stores and the checks;
+    // returns its CFL signal speed
+    auto cell = [&](long long c, TU rho, TU mx, TU my, TU mz, TE e, TE sx, TE sy, TE sz, R w[8]) -> double {
+        const TU irho = TU(1) / rho;
+        const TU vx = mx * irho, vy = my * irho, vz = mz * irho;
+        TE p = cell_pressure<TU, TE>(rho, irho, mx, my, mz, vx, vy, vz, e, sx, sy, sz, gam);
+        if (pfloor > 0.0 && p < TE(pfloor)) {
+            if (nfloor) {
+                s.e[c] = e + (TE(pfloor) - p) / TE(gam - 1.0);
+                atomicAdd(nfloor, 1ull);
+            }
+            p = TE(pfloor);
+        }
+        w[0] = R(rho); w[1] = R(vx); w[2] = R(vy); w[3] = R(vz); w[4] = narrow<R>(p);
+        w[5] = R(0.5) * narrow<R>(sx); w[6] = R(0.5) * narrow<R>(sy); w[7] = R(0.5) * narrow<R>(sz);
+        if (!(w[0] > R(0)) || !(w[4] > R(0))) atomicMin(bad_cell, (unsigned long long)c);
+        return smax_acc ? (double)cell_signal(w, gam) : 0.0;
+    };
+    for (long long v = blockIdx.x; v < B.nvq; v += gridDim.x) {
+        const int bi = box_of_vq(B, v);
+        if (smax_acc && bi != cur) {
+            if (cur >= 0) block_max_to(run, red, smax_acc + cur);
+            run = 0.0;
+            cur = bi;
+        }
+        BoxDev g = B.b[bi];
+        g.bc = 0;
+        double local = 0.0;
+        if (!g.quad) {                                     // one cell per thread
+            const long long lc = (v - g.vq0) * CELL_THREADS + threadIdx.x;
+            if (lc < g.n) {
+                int i, j, k;
+                coords(g, lc, i, j, k);
+                const long long c = g.off + lc;
+                const TE sx = s.b[0][c] + s.b[0][nbr(g, i, j, k, 0, 1)];
+                const TE sy = s.b[1][c] + s.b[1][nbr(g, i, j, k, 1, 1)];
+                const TE sz = s.b[2][c] + s.b[2][nbr(g, i, j, k, 2, 1)];
+                R w[8];
+                local = cell(c, s.rho[c], s.m[0][c], s.m[1][c], s.m[2][c], s.e[c], sx, sy, sz, w);
+#pragma unroll
+                for (int f = 0; f < 8; f++) W[f * N + c] = w[f];
+            }
+        } else {
+            const long long lc = 4 * ((v - g.vq0) * CELL_THREADS + threadIdx.x);
+            if (lc < g.n) {
+                int i, j, k;
+                coords(g, lc, i, j, k);                    // i: a multiple of 4
+                const long long c = g.off + lc;
+                const long long cx = cell_of(g, i + 4 < g.nx ? i + 4 : 0, j, k);
+                const long long cy = nbr(g, i, j, k, 1, 1), cz = nbr(g, i, j, k, 2, 1);
+                TE b0[4], b1[4], b2[4], b1y[4], b2z[4], e[4];
+                TU rho[4], mx[4], my[4], mz[4];
+                ld4(s.b[0] + c, b0);
+                ld4(s.b[1] + c, b1);
+                ld4(s.b[2] + c, b2);
+                ld4(s.b[1] + cy, b1y);
+                ld4(s.b[2] + cz, b2z);
+                const TE b0x = s.b[0][cx];
+                ld4(s.rho + c, rho);
+                ld4(s.m[0] + c, mx);
+                ld4(s.m[1] + c, my);
+                ld4(s.m[2] + c, mz);
+                ld4(s.e + c, e);
+                R w[8][4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const TE sx = b0[q] + (q < 3 ? b0[q + 1] : b0x);
+                    const TE sy = b1[q] + b1y[q];
+                    const TE sz = b2[q] + b2z[q];
+                    R wq[8];
+                    local = fmax(local, cell(c + q, rho[q], mx[q], my[q], mz[q], e[q], sx, sy, sz, wq));
+#pragma unroll
+                    for (int f = 0; f < 8; f++) w[f][q] = wq[f];
+                }
+#pragma unroll
+                for (int f = 0; f < 8; f++) st4(W + f * N + c, w[f]);
+            }
         }
         run = fmax(run, local);
     }
@@ -1380,20 +1518,25 @@ __device__ __forceinline__ void half_faces(const R ec[3], const R en[3][3], R e2
 // divergence of the hydrodynamic fluxes (Eq. 10) of a cell from its lower
 // (fc) and upper (fn) faces per axis, sweep frames back to x, y, z: rho and
 // M in their storage type TU, the energy in TE
+// the contribution of axis d (lower face fc, upper face fn) to the divergence
+template <class R, class TU, class TE>
+__device__ __forceinline__ void flux_divergence_axis(int d, const R fc[5], const R fn[5], TU du[4], TE& due)
+{
+    const int t1 = d == 2 ? 0 : d + 1, t2 = d == 0 ? 2 : d - 1;
+    du[0] += TU(fn[0] - fc[0]);
+    du[1 + d] += TU(fn[1] - fc[1]);
+    du[1 + t1] += TU(fn[2] - fc[2]);
+    du[1 + t2] += TU(fn[3] - fc[3]);
+    due += widen<TE>(fn[4] - fc[4]);
+}
+
 template <class R, class TU, class TE>
 __device__ __forceinline__ void flux_divergence(const R fc[3][5], const R fn[3][5], TU du[4], TE& due)
 {
     du[0] = du[1] = du[2] = du[3] = TU(0);
     due = TE(0);
 #pragma unroll
-    for (int d = 0; d < 3; d++) {
-        const int t1 = d == 2 ? 0 : d + 1, t2 = d == 0 ? 2 : d - 1;
-        du[0] += TU(fn[d][0] - fc[d][0]);
-        du[1 + d] += TU(fn[d][1] - fc[d][1]);
-        du[1 + t1] += TU(fn[d][2] - fc[d][2]);
-        du[1 + t2] += TU(fn[d][3] - fc[d][3]);
-        due += widen<TE>(fn[d][4] - fc[d][4]);
-    }
+    for (int d = 0; d < 3; d++) flux_divergence_axis<R, TU, TE>(d, fc[d], fn[d], du, due);
 }
 
 // half-step cell state U^{n+1/2} = U^n - (dt/2) div F (Eq. 10) and its
@@ -1490,25 +1633,208 @@ __global__ void __launch_bounds__(CELL_THREADS) k_half(Boxes B, StateP<TU, TE> s
     }
 }
 
-// full update of cell c in place: rho and M in their storage type, the
-// energy in TE (Eq. 10) from the flux divergence du, due; the face field by
-// CT (Eq. 13), the circulation of E around each lower face d in the order of
-// curl_face (ec, en as in half_faces); ru, r = dt/dx in the types TU and TE
+// full update of one cell: rho and M in their storage type, the energy in
+// TE (Eq. 10) from the flux divergence du, due; the face field by CT (Eq. 13),
+// the circulation of E around each lower face d in the order of curl_face
+// (ec, en as in half_faces); ru, r = dt/dx in the types TU and TE.  u: the
+// updated rho, Mx, My, Mz; eb: e and the three lower faces.
+template <class R, class TU, class TE>
+__device__ __forceinline__ void full_values(TU rho0, TU mx0, TU my0, TU mz0, TE e0, const TE bo[3], const TU du[4],
+                                            TE due, const R ec[3], const R en[3][3], TU ru, TE r, TU u[4], TE eb[4])
+{
+    u[0] = rho0 - ru * du[0];
+    u[1] = mx0 - ru * du[1];
+    u[2] = my0 - ru * du[2];
+    u[3] = mz0 - ru * du[3];
+    eb[0] = e0 - r * due;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const int t1 = d == 2 ? 0 : d + 1, t2 = d == 0 ? 2 : d - 1;
+        const TE curl = (widen<TE>(en[t2][t1]) - widen<TE>(ec[t2])) - (widen<TE>(en[t1][t2]) - widen<TE>(ec[t1]));
+        eb[1 + d] = ct_face(bo[d], r, curl);
+    }
+}
+
+// full update of cell c in place (full_values, stored)
 template <class R, class TU, class TE>
 __device__ __forceinline__ void full_cell(const StateP<TU, TE>& s, long long c, TU rho0, TU mx0, TU my0, TU mz0, TE e0,
                                           const TE bo[3], const TU du[4], TE due, const R ec[3], const R en[3][3],
                                           TU ru, TE r)
 {
-    s.rho[c] = rho0 - ru * du[0];
-    s.m[0][c] = mx0 - ru * du[1];
-    s.m[1][c] = my0 - ru * du[2];
-    s.m[2][c] = mz0 - ru * du[3];
-    s.e[c] = e0 - r * due;
+    TU u[4];
+    TE eb[4];
+    full_values<R, TU, TE>(rho0, mx0, my0, mz0, e0, bo, du, due, ec, en, ru, r, u, eb);
+    s.rho[c] = u[0];
+    s.m[0][c] = u[1];
+    s.m[1][c] = u[2];
+    s.m[2][c] = u[3];
+    s.e[c] = eb[0];
 #pragma unroll
-    for (int d = 0; d < 3; d++) {
-        const int t1 = d == 2 ? 0 : d + 1, t2 = d == 0 ? 2 : d - 1;
-        const TE curl = (widen<TE>(en[t2][t1]) - widen<TE>(ec[t2])) - (widen<TE>(en[t1][t2]) - widen<TE>(ec[t1]));
-        s.b[d][c] = ct_face(bo[d], r, curl);
+    for (int d = 0; d < 3; d++) s.b[d][c] = eb[1 + d];
+}
+
+// ---------------------------------------------------------------------------
+// a8 + a1 by x-quads (periodic boxes): k_half's arithmetic for four
+// consecutive cells along x per thread, 16-byte loads and stores, the x
+// neighbours from the same vectors (as k_full4); one cell per thread in a
+// box that is not 16-byte aligned.
+// ---------------------------------------------------------------------------
+template <class R, class TU, class TE>
+__global__ void __launch_bounds__(CELL_THREADS) k_half4(Boxes B, StateP<TU, TE> s, const R* __restrict__ F,
+                                                        const R* __restrict__ E, const DtBox* __restrict__ dtb,
+                                                        double gam, TE* __restrict__ Bh0, TE* __restrict__ Bh1,
+                                                        TE* __restrict__ Bh2, R* __restrict__ Wh, double pfloor)
+{
+    const long long N = B.N;
+    TE* Bh[3] = {Bh0, Bh1, Bh2};
+    for (long long v = blockIdx.x; v < B.nvq; v += gridDim.x) {
+        const int bi = box_of_vq(B, v);
+        BoxDev g = B.b[bi];
+        g.bc = 0;
+        const TE r = DtOf<TE>::hdtdx(dtb[bi]);
+        const TU ru = DtOf<TU>::hdtdx(dtb[bi]);
+        if (!g.quad) {                                     // one cell per thread, as k_half
+            const long long lc = (v - g.vq0) * CELL_THREADS + threadIdx.x;
+            if (lc >= g.n) continue;
+            int i, j, k;
+            coords(g, lc, i, j, k);
+            const long long c = g.off + lc;
+            const int ip = wrapi(i + 1, g.nx), jp = wrapi(j + 1, g.ny), kp = wrapi(k + 1, g.nz);
+            const long long cp[3] = {cell_of(g, ip, j, k), cell_of(g, i, jp, k), cell_of(g, i, j, kp)};
+            R fc[3][5], fn[3][5];
+#pragma unroll
+            for (int d = 0; d < 3; d++)
+#pragma unroll
+                for (int m = 0; m < 5; m++) {
+                    fc[d][m] = F[((long long)d * 7 + m) * N + c];
+                    fn[d][m] = F[((long long)d * 7 + m) * N + cp[d]];
+                }
+            R ec[3], en[3][3];
+#pragma unroll
+            for (int m = 0; m < 3; m++) {
+                ec[m] = E[m * N + c];
+#pragma unroll
+                for (int a = 0; a < 3; a++)
+                    if (a != m) en[m][a] = E[m * N + cp[a]];
+            }
+            const R e2xy = E[2 * N + cell_of(g, ip, jp, k)], e1xz = E[N + cell_of(g, ip, j, kp)],
+                    e0yz = E[cell_of(g, i, jp, kp)];
+            TE blo[3], bhi[3];
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                blo[d] = s.b[d][c];
+                bhi[d] = s.b[d][cp[d]];
+            }
+            TE lo[3], bc[3];
+            half_faces<TE, R>(ec, en, e2xy, e1xz, e0yz, blo, bhi, r, lo, bc);
+#pragma unroll
+            for (int d = 0; d < 3; d++) Bh[d][c] = lo[d];
+            TU du[4];
+            TE due;
+            flux_divergence<R, TU, TE>(fc, fn, du, due);
+            R w[8];
+            half_prims<R, TU, TE>(s.rho[c], s.m[0][c], s.m[1][c], s.m[2][c], s.e[c], du, due, ru, r, bc, gam, pfloor,
+                                  w);
+#pragma unroll
+            for (int f = 0; f < 8; f++) Wh[f * N + c] = w[f];
+            continue;
+        }
+        const long long lc = 4 * ((v - g.vq0) * CELL_THREADS + threadIdx.x);
+        if (lc >= g.n) continue;
+        int i, j, k;
+        coords(g, lc, i, j, k);                            // i: a multiple of 4
+        const long long c = g.off + lc;
+        const int ix = i + 4 < g.nx ? i + 4 : 0;           // beyond the quad's last cell
+        const int jp = wrapi(j + 1, g.ny), kp = wrapi(k + 1, g.nz);
+        const long long cx = cell_of(g, ix, j, k), cy = cell_of(g, i, jp, k), cz = cell_of(g, i, j, kp);
+        TU du[4][4];
+        TE due[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            du[q][0] = du[q][1] = du[q][2] = du[q][3] = TU(0);
+            due[q] = TE(0);
+        }
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            R fc[5][4], fn[5][4];
+#pragma unroll
+            for (int m = 0; m < 5; m++) {
+                const R* Fm = F + ((long long)d * 7 + m) * N;
+                ld4(Fm + c, fc[m]);
+                if (d == 0) {
+                    fn[m][0] = fc[m][1];
+                    fn[m][1] = fc[m][2];
+                    fn[m][2] = fc[m][3];
+                    fn[m][3] = Fm[cx];
+                } else {
+                    ld4(Fm + (d == 1 ? cy : cz), fn[m]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const R a[5] = {fc[0][q], fc[1][q], fc[2][q], fc[3][q], fc[4][q]};
+                const R b[5] = {fn[0][q], fn[1][q], fn[2][q], fn[3][q], fn[4][q]};
+                flux_divergence_axis<R, TU, TE>(d, a, b, du[q], due[q]);
+            }
+        }
+        // edge fields: at the cells' edges, shifted by +1 along a != m, and on
+        // the diagonals the upper faces' circulations need
+        R ec[3][4], exy[4], exz[4], eyz[4], ezy[4], eyzd[4];
+#pragma unroll
+        for (int m = 0; m < 3; m++) ld4(E + m * N + c, ec[m]);
+        ld4(E + cy, exy);                                   // E_x at y+1
+        ld4(E + cz, exz);                                   // E_x at z+1
+        ld4(E + N + cz, eyz);                               // E_y at z+1
+        ld4(E + 2 * N + cy, ezy);                           // E_z at y+1
+        ld4(E + cell_of(g, i, jp, kp), eyzd);               // E_x at (y+1, z+1)
+        const R eyx = E[N + cx], ezx = E[2 * N + cx];        // E_y, E_z beyond the quad along x
+        const R ezxy = E[2 * N + cell_of(g, ix, jp, k)];     // E_z at (x+1, y+1) beyond the quad
+        const R eyxz = E[N + cell_of(g, ix, j, kp)];         // E_y at (x+1, z+1) beyond the quad
+        TE b0[4], b1[4], b2[4], b1y[4], b2z[4];
+        ld4(s.b[0] + c, b0);
+        ld4(s.b[1] + c, b1);
+        ld4(s.b[2] + c, b2);
+        ld4(s.b[1] + cy, b1y);
+        ld4(s.b[2] + cz, b2z);
+        const TE b0x = s.b[0][cx];
+        TU rho[4], mx[4], my[4], mz[4];
+        TE e[4];
+        ld4(s.rho + c, rho);
+        ld4(s.m[0] + c, mx);
+        ld4(s.m[1] + c, my);
+        ld4(s.m[2] + c, mz);
+        ld4(s.e + c, e);
+        TE lo0[4], lo1[4], lo2[4];
+        R w[8][4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const R ecq[3] = {ec[0][q], ec[1][q], ec[2][q]};
+            R en[3][3];
+            en[0][1] = exy[q];
+            en[0][2] = exz[q];
+            en[1][0] = q < 3 ? ec[1][q + 1] : eyx;
+            en[1][2] = eyz[q];
+            en[2][0] = q < 3 ? ec[2][q + 1] : ezx;
+            en[2][1] = ezy[q];
+            en[0][0] = en[1][1] = en[2][2] = R(0);   // unused
+            const R e2xy = q < 3 ? ezy[q + 1] : ezxy, e1xz = q < 3 ? eyz[q + 1] : eyxz, e0yz = eyzd[q];
+            const TE blo[3] = {b0[q], b1[q], b2[q]};
+            const TE bhi[3] = {q < 3 ? b0[q + 1] : b0x, b1y[q], b2z[q]};
+            TE lo[3], bc[3];
+            half_faces<TE, R>(ecq, en, e2xy, e1xz, e0yz, blo, bhi, r, lo, bc);
+            lo0[q] = lo[0];
+            lo1[q] = lo[1];
+            lo2[q] = lo[2];
+            R wq[8];
+            half_prims<R, TU, TE>(rho[q], mx[q], my[q], mz[q], e[q], du[q], due[q], ru, r, bc, gam, pfloor, wq);
+#pragma unroll
+            for (int f = 0; f < 8; f++) w[f][q] = wq[f];
+        }
+        st4(Bh0 + c, lo0);
+        st4(Bh1 + c, lo1);
+        st4(Bh2 + c, lo2);
+#pragma unroll
+        for (int f = 0; f < 8; f++) st4(Wh + f * N + c, w[f]);
     }
 }
 
@@ -1563,6 +1889,144 @@ __global__ void __launch_bounds__(CELL_THREADS) k_full(Boxes B, StateP<TU, TE> s
     if (g.bc) outer_divergence(g, i, j, k, c, N, F, Fout, cs, du, due);
     const TE bo[3] = {b00, b10, b20};
     full_cell<R, TU, TE>(s, c, rho0, mx0, my0, mz0, e0, bo, du, due, ec, en, DtOf<TU>::dtdx(dtb[bi]), r);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a10 by x-quads (periodic boxes): each thread updates four consecutive
+// cells along x with 16-byte loads and stores, taking the x neighbours of the
+// quad's cells from the same vectors (one more element for the last), so a
+// load instruction moves four times the bytes of k_full's.  The fluxes come
+// axis by axis (the divergence in flux_divergence's order of operations),
+// then the edge fields and the state; the arithmetic per cell is k_full's.
+// A box that is not 16-byte aligned in every field array (quad = 0) takes
+// one cell per thread.
+// ---------------------------------------------------------------------------
+template <class R, class TU, class TE>
+__global__ void __launch_bounds__(CELL_THREADS) k_full4(Boxes B, StateP<TU, TE> s, const R* __restrict__ F,
+                                                        const R* __restrict__ E, const DtBox* __restrict__ dtb)
+{
+    const long long N = B.N;
+    for (long long v = blockIdx.x; v < B.nvq; v += gridDim.x) {
+        const int bi = box_of_vq(B, v);
+        BoxDev g = B.b[bi];
+        g.bc = 0;
+        const TE r = DtOf<TE>::dtdx(dtb[bi]);
+        const TU ru = DtOf<TU>::dtdx(dtb[bi]);
+        if (!g.quad) {                                     // one cell per thread
+            const long long lc = (v - g.vq0) * CELL_THREADS + threadIdx.x;
+            if (lc >= g.n) continue;
+            int i, j, k;
+            coords(g, lc, i, j, k);
+            const long long c = g.off + lc;
+            const long long cp[3] = {nbr(g, i, j, k, 0, 1), nbr(g, i, j, k, 1, 1), nbr(g, i, j, k, 2, 1)};
+            R fc[3][5], fn[3][5];
+#pragma unroll
+            for (int d = 0; d < 3; d++)
+#pragma unroll
+                for (int m = 0; m < 5; m++) {
+                    fc[d][m] = F[((long long)d * 7 + m) * N + c];
+                    fn[d][m] = F[((long long)d * 7 + m) * N + cp[d]];
+                }
+            R ec[3], en[3][3];
+#pragma unroll
+            for (int m = 0; m < 3; m++) {
+                ec[m] = E[m * N + c];
+#pragma unroll
+                for (int a = 0; a < 3; a++)
+                    if (a != m) en[m][a] = E[m * N + cp[a]];
+            }
+            const TE bo[3] = {s.b[0][c], s.b[1][c], s.b[2][c]};
+            TU du[4];
+            TE due;
+            flux_divergence<R, TU, TE>(fc, fn, du, due);
+            full_cell<R, TU, TE>(s, c, s.rho[c], s.m[0][c], s.m[1][c], s.m[2][c], s.e[c], bo, du, due, ec, en, ru, r);
+            continue;
+        }
+        const long long lc = 4 * ((v - g.vq0) * CELL_THREADS + threadIdx.x);
+        if (lc >= g.n) continue;
+        int i, j, k;
+        coords(g, lc, i, j, k);                            // i: a multiple of 4
+        const long long c = g.off + lc;
+        const long long cx = cell_of(g, i + 4 < g.nx ? i + 4 : 0, j, k);   // beyond the quad's last cell
+        const long long cy = nbr(g, i, j, k, 1, 1), cz = nbr(g, i, j, k, 2, 1);
+        TU du[4][4];
+        TE due[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            du[q][0] = du[q][1] = du[q][2] = du[q][3] = TU(0);
+            due[q] = TE(0);
+        }
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            R fc[5][4], fn[5][4];
+#pragma unroll
+            for (int m = 0; m < 5; m++) {
+                const R* Fm = F + ((long long)d * 7 + m) * N;
+                ld4(Fm + c, fc[m]);
+                if (d == 0) {
+                    fn[m][0] = fc[m][1];
+                    fn[m][1] = fc[m][2];
+                    fn[m][2] = fc[m][3];
+                    fn[m][3] = Fm[cx];
+                } else {
+                    ld4(Fm + (d == 1 ? cy : cz), fn[m]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const R a[5] = {fc[0][q], fc[1][q], fc[2][q], fc[3][q], fc[4][q]};
+                const R b[5] = {fn[0][q], fn[1][q], fn[2][q], fn[3][q], fn[4][q]};
+                flux_divergence_axis<R, TU, TE>(d, a, b, du[q], due[q]);
+            }
+        }
+        // edge fields at the cells' edges and at those shifted by +1 along a != m
+        R ec[3][4], ey1[4], ez1[4], exy[4], exz[4], eyz[4], ezy[4];
+#pragma unroll
+        for (int m = 0; m < 3; m++) ld4(E + m * N + c, ec[m]);
+        ld4(E + cy, exy);                                   // E_x at y+1
+        ld4(E + cz, exz);                                   // E_x at z+1
+        ld4(E + N + cz, eyz);                               // E_y at z+1
+        ld4(E + 2 * N + cy, ezy);                           // E_z at y+1
+        const R eyx = E[N + cx], ezx = E[2 * N + cx];        // E_y, E_z beyond the quad along x
+        ey1[0] = ec[1][1]; ey1[1] = ec[1][2]; ey1[2] = ec[1][3]; ey1[3] = eyx;   // E_y at x+1
+        ez1[0] = ec[2][1]; ez1[1] = ec[2][2]; ez1[2] = ec[2][3]; ez1[3] = ezx;   // E_z at x+1
+        TU rho[4], mx[4], my[4], mz[4];
+        TE e[4], b0[4], b1[4], b2[4];
+        ld4(s.rho + c, rho);
+        ld4(s.m[0] + c, mx);
+        ld4(s.m[1] + c, my);
+        ld4(s.m[2] + c, mz);
+        ld4(s.e + c, e);
+        ld4(s.b[0] + c, b0);
+        ld4(s.b[1] + c, b1);
+        ld4(s.b[2] + c, b2);
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const R ecq[3] = {ec[0][q], ec[1][q], ec[2][q]};
+            R en[3][3];
+            en[0][1] = exy[q];
+            en[0][2] = exz[q];
+            en[1][0] = ey1[q];
+            en[1][2] = eyz[q];
+            en[2][0] = ez1[q];
+            en[2][1] = ezy[q];
+            en[0][0] = en[1][1] = en[2][2] = R(0);   // unused
+            const TE bo[3] = {b0[q], b1[q], b2[q]};
+            TU u[4];
+            TE eb[4];
+            full_values<R, TU, TE>(rho[q], mx[q], my[q], mz[q], e[q], bo, du[q], due[q], ecq, en, ru, r, u, eb);
+            rho[q] = u[0]; mx[q] = u[1]; my[q] = u[2]; mz[q] = u[3];
+            e[q] = eb[0]; b0[q] = eb[1]; b1[q] = eb[2]; b2[q] = eb[3];
+        }
+        st4(s.rho + c, rho);
+        st4(s.m[0] + c, mx);
+        st4(s.m[1] + c, my);
+        st4(s.m[2] + c, mz);
+        st4(s.e + c, e);
+        st4(s.b[0] + c, b0);
+        st4(s.b[1] + c, b1);
+        st4(s.b[2] + c, b2);
     }
 }
 

@@ -307,8 +307,8 @@ static void run_step_learned(mhd_ctx* c, bool device_dt)
     const size_t smem = sweep_smem_bytes<R>(PPM, g.tl);
 
     prof_mark(c, 0);
-    k_prim<R, float, float><<<nb, CELL_THREADS, 0, st>>>(g, s, W, gam, device_dt ? c->smax_part : nullptr, c->bad,
-                                                         c->sch.pfloor, c->nfloor);
+    k_prim4<R, float, float><<<c->quad_grid, CELL_THREADS, 0, st>>>(g, s, W, gam, device_dt ? c->smax_part : nullptr,
+                                                                     c->bad, c->sch.pfloor, c->nfloor);
     if (device_dt) k_finalize_dt<<<(c->nbox + 127) / 128, 128, 0, st>>>(g, c->smax_part, c->sch.cfl, c->dt, c->smax, c->dtc);
     // selector: features of the current state, one inference, tile lists
     const int fgrid = features_grid(c->hbox[0]);
@@ -369,8 +369,8 @@ static void run_step_learned(mhd_ctx* c, bool device_dt)
     } else {
         launch_emf<R>(c, g, F1, W, E, st);
         prof_mark(c, 5);
-        k_half<R, float, float><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2], Wh,
-                                                             c->sch.pfloor);
+        k_half4<R, float, float><<<c->quad_grid, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1],
+                                                                         Bh[2], Wh, c->sch.pfloor);
     }
     prof_mark(c, 6);
     // VL steps 4-7
@@ -404,7 +404,7 @@ static void run_step_learned(mhd_ctx* c, bool device_dt)
     } else {
         launch_emf<R>(c, g, F1, Wh, E, st);
         prof_mark(c, 10);
-        k_full<R, float, float><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc);
+        k_full4<R, float, float><<<c->quad_grid, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc);
     }
     prof_mark(c, 11);
     if (c->prof_on && c->prof_steps < c->prof_cap) c->prof_steps++;

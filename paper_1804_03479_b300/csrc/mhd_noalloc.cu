@@ -137,6 +137,9 @@ extern "C" mhd_status mhd_step_noalloc(const mhd_grid* grid, double gamma, const
     c.B.tl = tl;
     c.B.N = n;
     c.B.nvblk = (n + CELL_THREADS - 1) / CELL_THREADS;
+    hb.quad = 0;                       // the caller's arrays: one cell per thread in the x-quad kernels
+    hb.vq0 = 0;
+    c.B.nvq = c.B.nvblk;
     for (int d = 0; d < 3; d++) c.B.ntile[d] = tiles_of_box(hb.nx, hb.ny, hb.nz, d, tl);
     c.B.netile = emf_tiles_of_box(hb.nx, hb.ny, hb.nz);
     c.pencil_mask = 0;                 // tile sweeps only
@@ -161,6 +164,7 @@ extern "C" mhd_status mhd_step_noalloc(const mhd_grid* grid, double gamma, const
     c.nsm = nsm;
     c.sweep_bps = 4;
     c.cell_grid = (int)(c.B.nvblk < 16LL * nsm ? c.B.nvblk : 16LL * nsm);
+    c.quad_grid = c.cell_grid;
     cudaError_t attr = cudaSuccess;
     c.step = mhd_pick_fp64(scheme->integrator, scheme->recon, scheme->riemann, &attr);
     if (!c.step || attr != cudaSuccess) return reject(MHD_ECUDA, "mhd_step_noalloc: kernel set-up failed");

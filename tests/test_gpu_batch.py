@@ -137,3 +137,34 @@ def test_uneven_48_box_workload(M):
         assert checked == sum(1 for sd in sides if sd <= 64) and checked >= 10
     finally:
         s.free()
+
+
+@pytest.mark.parametrize("integ,recon,solver", [("vl", "plm", "roe"), ("ctu", "ppm", "hlld")])
+def test_batch_fp64_parity_quad_and_single_cell_boxes(M, integ, recon, solver):
+    """the x-quad kernels take a 16-byte aligned box four cells along x per
+    thread and any other box one: boxes with rows that are not a multiple of
+    4 cells (6, 10) between aligned ones, all in one launch"""
+    boxes = [I.abc(None, kmult=1, beta=0.5, seed=31, noise=2e-2, shape=(6, 4, 4)),
+             I.abc(16, kmult=1, beta=1.0, seed=32, noise=1e-2),
+             I.abc(None, kmult=1, beta=0.5, seed=33, noise=2e-2, shape=(10, 2, 2)),
+             I.abc(12, kmult=2, beta=0.5, seed=34, noise=1e-2)]
+    s = M.Solver(None, None, 5 / 3, integ, recon, solver, "fp64", 0.3,
+                 shapes=[b.U.shape[1:] for b in boxes], dxs=[b.dx for b in boxes])
+    try:
+        states = [(b.U.copy(), b.B.copy()) for b in boxes]
+        for it in range(2):
+            for k, (U, B) in enumerate(states):
+                s.set_state(U, B, box=k)
+            dts = np.array([orc.cfl_dt(U, B, b.dx, b.gamma, 0.3) for (U, B), b in zip(states, boxes)])
+            s.step(dts)
+            for k, ((U, B), b) in enumerate(zip(states, boxes)):
+                orc.step(U, B, b.dx, b.gamma, dts[k], integ, recon, solver)
+                Ug, Bg = s.get_state(box=k)
+                for f in range(5):
+                    den = np.abs(U[f]).sum()
+                    assert np.abs(Ug[f] - U[f]).sum() / den <= 1e-12, (it, k, f)
+                for d in range(3):
+                    den = max(np.abs(B[d]).sum(), 1e-2 * np.abs(B).sum() / 3)
+                    assert np.abs(Bg[d] - B[d]).sum() / den <= 1e-12, (it, k, d)
+    finally:
+        s.free()
