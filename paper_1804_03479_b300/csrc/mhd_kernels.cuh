@@ -37,10 +37,21 @@ constexpr int PENCIL_THREADS = 128;
 // HLLE sweeps already fit 5 blocks or more, and the FP64 sweeps (194-230
 // registers) are bound by the FP64 rate.
 template <class R, int RECON, int SOLVER, int MODE>
-constexpr int sweep_min_blocks()
+constexpr int xwarp_min_blocks()
 {
     if (sizeof(R) != 4 || SOLVER != ROE) return 0;
     return RECON == PPM ? (MODE == 2 ? 4 : 0) : 5;
+}
+
+// The first-order pencils (MODE 0) load the next cell while they solve the
+// current face; with Roe that takes 124 registers, and at the 96 of the
+// 5-block bound it spilled and lost to the walk without the prefetch, so
+// they get 4 blocks (y and z predictor at 256^3: 0.303 -> 0.268 ms).
+template <class R, int RECON, int SOLVER, int MODE>
+constexpr int sweep_min_blocks()
+{
+    if (sizeof(R) == 4 && SOLVER == ROE && (MODE == 0 || (MODE == 1 && RECON != PPM))) return 4;
+    return xwarp_min_blocks<R, RECON, SOLVER, MODE>();
 }
 
 struct BoxDev {
@@ -874,13 +885,21 @@ __global__ void __launch_bounds__(PENCIL_THREADS, (sweep_min_blocks<R, RECON, SO
     };
     R f[7];
     if (MODE == 0) {
-        // first-order states: the face i sees cells i-1 and i
-        R wl[7], wr[7], bdum;
+        // first-order states: the face i sees cells i-1 and i; cell i+1 is
+        // loaded while face i is solved
+        R wl[7], wr[7], wn[7], bdum;
         load_rot(W, N, pcell(p, i0 - 1), d, wl, bdum);
+        load_rot(W, N, p.base + (long long)i0 * p.stride, d, wn, bdum);
+        TE bnn = Bd[p.base + (long long)i0 * p.stride];
         for (int i = i0; i < i1; i++) {
             const long long ci = p.base + (long long)i * p.stride;
-            load_rot(W, N, ci, d, wr, bdum);
-            riemann<SOLVER>(wl, wr, R(Bd[ci]), gm1, gr, f);
+            copy7(wr, wn);
+            const R bnf = R(bnn);
+            if (i + 1 < i1) {
+                load_rot(W, N, ci + p.stride, d, wn, bdum);
+                bnn = Bd[ci + p.stride];
+            }
+            riemann<SOLVER>(wl, wr, bnf, gm1, gr, f);
 #pragma unroll
             for (int m = 0; m < 7; m++) F[(long long)m * N + ci] = f[m];
             copy7(wl, wr);
@@ -898,9 +917,21 @@ __global__ void __launch_bounds__(PENCIL_THREADS, (sweep_min_blocks<R, RECON, SO
         if (TR) trace_src(li, wb, bnb, wm, wpp);
         load_rot(W, N, pcell(p, i0 - 1), d, wa, bna);
         load_rot(W, N, pcell(p, i0), d, wb, bnb);
+        // VL corrector with Roe: cell i+2 is loaded while face i is computed
+        // (at 4 blocks per SM: y and z at 256^3 0.492 -> 0.47 ms; the HLLE
+        // corrector lost 7 % with it, HLLD and CTU were not faster)
+        constexpr bool PF = MODE == 1 && SOLVER == ROE;
+        R wn[7], bnn;
+        if (PF) load_rot(W, N, pcell(p, i0 + 1), d, wn, bnn);
         for (int i = i0; i < i1; i++) {
             const long long ci = p.base + (long long)i * p.stride;
-            load_rot(W, N, pcell(p, i + 1), d, wc, bnc);
+            if (PF) {
+                copy7(wc, wn);
+                bnc = bnn;
+                if (i + 1 < i1) load_rot(W, N, pcell(p, i + 2), d, wn, bnn);
+            } else {
+                load_rot(W, N, pcell(p, i + 1), d, wc, bnc);
+            }
             recon_cell<RECON, TR>(wa, wb, wc, bnb, gr, dum, dum, dum, dtdx, wm, wp);
             if (TR) {
                 trace_src(i, wb, bnb, wm, wp);
@@ -1058,7 +1089,7 @@ __device__ __forceinline__ int box_of_row(const Boxes& B, long long t)
 // CTU lead-in is cell 0 with its own stencil and source term; such boxes
 // keep the tile sweep along x.)
 template <class R, int RECON, int SOLVER, int MODE, class TE>
-__global__ void __launch_bounds__(PENCIL_THREADS, (sweep_min_blocks<R, RECON, SOLVER, MODE>())) k_xwarp(Boxes B, const R* __restrict__ W,
+__global__ void __launch_bounds__(PENCIL_THREADS, (xwarp_min_blocks<R, RECON, SOLVER, MODE>())) k_xwarp(Boxes B, const R* __restrict__ W,
                                                           const TE* __restrict__ Bd, R* __restrict__ F, double gam,
                                                           int dslot, const int* __restrict__ item_list = nullptr,
                                                           const int* __restrict__ item_count = nullptr,
