@@ -43,14 +43,16 @@ constexpr int xwarp_min_blocks()
     return RECON == PPM ? (MODE == 2 ? 4 : 0) : 5;
 }
 
-// The first-order pencils (MODE 0) load the next cell while they solve the
-// current face; with Roe that takes 124 registers, and at the 96 of the
-// 5-block bound it spilled and lost to the walk without the prefetch, so
-// they get 4 blocks (y and z predictor at 256^3: 0.303 -> 0.268 ms).
+// The pencils load the next cell while they solve the current face (the
+// first-order walk always, the PLM walk of the VL corrector with Roe and of
+// the CTU tracing); with Roe that takes 124-128 registers, and at the 96 of
+// the 5-block bound it spilled and lost to the walk without the prefetch, so
+// the FP32 Roe pencils other than PPM get 4 blocks (y and z predictor at
+// 256^3: 0.303 -> 0.268 ms).
 template <class R, int RECON, int SOLVER, int MODE>
 constexpr int sweep_min_blocks()
 {
-    if (sizeof(R) == 4 && SOLVER == ROE && (MODE == 0 || (MODE == 1 && RECON != PPM))) return 4;
+    if (sizeof(R) == 4 && SOLVER == ROE && (MODE == 0 || RECON != PPM)) return 4;
     return xwarp_min_blocks<R, RECON, SOLVER, MODE>();
 }
 
@@ -917,10 +919,12 @@ __global__ void __launch_bounds__(PENCIL_THREADS, (sweep_min_blocks<R, RECON, SO
         if (TR) trace_src(li, wb, bnb, wm, wpp);
         load_rot(W, N, pcell(p, i0 - 1), d, wa, bna);
         load_rot(W, N, pcell(p, i0), d, wb, bnb);
-        // VL corrector with Roe: cell i+2 is loaded while face i is computed
-        // (at 4 blocks per SM: y and z at 256^3 0.492 -> 0.47 ms; the HLLE
-        // corrector lost 7 % with it, HLLD and CTU were not faster)
-        constexpr bool PF = MODE == 1 && SOLVER == ROE;
+        // cell i+2 is loaded while face i is computed, where that measured
+        // faster at 256^3 FP32: the VL corrector with Roe (at 4 blocks per
+        // SM, y and z 0.492 -> 0.47 ms) and the CTU tracing with Roe and HLLD
+        // (0.70 -> 0.62 ms); the VL corrector with HLLE lost 7 % and with
+        // HLLD 1 %
+        constexpr bool PF = (MODE == 1 && SOLVER == ROE) || (MODE == 2 && SOLVER != HLLE);
         R wn[7], bnn;
         if (PF) load_rot(W, N, pcell(p, i0 + 1), d, wn, bnn);
         for (int i = i0; i < i1; i++) {
@@ -980,9 +984,21 @@ __global__ void __launch_bounds__(PENCIL_THREADS, (sweep_min_blocks<R, RECON, SO
             char_slope(wq, w0, w1, b0, gr, s0);
             char_slope(w0, w1, w2, b1, gr, s1);
         }
+        // the VL corrector loads cell i+3 while face i is computed (256^3
+        // FP32: y and z 0.81 -> 0.75 ms with Roe, -> 0.77 with HLLD); the CTU
+        // tracing lost 4-6 % with it
+        R wn[7], bnn;
+        constexpr bool PFP = MODE == 1;
+        if (PFP) load_rot(W, N, pcell(p, i0 + 2), d, wn, bnn);
         for (int i = i0; i < i1; i++) {
             const long long ci = p.base + (long long)i * p.stride;
-            load_rot(W, N, pcell(p, i + 2), d, w3, b3);
+            if (PFP) {
+                copy7(w3, wn);
+                b3 = bnn;
+                if (i + 1 < i1) load_rot(W, N, pcell(p, i + 3), d, wn, bnn);
+            } else {
+                load_rot(W, N, pcell(p, i + 2), d, w3, b3);
+            }
             char_slope(w1, w2, w3, b2, gr, s2);             // slope of i+1
             recon_cell<PPM, TR>(w0, w1, w2, b1, gr, s0, s1, s2, dtdx, wm, wp);
             if (TR) {
