@@ -81,9 +81,10 @@ EXEC_FLOPS_PER_FACE = {"corrector": 670.0, "predictor": 393.0, "tracing": 895.0,
 # dram__bytes_read.sum + dram__bytes_write.sum of the ncu captures in
 # profiles/ (FP32 at 160^3: pencil corrector 242.1 MB, x-warp corrector
 # 225.8 MB for 4,096,000 faces), scaled to other sizes by faces.  A kernel
-# changed since its capture has none (the predictor, CTU tracing and FP64
-# forms were re-built since theirs).
-TRAFFIC_PER_FACE = {"corrector_pencil": {"fp32": 59.1}, "corrector_xwarp": {"fp32": 55.1},
+# changed since its capture has none (the predictor, the y/z corrector
+# pencils, CTU tracing and FP64 forms were re-built since theirs; the
+# aligned x-march forms have none yet).
+TRAFFIC_PER_FACE = {"corrector_xwarp": {"fp32": 55.1},
                     "ctucorr_pencil": {"fp32": 147.0}, "ctucorr_xwarp": {"fp32": 146.6}}
 
 
@@ -350,7 +351,7 @@ def scheme_matrix(torch, mhd, st, steps_fp32, steps_fp64, stream, pk, apk):
     return out
 
 
-def kernels_of(groups, tuned, integ="vl"):
+def kernels_of(groups, tuned, integ="vl", recon="plm"):
     """the step's launches grouped by kernel: each sweep axis belongs to the
     tile, pencil or warp kernel of its stage (from the sweep configuration;
     CTU's stages are the tracing sweeps and the corrections, per cell where
@@ -365,7 +366,11 @@ def kernels_of(groups, tuned, integ="vl"):
                 d = AXES.index(k.split("_")[1])
                 stage = st if integ == "vl" else ("tracing" if st == "predictor" else "ctucorr")
                 other = "cell" if stage == "ctucorr" else "tile"
-                xform = "xpencil" if (mask & 16) and integ == "vl" else "xwarp"
+                xform = "xwarp"
+                if integ == "vl" and mask & 16:
+                    xform = "xpencil"
+                elif integ == "vl" and (mask & 32 if st == "predictor" else (mask & 64 and recon != "ppm")):
+                    xform = "xmarch"
                 name = f"{stage}_{(xform if d == 0 else 'pencil') if mask >> d & 1 else other}"
         ms, cnt = out.get(name, (0.0, 0))
         out[name] = (ms + v, cnt + nl)
@@ -380,7 +385,7 @@ def roofline(prec, groups, steps, n, pk, apk, scheme, tuned=None):
     against the ridge (measured FMA peak / measured HBM bandwidth); the other
     side and the kernel's executed flops (ncu counts) are reported beside."""
     integ = scheme[0]
-    ks = kernels_of(groups, tuned, integ)
+    ks = kernels_of(groups, tuned, integ, scheme[1])
     dom = max(ks, key=lambda k: ks[k][0])
     tot, launches = ks[dom]
     ms = tot / steps

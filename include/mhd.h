@@ -168,8 +168,9 @@ mhd_status mhd_helicity(mhd_ctx* ctx, double* h);
  * blocks_per_sm x SMs persistent blocks.  mhd_autotune times every pair on
  * the context's own batch (reps steps each, the state restored after each
  * trial), and for the VL integrator also the pencil sweeps below (on all
- * axes or on y and z, segment lengths 8, 16, 32, each with and without the
- * fused predictor where it applies); it keeps the fastest and
+ * axes or on y and z, segment lengths 8, 16, 32, with x by overlapping
+ * warps, staged pencils or aligned marching warps, and with the fused
+ * predictor where it applies); it keeps the fastest and
  * reports the tiling (ms per step in *ms_best; the pencil choice through
  * mhd_get_sweep_pencils).  The autotuner allocates a temporary copy of the
  * state. */
@@ -240,8 +241,20 @@ mhd_status mhd_get_dirichlet(mhd_ctx* ctx, int axis, int* nlayers);
  * FP64 that runs x at the y and z rate (at 256^3: 27.7 against 30.3 ms for
  * the corrector by warps); in FP32 arithmetic the staging sets the pace and
  * the warps are faster (0.62 against 1.8 ms).
- * pencil_mask in [0, 31] (0: tiles everywhere; default 23 for FP64 VL and 7
- * otherwise, with pencil_len 32), pencil_len in [1, 1024], else MHD_EINVAL. */
+ * Bits 5 and 6 with bit 0 (VL; ignored otherwise and where bit 4 applies): the x predictor (bit 5) and the PLM x corrector
+ * (bit 6; the PPM corrector keeps its warps) run by aligned marching warps:
+ * one warp per row, lane l of segment s on cell 32 s + l, every lane
+ * producing a face, the neighbours across a segment's ends from the
+ * previous segment's registers and the next segment's prefetch (the
+ * overlapping warps above produce 27 to 31 faces per 32 lanes from loads
+ * that start off a line boundary).  At 256^3 FP32 the predictor takes 0.36
+ * ms where the overlapping warps take 0.45 (Roe), the PLM corrector 0.60 /
+ * 0.53 / 0.43 ms against 0.62 / 0.57 / 0.50 (Roe / HLLD / HLLE).  With a
+ * learned selector the cheap x sweep marches every face and the full
+ * scheme's x-warp items, launched after it, overwrite theirs.
+ * pencil_mask in [0, 127] (0: tiles everywhere), pencil_len in [1, 1024],
+ * else MHD_EINVAL.  Defaults (pencil_len 32): VL FP64 23; VL FP32 and mixed
+ * 103; CTU 7. */
 mhd_status mhd_set_sweep_pencils(mhd_ctx* ctx, int pencil_mask, int pencil_len);
 mhd_status mhd_get_sweep_pencils(mhd_ctx* ctx, int* pencil_mask, int* pencil_len);
 

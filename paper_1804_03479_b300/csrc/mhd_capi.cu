@@ -274,11 +274,18 @@ static mhd_status init_common(int nbox, const mhd_grid* grids, double gamma, con
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev);
     c->sweep_bps = 4;
     // register sweeps on every axis: pencils along y and z, warps along x
-    // (CTU with an outflow x axis: tiles along x); for FP64 VL x by staged
-    // pencils (bit 4).  The fused predictor (bit 3) is not a default: at
-    // 256^3 it ties the sweeps it replaces (its halo solves and plane
-    // barriers cost what it saves in traffic).  The autotuner may change it.
-    c->pencil_mask = scheme->integrator == MHD_VL && scheme->precision == MHD_FP64 ? 23 : 7;
+    // (CTU with an outflow x axis: tiles along x).  VL: for FP64 x by staged
+    // pencils (bit 4); for FP32 and mixed x by aligned marching warps (bits
+    // 5 and 6; the PPM corrector keeps its overlapping warps).  The fused
+    // predictor (bit 3) is not a default: at 256^3 it ties the sweeps it
+    // replaces (its halo solves and plane barriers cost what it saves in
+    // traffic).  The autotuner may change the mask.
+    if (scheme->integrator != MHD_VL)
+        c->pencil_mask = 7;
+    else if (scheme->precision == MHD_FP64)
+        c->pencil_mask = 23;
+    else
+        c->pencil_mask = 103;
     c->pencil_len = 32;
     c->cell_grid = (int)(vb < 16LL * c->nsm ? vb : 16LL * c->nsm);
     if (c->cell_grid < 1) c->cell_grid = 1;
@@ -815,8 +822,8 @@ extern "C" mhd_status mhd_get_boundary(mhd_ctx* c, int* outflow_mask)
 extern "C" mhd_status mhd_set_sweep_pencils(mhd_ctx* c, int pencil_mask, int pencil_len)
 {
     if (!c) return MHD_EINVAL;
-    if (pencil_mask < 0 || pencil_mask > 31 || pencil_len < 1 || pencil_len > 1024)
-        return fail(c, MHD_EINVAL, "pencil_mask must be in [0, 31] and pencil_len in [1, 1024]");
+    if (pencil_mask < 0 || pencil_mask > 127 || pencil_len < 1 || pencil_len > 1024)
+        return fail(c, MHD_EINVAL, "pencil_mask must be in [0, 127] and pencil_len in [1, 1024]");
     c->pencil_mask = pencil_mask;
     c->pencil_len = pencil_len;
     CK(layout_tiles(c, c->B.tl));
@@ -917,11 +924,12 @@ extern "C" mhd_status mhd_autotune(mhd_ctx* c, int reps, int* tile_len, int* blo
     // pencils on all axes or on y and z only (x keeps the best tiles), per
     // segment length (VL: x by warps; CTU: x by pencil threads)
     {
-        // (VL without a selector: also with x by staged pencils, bit 4, and
-        // for periodic boxes with the fused predictor, bit 3)
-        const int masks[5] = {7, 6, 23, 15, 31};
+        // (VL without a selector: also with x by staged pencils, bit 4, by
+        // aligned marching warps, bits 5 and 6, and for periodic boxes with
+        // the fused predictor, bit 3)
+        const int masks[7] = {7, 6, 23, 103, 15, 31, 111};
         const int lens[3] = {8, 16, 32};
-        const int nmask = c->sch.integrator != MHD_VL || c->sel ? 2 : (!c->bc ? 5 : 3);
+        const int nmask = c->sch.integrator != MHD_VL || c->sel ? 2 : (!c->bc ? 7 : 4);
         c->sweep_bps = bbps;
         for (int i = 0; i < nmask && st == MHD_OK; i++)
             for (int j = 0; j < 3 && st == MHD_OK; j++) {

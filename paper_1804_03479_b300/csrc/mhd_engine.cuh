@@ -6,6 +6,7 @@
 #include "mhd_kernels.cuh"
 #include "mhd_fused.cuh"
 #include "mhd_xpencil.cuh"
+#include "mhd_xmarch.cuh"
 #include "mhd_tma.cuh"
 
 struct mhd_ctx;
@@ -215,6 +216,24 @@ void launch_xpencil(mhd_ctx* c, const Boxes& g, const R* W, const TE* Bd, R* F, 
     k_xpencil<R, RECON, SOLVER, MODE, TE><<<grid, PENCIL_THREADS, smem, st>>>(g, W, Bd, F, c->gamma);
 }
 
+// the VL x sweeps by aligned marching warps (k_xmarch) instead of the
+// overlapping x-warps: the predictor with pencil-mask bits 0 and 5, the
+// corrector with bits 0 and 6 and a PLM stencil (the PPM corrector keeps its
+// x-warp); bit 4 (staged x pencils) takes precedence
+template <int RECON, int MODE>
+inline bool x_march(const mhd_ctx* c)
+{
+    if (MODE == 0) return (c->pencil_mask & 33) == 33;
+    return (c->pencil_mask & 65) == 65 && RECON != PPM;
+}
+
+template <class R, int RECON, int SOLVER, int MODE, class TE>
+void launch_xmarch(mhd_ctx* c, const Boxes& g, const R* W, const TE* Bd, R* F, cudaStream_t st)
+{
+    if constexpr (MODE == 0 || RECON != PPM)
+        k_xmarch<R, RECON, SOLVER, MODE, TE><<<xrow_grid(c), PENCIL_THREADS, 0, st>>>(g, W, Bd, F, c->gamma);
+}
+
 // the VL predictor runs fused (k_vl_predictor) when the pencil mask has bit 3,
 // the scheme is VL without a learned selector and every box is periodic
 inline bool fused_predictor(const mhd_ctx* c)
@@ -383,6 +402,8 @@ void run_step(mhd_ctx* c, bool device_dt)
             for (int d = 0; d < 3; d++) {
                 if (d == 0 && x_pencils(c))
                     launch_xpencil<R, RECON, SOLVER, 0, TE>(c, g, W, s.b[0], F1, st);
+                else if (d == 0 && x_march<RECON, 0>(c))
+                    launch_xmarch<R, RECON, SOLVER, 0, TE>(c, g, W, s.b[0], F1, st);
                 else if ((c->pencil_mask >> d & 1) && d == 0)
                     k_xwarp<R, RECON, SOLVER, 0, TE><<<xrow_grid(c), PENCIL_THREADS, 0, st>>>(
                         g, W, s.b[d], F1, gam, XW<RECON, 0>::slot);
@@ -417,6 +438,8 @@ void run_step(mhd_ctx* c, bool device_dt)
         for (int d = 0; d < 3; d++) {
             if (d == 0 && x_pencils(c))
                 launch_xpencil<R, RECON, SOLVER, 1, TE>(c, g, Wh, Bh[0], F1, st);
+            else if (d == 0 && x_march<RECON, 1>(c))
+                launch_xmarch<R, RECON, SOLVER, 1, TE>(c, g, Wh, Bh[0], F1, st);
             else if ((c->pencil_mask >> d & 1) && d == 0)
                 k_xwarp<R, RECON, SOLVER, 1, TE><<<xrow_grid(c), PENCIL_THREADS, 0, st>>>(
                     g, Wh, Bh[d], F1, gam, XW<RECON, 1>::slot);

@@ -317,6 +317,10 @@ static void run_step_learned(mhd_ctx* c, bool device_dt)
     k_mlp_infer<<<igrid, 256, 0, st>>>(mlp_dev(c->sel), c->sel_feats, nblk, nullptr, c->sel_flags);
     cudaMemsetAsync(c->sel_cnt, 0, 8 * sizeof(int), st);
     const bool xw = c->pencil_mask & 1;
+    // x by aligned marching warps (bits 5 / 6): the cheap kernel solves every
+    // face of the sweep (its segments are not the x-warp items of the lists)
+    // and the full kernel, launched after it, overwrites the listed items
+    const bool xm0 = xw && (c->pencil_mask & 32), xm1 = xw && (c->pencil_mask & 64);
     // unit q (2d: axis d; 6: the x corrector's items): skip bytes sel_of(c, q),
     // full list sel_list[q + 1] with its count sel_cnt[q + 1]
     for (int d = 0; d < 3; d++) {
@@ -341,8 +345,12 @@ static void run_step_learned(mhd_ctx* c, bool device_dt)
     // (x: warps marching their rows), the full kernel over the full list
     for (int d = 0; d < 3; d++) {
         if (d == 0 && xw) {
-            k_xwarp<R, PLM_PRIM, HLLE, 0, float><<<xrow_grid(c), PENCIL_THREADS, 0, st>>>(
-                g, W, s.b[0], F1, gam, 0, nullptr, nullptr, nullptr, nullptr, nullptr, sel_of(c, 0));
+            if (xm0)
+                k_xmarch<R, PLM_PRIM, HLLE, 0, float><<<xrow_grid(c), PENCIL_THREADS, 0, st>>>(g, W, s.b[0], F1,
+                                                                                               gam);
+            else
+                k_xwarp<R, PLM_PRIM, HLLE, 0, float><<<xrow_grid(c), PENCIL_THREADS, 0, st>>>(
+                    g, W, s.b[0], F1, gam, 0, nullptr, nullptr, nullptr, nullptr, nullptr, sel_of(c, 0));
             k_xwarp<R, PPM, HLLD, 0, float><<<list_grid_xwarp(c, 0), PENCIL_THREADS, 0, st>>>(
                 g, W, s.b[0], F1, gam, 0, c->sel_list[1], c->sel_cnt + 1);
         } else if (c->pencil_mask >> d & 1) {
@@ -376,8 +384,12 @@ static void run_step_learned(mhd_ctx* c, bool device_dt)
     // VL steps 4-7
     for (int d = 0; d < 3; d++) {
         if (d == 0 && xw) {
-            k_xwarp<R, PLM_PRIM, HLLE, 1, float><<<xrow_grid(c), PENCIL_THREADS, 0, st>>>(
-                g, Wh, Bh[0], F1, gam, 2, nullptr, nullptr, nullptr, nullptr, nullptr, sel_of(c, 6));
+            if (xm1)
+                k_xmarch<R, PLM_PRIM, HLLE, 1, float><<<xrow_grid(c), PENCIL_THREADS, 0, st>>>(g, Wh, Bh[0], F1,
+                                                                                               gam);
+            else
+                k_xwarp<R, PLM_PRIM, HLLE, 1, float><<<xrow_grid(c), PENCIL_THREADS, 0, st>>>(
+                    g, Wh, Bh[0], F1, gam, 2, nullptr, nullptr, nullptr, nullptr, nullptr, sel_of(c, 6));
             k_xwarp<R, PPM, HLLD, 1, float><<<list_grid_xwarp(c, 2), PENCIL_THREADS, 0, st>>>(
                 g, Wh, Bh[0], F1, gam, 2, c->sel_list[7], c->sel_cnt + 7);
         } else if (c->pencil_mask >> d & 1) {

@@ -1,0 +1,163 @@
+// mhd_xmarch.cuh -- the VL face sweeps along x (Sec. 3.2: the first-order
+// predictor fluxes and the PLM corrector fluxes) by warps marching their row
+// in segments of 32 cells aligned to the row's start.
+//
+// Lane l of segment s owns cell x = 32 s + l and the face below it: it
+// reconstructs that cell (the corrector) and solves the Riemann problem at
+// its lower face.  Every lane produces a face, and the warp's flux stores
+// start on the row's first cell, so a row that starts on a 128-byte line
+// (FP32, nx and the box offset multiples of 32) stores whole lines.  The
+// stencil's neighbours across a segment's ends come from registers kept
+// from the previous segment:
+//   predictor  lane l loads cell x, one segment ahead; lane 0 takes the
+//              previous segment's last cell;
+//   corrector  lane l loads cell x + 1, one segment ahead, so that the
+//              stencil x - 1 .. x + 1 of every lane lies in this segment's
+//              loads or, for lanes 0 and 1, the previous segment's; lane 0
+//              takes the previous segment's last "+" state.
+// (An unshifted corrector needs the next segment's first cell in the
+// current iteration, so two segments ahead in flight: its registers
+// spilled and it ran slower, 0.62 against 0.60 ms at 256^3 FP32 Roe.)
+// The corrector starts with a lead-in segment -1 (cells -32 .. -1, periodic
+// or clamped), reconstructed but not solved, whose lane 31 gives face 0 its
+// lower state, exactly as the x-warp lane of cell -1 does.
+//
+// The x-warp form (k_xwarp) overlaps its segments by the stencil's reach
+// instead: 31 (predictor) or 29 (PLM corrector) of its 32 lanes produce a
+// face, a 256-cell row takes 9 segments where this form takes 8 (plus the
+// corrector's lead-in), and its loads and stores start off a line boundary.
+// At 256^3 FP32 this form takes 0.356 ms for the Roe predictor (x-warps
+// 0.449) and 0.602 / 0.526 / 0.432 ms for the PLM corrector with Roe, HLLD
+// and HLLE (x-warps 0.616 / 0.574 / 0.502).
+#pragma once
+#include "mhd_kernels.cuh"
+
+namespace mhd {
+
+// lane l gets v of lane l - 1; lane 0 gets c of lane 31 (the previous
+// segment's last cell)
+template <class R>
+__device__ __forceinline__ void from_below(R o[7], const R v[7], const R c[7])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int m = 0; m < 7; m++) o[m] = __shfl_sync(0xffffffffu, lane == 31 ? c[m] : v[m], (lane + 31) & 31);
+}
+
+// lane l gets v of lane l + 1; lane 31 gets n of lane 0 (the next segment's
+// first cell)
+template <class R>
+__device__ __forceinline__ void from_above(R o[7], const R v[7], const R n[7])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int m = 0; m < 7; m++) o[m] = __shfl_sync(0xffffffffu, lane == 0 ? n[m] : v[m], (lane + 1) & 31);
+}
+
+// register bound: four resident blocks for the FP32 Roe walks (122 and 128
+// registers; at the x-warps' five blocks the predictor spilled and ran
+// slower, 0.375 against 0.356 ms at 256^3)
+template <class R, int RECON, int SOLVER, int MODE>
+constexpr int xmarch_min_blocks()
+{
+    return sizeof(R) == 4 && SOLVER == ROE ? 4 : xwarp_min_blocks<R, RECON, SOLVER, MODE>();
+}
+
+// MODE 0: first-order states (the VL predictor); MODE 1: PLM-reconstructed
+// (the corrector).  One warp per grid row of every box (B.nxr rows); x
+// periodic or outflow (clamped cells, as in the x-warps).
+template <class R, int RECON, int SOLVER, int MODE, class TE>
+__global__ void __launch_bounds__(PENCIL_THREADS, (xmarch_min_blocks<R, RECON, SOLVER, MODE>()))
+k_xmarch(Boxes B, const R* __restrict__ W, const TE* __restrict__ Bd, R* __restrict__ F, double gam)
+{
+    static_assert(MODE == 0 || (MODE == 1 && RECON != PPM), "the march reconstructs PLM stencils only");
+    const int lane = threadIdx.x & 31;
+    const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    if (wid >= B.nxr) return;                        // uniform over the warp
+    const int bi = box_of_row(B, wid);
+    const int nx = B.b[bi].nx, out = B.b[bi].bc & 1;
+    const long long row = B.b[bi].off + (wid - B.b[bi].xr0) * nx;
+    const long long N = B.N;
+    const R gr = R(gam), gm1 = R(gam - 1.0);
+    const int nseg = (nx + 31) >> 5;
+    R w[7], bn, wn[7], bnn, f[7];
+    TE fb, fbn;
+    if (MODE == 0) {
+        // face x sees cells x - 1 and x; wc: the previous segment's cells
+        R wc[7], bdum;
+        load_rot(W, N, row + bidx(-1, nx, out), 0, wc, bdum);   // cell -1 (every lane: one address)
+        {
+            const long long c0 = row + bidx(lane, nx, out);
+            load_rot(W, N, c0, 0, w, bn);
+            fb = Bd[c0];
+        }
+        for (int s = 0; s < nseg; s++) {
+            const int x = 32 * s + lane;
+            if (s + 1 < nseg) {
+                const long long cn = row + bidx(x + 32, nx, out);
+                load_rot(W, N, cn, 0, wn, bnn);
+                fbn = Bd[cn];
+            }
+            R wl[7];
+            from_below(wl, w, wc);
+            if (x < nx) {
+                riemann<SOLVER>(wl, w, R(fb), gm1, gr, f);
+#pragma unroll
+                for (int m = 0; m < 7; m++) F[(long long)m * N + row + x] = f[m];
+            }
+            if (s + 1 < nseg) {
+                copy7(wc, w);
+                copy7(w, wn);
+                fb = fbn;
+            }
+        }
+    } else {
+        // cell x is reconstructed from x - 1, x, x + 1; face x takes the "+"
+        // state of cell x - 1 and the "-" state of cell x.  Lane l holds
+        // cell x + 1 (v; one cell past its own, loaded one segment ahead), so
+        // that its whole stencil is in this segment's lanes or, for lanes 0
+        // and 1, the previous segment's (vc); wpc: the previous segment's
+        // "+" states.
+        R dum[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};   // slopes: unused by PLM
+        R v[7], bv, vc[7], bvc, wpc[7];
+        load_rot(W, N, row + bidx(lane - 31, nx, out), 0, v, bv);   // the lead-in segment -1
+        copy7(vc, v);                                // (lanes 0 and 1 in the lead-in: not used)
+        bvc = bv;
+        copy7(wpc, v);
+        for (int s = -1; s < nseg; s++) {
+            const int x = 32 * s + lane;
+            R vn[7], bvn;
+            if (s + 1 < nseg) {                      // segment s + 1: its cells (shifted) and faces
+                load_rot(W, N, row + bidx(x + 33, nx, out), 0, vn, bvn);
+                fbn = Bd[row + bidx(x + 32, nx, out)];
+            }
+            R wm1[7], wm[7], wp[7];
+#pragma unroll
+            for (int m = 0; m < 7; m++) {
+                w[m] = __shfl_sync(0xffffffffu, lane == 31 ? vc[m] : v[m], (lane + 31) & 31);
+                wm1[m] = __shfl_sync(0xffffffffu, lane >= 30 ? vc[m] : v[m], (lane + 30) & 31);
+            }
+            bn = __shfl_sync(0xffffffffu, lane == 31 ? bvc : bv, (lane + 31) & 31);
+            recon_cell<RECON, false>(wm1, w, v, bn, gr, dum, dum, dum, R(0), wm, wp);
+            if (s >= 0) {
+                R wl[7];
+                from_below(wl, wp, wpc);
+                if (x < nx) {
+                    riemann<SOLVER>(wl, wm, R(fb), gm1, gr, f);
+#pragma unroll
+                    for (int m = 0; m < 7; m++) F[(long long)m * N + row + x] = f[m];
+                }
+            }
+            if (s + 1 < nseg) {
+                copy7(wpc, wp);
+                copy7(vc, v);
+                bvc = bv;
+                copy7(v, vn);
+                bv = bvn;
+                fb = fbn;
+            }
+        }
+    }
+}
+
+}  // namespace mhd

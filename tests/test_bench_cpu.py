@@ -60,12 +60,24 @@ def test_roofline_of_the_dominant_kernel():
     assert r["hbm_view"]["frac"] == pytest.approx(byts / per_launch_s / 6491.2e9, rel=1e-12)
     ex = r["executed_view"]
     assert ex["achieved"] == pytest.approx(n * bench.EXEC_FLOPS_PER_FACE["corrector"] / per_launch_s / 1e12)
-    assert r["traffic"] == pytest.approx(bench.TRAFFIC_PER_FACE["corrector_pencil"]["fp32"] * n)
+    tpf = bench.TRAFFIC_PER_FACE.get("corrector_pencil", {}).get("fp32")
+    assert r["traffic"] == (pytest.approx(tpf * n) if tpf else None)
     # with a much faster arithmetic pipe the same kernel is HBM-bound
     r2 = bench.roofline("fp32", groups, steps, n, pk, {"fp32": 1e4, "fp64": 1.0, "src": "t"}, scheme, tuned)
     assert r2["bound"] == "hbm" and r2["frac"] == pytest.approx(r["hbm_view"]["frac"])
     # without pencils the same groups belong to the tile kernels
     assert "corrector_tile" in bench.kernels_of(groups, {"pencil_mask": 0})
+    # x by aligned marching warps: bit 5 the predictor, bit 6 the PLM corrector
+    ks = bench.kernels_of(groups, {"pencil_mask": 103})
+    assert ks["predictor_xmarch"] == (4.8, 1) and ks["corrector_xmarch"] == (6.2, 1)
+    ks = bench.kernels_of(groups, {"pencil_mask": 103}, "vl", "ppm")
+    assert ks["predictor_xmarch"] == (4.8, 1) and ks["corrector_xwarp"] == (6.2, 1)
+    ks = bench.kernels_of(groups, {"pencil_mask": 39})
+    assert ks["predictor_xmarch"] == (4.8, 1) and ks["corrector_xwarp"] == (6.2, 1)
+    ks = bench.kernels_of(groups, {"pencil_mask": 119})          # bit 4 takes precedence
+    assert ks["predictor_xpencil"] == (4.8, 1) and ks["corrector_xpencil"] == (6.2, 1)
+    ks = bench.kernels_of(groups, {"pencil_mask": 103}, "ctu")   # CTU keeps its x-warps
+    assert ks["tracing_xwarp"] == (4.8, 1) and ks["ctucorr_xwarp"] == (6.2, 1)
 
 
 def test_roofline_of_a_ctu_step():

@@ -189,12 +189,14 @@ def constant_net(mhd, logit):
     return net
 
 
-@pytest.mark.parametrize("mask", [0, 6, 7])
+@pytest.mark.parametrize("mask", [0, 6, 7, 103])
 @pytest.mark.parametrize("logit,scheme", [(-50.0, ("vl", "ppm", "hlld")), (50.0, ("vl", "plm_prim", "hlle"))])
 def test_selector_limits_equal_plain_schemes(env, logit, scheme, mask):
     """a network that always says 'full' (or always 'cheap') must reproduce the
     plain full (or cheap) scheme bit for bit, with tile sweeps (mask 0) or
-    pencil segments (the selector's segment lists) on the masked axes"""
+    pencil segments (the selector's segment lists) on the masked axes; with
+    x by aligned marching warps (mask 103) the cheap march solves every x
+    face and the full x-warp items overwrite theirs"""
     torch, mhd = env
     st = I.abc_blasts(32, kmult=2, beta=0.3, nblast=2, radius=0.1, seed=8, noise=1e-2)
     U = st.U.astype(np.float32); Bf = st.B.astype(np.float32)
