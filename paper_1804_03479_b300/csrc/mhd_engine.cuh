@@ -115,6 +115,12 @@ inline int xrow_grid(const mhd_ctx* c)
     return (int)((c->B.nxr * 32 + PENCIL_THREADS - 1) / PENCIL_THREADS);
 }
 
+// the aligned x-march: XMARCH_ROWS rows per warp
+inline int xmarch_grid(const mhd_ctx* c)
+{
+    return (int)((xmarch_warps(c->B.nxr) * 32 + PENCIL_THREADS - 1) / PENCIL_THREADS);
+}
+
 inline int xwarp_grid(const mhd_ctx* c, int slot)
 {
     return (int)((c->B.nxw[slot] * 32 + PENCIL_THREADS - 1) / PENCIL_THREADS);
@@ -231,7 +237,7 @@ template <class R, int RECON, int SOLVER, int MODE, class TE>
 void launch_xmarch(mhd_ctx* c, const Boxes& g, const R* W, const TE* Bd, R* F, cudaStream_t st)
 {
     if constexpr (MODE == 0 || RECON != PPM)
-        k_xmarch<R, RECON, SOLVER, MODE, TE><<<xrow_grid(c), PENCIL_THREADS, 0, st>>>(g, W, Bd, F, c->gamma);
+        k_xmarch<R, RECON, SOLVER, MODE, TE><<<xmarch_grid(c), PENCIL_THREADS, 0, st>>>(g, W, Bd, F, c->gamma);
 }
 
 // the VL predictor runs fused (k_vl_predictor) when the pencil mask has bit 3,

@@ -346,7 +346,7 @@ static void run_step_learned(mhd_ctx* c, bool device_dt)
     for (int d = 0; d < 3; d++) {
         if (d == 0 && xw) {
             if (xm0)
-                k_xmarch<R, PLM_PRIM, HLLE, 0, float><<<xrow_grid(c), PENCIL_THREADS, 0, st>>>(g, W, s.b[0], F1,
+                k_xmarch<R, PLM_PRIM, HLLE, 0, float><<<xmarch_grid(c), PENCIL_THREADS, 0, st>>>(g, W, s.b[0], F1,
                                                                                                gam);
             else
                 k_xwarp<R, PLM_PRIM, HLLE, 0, float><<<xrow_grid(c), PENCIL_THREADS, 0, st>>>(
@@ -385,7 +385,7 @@ static void run_step_learned(mhd_ctx* c, bool device_dt)
     for (int d = 0; d < 3; d++) {
         if (d == 0 && xw) {
             if (xm1)
-                k_xmarch<R, PLM_PRIM, HLLE, 1, float><<<xrow_grid(c), PENCIL_THREADS, 0, st>>>(g, Wh, Bh[0], F1,
+                k_xmarch<R, PLM_PRIM, HLLE, 1, float><<<xmarch_grid(c), PENCIL_THREADS, 0, st>>>(g, Wh, Bh[0], F1,
                                                                                                gam);
             else
                 k_xwarp<R, PLM_PRIM, HLLE, 1, float><<<xrow_grid(c), PENCIL_THREADS, 0, st>>>(

@@ -16,8 +16,10 @@
 //              loads or, for lanes 0 and 1, the previous segment's; lane 0
 //              takes the previous segment's last "+" state.
 // (An unshifted corrector needs the next segment's first cell in the
-// current iteration, so two segments ahead in flight: its registers
-// spilled and it ran slower, 0.62 against 0.60 ms at 256^3 FP32 Roe.)
+// current iteration, so two segments in flight: at 256^3 FP32 Roe it
+// spilled 60 bytes and took 0.62 ms.  The shifted one took 0.60 ms in a
+// plain loop over the row's segments (20 bytes spilled) and 0.51 ms in the
+// loop below, which ptxas fits in 128 registers without spilling.)
 // The corrector starts with a lead-in segment -1 (cells -32 .. -1, periodic
 // or clamped), reconstructed but not solved, whose lane 31 gives face 0 its
 // lower state, exactly as the x-warp lane of cell -1 does.
@@ -27,8 +29,8 @@
 // face, a 256-cell row takes 9 segments where this form takes 8 (plus the
 // corrector's lead-in), and its loads and stores start off a line boundary.
 // At 256^3 FP32 this form takes 0.356 ms for the Roe predictor (x-warps
-// 0.449) and 0.602 / 0.526 / 0.432 ms for the PLM corrector with Roe, HLLD
-// and HLLE (x-warps 0.616 / 0.574 / 0.502).
+// 0.449) and 0.510 / 0.509 ms for the PLM corrector with Roe and HLLD
+// (x-warps 0.616 / 0.574).
 #pragma once
 #include "mhd_kernels.cuh"
 
@@ -63,8 +65,39 @@ constexpr int xmarch_min_blocks()
     return sizeof(R) == 4 && SOLVER == ROE ? 4 : xwarp_min_blocks<R, RECON, SOLVER, MODE>();
 }
 
+// grid rows marched by one warp.  The corrector's loop chains them (the
+// next row's lead-in loads issued while the current row's last segment is
+// solved); more than one row a warp measured slower at 256^3 FP32 Roe
+// (corrector 0.510 / 0.512 / 0.514 / 0.520 ms for 1 / 2 / 4 / 8 rows,
+// predictor chained likewise 0.368 to 0.405 ms): fewer warps, and no
+// latency left to hide at a row's start.  So one row a warp.
+constexpr int XMARCH_ROWS = 1;
+
+__host__ __device__ __forceinline__ long long xmarch_warps(long long nrows)
+{
+    return (nrows + XMARCH_ROWS - 1) / XMARCH_ROWS;
+}
+
+// one grid row: its box's x length, outflow flag and first cell
+struct XRow {
+    int nx, out, nseg;
+    long long base;
+};
+
+__device__ __forceinline__ XRow xrow_of(const Boxes& B, long long r)
+{
+    const int bi = box_of_row(B, r);
+    XRow q;
+    q.nx = B.b[bi].nx;
+    q.out = B.b[bi].bc & 1;
+    q.nseg = (q.nx + 31) >> 5;
+    q.base = B.b[bi].off + (r - B.b[bi].xr0) * q.nx;
+    return q;
+}
+
 // MODE 0: first-order states (the VL predictor); MODE 1: PLM-reconstructed
-// (the corrector).  One warp per grid row of every box (B.nxr rows); x
+// (the corrector).  Warp w marches grid rows w XMARCH_ROWS .. (w + 1)
+// XMARCH_ROWS - 1 of the whole batch (B.nxr rows, each of its own box); x
 // periodic or outflow (clamped cells, as in the x-warps).
 template <class R, int RECON, int SOLVER, int MODE, class TE>
 __global__ void __launch_bounds__(PENCIL_THREADS, (xmarch_min_blocks<R, RECON, SOLVER, MODE>()))
@@ -73,39 +106,42 @@ k_xmarch(Boxes B, const R* __restrict__ W, const TE* __restrict__ Bd, R* __restr
     static_assert(MODE == 0 || (MODE == 1 && RECON != PPM), "the march reconstructs PLM stencils only");
     const int lane = threadIdx.x & 31;
     const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    if (wid >= B.nxr) return;                        // uniform over the warp
-    const int bi = box_of_row(B, wid);
-    const int nx = B.b[bi].nx, out = B.b[bi].bc & 1;
-    const long long row = B.b[bi].off + (wid - B.b[bi].xr0) * nx;
+    long long r = wid * XMARCH_ROWS;
+    if (r >= B.nxr) return;                          // uniform over the warp
+    const long long rend = r + XMARCH_ROWS < B.nxr ? r + XMARCH_ROWS : B.nxr;
     const long long N = B.N;
     const R gr = R(gam), gm1 = R(gam - 1.0);
-    const int nseg = (nx + 31) >> 5;
-    R w[7], bn, wn[7], bnn, f[7];
+    XRow q = xrow_of(B, r);
+    R f[7];
     TE fb, fbn;
     if (MODE == 0) {
         // face x sees cells x - 1 and x; wc: the previous segment's cells
-        R wc[7], bdum;
-        load_rot(W, N, row + bidx(-1, nx, out), 0, wc, bdum);   // cell -1 (every lane: one address)
+        // (at the row's start its cell -1, in every lane).  One row a warp:
+        // an outer loop over rows cost registers and time (0.375 against
+        // 0.356 ms at 256^3 FP32 Roe, even at one row)
+        static_assert(XMARCH_ROWS == 1, "the predictor marches one row a warp");
+        R w[7], bn, wn[7], bnn, wc[7], bdum;
+        load_rot(W, N, q.base + bidx(-1, q.nx, q.out), 0, wc, bdum);
         {
-            const long long c0 = row + bidx(lane, nx, out);
+            const long long c0 = q.base + bidx(lane, q.nx, q.out);
             load_rot(W, N, c0, 0, w, bn);
             fb = Bd[c0];
         }
-        for (int s = 0; s < nseg; s++) {
+        for (int s = 0; s < q.nseg; s++) {
             const int x = 32 * s + lane;
-            if (s + 1 < nseg) {
-                const long long cn = row + bidx(x + 32, nx, out);
+            if (s + 1 < q.nseg) {
+                const long long cn = q.base + bidx(x + 32, q.nx, q.out);
                 load_rot(W, N, cn, 0, wn, bnn);
                 fbn = Bd[cn];
             }
             R wl[7];
             from_below(wl, w, wc);
-            if (x < nx) {
+            if (x < q.nx) {
                 riemann<SOLVER>(wl, w, R(fb), gm1, gr, f);
 #pragma unroll
-                for (int m = 0; m < 7; m++) F[(long long)m * N + row + x] = f[m];
+                for (int m = 0; m < 7; m++) F[(long long)m * N + q.base + x] = f[m];
             }
-            if (s + 1 < nseg) {
+            if (s + 1 < q.nseg) {
                 copy7(wc, w);
                 copy7(w, wn);
                 fb = fbn;
@@ -117,21 +153,32 @@ k_xmarch(Boxes B, const R* __restrict__ W, const TE* __restrict__ Bd, R* __restr
         // cell x + 1 (v; one cell past its own, loaded one segment ahead), so
         // that its whole stencil is in this segment's lanes or, for lanes 0
         // and 1, the previous segment's (vc); wpc: the previous segment's
-        // "+" states.
+        // "+" states.  Each row starts with its lead-in segment -1.
         R dum[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};   // slopes: unused by PLM
         R v[7], bv, vc[7], bvc, wpc[7];
-        load_rot(W, N, row + bidx(lane - 31, nx, out), 0, v, bv);   // the lead-in segment -1
-        copy7(vc, v);                                // (lanes 0 and 1 in the lead-in: not used)
+        load_rot(W, N, q.base + bidx(lane - 31, q.nx, q.out), 0, v, bv);
+        copy7(vc, v);                                // (lanes 0 and 1 in a lead-in: not used)
         bvc = bv;
         copy7(wpc, v);
-        for (int s = -1; s < nseg; s++) {
+        int s = -1;
+        for (;;) {
             const int x = 32 * s + lane;
-            R vn[7], bvn;
-            if (s + 1 < nseg) {                      // segment s + 1: its cells (shifted) and faces
-                load_rot(W, N, row + bidx(x + 33, nx, out), 0, vn, bvn);
-                fbn = Bd[row + bidx(x + 32, nx, out)];
+            // the next segment: of this row, else the next row's lead-in
+            int sn = s + 1;
+            long long rn = r;
+            XRow qn = q;
+            if (sn == q.nseg) {
+                sn = -1;
+                rn = r + 1;
+                if (rn < rend) qn = xrow_of(B, rn);
             }
-            R wm1[7], wm[7], wp[7];
+            const bool more = rn < rend;
+            R vn[7], bvn;
+            if (more) {                              // its cells (shifted by one) and faces
+                load_rot(W, N, qn.base + bidx(32 * sn + lane + 1, qn.nx, qn.out), 0, vn, bvn);
+                if (sn >= 0) fbn = Bd[qn.base + bidx(32 * sn + lane, qn.nx, qn.out)];
+            }
+            R w[7], bn, wm1[7], wm[7], wp[7];
 #pragma unroll
             for (int m = 0; m < 7; m++) {
                 w[m] = __shfl_sync(0xffffffffu, lane == 31 ? vc[m] : v[m], (lane + 31) & 31);
@@ -142,20 +189,22 @@ k_xmarch(Boxes B, const R* __restrict__ W, const TE* __restrict__ Bd, R* __restr
             if (s >= 0) {
                 R wl[7];
                 from_below(wl, wp, wpc);
-                if (x < nx) {
+                if (x < q.nx) {
                     riemann<SOLVER>(wl, wm, R(fb), gm1, gr, f);
 #pragma unroll
-                    for (int m = 0; m < 7; m++) F[(long long)m * N + row + x] = f[m];
+                    for (int m = 0; m < 7; m++) F[(long long)m * N + q.base + x] = f[m];
                 }
             }
-            if (s + 1 < nseg) {
-                copy7(wpc, wp);
-                copy7(vc, v);
-                bvc = bv;
-                copy7(v, vn);
-                bv = bvn;
-                fb = fbn;
-            }
+            if (!more) break;
+            copy7(wpc, wp);
+            copy7(vc, v);
+            bvc = bv;
+            copy7(v, vn);
+            bv = bvn;
+            if (sn >= 0) fb = fbn;
+            s = sn;
+            r = rn;
+            q = qn;
         }
     }
 }

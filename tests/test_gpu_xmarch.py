@@ -1,16 +1,16 @@
 """x by aligned marching warps (k_xmarch; pencil-mask bit 5 for the
 predictor, bit 6 for the corrector, each with bit 0): the VL predictor and
-PLM corrector sweeps along x by one warp per grid row,
-lane l of segment s on cell 32 s + l, the neighbours across the segment ends
-from the previous segment's registers and the next segment's prefetch, and
-the corrector's lead-in segment -1.
+PLM corrector sweeps along x, each warp marching a few grid rows back to
+back, lane l of segment s on cell 32 s + l, the neighbours across the
+segment ends from the previous segment's registers and the next segment's
+prefetch, and each row's lead-in segment -1 in the corrector.
 
 FP64 parity with the oracle at the 1e-12 bar per field and step: every VL
 scheme (PPM: the predictor marches, the corrector keeps its x-warp); rows of
 whole segments, ragged last segments, rows shorter than a segment (nx = 1:
 every neighbour is the cell itself); outflow x (the clamped lead-in) and
-every outflow mask; an uneven batch whose boxes do not start on a segment
-boundary.  FP32 and mixed agreement with the x-warp form after three steps;
+every outflow mask; uneven batches whose boxes do not start on a segment
+boundary and whose warps run from one box into the next.  FP32 and mixed agreement with the x-warp form after three steps;
 the mask's range and precedence."""
 import numpy as np
 import pytest
@@ -127,6 +127,36 @@ def test_xmarch_fp64_batch_parity(M):
             Ug, Bg = s.get_state(box=k)
             # perturbation-size fields (the linear wave's momentum, the extruded
             # Orszag-Tang B_z): floors as in the batch tests
+            mfloor = 1e-2 * np.abs(U[0]).sum()
+            for f in range(5):
+                den = max(np.abs(U[f]).sum(), mfloor if f in (1, 2, 3) else 0.0)
+                assert np.abs(Ug[f] - U[f]).sum() / den <= 1e-12, (k, f)
+            bfloor = 1e-2 * np.abs(B).sum() / 3
+            for d in range(3):
+                assert np.abs(Bg[d] - B[d]).sum() / max(np.abs(B[d]).sum(), bfloor) <= 1e-12, (k, d)
+    finally:
+        s.free()
+
+
+@pytest.mark.parametrize("scheme", [("vl", "plm", "roe"), ("vl", "plm_prim", "hlld")])
+def test_xmarch_fp64_batch_warps_cross_boxes(M, scheme):
+    """row counts (15, 21, 25, 9) that are not multiples of a warp's rows:
+    warps whose rows run from one box into the next, with another x length,
+    offset and periodic wrap"""
+    shapes = [(16, 3, 5), (33, 7, 3), (40, 5, 5), (70, 3, 3)]
+    boxes = [I.abc(None, kmult=1, beta=0.5, seed=60 + k, noise=3e-2, shape=sh) for k, sh in enumerate(shapes)]
+    s = M.Solver(None, None, 5 / 3, *scheme, "fp64", 0.3,
+                 shapes=[b.U.shape[1:] for b in boxes], dxs=[b.dx for b in boxes])
+    try:
+        s.set_sweep_pencils(MARCH, 32)
+        for k, b in enumerate(boxes):
+            s.set_state(b.U, b.B, box=k)
+        dts = np.array([orc.cfl_dt(b.U, b.B, b.dx, b.gamma, 0.3) for b in boxes])
+        s.step(dts)
+        for k, b in enumerate(boxes):
+            U, B = b.U.copy(), b.B.copy()
+            orc.step(U, B, b.dx, b.gamma, float(dts[k]), *scheme)
+            Ug, Bg = s.get_state(box=k)
             mfloor = 1e-2 * np.abs(U[0]).sum()
             for f in range(5):
                 den = max(np.abs(U[f]).sum(), mfloor if f in (1, 2, 3) else 0.0)
