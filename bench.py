@@ -372,6 +372,8 @@ def kernels_of(groups, tuned, integ="vl", recon="plm"):
                     xform = "xpencil"
                 elif integ == "vl" and (mask & 32 if st == "predictor" else (mask & 64 and recon != "ppm")):
                     xform = "xmarch"
+                elif integ != "vl" and st == "predictor" and mask & 32 and recon != "ppm":
+                    xform = "xmarch"                 # the CTU tracing (the correction keeps its warps)
                 name = f"{stage}_{(xform if d == 0 else 'pencil') if mask >> d & 1 else other}"
         ms, cnt = out.get(name, (0.0, 0))
         out[name] = (ms + v, cnt + nl)

@@ -276,12 +276,13 @@ static mhd_status init_common(int nbox, const mhd_grid* grids, double gamma, con
     // register sweeps on every axis: pencils along y and z, warps along x
     // (CTU with an outflow x axis: tiles along x).  VL: for FP64 x by staged
     // pencils (bit 4); for FP32 and mixed x by aligned marching warps (bits
-    // 5 and 6; the PPM corrector keeps its overlapping warps).  The fused
+    // 5 and 6; the PPM corrector keeps its overlapping warps).  CTU: the
+    // PLM tracing along x by aligned marching warps (bit 5).  The fused
     // predictor (bit 3) is not a default: at 256^3 it ties the sweeps it
     // replaces (its halo solves and plane barriers cost what it saves in
     // traffic).  The autotuner may change the mask.
     if (scheme->integrator != MHD_VL)
-        c->pencil_mask = 7;
+        c->pencil_mask = 39;
     else if (scheme->precision == MHD_FP64)
         c->pencil_mask = 23;
     else
@@ -927,9 +928,12 @@ extern "C" mhd_status mhd_autotune(mhd_ctx* c, int reps, int* tile_len, int* blo
         // (VL without a selector: also with x by staged pencils, bit 4, by
         // aligned marching warps, bits 5 and 6, and for periodic boxes with
         // the fused predictor, bit 3)
-        const int masks[7] = {7, 6, 23, 103, 15, 31, 111};
+        // (CTU: also with the x tracing by aligned marching warps, bit 5)
+        const int vl_masks[7] = {7, 6, 23, 103, 15, 31, 111}, ctu_masks[3] = {7, 6, 39};
+        const bool ctu = c->sch.integrator != MHD_VL;
+        const int* masks = ctu ? ctu_masks : vl_masks;
         const int lens[3] = {8, 16, 32};
-        const int nmask = c->sch.integrator != MHD_VL || c->sel ? 2 : (!c->bc ? 7 : 4);
+        const int nmask = ctu ? 3 : (c->sel ? 2 : (!c->bc ? 7 : 4));
         c->sweep_bps = bbps;
         for (int i = 0; i < nmask && st == MHD_OK; i++)
             for (int j = 0; j < 3 && st == MHD_OK; j++) {

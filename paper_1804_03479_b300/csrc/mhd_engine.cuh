@@ -222,22 +222,27 @@ void launch_xpencil(mhd_ctx* c, const Boxes& g, const R* W, const TE* Bd, R* F, 
     k_xpencil<R, RECON, SOLVER, MODE, TE><<<grid, PENCIL_THREADS, smem, st>>>(g, W, Bd, F, c->gamma);
 }
 
-// the VL x sweeps by aligned marching warps (k_xmarch) instead of the
-// overlapping x-warps: the predictor with pencil-mask bits 0 and 5, the
+// the x sweeps by aligned marching warps (k_xmarch) instead of the
+// overlapping x-warps: the VL predictor with pencil-mask bits 0 and 5, the VL
 // corrector with bits 0 and 6 and a PLM stencil (the PPM corrector keeps its
-// x-warp); bit 4 (staged x pencils) takes precedence
+// x-warp; bit 4, staged x pencils, takes precedence); the CTU tracing (MODE
+// 2) with bits 0 and 5, a PLM stencil and a periodic x (the caller checks
+// the boundary)
 template <int RECON, int MODE>
 inline bool x_march(const mhd_ctx* c)
 {
     if (MODE == 0) return (c->pencil_mask & 33) == 33;
+    if (MODE == 2) return (c->pencil_mask & 33) == 33 && RECON != PPM;
     return (c->pencil_mask & 65) == 65 && RECON != PPM;
 }
 
 template <class R, int RECON, int SOLVER, int MODE, class TE>
-void launch_xmarch(mhd_ctx* c, const Boxes& g, const R* W, const TE* Bd, R* F, cudaStream_t st)
+void launch_xmarch(mhd_ctx* c, const Boxes& g, const R* W, const TE* Bd, R* F, cudaStream_t st, R* WM = nullptr,
+                   R* WP = nullptr)
 {
     if constexpr (MODE == 0 || RECON != PPM)
-        k_xmarch<R, RECON, SOLVER, MODE, TE><<<xmarch_grid(c), PENCIL_THREADS, 0, st>>>(g, W, Bd, F, c->gamma);
+        k_xmarch<R, RECON, SOLVER, MODE, TE><<<xmarch_grid(c), PENCIL_THREADS, 0, st>>>(g, W, Bd, F, c->gamma, WM,
+                                                                                         WP, c->dtc);
 }
 
 // the VL predictor runs fused (k_vl_predictor) when the pencil mask has bit 3,
@@ -481,7 +486,9 @@ void run_step(mhd_ctx* c, bool device_dt)
         // pencils on y and z and warps on x (x periodic) where the pencil
         // mask has the axis, else by tiles
         for (int d = 0; d < 3; d++) {
-            if ((c->pencil_mask & 1) && d == 0 && !(c->bc & 1))
+            if (d == 0 && x_march<RECON, 2>(c) && !(c->bc & 1))
+                launch_xmarch<R, RECON, SOLVER, 2, TE>(c, g, W, s.b[0], F1, st, WM, WP);
+            else if ((c->pencil_mask & 1) && d == 0 && !(c->bc & 1))
                 k_xwarp<R, RECON, SOLVER, 2, TE><<<xrow_grid(c), PENCIL_THREADS, 0, st>>>(
                     g, W, s.b[0], F1, gam, XW<RECON, 2>::slot, nullptr, nullptr, WM, WP, c->dtc);
             else if ((c->pencil_mask >> d & 1) && d > 0)

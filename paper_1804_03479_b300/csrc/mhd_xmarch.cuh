@@ -78,9 +78,9 @@ __host__ __device__ __forceinline__ long long xmarch_warps(long long nrows)
     return (nrows + XMARCH_ROWS - 1) / XMARCH_ROWS;
 }
 
-// one grid row: its box's x length, outflow flag and first cell
+// one grid row: its box, x length, outflow flag and first cell
 struct XRow {
-    int nx, out, nseg;
+    int bi, nx, out, nseg;
     long long base;
 };
 
@@ -88,6 +88,7 @@ __device__ __forceinline__ XRow xrow_of(const Boxes& B, long long r)
 {
     const int bi = box_of_row(B, r);
     XRow q;
+    q.bi = bi;
     q.nx = B.b[bi].nx;
     q.out = B.b[bi].bc & 1;
     q.nseg = (q.nx + 31) >> 5;
@@ -96,14 +97,19 @@ __device__ __forceinline__ XRow xrow_of(const Boxes& B, long long r)
 }
 
 // MODE 0: first-order states (the VL predictor); MODE 1: PLM-reconstructed
-// (the corrector).  Warp w marches grid rows w XMARCH_ROWS .. (w + 1)
-// XMARCH_ROWS - 1 of the whole batch (B.nxr rows, each of its own box); x
-// periodic or outflow (clamped cells, as in the x-warps).
+// (the VL corrector); MODE 2: PLM-reconstructed with the characteristic
+// tracing and the dB_n/dn source terms (CTU steps 1-2, as the tracing
+// pencils do), each cell's traced lower and upper states also written to
+// WMg / WPg.  Warp w marches grid rows w XMARCH_ROWS .. (w + 1) XMARCH_ROWS
+// - 1 of the whole batch (B.nxr rows, each of its own box); x periodic or
+// (MODE 0 and 1) outflow, with clamped cells as in the x-warps.
 template <class R, int RECON, int SOLVER, int MODE, class TE>
 __global__ void __launch_bounds__(PENCIL_THREADS, (xmarch_min_blocks<R, RECON, SOLVER, MODE>()))
-k_xmarch(Boxes B, const R* __restrict__ W, const TE* __restrict__ Bd, R* __restrict__ F, double gam)
+k_xmarch(Boxes B, const R* __restrict__ W, const TE* __restrict__ Bd, R* __restrict__ F, double gam,
+         R* __restrict__ WMg = nullptr, R* __restrict__ WPg = nullptr, const DtBox* __restrict__ dtb = nullptr)
 {
-    static_assert(MODE == 0 || (MODE == 1 && RECON != PPM), "the march reconstructs PLM stencils only");
+    static_assert(MODE == 0 || RECON != PPM, "the march reconstructs PLM stencils only");
+    constexpr bool TR = MODE == 2;
     const int lane = threadIdx.x & 31;
     const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     long long r = wid * XMARCH_ROWS;
@@ -153,13 +159,24 @@ k_xmarch(Boxes B, const R* __restrict__ W, const TE* __restrict__ Bd, R* __restr
         // cell x + 1 (v; one cell past its own, loaded one segment ahead), so
         // that its whole stencil is in this segment's lanes or, for lanes 0
         // and 1, the previous segment's (vc); wpc: the previous segment's
-        // "+" states.  Each row starts with its lead-in segment -1.
+        // "+" states.  Each row starts with its lead-in segment -1.  The
+        // tracing form loads the face field shifted by one as well (fs: face
+        // x + 1; face x from the lane below, or for lane 0 the previous
+        // segment's fsc), which gives each cell its dB_n/dn.
         R dum[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};   // slopes: unused by PLM
         R v[7], bv, vc[7], bvc, wpc[7];
+        TE fs, fsc, fsn;
+        R dtdx = R(0), hdt = R(0);
         load_rot(W, N, q.base + bidx(lane - 31, q.nx, q.out), 0, v, bv);
         copy7(vc, v);                                // (lanes 0 and 1 in a lead-in: not used)
         bvc = bv;
         copy7(wpc, v);
+        if constexpr (TR) {
+            fs = Bd[q.base + bidx(lane - 31, q.nx, q.out)];
+            fsc = fs;
+            dtdx = DtOf<R>::dtdx(dtb[q.bi]);
+            hdt = DtOf<R>::hdt(dtb[q.bi]);
+        }
         int s = -1;
         for (;;) {
             const int x = 32 * s + lane;
@@ -175,8 +192,12 @@ k_xmarch(Boxes B, const R* __restrict__ W, const TE* __restrict__ Bd, R* __restr
             const bool more = rn < rend;
             R vn[7], bvn;
             if (more) {                              // its cells (shifted by one) and faces
-                load_rot(W, N, qn.base + bidx(32 * sn + lane + 1, qn.nx, qn.out), 0, vn, bvn);
-                if (sn >= 0) fbn = Bd[qn.base + bidx(32 * sn + lane, qn.nx, qn.out)];
+                const long long cv = qn.base + bidx(32 * sn + lane + 1, qn.nx, qn.out);
+                load_rot(W, N, cv, 0, vn, bvn);
+                if constexpr (TR)
+                    fsn = Bd[cv];
+                else if (sn >= 0)
+                    fbn = Bd[qn.base + bidx(32 * sn + lane, qn.nx, qn.out)];
             }
             R w[7], bn, wm1[7], wm[7], wp[7];
 #pragma unroll
@@ -185,11 +206,24 @@ k_xmarch(Boxes B, const R* __restrict__ W, const TE* __restrict__ Bd, R* __restr
                 wm1[m] = __shfl_sync(0xffffffffu, lane >= 30 ? vc[m] : v[m], (lane + 30) & 31);
             }
             bn = __shfl_sync(0xffffffffu, lane == 31 ? bvc : bv, (lane + 31) & 31);
-            recon_cell<RECON, false>(wm1, w, v, bn, gr, dum, dum, dum, R(0), wm, wp);
+            recon_cell<RECON, TR>(wm1, w, v, bn, gr, dum, dum, dum, dtdx, wm, wp);
+            if constexpr (TR) {
+                fb = __shfl_sync(0xffffffffu, lane == 31 ? fsc : fs, (lane + 31) & 31);   // face x
+                const R dbn = sizeof(R) == 8 ? R((double)(fs - fb) / B.b[q.bi].dx)
+                                             : R(fs - fb) * R(B.b[q.bi].inv_dx);   // as face_gradient
+                trace_source(w, bn, dbn, hdt, gm1, wm, wp);
+            }
             if (s >= 0) {
                 R wl[7];
                 from_below(wl, wp, wpc);
                 if (x < q.nx) {
+                    if constexpr (TR) {
+#pragma unroll
+                        for (int m = 0; m < 7; m++) {
+                            WMg[(long long)m * N + q.base + x] = wm[m];
+                            WPg[(long long)m * N + q.base + x] = wp[m];
+                        }
+                    }
                     riemann<SOLVER>(wl, wm, R(fb), gm1, gr, f);
 #pragma unroll
                     for (int m = 0; m < 7; m++) F[(long long)m * N + q.base + x] = f[m];
@@ -201,7 +235,16 @@ k_xmarch(Boxes B, const R* __restrict__ W, const TE* __restrict__ Bd, R* __restr
             bvc = bv;
             copy7(v, vn);
             bv = bvn;
-            if (sn >= 0) fb = fbn;
+            if constexpr (TR) {
+                fsc = fs;
+                fs = fsn;
+                if (qn.bi != q.bi) {
+                    dtdx = DtOf<R>::dtdx(dtb[qn.bi]);
+                    hdt = DtOf<R>::hdt(dtb[qn.bi]);
+                }
+            } else if (sn >= 0) {
+                fb = fbn;
+            }
             s = sn;
             r = rn;
             q = qn;

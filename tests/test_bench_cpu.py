@@ -76,7 +76,9 @@ def test_roofline_of_the_dominant_kernel():
     assert ks["predictor_xmarch"] == (4.8, 1) and ks["corrector_xwarp"] == (6.2, 1)
     ks = bench.kernels_of(groups, {"pencil_mask": 119})          # bit 4 takes precedence
     assert ks["predictor_xpencil"] == (4.8, 1) and ks["corrector_xpencil"] == (6.2, 1)
-    ks = bench.kernels_of(groups, {"pencil_mask": 103}, "ctu")   # CTU keeps its x-warps
+    ks = bench.kernels_of(groups, {"pencil_mask": 39}, "ctu")    # CTU: the x tracing marches
+    assert ks["tracing_xmarch"] == (4.8, 1) and ks["ctucorr_xwarp"] == (6.2, 1)
+    ks = bench.kernels_of(groups, {"pencil_mask": 39}, "ctu", "ppm")
     assert ks["tracing_xwarp"] == (4.8, 1) and ks["ctucorr_xwarp"] == (6.2, 1)
 
 

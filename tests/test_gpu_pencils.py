@@ -139,7 +139,7 @@ def test_pencil_arguments(M):
         s.free()
     s = M.Solver(st.U.shape[1:], st.dx, st.gamma, "ctu", "plm", "roe", "fp64", 0.3)
     try:
-        assert s.sweep_pencils() == (7, 32)       # the CTU default: warps on x, pencils on y and z
+        assert s.sweep_pencils() == (39, 32)      # the CTU default: x tracing by aligned marching warps, pencils on y and z
         s.set_sweep_pencils(6, 16)
         assert s.sweep_pencils() == (6, 16)
     finally:

@@ -46,7 +46,8 @@ def parity(M, U, B, dx, gam, scheme, nsteps, bc=0, mask=MARCH, tol=1e-12):
         if bc:
             s.set_boundary(bc)
         s.set_sweep_pencils(mask, 32)
-        assert s.launches_per_step() == 12 + (2 * bin(bc).count("1") if bc else 0)
+        per_axis = 2 if scheme[0] == "vl" else 1          # outer-face passes per outflow axis
+        assert s.launches_per_step() == 12 + per_axis * bin(bc).count("1")
         for it in range(nsteps):
             s.set_state(U, B)
             dt = orc.cfl_dt(U, B, dx, gam, 0.3, bc=bc) if bc else orc.cfl_dt(U, B, dx, gam, 0.3)
@@ -193,6 +194,84 @@ def test_xmarch_agrees_with_xwarps(M, prec, scheme):
         assert rel_l1(Ba[d].astype(np.float64), Bb[d].astype(np.float64)) <= 1e-5, (prec, scheme, d)
 
 
+CTU = [("ctu", r, s) for r in ("plm", "ppm") for s in ("roe", "hlld", "hlle")]   # (PLM_PRIM: VL only)
+
+
+@pytest.mark.parametrize("scheme", CTU)
+def test_xmarch_ctu_tracing_fp64_parity(M, scheme):
+    """CTU steps 1-2 along x by the march (mask bit 5): traced states with
+    the dB_n/dn source from the shifted face field, written per cell, and
+    their fluxes (PPM: the x-warps)"""
+    st = I.abc(None, kmult=1, beta=0.5, seed=57, noise=2e-2, shape=(64, 12, 10))
+    parity(M, st.U, st.B, st.dx, st.gamma, scheme, 2, mask=39)
+
+
+@pytest.mark.parametrize("shape", [(40, 12, 8), (33, 9, 6), (5, 9, 7), (1, 16, 16)])
+def test_xmarch_ctu_tracing_fp64_parity_ragged_and_short(M, shape):
+    L = shape[1] / 16.0
+    st = I.abc(None, kmult=L, beta=0.5, seed=58, noise=3e-2, shape=shape, L=L)
+    parity(M, st.U, st.B, st.dx, st.gamma, ("ctu", "plm", "roe"), 2, mask=39)
+    parity(M, st.U, st.B, st.dx, st.gamma, ("ctu", "plm", "hlld"), 2, mask=39)
+
+
+@pytest.mark.parametrize("bc", [1, 6])
+def test_xmarch_ctu_fp64_parity_outflow(M, bc):
+    """an outflow x keeps the tile sweep along x (its lead-in is cell 0 with
+    its own stencil); outflow y / z with x periodic marches"""
+    st = I.open_box((26, 20, 18), seed=13)
+    parity(M, st.U, st.B, st.dx, st.gamma, ("ctu", "plm", "roe"), 2, bc=bc, mask=39)
+
+
+def test_xmarch_ctu_fp64_batch_parity(M):
+    """uneven boxes, per-box dt and dx in the traced states"""
+    shapes = [(16, 3, 5), (33, 7, 3), (40, 5, 5), (70, 3, 3)]
+    boxes = [I.abc(None, kmult=1, beta=0.5, seed=70 + k, noise=3e-2, shape=sh) for k, sh in enumerate(shapes)]
+    scheme = ("ctu", "plm", "hlle")
+    s = M.Solver(None, None, 5 / 3, *scheme, "fp64", 0.3,
+                 shapes=[b.U.shape[1:] for b in boxes], dxs=[b.dx for b in boxes])
+    try:
+        s.set_sweep_pencils(39, 32)
+        for k, b in enumerate(boxes):
+            s.set_state(b.U, b.B, box=k)
+        dts = np.array([orc.cfl_dt(b.U, b.B, b.dx, b.gamma, 0.3) for b in boxes])
+        s.step(dts)
+        for k, b in enumerate(boxes):
+            U, B = b.U.copy(), b.B.copy()
+            orc.step(U, B, b.dx, b.gamma, float(dts[k]), *scheme)
+            Ug, Bg = s.get_state(box=k)
+            mfloor = 1e-2 * np.abs(U[0]).sum()
+            for f in range(5):
+                den = max(np.abs(U[f]).sum(), mfloor if f in (1, 2, 3) else 0.0)
+                assert np.abs(Ug[f] - U[f]).sum() / den <= 1e-12, (k, f)
+            bfloor = 1e-2 * np.abs(B).sum() / 3
+            for d in range(3):
+                assert np.abs(Bg[d] - B[d]).sum() / max(np.abs(B[d]).sum(), bfloor) <= 1e-12, (k, d)
+    finally:
+        s.free()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+@pytest.mark.parametrize("scheme", [("ctu", "plm", "roe"), ("ctu", "plm", "hlld"), ("ctu", "plm", "hlle")])
+def test_xmarch_ctu_agrees_with_xwarps(M, prec, scheme):
+    st = I.abc(None, kmult=1, beta=0.5, seed=59, noise=2e-2, shape=(64, 24, 40))
+    cast = np.float32 if prec == "fp32" else np.float64
+    out = []
+    for mask in (39, 7):
+        s = M.Solver(st.U.shape[1:], st.dx, st.gamma, *scheme, prec, 0.3)
+        try:
+            s.set_sweep_pencils(mask, 32)
+            s.set_state(st.U.astype(cast), st.B.astype(cast))
+            s.advance(3)
+            out.append(s.get_state())
+        finally:
+            s.free()
+    (Ua, Ba), (Ub, Bb) = out
+    for f in range(5):
+        assert rel_l1(Ua[f].astype(np.float64), Ub[f].astype(np.float64)) <= 1e-5, (prec, scheme, f)
+    for d in range(3):
+        assert rel_l1(Ba[d].astype(np.float64), Bb[d].astype(np.float64)) <= 1e-5, (prec, scheme, d)
+
+
 def test_xmarch_fp32_divergence_free(M):
     st = I.abc(None, kmult=1, beta=0.5, seed=55, noise=2e-2, shape=(64, 24, 36))
     s = M.Solver(st.U.shape[1:], st.dx, st.gamma, "vl", "plm", "roe", "fp32", 0.3)
@@ -221,7 +300,7 @@ def test_xmarch_mask_range_and_precedence(M):
         s.free()
     for prec, scheme, mask in [("fp32", ("vl", "plm", "roe"), 103), ("fp32", ("vl", "plm_prim", "hlle"), 103),
                                ("fp32", ("vl", "ppm", "hlld"), 103), ("mixed", ("vl", "plm", "roe"), 103),
-                               ("fp32", ("ctu", "plm", "roe"), 7), ("fp64", ("ctu", "plm", "roe"), 7)]:
+                               ("fp32", ("ctu", "plm", "roe"), 39), ("fp64", ("ctu", "plm", "roe"), 39)]:
         s = M.Solver(st.U.shape[1:], st.dx, st.gamma, *scheme, prec, 0.3)
         try:
             assert s.sweep_pencils() == (mask, 32), (prec, scheme)
