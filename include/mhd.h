@@ -247,9 +247,11 @@ mhd_status mhd_get_dirichlet(mhd_ctx* ctx, int axis, int* nlayers);
  * producing a face, the neighbours across a segment's ends from the
  * previous segment's registers and the next segment's prefetch (the
  * overlapping warps above produce 27 to 31 faces per 32 lanes from loads
- * that start off a line boundary).  At 256^3 FP32 the predictor takes 0.36
- * ms where the overlapping warps take 0.45 (Roe), the PLM corrector 0.60 /
- * 0.53 / 0.43 ms against 0.62 / 0.57 / 0.50 (Roe / HLLD / HLLE).  With a
+ * that start off a line boundary; FP32 predictor rows of whole aligned
+ * segments stream three segments per warp through shared memory by
+ * asynchronous copies).  At 256^3 FP32 the predictor takes 0.27 ms where the
+ * overlapping warps take 0.45 (Roe), the PLM corrector 0.51 / 0.51 / 0.44 ms
+ * against 0.62 / 0.57 / 0.50 (Roe / HLLD / HLLE).  With a
  * learned selector the cheap x sweep marches every face and the full
  * scheme's x-warp items, launched after it, overwrite theirs.
  * For CTU, bit 5 with bit 0 runs the PLM tracing along a periodic x (CTU

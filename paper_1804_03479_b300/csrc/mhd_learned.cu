@@ -294,7 +294,6 @@ static void run_step_learned(mhd_ctx* c, bool device_dt)
     typedef float R;
     const Boxes g = c->B;
     const long long n = g.N;
-    const int nb = c->cell_grid;
     cudaStream_t st = c->stream;
     StateP<float, float> s = state_of<float, float>(c);
     R* W = (R*)c->W;

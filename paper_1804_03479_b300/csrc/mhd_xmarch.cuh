@@ -9,8 +9,11 @@
 // (FP32, nx and the box offset multiples of 32) stores whole lines.  The
 // stencil's neighbours across a segment's ends come from registers kept
 // from the previous segment:
-//   predictor  lane l loads cell x, one segment ahead; lane 0 takes the
-//              previous segment's last cell;
+//   predictor  lane l takes cell x, and lane 0 the previous segment's last
+//              cell.  FP32 rows of whole 16-byte-aligned segments come
+//              through shared memory by asynchronous copies, three segments
+//              in flight per warp; other rows load cell x one segment ahead
+//              into registers;
 //   corrector  lane l loads cell x + 1, one segment ahead, so that the
 //              stencil x - 1 .. x + 1 of every lane lies in this segment's
 //              loads or, for lanes 0 and 1, the previous segment's; lane 0
@@ -28,9 +31,9 @@
 // instead: 31 (predictor) or 29 (PLM corrector) of its 32 lanes produce a
 // face, a 256-cell row takes 9 segments where this form takes 8 (plus the
 // corrector's lead-in), and its loads and stores start off a line boundary.
-// At 256^3 FP32 this form takes 0.356 ms for the Roe predictor (x-warps
-// 0.449) and 0.510 / 0.509 ms for the PLM corrector with Roe and HLLD
-// (x-warps 0.616 / 0.574).
+// At 256^3 FP32 this form takes 0.266 ms for the Roe predictor (x-warps
+// 0.449; 0.356 with the register prefetch of one segment) and 0.510 / 0.509
+// ms for the PLM corrector with Roe and HLLD (x-warps 0.616 / 0.574).
 #pragma once
 #include "mhd_kernels.cuh"
 
@@ -64,6 +67,29 @@ constexpr int xmarch_min_blocks()
 {
     return sizeof(R) == 4 && SOLVER == ROE ? 4 : xwarp_min_blocks<R, RECON, SOLVER, MODE>();
 }
+
+// 16-byte asynchronous copy global -> shared (cache at L2 only)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_group()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// wait until at most N of this thread's committed copy groups are pending
+template <int N>
+__device__ __forceinline__ void cp_async_wait_pending()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// the staged predictor: segments in flight per warp, and the arrays of a
+// segment (the 7 primitives of the x frame and the face field)
+constexpr int XM_SLOTS = 3, XM_ARR = 8;
 
 // grid rows marched by one warp.  The corrector's loop chains them (the
 // next row's lead-in loads issued while the current row's last segment is
@@ -126,6 +152,57 @@ k_xmarch(Boxes B, const R* __restrict__ W, const TE* __restrict__ Bd, R* __restr
         // an outer loop over rows cost registers and time (0.375 against
         // 0.356 ms at 256^3 FP32 Roe, even at one row)
         static_assert(XMARCH_ROWS == 1, "the predictor marches one row a warp");
+        if constexpr (sizeof(R) == 4 && sizeof(TE) == 4) {
+            // FP32 rows of whole 16-byte-aligned segments (periodic x, a quad
+            // box: nx, the offset and the field stride multiples of 4 cells,
+            // nx a multiple of 32): the segments come through shared memory,
+            // XM_SLOTS of them in flight per warp, by asynchronous copies that
+            // hold no registers; one register segment in flight left the
+            // kernel waiting on memory (long_scoreboard first): 0.266 against
+            // 0.356 ms at 256^3 (Roe), the y/z pencils' rate
+            __shared__ __align__(16) float xm_buf[PENCIL_THREADS / 32][XM_SLOTS][XM_ARR][32];
+            if (!q.out && q.nx % 32 == 0 && B.b[q.bi].quad) {
+                float (*buf)[XM_ARR][32] = xm_buf[threadIdx.x >> 5];
+                // segment sg into slot sl: lane l copies pieces l and l + 32
+                // of the 8 x 8 16-byte pieces (array a = piece / 8)
+                auto stage = [&](int sg, int sl) {
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        const int pc = lane + 32 * h, a = pc >> 3, o = (pc & 7) * 4;
+                        const int fld = a < 5 ? a : a + 1;             // W fields 0-4, 6, 7
+                        const float* src = a < 7 ? (const float*)W + (long long)fld * N : (const float*)Bd;
+                        cp_async16(&buf[sl][a][o], src + q.base + 32 * sg + o);
+                    }
+                };
+                R wc[7], bdum;
+                load_rot(W, N, q.base + q.nx - 1, 0, wc, bdum);      // cell -1: the row's last cell
+#pragma unroll
+                for (int k = 0; k < XM_SLOTS; k++) {
+                    if (k < q.nseg) stage(k, k);
+                    cp_async_group();                                // one group per segment, empty past the row
+                }
+                for (int sg = 0; sg < q.nseg; sg++) {
+                    const int sl = sg % XM_SLOTS;
+                    cp_async_wait_pending<XM_SLOTS - 1>();           // segment sg has landed (this lane's part)
+                    __syncwarp();                                    // ... and every lane's
+                    R w[7];
+#pragma unroll
+                    for (int m = 0; m < 7; m++) w[m] = buf[sl][m][lane];
+                    const R fbv = buf[sl][7][lane];
+                    __syncwarp();                                    // every lane is done with the slot
+                    if (sg + XM_SLOTS < q.nseg) stage(sg + XM_SLOTS, sl);
+                    cp_async_group();
+                    R wl[7];
+                    from_below(wl, w, wc);
+                    riemann<SOLVER>(wl, w, fbv, gm1, gr, f);
+#pragma unroll
+                    for (int m = 0; m < 7; m++) F[(long long)m * N + q.base + 32 * sg + lane] = f[m];
+                    copy7(wc, w);
+                }
+                cp_async_wait_pending<0>();
+                return;
+            }
+        }
         R w[7], bn, wn[7], bnn, wc[7], bdum;
         load_rot(W, N, q.base + bidx(-1, q.nx, q.out), 0, wc, bdum);
         {
