@@ -62,6 +62,19 @@ static cudaError_t dalloc(mhd_ctx* c, void** p, size_t bytes)
     return e;
 }
 
+// the second flux array of a VL context, on first use: the corrector's
+// fluxes when its y sweep runs fused with the half update (pencil-mask bit 7)
+static cudaError_t ensure_f2(mhd_ctx* c)
+{
+    if (c->F2 || c->sch.integrator != MHD_VL) return cudaSuccess;
+    cudaError_t e = dalloc(c, &c->F2, 21 * (size_t)c->B.N * c->szr);
+    if (e != cudaSuccess) {
+        c->F2 = nullptr;
+        cudaGetLastError();   // an allocation failure is not sticky: clear it for the next check
+    }
+    return e;
+}
+
 // the driver's tensor-map encoder, looked up once through the runtime (no
 // link against the driver library)
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
@@ -280,13 +293,17 @@ static mhd_status init_common(int nbox, const mhd_grid* grids, double gamma, con
     // PLM tracing along x by aligned marching warps (bit 5).  The fused
     // predictor (bit 3) is not a default: at 256^3 it ties the sweeps it
     // replaces (its halo solves and plane barriers cost what it saves in
-    // traffic).  The autotuner may change the mask.
+    // traffic).  FP32 and mixed PLM: the half update inside the y corrector
+    // pencils (bit 7; 256^3 FP32 Roe: 0.708 ms against 0.439 + 0.475 for the
+    // two kernels, mixed 1.90 against 1.46 + 0.49); FP64 keeps the two (its
+    // corrector is bound by the FP64 pipe: 30.8 against 2.8 + 27.5 ms).  The
+    // autotuner may change the mask.
     if (scheme->integrator != MHD_VL)
         c->pencil_mask = 39;
     else if (scheme->precision == MHD_FP64)
         c->pencil_mask = 23;
     else
-        c->pencil_mask = 103;
+        c->pencil_mask = scheme->recon != MHD_PPM ? 231 : 103;   // PLM: the half update in the y corrector
     c->pencil_len = 32;
     c->cell_grid = (int)(vb < 16LL * c->nsm ? vb : 16LL * c->nsm);
     if (c->cell_grid < 1) c->cell_grid = 1;
@@ -308,7 +325,9 @@ static mhd_status init_common(int nbox, const mhd_grid* grids, double gamma, con
     if (e == cudaSuccess) e = dalloc(c, &c->W, 8 * n * c->szr);
     if (e == cudaSuccess) e = dalloc(c, &c->Wh, 8 * n * c->szr);
     if (e == cudaSuccess) e = dalloc(c, &c->F1, 21 * n * c->szr);
-    if (e == cudaSuccess && ctu) e = dalloc(c, &c->F2, 21 * n * c->szr);
+    // (VL: the second flux array for the y corrector fused with the half
+    // update, pencil-mask bit 7, the FP32 and mixed PLM default)
+    if (e == cudaSuccess && (ctu || (c->pencil_mask & 128))) e = dalloc(c, &c->F2, 21 * n * c->szr);
     if (e == cudaSuccess) e = dalloc(c, &c->E, 3 * n * c->szr);
     for (int d = 0; d < 3 && e == cudaSuccess; d++) e = dalloc(c, &c->Bh[d], n * c->sze);
     if (e == cudaSuccess && ctu) e = dalloc(c, &c->WM, 21 * n * c->szr);
@@ -717,7 +736,7 @@ static void count_launches(mhd_ctx* c)
     }
     // (CTU: one stage-1 outer-face pass per outflow axis; the stage-2 ones
     // are part of the corrections)
-    int n = fused_predictor(c) ? 8 : 12;
+    int n = fused_predictor(c) ? 8 : (y_half(c) ? 11 : 12);   // (the y corrector takes the half update)
     if (emf_form(c) == 2) n -= fused_predictor(c) ? 1 : 2;   // each edge-field kernel takes its update
     const int per_axis = c->sch.integrator == MHD_VL ? 2 : 1;
     for (int d = 0; d < 3; d++) n += per_axis * (c->bc >> d & 1) + (c->fix_nl[d] > 0);
@@ -823,8 +842,10 @@ extern "C" mhd_status mhd_get_boundary(mhd_ctx* c, int* outflow_mask)
 extern "C" mhd_status mhd_set_sweep_pencils(mhd_ctx* c, int pencil_mask, int pencil_len)
 {
     if (!c) return MHD_EINVAL;
-    if (pencil_mask < 0 || pencil_mask > 127 || pencil_len < 1 || pencil_len > 1024)
-        return fail(c, MHD_EINVAL, "pencil_mask must be in [0, 127] and pencil_len in [1, 1024]");
+    if (pencil_mask < 0 || pencil_mask > 255 || pencil_len < 1 || pencil_len > 1024)
+        return fail(c, MHD_EINVAL, "pencil_mask must be in [0, 255] and pencil_len in [1, 1024]");
+    if ((pencil_mask & 128) && ensure_f2(c) != cudaSuccess)
+        return fail(c, MHD_ENOMEM, "second flux array for the fused y corrector");
     c->pencil_mask = pencil_mask;
     c->pencil_len = pencil_len;
     CK(layout_tiles(c, c->B.tl));
@@ -929,11 +950,14 @@ extern "C" mhd_status mhd_autotune(mhd_ctx* c, int reps, int* tile_len, int* blo
         // aligned marching warps, bits 5 and 6, and for periodic boxes with
         // the fused predictor, bit 3)
         // (CTU: also with the x tracing by aligned marching warps, bit 5)
-        const int vl_masks[7] = {7, 6, 23, 103, 15, 31, 111}, ctu_masks[3] = {7, 6, 39};
+        // (VL, periodic, no selector: also with the half update fused into
+        // the y corrector pencils, bit 7, when its flux array can be had)
+        const int vl_masks[9] = {7, 6, 23, 103, 15, 31, 111, 151, 231}, ctu_masks[3] = {7, 6, 39};
         const bool ctu = c->sch.integrator != MHD_VL;
         const int* masks = ctu ? ctu_masks : vl_masks;
         const int lens[3] = {8, 16, 32};
-        const int nmask = ctu ? 3 : (c->sel ? 2 : (!c->bc ? 7 : 4));
+        const bool yh = c->sch.recon != MHD_PPM && ensure_f2(c) == cudaSuccess;
+        const int nmask = ctu ? 3 : (c->sel ? 2 : (!c->bc ? (yh ? 9 : 7) : 4));
         c->sweep_bps = bbps;
         for (int i = 0; i < nmask && st == MHD_OK; i++)
             for (int j = 0; j < 3 && st == MHD_OK; j++) {

@@ -8,6 +8,7 @@
 #include "mhd_xpencil.cuh"
 #include "mhd_xmarch.cuh"
 #include "mhd_tma.cuh"
+#include "mhd_yhalf.cuh"
 
 struct mhd_ctx;
 struct mhd_mlp;
@@ -286,6 +287,25 @@ inline int emf_form(const mhd_ctx* c)
     return c->emf_stage_req == 2 && !c->bc ? 2 : 0;
 }
 
+// the VL half update fused into the corrector's y pencils (k_yhalf) with
+// pencil-mask bits 1 and 7: a PLM stencil, periodic boxes without a learned
+// selector, the predictor and the edge fields as separate kernels, and the
+// second flux array allocated (the corrector's fluxes go there)
+inline bool y_half(const mhd_ctx* c)
+{
+    return c->sch.recon != MHD_PPM && (c->pencil_mask & 130) == 130 && c->sch.integrator == MHD_VL && !c->bc &&
+           !c->sel && c->F2 && !fused_predictor(c) && emf_form(c) == 0;
+}
+
+template <class R, class TU, class TE, int RECON, int SOLVER>
+void launch_yhalf(mhd_ctx* c, const Boxes& g, const StateP<TU, TE>& s, const R* F, const R* E, TE* const Bh[3],
+                  R* Wh, R* Fc, cudaStream_t st)
+{
+    if constexpr (RECON != PPM)
+        k_yhalf<R, TU, TE, RECON, SOLVER><<<pencil_grid(c, 1), PENCIL_THREADS, 0, st>>>(
+            g, s, F, E, c->dtc, c->gamma, c->sch.pfloor, Bh[0], Bh[1], Bh[2], Wh, Fc + 7 * g.N);
+}
+
 // k_emf_update: the edge fields of F and W, then the half (HALF: into Bh and
 // Wh) or full update; persistent grid as launch_vl_predictor
 template <class R, class TU, class TE, bool HALF>
@@ -403,6 +423,7 @@ void run_step(mhd_ctx* c, bool device_dt)
 
     if (INTEG == VL) {
         const int cs = c->bc ? cross_size(c->hbox[0].nx, c->hbox[0].ny, c->hbox[0].nz) : 0;
+        const bool yh = RECON != PPM && y_half(c);
         if (fused_predictor(c)) {
             // VL steps 1-3 in one kernel (its time goes to the half-update group)
             for (int b = 2; b <= 5; b++) prof_mark(c, b);
@@ -440,33 +461,40 @@ void run_step(mhd_ctx* c, bool device_dt)
                     k_half<R, TU, TE, true><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1],
                                                                          Bh[2], Wh, c->sch.pfloor,
                                                                          (const R*)c->fout, cs);
+                else if (yh)     // the half update inside the y corrector pencils (its time: the half group)
+                    launch_yhalf<R, TU, TE, RECON, SOLVER>(c, g, s, F1, E, Bh, Wh, F2, st);
                 else
                     launch_half<R, TU, TE>(c, g, s, F1, E, Bh, Wh, st);
             }
             prof_mark(c, 6);
         }
-        // VL steps 4-7: reconstruct at the half step, Riemann, edge E, full update
+        // VL steps 4-7: reconstruct at the half step, Riemann, edge E, full
+        // update; the corrector's fluxes go to F2 when the y sweep ran fused
+        // with the half update (the predictor's F1 was read while it ran)
+        R* Fc = yh ? F2 : F1;
         for (int d = 0; d < 3; d++) {
-            if (d == 0 && x_pencils(c))
-                launch_xpencil<R, RECON, SOLVER, 1, TE>(c, g, Wh, Bh[0], F1, st);
+            if (d == 1 && yh)
+                ;                                       // done with the half update
+            else if (d == 0 && x_pencils(c))
+                launch_xpencil<R, RECON, SOLVER, 1, TE>(c, g, Wh, Bh[0], Fc, st);
             else if (d == 0 && x_march<RECON, 1>(c))
-                launch_xmarch<R, RECON, SOLVER, 1, TE>(c, g, Wh, Bh[0], F1, st);
+                launch_xmarch<R, RECON, SOLVER, 1, TE>(c, g, Wh, Bh[0], Fc, st);
             else if ((c->pencil_mask >> d & 1) && d == 0)
                 k_xwarp<R, RECON, SOLVER, 1, TE><<<xrow_grid(c), PENCIL_THREADS, 0, st>>>(
-                    g, Wh, Bh[d], F1, gam, XW<RECON, 1>::slot);
+                    g, Wh, Bh[d], Fc, gam, XW<RECON, 1>::slot);
             else if (c->pencil_mask >> d & 1)
                 launch_pencil<R, RECON, SOLVER, 1, TE>(d, pencil_grid(c, d), st, g, Wh, Bh[d],
-                                                       F1 + (long long)d * 7 * n, gam);
+                                                       Fc + (long long)d * 7 * n, gam);
             else
                 k_sweep<R, RECON, SOLVER, 1, TE><<<sweep_grid(c, d), SWEEP_THREADS, smem, st>>>(
-                    g, d, Wh, Bh[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam);
+                    g, d, Wh, Bh[d], Fc + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam);
             prof_mark(c, 7 + d);
         }
         if (emf_form(c) == 2) {       // edge fields and full update in one kernel (the full group)
             prof_mark(c, 10);
             launch_emf_update<R, TU, TE, false>(c, g, s, F1, Wh, nullptr, nullptr, st);
         } else {
-            launch_emf<R>(c, g, F1, Wh, E, st);
+            launch_emf<R>(c, g, Fc, Wh, E, st);
             prof_mark(c, 10);
             for (int d = 0; d < 3; d++)
                 if (c->bc >> d & 1)
@@ -475,7 +503,7 @@ void run_step(mhd_ctx* c, bool device_dt)
             if (c->bc)
                 k_full<R, TU, TE, true><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, (const R*)c->fout, cs);
             else
-                launch_full<R, TU, TE>(c, g, s, F1, E, st);
+                launch_full<R, TU, TE>(c, g, s, Fc, E, st);
         }
         fix_layers(c, s, st);
         prof_mark(c, 11);

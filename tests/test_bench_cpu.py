@@ -126,3 +126,39 @@ def test_step_roofline_binds_at_the_lower_ceiling():
     assert r64["bound"] == "alu" and r64["alu"]["peak_tflops"] == 1.2
     rm = bench.step_roofline("mixed", n, 6.0, pk, apk, scheme)
     assert rm["hbm"]["bytes_per_cell_update"] == 96 and rm["alu"]["peak_tflops"] == 70.0
+
+
+def test_roofline_of_the_y_corrector_with_the_half_update():
+    """pencil-mask bit 7 (with bit 1, PLM, no bit 3): the library's half
+    group times the y corrector that forms the half-step states and its y
+    group is empty; the bench names them corrector_yhalf, whose work per cell
+    is the half update's plus one corrector face"""
+    import bench
+    n = 256 ** 3
+    steps = 10
+    groups = {"prim_cfl": 1.8, "predictor_x": 2.7, "predictor_y": 2.7, "predictor_z": 2.7, "emf1": 2.9,
+              "half_update": 7.1, "corrector_x": 5.1, "corrector_y": 0.01, "corrector_z": 4.7, "emf2": 3.0,
+              "full_update": 4.1}
+    tuned = {"pencil_mask": 231}
+    assert bench.is_yhalf(tuned) and not bench.is_yhalf(tuned, "vl", "ppm")
+    assert not bench.is_yhalf({"pencil_mask": 103}) and not bench.is_yhalf({"pencil_mask": 239})
+    g = bench.fold_groups(groups, tuned, "vl", "plm")
+    assert "half_update" not in g and "corrector_y" not in g
+    assert g["corrector_yhalf"] == pytest.approx(7.11)
+    assert bench.fold_groups(groups, tuned, "vl", "ppm") == groups
+    st = bench.stages_of(g)
+    assert st["corrector_yhalf"] == pytest.approx(7.11) and st["corrector_sweeps"] == pytest.approx(9.8)
+    pk = {"hbm_gbs": 6491.2, "src": "measured"}
+    apk = {"fp32": 75.0, "fp64": 1.0, "src": "test"}
+    scheme = ("vl", "plm", "roe")
+    r = bench.roofline("fp32", g, steps, n, pk, apk, scheme, tuned)
+    assert r["kernel"] == "corrector_yhalf" and r["launches"] == 1
+    af = bench.alg_flops(scheme)
+    fpu = af["per_cell"]["half_update"] + af["per_face"]["corrector"]
+    assert r["alu_view"]["achieved"] == pytest.approx(n * fpu / (7.11 / steps * 1e-3) / 1e12, rel=1e-12)
+    # bytes: rho, M, e and the faces (32), the 15 fluxes and 3 edge fields
+    # (72) in; the half-step faces (12), primitives (32) and y fluxes (28) out
+    assert r["hbm_view"]["algorithmic_bytes_per_launch"] == n * (32 + 72 + 12 + 32 + 28)
+    gb = bench.group_bytes("fp32", n, "vl", False, True)
+    assert "half_update" not in gb and gb["corrector_sweeps"] == 2 * n * 64
+    assert sum(gb.values()) == sum(bench.group_bytes("fp32", n, "vl").values()) - n * 64 + n * 28

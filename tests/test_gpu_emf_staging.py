@@ -34,6 +34,11 @@ def run(M, st, scheme, prec, mode, nsteps, bc=0):
     cast = np.float32 if prec == "fp32" else np.float64
     s = M.Solver(st.U.shape[1:], st.dx, st.gamma, *scheme, prec, 0.3)
     try:
+        # the same sweep forms in both runs: the half update inside the y
+        # corrector (mask bit 7, the FP32 / mixed PLM default) needs the
+        # edge fields as their own kernel, so the copied form runs without it
+        m, plen = s.sweep_pencils()
+        s.set_sweep_pencils(m & 127, plen)
         s.set_emf_staging(mode)
         if bc:
             s.set_boundary(bc)
