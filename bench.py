@@ -37,7 +37,7 @@ PAPER_P100 = {"fp32": 1.2e8, "fp64": 5.5e7}   # Sec. 5.2 (i), Tesla P100, VL + P
 # the step's kernel groups as the library's profiler reports them (one per
 # sweep axis) and their aggregation into the seven stages of the step
 AXES = ("x", "y", "z")
-STAGES = ["prim_cfl", "predictor_fused", "predictor_sweeps", "emf1", "half_update", "corrector_yhalf",
+STAGES = ["prim_cfl", "predictor_yprim", "predictor_fused", "predictor_sweeps", "emf1", "half_update", "corrector_yhalf",
           "corrector_sweeps", "emf2", "full_update"]
 
 
@@ -53,15 +53,28 @@ def is_yhalf(tuned, integ="vl", recon="plm"):
     return integ == "vl" and recon != "ppm" and (m & 130) == 130 and not m & 8
 
 
-def fold_groups(groups, tuned, integ="vl", recon="plm"):
+def is_yprim(tuned, integ="vl", pfloor=0.0):
+    """the t^n primitives and CFL speeds run inside the y predictor pencils
+    (pencil-mask bits 1 and 8, bit 3 clear, no pressure floor; periodic)"""
+    m = (tuned or {}).get("pencil_mask", 0) or 0
+    return integ == "vl" and (m & 258) == 258 and not m & 8 and not pfloor > 0
+
+
+def fold_groups(groups, tuned, integ="vl", recon="plm", pfloor=0.0):
     """With the fused VL predictor the library's half-update group times the
     fused kernel, and the predictor-sweep and first edge-field groups are
     empty (back-to-back events): name the group for what it ran.  With the
     half update inside the y corrector pencils the half-update group times
-    that kernel and the y corrector group is empty: corrector_yhalf."""
-    if is_yhalf(tuned, integ, recon):
+    that kernel and the y corrector group is empty: corrector_yhalf.  With
+    the primitives inside the y predictor pencils the primitive group times
+    that kernel and the y predictor group is empty: predictor_yprim."""
+    yp, yh = is_yprim(tuned, integ, pfloor), is_yhalf(tuned, integ, recon)
+    if yp or yh:
         out = dict(groups)
-        out["corrector_yhalf"] = out.pop("half_update", 0.0) + out.pop("corrector_y", 0.0)
+        if yp:
+            out["predictor_yprim"] = out.pop("prim_cfl", 0.0) + out.pop("predictor_y", 0.0)
+        if yh:
+            out["corrector_yhalf"] = out.pop("half_update", 0.0) + out.pop("corrector_y", 0.0)
         return out
     if not is_fused(tuned, integ):
         return groups
@@ -292,13 +305,15 @@ def sweep_bytes_per_face(prec, kind="vl"):
             "ctucorr": 29 * szr + sze + 7 * szr}[kind]
 
 
-def group_bytes(prec, n, integ="vl", fused=False, yhalf=False):
+def group_bytes(prec, n, integ="vl", fused=False, yhalf=False, yprim=False):
     """algorithmic HBM bytes of each stage of one step on n cells: every
     array element a kernel needs is read once and every result written once
     (neighbour re-reads assumed to hit in cache).  The fused VL predictor
     reads W, the face field and rho, M, e and writes Bh and Wh.  The y
     corrector with the half update reads what the half update reads and
-    writes what it writes, plus the 7 y fluxes."""
+    writes what it writes, plus the 7 y fluxes; the y predictor with the
+    primitives reads and writes what the primitive pass does, plus the 7 y
+    fluxes."""
     szu, sze, szr = SIZES[prec]
     u = 4 * szu + 4 * sze          # rho, M (TU) and e, B faces (TE)
     emf = (9 + 6 + 3) * szr        # F_rho and the two E fluxes of 3 axes, v and B_cc, E out
@@ -311,9 +326,13 @@ def group_bytes(prec, n, integ="vl", fused=False, yhalf=False):
         for k in ("predictor_sweeps", "emf1", "half_update"):
             del out[k]
         out["predictor_fused"] = n * (8 * szr + u + 3 * sze + 8 * szr)
-    elif yhalf:
-        out["corrector_yhalf"] = out.pop("half_update") + n * 7 * szr
-        out["corrector_sweeps"] = 2 * n * sweep_bytes_per_face(prec, s2)
+    else:
+        if yhalf:
+            out["corrector_yhalf"] = out.pop("half_update") + n * 7 * szr
+            out["corrector_sweeps"] = 2 * n * sweep_bytes_per_face(prec, s2)
+        if yprim:
+            out["predictor_yprim"] = out.pop("prim_cfl") + n * 7 * szr
+            out["predictor_sweeps"] = 2 * n * sweep_bytes_per_face(prec, s1)
     return out
 
 
@@ -322,7 +341,8 @@ def group_bytes(prec, n, integ="vl", fused=False, yhalf=False):
 STATE_BYTES = {"fp64": 128, "fp32": 64, "mixed": 96}
 
 
-def step_roofline(prec, n, ms_per_step, pk, apk, scheme, flops_per_cell=None, fused=False, yhalf=False):
+def step_roofline(prec, n, ms_per_step, pk, apk, scheme, flops_per_cell=None, fused=False, yhalf=False,
+                  yprim=False):
     """The whole step against its two ceilings, both from the method, not
     from this implementation's kernel split: HBM (the state read once and
     written once: 64 / 96 / 128 B per cell-update) and the arithmetic pipe
@@ -337,7 +357,7 @@ def step_roofline(prec, n, ms_per_step, pk, apk, scheme, flops_per_cell=None, fu
     alu_peak = alu_peak_of(prec, apk)
     alu_ceil = alu_peak * 1e12 / fl
     bound = "alu" if alu_ceil < hbm_ceil else "hbm"
-    design = sum(group_bytes(prec, n, scheme[0], fused, yhalf).values()) / n
+    design = sum(group_bytes(prec, n, scheme[0], fused, yhalf, yprim).values()) / n
     return {"bound": bound, "frac": cups / min(alu_ceil, hbm_ceil),
             "hbm": {"bytes_per_cell_update": STATE_BYTES[prec], "ceiling_cell_updates_per_s": hbm_ceil,
                     "frac": cups / hbm_ceil, "peak_gbs": pk["hbm_gbs"], "peak_src": pk["src"]},
@@ -368,7 +388,8 @@ def scheme_matrix(torch, mhd, st, steps_fp32, steps_fp64, stream, pk, apk):
                         "value": v, "ms_per_step": ms / k, "steps": k, "sweep": s.tuned,
                         "step_roofline": step_roofline(prec, n, ms / k, pk, apk, (integ, recon, riem),
                                                        fused=is_fused(s.tuned, integ),
-                                                       yhalf=is_yhalf(s.tuned, integ, recon))}
+                                                       yhalf=is_yhalf(s.tuned, integ, recon),
+                                                       yprim=is_yprim(s.tuned, integ))}
     return out
 
 
@@ -419,10 +440,19 @@ def roofline(prec, groups, steps, n, pk, apk, scheme, tuned=None):
     sweep = dom.split("_")[0]
     alu_peak = alu_peak_of(prec, apk)
     yh = is_yhalf(tuned, integ, scheme[1])
-    if dom == "corrector_yhalf":
+    yp = is_yprim(tuned, integ)
+    if dom == "predictor_yprim":
+        # per cell: its primitives and signal speed and its first-order y face
+        bpu = group_bytes(prec, n, integ, False, yh, True)[dom] / n
+        fpu = af["per_cell"]["prim_cfl"] + af["per_face"]["predictor"]
+        unit_name = "cells"
+        tpf = TRAFFIC_PER_FACE.get(dom, {}).get(prec)
+        traffic = tpf * n if tpf else None
+        executed = None
+    elif dom == "corrector_yhalf":
         # per cell: its half-step state and its y face (PLM reconstruction
         # and Riemann solve)
-        bpu = group_bytes(prec, n, integ, False, True)[dom] / n
+        bpu = group_bytes(prec, n, integ, False, True, yp)[dom] / n
         fpu = af["per_cell"]["half_update"] + af["per_face"]["corrector"]
         unit_name = "cells"
         tpf = TRAFFIC_PER_FACE.get(dom, {}).get(prec)
@@ -444,7 +474,7 @@ def roofline(prec, groups, steps, n, pk, apk, scheme, tuned=None):
         executed = EXEC_FLOPS_PER_FACE.get(sweep) if prec != "fp64" else None
     else:
         stage = dom
-        bpu = group_bytes(prec, n, integ, is_fused(tuned, integ), yh)[stage] / launches / n
+        bpu = group_bytes(prec, n, integ, is_fused(tuned, integ), yh, yp)[stage] / launches / n
         fpu = af["per_cell"].get(stage, 0.0)
         unit_name = "cells"
         traffic, executed = None, None
@@ -715,7 +745,7 @@ def learned_variant(torch, mhd, K, stream, pk, apk):
         groups, rec = s.profile_end()
         if name != "selected":            # the plain schemes' own sweep configuration
             groups = fold_groups(groups, {"pencil_mask": s.sweep_pencils()[0]}, "vl",
-                                 (LRN.CHEAP if name == "cheap" else LRN.FULL)[1])
+                                 (LRN.CHEAP if name == "cheap" else LRN.FULL)[1], LRN.PFLOOR)
         if name == "selected":
             out["cheap_fraction_blocks"], out["cheap_fraction_tiles"] = s.selector_stats()
         s.get_state(U, B)
@@ -1011,7 +1041,8 @@ def main():
         "roofline": roofline(args.precision, groups, rec, n, pk, apk, scheme, s.tuned) if rec else None,
         "step_roofline": step_roofline(args.precision, n, ms / args.steps, pk, apk, scheme,
                                        fused=is_fused(s.tuned, scheme[0]),
-                                       yhalf=is_yhalf(s.tuned, scheme[0], scheme[1])),
+                                       yhalf=is_yhalf(s.tuned, scheme[0], scheme[1]),
+                                       yprim=is_yprim(s.tuned, scheme[0])),
         "alu_peaks_tflops": apk,
         "kernel_ms_per_step": {k: v / rec for k, v in stages_of(groups).items()} if rec else None,
         "sweep_ms_per_step": {k: v / rec for k, v in groups.items() if "_" in k and k.split("_")[1] in AXES}
@@ -1033,7 +1064,8 @@ def main():
                               if recv else None,
                               "step_roofline": step_roofline(prec, n, msv / kv, pk, apk, scheme,
                                                              fused=is_fused(sv.tuned, scheme[0]),
-                                                             yhalf=is_yhalf(sv.tuned, scheme[0], scheme[1])),
+                                                             yhalf=is_yhalf(sv.tuned, scheme[0], scheme[1]),
+                                                             yprim=is_yprim(sv.tuned, scheme[0])),
                               "kernel_ms_per_step": {k: v / recv for k, v in stages_of(gv).items()} if recv else None,
                               "sweep": sv.tuned}
         if not args.no_matrix:

@@ -297,13 +297,19 @@ static mhd_status init_common(int nbox, const mhd_grid* grids, double gamma, con
     // pencils (bit 7; 256^3 FP32 Roe: 0.708 ms against 0.439 + 0.475 for the
     // two kernels, mixed 1.90 against 1.46 + 0.49); FP64 keeps the two (its
     // corrector is bound by the FP64 pipe: 30.8 against 2.8 + 27.5 ms).  The
-    // autotuner may change the mask.
+    // mixed form also forms the t^n primitives inside the y predictor pencils
+    // (bit 8; 256^3 PLM + Roe: 0.718 ms against 0.644 + 0.307, whose FP64
+    // per-cell arithmetic then overlaps the sweep's); in FP32 and FP64 that
+    // ties the two kernels (0.451 against 0.179 + 0.267 ms; 20.2 against
+    // 5.4 + 14.8 ms).  The autotuner may change the mask.
     if (scheme->integrator != MHD_VL)
         c->pencil_mask = 39;
     else if (scheme->precision == MHD_FP64)
         c->pencil_mask = 23;
-    else
+    else if (scheme->precision == MHD_FP32)
         c->pencil_mask = scheme->recon != MHD_PPM ? 231 : 103;   // PLM: the half update in the y corrector
+    else
+        c->pencil_mask = scheme->recon != MHD_PPM ? 487 : 359;   // mixed: and the primitives in the y predictor
     c->pencil_len = 32;
     c->cell_grid = (int)(vb < 16LL * c->nsm ? vb : 16LL * c->nsm);
     if (c->cell_grid < 1) c->cell_grid = 1;
@@ -736,7 +742,8 @@ static void count_launches(mhd_ctx* c)
     }
     // (CTU: one stage-1 outer-face pass per outflow axis; the stage-2 ones
     // are part of the corrections)
-    int n = fused_predictor(c) ? 8 : (y_half(c) ? 11 : 12);   // (the y corrector takes the half update)
+    // (the y corrector takes the half update, the y predictor the primitives)
+    int n = fused_predictor(c) ? 8 : 12 - (y_half(c) ? 1 : 0) - (y_prim(c) ? 1 : 0);
     if (emf_form(c) == 2) n -= fused_predictor(c) ? 1 : 2;   // each edge-field kernel takes its update
     const int per_axis = c->sch.integrator == MHD_VL ? 2 : 1;
     for (int d = 0; d < 3; d++) n += per_axis * (c->bc >> d & 1) + (c->fix_nl[d] > 0);
@@ -842,8 +849,8 @@ extern "C" mhd_status mhd_get_boundary(mhd_ctx* c, int* outflow_mask)
 extern "C" mhd_status mhd_set_sweep_pencils(mhd_ctx* c, int pencil_mask, int pencil_len)
 {
     if (!c) return MHD_EINVAL;
-    if (pencil_mask < 0 || pencil_mask > 255 || pencil_len < 1 || pencil_len > 1024)
-        return fail(c, MHD_EINVAL, "pencil_mask must be in [0, 255] and pencil_len in [1, 1024]");
+    if (pencil_mask < 0 || pencil_mask > 511 || pencil_len < 1 || pencil_len > 1024)
+        return fail(c, MHD_EINVAL, "pencil_mask must be in [0, 511] and pencil_len in [1, 1024]");
     if ((pencil_mask & 128) && ensure_f2(c) != cudaSuccess)
         return fail(c, MHD_ENOMEM, "second flux array for the fused y corrector");
     c->pencil_mask = pencil_mask;
@@ -952,12 +959,22 @@ extern "C" mhd_status mhd_autotune(mhd_ctx* c, int reps, int* tile_len, int* blo
         // (CTU: also with the x tracing by aligned marching warps, bit 5)
         // (VL, periodic, no selector: also with the half update fused into
         // the y corrector pencils, bit 7, when its flux array can be had)
-        const int vl_masks[9] = {7, 6, 23, 103, 15, 31, 111, 151, 231}, ctu_masks[3] = {7, 6, 39};
+        // (VL, periodic, no selector: also with the primitives inside the y
+        // predictor pencils, bit 8, and for PLM with the half update inside
+        // the y corrector pencils, bit 7, when its flux array can be had)
+        int vl_masks[10] = {7, 6, 23, 103, 15, 31, 111, 359, 0, 0};
+        const int ctu_masks[3] = {7, 6, 39};
         const bool ctu = c->sch.integrator != MHD_VL;
         const int* masks = ctu ? ctu_masks : vl_masks;
         const int lens[3] = {8, 16, 32};
-        const bool yh = c->sch.recon != MHD_PPM && ensure_f2(c) == cudaSuccess;
-        const int nmask = ctu ? 3 : (c->sel ? 2 : (!c->bc ? (yh ? 9 : 7) : 4));
+        int nvl = 8;
+        if (c->sch.recon != MHD_PPM && !c->sel && !c->bc && ensure_f2(c) == cudaSuccess) {
+            vl_masks[7] = 151;
+            vl_masks[8] = 231;
+            vl_masks[9] = 487;
+            nvl = 10;
+        }
+        const int nmask = ctu ? 3 : (c->sel ? 2 : (!c->bc ? nvl : 4));
         c->sweep_bps = bbps;
         for (int i = 0; i < nmask && st == MHD_OK; i++)
             for (int j = 0; j < 3 && st == MHD_OK; j++) {

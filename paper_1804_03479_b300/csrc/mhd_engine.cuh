@@ -297,6 +297,15 @@ inline bool y_half(const mhd_ctx* c)
            !c->sel && c->F2 && !fused_predictor(c) && emf_form(c) == 0;
 }
 
+// the t^n primitives and CFL signal speeds inside the VL predictor's y
+// pencils (k_yprim) with pencil-mask bits 1 and 8: periodic boxes without a
+// learned selector or a pressure floor, bit 3 clear
+inline bool y_prim(const mhd_ctx* c)
+{
+    return (c->pencil_mask & 258) == 258 && c->sch.integrator == MHD_VL && !c->bc && !c->sel &&
+           !(c->sch.pfloor > 0.0) && !fused_predictor(c);
+}
+
 template <class R, class TU, class TE, int RECON, int SOLVER>
 void launch_yhalf(mhd_ctx* c, const Boxes& g, const StateP<TU, TE>& s, const R* F, const R* E, TE* const Bh[3],
                   R* Wh, R* Fc, cudaStream_t st)
@@ -408,8 +417,14 @@ void run_step(mhd_ctx* c, bool device_dt)
     const double gam = c->gamma;
     const size_t smem = sweep_smem_bytes<R>(RECON, g.tl);
 
+    // VL with pencil-mask bit 8: the primitives inside the y predictor (its
+    // time goes to the primitive group)
+    const bool yp = INTEG == VL && y_prim(c);
     prof_mark(c, 0);
-    if (c->bc)
+    if (yp)
+        k_yprim<R, TU, TE, SOLVER><<<pencil_grid(c, 1), PENCIL_THREADS, 0, st>>>(
+            g, s, W, gam, device_dt ? c->smax_part : nullptr, c->bad, F1 + 7 * n);
+    else if (c->bc)
         k_prim<R, TU, TE, true><<<nb, CELL_THREADS, 0, st>>>(g, s, W, gam, device_dt ? c->smax_part : nullptr,
                                                              c->bad, c->sch.pfloor, c->nfloor);
     else if constexpr (sizeof(TU) == 4 && sizeof(TE) == 4)
@@ -432,7 +447,9 @@ void run_step(mhd_ctx* c, bool device_dt)
         } else {
             // VL steps 1-3: first-order fluxes with the face B_n, edge E, half update
             for (int d = 0; d < 3; d++) {
-                if (d == 0 && x_pencils(c))
+                if (d == 1 && yp)
+                    ;                                   // done with the primitives
+                else if (d == 0 && x_pencils(c))
                     launch_xpencil<R, RECON, SOLVER, 0, TE>(c, g, W, s.b[0], F1, st);
                 else if (d == 0 && x_march<RECON, 0>(c))
                     launch_xmarch<R, RECON, SOLVER, 0, TE>(c, g, W, s.b[0], F1, st);

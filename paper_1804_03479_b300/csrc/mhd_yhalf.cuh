@@ -1,4 +1,6 @@
-// mhd_yhalf.cuh -- the VL half update (Sec. 3.2, VL step 3: B^{n+1/2} by
+// mhd_yhalf.cuh -- per-cell passes inside the y pencils of the VL step.
+//
+// k_yhalf: the VL half update (Sec. 3.2, VL step 3: B^{n+1/2} by
 // Eq. 13 and U^{n+1/2} by Eq. 10 with dt/2, and their primitives, Eq. 5)
 // computed inside the corrector's y pencils (VL steps 4-5 along y: PLM
 // reconstruction of the half-step state and the Riemann fluxes).
@@ -29,6 +31,16 @@
 // update read it.
 //
 // Periodic boxes (one or a batch), PLM reconstructions.
+//
+// k_yprim: the primitives at t^n (Eq. 5, with the cell-centred field the
+// mean of the two faces) and the CFL signal speeds (Sec. 3.2) inside the
+// first-order y predictor pencils, by the same reasoning: each thread forms
+// the primitives of its segment's cells and of the one lead-in cell, stores
+// those of its own cells (the x and z predictors and the predictor's edge
+// fields read them), folds their signal speeds into the box's maximum and
+// solves its y faces.  Periodic boxes without a pressure floor (a floored
+// cell's energy is raised in place by its owner while a neighbouring
+// segment's lead-in may be reading it).
 #pragma once
 #include "mhd_kernels.cuh"
 
@@ -182,6 +194,101 @@ k_yhalf(Boxes B, StateP<TU, TE> s, const R* __restrict__ Fp, const R* __restrict
         copy7(wb, wc); bnb = bnc; lb = lc;
     }
     (void)bna;
+}
+
+// the primitives of one cell (Eq. 5) from rho, M, e and twice its
+// cell-centred field, as k_prim forms them
+template <class R, class TU, class TE>
+__device__ __forceinline__ void cell_prims(TU rho, TU mx, TU my, TU mz, TE e, TE sx, TE sy, TE sz, double gam,
+                                           R w[8])
+{
+    const TU irho = TU(1) / rho;
+    const TU vx = mx * irho, vy = my * irho, vz = mz * irho;
+    const TE p = cell_pressure<TU, TE>(rho, irho, mx, my, mz, vx, vy, vz, e, sx, sy, sz, gam);
+    w[0] = R(rho); w[1] = R(vx); w[2] = R(vy); w[3] = R(vz); w[4] = narrow<R>(p);
+    w[5] = R(0.5) * narrow<R>(sx); w[6] = R(0.5) * narrow<R>(sy); w[7] = R(0.5) * narrow<R>(sz);
+}
+
+template <class R, class TU, class TE, int SOLVER>
+__global__ void __launch_bounds__(PENCIL_THREADS, (sweep_min_blocks<R, PLM, SOLVER, 0>()))
+k_yprim(Boxes B, StateP<TU, TE> s, R* __restrict__ W, double gam, unsigned long long* __restrict__ smax_acc,
+        unsigned long long* __restrict__ bad_cell, R* __restrict__ Fy)
+{
+    const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const bool live = gt < B.npth[1];      // the live threads are a prefix of each warp
+    int bi = -1;
+    double smax = 0.0;
+    if (live) {
+        bi = box_of_pth(B, 1, gt);
+        const BoxDev g = B.b[bi];
+        int na, nb, ns;
+        pencil_dims(g.nx, g.ny, g.nz, 1, B.pl, na, nb, ns);
+        long long t = gt - g.pth0[1];
+        const int ix = (int)(t % na);
+        t /= na;
+        const int iz = (int)(t % nb);
+        const int sg = (int)(t / nb);
+        const long long N = B.N;
+        const int nx = g.nx, ny = g.ny;
+        const long long plane = (long long)nx * ny;
+        const long long base = g.off + (long long)iz * plane + ix;
+        const long long ox = ix + 1 < nx ? 1 : 1 - nx;
+        const long long oz = iz + 1 < g.nz ? plane : plane - (long long)g.nz * plane;
+        const int i0 = sg * B.pl;
+        const int i1 = i0 + B.pl < ny ? i0 + B.pl : ny;
+        const R gr = R(gam), gm1 = R(gam - 1.0);
+        // the lower y face of the walk's next cell (the upper face of the one before)
+        TE by = s.b[1][base + (long long)wrapi(i0 - 1, ny) * nx];
+        // the primitives of line cell i in the y sweep frame (as load_rot with
+        // d = 1), its lower y face in fb; stored, checked and counted in the
+        // CFL maximum when the segment owns the cell
+        auto prim_cell = [&](int i, R w[7], TE& fb) {
+            const long long c = base + (long long)wrapi(i, ny) * nx;
+            const long long cy = base + (long long)wrapi(i + 1, ny) * nx;
+            const TE byu = s.b[1][cy];
+            const TE sx = s.b[0][c] + s.b[0][c + ox];
+            const TE sy = by + byu;
+            const TE sz = s.b[2][c] + s.b[2][c + oz];
+            R w8[8];
+            cell_prims<R, TU, TE>(s.rho[c], s.m[0][c], s.m[1][c], s.m[2][c], s.e[c], sx, sy, sz, gam, w8);
+            if (i >= i0 && i < i1) {
+#pragma unroll
+                for (int f = 0; f < 8; f++) W[f * N + c] = w8[f];
+                if (!(w8[0] > R(0)) || !(w8[4] > R(0))) atomicMin(bad_cell, (unsigned long long)c);
+                if (smax_acc) smax = fmax(smax, (double)cell_signal(w8, gam));
+            }
+            w[0] = w8[0]; w[1] = w8[2]; w[2] = w8[3]; w[3] = w8[1];
+            w[4] = w8[4]; w[5] = w8[7]; w[6] = w8[5];
+            fb = by;
+            by = byu;
+        };
+        // first-order states: face i sees cells i - 1 and i
+        R wl[7], wr[7], f[7];
+        TE fdum, fb;
+        prim_cell(i0 - 1, wl, fdum);
+        for (int i = i0; i < i1; i++) {
+            prim_cell(i, wr, fb);
+            riemann<SOLVER>(wl, wr, R(fb), gm1, gr, f);
+            const long long ci = base + (long long)i * nx;
+#pragma unroll
+            for (int m = 0; m < 7; m++) Fy[(long long)m * N + ci] = f[m];
+            copy7(wl, wr);
+        }
+    }
+    if (!smax_acc) return;
+    // the warp's maximum into its box's accumulator (the bits of a double
+    // >= 0 order as its value); a warp across two boxes folds lane by lane
+    const int b0 = __shfl_sync(0xffffffffu, bi, 0);
+    if (__all_sync(0xffffffffu, !live || bi == b0)) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+        if (!(smax > 0.0)) smax = 0.0;
+        if ((threadIdx.x & 31) == 0 && b0 >= 0)
+            atomicMax(smax_acc + b0, (unsigned long long)__double_as_longlong(smax));
+    } else if (live) {
+        if (!(smax > 0.0)) smax = 0.0;
+        atomicMax(smax_acc + bi, (unsigned long long)__double_as_longlong(smax));
+    }
 }
 
 }  // namespace mhd

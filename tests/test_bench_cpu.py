@@ -162,3 +162,29 @@ def test_roofline_of_the_y_corrector_with_the_half_update():
     gb = bench.group_bytes("fp32", n, "vl", False, True)
     assert "half_update" not in gb and gb["corrector_sweeps"] == 2 * n * 64
     assert sum(gb.values()) == sum(bench.group_bytes("fp32", n, "vl").values()) - n * 64 + n * 28
+
+
+def test_folding_of_the_y_predictor_with_the_primitives():
+    """pencil-mask bit 8 (with bit 1, no bit 3, no pressure floor): the
+    primitive group times the y predictor that forms the primitives and the
+    y predictor group is empty; with bit 7 as well both fold"""
+    import bench
+    n = 256 ** 3
+    groups = {"prim_cfl": 7.2, "predictor_x": 2.7, "predictor_y": 0.01, "predictor_z": 2.7, "emf1": 2.9,
+              "half_update": 19.0, "corrector_x": 5.1, "corrector_y": 0.01, "corrector_z": 4.7, "emf2": 3.0,
+              "full_update": 5.7}
+    assert bench.is_yprim({"pencil_mask": 487}) and not bench.is_yprim({"pencil_mask": 487}, "vl", 1e-4)
+    assert not bench.is_yprim({"pencil_mask": 231}) and not bench.is_yprim({"pencil_mask": 487}, "ctu")
+    g = bench.fold_groups(groups, {"pencil_mask": 487}, "vl", "plm")
+    assert set(g) == {"predictor_yprim", "predictor_x", "predictor_z", "emf1", "corrector_yhalf", "corrector_x",
+                      "corrector_z", "emf2", "full_update"}
+    assert g["predictor_yprim"] == pytest.approx(7.21) and g["corrector_yhalf"] == pytest.approx(19.01)
+    g2 = bench.fold_groups(groups, {"pencil_mask": 359}, "vl", "ppm")
+    assert "predictor_yprim" in g2 and "half_update" in g2 and "corrector_y" in g2
+    r = bench.roofline("mixed", g, 10, n, {"hbm_gbs": 6491.2, "src": "measured"},
+                       {"fp32": 75.0, "fp64": 1.0, "src": "test"}, ("vl", "plm", "roe"), {"pencil_mask": 487})
+    assert r["kernel"] == "corrector_yhalf"
+    gb = bench.group_bytes("mixed", n, "vl", False, True, True)
+    szu, sze, szr = bench.SIZES["mixed"]
+    assert gb["predictor_yprim"] == n * (4 * szu + 4 * sze + 8 * szr + 7 * szr)
+    assert gb["predictor_sweeps"] == 2 * n * bench.sweep_bytes_per_face("mixed", "vl")

@@ -130,7 +130,7 @@ def test_pencil_arguments(M):
     st = I.abc(8, kmult=1, beta=1.0)
     s = M.Solver(st.U.shape[1:], st.dx, st.gamma, "vl", "plm", "roe", "fp64", 0.3)
     try:
-        for mask, plen in [(256, 16), (-1, 16), (7, 0), (7, 2000)]:
+        for mask, plen in [(512, 16), (-1, 16), (7, 0), (7, 2000)]:
             with pytest.raises(M.MHDError):
                 s.set_sweep_pencils(mask, plen)
             lib = M.lib()

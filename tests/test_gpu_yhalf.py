@@ -1,4 +1,12 @@
-"""The VL half update fused into the corrector's y pencils (k_yhalf;
+"""Per-cell passes inside the VL step's y pencils.
+
+The primitives at t^n and the CFL signal speeds inside the first-order y
+predictor pencils (k_yprim; pencil-mask bit 8 with bit 1): each pencil
+thread forms the primitives of its segment's cells and one lead-in cell,
+stores its own cells', folds their signal speeds into the box maximum
+(device dt) and solves its y faces.
+
+The VL half update fused into the corrector's y pencils (k_yhalf;
 pencil-mask bit 7 with bit 1): each pencil thread forms the half-step state
 (Sec. 3.2 VL step 3: Eq. 13 for the faces, Eq. 10 with dt/2 for the cells,
 Eq. 5 for the primitives) of every cell its PLM walk reconstructs, stores
@@ -26,6 +34,7 @@ pytestmark = pytest.mark.gpu
 
 PLM = [("vl", r, s) for r in ("plm", "plm_prim") for s in ("roe", "hlld", "hlle")]
 FUSED64, FUSED32 = 23 | 128, 103 | 128     # the precision defaults with bit 7
+PRIM = 256                                   # bit 8
 
 
 @pytest.fixture(scope="module")
@@ -38,17 +47,27 @@ def M():
     return mhd
 
 
-def parity(M, st, scheme, nsteps, mask=FUSED64, plen=32, pfloor=0.0, tol=1e-12):
+def parity(M, st, scheme, nsteps, mask=FUSED64, plen=32, pfloor=0.0, tol=1e-12, device_dt=False):
+    """FP64 steps against the oracle from the same state; with device_dt
+    the library's own CFL dt (the signal speeds of the primitive pass), held
+    to 1e-14 of the oracle's"""
     U, B = st.U.copy(), st.B.copy()
     s = M.Solver(U.shape[1:], st.dx, st.gamma, *scheme, "fp64", 0.3, pfloor=pfloor)
     try:
         s.set_sweep_pencils(mask, plen)
-        assert s.launches_per_step() == 11          # no separate half update
+        fused = (mask & 128 and scheme[1] != "ppm") + (mask & PRIM and not pfloor)
+        assert s.launches_per_step() == 12 - fused
         for it in range(nsteps):
             s.set_state(U, B)
             dt = orc.cfl_dt(U, B, st.dx, st.gamma, 0.3, pfloor=pfloor) if pfloor else \
                 orc.cfl_dt(U, B, st.dx, st.gamma, 0.3)
-            s.step(dt)
+            if device_dt:
+                s.advance(1)
+                dtg = s.last_dt()
+                assert abs(dtg - dt) <= 1e-14 * dt, (dtg, dt)
+                dt = dtg
+            else:
+                s.step(dt)
             if pfloor:
                 orc.step_floor(U, B, st.dx, st.gamma, dt, *scheme, pfloor=pfloor)
             else:
@@ -63,6 +82,77 @@ def parity(M, st, scheme, nsteps, mask=FUSED64, plen=32, pfloor=0.0, tol=1e-12):
             for d in range(3):
                 den = np.abs(B[d]).sum()
                 assert np.abs(Bg[d] - B[d]).sum() / (den if den > 0 else 1.0) <= tol, (scheme, it, d)
+    finally:
+        s.free()
+
+
+VL = [("vl", r, s) for r in ("plm", "ppm", "plm_prim") for s in ("roe", "hlld", "hlle")]
+
+
+@pytest.mark.parametrize("scheme", VL)
+def test_yprim_fp64_parity_device_dt(M, scheme):
+    """bit 8 alone and with bit 7 (PLM): the device dt from the pencils'
+    signal speeds and the whole step against the oracle"""
+    st = I.abc(None, kmult=1, beta=0.5, seed=86, noise=2e-2, shape=(10, 64, 12))
+    parity(M, st, scheme, 2, mask=23 | PRIM, device_dt=True)
+    if scheme[1] != "ppm":
+        parity(M, st, scheme, 2, mask=23 | PRIM | 128, device_dt=True)
+
+
+@pytest.mark.parametrize("shape", [(8, 40, 12), (6, 33, 9), (5, 2, 9), (9, 1, 7), (3, 3, 1)])
+@pytest.mark.parametrize("plen", [1, 3, 32])
+def test_yprim_fp64_parity_ragged_short(M, shape, plen):
+    L = max(shape[1], 1) / 16.0
+    st = I.abc(None, kmult=L, beta=0.5, seed=87, noise=3e-2, shape=shape, L=L)
+    parity(M, st, ("vl", "plm", "roe"), 2, mask=23 | PRIM | 128, plen=plen, device_dt=True)
+
+
+def test_yprim_fp64_batch_device_dt(M):
+    """uneven boxes: each box's dt from its own signal-speed maximum, warps
+    whose lanes run from one box into the next"""
+    shapes = [(5, 16, 3), (3, 33, 7), (5, 40, 5), (3, 70, 3), (2, 5, 1)]
+    boxes = [I.abc(None, kmult=1, beta=0.5, seed=95 + k, noise=3e-2, shape=sh) for k, sh in enumerate(shapes)]
+    scheme = ("vl", "plm", "hlld")
+    s = M.Solver(None, None, 5 / 3, *scheme, "fp64", 0.3,
+                 shapes=[b.U.shape[1:] for b in boxes], dxs=[b.dx for b in boxes])
+    try:
+        s.set_sweep_pencils(23 | PRIM | 128, 8)
+        for k, b in enumerate(boxes):
+            s.set_state(b.U, b.B, box=k)
+        s.advance(1)
+        dts = s.last_dts()
+        for k, b in enumerate(boxes):
+            dto = orc.cfl_dt(b.U, b.B, b.dx, b.gamma, 0.3)
+            assert abs(dts[k] - dto) <= 1e-14 * dto, (k, dts[k], dto)
+            U, B = b.U.copy(), b.B.copy()
+            orc.step(U, B, b.dx, b.gamma, float(dts[k]), *scheme)
+            Ug, Bg = s.get_state(box=k)
+            mfloor = 1e-2 * np.abs(U[0]).sum()
+            for f in range(5):
+                den = max(np.abs(U[f]).sum(), mfloor if f in (1, 2, 3) else 0.0)
+                assert np.abs(Ug[f] - U[f]).sum() / den <= 1e-12, (k, f)
+            bfloor = 1e-2 * np.abs(B).sum() / 3
+            for d in range(3):
+                assert np.abs(Bg[d] - B[d]).sum() / max(np.abs(B[d]).sum(), bfloor) <= 1e-12, (k, d)
+    finally:
+        s.free()
+
+
+def test_yprim_reports_a_negative_pressure(M):
+    """the anomaly record (MHD_ENEGATIVE with the first bad cell) from the
+    fused primitive pass"""
+    st = I.abc(16, kmult=1, beta=0.5, seed=88)
+    U, B = st.U.copy(), st.B.copy()
+    U[4, 3, 5, 7] = -1.0                               # energy below the magnetic and kinetic parts
+    s = M.Solver(U.shape[1:], st.dx, st.gamma, "vl", "plm", "roe", "fp64", 0.3)
+    try:
+        s.set_sweep_pencils(23 | PRIM, 32)
+        s.set_state(U, B)
+        s.advance(1)
+        with pytest.raises(M.MHDError) as ei:
+            s.sync()
+        assert ei.value.status == M.MHD_ENEGATIVE
+        assert s.bad_cell() == (3 * 16 + 5) * 16 + 7
     finally:
         s.free()
 
@@ -97,8 +187,8 @@ def agree(M, st, prec, scheme, nsteps, pfloor=0.0):
     relative L1 of the difference; returns the two floor counts"""
     cast = np.float32 if prec == "fp32" else np.float64
     base = 23 if prec == "fp64" else 103
-    out, floors = [], []
-    for mask in (base, base | 128):
+    out, floors, dts = [], [], []
+    for mask in (base, base | 128 | (0 if pfloor else PRIM)):
         s = M.Solver(st.U.shape[1:], st.dx, st.gamma, *scheme, prec, 0.3, pfloor=pfloor)
         try:
             s.set_sweep_pencils(mask, 32)
@@ -106,10 +196,12 @@ def agree(M, st, prec, scheme, nsteps, pfloor=0.0):
             s.advance(nsteps, use_graph=True)
             out.append(s.get_state())
             floors.append(s.floor_count())
+            dts.append(s.last_dt())
         finally:
             s.free()
     (Ua, Ba), (Ub, Bb) = out
     tol = 1e-12 if prec == "fp64" else 1e-5
+    assert abs(dts[0] - dts[1]) <= (1e-14 if prec == "fp64" else 1e-6) * dts[0], dts
     for f in range(5):
         a, b = Ua[f].astype(np.float64), Ub[f].astype(np.float64)
         den = max(np.abs(b).sum(), 1e-2 * np.abs(Ub[0]).sum() if f in (1, 2, 3) else 0.0)
@@ -168,39 +260,47 @@ def test_yhalf_agrees_with_separate_kernels(M, prec, scheme):
     agree(M, st, prec, scheme, 3)
 
 
-def test_yhalf_mask_range_and_fallbacks(M):
-    """bit 7 is accepted up to 255 and is the FP32 / mixed PLM default; with
-    PPM, outflow boundaries or without bit 1 the separate half update runs
-    (12 launches)"""
+def test_mask_range_defaults_and_fallbacks(M):
+    """bits 7 and 8 are accepted up to 511; bit 7 is the FP32 PLM default,
+    bits 7 and 8 the mixed PLM default, bit 8 the mixed PPM default; with
+    PPM (bit 7), a pressure floor (bit 8), outflow boundaries or without
+    bit 1 the separate kernels run"""
     st = I.abc(16, kmult=1, beta=0.5, seed=85)
-    for prec, recon, mask in [("fp32", "plm", FUSED32), ("mixed", "plm_prim", FUSED32), ("fp64", "plm", 23),
-                              ("fp32", "ppm", 103)]:
+    for prec, recon, mask, nl in [("fp32", "plm", FUSED32, 11), ("fp32", "ppm", 103, 12),
+                                  ("mixed", "plm_prim", FUSED32 | PRIM, 10), ("mixed", "ppm", 103 | PRIM, 11),
+                                  ("fp64", "plm", 23, 12)]:
         s = M.Solver(st.U.shape[1:], st.dx, st.gamma, "vl", recon, "roe", prec, 0.3)
         try:
             assert s.sweep_pencils() == (mask, 32), (prec, recon)
-            assert s.launches_per_step() == (11 if mask & 128 else 12), (prec, recon)
+            assert s.launches_per_step() == nl, (prec, recon)
         finally:
             s.free()
     s = M.Solver(st.U.shape[1:], st.dx, st.gamma, "vl", "plm", "roe", "fp32", 0.3)
     try:
-        s.set_sweep_pencils(255, 32)
-        assert s.sweep_pencils() == (255, 32)
+        s.set_sweep_pencils(511, 32)
+        assert s.sweep_pencils() == (511, 32)
         assert s.launches_per_step() == 8          # bit 3, the fused predictor, takes precedence
-        s.set_sweep_pencils(FUSED32, 32)
-        assert s.launches_per_step() == 11
-        s.set_sweep_pencils(FUSED32 & ~2, 32)      # y by tiles: no fused y corrector
+        s.set_sweep_pencils(FUSED32 | PRIM, 32)
+        assert s.launches_per_step() == 10
+        s.set_sweep_pencils((FUSED32 | PRIM) & ~2, 32)   # y by tiles: neither y pencil takes a pass
         assert s.launches_per_step() == 12
         with pytest.raises(M.MHDError):
-            s.set_sweep_pencils(256, 32)
+            s.set_sweep_pencils(512, 32)
         M.lib().mhd_clear_error(s.h)
-        s.set_sweep_pencils(FUSED32, 32)
+        s.set_sweep_pencils(FUSED32 | PRIM, 32)
         s.set_boundary(2)                          # outflow y
         assert s.launches_per_step() == 12 + 2
     finally:
         s.free()
     s = M.Solver(st.U.shape[1:], st.dx, st.gamma, "vl", "ppm", "roe", "fp32", 0.3)
     try:
-        s.set_sweep_pencils(FUSED32, 32)
-        assert s.launches_per_step() == 12
+        s.set_sweep_pencils(FUSED32 | PRIM, 32)
+        assert s.launches_per_step() == 11         # PPM: the primitives only
+    finally:
+        s.free()
+    s = M.Solver(st.U.shape[1:], st.dx, st.gamma, "vl", "plm", "roe", "mixed", 0.3, pfloor=1e-6)
+    try:
+        assert s.sweep_pencils() == (FUSED32 | PRIM, 32)
+        assert s.launches_per_step() == 11         # a pressure floor: the primitive pass of its own
     finally:
         s.free()
