@@ -105,12 +105,14 @@ SIZES = {"fp64": (8, 8, 8), "fp32": (4, 4, 4), "mixed": (4, 8, 4)}   # (rho/M, e
 EXEC_FLOPS_PER_FACE = {"corrector": 670.0, "predictor": 393.0, "tracing": 895.0, "ctucorr": 524.0}
 # DRAM bytes (read + write) per face of one sweep launch, per kernel, from
 # dram__bytes_read.sum + dram__bytes_write.sum of the ncu captures in
-# profiles/ (FP32 at 160^3 for 4,096,000 faces: pencil corrector 234.7 MB,
+# profiles/ (FP32 at 160^3 for 4,096,000 faces: the y corrector with the
+# half update 727.6 MB (one face and one half-step state per cell), pencil corrector 234.7 MB,
 # x-march corrector 225.5 MB, x-warp corrector 225.8 MB, pencil predictor
 # 208.0 MB, staged x-march predictor 204.7 MB), scaled to other sizes by
 # faces.  A kernel changed since its capture has none (CTU tracing and the
 # FP64 forms were re-built since theirs).
-TRAFFIC_PER_FACE = {"corrector_pencil": {"fp32": 57.3}, "corrector_xmarch": {"fp32": 55.0},
+TRAFFIC_PER_FACE = {"corrector_yhalf": {"fp32": 177.6},      # per cell (727.6 MB for 4,096,000 cells)
+                    "corrector_pencil": {"fp32": 57.3}, "corrector_xmarch": {"fp32": 55.0},
                     "predictor_pencil": {"fp32": 50.8}, "predictor_xmarch": {"fp32": 50.0},
                     "corrector_xwarp": {"fp32": 55.1},
                     "ctucorr_pencil": {"fp32": 147.0}, "ctucorr_xwarp": {"fp32": 146.6}}
