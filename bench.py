@@ -38,7 +38,7 @@ PAPER_P100 = {"fp32": 1.2e8, "fp64": 5.5e7}   # Sec. 5.2 (i), Tesla P100, VL + P
 # sweep axis) and their aggregation into the seven stages of the step
 AXES = ("x", "y", "z")
 STAGES = ["prim_cfl", "predictor_yprim", "predictor_fused", "predictor_sweeps", "emf1", "half_update", "corrector_yhalf",
-          "corrector_sweeps", "emf2", "full_update"]
+          "corrector_sweeps", "corrector_zfull", "emf2", "full_update"]
 
 
 def is_fused(tuned, integ="vl"):
@@ -60,6 +60,14 @@ def is_yprim(tuned, integ="vl", pfloor=0.0):
     return integ == "vl" and (m & 258) == 258 and not m & 8 and not pfloor > 0
 
 
+def is_zfull(tuned, integ="vl", recon="plm"):
+    """the conservative full update runs inside the z corrector pencils and
+    the full-update group times the CT kernel (pencil-mask bits 2 and 9, a
+    PLM reconstruction, bit 3 clear; periodic boxes)"""
+    m = (tuned or {}).get("pencil_mask", 0) or 0
+    return integ == "vl" and recon != "ppm" and (m & 516) == 516 and not m & 8
+
+
 def fold_groups(groups, tuned, integ="vl", recon="plm", pfloor=0.0):
     """With the fused VL predictor the library's half-update group times the
     fused kernel, and the predictor-sweep and first edge-field groups are
@@ -67,14 +75,20 @@ def fold_groups(groups, tuned, integ="vl", recon="plm", pfloor=0.0):
     half update inside the y corrector pencils the half-update group times
     that kernel and the y corrector group is empty: corrector_yhalf.  With
     the primitives inside the y predictor pencils the primitive group times
-    that kernel and the y predictor group is empty: predictor_yprim."""
+    that kernel and the y predictor group is empty: predictor_yprim.  With
+    the conservative full update inside the z corrector pencils the z
+    corrector group is corrector_zfull (the full-update group is then CT
+    alone)."""
     yp, yh = is_yprim(tuned, integ, pfloor), is_yhalf(tuned, integ, recon)
-    if yp or yh:
+    zf = is_zfull(tuned, integ, recon)
+    if yp or yh or zf:
         out = dict(groups)
         if yp:
             out["predictor_yprim"] = out.pop("prim_cfl", 0.0) + out.pop("predictor_y", 0.0)
         if yh:
             out["corrector_yhalf"] = out.pop("half_update", 0.0) + out.pop("corrector_y", 0.0)
+        if zf:
+            out["corrector_zfull"] = out.pop("corrector_z", 0.0)
         return out
     if not is_fused(tuned, integ):
         return groups
@@ -307,7 +321,7 @@ def sweep_bytes_per_face(prec, kind="vl"):
             "ctucorr": 29 * szr + sze + 7 * szr}[kind]
 
 
-def group_bytes(prec, n, integ="vl", fused=False, yhalf=False, yprim=False):
+def group_bytes(prec, n, integ="vl", fused=False, yhalf=False, yprim=False, zfull=False):
     """algorithmic HBM bytes of each stage of one step on n cells: every
     array element a kernel needs is read once and every result written once
     (neighbour re-reads assumed to hit in cache).  The fused VL predictor
@@ -315,7 +329,10 @@ def group_bytes(prec, n, integ="vl", fused=False, yhalf=False, yprim=False):
     corrector with the half update reads what the half update reads and
     writes what it writes, plus the 7 y fluxes; the y predictor with the
     primitives reads and writes what the primitive pass does, plus the 7 y
-    fluxes."""
+    fluxes; the z corrector with the conservative update reads W and B_n, rho,
+    M, e and the x and y fluxes' 10 hydrodynamic components and writes rho, M,
+    e and 3 z flux components, and the CT update that follows reads E and B
+    and writes B."""
     szu, sze, szr = SIZES[prec]
     u = 4 * szu + 4 * sze          # rho, M (TU) and e, B faces (TE)
     emf = (9 + 6 + 3) * szr        # F_rho and the two E fluxes of 3 axes, v and B_cc, E out
@@ -335,6 +352,10 @@ def group_bytes(prec, n, integ="vl", fused=False, yhalf=False, yprim=False):
         if yprim:
             out["predictor_yprim"] = out.pop("prim_cfl") + n * 7 * szr
             out["predictor_sweeps"] = 2 * n * sweep_bytes_per_face(prec, s1)
+        if zfull:
+            out["corrector_zfull"] = n * (8 * szr + sze + 3 * szr + 2 * (4 * szu + sze) + 10 * szr)
+            out["corrector_sweeps"] -= n * sweep_bytes_per_face(prec, s2)
+            out["full_update"] = n * (3 * szr + 6 * sze)
     return out
 
 
@@ -344,7 +365,7 @@ STATE_BYTES = {"fp64": 128, "fp32": 64, "mixed": 96}
 
 
 def step_roofline(prec, n, ms_per_step, pk, apk, scheme, flops_per_cell=None, fused=False, yhalf=False,
-                  yprim=False):
+                  yprim=False, zfull=False):
     """The whole step against its two ceilings, both from the method, not
     from this implementation's kernel split: HBM (the state read once and
     written once: 64 / 96 / 128 B per cell-update) and the arithmetic pipe
@@ -359,7 +380,7 @@ def step_roofline(prec, n, ms_per_step, pk, apk, scheme, flops_per_cell=None, fu
     alu_peak = alu_peak_of(prec, apk)
     alu_ceil = alu_peak * 1e12 / fl
     bound = "alu" if alu_ceil < hbm_ceil else "hbm"
-    design = sum(group_bytes(prec, n, scheme[0], fused, yhalf, yprim).values()) / n
+    design = sum(group_bytes(prec, n, scheme[0], fused, yhalf, yprim, zfull).values()) / n
     return {"bound": bound, "frac": cups / min(alu_ceil, hbm_ceil),
             "hbm": {"bytes_per_cell_update": STATE_BYTES[prec], "ceiling_cell_updates_per_s": hbm_ceil,
                     "frac": cups / hbm_ceil, "peak_gbs": pk["hbm_gbs"], "peak_src": pk["src"]},
@@ -391,7 +412,8 @@ def scheme_matrix(torch, mhd, st, steps_fp32, steps_fp64, stream, pk, apk):
                         "step_roofline": step_roofline(prec, n, ms / k, pk, apk, (integ, recon, riem),
                                                        fused=is_fused(s.tuned, integ),
                                                        yhalf=is_yhalf(s.tuned, integ, recon),
-                                                       yprim=is_yprim(s.tuned, integ))}
+                                                       yprim=is_yprim(s.tuned, integ),
+                                                       zfull=is_zfull(s.tuned, integ, recon))}
     return out
 
 
@@ -443,9 +465,19 @@ def roofline(prec, groups, steps, n, pk, apk, scheme, tuned=None):
     alu_peak = alu_peak_of(prec, apk)
     yh = is_yhalf(tuned, integ, scheme[1])
     yp = is_yprim(tuned, integ)
-    if dom == "predictor_yprim":
+    zf = is_zfull(tuned, integ, scheme[1])
+    if dom == "corrector_zfull":
+        # per cell: one corrector face and the conservative update (the
+        # oracle's full-update count, its CT part included)
+        bpu = group_bytes(prec, n, integ, False, yh, yp, True)[dom] / n
+        fpu = af["per_face"]["corrector"] + af["per_cell"]["full_update"]
+        unit_name = "cells"
+        tpf = TRAFFIC_PER_FACE.get(dom, {}).get(prec)
+        traffic = tpf * n if tpf else None
+        executed = None
+    elif dom == "predictor_yprim":
         # per cell: its primitives and signal speed and its first-order y face
-        bpu = group_bytes(prec, n, integ, False, yh, True)[dom] / n
+        bpu = group_bytes(prec, n, integ, False, yh, True, zf)[dom] / n
         fpu = af["per_cell"]["prim_cfl"] + af["per_face"]["predictor"]
         unit_name = "cells"
         tpf = TRAFFIC_PER_FACE.get(dom, {}).get(prec)
@@ -454,7 +486,7 @@ def roofline(prec, groups, steps, n, pk, apk, scheme, tuned=None):
     elif dom == "corrector_yhalf":
         # per cell: its half-step state and its y face (PLM reconstruction
         # and Riemann solve)
-        bpu = group_bytes(prec, n, integ, False, True, yp)[dom] / n
+        bpu = group_bytes(prec, n, integ, False, True, yp, zf)[dom] / n
         fpu = af["per_cell"]["half_update"] + af["per_face"]["corrector"]
         unit_name = "cells"
         tpf = TRAFFIC_PER_FACE.get(dom, {}).get(prec)
@@ -476,7 +508,7 @@ def roofline(prec, groups, steps, n, pk, apk, scheme, tuned=None):
         executed = EXEC_FLOPS_PER_FACE.get(sweep) if prec != "fp64" else None
     else:
         stage = dom
-        bpu = group_bytes(prec, n, integ, is_fused(tuned, integ), yh, yp)[stage] / launches / n
+        bpu = group_bytes(prec, n, integ, is_fused(tuned, integ), yh, yp, zf)[stage] / launches / n
         fpu = af["per_cell"].get(stage, 0.0)
         unit_name = "cells"
         traffic, executed = None, None
@@ -1044,7 +1076,8 @@ def main():
         "step_roofline": step_roofline(args.precision, n, ms / args.steps, pk, apk, scheme,
                                        fused=is_fused(s.tuned, scheme[0]),
                                        yhalf=is_yhalf(s.tuned, scheme[0], scheme[1]),
-                                       yprim=is_yprim(s.tuned, scheme[0])),
+                                       yprim=is_yprim(s.tuned, scheme[0]),
+                                       zfull=is_zfull(s.tuned, scheme[0], scheme[1])),
         "alu_peaks_tflops": apk,
         "kernel_ms_per_step": {k: v / rec for k, v in stages_of(groups).items()} if rec else None,
         "sweep_ms_per_step": {k: v / rec for k, v in groups.items() if "_" in k and k.split("_")[1] in AXES}
@@ -1067,7 +1100,8 @@ def main():
                               "step_roofline": step_roofline(prec, n, msv / kv, pk, apk, scheme,
                                                              fused=is_fused(sv.tuned, scheme[0]),
                                                              yhalf=is_yhalf(sv.tuned, scheme[0], scheme[1]),
-                                                             yprim=is_yprim(sv.tuned, scheme[0])),
+                                                             yprim=is_yprim(sv.tuned, scheme[0]),
+                                                             zfull=is_zfull(sv.tuned, scheme[0], scheme[1])),
                               "kernel_ms_per_step": {k: v / recv for k, v in stages_of(gv).items()} if recv else None,
                               "sweep": sv.tuned}
         if not args.no_matrix:

@@ -301,13 +301,17 @@ static mhd_status init_common(int nbox, const mhd_grid* grids, double gamma, con
     // (bit 8; 256^3 PLM + Roe: 0.718 ms against 0.644 + 0.307, whose FP64
     // per-cell arithmetic then overlaps the sweep's); in FP32 and FP64 that
     // ties the two kernels (0.451 against 0.179 + 0.267 ms; 20.2 against
-    // 5.4 + 14.8 ms).  The autotuner may change the mask.
+    // 5.4 + 14.8 ms).  FP32 PLM also runs the conservative part of the full
+    // update inside the z corrector pencils and the face field by CT alone
+    // (bit 9; 256^3 Roe: z corrector 0.468 -> 0.685 ms, full update 0.412 ->
+    // 0.098, step 3.67 -> 3.58 ms); the mixed form (5.43 -> 5.51 ms) and FP64
+    // (144.0 -> 144.8 ms) lose with it.  The autotuner may change the mask.
     if (scheme->integrator != MHD_VL)
         c->pencil_mask = 39;
     else if (scheme->precision == MHD_FP64)
         c->pencil_mask = 23;
-    else if (scheme->precision == MHD_FP32)
-        c->pencil_mask = scheme->recon != MHD_PPM ? 231 : 103;   // PLM: the half update in the y corrector
+    else if (scheme->precision == MHD_FP32)   // PLM: the half update in the y corrector, the conservative
+        c->pencil_mask = scheme->recon != MHD_PPM ? 743 : 103;   // update in the z corrector
     else
         c->pencil_mask = scheme->recon != MHD_PPM ? 487 : 359;   // mixed: and the primitives in the y predictor
     c->pencil_len = 32;
@@ -849,8 +853,8 @@ extern "C" mhd_status mhd_get_boundary(mhd_ctx* c, int* outflow_mask)
 extern "C" mhd_status mhd_set_sweep_pencils(mhd_ctx* c, int pencil_mask, int pencil_len)
 {
     if (!c) return MHD_EINVAL;
-    if (pencil_mask < 0 || pencil_mask > 511 || pencil_len < 1 || pencil_len > 1024)
-        return fail(c, MHD_EINVAL, "pencil_mask must be in [0, 511] and pencil_len in [1, 1024]");
+    if (pencil_mask < 0 || pencil_mask > 1023 || pencil_len < 1 || pencil_len > 1024)
+        return fail(c, MHD_EINVAL, "pencil_mask must be in [0, 1023] and pencil_len in [1, 1024]");
     if ((pencil_mask & 128) && ensure_f2(c) != cudaSuccess)
         return fail(c, MHD_ENOMEM, "second flux array for the fused y corrector");
     c->pencil_mask = pencil_mask;
@@ -962,7 +966,7 @@ extern "C" mhd_status mhd_autotune(mhd_ctx* c, int reps, int* tile_len, int* blo
         // (VL, periodic, no selector: also with the primitives inside the y
         // predictor pencils, bit 8, and for PLM with the half update inside
         // the y corrector pencils, bit 7, when its flux array can be had)
-        int vl_masks[10] = {7, 6, 23, 103, 15, 31, 111, 359, 0, 0};
+        int vl_masks[12] = {7, 6, 23, 103, 15, 31, 111, 359, 0, 0, 0, 0};
         const int ctu_masks[3] = {7, 6, 39};
         const bool ctu = c->sch.integrator != MHD_VL;
         const int* masks = ctu ? ctu_masks : vl_masks;
@@ -972,7 +976,9 @@ extern "C" mhd_status mhd_autotune(mhd_ctx* c, int reps, int* tile_len, int* blo
             vl_masks[7] = 151;
             vl_masks[8] = 231;
             vl_masks[9] = 487;
-            nvl = 10;
+            vl_masks[10] = 743;            // (bit 9: the conservative update in the z corrector)
+            vl_masks[11] = 999;
+            nvl = 12;
         }
         const int nmask = ctu ? 3 : (c->sel ? 2 : (!c->bc ? nvl : 4));
         c->sweep_bps = bbps;

@@ -41,6 +41,16 @@
 // solves its y faces.  Periodic boxes without a pressure floor (a floored
 // cell's energy is raised in place by its owner while a neighbouring
 // segment's lead-in may be reading it).
+//
+// k_zfull: the conservative part of the VL full update (Eq. 10 for rho, M
+// and e with dt) inside the corrector's z pencils, the last corrector sweep:
+// each thread, having solved the z faces below and above a cell of its
+// segment, updates that cell's rho, M and e in place from U^n, the x and y
+// corrector fluxes and its own two z fluxes, and stores only the three z
+// flux components the corrector's edge fields read (the mass flux and the
+// two field fluxes).  The face field then advances by CT (Eq. 13) in k_ct
+// or k_ct4, which read only E and B.  A segment of pl faces solves pl + 1
+// (its last cell's upper face is the next segment's first).
 #pragma once
 #include "mhd_kernels.cuh"
 
@@ -288,6 +298,224 @@ k_yprim(Boxes B, StateP<TU, TE> s, R* __restrict__ W, double gam, unsigned long 
     } else if (live) {
         if (!(smax > 0.0)) smax = 0.0;
         atomicMax(smax_acc + bi, (unsigned long long)__double_as_longlong(smax));
+    }
+}
+
+// the conservative full update of one cell from its U^n and flux
+// divergence (full_values without the face field)
+template <class TU, class TE>
+__device__ __forceinline__ void full_hydro(TU rho0, TU mx0, TU my0, TU mz0, TE e0, const TU du[4], TE due, TU ru,
+                                           TE r, TU u[4], TE& e)
+{
+    u[0] = rho0 - ru * du[0];
+    u[1] = mx0 - ru * du[1];
+    u[2] = my0 - ru * du[2];
+    u[3] = mz0 - ru * du[3];
+    e = e0 - r * due;
+}
+
+template <class R, class TU, class TE, int RECON, int SOLVER>
+__global__ void __launch_bounds__(PENCIL_THREADS, (sweep_min_blocks<R, RECON, SOLVER, 1>()))
+k_zfull(Boxes B, StateP<TU, TE> s, const R* __restrict__ Wh, const TE* __restrict__ Bhz, R* __restrict__ F,
+        const DtBox* __restrict__ dtb, double gam)
+{
+    static_assert(RECON != PPM, "the fused walk reconstructs PLM stencils only");
+    constexpr int d = 2;
+    const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (gt >= B.npth[d]) return;
+    const int bi = box_of_pth(B, d, gt);
+    const BoxDev g = B.b[bi];
+    int na, nb, ns;
+    pencil_dims(g.nx, g.ny, g.nz, d, B.pl, na, nb, ns);
+    long long t = gt - g.pth0[d];
+    const int ix = (int)(t % na);          // the line's x
+    t /= na;
+    const int iy = (int)(t % nb);          // and y
+    const int sg = (int)(t / nb);
+    Pencil p;
+    p.base = g.off + (long long)iy * g.nx + ix;
+    p.stride = (long long)g.nx * g.ny;
+    p.n = g.nz;
+    p.out = 0;
+    const long long N = B.N;
+    const long long ox = ix + 1 < g.nx ? 1 : 1 - g.nx;                               // to x + 1
+    const long long oy = iy + 1 < g.ny ? g.nx : g.nx - (long long)g.ny * g.nx;        // to y + 1
+    const int i0 = sg * B.pl;
+    const int i1 = i0 + B.pl < p.n ? i0 + B.pl : p.n;
+    const TE r = DtOf<TE>::dtdx(dtb[bi]);
+    const TU ru = DtOf<TU>::dtdx(dtb[bi]);
+    const R gr = R(gam), gm1 = R(gam - 1.0);
+    R* Fz = F + 14 * N;
+    // cell c (line cell i - 1) from its two z fluxes fl (lower) and fu (upper)
+    auto update = [&](long long c, const R fl[7], const R fu[7]) {
+        R fc[3][5], fn[3][5];
+#pragma unroll
+        for (int m = 0; m < 5; m++) {
+            fc[0][m] = F[(long long)m * N + c];
+            fn[0][m] = F[(long long)m * N + c + ox];
+            fc[1][m] = F[(7LL + m) * N + c];
+            fn[1][m] = F[(7LL + m) * N + c + oy];
+            fc[2][m] = fl[m];
+            fn[2][m] = fu[m];
+        }
+        const TU rho0 = s.rho[c], mx0 = s.m[0][c], my0 = s.m[1][c], mz0 = s.m[2][c];
+        const TE e0 = s.e[c];
+        TU du[4];
+        TE due;
+        flux_divergence<R, TU, TE>(fc, fn, du, due);
+        TU u[4];
+        TE e;
+        full_hydro<TU, TE>(rho0, mx0, my0, mz0, e0, du, due, ru, r, u, e);
+        s.rho[c] = u[0];
+        s.m[0][c] = u[1];
+        s.m[1][c] = u[2];
+        s.m[2][c] = u[3];
+        s.e[c] = e;
+    };
+    // PLM walk as the corrector pencil, one face further: cells i-1, i, i+1
+    // in registers, wpp the "+" state of cell i-1; the cell i+2 loaded while
+    // face i is solved
+    R wa[7], wb[7], wc[7], bna, bnb, bnc, wpp[7], wm[7], wp[7];
+    R dum[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};   // slopes: unused by PLM
+    load_rot(Wh, N, pcell(p, i0 - 2), d, wa, bna);
+    load_rot(Wh, N, pcell(p, i0 - 1), d, wb, bnb);
+    load_rot(Wh, N, pcell(p, i0), d, wc, bnc);
+    recon_cell<RECON, false>(wa, wb, wc, bnb, gr, dum, dum, dum, R(0), wm, wpp);   // "+" of cell i0 - 1
+    copy7(wa, wb); bna = bnb;
+    copy7(wb, wc); bnb = bnc;
+    R wn[7], bnn, f[7], fprev[7];
+    load_rot(Wh, N, pcell(p, i0 + 1), d, wn, bnn);
+    for (int i = i0; i <= i1; i++) {
+        const long long ci = pcell(p, i);
+        copy7(wc, wn);
+        bnc = bnn;
+        if (i < i1) load_rot(Wh, N, pcell(p, i + 2), d, wn, bnn);
+        recon_cell<RECON, false>(wa, wb, wc, bnb, gr, dum, dum, dum, R(0), wm, wp);
+        riemann<SOLVER>(wpp, wm, R(Bhz[ci]), gm1, gr, f);
+        if (i < i1) {                       // the components the edge fields read
+            Fz[ci] = f[0];
+            Fz[5 * N + ci] = f[5];
+            Fz[6 * N + ci] = f[6];
+        }
+        if (i > i0) update(pcell(p, i - 1), fprev, f);
+        copy7(fprev, f);
+        copy7(wpp, wp);
+        copy7(wa, wb); bna = bnb;
+        copy7(wb, wc); bnb = bnc;
+    }
+    (void)bna;
+}
+
+// CT (Eq. 13) of the three lower faces of every cell with dt, from E and
+// B^n, in place: full_values' face arithmetic, for the step whose
+// conservative update ran in the z corrector (k_zfull).  By x-quads (16-byte
+// loads, the x neighbours from the same vectors) in boxes that are 16-byte
+// aligned with an FP32 field, one cell per thread elsewhere.
+template <class R, class TE>
+__device__ __forceinline__ void ct_faces(const R ec[3], const R en[3][3], const TE bo[3], TE r, TE bn[3])
+{
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const int t1 = d == 2 ? 0 : d + 1, t2 = d == 0 ? 2 : d - 1;
+        const TE curl = (widen<TE>(en[t2][t1]) - widen<TE>(ec[t2])) - (widen<TE>(en[t1][t2]) - widen<TE>(ec[t1]));
+        bn[d] = ct_face(bo[d], r, curl);
+    }
+}
+
+// one cell of k_ct / k_ct4's one-cell path: its three lower faces
+template <class R, class TU, class TE>
+__device__ __forceinline__ void ct_cell(const BoxDev& g, long long N, const StateP<TU, TE>& s,
+                                        const R* __restrict__ E, long long lc, TE r)
+{
+    int i, j, k;
+    coords(g, lc, i, j, k);
+    const long long c = g.off + lc;
+    const long long cp[3] = {nbr(g, i, j, k, 0, 1), nbr(g, i, j, k, 1, 1), nbr(g, i, j, k, 2, 1)};
+    R ec[3], en[3][3];
+#pragma unroll
+    for (int m = 0; m < 3; m++) {
+        ec[m] = E[m * N + c];
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+            if (a != m) en[m][a] = E[m * N + cp[a]];
+    }
+    const TE bo[3] = {s.b[0][c], s.b[1][c], s.b[2][c]};
+    TE bn[3];
+    ct_faces<R, TE>(ec, en, bo, r, bn);
+#pragma unroll
+    for (int d = 0; d < 3; d++) s.b[d][c] = bn[d];
+}
+
+template <class R, class TU, class TE>
+__global__ void __launch_bounds__(CELL_THREADS) k_ct(Boxes B, StateP<TU, TE> s, const R* __restrict__ E,
+                                                     const DtBox* __restrict__ dtb)
+{
+    for (long long v = blockIdx.x; v < B.nvblk; v += gridDim.x) {
+        const int bi = box_of_vblk(B, v);
+        BoxDev g = B.b[bi];
+        g.bc = 0;
+        const long long lc = (v - g.vblk0) * CELL_THREADS + threadIdx.x;
+        if (lc < g.n) ct_cell<R, TU, TE>(g, B.N, s, E, lc, DtOf<TE>::dtdx(dtb[bi]));
+    }
+}
+
+template <class R, class TU, class TE>
+__global__ void __launch_bounds__(CELL_THREADS) k_ct4(Boxes B, StateP<TU, TE> s, const R* __restrict__ E,
+                                                      const DtBox* __restrict__ dtb)
+{
+    static_assert(sizeof(TE) == 4, "x-quads of the FP32 field");
+    const long long N = B.N;
+    for (long long v = blockIdx.x; v < B.nvq; v += gridDim.x) {
+        const int bi = box_of_vq(B, v);
+        BoxDev g = B.b[bi];
+        g.bc = 0;
+        const TE r = DtOf<TE>::dtdx(dtb[bi]);
+        if (!g.quad) {                                     // one cell per thread
+            const long long lc = (v - g.vq0) * CELL_THREADS + threadIdx.x;
+            if (lc < g.n) ct_cell<R, TU, TE>(g, N, s, E, lc, r);
+            continue;
+        }
+        const long long lc = 4 * ((v - g.vq0) * CELL_THREADS + threadIdx.x);
+        if (lc >= g.n) continue;
+        int i, j, k;
+        coords(g, lc, i, j, k);                            // i: a multiple of 4
+        const long long c = g.off + lc;
+        const long long cx = cell_of(g, i + 4 < g.nx ? i + 4 : 0, j, k);
+        const long long cy = nbr(g, i, j, k, 1, 1), cz = nbr(g, i, j, k, 2, 1);
+        R ec[3][4], exy[4], exz[4], eyz[4], ezy[4];
+#pragma unroll
+        for (int m = 0; m < 3; m++) ld4(E + m * N + c, ec[m]);
+        ld4(E + cy, exy);                                   // E_x at y+1
+        ld4(E + cz, exz);                                   // E_x at z+1
+        ld4(E + N + cz, eyz);                               // E_y at z+1
+        ld4(E + 2 * N + cy, ezy);                           // E_z at y+1
+        const R eyx = E[N + cx], ezx = E[2 * N + cx];        // E_y, E_z beyond the quad along x
+        TE b0[4], b1[4], b2[4];
+        ld4(s.b[0] + c, b0);
+        ld4(s.b[1] + c, b1);
+        ld4(s.b[2] + c, b2);
+        TE o0[4], o1[4], o2[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const R ecq[3] = {ec[0][q], ec[1][q], ec[2][q]};
+            R en[3][3];
+            en[0][1] = exy[q];
+            en[0][2] = exz[q];
+            en[1][0] = q < 3 ? ec[1][q + 1] : eyx;
+            en[1][2] = eyz[q];
+            en[2][0] = q < 3 ? ec[2][q + 1] : ezx;
+            en[2][1] = ezy[q];
+            en[0][0] = en[1][1] = en[2][2] = R(0);   // unused
+            const TE bo[3] = {b0[q], b1[q], b2[q]};
+            TE bn[3];
+            ct_faces<R, TE>(ecq, en, bo, r, bn);
+            o0[q] = bn[0];
+            o1[q] = bn[1];
+            o2[q] = bn[2];
+        }
+        st4(s.b[0] + c, o0);
+        st4(s.b[1] + c, o1);
+        st4(s.b[2] + c, o2);
     }
 }
 

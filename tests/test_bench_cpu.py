@@ -188,3 +188,25 @@ def test_folding_of_the_y_predictor_with_the_primitives():
     szu, sze, szr = bench.SIZES["mixed"]
     assert gb["predictor_yprim"] == n * (4 * szu + 4 * sze + 8 * szr + 7 * szr)
     assert gb["predictor_sweeps"] == 2 * n * bench.sweep_bytes_per_face("mixed", "vl")
+
+
+def test_folding_of_the_z_corrector_with_the_conservative_update():
+    """pencil-mask bit 9 (with bit 2, PLM, no bit 3): the z corrector group
+    is corrector_zfull and the full-update group times CT alone"""
+    import bench
+    n = 256 ** 3
+    groups = {"prim_cfl": 1.8, "predictor_x": 2.7, "predictor_y": 2.7, "predictor_z": 2.7, "emf1": 2.9,
+              "half_update": 7.1, "corrector_x": 5.1, "corrector_y": 0.01, "corrector_z": 6.9, "emf2": 3.0,
+              "full_update": 1.0}
+    tuned = {"pencil_mask": 743}
+    assert bench.is_zfull(tuned) and not bench.is_zfull(tuned, "vl", "ppm") and not bench.is_zfull({"pencil_mask": 231})
+    g = bench.fold_groups(groups, tuned, "vl", "plm")
+    assert g["corrector_zfull"] == 6.9 and "corrector_z" not in g and g["corrector_yhalf"] == pytest.approx(7.11)
+    ks = bench.kernels_of(g, tuned)
+    assert ks["corrector_zfull"] == (6.9, 1) and ks["corrector_xmarch"] == (5.1, 1)
+    gb = bench.group_bytes("fp32", n, "vl", False, True, False, True)
+    assert gb["corrector_zfull"] == n * 4 * (9 + 3 + 10 + 10)     # W, B_n; F_z 3; rho, M, e in and out; F_x, F_y
+    assert gb["full_update"] == n * 4 * 9 and gb["corrector_sweeps"] == n * 64
+    r = bench.roofline("fp32", g, 10, n, {"hbm_gbs": 6491.2, "src": "measured"},
+                       {"fp32": 75.0, "fp64": 1.0, "src": "test"}, ("vl", "plm", "roe"), tuned)
+    assert r["kernel"] == "corrector_yhalf"

@@ -141,7 +141,7 @@ def test_emf_update_launch_counts_and_fallbacks(M):
     st = I.abc(16, kmult=1, beta=0.5, seed=15)
     s = M.Solver(st.U.shape[1:], st.dx, st.gamma, "vl", "plm", "roe", "fp32", 0.3)
     try:
-        assert s.emf_staging() == (0, 0) and s.sweep_pencils()[0] == 231
+        assert s.emf_staging() == (0, 0) and s.sweep_pencils()[0] == 743
         s.set_sweep_pencils(15, 32)
         assert s.launches_per_step() == 8
         s.set_emf_staging(2)

@@ -178,8 +178,9 @@ def test_fused_bit_is_ignored_where_it_does_not_apply(M):
         assert s.launches_per_step() == 12
         s.free()
         s = M.Solver(st.U.shape[1:], st.dx, st.gamma, "vl", "plm", "roe", "fp32", 0.3)
-        assert s.sweep_pencils() == (231, 32)       # the FP32 VL PLM default: x by aligned marching warps,
-        assert s.launches_per_step() == 11           # the half update in the y corrector
+        assert s.sweep_pencils() == (743, 32)       # the FP32 VL PLM default: x by aligned marching warps,
+        assert s.launches_per_step() == 11           # the half update in the y corrector, the
+                                                     # conservative update in the z corrector
         s.set_sweep_pencils(15, 32)
         assert s.launches_per_step() == 8
         s.set_sweep_pencils(7, 32)

@@ -293,12 +293,12 @@ def test_xmarch_mask_range_and_precedence(M):
         s.set_sweep_pencils(127, 32)
         assert s.sweep_pencils() == (127, 32)
         with pytest.raises(M.MHDError):
-            s.set_sweep_pencils(512, 32)
+            s.set_sweep_pencils(1024, 32)
         M.lib().mhd_clear_error(s.h)
         assert s.sweep_pencils() == (127, 32)
     finally:
         s.free()
-    for prec, scheme, mask in [("fp32", ("vl", "plm", "roe"), 231), ("fp32", ("vl", "plm_prim", "hlle"), 231),
+    for prec, scheme, mask in [("fp32", ("vl", "plm", "roe"), 743), ("fp32", ("vl", "plm_prim", "hlle"), 743),
                                ("fp32", ("vl", "ppm", "hlld"), 103), ("mixed", ("vl", "plm", "roe"), 487),
                                ("fp32", ("ctu", "plm", "roe"), 39), ("fp64", ("ctu", "plm", "roe"), 39)]:
         s = M.Solver(st.U.shape[1:], st.dx, st.gamma, *scheme, prec, 0.3)

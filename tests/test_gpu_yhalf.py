@@ -6,6 +6,10 @@ thread forms the primitives of its segment's cells and one lead-in cell,
 stores its own cells', folds their signal speeds into the box maximum
 (device dt) and solves its y faces.
 
+The conservative part of the full update inside the corrector's z pencils
+(k_zfull; pencil-mask bit 9 with bit 2), the face field by CT alone after
+the edge fields (k_ct, k_ct4).
+
 The VL half update fused into the corrector's y pencils (k_yhalf;
 pencil-mask bit 7 with bit 1): each pencil thread forms the half-step state
 (Sec. 3.2 VL step 3: Eq. 13 for the faces, Eq. 10 with dt/2 for the cells,
@@ -35,6 +39,7 @@ pytestmark = pytest.mark.gpu
 PLM = [("vl", r, s) for r in ("plm", "plm_prim") for s in ("roe", "hlld", "hlle")]
 FUSED64, FUSED32 = 23 | 128, 103 | 128     # the precision defaults with bit 7
 PRIM = 256                                   # bit 8
+ZFULL = 512                                  # bit 9
 
 
 @pytest.fixture(scope="module")
@@ -87,6 +92,63 @@ def parity(M, st, scheme, nsteps, mask=FUSED64, plen=32, pfloor=0.0, tol=1e-12, 
 
 
 VL = [("vl", r, s) for r in ("plm", "ppm", "plm_prim") for s in ("roe", "hlld", "hlle")]
+
+
+@pytest.mark.parametrize("scheme", PLM)
+def test_zfull_fp64_parity(M, scheme):
+    """bit 9 alone, and with bits 7 and 8 (the corrector fluxes in the second
+    array), against the oracle"""
+    st = I.abc(None, kmult=1, beta=0.5, seed=89, noise=2e-2, shape=(64, 10, 12))
+    parity(M, st, scheme, 2, mask=23 | ZFULL)
+    parity(M, st, scheme, 2, mask=23 | ZFULL | 128 | PRIM, device_dt=True)
+
+
+@pytest.mark.parametrize("shape", [(40, 8, 12), (33, 6, 9), (2, 5, 9), (1, 9, 7), (3, 3, 1), (36, 6, 20)])
+@pytest.mark.parametrize("plen", [1, 3, 32])
+def test_zfull_fp64_parity_ragged_short(M, shape, plen):
+    """last segments of 8 and 1 faces, lines of 1-3 cells, 16-byte aligned
+    and unaligned rows (the CT kernel's quads and single cells); the box
+    length from ny, as the other ragged cases"""
+    L = max(shape[1], 1) / 16.0
+    st = I.abc(None, kmult=L, beta=0.5, seed=90, noise=3e-2, shape=shape, L=L)
+    parity(M, st, ("vl", "plm", "roe"), 2, mask=23 | ZFULL | 128, plen=plen)
+
+
+def test_zfull_fp64_batch(M):
+    shapes = [(16, 5, 3), (33, 3, 7), (40, 5, 5), (70, 3, 3), (5, 2, 1)]
+    boxes = [I.abc(None, kmult=1, beta=0.5, seed=100 + k, noise=3e-2, shape=sh) for k, sh in enumerate(shapes)]
+    scheme = ("vl", "plm_prim", "hlle")
+    s = M.Solver(None, None, 5 / 3, *scheme, "fp64", 0.3,
+                 shapes=[b.U.shape[1:] for b in boxes], dxs=[b.dx for b in boxes])
+    try:
+        s.set_sweep_pencils(23 | ZFULL | 128 | PRIM, 8)
+        for k, b in enumerate(boxes):
+            s.set_state(b.U, b.B, box=k)
+        s.advance(1)
+        dts = s.last_dts()
+        for k, b in enumerate(boxes):
+            U, B = b.U.copy(), b.B.copy()
+            orc.step(U, B, b.dx, b.gamma, float(dts[k]), *scheme)
+            Ug, Bg = s.get_state(box=k)
+            mfloor = 1e-2 * np.abs(U[0]).sum()
+            for f in range(5):
+                den = max(np.abs(U[f]).sum(), mfloor if f in (1, 2, 3) else 0.0)
+                assert np.abs(Ug[f] - U[f]).sum() / den <= 1e-12, (k, f)
+            bfloor = 1e-2 * np.abs(B).sum() / 3
+            for d in range(3):
+                assert np.abs(Bg[d] - B[d]).sum() / max(np.abs(B[d]).sum(), bfloor) <= 1e-12, (k, d)
+    finally:
+        s.free()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+@pytest.mark.parametrize("scheme", [("vl", "plm", "roe"), ("vl", "plm_prim", "hlld")])
+def test_zfull_agrees_with_the_full_update(M, prec, scheme):
+    """three graph-replayed steps with bits 7, 8 and 9 against the separate
+    kernels (quad-aligned box and a 33-wide one)"""
+    for shape in [(40, 48, 64), (20, 12, 33)]:
+        st = I.abc(None, kmult=1, beta=0.5, seed=91, noise=2e-2, shape=shape)
+        agree(M, st, prec, scheme, 3, extra=ZFULL)
 
 
 @pytest.mark.parametrize("scheme", VL)
@@ -182,13 +244,13 @@ def test_yhalf_fp64_parity_short_segments(M, plen):
     parity(M, st, ("vl", "plm", "hlle"), 2, plen=plen)
 
 
-def agree(M, st, prec, scheme, nsteps, pfloor=0.0):
+def agree(M, st, prec, scheme, nsteps, pfloor=0.0, extra=0):
     """the same steps with and without bit 7 (graph-replayed), per-field
     relative L1 of the difference; returns the two floor counts"""
     cast = np.float32 if prec == "fp32" else np.float64
     base = 23 if prec == "fp64" else 103
     out, floors, dts = [], [], []
-    for mask in (base, base | 128 | (0 if pfloor else PRIM)):
+    for mask in (base, base | 128 | (0 if pfloor else PRIM) | extra):
         s = M.Solver(st.U.shape[1:], st.dx, st.gamma, *scheme, prec, 0.3, pfloor=pfloor)
         try:
             s.set_sweep_pencils(mask, 32)
@@ -261,12 +323,12 @@ def test_yhalf_agrees_with_separate_kernels(M, prec, scheme):
 
 
 def test_mask_range_defaults_and_fallbacks(M):
-    """bits 7 and 8 are accepted up to 511; bit 7 is the FP32 PLM default,
-    bits 7 and 8 the mixed PLM default, bit 8 the mixed PPM default; with
+    """bits 7 to 9 are accepted up to 1023; bits 7 and 9 are the FP32 PLM
+    default, bits 7 and 8 the mixed PLM default, bit 8 the mixed PPM default; with
     PPM (bit 7), a pressure floor (bit 8), outflow boundaries or without
     bit 1 the separate kernels run"""
     st = I.abc(16, kmult=1, beta=0.5, seed=85)
-    for prec, recon, mask, nl in [("fp32", "plm", FUSED32, 11), ("fp32", "ppm", 103, 12),
+    for prec, recon, mask, nl in [("fp32", "plm", FUSED32 | ZFULL, 11), ("fp32", "ppm", 103, 12),
                                   ("mixed", "plm_prim", FUSED32 | PRIM, 10), ("mixed", "ppm", 103 | PRIM, 11),
                                   ("fp64", "plm", 23, 12)]:
         s = M.Solver(st.U.shape[1:], st.dx, st.gamma, "vl", recon, "roe", prec, 0.3)
@@ -285,7 +347,7 @@ def test_mask_range_defaults_and_fallbacks(M):
         s.set_sweep_pencils((FUSED32 | PRIM) & ~2, 32)   # y by tiles: neither y pencil takes a pass
         assert s.launches_per_step() == 12
         with pytest.raises(M.MHDError):
-            s.set_sweep_pencils(512, 32)
+            s.set_sweep_pencils(1024, 32)
         M.lib().mhd_clear_error(s.h)
         s.set_sweep_pencils(FUSED32 | PRIM, 32)
         s.set_boundary(2)                          # outflow y
