@@ -48,9 +48,9 @@ def is_fused(tuned, integ="vl"):
 
 def is_yhalf(tuned, integ="vl", recon="plm"):
     """the VL half update runs inside the y corrector pencils (pencil-mask
-    bits 1 and 7, a PLM reconstruction, bit 3 clear; periodic boxes)"""
+    bits 1 and 7, bit 3 clear; periodic boxes)"""
     m = (tuned or {}).get("pencil_mask", 0) or 0
-    return integ == "vl" and recon != "ppm" and (m & 130) == 130 and not m & 8
+    return integ == "vl" and (m & 130) == 130 and not m & 8
 
 
 def is_yprim(tuned, integ="vl", pfloor=0.0):

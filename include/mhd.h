@@ -259,7 +259,7 @@ mhd_status mhd_get_dirichlet(mhd_ctx* ctx, int axis, int* nlayers);
  * by the same aligned march: at 256^3 FP32 0.64 ms where the overlapping
  * warps take 0.81 (Roe); the PPM tracing and the transverse correction keep
  * their warps.
- * Bit 7 with bit 1 (VL with a PLM reconstruction, every box periodic, no
+ * Bit 7 with bit 1 (VL, every box periodic, no
  * learned selector, bit 3 clear and the edge fields as their own kernel;
  * ignored otherwise): the half update (Sec. 3.2, VL step 3: B^{n+1/2} by
  * Eq. 13, U^{n+1/2} by Eq. 10 with dt/2, and its primitives) runs inside
@@ -268,7 +268,8 @@ mhd_status mhd_get_dirichlet(mhd_ctx* ctx, int axis, int* nlayers);
  * cells and one past its end), stores the half-step primitives and faces
  * of the cells it owns and solves its y faces; the x and z correctors
  * follow.  The half update's loads then overlap the corrector's arithmetic
- * (256^3 FP32 Roe: 0.708 ms for what the two kernels take 0.439 + 0.475)
+ * (256^3 FP32 PLM + Roe: 0.708 ms for what the two kernels take 0.439 +
+ * 0.475; PPM + Roe: step 4.86 -> 4.71 ms)
  * and the step is 11 launches.  The corrector's fluxes go to a second flux
  * array (21 values per cell in the arithmetic type), allocated on first
  * use (MHD_ENOMEM if that fails).  The states agree with the separate
@@ -293,7 +294,7 @@ mhd_status mhd_get_dirichlet(mhd_ctx* ctx, int axis, int* nlayers);
  * 256^3 FP32 Roe the step takes 3.58 ms against 3.67.
  * pencil_mask in [0, 1023] (0: tiles everywhere), pencil_len in [1, 1024],
  * else MHD_EINVAL.  Defaults (pencil_len 32): VL FP64 23; VL FP32 743 with
- * a PLM reconstruction, 103 with PPM; VL mixed 487 with PLM, 359 with PPM;
+ * a PLM reconstruction, 231 with PPM; VL mixed 487 with PLM, 359 with PPM;
  * CTU 39. */
 mhd_status mhd_set_sweep_pencils(mhd_ctx* ctx, int pencil_mask, int pencil_len);
 mhd_status mhd_get_sweep_pencils(mhd_ctx* ctx, int* pencil_mask, int* pencil_len);

@@ -301,7 +301,9 @@ static mhd_status init_common(int nbox, const mhd_grid* grids, double gamma, con
     // (bit 8; 256^3 PLM + Roe: 0.718 ms against 0.644 + 0.307, whose FP64
     // per-cell arithmetic then overlaps the sweep's); in FP32 and FP64 that
     // ties the two kernels (0.451 against 0.179 + 0.267 ms; 20.2 against
-    // 5.4 + 14.8 ms).  FP32 PLM also runs the conservative part of the full
+    // 5.4 + 14.8 ms).  FP32 PPM takes the half update in the y corrector too
+    // (256^3 Roe: step 4.86 -> 4.71 ms, HLLD 4.87 -> 4.67); the mixed PPM
+    // form ties with it (6.47 against 6.48 ms).  FP32 PLM also runs the conservative part of the full
     // update inside the z corrector pencils and the face field by CT alone
     // (bit 9; 256^3 Roe: z corrector 0.468 -> 0.685 ms, full update 0.412 ->
     // 0.098, step 3.67 -> 3.58 ms); the mixed form (5.43 -> 5.51 ms) and FP64
@@ -311,7 +313,7 @@ static mhd_status init_common(int nbox, const mhd_grid* grids, double gamma, con
     else if (scheme->precision == MHD_FP64)
         c->pencil_mask = 23;
     else if (scheme->precision == MHD_FP32)   // PLM: the half update in the y corrector, the conservative
-        c->pencil_mask = scheme->recon != MHD_PPM ? 743 : 103;   // update in the z corrector
+        c->pencil_mask = scheme->recon != MHD_PPM ? 743 : 231;   // update in the z corrector (PLM)
     else
         c->pencil_mask = scheme->recon != MHD_PPM ? 487 : 359;   // mixed: and the primitives in the y predictor
     c->pencil_len = 32;
@@ -961,24 +963,29 @@ extern "C" mhd_status mhd_autotune(mhd_ctx* c, int reps, int* tile_len, int* blo
         // aligned marching warps, bits 5 and 6, and for periodic boxes with
         // the fused predictor, bit 3)
         // (CTU: also with the x tracing by aligned marching warps, bit 5)
-        // (VL, periodic, no selector: also with the half update fused into
-        // the y corrector pencils, bit 7, when its flux array can be had)
         // (VL, periodic, no selector: also with the primitives inside the y
-        // predictor pencils, bit 8, and for PLM with the half update inside
-        // the y corrector pencils, bit 7, when its flux array can be had)
+        // predictor pencils, bit 8, with the half update inside the y
+        // corrector pencils, bit 7, when its flux array can be had, and for
+        // PLM with the conservative update inside the z corrector, bit 9)
         int vl_masks[12] = {7, 6, 23, 103, 15, 31, 111, 359, 0, 0, 0, 0};
         const int ctu_masks[3] = {7, 6, 39};
         const bool ctu = c->sch.integrator != MHD_VL;
         const int* masks = ctu ? ctu_masks : vl_masks;
         const int lens[3] = {8, 16, 32};
         int nvl = 8;
-        if (c->sch.recon != MHD_PPM && !c->sel && !c->bc && ensure_f2(c) == cudaSuccess) {
-            vl_masks[7] = 151;
-            vl_masks[8] = 231;
-            vl_masks[9] = 487;
-            vl_masks[10] = 743;            // (bit 9: the conservative update in the z corrector)
-            vl_masks[11] = 999;
-            nvl = 12;
+        if (!c->sel && !c->bc && ensure_f2(c) == cudaSuccess) {
+            if (c->sch.recon != MHD_PPM) {
+                vl_masks[7] = 151;
+                vl_masks[8] = 231;
+                vl_masks[9] = 487;
+                vl_masks[10] = 743;        // (bit 9: the conservative update in the z corrector)
+                vl_masks[11] = 999;
+                nvl = 12;
+            } else {
+                vl_masks[8] = 231;
+                vl_masks[9] = 487;
+                nvl = 10;
+            }
         }
         const int nmask = ctu ? 3 : (c->sel ? 2 : (!c->bc ? nvl : 4));
         c->sweep_bps = bbps;

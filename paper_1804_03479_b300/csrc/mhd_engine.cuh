@@ -288,13 +288,13 @@ inline int emf_form(const mhd_ctx* c)
 }
 
 // the VL half update fused into the corrector's y pencils (k_yhalf) with
-// pencil-mask bits 1 and 7: a PLM stencil, periodic boxes without a learned
+// pencil-mask bits 1 and 7: periodic boxes without a learned
 // selector, the predictor and the edge fields as separate kernels, and the
 // second flux array allocated (the corrector's fluxes go there)
 inline bool y_half(const mhd_ctx* c)
 {
-    return c->sch.recon != MHD_PPM && (c->pencil_mask & 130) == 130 && c->sch.integrator == MHD_VL && !c->bc &&
-           !c->sel && c->F2 && !fused_predictor(c) && emf_form(c) == 0;
+    return (c->pencil_mask & 130) == 130 && c->sch.integrator == MHD_VL && !c->bc && !c->sel && c->F2 &&
+           !fused_predictor(c) && emf_form(c) == 0;
 }
 
 // the t^n primitives and CFL signal speeds inside the VL predictor's y
@@ -329,8 +329,7 @@ template <class R, class TU, class TE, int RECON, int SOLVER>
 void launch_yhalf(mhd_ctx* c, const Boxes& g, const StateP<TU, TE>& s, const R* F, const R* E, TE* const Bh[3],
                   R* Wh, R* Fc, cudaStream_t st)
 {
-    if constexpr (RECON != PPM)
-        k_yhalf<R, TU, TE, RECON, SOLVER><<<pencil_grid(c, 1), PENCIL_THREADS, 0, st>>>(
+    k_yhalf<R, TU, TE, RECON, SOLVER><<<pencil_grid(c, 1), PENCIL_THREADS, 0, st>>>(
             g, s, F, E, c->dtc, c->gamma, c->sch.pfloor, Bh[0], Bh[1], Bh[2], Wh, Fc + 7 * g.N);
 }
 
@@ -457,7 +456,7 @@ void run_step(mhd_ctx* c, bool device_dt)
 
     if (INTEG == VL) {
         const int cs = c->bc ? cross_size(c->hbox[0].nx, c->hbox[0].ny, c->hbox[0].nz) : 0;
-        const bool yh = RECON != PPM && y_half(c);
+        const bool yh = y_half(c);
         if (fused_predictor(c)) {
             // VL steps 1-3 in one kernel (its time goes to the half-update group)
             for (int b = 2; b <= 5; b++) prof_mark(c, b);

@@ -30,7 +30,7 @@
 // then write theirs there too, and the corrector's edge fields and the full
 // update read it.
 //
-// Periodic boxes (one or a batch), PLM reconstructions.
+// Periodic boxes (one or a batch), PLM and PPM reconstructions.
 //
 // k_yprim: the primitives at t^n (Eq. 5, with the cell-centred field the
 // mean of the two faces) and the CFL signal speeds (Sec. 3.2) inside the
@@ -83,7 +83,6 @@ k_yhalf(Boxes B, StateP<TU, TE> s, const R* __restrict__ Fp, const R* __restrict
         const DtBox* __restrict__ dtb, double gam, double pfloor, TE* __restrict__ Bh0, TE* __restrict__ Bh1,
         TE* __restrict__ Bh2, R* __restrict__ Wh, R* __restrict__ Fy)
 {
-    static_assert(RECON != PPM, "the fused walk reconstructs PLM stencils only");
     const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (gt >= B.npth[1]) return;
     const int bi = box_of_pth(B, 1, gt);
@@ -109,7 +108,8 @@ k_yhalf(Boxes B, StateP<TU, TE> s, const R* __restrict__ Fp, const R* __restrict
 
     YCarry<R, TE> Y;
     {
-        const long long c = base + (long long)wrapi(i0 - 2, ny) * nx;
+        // the walk's first cell: two lead-in cells for PLM, three for PPM
+        const long long c = base + (long long)wrapi(i0 - (RECON == PPM ? 3 : 2), ny) * nx;
 #pragma unroll
         for (int m = 0; m < 5; m++) Y.fy[m] = Fp[(7LL + m) * N + c];
         Y.by = s.b[1][c];
@@ -177,6 +177,47 @@ k_yhalf(Boxes B, StateP<TU, TE> s, const R* __restrict__ Fp, const R* __restrict
         Y.exz = e0yz;
     };
 
+    if constexpr (RECON == PPM) {
+        // PPM walk as the corrector pencil: cells i-1 .. i+2 and the
+        // characteristic slopes of i-1 .. i+1 in registers, wpp the "+" state
+        // of cell i-1; a segment forms pl + 5 half-step states (cells i0 - 3
+        // .. i1 + 1), the lead-in's slopes serving the window as they are
+        R w0[7], w1[7], w2[7], w3[7], wq[7], b0, b1, b2, b3, bq;
+        R s0[7], s1[7], s2[7], wpp[7], wm[7], wp[7], f[7];
+        TE l1, l2, l3, ldum;
+        half_cell(i0 - 3, wq, bq, ldum);
+        half_cell(i0 - 2, w0, b0, ldum);
+        half_cell(i0 - 1, w1, b1, l1);
+        half_cell(i0, w2, b2, l2);
+        half_cell(i0 + 1, w3, b3, l3);
+        char_slope(wq, w0, w1, b0, gr, s0);                 // slope of i0 - 2
+        char_slope(w0, w1, w2, b1, gr, s1);                 // i0 - 1
+        char_slope(w1, w2, w3, b2, gr, s2);                 // i0
+        recon_cell<PPM, false>(w0, w1, w2, b1, gr, s0, s1, s2, R(0), wm, wpp);   // "+" of cell i0 - 1
+        copy7(w0, w1); b0 = b1;
+        copy7(w1, w2); b1 = b2; l1 = l2;
+        copy7(w2, w3); b2 = b3; l2 = l3;
+        copy7(s0, s1);
+        copy7(s1, s2);
+        for (int i = i0; i < i1; i++) {
+            const long long ci = base + (long long)i * nx;
+            half_cell(i + 2, w3, b3, l3);
+            char_slope(w1, w2, w3, b2, gr, s2);             // slope of i + 1
+            recon_cell<PPM, false>(w0, w1, w2, b1, gr, s0, s1, s2, R(0), wm, wp);
+            riemann<SOLVER>(wpp, wm, R(l1), gm1, gr, f);
+#pragma unroll
+            for (int m = 0; m < 7; m++) Fy[(long long)m * N + ci] = f[m];
+            copy7(wpp, wp);
+            copy7(w0, w1); b0 = b1;
+            copy7(w1, w2); b1 = b2; l1 = l2;
+            copy7(w2, w3); b2 = b3; l2 = l3;
+            copy7(s0, s1);
+            copy7(s1, s2);
+        }
+        (void)bq;
+        (void)b0;
+        return;
+    }
     // PLM walk as the corrector pencil: cells i-1, i, i+1 in registers, wpp
     // the "+" state of cell i-1.  The cell i+1 is formed just before face i
     // is solved: forming cell i+2 one face ahead (as the plain pencil loads

@@ -140,12 +140,12 @@ def test_roofline_of_the_y_corrector_with_the_half_update():
               "half_update": 7.1, "corrector_x": 5.1, "corrector_y": 0.01, "corrector_z": 4.7, "emf2": 3.0,
               "full_update": 4.1}
     tuned = {"pencil_mask": 231}
-    assert bench.is_yhalf(tuned) and not bench.is_yhalf(tuned, "vl", "ppm")
+    assert bench.is_yhalf(tuned) and bench.is_yhalf(tuned, "vl", "ppm") and not bench.is_yhalf(tuned, "ctu")
     assert not bench.is_yhalf({"pencil_mask": 103}) and not bench.is_yhalf({"pencil_mask": 239})
     g = bench.fold_groups(groups, tuned, "vl", "plm")
     assert "half_update" not in g and "corrector_y" not in g
     assert g["corrector_yhalf"] == pytest.approx(7.11)
-    assert bench.fold_groups(groups, tuned, "vl", "ppm") == groups
+    assert bench.fold_groups(groups, tuned, "vl", "ppm") == g
     st = bench.stages_of(g)
     assert st["corrector_yhalf"] == pytest.approx(7.11) and st["corrector_sweeps"] == pytest.approx(9.8)
     pk = {"hbm_gbs": 6491.2, "src": "measured"}
@@ -181,6 +181,8 @@ def test_folding_of_the_y_predictor_with_the_primitives():
     assert g["predictor_yprim"] == pytest.approx(7.21) and g["corrector_yhalf"] == pytest.approx(19.01)
     g2 = bench.fold_groups(groups, {"pencil_mask": 359}, "vl", "ppm")
     assert "predictor_yprim" in g2 and "half_update" in g2 and "corrector_y" in g2
+    g3 = bench.fold_groups(groups, {"pencil_mask": 487}, "vl", "ppm")
+    assert "predictor_yprim" in g3 and "corrector_yhalf" in g3 and "corrector_z" in g3
     r = bench.roofline("mixed", g, 10, n, {"hbm_gbs": 6491.2, "src": "measured"},
                        {"fp32": 75.0, "fp64": 1.0, "src": "test"}, ("vl", "plm", "roe"), {"pencil_mask": 487})
     assert r["kernel"] == "corrector_yhalf"

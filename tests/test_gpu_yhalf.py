@@ -60,7 +60,7 @@ def parity(M, st, scheme, nsteps, mask=FUSED64, plen=32, pfloor=0.0, tol=1e-12, 
     s = M.Solver(U.shape[1:], st.dx, st.gamma, *scheme, "fp64", 0.3, pfloor=pfloor)
     try:
         s.set_sweep_pencils(mask, plen)
-        fused = (mask & 128 and scheme[1] != "ppm") + (mask & PRIM and not pfloor)
+        fused = bool(mask & 128) + bool(mask & PRIM and not pfloor)
         assert s.launches_per_step() == 12 - fused
         for it in range(nsteps):
             s.set_state(U, B)
@@ -153,12 +153,11 @@ def test_zfull_agrees_with_the_full_update(M, prec, scheme):
 
 @pytest.mark.parametrize("scheme", VL)
 def test_yprim_fp64_parity_device_dt(M, scheme):
-    """bit 8 alone and with bit 7 (PLM): the device dt from the pencils'
-    signal speeds and the whole step against the oracle"""
+    """bit 8 alone and with bit 7: the device dt from the pencils' signal
+    speeds and the whole step against the oracle"""
     st = I.abc(None, kmult=1, beta=0.5, seed=86, noise=2e-2, shape=(10, 64, 12))
     parity(M, st, scheme, 2, mask=23 | PRIM, device_dt=True)
-    if scheme[1] != "ppm":
-        parity(M, st, scheme, 2, mask=23 | PRIM | 128, device_dt=True)
+    parity(M, st, scheme, 2, mask=23 | PRIM | 128, device_dt=True)
 
 
 @pytest.mark.parametrize("shape", [(8, 40, 12), (6, 33, 9), (5, 2, 9), (9, 1, 7), (3, 3, 1)])
@@ -219,7 +218,7 @@ def test_yprim_reports_a_negative_pressure(M):
         s.free()
 
 
-@pytest.mark.parametrize("scheme", PLM)
+@pytest.mark.parametrize("scheme", VL)
 def test_yhalf_fp64_parity(M, scheme):
     """ny = 64: two segments a line, lead-ins and look-ahead across them"""
     st = I.abc(None, kmult=1, beta=0.5, seed=81, noise=2e-2, shape=(10, 64, 12))
@@ -234,6 +233,7 @@ def test_yhalf_fp64_parity_ragged_and_short(M, shape):
     st = I.abc(None, kmult=L, beta=0.5, seed=82, noise=3e-2, shape=shape, L=L)
     parity(M, st, ("vl", "plm", "roe"), 2)
     parity(M, st, ("vl", "plm_prim", "hlld"), 2, mask=FUSED32)
+    parity(M, st, ("vl", "ppm", "hlle"), 2)
 
 
 @pytest.mark.parametrize("plen", [1, 2, 3, 5])
@@ -242,6 +242,7 @@ def test_yhalf_fp64_parity_short_segments(M, plen):
     lead-ins of one or two other segments"""
     st = I.abc(None, kmult=1, beta=0.5, seed=83, noise=2e-2, shape=(6, 23, 10))
     parity(M, st, ("vl", "plm", "hlle"), 2, plen=plen)
+    parity(M, st, ("vl", "ppm", "roe"), 2, plen=plen)
 
 
 def agree(M, st, prec, scheme, nsteps, pfloor=0.0, extra=0):
@@ -315,7 +316,7 @@ def test_yhalf_fp64_batch_parity(M):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "mixed", "fp64"])
-@pytest.mark.parametrize("scheme", PLM)
+@pytest.mark.parametrize("scheme", VL)
 def test_yhalf_agrees_with_separate_kernels(M, prec, scheme):
     """three graph-replayed steps with and without bit 7"""
     st = I.abc(None, kmult=1, beta=0.5, seed=84, noise=2e-2, shape=(40, 48, 64))
@@ -324,11 +325,12 @@ def test_yhalf_agrees_with_separate_kernels(M, prec, scheme):
 
 def test_mask_range_defaults_and_fallbacks(M):
     """bits 7 to 9 are accepted up to 1023; bits 7 and 9 are the FP32 PLM
-    default, bits 7 and 8 the mixed PLM default, bit 8 the mixed PPM default; with
-    PPM (bit 7), a pressure floor (bit 8), outflow boundaries or without
+    default, bit 7 the FP32 PPM default, bits 7 and 8 the mixed PLM default,
+    bit 8 the mixed PPM default; with
+    PPM (bit 9), a pressure floor (bit 8), outflow boundaries or without
     bit 1 the separate kernels run"""
     st = I.abc(16, kmult=1, beta=0.5, seed=85)
-    for prec, recon, mask, nl in [("fp32", "plm", FUSED32 | ZFULL, 11), ("fp32", "ppm", 103, 12),
+    for prec, recon, mask, nl in [("fp32", "plm", FUSED32 | ZFULL, 11), ("fp32", "ppm", FUSED32, 11),
                                   ("mixed", "plm_prim", FUSED32 | PRIM, 10), ("mixed", "ppm", 103 | PRIM, 11),
                                   ("fp64", "plm", 23, 12)]:
         s = M.Solver(st.U.shape[1:], st.dx, st.gamma, "vl", recon, "roe", prec, 0.3)
@@ -356,8 +358,8 @@ def test_mask_range_defaults_and_fallbacks(M):
         s.free()
     s = M.Solver(st.U.shape[1:], st.dx, st.gamma, "vl", "ppm", "roe", "fp32", 0.3)
     try:
-        s.set_sweep_pencils(FUSED32 | PRIM, 32)
-        assert s.launches_per_step() == 11         # PPM: the primitives only
+        s.set_sweep_pencils(FUSED32 | PRIM | ZFULL, 32)
+        assert s.launches_per_step() == 10         # PPM: bit 9 does not apply
     finally:
         s.free()
     s = M.Solver(st.U.shape[1:], st.dx, st.gamma, "vl", "plm", "roe", "mixed", 0.3, pfloor=1e-6)
