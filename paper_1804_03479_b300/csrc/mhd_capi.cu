@@ -743,7 +743,7 @@ extern "C" mhd_status mhd_get_sweep_config(mhd_ctx* c, int* tile_len, int* block
 static void count_launches(mhd_ctx* c)
 {
     if (c->sel) {
-        c->launches = 12 + 3 + 3 + 6 - (emf_form(c) == 2 ? 2 : 0);
+        c->launches = 12 + 3 + 3 + 6 - (emf_form(c) == 2 ? 2 : 0) - (sel_y_half(c) ? 1 : 0);
         return;
     }
     // (CTU: one stage-1 outer-face pass per outflow axis; the stage-2 ones

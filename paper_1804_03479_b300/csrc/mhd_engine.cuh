@@ -297,6 +297,14 @@ inline bool y_half(const mhd_ctx* c)
            !fused_predictor(c) && emf_form(c) == 0;
 }
 
+// the learned selector's step: the half update inside the cheap y corrector
+// pencils with pencil-mask bits 1 and 7 (the second flux array allocated,
+// the edge fields as their own kernel)
+inline bool sel_y_half(const mhd_ctx* c)
+{
+    return (c->pencil_mask & 130) == 130 && c->F2 && emf_form(c) != 2;
+}
+
 // the t^n primitives and CFL signal speeds inside the VL predictor's y
 // pencils (k_yprim) with pencil-mask bits 1 and 8: periodic boxes without a
 // learned selector or a pressure floor, bit 3 clear

@@ -370,52 +370,61 @@ static void run_step_learned(mhd_ctx* c, bool device_dt)
         prof_mark(c, 2 + d);
     }
     const bool eu = emf_form(c) == 2;   // edge fields fused with the update that uses them
+    // pencil-mask bits 1 and 7: the half update inside the cheap y corrector
+    // pencils, which then solve every y face (the full list pass overwrites
+    // its faces after them); the corrector's fluxes go to the second array
+    const bool yh = sel_y_half(c);
+    R* Fc = yh ? (R*)c->F2 : F1;
     if (eu) {
         prof_mark(c, 5);
         launch_emf_update<R, float, float, true>(c, g, s, F1, W, Bh, Wh, st);
     } else {
         launch_emf<R>(c, g, F1, W, E, st);
         prof_mark(c, 5);
-        k_half4<R, float, float><<<c->quad_grid, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1],
-                                                                         Bh[2], Wh, c->sch.pfloor);
+        if (yh)
+            launch_yhalf<R, float, float, PLM_PRIM, HLLE>(c, g, s, F1, E, Bh, Wh, (R*)c->F2, st);
+        else
+            k_half4<R, float, float><<<c->quad_grid, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1],
+                                                                             Bh[2], Wh, c->sch.pfloor);
     }
     prof_mark(c, 6);
     // VL steps 4-7
     for (int d = 0; d < 3; d++) {
         if (d == 0 && xw) {
             if (xm1)
-                k_xmarch<R, PLM_PRIM, HLLE, 1, float><<<xmarch_grid(c), PENCIL_THREADS, 0, st>>>(g, Wh, Bh[0], F1,
+                k_xmarch<R, PLM_PRIM, HLLE, 1, float><<<xmarch_grid(c), PENCIL_THREADS, 0, st>>>(g, Wh, Bh[0], Fc,
                                                                                                gam);
             else
                 k_xwarp<R, PLM_PRIM, HLLE, 1, float><<<xrow_grid(c), PENCIL_THREADS, 0, st>>>(
-                    g, Wh, Bh[0], F1, gam, 2, nullptr, nullptr, nullptr, nullptr, nullptr, sel_of(c, 6));
+                    g, Wh, Bh[0], Fc, gam, 2, nullptr, nullptr, nullptr, nullptr, nullptr, sel_of(c, 6));
             k_xwarp<R, PPM, HLLD, 1, float><<<list_grid_xwarp(c, 2), PENCIL_THREADS, 0, st>>>(
-                g, Wh, Bh[0], F1, gam, 2, c->sel_list[7], c->sel_cnt + 7);
+                g, Wh, Bh[0], Fc, gam, 2, c->sel_list[7], c->sel_cnt + 7);
         } else if (c->pencil_mask >> d & 1) {
-            launch_pencil<R, PLM_PRIM, HLLE, 1, float>(d, pencil_grid(c, d), st, g, Wh, Bh[d],
-                                                          F1 + (long long)d * 7 * n, gam, nullptr, nullptr, nullptr,
-                                                          nullptr, nullptr, sel_of(c, 2 * d));
+            if (!(d == 1 && yh))     // (y: the cheap faces were solved with the half update)
+                launch_pencil<R, PLM_PRIM, HLLE, 1, float>(d, pencil_grid(c, d), st, g, Wh, Bh[d],
+                                                              Fc + (long long)d * 7 * n, gam, nullptr, nullptr,
+                                                              nullptr, nullptr, nullptr, sel_of(c, 2 * d));
             launch_pencil<R, PPM, HLLD, 1, float>(d, list_grid_pencil(c, d), st, g, Wh, Bh[d],
-                                                          F1 + (long long)d * 7 * n, gam, c->sel_list[2 * d + 1],
+                                                          Fc + (long long)d * 7 * n, gam, c->sel_list[2 * d + 1],
                                                           c->sel_cnt + 2 * d + 1);
         } else {
             k_sweep<R, PLM_PRIM, HLLE, 1, float><<<sweep_grid(c, d), SWEEP_THREADS,
                                                    sweep_smem_bytes<R>(PLM_PRIM, g.tl), st>>>(
-                g, d, Wh, Bh[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam, nullptr, nullptr,
+                g, d, Wh, Bh[d], Fc + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam, nullptr, nullptr,
                 sel_of(c, 2 * d));
             k_sweep<R, PPM, HLLD, 1, float><<<sweep_grid(c, d), SWEEP_THREADS, smem, st>>>(
-                g, d, Wh, Bh[d], F1 + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam, c->sel_list[2 * d + 1],
+                g, d, Wh, Bh[d], Fc + (long long)d * 7 * n, nullptr, nullptr, c->dtc, gam, c->sel_list[2 * d + 1],
                 c->sel_cnt + 2 * d + 1);
         }
         prof_mark(c, 7 + d);
     }
     if (eu) {
         prof_mark(c, 10);
-        launch_emf_update<R, float, float, false>(c, g, s, F1, Wh, nullptr, nullptr, st);
+        launch_emf_update<R, float, float, false>(c, g, s, Fc, Wh, nullptr, nullptr, st);
     } else {
-        launch_emf<R>(c, g, F1, Wh, E, st);
+        launch_emf<R>(c, g, Fc, Wh, E, st);
         prof_mark(c, 10);
-        k_full4<R, float, float><<<c->quad_grid, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc);
+        k_full4<R, float, float><<<c->quad_grid, CELL_THREADS, 0, st>>>(g, s, Fc, E, c->dtc);
     }
     prof_mark(c, 11);
     if (c->prof_on && c->prof_steps < c->prof_cap) c->prof_steps++;

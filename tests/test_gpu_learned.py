@@ -276,3 +276,39 @@ def test_training_and_gain(env):
     assert fb > 0.3
     assert ft > 0.02
     net.free()
+
+
+@pytest.mark.parametrize("logit,scheme", [(-50.0, ("vl", "ppm", "hlld")), (50.0, ("vl", "plm_prim", "hlle"))])
+def test_selector_limits_with_the_half_update_in_the_y_corrector(env, logit, scheme):
+    """pencil-mask 231 (bit 7): the selector's step forms the half-step state
+    inside its cheap y corrector pencils, which solve every y face, the full
+    list pass overwriting its faces.  Always 'cheap' is then the plain cheap
+    scheme with the same mask bit for bit (the same kernels); always 'full'
+    is the plain full scheme with the same mask to rounding (its half-step
+    states come from another instantiation of the same arithmetic, its y
+    faces from the PPM pencil instead of the PPM walk with the half update)"""
+    torch, mhd = env
+    st = I.abc_blasts(32, kmult=2, beta=0.3, nblast=2, radius=0.1, seed=8, noise=1e-2)
+    U = st.U.astype(np.float32); Bf = st.B.astype(np.float32)
+    plain = mhd.Solver(U.shape[1:], st.dx, st.gamma, *scheme, "fp32", 0.3)
+    plain.set_sweep_pencils(231 if logit > 0 else 199, 8)   # full: its x predictor by x-warps, as above
+    plain.set_state(U, Bf)
+    plain.advance(3)
+    ref = plain.get_state()
+    plain.free()
+    net = constant_net(mhd, logit)
+    s = mhd.Solver(U.shape[1:], st.dx, st.gamma, "vl", "ppm", "hlld", "fp32", 0.3)
+    s.set_state(U, Bf)
+    s.set_selector(net)
+    s.set_sweep_pencils(231, 8)
+    assert s.launches_per_step() == 12 + 3 + 3 + 6 - 1
+    s.advance(3)
+    got = s.get_state()
+    s.free(); net.free()
+    if logit > 0:
+        assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+    else:
+        for a, b in ((got[0], ref[0]), (got[1], ref[1])):
+            for f in range(a.shape[0]):
+                den = max(np.abs(b[f]).sum(), 1e-2 * np.abs(ref[0][0]).sum())
+                assert np.abs(a[f].astype(np.float64) - b[f]).sum() / den <= 1e-5, f
