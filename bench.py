@@ -126,6 +126,7 @@ EXEC_FLOPS_PER_FACE = {"corrector": 670.0, "predictor": 393.0, "tracing": 895.0,
 # faces.  A kernel changed since its capture has none (CTU tracing and the
 # FP64 forms were re-built since theirs).
 TRAFFIC_PER_FACE = {"corrector_yhalf": {"fp32": 177.6},      # per cell (727.6 MB for 4,096,000 cells)
+                    "corrector_zfull": {"fp32": 127.0},      # per cell (520.2 MB)
                     "corrector_pencil": {"fp32": 57.3}, "corrector_xmarch": {"fp32": 55.0},
                     "predictor_pencil": {"fp32": 50.8}, "predictor_xmarch": {"fp32": 50.0},
                     "corrector_xwarp": {"fp32": 55.1},
