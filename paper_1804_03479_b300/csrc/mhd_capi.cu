@@ -52,6 +52,9 @@ static void release(mhd_ctx* c)
         free(c->prof_ev);
     }
     free(c->hbox);
+    if (c->sel_fork) cudaEventDestroy(c->sel_fork);
+    if (c->sel_join) cudaEventDestroy(c->sel_join);
+    if (c->sel_st) cudaStreamDestroy(c->sel_st);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 

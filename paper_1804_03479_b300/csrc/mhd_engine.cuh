@@ -72,6 +72,8 @@ struct mhd_ctx {
     // learned path selector (FP32 VL, one box)
     mhd_mlp* sel;
     float* sel_feats;               // [nblocks][48]
+    cudaStream_t sel_st;            // the selector's passes, beside the cheap predictor sweeps
+    cudaEvent_t sel_fork, sel_join; // (created with the selector; no timing)
     unsigned char* sel_flags;       // [nblocks], 1 = full path
     int* sel_cnt;                   // per list: entries
     int* sel_list[8];               // per axis d: [2d] one byte per unit (tile, pencil segment or x-warp

@@ -309,40 +309,71 @@ static void run_step_learned(mhd_ctx* c, bool device_dt)
     k_prim4<R, float, float><<<c->quad_grid, CELL_THREADS, 0, st>>>(g, s, W, gam, device_dt ? c->smax_part : nullptr,
                                                                      c->bad, c->sch.pfloor, c->nfloor);
     if (device_dt) k_finalize_dt<<<(c->nbox + 127) / 128, 128, 0, st>>>(g, c->smax_part, c->sch.cfl, c->dt, c->smax, c->dtc);
-    // selector: features of the current state, one inference, tile lists
-    const int fgrid = features_grid(c->hbox[0]);
-    k_block_features<R><<<fgrid, 256, 0, st>>>(c->hbox[0], W, n, (float)gam, c->sel_feats);
-    const int igrid = (int)((nblk / 16 + 8) / 8 < 1184 ? (nblk / 16 + 8) / 8 : 1184);
-    k_mlp_infer<<<igrid, 256, 0, st>>>(mlp_dev(c->sel), c->sel_feats, nblk, nullptr, c->sel_flags);
-    cudaMemsetAsync(c->sel_cnt, 0, 8 * sizeof(int), st);
     const bool xw = c->pencil_mask & 1;
     // x by aligned marching warps (bits 5 / 6): the cheap kernel solves every
     // face of the sweep (its segments are not the x-warp items of the lists)
     // and the full kernel, launched after it, overwrites the listed items
     const bool xm0 = xw && (c->pencil_mask & 32), xm1 = xw && (c->pencil_mask & 64);
+    // With the x predictor marching and y, z by pencils the cheap predictor
+    // sweeps need no list: they solve every face, the full list passes
+    // overwrite theirs after them.  The selector's passes (features,
+    // inference, classification) then run on the selector's stream beside
+    // them, and the full passes wait for it.
+    const bool ov = xm0 && (c->pencil_mask & 6) == 6 && c->sel_st;
+    cudaStream_t ss = st;
+    if (ov) {
+        cudaEventRecord(c->sel_fork, st);
+        cudaStreamWaitEvent(c->sel_st, c->sel_fork, 0);
+        ss = c->sel_st;
+    }
+    // selector: features of the current state, one inference, tile lists
+    const int fgrid = features_grid(c->hbox[0]);
+    k_block_features<R><<<fgrid, 256, 0, ss>>>(c->hbox[0], W, n, (float)gam, c->sel_feats);
+    const int igrid = (int)((nblk / 16 + 8) / 8 < 1184 ? (nblk / 16 + 8) / 8 : 1184);
+    k_mlp_infer<<<igrid, 256, 0, ss>>>(mlp_dev(c->sel), c->sel_feats, nblk, nullptr, c->sel_flags);
+    cudaMemsetAsync(c->sel_cnt, 0, 8 * sizeof(int), ss);
     // unit q (2d: axis d; 6: the x corrector's items): skip bytes sel_of(c, q),
     // full list sel_list[q + 1] with its count sel_cnt[q + 1]
     for (int d = 0; d < 3; d++) {
         if (d == 0 && xw) {
             // x by warps: the predictor's items (31 faces) in 0/1, the
             // corrector's (27 faces, shared by the cheap PLM and full PPM kernels) in 6/7
-            k_xw_classify<<<(int)((g.nxw[0] + 255) / 256 < 4096 ? (g.nxw[0] + 255) / 256 : 4096), 256, 0, st>>>(
+            k_xw_classify<<<(int)((g.nxw[0] + 255) / 256 < 4096 ? (g.nxw[0] + 255) / 256 : 4096), 256, 0, ss>>>(
                 c->hbox[0], 0, c->sel_flags, sel_of(c, 0), c->sel_list[1], c->sel_cnt + 1, g.nxw[0]);
-            k_xw_classify<<<(int)((g.nxw[2] + 255) / 256 < 4096 ? (g.nxw[2] + 255) / 256 : 4096), 256, 0, st>>>(
+            k_xw_classify<<<(int)((g.nxw[2] + 255) / 256 < 4096 ? (g.nxw[2] + 255) / 256 : 4096), 256, 0, ss>>>(
                 c->hbox[0], 2, c->sel_flags, sel_of(c, 6), c->sel_list[7], c->sel_cnt + 7, g.nxw[2]);
         } else if (c->pencil_mask >> d & 1)
-            k_seg_classify<<<(int)((g.npth[d] + 255) / 256 < 4096 ? (g.npth[d] + 255) / 256 : 4096), 256, 0, st>>>(
+            k_seg_classify<<<(int)((g.npth[d] + 255) / 256 < 4096 ? (g.npth[d] + 255) / 256 : 4096), 256, 0, ss>>>(
                 c->hbox[0], d, g.pl, c->sel_flags, sel_of(c, 2 * d), c->sel_list[2 * d + 1],
                 c->sel_cnt + 2 * d + 1, g.npth[d]);
         else
-            k_tile_classify<<<(g.ntile[d] + 255) / 256, 256, 0, st>>>(c->hbox[0], d, g.tl, c->sel_flags,
+            k_tile_classify<<<(g.ntile[d] + 255) / 256, 256, 0, ss>>>(c->hbox[0], d, g.tl, c->sel_flags,
                                                                        sel_of(c, 2 * d), c->sel_list[2 * d + 1],
                                                                        c->sel_cnt + 2 * d + 1, g.ntile[d]);
     }
+    if (ov) cudaEventRecord(c->sel_join, c->sel_st);
     prof_mark(c, 1);
     // VL steps 1-3: the cheap kernel over every unit but the marked ones
     // (x: warps marching their rows), the full kernel over the full list
-    for (int d = 0; d < 3; d++) {
+    if (ov) {
+        // the cheap sweeps over every face (their time goes to the x group),
+        // then the full passes once the lists are there
+        k_xmarch<R, PLM_PRIM, HLLE, 0, float><<<xmarch_grid(c), PENCIL_THREADS, 0, st>>>(g, W, s.b[0], F1, gam);
+        for (int d = 1; d < 3; d++)
+            launch_pencil<R, PLM_PRIM, HLLE, 0, float>(d, pencil_grid(c, d), st, g, W, s.b[d],
+                                                          F1 + (long long)d * 7 * n, gam);
+        cudaStreamWaitEvent(st, c->sel_join, 0);
+        k_xwarp<R, PPM, HLLD, 0, float><<<list_grid_xwarp(c, 0), PENCIL_THREADS, 0, st>>>(
+            g, W, s.b[0], F1, gam, 0, c->sel_list[1], c->sel_cnt + 1);
+        prof_mark(c, 2);
+        for (int d = 1; d < 3; d++) {
+            launch_pencil<R, PPM, HLLD, 0, float>(d, list_grid_pencil(c, d), st, g, W, s.b[d],
+                                                  F1 + (long long)d * 7 * n, gam, c->sel_list[2 * d + 1],
+                                                  c->sel_cnt + 2 * d + 1);
+            prof_mark(c, 2 + d);
+        }
+    }
+    for (int d = 0; d < 3 && !ov; d++) {
         if (d == 0 && xw) {
             if (xm0)
                 k_xmarch<R, PLM_PRIM, HLLE, 0, float><<<xmarch_grid(c), PENCIL_THREADS, 0, st>>>(g, W, s.b[0], F1,
@@ -495,6 +526,12 @@ extern "C" mhd_status mhd_set_selector(mhd_ctx* c, mhd_mlp* m)
                              (int)emf_tma_smem_bytes()) != cudaSuccess)
         return MHD_ECUDA;
     if (mhd_internal_selector_lists(c) != MHD_OK) return MHD_ENOMEM;
+    if (!c->sel_st) {
+        if (cudaStreamCreateWithFlags(&c->sel_st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->sel_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->sel_join, cudaEventDisableTiming) != cudaSuccess)
+            return MHD_ECUDA;
+    }
     c->sel = m;
     c->step = run_step_learned;
     mhd_internal_count_launches(c);

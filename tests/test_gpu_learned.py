@@ -312,3 +312,29 @@ def test_selector_limits_with_the_half_update_in_the_y_corrector(env, logit, sch
             for f in range(a.shape[0]):
                 den = max(np.abs(b[f]).sum(), 1e-2 * np.abs(ref[0][0]).sum())
                 assert np.abs(a[f].astype(np.float64) - b[f]).sum() / den <= 1e-5, f
+
+
+def test_selector_beside_the_cheap_sweeps_graph_and_direct(env):
+    """with the x predictor marching and y, z by pencils (masks 103, 231) the
+    selector's passes run on their own stream beside the cheap predictor
+    sweeps, which solve every face, and the full passes wait for the lists:
+    a captured graph replays the same steps bit for bit as direct launches,
+    with a network that mixes cheap and full blocks"""
+    torch, mhd = env
+    st = I.abc_blasts(32, kmult=2, beta=0.3, nblast=3, radius=0.1, seed=9, noise=1e-2)
+    U = st.U.astype(np.float32); Bf = st.B.astype(np.float32)
+    for mask in (103, 231):
+        out = []
+        for graph in (False, True):
+            net = mhd.MLP(seed=11)
+            net.set_weights(random_net(12))
+            s = mhd.Solver(U.shape[1:], st.dx, st.gamma, "vl", "ppm", "hlld", "fp32", 0.3)
+            s.set_state(U, Bf)
+            s.set_selector(net)
+            s.set_sweep_pencils(mask, 8)
+            s.advance(4, use_graph=graph)
+            fb, ft = s.selector_stats()
+            out.append(s.get_state())
+            s.free(); net.free()
+            assert 0.0 < fb < 1.0, fb
+        assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1]), mask
