@@ -316,7 +316,7 @@ static mhd_status init_common(int nbox, const mhd_grid* grids, double gamma, con
     else if (scheme->precision == MHD_FP64)
         c->pencil_mask = 23;
     else if (scheme->precision == MHD_FP32)   // PLM: the half update in the y corrector, the conservative
-        c->pencil_mask = scheme->recon != MHD_PPM ? 743 : 231;   // update in the z corrector (PLM)
+        c->pencil_mask = 743;                    // update in the z corrector (PLM, or a selector's cheap sweep)
     else
         c->pencil_mask = scheme->recon != MHD_PPM ? 487 : 359;   // mixed: and the primitives in the y predictor
     c->pencil_len = 32;

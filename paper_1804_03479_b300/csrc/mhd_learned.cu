@@ -406,6 +406,10 @@ static void run_step_learned(mhd_ctx* c, bool device_dt)
     // its faces after them); the corrector's fluxes go to the second array
     const bool yh = sel_y_half(c);
     R* Fc = yh ? (R*)c->F2 : F1;
+    // pencil-mask bits 2 and 9: the conservative update inside the cheap z
+    // corrector pencils, after the full z list pass, whose faces they read;
+    // the face field then by CT alone
+    const bool zf = yh && (c->pencil_mask & 516) == 516;
     if (eu) {
         prof_mark(c, 5);
         launch_emf_update<R, float, float, true>(c, g, s, F1, W, Bh, Wh, st);
@@ -430,6 +434,12 @@ static void run_step_learned(mhd_ctx* c, bool device_dt)
                     g, Wh, Bh[0], Fc, gam, 2, nullptr, nullptr, nullptr, nullptr, nullptr, sel_of(c, 6));
             k_xwarp<R, PPM, HLLD, 1, float><<<list_grid_xwarp(c, 2), PENCIL_THREADS, 0, st>>>(
                 g, Wh, Bh[0], Fc, gam, 2, c->sel_list[7], c->sel_cnt + 7);
+        } else if (d == 2 && zf) {
+            launch_pencil<R, PPM, HLLD, 1, float>(d, list_grid_pencil(c, d), st, g, Wh, Bh[d],
+                                                  Fc + (long long)d * 7 * n, gam, c->sel_list[2 * d + 1],
+                                                  c->sel_cnt + 2 * d + 1);
+            k_zfull<R, float, float, PLM_PRIM, HLLE><<<pencil_grid(c, 2), PENCIL_THREADS, 0, st>>>(
+                g, s, Wh, Bh[2], Fc, c->dtc, gam, sel_of(c, 2 * d));
         } else if (c->pencil_mask >> d & 1) {
             if (!(d == 1 && yh))     // (y: the cheap faces were solved with the half update)
                 launch_pencil<R, PLM_PRIM, HLLE, 1, float>(d, pencil_grid(c, d), st, g, Wh, Bh[d],
@@ -455,7 +465,10 @@ static void run_step_learned(mhd_ctx* c, bool device_dt)
     } else {
         launch_emf<R>(c, g, Fc, Wh, E, st);
         prof_mark(c, 10);
-        k_full4<R, float, float><<<c->quad_grid, CELL_THREADS, 0, st>>>(g, s, Fc, E, c->dtc);
+        if (zf)
+            k_ct4<R, float, float><<<c->quad_grid, CELL_THREADS, 0, st>>>(g, s, E, c->dtc);
+        else
+            k_full4<R, float, float><<<c->quad_grid, CELL_THREADS, 0, st>>>(g, s, Fc, E, c->dtc);
     }
     prof_mark(c, 11);
     if (c->prof_on && c->prof_steps < c->prof_cap) c->prof_steps++;

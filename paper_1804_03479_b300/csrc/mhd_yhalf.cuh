@@ -358,7 +358,7 @@ __device__ __forceinline__ void full_hydro(TU rho0, TU mx0, TU my0, TU mz0, TE e
 template <class R, class TU, class TE, int RECON, int SOLVER>
 __global__ void __launch_bounds__(PENCIL_THREADS, (sweep_min_blocks<R, RECON, SOLVER, 1>()))
 k_zfull(Boxes B, StateP<TU, TE> s, const R* __restrict__ Wh, const TE* __restrict__ Bhz, R* __restrict__ F,
-        const DtBox* __restrict__ dtb, double gam)
+        const DtBox* __restrict__ dtb, double gam, const unsigned char* __restrict__ skip = nullptr)
 {
     static_assert(RECON != PPM, "the fused walk reconstructs PLM stencils only");
     constexpr int d = 2;
@@ -387,6 +387,14 @@ k_zfull(Boxes B, StateP<TU, TE> s, const R* __restrict__ Wh, const TE* __restric
     const TU ru = DtOf<TU>::dtdx(dtb[bi]);
     const R gr = R(gam), gm1 = R(gam - 1.0);
     R* Fz = F + 14 * N;
+    // The learned selector's step (skip given): the segments it marks full
+    // had their faces solved by the full scheme's list pass, launched before
+    // this kernel; their fluxes are read from F instead of this walk's, and
+    // not stored.  The face past a segment belongs to the next segment of the
+    // line (the first one past the line's end), and is read from F when that
+    // one is marked.
+    const bool full = skip && skip[gt];
+    const bool next_full = skip && skip[g.pth0[d] + ix + (long long)na * (iy + (long long)nb * ((sg + 1) % ns))];
     // cell c (line cell i - 1) from its two z fluxes fl (lower) and fu (upper)
     auto update = [&](long long c, const R fl[7], const R fu[7]) {
         R fc[3][5], fn[3][5];
@@ -433,7 +441,10 @@ k_zfull(Boxes B, StateP<TU, TE> s, const R* __restrict__ Wh, const TE* __restric
         if (i < i1) load_rot(Wh, N, pcell(p, i + 2), d, wn, bnn);
         recon_cell<RECON, false>(wa, wb, wc, bnb, gr, dum, dum, dum, R(0), wm, wp);
         riemann<SOLVER>(wpp, wm, R(Bhz[ci]), gm1, gr, f);
-        if (i < i1) {                       // the components the edge fields read
+        if (i < i1 ? full : next_full) {    // the full scheme's face
+#pragma unroll
+            for (int m = 0; m < 5; m++) f[m] = Fz[(long long)m * N + ci];
+        } else if (i < i1) {                // the components the edge fields read
             Fz[ci] = f[0];
             Fz[5 * N + ci] = f[5];
             Fz[6 * N + ci] = f[6];

@@ -278,20 +278,24 @@ def test_training_and_gain(env):
     net.free()
 
 
+@pytest.mark.parametrize("mask", [231, 743])
 @pytest.mark.parametrize("logit,scheme", [(-50.0, ("vl", "ppm", "hlld")), (50.0, ("vl", "plm_prim", "hlle"))])
-def test_selector_limits_with_the_half_update_in_the_y_corrector(env, logit, scheme):
+def test_selector_limits_with_the_half_update_in_the_y_corrector(env, logit, scheme, mask):
     """pencil-mask 231 (bit 7): the selector's step forms the half-step state
     inside its cheap y corrector pencils, which solve every y face, the full
-    list pass overwriting its faces.  Always 'cheap' is then the plain cheap
+    list pass overwriting its faces.  743 (bit 9 as well): the cheap z
+    corrector pencils also do the conservative update, after the full z list
+    pass, whose faces they read.  Always 'cheap' is then the plain cheap
     scheme with the same mask bit for bit (the same kernels); always 'full'
     is the plain full scheme with the same mask to rounding (its half-step
     states come from another instantiation of the same arithmetic, its y
-    faces from the PPM pencil instead of the PPM walk with the half update)"""
+    faces from the PPM pencil instead of the PPM walk with the half update,
+    its conservative update from the z pencils instead of the update kernel)"""
     torch, mhd = env
     st = I.abc_blasts(32, kmult=2, beta=0.3, nblast=2, radius=0.1, seed=8, noise=1e-2)
     U = st.U.astype(np.float32); Bf = st.B.astype(np.float32)
     plain = mhd.Solver(U.shape[1:], st.dx, st.gamma, *scheme, "fp32", 0.3)
-    plain.set_sweep_pencils(231 if logit > 0 else 199, 8)   # full: its x predictor by x-warps, as above
+    plain.set_sweep_pencils(mask if logit > 0 else mask - 32, 8)   # full: its x predictor by x-warps, as above
     plain.set_state(U, Bf)
     plain.advance(3)
     ref = plain.get_state()
@@ -300,7 +304,7 @@ def test_selector_limits_with_the_half_update_in_the_y_corrector(env, logit, sch
     s = mhd.Solver(U.shape[1:], st.dx, st.gamma, "vl", "ppm", "hlld", "fp32", 0.3)
     s.set_state(U, Bf)
     s.set_selector(net)
-    s.set_sweep_pencils(231, 8)
+    s.set_sweep_pencils(mask, 8)
     assert s.launches_per_step() == 12 + 3 + 3 + 6 - 1
     s.advance(3)
     got = s.get_state()
@@ -323,7 +327,7 @@ def test_selector_beside_the_cheap_sweeps_graph_and_direct(env):
     torch, mhd = env
     st = I.abc_blasts(32, kmult=2, beta=0.3, nblast=3, radius=0.1, seed=9, noise=1e-2)
     U = st.U.astype(np.float32); Bf = st.B.astype(np.float32)
-    for mask in (103, 231):
+    for mask in (103, 231, 743):
         out = []
         for graph in (False, True):
             net = mhd.MLP(seed=11)

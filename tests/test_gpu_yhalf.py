@@ -330,7 +330,7 @@ def test_mask_range_defaults_and_fallbacks(M):
     PPM (bit 9), a pressure floor (bit 8), outflow boundaries or without
     bit 1 the separate kernels run"""
     st = I.abc(16, kmult=1, beta=0.5, seed=85)
-    for prec, recon, mask, nl in [("fp32", "plm", FUSED32 | ZFULL, 11), ("fp32", "ppm", FUSED32, 11),
+    for prec, recon, mask, nl in [("fp32", "plm", FUSED32 | ZFULL, 11), ("fp32", "ppm", FUSED32 | ZFULL, 11),
                                   ("mixed", "plm_prim", FUSED32 | PRIM, 10), ("mixed", "ppm", 103 | PRIM, 11),
                                   ("fp64", "plm", 23, 12)]:
         s = M.Solver(st.U.shape[1:], st.dx, st.gamma, "vl", recon, "roe", prec, 0.3)
