@@ -283,9 +283,10 @@ mhd_status mhd_get_dirichlet(mhd_ctx* ctx, int axis, int* nlayers);
  * whose FP64 primitive arithmetic then overlaps the sweep (256^3 PLM +
  * Roe: 0.718 ms against 0.644 + 0.307); in FP32 and FP64 it ties the two
  * kernels.
- * Bit 9 with bit 2 (VL with a PLM reconstruction; with a learned selector
- * and bit 7 as well, its cheap PLM z corrector, which runs after the full
- * z list pass and reads the marked segments' faces; ignored otherwise):
+ * Bit 9 with bit 2 (VL, every box periodic, bit 3 clear, the edge fields as
+ * their own kernel; with a learned selector and bit 7 as well, its cheap
+ * PLM z corrector, which runs after the full z list pass and reads the
+ * marked segments' faces; ignored otherwise):
  * the conservative part of the full update (Eq. 10 for rho, M
  * and e with dt) runs inside the corrector's z pencils, the last corrector
  * sweep: each thread updates the cells of its segment in place once it has
@@ -295,9 +296,8 @@ mhd_status mhd_get_dirichlet(mhd_ctx* ctx, int axis, int* nlayers);
  * field advances by CT (Eq. 13) in a kernel that reads only E and B.  At
  * 256^3 FP32 Roe the step takes 3.58 ms against 3.67.
  * pencil_mask in [0, 1023] (0: tiles everywhere), pencil_len in [1, 1024],
- * else MHD_EINVAL.  Defaults (pencil_len 32): VL FP64 23; VL FP32 743 (with
- * PPM bit 9 serves a selector only); VL mixed 487 with PLM, 359 with PPM;
- * CTU 39. */
+ * else MHD_EINVAL.  Defaults (pencil_len 32): VL FP64 23; VL FP32 743; VL
+ * mixed 487 with PLM, 359 with PPM; CTU 39. */
 mhd_status mhd_set_sweep_pencils(mhd_ctx* ctx, int pencil_mask, int pencil_len);
 mhd_status mhd_get_sweep_pencils(mhd_ctx* ctx, int* pencil_mask, int* pencil_len);
 

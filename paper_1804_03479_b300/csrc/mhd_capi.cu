@@ -987,7 +987,9 @@ extern "C" mhd_status mhd_autotune(mhd_ctx* c, int reps, int* tile_len, int* blo
             } else {
                 vl_masks[8] = 231;
                 vl_masks[9] = 487;
-                nvl = 10;
+                vl_masks[10] = 743;
+                vl_masks[11] = 999;
+                nvl = 12;
             }
         }
         const int nmask = ctu ? 3 : (c->sel ? 2 : (!c->bc ? nvl : 4));

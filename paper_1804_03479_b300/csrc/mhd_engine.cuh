@@ -318,12 +318,12 @@ inline bool y_prim(const mhd_ctx* c)
 
 // the conservative part of the VL full update inside the corrector's z
 // pencils (k_zfull), the face field by CT alone after the edge fields (k_ct /
-// k_ct4), with pencil-mask bits 2 and 9: as y_half (PLM, periodic boxes, no
+// k_ct4), with pencil-mask bits 2 and 9: as y_half (periodic boxes, no
 // selector, the predictor and the edge fields as separate kernels)
 inline bool z_full(const mhd_ctx* c)
 {
-    return c->sch.recon != MHD_PPM && (c->pencil_mask & 516) == 516 && c->sch.integrator == MHD_VL && !c->bc &&
-           !c->sel && !fused_predictor(c) && emf_form(c) == 0;
+    return (c->pencil_mask & 516) == 516 && c->sch.integrator == MHD_VL && !c->bc && !c->sel &&
+           !fused_predictor(c) && emf_form(c) == 0;
 }
 
 template <class R, class TU, class TE>
@@ -517,15 +517,13 @@ void run_step(mhd_ctx* c, bool device_dt)
         // update; the corrector's fluxes go to F2 when the y sweep ran fused
         // with the half update (the predictor's F1 was read while it ran)
         R* Fc = yh ? F2 : F1;
-        const bool zf = RECON != PPM && z_full(c);
+        const bool zf = z_full(c);
         for (int d = 0; d < 3; d++) {
             if (d == 1 && yh)
                 ;                                       // done with the half update
-            else if (d == 2 && zf) {                    // with the conservative full update
-                if constexpr (RECON != PPM)
-                    k_zfull<R, TU, TE, RECON, SOLVER><<<pencil_grid(c, 2), PENCIL_THREADS, 0, st>>>(
-                        g, s, Wh, Bh[2], Fc, c->dtc, gam);
-            }
+            else if (d == 2 && zf)                      // with the conservative full update
+                k_zfull<R, TU, TE, RECON, SOLVER><<<pencil_grid(c, 2), PENCIL_THREADS, 0, st>>>(
+                    g, s, Wh, Bh[2], Fc, c->dtc, gam);
             else if (d == 0 && x_pencils(c))
                 launch_xpencil<R, RECON, SOLVER, 1, TE>(c, g, Wh, Bh[0], Fc, st);
             else if (d == 0 && x_march<RECON, 1>(c))

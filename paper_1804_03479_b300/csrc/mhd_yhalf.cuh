@@ -360,7 +360,6 @@ __global__ void __launch_bounds__(PENCIL_THREADS, (sweep_min_blocks<R, RECON, SO
 k_zfull(Boxes B, StateP<TU, TE> s, const R* __restrict__ Wh, const TE* __restrict__ Bhz, R* __restrict__ F,
         const DtBox* __restrict__ dtb, double gam, const unsigned char* __restrict__ skip = nullptr)
 {
-    static_assert(RECON != PPM, "the fused walk reconstructs PLM stencils only");
     constexpr int d = 2;
     const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (gt >= B.npth[d]) return;
@@ -421,6 +420,62 @@ k_zfull(Boxes B, StateP<TU, TE> s, const R* __restrict__ Wh, const TE* __restric
         s.m[2][c] = u[3];
         s.e[c] = e;
     };
+    // face i's flux f: the full scheme's (read) or this walk's (its own
+    // faces' components stored); then the update of cell i - 1
+    R f[7], fprev[7];
+    auto face_done = [&](int i, long long ci) {
+        if (i < i1 ? full : next_full) {    // the full scheme's face
+#pragma unroll
+            for (int m = 0; m < 5; m++) f[m] = Fz[(long long)m * N + ci];
+        } else if (i < i1) {                // the components the edge fields read
+            Fz[ci] = f[0];
+            Fz[5 * N + ci] = f[5];
+            Fz[6 * N + ci] = f[6];
+        }
+        if (i > i0) update(pcell(p, i - 1), fprev, f);
+        copy7(fprev, f);
+    };
+    if constexpr (RECON == PPM) {
+        // PPM walk as the corrector pencil, one face further: cells i-1 ..
+        // i+2 and the slopes of i-1 .. i+1, wpp the "+" state of cell i-1;
+        // the cell i+3 loaded while face i is solved
+        R w0[7], w1[7], w2[7], w3[7], wq[7], b0, b1, b2, b3, bq, s0[7], s1[7], s2[7], wpp[7], wm[7], wp[7];
+        load_rot(Wh, N, pcell(p, i0 - 3), d, wq, bq);
+        load_rot(Wh, N, pcell(p, i0 - 2), d, w0, b0);
+        load_rot(Wh, N, pcell(p, i0 - 1), d, w1, b1);
+        load_rot(Wh, N, pcell(p, i0), d, w2, b2);
+        load_rot(Wh, N, pcell(p, i0 + 1), d, w3, b3);
+        char_slope(wq, w0, w1, b0, gr, s0);                 // slope of i0 - 2
+        char_slope(w0, w1, w2, b1, gr, s1);                 // i0 - 1
+        char_slope(w1, w2, w3, b2, gr, s2);                 // i0
+        recon_cell<PPM, false>(w0, w1, w2, b1, gr, s0, s1, s2, R(0), wm, wpp);   // "+" of cell i0 - 1
+        copy7(w0, w1); b0 = b1;
+        copy7(w1, w2); b1 = b2;
+        copy7(w2, w3); b2 = b3;
+        copy7(s0, s1);
+        copy7(s1, s2);
+        R wn[7], bnn;
+        load_rot(Wh, N, pcell(p, i0 + 2), d, wn, bnn);
+        for (int i = i0; i <= i1; i++) {
+            const long long ci = pcell(p, i);
+            copy7(w3, wn);
+            b3 = bnn;
+            if (i < i1) load_rot(Wh, N, pcell(p, i + 3), d, wn, bnn);
+            char_slope(w1, w2, w3, b2, gr, s2);             // slope of i + 1
+            recon_cell<PPM, false>(w0, w1, w2, b1, gr, s0, s1, s2, R(0), wm, wp);
+            riemann<SOLVER>(wpp, wm, R(Bhz[ci]), gm1, gr, f);
+            face_done(i, ci);
+            copy7(wpp, wp);
+            copy7(w0, w1); b0 = b1;
+            copy7(w1, w2); b1 = b2;
+            copy7(w2, w3); b2 = b3;
+            copy7(s0, s1);
+            copy7(s1, s2);
+        }
+        (void)bq;
+        (void)b0;
+        return;
+    }
     // PLM walk as the corrector pencil, one face further: cells i-1, i, i+1
     // in registers, wpp the "+" state of cell i-1; the cell i+2 loaded while
     // face i is solved
@@ -432,7 +487,7 @@ k_zfull(Boxes B, StateP<TU, TE> s, const R* __restrict__ Wh, const TE* __restric
     recon_cell<RECON, false>(wa, wb, wc, bnb, gr, dum, dum, dum, R(0), wm, wpp);   // "+" of cell i0 - 1
     copy7(wa, wb); bna = bnb;
     copy7(wb, wc); bnb = bnc;
-    R wn[7], bnn, f[7], fprev[7];
+    R wn[7], bnn;
     load_rot(Wh, N, pcell(p, i0 + 1), d, wn, bnn);
     for (int i = i0; i <= i1; i++) {
         const long long ci = pcell(p, i);
@@ -441,16 +496,7 @@ k_zfull(Boxes B, StateP<TU, TE> s, const R* __restrict__ Wh, const TE* __restric
         if (i < i1) load_rot(Wh, N, pcell(p, i + 2), d, wn, bnn);
         recon_cell<RECON, false>(wa, wb, wc, bnb, gr, dum, dum, dum, R(0), wm, wp);
         riemann<SOLVER>(wpp, wm, R(Bhz[ci]), gm1, gr, f);
-        if (i < i1 ? full : next_full) {    // the full scheme's face
-#pragma unroll
-            for (int m = 0; m < 5; m++) f[m] = Fz[(long long)m * N + ci];
-        } else if (i < i1) {                // the components the edge fields read
-            Fz[ci] = f[0];
-            Fz[5 * N + ci] = f[5];
-            Fz[6 * N + ci] = f[6];
-        }
-        if (i > i0) update(pcell(p, i - 1), fprev, f);
-        copy7(fprev, f);
+        face_done(i, ci);
         copy7(wpp, wp);
         copy7(wa, wb); bna = bnb;
         copy7(wb, wc); bnb = bnc;

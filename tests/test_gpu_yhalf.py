@@ -94,7 +94,7 @@ def parity(M, st, scheme, nsteps, mask=FUSED64, plen=32, pfloor=0.0, tol=1e-12, 
 VL = [("vl", r, s) for r in ("plm", "ppm", "plm_prim") for s in ("roe", "hlld", "hlle")]
 
 
-@pytest.mark.parametrize("scheme", PLM)
+@pytest.mark.parametrize("scheme", PLM + [("vl", "ppm", s) for s in ("roe", "hlld", "hlle")])
 def test_zfull_fp64_parity(M, scheme):
     """bit 9 alone, and with bits 7 and 8 (the corrector fluxes in the second
     array), against the oracle"""
@@ -112,6 +112,7 @@ def test_zfull_fp64_parity_ragged_short(M, shape, plen):
     L = max(shape[1], 1) / 16.0
     st = I.abc(None, kmult=L, beta=0.5, seed=90, noise=3e-2, shape=shape, L=L)
     parity(M, st, ("vl", "plm", "roe"), 2, mask=23 | ZFULL | 128, plen=plen)
+    parity(M, st, ("vl", "ppm", "hlld"), 2, mask=23 | ZFULL, plen=plen)
 
 
 def test_zfull_fp64_batch(M):
@@ -142,7 +143,7 @@ def test_zfull_fp64_batch(M):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "mixed"])
-@pytest.mark.parametrize("scheme", [("vl", "plm", "roe"), ("vl", "plm_prim", "hlld")])
+@pytest.mark.parametrize("scheme", [("vl", "plm", "roe"), ("vl", "plm_prim", "hlld"), ("vl", "ppm", "hlld")])
 def test_zfull_agrees_with_the_full_update(M, prec, scheme):
     """three graph-replayed steps with bits 7, 8 and 9 against the separate
     kernels (quad-aligned box and a 33-wide one)"""
@@ -359,7 +360,7 @@ def test_mask_range_defaults_and_fallbacks(M):
     s = M.Solver(st.U.shape[1:], st.dx, st.gamma, "vl", "ppm", "roe", "fp32", 0.3)
     try:
         s.set_sweep_pencils(FUSED32 | PRIM | ZFULL, 32)
-        assert s.launches_per_step() == 10         # PPM: bit 9 does not apply
+        assert s.launches_per_step() == 10         # (bit 9: the same count)
     finally:
         s.free()
     s = M.Solver(st.U.shape[1:], st.dx, st.gamma, "vl", "plm", "roe", "mixed", 0.3, pfloor=1e-6)
