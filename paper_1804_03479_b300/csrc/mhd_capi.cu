@@ -310,9 +310,13 @@ static mhd_status init_common(int nbox, const mhd_grid* grids, double gamma, con
     // update inside the z corrector pencils and the face field by CT alone
     // (bit 9; 256^3 Roe: z corrector 0.468 -> 0.685 ms, full update 0.412 ->
     // 0.098, step 3.67 -> 3.58 ms); the mixed form (5.43 -> 5.51 ms) and FP64
-    // (144.0 -> 144.8 ms) lose with it.  The autotuner may change the mask.
-    if (scheme->integrator != MHD_VL)
-        c->pencil_mask = 39;
+    // (144.0 -> 144.8 ms) lose with it.  CTU FP32 and mixed run the dt/2
+    // update inside the y pencils of the transverse correction (bit 7; 256^3
+    // PLM + Roe 5.32 -> 5.22 ms, PPM + HLLD 6.23 -> 6.09, mixed 7.11 -> 6.79);
+    // FP64 ties (128^3: 24.65 against 24.69 ms) and keeps 39.  The autotuner
+    // may change the mask.
+    if (scheme->integrator != MHD_VL)   // FP32, mixed: the dt/2 update in the y correction (bit 7)
+        c->pencil_mask = scheme->precision == MHD_FP64 ? 39 : 167;
     else if (scheme->precision == MHD_FP64)
         c->pencil_mask = 23;
     else if (scheme->precision == MHD_FP32)   // PLM: the half update in the y corrector, the conservative
@@ -752,7 +756,7 @@ static void count_launches(mhd_ctx* c)
     // (CTU: one stage-1 outer-face pass per outflow axis; the stage-2 ones
     // are part of the corrections)
     // (the y corrector takes the half update, the y predictor the primitives)
-    int n = fused_predictor(c) ? 8 : 12 - (y_half(c) ? 1 : 0) - (y_prim(c) ? 1 : 0);
+    int n = fused_predictor(c) ? 8 : 12 - (y_half(c) || ctu_y_half(c) ? 1 : 0) - (y_prim(c) ? 1 : 0);
     if (emf_form(c) == 2) n -= fused_predictor(c) ? 1 : 2;   // each edge-field kernel takes its update
     const int per_axis = c->sch.integrator == MHD_VL ? 2 : 1;
     for (int d = 0; d < 3; d++) n += per_axis * (c->bc >> d & 1) + (c->fix_nl[d] > 0);
@@ -971,7 +975,7 @@ extern "C" mhd_status mhd_autotune(mhd_ctx* c, int reps, int* tile_len, int* blo
         // corrector pencils, bit 7, when its flux array can be had, and for
         // PLM with the conservative update inside the z corrector, bit 9)
         int vl_masks[12] = {7, 6, 23, 103, 15, 31, 111, 359, 0, 0, 0, 0};
-        const int ctu_masks[3] = {7, 6, 39};
+        const int ctu_masks[4] = {7, 6, 39, 167};      // (167: bit 7, the dt/2 update in the y correction)
         const bool ctu = c->sch.integrator != MHD_VL;
         const int* masks = ctu ? ctu_masks : vl_masks;
         const int lens[3] = {8, 16, 32};
@@ -992,7 +996,7 @@ extern "C" mhd_status mhd_autotune(mhd_ctx* c, int reps, int* tile_len, int* blo
                 nvl = 12;
             }
         }
-        const int nmask = ctu ? 3 : (c->sel ? 2 : (!c->bc ? nvl : 4));
+        const int nmask = ctu ? (!c->bc ? 4 : 3) : (c->sel ? 2 : (!c->bc ? nvl : 4));
         c->sweep_bps = bbps;
         for (int i = 0; i < nmask && st == MHD_OK; i++)
             for (int j = 0; j < 3 && st == MHD_OK; j++) {

@@ -299,6 +299,14 @@ inline bool y_half(const mhd_ctx* c)
            !fused_predictor(c) && emf_form(c) == 0;
 }
 
+// CTU: the dt/2 update inside the y pencils of the transverse correction
+// (k_ctu_yhalf) with pencil-mask bits 1 and 7: periodic boxes, the edge
+// fields as their own kernel
+inline bool ctu_y_half(const mhd_ctx* c)
+{
+    return c->sch.integrator == MHD_CTU && (c->pencil_mask & 130) == 130 && !c->bc && emf_form(c) == 0;
+}
+
 // the learned selector's step: the half update inside the cheap y corrector
 // pencils with pencil-mask bits 1 and 7 (the second flux array allocated,
 // the edge fields as their own kernel)
@@ -606,16 +614,21 @@ void run_step(mhd_ctx* c, bool device_dt)
             if (c->bc >> d & 1)
                 k_outer_flux_traced<R, SOLVER, TE><<<(cs + 127) / 128, 128, 0, st>>>(
                     c->hbox[0], d, WP + (long long)d * 7 * n, WM + (long long)d * 7 * n, s.b[d], gam, n, fo1, cs);
+        const bool cyh = ctu_y_half(c);
         if (c->bc)
             k_half<R, TU, TE, true><<<nb, CELL_THREADS, 0, st>>>(g, s, F1, E, c->dtc, gam, Bh[0], Bh[1], Bh[2], Wh,
                                                                  c->sch.pfloor, fo1, cs);
+        else if (cyh)           // the dt/2 update with the y correction (its time: the half group)
+            k_ctu_yhalf<R, TU, TE, SOLVER><<<pencil_grid(c, 1), PENCIL_THREADS, 0, st>>>(
+                g, s, WM + (long long)7 * n, WP + (long long)7 * n, W, F1, E, F2 + (long long)7 * n, c->dtc, gam,
+                c->sch.pfloor, Bh[0], Bh[1], Bh[2], Wh);
         else if (!eu)
             launch_half<R, TU, TE>(c, g, s, F1, E, Bh, Wh, st);
         prof_mark(c, 6);
         // steps 5-6: transverse correction and corrector fluxes
         ctu_correct_axis<R, SOLVER, TE, 0>(c, g, WM, WP, W, F1, Bh[0], F2, gam, fo1, cs, fo2, st);
         prof_mark(c, 7);
-        ctu_correct_axis<R, SOLVER, TE, 1>(c, g, WM, WP, W, F1, Bh[1], F2, gam, fo1, cs, fo2, st);
+        if (!cyh) ctu_correct_axis<R, SOLVER, TE, 1>(c, g, WM, WP, W, F1, Bh[1], F2, gam, fo1, cs, fo2, st);
         prof_mark(c, 8);
         ctu_correct_axis<R, SOLVER, TE, 2>(c, g, WM, WP, W, F1, Bh[2], F2, gam, fo1, cs, fo2, st);
         prof_mark(c, 9);

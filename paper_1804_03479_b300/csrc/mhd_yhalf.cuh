@@ -68,6 +68,71 @@ struct YCarry {
     R ex, ez, ezx, exz;
 };
 
+// the half-step state of cell c (its y + 1 neighbour cy, x + 1 and z + 1
+// offsets ox, oz) with k_half's arithmetic: the primitives w8 and the three
+// lower half-step faces lo; Y holds what it shares with the cell below along
+// y and leaves what the cell above takes from it
+template <class R, class TU, class TE>
+__device__ __forceinline__ void yhalf_state(const StateP<TU, TE>& s, const R* __restrict__ Fp,
+                                            const R* __restrict__ E, long long N, long long c, long long cy,
+                                            long long ox, long long oz, TE r, TU ru, double gam, double pfloor,
+                                            YCarry<R, TE>& Y, R w8[8], TE lo[3])
+{
+    R fc[3][5], fn[3][5];
+#pragma unroll
+    for (int m = 0; m < 5; m++) {
+        fc[0][m] = Fp[(long long)m * N + c];
+        fn[0][m] = Fp[(long long)m * N + c + ox];
+        fc[1][m] = Y.fy[m];
+        fn[1][m] = Fp[(7LL + m) * N + cy];
+        fc[2][m] = Fp[(14LL + m) * N + c];
+        fn[2][m] = Fp[(14LL + m) * N + c + oz];
+    }
+    const R ec[3] = {Y.ex, E[N + c], Y.ez};
+    R en[3][3];
+    en[0][1] = E[cy];
+    en[0][2] = Y.exz;
+    en[1][0] = E[N + c + ox];
+    en[1][2] = E[N + c + oz];
+    en[2][0] = Y.ezx;
+    en[2][1] = E[2 * N + cy];
+    en[0][0] = en[1][1] = en[2][2] = R(0);   // unused
+    const R e2xy = E[2 * N + cy + ox], e1xz = E[N + c + ox + oz], e0yz = E[cy + oz];
+    const TE blo[3] = {s.b[0][c], Y.by, s.b[2][c]};
+    const TE bhi[3] = {s.b[0][c + ox], s.b[1][cy], s.b[2][c + oz]};
+    const TU rho0 = s.rho[c], mx0 = s.m[0][c], my0 = s.m[1][c], mz0 = s.m[2][c];
+    const TE e0 = s.e[c];
+    TE bc[3];
+    half_faces<TE, R>(ec, en, e2xy, e1xz, e0yz, blo, bhi, r, lo, bc);
+    TU du[4];
+    TE due;
+    flux_divergence<R, TU, TE>(fc, fn, du, due);
+    half_prims<R, TU, TE>(rho0, mx0, my0, mz0, e0, du, due, ru, r, bc, gam, pfloor, w8);
+    // the next cell's operands from below
+#pragma unroll
+    for (int m = 0; m < 5; m++) Y.fy[m] = fn[1][m];
+    Y.by = bhi[1];
+    Y.ex = en[0][1];
+    Y.ez = en[2][1];
+    Y.ezx = e2xy;
+    Y.exz = e0yz;
+}
+
+// the carry of the walk's first cell c
+template <class R, class TU, class TE>
+__device__ __forceinline__ void yhalf_carry(const StateP<TU, TE>& s, const R* __restrict__ Fp,
+                                            const R* __restrict__ E, long long N, long long c, long long ox,
+                                            long long oz, YCarry<R, TE>& Y)
+{
+#pragma unroll
+    for (int m = 0; m < 5; m++) Y.fy[m] = Fp[(7LL + m) * N + c];
+    Y.by = s.b[1][c];
+    Y.ex = E[c];
+    Y.ez = E[2 * N + c];
+    Y.ezx = E[2 * N + c + ox];
+    Y.exz = E[c + oz];
+}
+
 // register bound: as the PLM corrector pencils it extends (FP32 Roe: 4
 // blocks of 128 threads, 128 registers with 16 bytes spilled; at 3 blocks
 // and 167 registers it ran 0.760 against 0.708 ms at 256^3)
@@ -106,55 +171,17 @@ k_yhalf(Boxes B, StateP<TU, TE> s, const R* __restrict__ Fp, const R* __restrict
     const TU ru = DtOf<TU>::hdtdx(dtb[bi]);
     const R gr = R(gam), gm1 = R(gam - 1.0);
 
-    YCarry<R, TE> Y;
-    {
-        // the walk's first cell: two lead-in cells for PLM, three for PPM
-        const long long c = base + (long long)wrapi(i0 - (RECON == PPM ? 3 : 2), ny) * nx;
-#pragma unroll
-        for (int m = 0; m < 5; m++) Y.fy[m] = Fp[(7LL + m) * N + c];
-        Y.by = s.b[1][c];
-        Y.ex = E[c];
-        Y.ez = E[2 * N + c];
-        Y.ezx = E[2 * N + c + ox];
-        Y.exz = E[c + oz];
-    }
+    YCarry<R, TE> Y;   // the walk's first cell: two lead-in cells for PLM, three for PPM
+    yhalf_carry<R, TU, TE>(s, Fp, E, N, base + (long long)wrapi(i0 - (RECON == PPM ? 3 : 2), ny) * nx, ox, oz, Y);
     // the half-step state of line cell i (the next one along the walk after
     // the previous call): w and bn in the y sweep frame, lo the lower y face;
     // stored when the segment owns the cell
     auto half_cell = [&](int i, R w[7], R& bn, TE& lo_y) {
         const long long c = base + (long long)wrapi(i, ny) * nx;
         const long long cy = base + (long long)wrapi(i + 1, ny) * nx;
-        R fc[3][5], fn[3][5];
-#pragma unroll
-        for (int m = 0; m < 5; m++) {
-            fc[0][m] = Fp[(long long)m * N + c];
-            fn[0][m] = Fp[(long long)m * N + c + ox];
-            fc[1][m] = Y.fy[m];
-            fn[1][m] = Fp[(7LL + m) * N + cy];
-            fc[2][m] = Fp[(14LL + m) * N + c];
-            fn[2][m] = Fp[(14LL + m) * N + c + oz];
-        }
-        const R ec[3] = {Y.ex, E[N + c], Y.ez};
-        R en[3][3];
-        en[0][1] = E[cy];
-        en[0][2] = Y.exz;
-        en[1][0] = E[N + c + ox];
-        en[1][2] = E[N + c + oz];
-        en[2][0] = Y.ezx;
-        en[2][1] = E[2 * N + cy];
-        en[0][0] = en[1][1] = en[2][2] = R(0);   // unused
-        const R e2xy = E[2 * N + cy + ox], e1xz = E[N + c + ox + oz], e0yz = E[cy + oz];
-        const TE blo[3] = {s.b[0][c], Y.by, s.b[2][c]};
-        const TE bhi[3] = {s.b[0][c + ox], s.b[1][cy], s.b[2][c + oz]};
-        const TU rho0 = s.rho[c], mx0 = s.m[0][c], my0 = s.m[1][c], mz0 = s.m[2][c];
-        const TE e0 = s.e[c];
-        TE lo[3], bc[3];
-        half_faces<TE, R>(ec, en, e2xy, e1xz, e0yz, blo, bhi, r, lo, bc);
-        TU du[4];
-        TE due;
-        flux_divergence<R, TU, TE>(fc, fn, du, due);
         R w8[8];
-        half_prims<R, TU, TE>(rho0, mx0, my0, mz0, e0, du, due, ru, r, bc, gam, pfloor, w8);
+        TE lo[3];
+        yhalf_state<R, TU, TE>(s, Fp, E, N, c, cy, ox, oz, r, ru, gam, pfloor, Y, w8, lo);
         if (i >= i0 && i < i1) {
             Bh0[c] = lo[0];
             Bh1[c] = lo[1];
@@ -167,14 +194,6 @@ k_yhalf(Boxes B, StateP<TU, TE> s, const R* __restrict__ Fp, const R* __restrict
         w[4] = w8[4]; w[5] = w8[7]; w[6] = w8[5];
         bn = w8[6];
         lo_y = lo[1];
-        // the next cell's operands from below
-#pragma unroll
-        for (int m = 0; m < 5; m++) Y.fy[m] = fn[1][m];
-        Y.by = bhi[1];
-        Y.ex = en[0][1];
-        Y.ez = en[2][1];
-        Y.ezx = e2xy;
-        Y.exz = e0yz;
     };
 
     if constexpr (RECON == PPM) {
@@ -614,6 +633,83 @@ __global__ void __launch_bounds__(CELL_THREADS) k_ct4(Boxes B, StateP<TU, TE> s,
         st4(s.b[0] + c, o0);
         st4(s.b[1] + c, o1);
         st4(s.b[2] + c, o2);
+    }
+}
+
+// CTU (Sec. 3.2, steps 3-6 along y): the dt/2 update (k_half's arithmetic,
+// through yhalf_state) inside the y pencils of the transverse correction and
+// corrector solve (k_ctu_pencil's arithmetic).  The correction of a y face
+// takes the half-step normal field of the face's cell, which the walk forms
+// with the cell's whole half-step state; each cell is formed once, by the
+// segment that owns it, which stores its half-step primitives and faces for
+// the x and z corrections and the corrector's edge fields.  Periodic boxes.
+template <class R, class TU, class TE, int SOLVER>
+__global__ void __launch_bounds__(PENCIL_THREADS, (sizeof(R) == 4 && SOLVER == ROE ? 4 : 0))
+k_ctu_yhalf(Boxes B, StateP<TU, TE> s, const R* __restrict__ WM, const R* __restrict__ WP, const R* __restrict__ W,
+            const R* __restrict__ F1, const R* __restrict__ E, R* __restrict__ F2, const DtBox* __restrict__ dtb,
+            double gam, double pfloor, TE* __restrict__ Bh0, TE* __restrict__ Bh1, TE* __restrict__ Bh2,
+            R* __restrict__ Wh)
+{
+    constexpr int d = 1;
+    const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (gt >= B.npth[d]) return;
+    const int bi = box_of_pth(B, d, gt);
+    BoxDev g = B.b[bi];
+    g.bc = 0;
+    int na, nb, ns;
+    pencil_dims(g.nx, g.ny, g.nz, d, B.pl, na, nb, ns);
+    long long t = gt - g.pth0[d];
+    const int ia = (int)(t % na);          // x
+    t /= na;
+    const int ib = (int)(t % nb);          // z
+    const int sg = (int)(t / nb);
+    const int n = g.ny, nx = g.nx;
+    const int i0 = sg * B.pl;
+    const int i1 = i0 + B.pl < n ? i0 + B.pl : n;
+    const long long N = B.N;
+    const long long plane = (long long)nx * n;
+    const long long base = g.off + (long long)ib * plane + ia;
+    const long long ox = ia + 1 < nx ? 1 : 1 - nx;
+    const long long oz = ib + 1 < g.nz ? plane : plane - (long long)g.nz * plane;
+    const R gm1 = R(gam - 1.0), gr = R(gam);
+    const R r = DtOf<R>::hdtdx(dtb[bi]);
+    const TE rh = DtOf<TE>::hdtdx(dtb[bi]);
+    const TU ruh = DtOf<TU>::hdtdx(dtb[bi]);
+    R df[2][7], w[7], wpp[7];
+    {
+        const int sj = wrapi(i0 - 1, n);
+        const long long sc = base + (long long)sj * nx;
+#pragma unroll
+        for (int m = 0; m < 7; m++) w[m] = WP[(long long)m * N + sc];
+        ctu_tdiff<R, false, d>(g, ia, sj, ib, sc, F1, nullptr, 0, N, df);
+        ctu_apply<R, d>(w, W[(5 + d) * N + sc], df, r, gm1, wpp);
+    }
+    YCarry<R, TE> Y;
+    yhalf_carry<R, TU, TE>(s, F1, E, N, base + (long long)i0 * nx, ox, oz, Y);
+    for (int p = i0; p < i1; p++) {
+        const long long c = base + (long long)p * nx;
+        const long long cy = base + (long long)wrapi(p + 1, n) * nx;
+        R w8[8];
+        TE lo[3];
+        yhalf_state<R, TU, TE>(s, F1, E, N, c, cy, ox, oz, rh, ruh, gam, pfloor, Y, w8, lo);
+        Bh0[c] = lo[0];
+        Bh1[c] = lo[1];
+        Bh2[c] = lo[2];
+#pragma unroll
+        for (int f = 0; f < 8; f++) Wh[f * N + c] = w8[f];
+        ctu_tdiff<R, false, d>(g, ia, p, ib, c, F1, nullptr, 0, N, df);
+        const R bnc = W[(5 + d) * N + c];
+        const R bface = R(lo[1]);
+        R wm[7], f[7];
+#pragma unroll
+        for (int m = 0; m < 7; m++) w[m] = WM[(long long)m * N + c];
+        ctu_apply<R, d>(w, bnc, df, r, gm1, wm);
+        riemann<SOLVER>(wpp, wm, bface, gm1, gr, f);
+#pragma unroll
+        for (int m = 0; m < 7; m++) F2[(long long)m * N + c] = f[m];
+#pragma unroll
+        for (int m = 0; m < 7; m++) w[m] = WP[(long long)m * N + c];
+        ctu_apply<R, d>(w, bnc, df, r, gm1, wpp);
     }
 }
 

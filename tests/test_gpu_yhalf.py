@@ -369,3 +369,76 @@ def test_mask_range_defaults_and_fallbacks(M):
         assert s.launches_per_step() == 11         # a pressure floor: the primitive pass of its own
     finally:
         s.free()
+
+
+CTU = [("ctu", r, s) for r in ("plm", "ppm") for s in ("roe", "hlld", "hlle")]
+
+
+@pytest.mark.parametrize("scheme", CTU)
+def test_ctu_yhalf_fp64_parity(M, scheme):
+    """CTU with bit 7 (k_ctu_yhalf): the dt/2 update inside the y pencils of
+    the transverse correction, against the oracle"""
+    st = I.abc(None, kmult=1, beta=0.5, seed=110, noise=2e-2, shape=(12, 64, 10))
+    parity(M, st, scheme, 2, mask=39 | 128)
+    parity(M, st, scheme, 2, mask=39 | 128, device_dt=True)
+
+
+@pytest.mark.parametrize("shape", [(8, 40, 12), (6, 33, 9), (5, 2, 9), (9, 1, 7), (3, 3, 1)])
+@pytest.mark.parametrize("plen", [1, 32])
+def test_ctu_yhalf_fp64_parity_ragged_short(M, shape, plen):
+    L = max(shape[1], 1) / 16.0
+    st = I.abc(None, kmult=L, beta=0.5, seed=111, noise=3e-2, shape=shape, L=L)
+    parity(M, st, ("ctu", "plm", "roe"), 2, mask=39 | 128, plen=plen)
+
+
+def test_ctu_yhalf_fp64_batch(M):
+    shapes = [(5, 16, 3), (3, 33, 7), (5, 40, 5), (3, 70, 3)]
+    boxes = [I.abc(None, kmult=1, beta=0.5, seed=120 + k, noise=3e-2, shape=sh) for k, sh in enumerate(shapes)]
+    scheme = ("ctu", "ppm", "hlld")
+    s = M.Solver(None, None, 5 / 3, *scheme, "fp64", 0.3,
+                 shapes=[b.U.shape[1:] for b in boxes], dxs=[b.dx for b in boxes])
+    try:
+        s.set_sweep_pencils(39 | 128, 16)
+        for k, b in enumerate(boxes):
+            s.set_state(b.U, b.B, box=k)
+        dts = np.array([orc.cfl_dt(b.U, b.B, b.dx, b.gamma, 0.3) for b in boxes])
+        s.step(dts)
+        for k, b in enumerate(boxes):
+            U, B = b.U.copy(), b.B.copy()
+            orc.step(U, B, b.dx, b.gamma, float(dts[k]), *scheme)
+            Ug, Bg = s.get_state(box=k)
+            mfloor = 1e-2 * np.abs(U[0]).sum()
+            for f in range(5):
+                den = max(np.abs(U[f]).sum(), mfloor if f in (1, 2, 3) else 0.0)
+                assert np.abs(Ug[f] - U[f]).sum() / den <= 1e-12, (k, f)
+            bfloor = 1e-2 * np.abs(B).sum() / 3
+            for d in range(3):
+                assert np.abs(Bg[d] - B[d]).sum() / max(np.abs(B[d]).sum(), bfloor) <= 1e-12, (k, d)
+    finally:
+        s.free()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+@pytest.mark.parametrize("scheme", [("ctu", "plm", "roe"), ("ctu", "ppm", "hlld")])
+def test_ctu_yhalf_agrees_with_separate_kernels(M, prec, scheme):
+    st = I.abc(None, kmult=1, beta=0.5, seed=112, noise=2e-2, shape=(40, 48, 64))
+    cast = np.float32 if prec == "fp32" else np.float64
+    out = []
+    for mask in (39, 39 | 128):
+        s = M.Solver(st.U.shape[1:], st.dx, st.gamma, *scheme, prec, 0.3)
+        try:
+            s.set_sweep_pencils(mask, 32)
+            assert s.launches_per_step() == (11 if mask & 128 else 12)
+            s.set_state(st.U.astype(cast), st.B.astype(cast))
+            s.advance(3, use_graph=True)
+            out.append(s.get_state())
+        finally:
+            s.free()
+    (Ua, Ba), (Ub, Bb) = out
+    for f in range(5):
+        a, b = Ua[f].astype(np.float64), Ub[f].astype(np.float64)
+        den = max(np.abs(a).sum(), 1e-2 * np.abs(Ua[0]).sum() if f in (1, 2, 3) else 0.0)
+        assert np.abs(a - b).sum() / den <= 1e-5, (prec, scheme, f)
+    for d in range(3):
+        a, b = Ba[d].astype(np.float64), Bb[d].astype(np.float64)
+        assert np.abs(a - b).sum() / np.abs(a).sum() <= 1e-5, (prec, scheme, d)
