@@ -1,4 +1,5 @@
-// mhd_yhalf.cuh -- per-cell passes inside the y pencils of the VL step.
+// mhd_yhalf.cuh -- per-cell passes inside the y and z pencils of the step
+// (VL, and the CTU dt/2 update).
 //
 // k_yhalf: the VL half update (Sec. 3.2, VL step 3: B^{n+1/2} by
 // Eq. 13 and U^{n+1/2} by Eq. 10 with dt/2, and their primitives, Eq. 5)
@@ -13,9 +14,10 @@
 // Riemann solves of other warps.  The thread stores the half-step
 // primitives and the three lower half-step faces of the cells it owns (the
 // x and z corrector sweeps and the corrector's edge fields read them), and
-// the y fluxes.  A segment of pl faces forms pl + 3 half-step states (its
-// lead-in cells i0 - 2, i0 - 1 and the cell past its end): the three extra
-// ones are recomputed where the neighbouring segment owns them.
+// the y fluxes.  A segment of pl faces forms pl + 3 half-step states with
+// PLM (its lead-in cells i0 - 2, i0 - 1 and the cell past its end), pl + 5
+// with PPM (three lead-in cells, two past its end): the extra ones are
+// recomputed where the neighbouring segment owns them.
 //
 // The arithmetic of each half-step state is k_half's (half_faces,
 // flux_divergence, half_prims on the same operands), and of each face the
@@ -50,7 +52,14 @@
 // flux components the corrector's edge fields read (the mass flux and the
 // two field fluxes).  The face field then advances by CT (Eq. 13) in k_ct
 // or k_ct4, which read only E and B.  A segment of pl faces solves pl + 1
-// (its last cell's upper face is the next segment's first).
+// (its last cell's upper face is the next segment's first).  PLM and PPM;
+// in the learned selector's step it is the cheap z corrector, after the full
+// scheme's list pass, whose faces it reads for the segments marked full.
+//
+// k_ctu_yhalf: the CTU dt/2 update (steps 3-4) inside the y pencils of the
+// transverse correction and corrector solve, each owned cell's half-step
+// state formed once (the y correction needs only the cells' own half-step
+// normal field).
 #pragma once
 #include "mhd_kernels.cuh"
 
