@@ -301,10 +301,12 @@ mhd_status mhd_get_dirichlet(mhd_ctx* ctx, int axis, int* nlayers);
  * forms the half-step state of its segment's cells, stores their half-step
  * primitives and faces and corrects its y faces with the cells' half-step
  * normal field; the x and z corrections follow (256^3 FP32 PLM + Roe: 5.32
- * -> 5.22 ms; mixed 7.11 -> 6.79).
+ * -> 5.22 ms; mixed 7.11 -> 6.79).  For CTU, bit 9 with bit 2 (the same
+ * conditions) runs the conservative update inside the z pencils of the
+ * transverse correction, as for VL (FP32: 5.23 -> 5.18 ms).
  * pencil_mask in [0, 1023] (0: tiles everywhere), pencil_len in [1, 1024],
  * else MHD_EINVAL.  Defaults (pencil_len 32): VL FP64 23; VL FP32 743; VL
- * mixed 487 with PLM, 359 with PPM; CTU 167, FP64 39. */
+ * mixed 487 with PLM, 359 with PPM; CTU FP32 679, mixed 167, FP64 39. */
 mhd_status mhd_set_sweep_pencils(mhd_ctx* ctx, int pencil_mask, int pencil_len);
 mhd_status mhd_get_sweep_pencils(mhd_ctx* ctx, int* pencil_mask, int* pencil_len);
 

@@ -313,10 +313,13 @@ static mhd_status init_common(int nbox, const mhd_grid* grids, double gamma, con
     // (144.0 -> 144.8 ms) lose with it.  CTU FP32 and mixed run the dt/2
     // update inside the y pencils of the transverse correction (bit 7; 256^3
     // PLM + Roe 5.32 -> 5.22 ms, PPM + HLLD 6.23 -> 6.09, mixed 7.11 -> 6.79);
-    // FP64 ties (128^3: 24.65 against 24.69 ms) and keeps 39.  The autotuner
-    // may change the mask.
-    if (scheme->integrator != MHD_VL)   // FP32, mixed: the dt/2 update in the y correction (bit 7)
-        c->pencil_mask = scheme->precision == MHD_FP64 ? 39 : 167;
+    // FP64 ties (128^3: 24.65 against 24.69 ms) and keeps 39.  CTU FP32 also
+    // runs the conservative update inside the z correction pencils (bit 9;
+    // 5.23 -> 5.18 ms, PPM + HLLD 6.09 -> 6.06); mixed loses with it (6.79 ->
+    // 6.93 ms).  The autotuner may change the mask.
+    if (scheme->integrator != MHD_VL)   // FP32, mixed: the dt/2 update in the y correction (bit 7),
+        c->pencil_mask = scheme->precision == MHD_FP64 ? 39 : (scheme->precision == MHD_FP32 ? 679 : 167);   // FP32:
+                                        // and the conservative update in the z correction (bit 9)
     else if (scheme->precision == MHD_FP64)
         c->pencil_mask = 23;
     else if (scheme->precision == MHD_FP32)   // PLM: the half update in the y corrector, the conservative
@@ -975,7 +978,9 @@ extern "C" mhd_status mhd_autotune(mhd_ctx* c, int reps, int* tile_len, int* blo
         // corrector pencils, bit 7, when its flux array can be had, and for
         // PLM with the conservative update inside the z corrector, bit 9)
         int vl_masks[12] = {7, 6, 23, 103, 15, 31, 111, 359, 0, 0, 0, 0};
-        const int ctu_masks[4] = {7, 6, 39, 167};      // (167: bit 7, the dt/2 update in the y correction)
+        // (167: bit 7, the dt/2 update in the y correction; 679: and bit 9, the
+        // conservative update in the z correction)
+        const int ctu_masks[5] = {7, 6, 39, 167, 679};
         const bool ctu = c->sch.integrator != MHD_VL;
         const int* masks = ctu ? ctu_masks : vl_masks;
         const int lens[3] = {8, 16, 32};
@@ -996,7 +1001,7 @@ extern "C" mhd_status mhd_autotune(mhd_ctx* c, int reps, int* tile_len, int* blo
                 nvl = 12;
             }
         }
-        const int nmask = ctu ? (!c->bc ? 4 : 3) : (c->sel ? 2 : (!c->bc ? nvl : 4));
+        const int nmask = ctu ? (!c->bc ? 5 : 3) : (c->sel ? 2 : (!c->bc ? nvl : 4));
         c->sweep_bps = bbps;
         for (int i = 0; i < nmask && st == MHD_OK; i++)
             for (int j = 0; j < 3 && st == MHD_OK; j++) {

@@ -307,6 +307,14 @@ inline bool ctu_y_half(const mhd_ctx* c)
     return c->sch.integrator == MHD_CTU && (c->pencil_mask & 130) == 130 && !c->bc && emf_form(c) == 0;
 }
 
+// CTU: the conservative update inside the z pencils of the transverse
+// correction (k_ctu_zfull), CT alone after the edge fields, with pencil-mask
+// bits 2 and 9: periodic boxes, the edge fields as their own kernel
+inline bool ctu_z_full(const mhd_ctx* c)
+{
+    return c->sch.integrator == MHD_CTU && (c->pencil_mask & 516) == 516 && !c->bc && emf_form(c) == 0;
+}
+
 // the learned selector's step: the half update inside the cheap y corrector
 // pencils with pencil-mask bits 1 and 7 (the second flux array allocated,
 // the edge fields as their own kernel)
@@ -630,7 +638,12 @@ void run_step(mhd_ctx* c, bool device_dt)
         prof_mark(c, 7);
         if (!cyh) ctu_correct_axis<R, SOLVER, TE, 1>(c, g, WM, WP, W, F1, Bh[1], F2, gam, fo1, cs, fo2, st);
         prof_mark(c, 8);
-        ctu_correct_axis<R, SOLVER, TE, 2>(c, g, WM, WP, W, F1, Bh[2], F2, gam, fo1, cs, fo2, st);
+        const bool czf = ctu_z_full(c);
+        if (czf)                // with the conservative full update
+            k_ctu_zfull<R, TU, TE, SOLVER><<<pencil_grid(c, 2), PENCIL_THREADS, 0, st>>>(g, s, WM, WP, W, F1, Bh[2],
+                                                                                     F2, c->dtc, gam);
+        else
+            ctu_correct_axis<R, SOLVER, TE, 2>(c, g, WM, WP, W, F1, Bh[2], F2, gam, fo1, cs, fo2, st);
         prof_mark(c, 9);
         // steps 7-8
         if (eu) {
@@ -641,6 +654,8 @@ void run_step(mhd_ctx* c, bool device_dt)
             prof_mark(c, 10);
             if (c->bc)
                 k_full<R, TU, TE, true><<<nb, CELL_THREADS, 0, st>>>(g, s, F2, E, c->dtc, fo2, cs);
+            else if (czf)
+                launch_ct<R, TU, TE>(c, g, s, E, st);
             else
                 launch_full<R, TU, TE>(c, g, s, F2, E, st);
         }

@@ -722,4 +722,103 @@ k_ctu_yhalf(Boxes B, StateP<TU, TE> s, const R* __restrict__ WM, const R* __rest
     }
 }
 
+// CTU (steps 5-7 along z): the transverse correction and corrector solve of
+// the z faces (k_ctu_pencil's arithmetic) with the conservative part of the
+// full update, as k_zfull does for VL: one face past the segment, each cell
+// updated in place once its two z faces are solved, from U^n, the x and y
+// corrector fluxes and its own z fluxes; only the three z flux components
+// the edge fields read are stored.  Periodic boxes.
+template <class R, class TU, class TE, int SOLVER>
+__global__ void __launch_bounds__(PENCIL_THREADS, (sizeof(R) == 4 && SOLVER == ROE ? 4 : 0))
+k_ctu_zfull(Boxes B, StateP<TU, TE> s, const R* __restrict__ WM, const R* __restrict__ WP, const R* __restrict__ W,
+            const R* __restrict__ F1, const TE* __restrict__ Bhz, R* __restrict__ F2, const DtBox* __restrict__ dtb,
+            double gam)
+{
+    constexpr int d = 2;
+    const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (gt >= B.npth[d]) return;
+    const int bi = box_of_pth(B, d, gt);
+    BoxDev g = B.b[bi];
+    g.bc = 0;
+    int na, nb, ns;
+    pencil_dims(g.nx, g.ny, g.nz, d, B.pl, na, nb, ns);
+    long long t = gt - g.pth0[d];
+    const int ia = (int)(t % na);          // x
+    t /= na;
+    const int ib = (int)(t % nb);          // y
+    const int sg = (int)(t / nb);
+    const int n = g.nz;
+    const int i0 = sg * B.pl;
+    const int i1 = i0 + B.pl < n ? i0 + B.pl : n;
+    const long long N = B.N;
+    const long long plane = (long long)g.nx * g.ny;
+    const long long base = g.off + (long long)ib * g.nx + ia;      // cell (x, y, 0)
+    const long long ox = ia + 1 < g.nx ? 1 : 1 - g.nx;
+    const long long oy = ib + 1 < g.ny ? g.nx : g.nx - (long long)g.ny * g.nx;
+    const R gm1 = R(gam - 1.0), gr = R(gam);
+    const R r = DtOf<R>::hdtdx(dtb[bi]);
+    const TE rf = DtOf<TE>::dtdx(dtb[bi]);
+    const TU ruf = DtOf<TU>::dtdx(dtb[bi]);
+    const R* WMd = WM + 14 * N;
+    const R* WPd = WP + 14 * N;
+    R* Fz = F2 + 14 * N;
+    R df[2][7], w[7], wpp[7], f[7], fprev[7];
+    {
+        const int sk = wrapi(i0 - 1, n);
+        const long long sc = base + (long long)sk * plane;
+#pragma unroll
+        for (int m = 0; m < 7; m++) w[m] = WPd[(long long)m * N + sc];
+        ctu_tdiff<R, false, d>(g, ia, ib, sk, sc, F1, nullptr, 0, N, df);
+        ctu_apply<R, d>(w, W[(5 + d) * N + sc], df, r, gm1, wpp);
+    }
+    for (int p = i0; p <= i1; p++) {
+        const int k = p < n ? p : p - n;
+        const long long c = base + (long long)k * plane;
+        ctu_tdiff<R, false, d>(g, ia, ib, k, c, F1, nullptr, 0, N, df);
+        const R bnc = W[(5 + d) * N + c];
+        R wm[7];
+#pragma unroll
+        for (int m = 0; m < 7; m++) w[m] = WMd[(long long)m * N + c];
+        ctu_apply<R, d>(w, bnc, df, r, gm1, wm);
+        riemann<SOLVER>(wpp, wm, R(Bhz[c]), gm1, gr, f);
+        if (p < i1) {                       // the components the edge fields read
+            Fz[c] = f[0];
+            Fz[5 * N + c] = f[5];
+            Fz[6 * N + c] = f[6];
+        }
+        if (p > i0) {                       // cell p - 1 between faces p - 1 and p
+            const long long cc = base + (long long)(p - 1) * plane;
+            R fc[3][5], fn[3][5];
+#pragma unroll
+            for (int m = 0; m < 5; m++) {
+                fc[0][m] = F2[(long long)m * N + cc];
+                fn[0][m] = F2[(long long)m * N + cc + ox];
+                fc[1][m] = F2[(7LL + m) * N + cc];
+                fn[1][m] = F2[(7LL + m) * N + cc + oy];
+                fc[2][m] = fprev[m];
+                fn[2][m] = f[m];
+            }
+            const TU rho0 = s.rho[cc], mx0 = s.m[0][cc], my0 = s.m[1][cc], mz0 = s.m[2][cc];
+            const TE e0 = s.e[cc];
+            TU du[4];
+            TE due;
+            flux_divergence<R, TU, TE>(fc, fn, du, due);
+            TU u[4];
+            TE e;
+            full_hydro<TU, TE>(rho0, mx0, my0, mz0, e0, du, due, ruf, rf, u, e);
+            s.rho[cc] = u[0];
+            s.m[0][cc] = u[1];
+            s.m[1][cc] = u[2];
+            s.m[2][cc] = u[3];
+            s.e[cc] = e;
+        }
+        copy7(fprev, f);
+        if (p < i1) {
+#pragma unroll
+            for (int m = 0; m < 7; m++) w[m] = WPd[(long long)m * N + c];
+            ctu_apply<R, d>(w, bnc, df, r, gm1, wpp);
+        }
+    }
+}
+
 }  // namespace mhd

@@ -300,7 +300,7 @@ def test_xmarch_mask_range_and_precedence(M):
         s.free()
     for prec, scheme, mask in [("fp32", ("vl", "plm", "roe"), 743), ("fp32", ("vl", "plm_prim", "hlle"), 743),
                                ("fp32", ("vl", "ppm", "hlld"), 743), ("mixed", ("vl", "plm", "roe"), 487),
-                               ("fp32", ("ctu", "plm", "roe"), 167), ("fp64", ("ctu", "plm", "roe"), 39)]:
+                               ("fp32", ("ctu", "plm", "roe"), 679), ("fp64", ("ctu", "plm", "roe"), 39)]:
         s = M.Solver(st.U.shape[1:], st.dx, st.gamma, *scheme, prec, 0.3)
         try:
             assert s.sweep_pencils() == (mask, 32), (prec, scheme)

@@ -383,12 +383,23 @@ def test_ctu_yhalf_fp64_parity(M, scheme):
     parity(M, st, scheme, 2, mask=39 | 128, device_dt=True)
 
 
+@pytest.mark.parametrize("scheme", CTU)
+def test_ctu_zfull_fp64_parity(M, scheme):
+    """CTU with bit 9 (k_ctu_zfull): the conservative update inside the z
+    pencils of the transverse correction, alone and with bit 7"""
+    st = I.abc(None, kmult=1, beta=0.5, seed=113, noise=2e-2, shape=(12, 10, 64))
+    parity(M, st, scheme, 2, mask=39 | ZFULL)
+    parity(M, st, scheme, 2, mask=39 | 128 | ZFULL, device_dt=True)
+
+
 @pytest.mark.parametrize("shape", [(8, 40, 12), (6, 33, 9), (5, 2, 9), (9, 1, 7), (3, 3, 1)])
 @pytest.mark.parametrize("plen", [1, 32])
 def test_ctu_yhalf_fp64_parity_ragged_short(M, shape, plen):
     L = max(shape[1], 1) / 16.0
     st = I.abc(None, kmult=L, beta=0.5, seed=111, noise=3e-2, shape=shape, L=L)
     parity(M, st, ("ctu", "plm", "roe"), 2, mask=39 | 128, plen=plen)
+    st = I.abc(None, kmult=L, beta=0.5, seed=114, noise=3e-2, shape=(shape[0], shape[2], shape[1]), L=L)
+    parity(M, st, ("ctu", "ppm", "hlle"), 2, mask=39 | 128 | ZFULL, plen=plen)
 
 
 def test_ctu_yhalf_fp64_batch(M):
@@ -398,7 +409,7 @@ def test_ctu_yhalf_fp64_batch(M):
     s = M.Solver(None, None, 5 / 3, *scheme, "fp64", 0.3,
                  shapes=[b.U.shape[1:] for b in boxes], dxs=[b.dx for b in boxes])
     try:
-        s.set_sweep_pencils(39 | 128, 16)
+        s.set_sweep_pencils(39 | 128 | ZFULL, 16)
         for k, b in enumerate(boxes):
             s.set_state(b.U, b.B, box=k)
         dts = np.array([orc.cfl_dt(b.U, b.B, b.dx, b.gamma, 0.3) for b in boxes])
@@ -424,7 +435,7 @@ def test_ctu_yhalf_agrees_with_separate_kernels(M, prec, scheme):
     st = I.abc(None, kmult=1, beta=0.5, seed=112, noise=2e-2, shape=(40, 48, 64))
     cast = np.float32 if prec == "fp32" else np.float64
     out = []
-    for mask in (39, 39 | 128):
+    for mask in (39, 39 | 128 | ZFULL):
         s = M.Solver(st.U.shape[1:], st.dx, st.gamma, *scheme, prec, 0.3)
         try:
             s.set_sweep_pencils(mask, 32)
