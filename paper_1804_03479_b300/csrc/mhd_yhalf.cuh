@@ -144,7 +144,10 @@ __device__ __forceinline__ void yhalf_carry(const StateP<TU, TE>& s, const R* __
 
 // register bound: as the PLM corrector pencils it extends (FP32 Roe: 4
 // blocks of 128 threads, 128 registers with 16 bytes spilled; at 3 blocks
-// and 167 registers it ran 0.760 against 0.708 ms at 256^3)
+// and 167 registers it ran 0.760 against 0.708 ms at 256^3, at 5 blocks and
+// 96 registers, 128 bytes spilled, 0.835 against 0.705; the z and CTU forms
+// lost likewise at 5 blocks: 0.84 against 0.68 ms, CTU step 5.67 against
+// 5.18 ms)
 template <class R, int RECON, int SOLVER>
 constexpr int yhalf_min_blocks()
 {
